@@ -1,0 +1,136 @@
+/*
+ * hd.h -- C ABI of the GB300 Householder Dice library (libhd.so).
+ *
+ * Householder Dice (Y. M. Lu, arXiv 2101.07464) simulates the dynamics of eq. (dynamics),
+ *     x_{t+1} = f_t(M_t x_t, x_t, ..., x_{t-d}),   M_t in {Q, Q^T},
+ * for a random Q from the Ginibre ensemble Gin(m, n) (Algorithm 1, Section 3.2) or the
+ * Haar ensemble on O(n) (Algorithm 2, Section 3.3) without ever forming Q: each call
+ * reveals only the randomness the current product needs, applies the stored Householder
+ * reflectors and appends new ones, for O((m+n)T) memory and O((m+n)T^2) work.
+ * The caller owns the dynamics f_t and chooses M_t at every step.
+ *
+ * Conventions of every entry point:
+ *   - Return value: an hd_status (0 = HD_OK).  Functions never abort the process.
+ *   - Pointers named x, y, out are DEVICE pointers (cudaMalloc / torch CUDA tensors) on
+ *     the current CUDA device, unless the name ends in _host.  They are caller-owned;
+ *     the library keeps no reference after the call returns.
+ *   - Work is enqueued on the state's CUDA stream (hd_set_options; default stream 0) and
+ *     is asynchronous: results are ready when that stream is synchronised.  Calls on one
+ *     state must be ordered on one stream; distinct states are independent.
+ *   - Layout: vectors are dense, contiguous, 8-byte (HD_F64) or 4-byte (HD_F32) elements.
+ *     Buffers aligned to 16 bytes take the vectorised path; others are accepted and take
+ *     a scalar path.
+ *   - After an error inside a step (HD_ERR_CUDA, HD_ERR_TIMEOUT) the state is poisoned:
+ *     every later hd_apply returns the same code until hd_reset.
+ */
+#ifndef HD_H
+#define HD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define HD_API __attribute__((visibility("default")))
+#else
+#define HD_API
+#endif
+
+typedef struct hd_state hd_state;
+
+typedef enum {
+  HD_OK = 0,
+  HD_ERR_ARG = 1,      /* null or invalid argument (bad enum, non-finite sigma, ...)      */
+  HD_ERR_DIM = 2,      /* non-positive sizes, or m != n for the Haar ensemble            */
+  HD_ERR_TMAX = 3,     /* the step would exceed T_max, or T_max > min(m, n) (Alg. 1) /
+                          T_max > n (Alg. 2)                                              */
+  HD_ERR_OOM = 4,      /* device allocation failed                                        */
+  HD_ERR_CUDA = 5,     /* a CUDA call or kernel launch failed                             */
+  HD_ERR_TIMEOUT = 6,  /* a bounded device-side wait expired                              */
+  HD_ERR_STATE = 7     /* the state was poisoned by an earlier error                     */
+} hd_status;
+
+typedef enum { HD_GINIBRE = 0, HD_HAAR = 1 } hd_ensemble;
+/* HD_F64: vectors, reflector stacks and all arithmetic in FP64.
+ * HD_F32: vectors and reflector stacks stored and streamed in FP32 with FP32 math; the
+ *         cross-warp/cross-block sums of every dot product and norm, the Householder
+ *         coefficients and the compact-WY triangular factor S stay in FP64.            */
+typedef enum { HD_F64 = 0, HD_F32 = 1 } hd_dtype;
+
+/* Create a state for y = M_t x with Q ~ Gin(m, n) (entries sigma * N(0,1), sigma = 1 by
+ * default: Section 3 notation) or Q ~ Haar(n) (requires m == n).  T_max bounds the number
+ * of products: T_max <= min(m, n) for Gin (Algorithm 1 requires T <= min(m, n)), T_max <= n
+ * for Haar (Algorithm 2 requires T <= n); this library also caps T_max at 1024 (FP32) and at
+ * the largest value whose K2 shared-memory tile fits (about 850 for FP64).  Allocates all device memory up front:
+ * two reflector stacks (n x T_max and m x T_max elements), for Gin two basis stores of the
+ * same sizes, and O(T_max^2) FP64 coefficients.  seed keys the Philox4x32-10 generator
+ * that draws the Gaussian vectors g_t (key = seed, counter = (index/2, t, trial, 0)).
+ * *out receives the state (owned by the caller; release with hd_destroy). */
+HD_API int hd_create(int ensemble, int64_t m, int64_t n, int32_t T_max, uint64_t seed,
+                     int dtype, hd_state** out);
+
+/* Options; take effect from the next step.  sigma: entry standard deviation of the
+ * Ginibre ensemble (> 0, finite; ignored for Haar, whose reflector H(g) does not depend on
+ * the scale of g).  trial: the Philox counter word that separates independent trials
+ * sharing one seed.  stream: a cudaStream_t (NULL = legacy default stream).
+ * Changing sigma or trial after the first step returns HD_ERR_ARG (the draws of one
+ * matrix must come from one stream of randomness); call hd_reset first. */
+HD_API int hd_set_options(hd_state* st, double sigma, uint32_t trial, void* stream);
+
+/* One product of eq. (dynamics): y = M_t x with M_t = Q (transpose = 0; x in R^n,
+ * y in R^m) or M_t = Q^T (transpose = 1; x in R^m, y in R^n), for the t-th call since
+ * create/reset (Algorithm 1 lines for M_t = Q / Q^T; Algorithm 2).  Draws g_t, extends the
+ * reflector stacks by the new reflector(s) and writes y.  x and y must not overlap.
+ * Errors: HD_ERR_TMAX when t would exceed T_max (state unchanged), HD_ERR_ARG for null
+ * pointers or a bad transpose flag. */
+HD_API int hd_apply(hd_state* st, const void* x, int transpose, void* y);
+
+/* Consistency probe (does not add a step): y = Q^(t) x (or its transpose) using only the
+ * revealed part of the current representation (eq. Gaussian_t for Gin, eq. H_t for Haar),
+ * and *unrevealed_host = the norm of the component of x that the hidden block would see
+ * (||Z_{1:r} R_r...R_1 x|| for Q); y equals M x exactly when it is zero, e.g. for any
+ * earlier input x_s of the same direction, or Q^T applied to an earlier output.
+ * Synchronises the state's stream (the norm is returned on the host). */
+HD_API int hd_probe(hd_state* st, const void* x, int transpose, void* y,
+                    double* unrevealed_host);
+
+/* Forget all steps (t = r = l = 0) and re-key the generator with seed; keeps the
+ * allocations and options.  Clears a poisoned state. */
+HD_API int hd_reset(hd_state* st, uint64_t seed);
+
+/* Release the state and its device memory (synchronises its stream).  NULL is allowed. */
+HD_API void hd_destroy(hd_state* st);
+
+/* Step counters: *t = products so far, *r = number of Q products, *l = number of Q^T
+ * products (r + l = t; for Haar both stacks hold t reflectors). */
+HD_API int hd_get_counts(const hd_state* st, int32_t* t, int32_t* r, int32_t* l);
+
+/* Device bytes allocated by the state. */
+HD_API int hd_get_device_bytes(const hd_state* st, int64_t* bytes);
+
+/* Text of the last CUDA failure seen by a call of this library in the calling thread
+ * (empty if none); valid until the next failing call in that thread. */
+HD_API const char* hd_last_error(void);
+
+/* Human-readable name of a status code (static string). */
+HD_API const char* hd_status_string(int status);
+
+/* The library's Gaussian draws, exposed for checking the generator:
+ * out[k] = the normal of absolute index start+k of (seed, trial, step, stream), as
+ * defined for hd_create (Box-Muller on 53-bit uniforms in FP64 for HD_F64; the same
+ * Philox words through a 32-bit Box-Muller for HD_F32).  out is a device buffer of count
+ * elements of the dtype.  Enqueued on `stream`. */
+HD_API int hd_philox_normals(uint64_t seed, uint32_t trial, uint32_t step, uint32_t stream_id,
+                             int64_t start, int64_t count, int dtype, void* out, void* stream);
+
+/* Raw Philox4x32-10 words: for block b < nblocks, counter = counters[4b .. 4b+3] and key =
+ * seed; out[4b .. 4b+3] = the four output words.  Both are device buffers. */
+HD_API int hd_philox_words(uint64_t seed, const uint32_t* counters, int64_t nblocks,
+                           uint32_t* out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HD_H */

@@ -1,0 +1,214 @@
+"""Thin ctypes binding of libhd.so (include/hd.h), with the same names as the C ABI.
+
+Argument marshalling only: torch CUDA tensors are checked (device, dtype, length,
+contiguity) and passed as raw device pointers; every step of the computation runs in the
+library's CUDA kernels.  There is no CPU fallback: if the library is missing or cannot be
+loaded, every call raises.
+"""
+import ctypes
+import os
+
+from . import build as _build
+
+HD_GINIBRE, HD_HAAR = 0, 1
+HD_F64, HD_F32 = 0, 1
+HD_OK, HD_ERR_ARG, HD_ERR_DIM, HD_ERR_TMAX = 0, 1, 2, 3
+HD_ERR_OOM, HD_ERR_CUDA, HD_ERR_TIMEOUT, HD_ERR_STATE = 4, 5, 6, 7
+
+ENSEMBLES = {"ginibre": HD_GINIBRE, "haar": HD_HAAR}
+DTYPES = {"f64": HD_F64, "f32": HD_F32}
+
+_LIB = None
+
+_c = ctypes
+_P = _c.c_void_p
+_PROTOS = {
+    "hd_create": (_c.c_int, [_c.c_int, _c.c_int64, _c.c_int64, _c.c_int32, _c.c_uint64, _c.c_int,
+                             _c.POINTER(_P)]),
+    "hd_set_options": (_c.c_int, [_P, _c.c_double, _c.c_uint32, _P]),
+    "hd_apply": (_c.c_int, [_P, _P, _c.c_int, _P]),
+    "hd_probe": (_c.c_int, [_P, _P, _c.c_int, _P, _c.POINTER(_c.c_double)]),
+    "hd_reset": (_c.c_int, [_P, _c.c_uint64]),
+    "hd_destroy": (None, [_P]),
+    "hd_get_counts": (_c.c_int, [_P, _c.POINTER(_c.c_int32), _c.POINTER(_c.c_int32),
+                                 _c.POINTER(_c.c_int32)]),
+    "hd_get_device_bytes": (_c.c_int, [_P, _c.POINTER(_c.c_int64)]),
+    "hd_status_string": (_c.c_char_p, [_c.c_int]),
+    "hd_last_error": (_c.c_char_p, []),
+    "hd_philox_normals": (_c.c_int, [_c.c_uint64, _c.c_uint32, _c.c_uint32, _c.c_uint32, _c.c_int64,
+                                     _c.c_int64, _c.c_int, _P, _P]),
+    "hd_philox_words": (_c.c_int, [_c.c_uint64, _P, _c.c_int64, _P, _P]),
+}
+
+
+class HDError(RuntimeError):
+    def __init__(self, code, where=""):
+        self.code = code
+        msg = lib().hd_status_string(code).decode() if _LIB is not None else str(code)
+        if code in (HD_ERR_CUDA, HD_ERR_TIMEOUT) and _LIB is not None:
+            msg += " (%s)" % lib().hd_last_error().decode()
+        super().__init__("%s%s" % (where + ": " if where else "", msg))
+
+
+def library_path():
+    return _build.LIB
+
+
+def lib():
+    """Load libhd.so (built in-tree by paper_2101_07464_gb300.build); raises if absent."""
+    global _LIB
+    if _LIB is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError("libhd.so is not built (%s); run paper_2101_07464_gb300.build.build() "
+                               "or __graft_entry__.build() first" % path)
+        L = ctypes.CDLL(path)
+        for name, (res, args) in _PROTOS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def _check(rc, where):
+    if rc != HD_OK:
+        raise HDError(rc, where)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream or None
+    return stream.cuda_stream or None  # torch.cuda.Stream
+
+
+def _ptr(t, dtype_code=None, numel=None, what="tensor"):
+    """Raw device pointer of a contiguous CUDA tensor (or an int address)."""
+    if isinstance(t, int):
+        return t
+    import torch
+    if not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % what)
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % what)
+    if dtype_code is not None:
+        want = torch.float64 if dtype_code == HD_F64 else torch.float32
+        if t.dtype != want:
+            raise ValueError("%s must be %s" % (what, want))
+    if numel is not None and t.numel() != numel:
+        raise ValueError("%s must have %d elements, got %d" % (what, numel, t.numel()))
+    return t.data_ptr()
+
+
+def hd_create(ensemble, m, n, T_max, seed, dtype):
+    ens = ENSEMBLES.get(ensemble, ensemble)
+    dt = DTYPES.get(dtype, dtype)
+    h = _P()
+    _check(lib().hd_create(ens, m, n, T_max, seed & 0xFFFFFFFFFFFFFFFF, dt, ctypes.byref(h)),
+           "hd_create")
+    return h
+
+
+def hd_set_options(state, sigma=1.0, trial=0, stream=None):
+    _check(lib().hd_set_options(state, sigma, trial, _stream_ptr(stream)), "hd_set_options")
+
+
+def hd_apply(state, x, transpose, y):
+    _check(lib().hd_apply(state, _ptr(x, what="x"), int(bool(transpose)), _ptr(y, what="y")), "hd_apply")
+
+
+def hd_probe(state, x, transpose, y):
+    u = ctypes.c_double()
+    _check(lib().hd_probe(state, _ptr(x, what="x"), int(bool(transpose)), _ptr(y, what="y"),
+                          ctypes.byref(u)), "hd_probe")
+    return u.value
+
+
+def hd_reset(state, seed):
+    _check(lib().hd_reset(state, seed & 0xFFFFFFFFFFFFFFFF), "hd_reset")
+
+
+def hd_destroy(state):
+    if state:
+        lib().hd_destroy(state)
+
+
+def hd_get_counts(state):
+    t, r, l = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().hd_get_counts(state, ctypes.byref(t), ctypes.byref(r), ctypes.byref(l)),
+           "hd_get_counts")
+    return t.value, r.value, l.value
+
+
+def hd_get_device_bytes(state):
+    b = ctypes.c_int64()
+    _check(lib().hd_get_device_bytes(state, ctypes.byref(b)), "hd_get_device_bytes")
+    return b.value
+
+
+def hd_philox_normals(seed, trial, step, stream_id, start, count, dtype, out, stream=None):
+    dt = DTYPES.get(dtype, dtype)
+    _check(lib().hd_philox_normals(seed & 0xFFFFFFFFFFFFFFFF, trial, step, stream_id, start, count,
+                                   dt, _ptr(out, dt, count, "out"), _stream_ptr(stream)),
+           "hd_philox_normals")
+
+
+def hd_philox_words(seed, counters, nblocks, out, stream=None):
+    _check(lib().hd_philox_words(seed & 0xFFFFFFFFFFFFFFFF, _ptr(counters, what="counters"), nblocks,
+                                 _ptr(out, what="out"), _stream_ptr(stream)), "hd_philox_words")
+
+
+class HD:
+    """Convenience owner of one hd_state: y = M_t x through hd_apply.
+
+    HD("haar", n, n, T_max, seed, "f32").apply(x, transpose) returns a new CUDA tensor.
+    Work goes on torch's current CUDA stream at construction (or `stream`).
+    """
+
+    def __init__(self, ensemble, m, n, T_max, seed, dtype="f64", sigma=1.0, trial=0, stream=None):
+        import torch
+        self.ensemble, self.m, self.n, self.T_max = ensemble, m, n, T_max
+        self.dtype_code = DTYPES.get(dtype, dtype)
+        self.torch_dtype = torch.float64 if self.dtype_code == HD_F64 else torch.float32
+        self.h = hd_create(ensemble, m, n, T_max, seed, self.dtype_code)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        hd_set_options(self.h, sigma, trial, stream)
+
+    def apply(self, x, transpose=False, out=None):
+        import torch
+        dim_in, dim_out = (self.m, self.n) if transpose else (self.n, self.m)
+        _ptr(x, self.dtype_code, dim_in, "x")
+        if out is None:
+            out = torch.empty(dim_out, dtype=self.torch_dtype, device=x.device)
+        else:
+            _ptr(out, self.dtype_code, dim_out, "out")
+        hd_apply(self.h, x, transpose, out)
+        return out
+
+    def probe(self, x, transpose=False):
+        import torch
+        dim_out = self.n if transpose else self.m
+        out = torch.empty(dim_out, dtype=self.torch_dtype, device=x.device)
+        u = hd_probe(self.h, x, transpose, out)
+        return out, u
+
+    def reset(self, seed):
+        hd_reset(self.h, seed)
+
+    def counts(self):
+        return hd_get_counts(self.h)
+
+    def close(self):
+        if self.h:
+            hd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

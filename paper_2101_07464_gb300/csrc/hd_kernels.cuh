@@ -1,0 +1,116 @@
+// Kernel argument blocks and launchers of the Householder Dice step (sm_103a).
+//
+// Representation (Remark after Algorithm 1: products of reflectors in compact storage,
+// Schreiber & Van Loan).  A stack of k generalised reflectors H_j(a_j) = D_j P_j, j = 0..k-1
+// (0-based pivot j), with P_j = I - tau_j u_j u_j^T, u_j = a_j[j:] + s_j ||a_j[j:]|| e_j and
+// D_j = diag(I_j, -s_j I) (the scalar -sign of eq. Householder), is kept as
+//   V = [u_0 .. u_{k-1}]           column-major, dim x T_max, column j zero above row j,
+//   S   (k x k, upper triangular)  P_0 P_1 ... P_{k-1} = I - V S V^T,
+//   G = V^T V                      (k x k, FP64),
+//   dpre[q] = prod_{j<q} (-s_j)    (D_j commutes with P_i for i >= j, so the signs collect
+//                                   into the diagonal Delta_k[i] = dpre[min(i, k-1) + 1]).
+// Then   H_{k-1}...H_0 = Delta_k (I - V S^T V^T)      ("forward" product, first acts first)
+//        H_0...H_{k-1} = (I - V S V^T) Delta_k        ("backward" product).
+// A step needs two streaming passes over the data-side stack (z = V^T x, then
+// p = Delta (x - V S^T z)) and one over the other stack (the output), see hd_kernels.cu.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "hd_common.cuh"
+
+namespace hd {
+
+// Offsets of the FP64 scalar slots in Ws::scal.
+enum ScalSlot {
+  kPpiv = 0,     // data-side p at the pivot row
+  kAlpha = 1,    // ||p[k:]||
+  kCoef = 2,     // Haar: alpha / ||g[k:]||
+  kUpivG = 3,    // Haar: pivot entry of the new random-side reflector vector
+  kGFlag = 4,    // Haar: 1 when g[k:] = 0 (the random reflector is the identity)
+  kErr = 5,      // device error word (0 = fine)
+  kNumScal = 8
+};
+
+struct StackDev {
+  void* V;        // T*, column-major, dim x Tm with leading dimension ld
+  int64_t ld;
+  int64_t dim;
+  double* S;      // Tm x Tm, S[i + j*Tm], upper triangular
+  double* dpre;   // Tm + 1 prefix signs, dpre[0] = 1
+  void* gbuf;     // T*, dim: the next Gaussian draw in this stack's space (rows >= count)
+  double* gdot;   // Tm + 1: dots of gbuf with the stack's columns (rows >= count)
+  double* gg;     // 1: squared norm of gbuf over rows >= count + 1 (pivot excluded)
+};
+
+struct Ws {
+  double* z;      // 2 Tm: x . data-stack columns, then x . data-space basis columns (Ginibre)
+  double* w;      // Tm: S^T z
+  double* phead;  // Tm + 1: p rows < k
+  double* wout;   // Tm: output coefficients (Haar w'; Ginibre w_h)
+  double* wout2;  // Tm: Ginibre w_2
+  double* scrb;   // 4 scratch vectors of scr_stride doubles (V^T u, top-block products, sums)
+  int64_t scr_stride;
+  double* scal;   // kNumScal
+  double* part;   // per-CTA partial sums
+  double* gpart;  // per-group partial sums
+  unsigned int* cnt;  // election counters: [3][kMaxGroups + 1]
+  __device__ __forceinline__ double* scr(int i) const { return scrb + i * scr_stride; }
+};
+constexpr int kMaxGroups = 512;
+
+struct Grid {
+  int ctas;         // CTAs of the sweep
+  int64_t vpc;      // 16-byte vectors per CTA
+  int gsize;        // CTAs per election group
+  int ngroups;
+};
+
+// The three sweeps of one step plus the first draw; T = float or double.
+template <typename T>
+struct StepPlan {
+  int ens;              // 0 Ginibre, 1 Haar
+  int Tm;
+  int kD, kN;           // reflectors in the data / other stack before the step
+  StackDev D, N;        // data-side and other stack
+  void* Bd;             // Ginibre: basis columns living in the data space (kN of them)
+  int64_t ldBd;
+  void* Bn;             // Ginibre: basis columns living in the other space (kD + 1 after)
+  int64_t ldBn;
+  const T* x;
+  int xal;
+  T* y;
+  int yal;
+  Ws ws;
+  DrawKey key_next;     // the next step's draw (t + 1)
+  T sigma;              // entry scale of the draws (Ginibre), 1 for Haar
+  Grid g1, g2, g3;      // launch shapes of the three sweeps
+  int R2;               // rows per shared-memory tile of K2
+  int64_t ntiles2;      // tiles of K2
+};
+
+// Dynamic shared memory of K2 for k columns and R-row tiles.
+template <typename T>
+inline size_t update_smem_bytes(int k, int R) {
+  return ((size_t)k * (R + 1) + 2 * (size_t)R + kThreads + (size_t)k) * sizeof(T);
+}
+
+template <typename T>
+cudaError_t launch_first_draw(StackDev X, int64_t count, DrawKey key, T sigma, Ws ws,
+                              int cnt_set, Grid g, cudaStream_t s);
+template <typename T>
+cudaError_t launch_step(const StepPlan<T>& p, cudaStream_t s);
+template <typename T>
+cudaError_t launch_probe(const StepPlan<T>& p, double* q, double* unrevealed, cudaStream_t s);
+
+template <typename T>
+int kernel_occupancy(int which, size_t dynsmem);
+template <typename T>
+cudaError_t set_update_smem_limit(int bytes);
+
+cudaError_t launch_philox_normals(DrawKey key, int64_t start, int64_t count, int dtype, void* out,
+                                  cudaStream_t s);
+cudaError_t launch_philox_words(uint32_t k0, uint32_t k1, const uint32_t* ctr, int64_t nblocks,
+                                uint32_t* out, cudaStream_t s);
+
+}  // namespace hd

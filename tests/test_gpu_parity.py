@@ -1,0 +1,183 @@
+"""GPU parity: the CUDA path (through the C ABI) against the oracle on the same inputs.
+
+* Philox words bit-exact; normals to rounding (FP64) or FP32 Box-Muller accuracy.
+* Haar (Algorithm 2) and Ginibre (Algorithm 1), FP64 and FP32-storage, teacher-forced:
+  per step ||y_gpu - y_oracle|| / ||y_oracle|| <= 1e-12 (FP64) or 1e-5 (FP32).
+  Sizes span one to several CTAs, ragged ends (dim % 4 != 0), tiny and T = n cases,
+  Q / Q^T schedules, rectangular m != n, sigma scaling, and a zero input (H = I).
+"""
+import numpy as np
+import pytest
+
+from gpu_util import TOL, teacher_forced
+from oracle import philox
+from oracle.dynamics import f_sign_mem, f_tanh
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+ALT = lambda t: t % 2 == 0
+ALLQ = lambda t: False
+MIXED = lambda t: t in (2, 3, 7, 8, 9, 14)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def test_philox_words_bit_exact():
+    import paper_2101_07464_gb300 as hd
+    rng = np.random.default_rng(0)
+    nb = 100_000
+    ctr = rng.integers(0, 2 ** 32, size=(nb, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[:10] = 0
+    ctr[10:20] = 0xFFFFFFFF
+    seed = 0x0123456789ABCDEF
+    dctr = torch.tensor(ctr.view(np.int32), device="cuda")
+    out = torch.empty(nb * 4, dtype=torch.int32, device="cuda")
+    hd.hd_philox_words(seed, dctr.data_ptr(), nb, out.data_ptr())
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().view(np.uint32).reshape(nb, 4)
+    ref = np.stack(philox.philox4x32(ctr[:, 0], ctr[:, 1], ctr[:, 2], ctr[:, 3], seed), 1)
+    np.testing.assert_array_equal(got, ref.astype(np.uint32))
+
+
+@pytest.mark.parametrize("start,count", [(0, 1000), (1, 999), (77, 4097), (1_000_000, 3)])
+def test_philox_normals(start, count):
+    import paper_2101_07464_gb300 as hd
+    ref = philox.normals(11, 3, 5, start, count, stream=0)
+    o64 = torch.empty(count, dtype=torch.float64, device="cuda")
+    hd.hd_philox_normals(11, 3, 5, 0, start, count, "f64", o64)
+    o32 = torch.empty(count, dtype=torch.float32, device="cuda")
+    hd.hd_philox_normals(11, 3, 5, 0, start, count, "f32", o32)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(o64.cpu().numpy(), ref, rtol=0, atol=1e-13)
+    # 32-bit Box-Muller of the same words: absolute error a few float ulps of |z| <= 9
+    np.testing.assert_allclose(o32.double().cpu().numpy(), ref, rtol=0, atol=5e-6)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("n,T,sched", [
+    (8, 8, MIXED), (17, 12, ALT), (33, 20, ALLQ), (1000, 16, ALT), (5003, 24, MIXED),
+    (100_003, 12, ALT), (262_147, 8, ALLQ)])
+def test_haar_teacher_forced(dtype, n, T, sched):
+    errs = teacher_forced("haar", n, n, T, seed=1234 + n, dtype=dtype, schedule=sched)
+    assert errs.max() <= TOL[dtype], errs
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("m,n,T,sched,sigma", [
+    (8, 8, 8, ALLQ, 1.0), (13, 9, 9, MIXED, 0.5), (9, 13, 9, ALT, 1.0),
+    (1000, 1000, 10, ALLQ, 1000 ** -0.5), (2003, 4001, 20, ALT, 2003 ** -0.5),
+    (50_001, 100_003, 12, MIXED, 50_001 ** -0.5)])
+def test_ginibre_teacher_forced(dtype, m, n, T, sched, sigma):
+    errs = teacher_forced("ginibre", m, n, T, seed=99 + m, dtype=dtype, schedule=sched, sigma=sigma)
+    assert errs.max() <= TOL[dtype], errs
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_ginibre_small_config_trajectory(dtype):
+    """Gin(1000, 1000), entries N(0, 1/n), T = 10, all Q, x_{t+1} = tanh(Q x_t)."""
+    n = 1000
+    errs = teacher_forced("ginibre", n, n, 10, seed=1, dtype=dtype, schedule=ALLQ,
+                          sigma=n ** -0.5, dynamics=lambda y, x, xp: f_tanh(y, x, xp))
+    assert errs.max() <= TOL[dtype], errs
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_haar_sign_dynamics(dtype):
+    """x_{t+1} = sign(M_t x_t) + 0.5 x_{t-1}, alternating Q / Q^T (the large Haar workload's
+    dynamics at a reduced size)."""
+    n = 20_000
+
+    def f(y, x, xp):
+        return f_sign_mem(y, x, np.zeros_like(x) if xp is None else xp)
+    errs = teacher_forced("haar", n, n, 30, seed=5, dtype=dtype, schedule=ALT, dynamics=f)
+    assert errs.max() <= TOL[dtype], errs
+
+
+@pytest.mark.parametrize("ens", ["haar", "ginibre"])
+def test_zero_input_gives_zero_and_identity_reflector(ens):
+    n = 64
+    x1 = np.zeros(n)
+    errs = teacher_forced(ens, n, n, 6, seed=3, dtype="f64", schedule=ALT, x1=x1)
+    # step 1 output is exactly 0 on both sides; later steps are ordinary
+    assert np.all(errs <= TOL["f64"]), errs
+
+
+def test_unaligned_and_tiny():
+    from paper_2101_07464_gb300 import HD
+    from oracle.hd import HaarOracle
+    n = 11
+    st = HD("haar", n, n, 5, 7, "f64")
+    ora = HaarOracle(n, 5, 7)
+    buf = torch.zeros(n + 1, dtype=torch.float64, device="cuda")
+    x = np.random.default_rng(1).standard_normal(n)
+    buf[1:] = torch.tensor(x, device="cuda")
+    out = torch.zeros(n + 1, dtype=torch.float64, device="cuda")
+    from paper_2101_07464_gb300 import hd_apply
+    hd_apply(st.h, buf[1:].data_ptr(), 0, out[1:].data_ptr())
+    yo = ora.apply(x).numpy()
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(out[1:].cpu().numpy(), yo, atol=1e-13)
+    assert out[0].item() == 0.0
+    st.close()
+    # n = 1: Q = +-1
+    one = HD("haar", 1, 1, 1, 3, "f64")
+    y = one.apply(torch.tensor([2.5], dtype=torch.float64, device="cuda"))
+    yo = HaarOracle(1, 1, 3).apply(np.array([2.5])).numpy()
+    np.testing.assert_allclose(y.cpu().numpy(), yo, atol=1e-15)
+
+
+def test_step_limit_and_reset_replay():
+    from paper_2101_07464_gb300 import HD, HDError
+    n = 300
+    st = HD("haar", n, n, 3, 42, "f64")
+    x = torch.tensor(np.random.default_rng(2).standard_normal(n), device="cuda")
+    ys = [st.apply(x, t % 2 == 1).clone() for t in range(3)]
+    with pytest.raises(HDError) as ei:
+        st.apply(x)
+    assert ei.value.code == 3
+    st.reset(42)
+    ys2 = [st.apply(x, t % 2 == 1).clone() for t in range(3)]
+    for a, b in zip(ys, ys2):
+        assert torch.equal(a, b)   # counter-based draws: reset + replay is bit-identical
+    st.close()
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("ens,m,n", [("haar", 5003, 5003), ("ginibre", 3001, 4999)])
+def test_probe_reproduces_earlier_queries(dtype, ens, m, n):
+    """After s steps the state still maps every earlier x_t to y_t (unrevealed part 0), and
+    for Haar Q^T maps y_t back to x_t (eq. H_t / eq. Gaussian_t)."""
+    from paper_2101_07464_gb300 import HD
+    import synth
+    T = 16
+    sched = MIXED
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    st = HD(ens, m, n, T, 77, dtype, sigma=1.0 if ens == "haar" else m ** -0.5)
+    xs, ys = [], []
+    x = torch.tensor(synth.x1(n, 3), dtype=tdt, device="cuda")
+    for t in range(1, T + 1):
+        tr = sched(t)
+        y = st.apply(x, tr)
+        xs.append(x.clone())
+        ys.append(y.clone())
+        want = m if sched(t + 1) else n
+        x = torch.tanh(y) if y.numel() == want else torch.tensor(synth.x1(want, 3, trial=t), dtype=tdt, device="cuda")
+    tol = TOL[dtype] * 10
+    for t in range(1, T + 1):
+        tr = sched(t)
+        yp, unrev = st.probe(xs[t - 1], tr)
+        assert unrev <= tol * xs[t - 1].norm().item()
+        assert (yp - ys[t - 1]).norm().item() <= tol * ys[t - 1].norm().item()
+        if ens == "haar":
+            xb, unrev2 = st.probe(ys[t - 1], not tr)
+            assert unrev2 <= tol * ys[t - 1].norm().item()
+            assert (xb - xs[t - 1]).norm().item() <= tol * xs[t - 1].norm().item()
+    # a fresh direction is seen by the hidden block
+    _, unrev = st.probe(torch.tensor(synth.x1(n, 99), dtype=tdt, device="cuda"), False)
+    assert unrev > 0.5 * np.sqrt(n)
+    st.close()

@@ -1,0 +1,332 @@
+"""Benchmark of the Householder Dice hot path on one GB300 (or N, one process per GPU).
+
+Workload (the paper's method on its Haar ensemble, Algorithm 2): Q ~ Haar(n), n = 10^6,
+T = 100 products alternating Q and Q^T, dynamics x_{t+1} = sign(M_t x_t) + 0.5 x_{t-1},
+x_1 ~ N(0, I_n) (seeded, synthetic).  One bench "step" is one whole trajectory: T products
+(every row of the hot path: draws, the data-side reflector products, the new reflectors,
+the outputs) plus the dynamics, all in libhd.so kernels, replayed from one CUDA graph.
+Metric: n T^2 / s (the O(nT^2) work unit of the method).  The FP32-storage form is the
+headline line; the plain FP64 form is measured on the same workload and reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--dtype f32|f64] [--impl reference]
+
+--impl reference times the CPU FP64 oracle on the machine's host cores on a bounded sample of
+the same workload (the first products of the trajectory at full n).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_DEFAULT, T_DEFAULT = 10 ** 6, 100
+METRIC = "HD throughput n*T^2/s (Haar n=1e6, T=100, Q/Q^T alternating)"
+UNIT = "n*T^2/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--T", type=int, default=T_DEFAULT)
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 side measurement")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    return ap.parse_args()
+
+
+def schedule(T):
+    return [1 if t % 2 == 0 else 0 for t in range(1, T + 1)]
+
+
+def dist_info():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), \
+        int(os.environ.get("LOCAL_RANK", 0))
+
+
+# ----------------------------------------------------------------------------------------
+# CPU oracle (baseline and reference arm)
+def oracle_sample(n, T, seed, budget_s, max_products=None):
+    """Run the oracle's first products of the workload until budget_s; returns
+    (products done, seconds, threads)."""
+    import numpy as np
+    import torch
+    import synth
+    from oracle.dynamics import f_sign_mem
+    from oracle.hd import HaarOracle
+    ora = HaarOracle(n, T, seed)
+    x = synth.x1(n, seed)
+    xp = np.zeros(n)
+    sched = schedule(T)
+    t0 = time.perf_counter()
+    done = 0
+    for t in range(T):
+        y = ora.apply(x, bool(sched[t])).numpy()
+        x, xp = f_sign_mem(y, x, xp), x
+        done += 1
+        if time.perf_counter() - t0 > budget_s or (max_products and done >= max_products):
+            break
+    return done, time.perf_counter() - t0, torch.get_num_threads()
+
+
+def cpu_units(n, k):
+    """Work of the first k products in the n T^2 unit (work grows like n t for product t)."""
+    return float(n) * k * k
+
+
+def run_reference(args):
+    rank, world, _ = dist_info()
+    if world > 1 and rank != 0:
+        return
+    n, T = args.n, args.T
+    k_sample = 10
+    times = []
+    for i in range(args.warmup + args.steps):
+        done, secs, thr = oracle_sample(n, T, args.seed, budget_s=1e9, max_products=k_sample)
+        if i >= args.warmup:
+            times.append(secs)
+    mean = statistics.mean(times)
+    value = cpu_units(n, k_sample) / mean
+    sample = "first %d of %d products at n=%d (Haar, Q/Q^T alternating, sign dynamics), FP64" % (
+        k_sample, T, n)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "haar_sign n=%d T=%d (sampled: first %d products)" % (n, T, k_sample),
+                       "n": n, "T": T},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": thr, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [c.strip() for c in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def time_trajectories(st, spec, x1, xout, steps, warmup, dist, profile=False):
+    """Replay the trajectory graph; returns (seconds max over ranks, per-kernel profile,
+    kernels launched in the timed region)."""
+    import torch
+    import paper_2101_07464_gb300 as hd
+    for _ in range(warmup):
+        hd.hd_run(st.h, spec, x1, xout)
+    torch.cuda.synchronize()
+    if profile:
+        hd.hd_profile_enable(st.h, True)
+        hd.hd_run(st.h, spec, x1, xout)   # capture the graph with the event records
+        torch.cuda.synchronize()
+        hd.hd_profile_read(st.h, clear=True)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = hd.hd_get_launches(st.h)
+    e0.record(stream)
+    for _ in range(steps):
+        hd.hd_run(st.h, spec, x1, xout)
+        if profile:
+            hd.hd_profile_read(st.h)   # events of this replay (synchronises the stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = hd.hd_get_launches(st.h) - l0
+    secs = e0.elapsed_time(e1) / 1e3
+    prof = hd.hd_profile_read(st.h) if profile else None
+    if profile:
+        hd.hd_profile_enable(st.h, False)
+    if dist is not None:
+        t = torch.tensor([secs], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        secs = float(t.item())
+    return secs, prof, launches
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import synth
+    import paper_2101_07464_gb300 as hd
+    from paper_2101_07464_gb300 import build as hdbuild
+
+    rank, world, local = dist_info()
+    dist = None
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl")
+        dist = tdist
+    torch.cuda.set_device(local)
+    hdbuild.build()
+    n, T = args.n, args.T
+    flags = schedule(T)
+
+    def measure(dtype, profile):
+        tdt = torch.float32 if dtype == "f32" else torch.float64
+        st = hd.HD("haar", n, n, T, args.seed, dtype, trial=rank)
+        spec = hd.make_run_spec(flags, "sign_mem", 0.5, use_graph=True)
+        x1 = torch.tensor(synth.x1(n, args.seed, trial=rank), dtype=tdt, device="cuda")
+        xout = torch.empty(n, dtype=tdt, device="cuda")
+        secs, prof, launches = time_trajectories(st, spec, x1, xout, args.steps, args.warmup,
+                                                 dist, profile)
+        return st, spec, secs, prof, launches
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    st, spec, secs, prof, launches = measure(args.dtype, profile=True)
+    clk = clocks.stop()
+    per_step = secs / args.steps
+    units = float(n) * T * T * world
+    value = units / per_step
+
+    # end to end through the public API: pinned host x_1 in, x_{T+1} back, every step
+    tdt = torch.float32 if args.dtype == "f32" else torch.float64
+    x1h = torch.tensor(synth.x1(n, args.seed, trial=rank), dtype=tdt).pin_memory()
+    xouth = torch.empty(n, dtype=tdt).pin_memory()
+    for _ in range(args.warmup):
+        hd.hd_run(st.h, spec, x1h, xouth)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        hd.hd_run(st.h, spec, x1h, xouth)
+        torch.cuda.current_stream().synchronize()   # the result is on the host
+        float(xouth[0])
+    e2e_secs = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_secs], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_secs = float(t.item())
+    e2e = {"value": units / (e2e_secs / args.steps), "unit": UNIT,
+           "h2d_bytes_per_step": n * x1h.element_size(), "d2h_bytes_per_step": n * xouth.element_size()}
+    st.close()
+
+    # roofline of the dominant kernel (largest total time inside the timed region)
+    peak, peak_kind = measured_peaks()
+    dom = max(prof, key=lambda k: prof[k][0])
+    ms, nl, by = prof[dom]
+    achieved = (by / nl) / ((ms / nl) / 1e3) / 1e9 if nl else 0.0
+    roofline = {"bound": "hbm", "kernel": {"dots": "k_dots", "update": "k_update",
+                                            "output": "k_out_haar"}[dom],
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_source": peak_kind, "traffic": None,
+                "per_kernel": {k: {"ms_total": v[0], "launches": v[1],
+                                   "GBps": (v[2] / (v[0] / 1e3) / 1e9) if v[0] else None}
+                               for k, v in prof.items()}}
+    if args.dtype == "f64":
+        roofline["note"] = "FP64 sweeps are bound by the FP64 FMA rate, not HBM"
+    credited = 2.0 * n * tdt.itemsize * T * (T + 1) / 2.0 * world
+    step_gbps = credited / per_step / 1e9
+
+    fp64 = None
+    if args.dtype == "f32" and not args.no_fp64:
+        st64, _, secs64, _, _ = measure("f64", profile=False)
+        st64.close()
+        fp64 = {"value": units / (secs64 / args.steps), "ms_per_step": secs64 / args.steps * 1e3,
+                "unit": UNIT}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        done, csecs, thr = oracle_sample(n, T, args.seed, budget_s=15.0)
+        cpu = {"value": cpu_units(n, done) / csecs, "unit": UNIT, "cores": thr, "kind": "oracle",
+               "sample": "first %d of %d products at n=%d, FP64, wall %.1f s" % (done, T, n, csecs)}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": args.dtype, "data": "synthetic",
+                "config": {"workload": "haar_sign", "ensemble": "haar", "n": n, "T": T,
+                           "schedule": "Q/Q^T alternating", "dynamics": "sign(y)+0.5x_{t-1}",
+                           "storage": "FP32 stacks, FP64 coefficients" if args.dtype == "f32"
+                           else "FP64", "per_rank": "independent trial (Philox trial word = rank)",
+                           "l2": "inputs larger than L2 (two reflector stacks of %.0f MB each)"
+                           % (n * T * tdt.itemsize / 1e6),
+                           "graph": "one CUDA graph per trajectory"},
+                "roofline": roofline,
+                "step_credited_GBps": step_gbps,
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clk, "fp64": fp64}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

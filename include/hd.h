@@ -62,8 +62,7 @@ typedef enum { HD_F64 = 0, HD_F32 = 1 } hd_dtype;
 /* Create a state for y = M_t x with Q ~ Gin(m, n) (entries sigma * N(0,1), sigma = 1 by
  * default: Section 3 notation) or Q ~ Haar(n) (requires m == n).  T_max bounds the number
  * of products: T_max <= min(m, n) for Gin (Algorithm 1 requires T <= min(m, n)), T_max <= n
- * for Haar (Algorithm 2 requires T <= n); this library also caps T_max at 1024 (FP32) and at
- * the largest value whose K2 shared-memory tile fits (about 850 for FP64).  Allocates all device memory up front:
+ * for Haar (Algorithm 2 requires T <= n); this library also caps T_max at 256.  Allocates all device memory up front:
  * two reflector stacks (n x T_max and m x T_max elements), for Gin two basis stores of the
  * same sizes, and O(T_max^2) FP64 coefficients.  seed keys the Philox4x32-10 generator
  * that draws the Gaussian vectors g_t (key = seed, counter = (index/2, t, trial, 0)).
@@ -96,6 +95,38 @@ HD_API int hd_apply(hd_state* st, const void* x, int transpose, void* y);
 HD_API int hd_probe(hd_state* st, const void* x, int transpose, void* y,
                     double* unrevealed_host);
 
+/* Built-in dynamics f_t for hd_run (elementwise, run in the library's kernels):
+ *   HD_DYN_TANH       x_{t+1} = tanh(y_t)
+ *   HD_DYN_SIGN_MEM   x_{t+1} = sign(y_t) + a x_{t-1}   (sign(0) = 0; x_0 = 0)
+ *   HD_DYN_NORM_TANH  x_{t+1} = v/||v||, v = tanh(y_t) + a x_t                        */
+typedef enum { HD_DYN_TANH = 1, HD_DYN_SIGN_MEM = 2, HD_DYN_NORM_TANH = 3 } hd_dynamics;
+
+typedef struct {
+  int32_t T;                 /* number of products, 1 <= T <= T_max                      */
+  const uint8_t* transpose;  /* host array of T flags: M_t = Q^T where nonzero           */
+  int32_t dynamics;          /* an hd_dynamics value                                     */
+  double a;                  /* coefficient of the dynamics                              */
+  int32_t use_graph;         /* nonzero: capture the trajectory once in a CUDA graph and
+                                replay it on later calls with the same (T, flags,
+                                dynamics, a); the first call with use_graph must not
+                                happen while the state's stream is being captured       */
+} hd_run_spec;
+
+/* A whole trajectory of eq. (dynamics): resets the state (same seed, trial and sigma),
+ * then for t = 1..T computes y_t = M_t x_t (hd_apply) and x_{t+1} = f_t(y_t, x_t, x_{t-1})
+ * with the built-in dynamics, all on the state's stream.  x1 (input, length n if M_1 = Q,
+ * else m) and x_out (output x_{T+1}) may be device or page-locked host pointers (copied
+ * with cudaMemcpyAsync, cudaMemcpyDefault); they are read/written on the stream.  Every
+ * step's input dimension must match the previous output (HD_ERR_DIM otherwise: for a
+ * rectangular Gin, Q and Q^T must alternate).  Work vectors are allocated by the state
+ * on the first call (3 x max(m, n) elements). */
+HD_API int hd_run(hd_state* st, const hd_run_spec* spec, const void* x1, void* x_out);
+
+/* Synchronise the state's stream and check the device error word: returns HD_ERR_TIMEOUT
+ * (and poisons the state) if a bounded device-side wait expired in an earlier step, else the
+ * state's sticky status (HD_OK when healthy). */
+HD_API int hd_sync(hd_state* st);
+
 /* Forget all steps (t = r = l = 0) and re-key the generator with seed; keeps the
  * allocations and options.  Clears a poisoned state. */
 HD_API int hd_reset(hd_state* st, uint64_t seed);
@@ -113,6 +144,20 @@ HD_API int hd_get_device_bytes(const hd_state* st, int64_t* bytes);
 /* Text of the last CUDA failure seen by a call of this library in the calling thread
  * (empty if none); valid until the next failing call in that thread. */
 HD_API const char* hd_last_error(void);
+
+/* Profiling of the three sweeps of every step (kind 0 = dots K1, 1 = update K2, 2 = output
+ * K3): when enabled, CUDA events are recorded on the state's stream around each sweep
+ * launch (also inside a graph captured by hd_run, which then re-records the same events on
+ * every replay).  hd_profile_read synchronises the stream, adds the elapsed times of the
+ * recorded launches to running totals and returns, per kind, the total milliseconds, the
+ * number of launches and their algorithmic bytes (each stack read once plus the vectors
+ * the sweep reads and writes); clear != 0 zeroes the totals after reading. */
+HD_API int hd_profile_enable(hd_state* st, int on);
+HD_API int hd_profile_read(hd_state* st, double* ms3, int64_t* launches3, double* bytes3,
+                           int clear);
+
+/* Number of kernels this state has launched (graph replays count their kernels). */
+HD_API int hd_get_launches(const hd_state* st, int64_t* launches);
 
 /* Human-readable name of a status code (static string). */
 HD_API const char* hd_status_string(int status);

@@ -20,6 +20,14 @@ DTYPES = {"f64": HD_F64, "f32": HD_F32}
 
 _LIB = None
 
+HD_DYN_TANH, HD_DYN_SIGN_MEM, HD_DYN_NORM_TANH = 1, 2, 3
+DYNAMICS = {"tanh": HD_DYN_TANH, "sign_mem": HD_DYN_SIGN_MEM, "norm_tanh": HD_DYN_NORM_TANH}
+
+
+class hd_run_spec(ctypes.Structure):
+    _fields_ = [("T", ctypes.c_int32), ("transpose", ctypes.POINTER(ctypes.c_uint8)),
+                ("dynamics", ctypes.c_int32), ("a", ctypes.c_double), ("use_graph", ctypes.c_int32)]
+
 _c = ctypes
 _P = _c.c_void_p
 _PROTOS = {
@@ -29,6 +37,12 @@ _PROTOS = {
     "hd_apply": (_c.c_int, [_P, _P, _c.c_int, _P]),
     "hd_probe": (_c.c_int, [_P, _P, _c.c_int, _P, _c.POINTER(_c.c_double)]),
     "hd_reset": (_c.c_int, [_P, _c.c_uint64]),
+    "hd_sync": (_c.c_int, [_P]),
+    "hd_run": (_c.c_int, [_P, _P, _P, _P]),
+    "hd_profile_enable": (_c.c_int, [_P, _c.c_int]),
+    "hd_profile_read": (_c.c_int, [_P, _c.POINTER(_c.c_double), _c.POINTER(_c.c_int64),
+                                   _c.POINTER(_c.c_double), _c.c_int]),
+    "hd_get_launches": (_c.c_int, [_P, _c.POINTER(_c.c_int64)]),
     "hd_destroy": (None, [_P]),
     "hd_get_counts": (_c.c_int, [_P, _c.POINTER(_c.c_int32), _c.POINTER(_c.c_int32),
                                  _c.POINTER(_c.c_int32)]),
@@ -124,6 +138,51 @@ def hd_probe(state, x, transpose, y):
     _check(lib().hd_probe(state, _ptr(x, what="x"), int(bool(transpose)), _ptr(y, what="y"),
                           ctypes.byref(u)), "hd_probe")
     return u.value
+
+
+def make_run_spec(transpose_flags, dynamics, a=0.0, use_graph=True):
+    """hd_run_spec for a schedule (sequence of 0/1 flags) and a built-in dynamics name/code."""
+    flags = (ctypes.c_uint8 * len(transpose_flags))(*[1 if f else 0 for f in transpose_flags])
+    spec = hd_run_spec(len(transpose_flags), ctypes.cast(flags, ctypes.POINTER(ctypes.c_uint8)),
+                       DYNAMICS.get(dynamics, dynamics), float(a), 1 if use_graph else 0)
+    spec._flags = flags  # keep the array alive with the struct
+    return spec
+
+
+def hd_run(state, spec, x1, x_out):
+    """x1 / x_out: CUDA tensors, page-locked CPU tensors, or raw addresses."""
+    def addr(t, what):
+        if isinstance(t, int):
+            return t
+        if not t.is_contiguous():
+            raise ValueError("%s must be contiguous" % what)
+        if not t.is_cuda and not t.is_pinned():
+            raise ValueError("%s must be a CUDA tensor or page-locked host memory" % what)
+        return t.data_ptr()
+    _check(lib().hd_run(state, ctypes.byref(spec), addr(x1, "x1"), addr(x_out, "x_out")), "hd_run")
+
+
+def hd_profile_enable(state, on=True):
+    _check(lib().hd_profile_enable(state, 1 if on else 0), "hd_profile_enable")
+
+
+def hd_profile_read(state, clear=False):
+    """Returns {kind: (ms, launches, bytes)} for kinds 'dots', 'update', 'output'."""
+    ms = (ctypes.c_double * 3)()
+    nl = (ctypes.c_int64 * 3)()
+    by = (ctypes.c_double * 3)()
+    _check(lib().hd_profile_read(state, ms, nl, by, 1 if clear else 0), "hd_profile_read")
+    return {k: (ms[i], nl[i], by[i]) for i, k in enumerate(("dots", "update", "output"))}
+
+
+def hd_get_launches(state):
+    v = ctypes.c_int64()
+    _check(lib().hd_get_launches(state, ctypes.byref(v)), "hd_get_launches")
+    return v.value
+
+
+def hd_sync(state):
+    _check(lib().hd_sync(state), "hd_sync")
 
 
 def hd_reset(state, seed):

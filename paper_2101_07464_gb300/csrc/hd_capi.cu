@@ -7,10 +7,12 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include <cuda_runtime.h>
 
 #include "../../include/hd.h"
+#include "hd_dynamics.cuh"
 #include "hd_kernels.cuh"
 
 using namespace hd;
@@ -34,12 +36,40 @@ struct hd_state {
   Ws ws;
   Grid grid[2];          // launch shape for each space (0: n, 1: m)
   int nsm = 1;
-  int occ_upd_regs = 1;  // K2 CTAs per SM allowed by registers
+  int occ_regs[4] = {1, 1, 1, 1};  // CTAs per SM allowed by registers: K1, K2, K3 Haar, K3 Gin
   int smem_sm = 0;       // shared memory per SM usable by CTAs
   int smem_blk_max = 0;  // opt-in dynamic shared memory per CTA
   int64_t bytes = 0;
-  void* allocs[32];
+  void* allocs[40];
   int nalloc = 0;
+  // hd_run: work vectors and the cached trajectory graph
+  void* xw[2] = {nullptr, nullptr};
+  void* yw = nullptr;
+  double* sumsq = nullptr;
+  int run_final = 0;
+  cudaStream_t own_stream = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<uint8_t> g_flags;
+  int g_T = 0, g_dyn = 0;
+  double g_a = 0.0, g_sigma = 0.0;
+  uint64_t g_seed = 0;
+  uint32_t g_trial = 0;
+  cudaStream_t g_stream = nullptr;
+  int g_final = 0;
+  int g_launches = 0;
+  int g_prof = 0;
+  // kernel launches issued (graph replays count the captured launches)
+  int64_t launches = 0;
+  // profiling: event pairs around each sweep, algorithmic bytes of each recorded launch
+  int prof_on = 0;
+  int prof_cap = 0;
+  int prof_used = 0;
+  std::vector<cudaEvent_t> prof_ev;   // 2 per slot
+  std::vector<int> prof_kind;
+  std::vector<double> prof_bytes;
+  double prof_ms[3] = {0, 0, 0};
+  int64_t prof_n[3] = {0, 0, 0};
+  double prof_b[3] = {0, 0, 0};
 };
 
 namespace {
@@ -116,31 +146,62 @@ int first_draws(hd_state* st) {
   return HD_OK;
 }
 
-// K2 tile: the largest R in {256, 128, 64, 32} whose shared-memory footprint leaves room for
-// two or more CTAs per SM (else the largest that fits one), grid = min(tiles, CTAs resident).
+// Launch shape of a tiled sweep over ncol columns of a dim-row stack: the largest tile
+// height R in {256, 128, 64, 32} whose two-stage footprint leaves room for two CTAs per
+// SM; else one CTA per SM with two stages; else one stage.  Persistent grid of
+// min(tiles, resident CTAs).
+// Launch shape of a sweep over ncolT staged columns and NRV staged row vectors (ncolC
+// column-owner columns, NR right-hand sides) of a dim-row stack: the (warps per CTA, pipeline
+// stages per warp) pair that puts the most bytes in flight per SM (capped at 128 KB; then
+// more resident warps, then fewer stages), and a persistent grid of min(sub-tile groups,
+// resident CTAs).
 template <typename T>
-void choose_update_tiles(const hd_state* st, int k, int64_t dim, StepPlan<T>* p) {
-  int R = 32;
-  for (int cand = 256; cand >= 32; cand /= 2) {
-    const size_t b = update_smem_bytes<T>(k, cand);
-    if ((int)(2 * (b + 1024)) <= st->smem_sm || cand == 32) {
-      R = cand;
-      break;
+SweepCfg make_sweep(const hd_state* st, int which, int ncolT, int NRV, int ncolC, int NR, int64_t dim) {
+  SweepCfg c;
+  c.W = 8;
+  c.nbuf = 1;
+  const int blk = st->smem_blk_max - 1024;
+  const double stage = (double)(ncolT + NRV) * 32.0 * sizeof(T);
+  double best = -1.0;
+  for (int W = 8; W >= 1; W /= 2) {
+    for (int nb = 1; nb <= 8; nb *= 2) {
+      const size_t b = sweep_smem_bytes<T>(W, nb, ncolT, NRV, ncolC, NR);
+      if ((int)b > blk) continue;
+      const int by_regs = std::max(1, st->occ_regs[which] * 8 / W);
+      const int ctas = std::min(by_regs, (int)(st->smem_sm / (b + 1024)));
+      if (ctas < 1) continue;
+      const int warps = std::min(64, ctas * W);
+      const double inflight = std::min(warps * nb * stage, 131072.0);
+      const double score = inflight * 1e4 + warps * 10.0 - nb;
+      if (score > best) {
+        best = score;
+        c.W = W;
+        c.nbuf = nb;
+      }
     }
   }
-  const size_t bytes = update_smem_bytes<T>(k, R);
-  int occ = std::max(1, std::min(st->occ_upd_regs, (int)(st->smem_sm / (bytes + 1024))));
-  const int64_t ntiles = (dim + R - 1) / R;
-  int64_t ctas = std::min<int64_t>(ntiles, (int64_t)occ * st->nsm);
+  const size_t bytes = sweep_smem_bytes<T>(c.W, c.nbuf, ncolT, NRV, ncolC, NR);
+  const int by_regs = std::max(1, st->occ_regs[which] * 8 / c.W);
+  const int occ = std::max(1, std::min(by_regs, (int)(st->smem_sm / (bytes + 1024))));
+  const int64_t nsub = (dim + 31) / 32;
+  int64_t ctas = std::min<int64_t>((nsub + c.W - 1) / c.W, (int64_t)occ * st->nsm);
   if (ctas < 1) ctas = 1;
-  p->R2 = R;
-  p->ntiles2 = ntiles;
-  Grid g;
-  g.ctas = (int)ctas;
-  g.vpc = 0;
-  g.gsize = std::max(1, (int)std::ceil(std::sqrt((double)ctas)));
-  g.ngroups = (int)((ctas + g.gsize - 1) / g.gsize);
-  p->g2 = g;
+  c.g.ctas = (int)ctas;
+  c.g.vpc = 0;
+  c.g.gsize = std::max(1, (int)std::ceil(std::sqrt((double)ctas)));
+  c.g.ngroups = (int)((ctas + c.g.gsize - 1) / c.g.gsize);
+  return c;
+}
+
+template <typename T>
+void set_sweeps(const hd_state* st, StepPlan<T>* p) {
+  const int nc1 = p->kD + ((p->ens == 0) ? p->kN : 0);
+  p->c1 = make_sweep<T>(st, 0, nc1, 1, nc1, 1, p->D.dim);
+  p->c2 = make_sweep<T>(st, 1, p->kD, 1, p->kD, 2, p->D.dim);
+  if (p->ens == 1)
+    p->c3 = make_sweep<T>(st, 2, p->kN, 2, p->kN, 1, p->N.dim);
+  else
+    p->c3 = make_sweep<T>(st, 3, p->kN + p->kD, 1, p->kN, 1, p->N.dim);
 }
 
 template <typename T>
@@ -173,11 +234,35 @@ int do_step(hd_state* st, const void* x, int transpose, void* y) {
   p.ws = st->ws;
   p.key_next = key_for(st, st->t + 2);
   p.sigma = (st->ens == HD_GINIBRE) ? (T)st->sigma : T(1);
-  p.g1 = st->grid[d];
-  p.g3 = st->grid[1 - d];
-  choose_update_tiles<T>(st, p.kD, p.D.dim, &p);
-  cudaError_t e = launch_step<T>(p, st->stream);
+  set_sweeps<T>(st, &p);
+  cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  int slot0 = -1;
+  if (st->prof_on && st->prof_used + 3 <= st->prof_cap) {
+    slot0 = st->prof_used;
+    for (int q = 0; q < 3; q++) {
+      ev[2 * q] = st->prof_ev[2 * (slot0 + q)];
+      ev[2 * q + 1] = st->prof_ev[2 * (slot0 + q) + 1];
+    }
+  }
+  int launched[3] = {0, 0, 0};
+  cudaError_t e = launch_step<T>(p, st->stream, ev, launched);
   if (e != cudaSuccess) return cuda_fail(st, e);
+  st->launches += launched[0] + launched[1] + launched[2];
+  if (slot0 >= 0) {
+    // algorithmic bytes: each sweep reads its stack once plus its vectors
+    const double es = (double)sizeof(T);
+    const double nD = (double)p.D.dim, nN = (double)p.N.dim;
+    const double bd = (st->ens == HD_GINIBRE) ? (double)p.kN * nD : 0.0;  // data-space basis
+    const double bn = (st->ens == HD_GINIBRE) ? (double)(p.kD + 1) * nN : 0.0;
+    const double b[3] = {es * (nD * p.kD + bd + nD),
+                         es * (nD * p.kD + 3.0 * nD),
+                         es * (nN * p.kN + bn + 4.0 * nN)};
+    for (int q = 0; q < 3; q++) {
+      st->prof_kind[slot0 + q] = launched[q] ? q : -1;
+      st->prof_bytes[slot0 + q] = b[q];
+    }
+    st->prof_used += 3;
+  }
   st->t += 1;
   if (transpose) st->l += 1; else st->r += 1;
   return HD_OK;
@@ -208,8 +293,7 @@ int do_probe(hd_state* st, const void* x, int transpose, void* y, double* unreve
   p.yal = aligned16(y);
   p.ws = st->ws;
   p.sigma = T(1);
-  p.g1 = st->grid[d];
-  p.g3 = st->grid[1 - d];
+  set_sweeps<T>(st, &p);
   double* q = nullptr;
   if (cudaMalloc(&q, (size_t)(p.D.dim + 1) * 8) != cudaSuccess) {
     set_error("hd_probe cudaMalloc", cudaGetLastError());
@@ -227,9 +311,147 @@ int do_probe(hd_state* st, const void* x, int transpose, void* y, double* unreve
   return HD_OK;
 }
 
+template <typename T>
+int run_steps(hd_state* st, const hd_run_spec* sp) {
+  if (st->prof_on) st->prof_used = 0;
+  st->t = st->r = st->l = 0;
+  st->drawn = 0;
+  int cur = 0;
+  for (int t = 0; t < sp->T; t++) {
+    const int tr = sp->transpose[t] ? 1 : 0;
+    int rc = do_step<T>(st, st->xw[cur], tr, st->yw);
+    if (rc) return rc;
+    const int64_t nout = tr ? st->n : st->m;
+    cudaError_t e = launch_dynamics<T>(sp->dynamics, sp->a, (const T*)st->yw, (const T*)st->xw[cur],
+                                       (const T*)st->xw[1 - cur], (T*)st->xw[1 - cur], nout,
+                                       st->sumsq, st->stream);
+    if (e != cudaSuccess) return cuda_fail(st, e);
+    st->launches += (sp->dynamics == HD_DYN_NORM_TANH) ? 2 : 1;
+    cur = 1 - cur;
+  }
+  st->run_final = cur;
+  return HD_OK;
+}
+
+bool graph_matches(const hd_state* st, const hd_run_spec* sp) {
+  if (!st->gexec || st->g_T != sp->T || st->g_dyn != sp->dynamics || st->g_a != sp->a) return false;
+  if (st->g_seed != st->seed || st->g_trial != st->trial || st->g_sigma != st->sigma) return false;
+  if (st->g_stream != st->stream || st->g_prof != st->prof_on) return false;
+  for (int t = 0; t < sp->T; t++)
+    if (st->g_flags[t] != (sp->transpose[t] ? 1 : 0)) return false;
+  return true;
+}
+
 }  // namespace
 
 extern "C" {
+
+HD_API int hd_run(hd_state* st, const hd_run_spec* sp, const void* x1, void* x_out) {
+  if (!st || !sp || !sp->transpose || !x1 || !x_out) return HD_ERR_ARG;
+  if (st->poisoned) return st->poisoned;
+  if (sp->T < 1 || sp->T > st->Tm) return HD_ERR_TMAX;
+  if (sp->dynamics != HD_DYN_TANH && sp->dynamics != HD_DYN_SIGN_MEM && sp->dynamics != HD_DYN_NORM_TANH)
+    return HD_ERR_ARG;
+  if (!std::isfinite(sp->a)) return HD_ERR_ARG;
+  // dimensions: input of step t+1 = output of step t; x_{t-1} (sign_mem) matches y_t
+  for (int t = 0; t + 1 < sp->T; t++) {
+    const int64_t out_t = sp->transpose[t] ? st->n : st->m;
+    const int64_t in_next = sp->transpose[t + 1] ? st->m : st->n;
+    if (out_t != in_next) return HD_ERR_DIM;
+  }
+  if (cudaSetDevice(st->device) != cudaSuccess) return cuda_fail(st, cudaErrorInvalidDevice);
+  const int64_t dmax = std::max(st->m, st->n);
+  if (!st->yw) {
+    const int64_t ld = round_up(dmax, 64);
+    st->xw[0] = dalloc(st, (size_t)ld * st->esz);
+    st->xw[1] = dalloc(st, (size_t)ld * st->esz);
+    st->yw = dalloc(st, (size_t)ld * st->esz);
+    st->sumsq = (double*)dalloc(st, 64);
+    if (!st->xw[0] || !st->xw[1] || !st->yw || !st->sumsq) return HD_ERR_OOM;
+  }
+  const int64_t nin = sp->transpose[0] ? st->m : st->n;
+  const int64_t nfin = sp->transpose[sp->T - 1] ? st->n : st->m;
+  cudaError_t e = cudaMemcpyAsync(st->xw[0], x1, (size_t)nin * st->esz, cudaMemcpyDefault, st->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(st->xw[1], 0, (size_t)dmax * st->esz, st->stream);
+  if (e != cudaSuccess) {
+    set_error("hd_run input copy", e);
+    return cuda_fail(st, e);
+  }
+  int rc = HD_OK;
+  if (sp->use_graph) {
+    if (!graph_matches(st, sp)) {
+      if (st->gexec) {
+        cudaGraphExecDestroy(st->gexec);
+        st->gexec = nullptr;
+      }
+      cudaStream_t user = st->stream;
+      cudaStream_t cap = user;
+      if (!cap) {
+        if (!st->own_stream && cudaStreamCreateWithFlags(&st->own_stream, cudaStreamNonBlocking) != cudaSuccess)
+          return cuda_fail(st, cudaGetLastError());
+        cap = st->own_stream;
+        // order the capture stream after the input copies on the legacy stream
+        if (cudaStreamSynchronize(user) != cudaSuccess) return cuda_fail(st, cudaGetLastError());
+      }
+      cudaGraph_t graph = nullptr;
+      e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) {
+        set_error("cudaStreamBeginCapture", e);
+        return cuda_fail(st, e);
+      }
+      st->stream = cap;
+      const int64_t l0 = st->launches;
+      rc = (st->dtype == HD_F64) ? run_steps<double>(st, sp) : run_steps<float>(st, sp);
+      st->g_launches = (int)(st->launches - l0);
+      st->launches = l0;
+      st->stream = user;
+      e = cudaStreamEndCapture(cap, &graph);
+      if (rc) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+      }
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&st->gexec, graph, 0);
+      if (graph) cudaGraphDestroy(graph);
+      if (e != cudaSuccess) {
+        set_error("graph capture", e);
+        st->gexec = nullptr;
+        return cuda_fail(st, e);
+      }
+      st->g_T = sp->T;
+      st->g_dyn = sp->dynamics;
+      st->g_a = sp->a;
+      st->g_seed = st->seed;
+      st->g_trial = st->trial;
+      st->g_sigma = st->sigma;
+      st->g_stream = st->stream;
+      st->g_flags.assign(sp->transpose, sp->transpose + sp->T);
+      for (auto& f : st->g_flags) f = f ? 1 : 0;
+      st->g_final = st->run_final;
+      st->g_prof = st->prof_on;
+    }
+    e = cudaGraphLaunch(st->gexec, st->stream);
+    if (e != cudaSuccess) {
+      set_error("cudaGraphLaunch", e);
+      return cuda_fail(st, e);
+    }
+    st->launches += st->g_launches;
+    st->t = sp->T;
+    st->r = st->l = 0;
+    for (int t = 0; t < sp->T; t++) (sp->transpose[t] ? st->l : st->r) += 1;
+    st->drawn = 1;
+    st->run_final = st->g_final;
+  } else {
+    rc = (st->dtype == HD_F64) ? run_steps<double>(st, sp) : run_steps<float>(st, sp);
+    if (rc) return rc;
+  }
+  e = cudaMemcpyAsync(x_out, st->xw[st->run_final], (size_t)nfin * st->esz, cudaMemcpyDefault, st->stream);
+  if (e != cudaSuccess) {
+    set_error("hd_run output copy", e);
+    return cuda_fail(st, e);
+  }
+  return HD_OK;
+}
+
 
 HD_API const char* hd_last_error(void) { return g_last_error; }
 
@@ -285,14 +507,14 @@ HD_API int hd_create(int ensemble, int64_t m, int64_t n, int32_t T_max, uint64_t
   st->smem_sm = smem_sm;
   st->smem_blk_max = smem_blk;
   {
-    const size_t need = (dtype == HD_F64) ? update_smem_bytes<double>(T_max, 32)
-                                          : update_smem_bytes<float>(T_max, 32);
-    if ((int)need > smem_blk) {
+    const size_t need = (dtype == HD_F64) ? sweep_smem_bytes<double>(1, 1, T_max, 2, T_max, 2)
+                                          : sweep_smem_bytes<float>(1, 1, T_max, 2, T_max, 2);
+    if ((int)need > smem_blk - 1024) {
       delete st;
       return HD_ERR_TMAX;
     }
-    cudaError_t e = (dtype == HD_F64) ? set_update_smem_limit<double>(smem_blk - 1024)
-                                      : set_update_smem_limit<float>(smem_blk - 1024);
+    cudaError_t e = (dtype == HD_F64) ? set_sweep_smem_limit<double>(smem_blk - 1024)
+                                      : set_sweep_smem_limit<float>(smem_blk - 1024);
     if (e != cudaSuccess) {
       set_error("cudaFuncSetAttribute", e);
       cudaGetLastError();
@@ -303,15 +525,10 @@ HD_API int hd_create(int ensemble, int64_t m, int64_t n, int32_t T_max, uint64_t
   const int vec = (dtype == HD_F64) ? 2 : 4;
   int occ;
   const size_t dsm = (size_t)3 * T_max * st->esz;
-  if (dtype == HD_F64) {
-    occ = std::min(kernel_occupancy<double>(0, 0),
-                   kernel_occupancy<double>(ensemble == HD_HAAR ? 2 : 3, dsm));
-    st->occ_upd_regs = kernel_occupancy<double>(1, 0);
-  } else {
-    occ = std::min(kernel_occupancy<float>(0, 0),
-                   kernel_occupancy<float>(ensemble == HD_HAAR ? 2 : 3, dsm));
-    st->occ_upd_regs = kernel_occupancy<float>(1, 0);
-  }
+  (void)dsm;
+  for (int q = 0; q < 4; q++)
+    st->occ_regs[q] = (dtype == HD_F64) ? kernel_occupancy<double>(q, 0) : kernel_occupancy<float>(q, 0);
+  occ = 4;
   const int64_t dims[2] = {n, m};
   int64_t maxctas = (int64_t)nsm * 8;
   for (int s = 0; s < 2; s++) {
@@ -327,7 +544,7 @@ HD_API int hd_create(int ensemble, int64_t m, int64_t n, int32_t T_max, uint64_t
   for (int s = 0; s < 2 && ok; s++) {
     StackDev& X = st->st[s];
     X.dim = dims[s];
-    X.ld = round_up(dims[s], 64);
+    X.ld = round_up(dims[s], 256);
     X.V = dalloc(st, (size_t)X.ld * Tm * st->esz);
     X.S = (double*)dalloc(st, (size_t)Tm * Tm * 8);
     X.dpre = (double*)dalloc(st, (size_t)(Tm + 1) * 8);
@@ -355,8 +572,9 @@ HD_API int hd_create(int ensemble, int64_t m, int64_t n, int32_t T_max, uint64_t
     w.part = (double*)dalloc(st, (size_t)maxctas * (2 * Tm + 8) * 8);
     w.gpart = (double*)dalloc(st, (size_t)kMaxGroups * (2 * Tm + 8) * 8);
     w.cnt = (unsigned int*)dalloc(st, (size_t)3 * (kMaxGroups + 1) * sizeof(unsigned int));
+    w.err = (unsigned int*)dalloc(st, 16);
     ok = w.z && w.w && w.phead && w.wout && w.wout2 && w.scrb && w.scal && w.part &&
-         w.gpart && w.cnt;
+         w.gpart && w.cnt && w.err;
   }
   if (!ok) {
     free_all(st);
@@ -376,6 +594,7 @@ HD_API int hd_create(int ensemble, int64_t m, int64_t n, int32_t T_max, uint64_t
     if (zok) zok = cudaMemcpy(X.dpre, &one, 8, cudaMemcpyHostToDevice) == cudaSuccess;
   }
   if (zok) zok = cudaMemset(st->ws.cnt, 0, (size_t)3 * (kMaxGroups + 1) * sizeof(unsigned int)) == cudaSuccess;
+  if (zok) zok = cudaMemset(st->ws.err, 0, 16) == cudaSuccess;
   if (zok) zok = cudaMemset(st->ws.scal, 0, kNumScal * 8) == cudaSuccess;
   if (zok) zok = cudaDeviceSynchronize() == cudaSuccess;
   if (!zok) {
@@ -417,8 +636,85 @@ HD_API int hd_probe(hd_state* st, const void* x, int transpose, void* y, double*
                                : do_probe<float>(st, x, transpose, y, unrevealed_host);
 }
 
+HD_API int hd_profile_enable(hd_state* st, int on) {
+  if (!st) return HD_ERR_ARG;
+  if (on && st->prof_cap == 0) {
+    const int slots = 3 * st->Tm;
+    st->prof_ev.assign(2 * slots, nullptr);
+    for (auto& ev : st->prof_ev)
+      if (cudaEventCreate(&ev) != cudaSuccess) {
+        set_error("cudaEventCreate", cudaGetLastError());
+        return HD_ERR_CUDA;
+      }
+    st->prof_kind.assign(slots, -1);
+    st->prof_bytes.assign(slots, 0.0);
+    st->prof_cap = slots;
+  }
+  st->prof_on = on ? 1 : 0;
+  st->prof_used = 0;
+  return HD_OK;
+}
+
+HD_API int hd_profile_read(hd_state* st, double* ms3, int64_t* launches3, double* bytes3, int clear) {
+  if (!st) return HD_ERR_ARG;
+  if (st->prof_used > 0) {
+    if (cudaStreamSynchronize(st->stream) != cudaSuccess) return cuda_fail(st, cudaGetLastError());
+    for (int s = 0; s < st->prof_used; s++) {
+      const int q = st->prof_kind[s];
+      if (q < 0) continue;
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, st->prof_ev[2 * s], st->prof_ev[2 * s + 1]) != cudaSuccess) {
+        set_error("cudaEventElapsedTime", cudaGetLastError());
+        return HD_ERR_CUDA;
+      }
+      st->prof_ms[q] += ms;
+      st->prof_n[q] += 1;
+      st->prof_b[q] += st->prof_bytes[s];
+    }
+    // graph replays re-record the same events: keep the slots, read them again next time
+    if (!st->gexec || !st->prof_on) st->prof_used = 0;
+  }
+  for (int q = 0; q < 3; q++) {
+    if (ms3) ms3[q] = st->prof_ms[q];
+    if (launches3) launches3[q] = st->prof_n[q];
+    if (bytes3) bytes3[q] = st->prof_b[q];
+  }
+  if (clear)
+    for (int q = 0; q < 3; q++) st->prof_ms[q] = st->prof_n[q] = 0, st->prof_b[q] = 0.0;
+  return HD_OK;
+}
+
+HD_API int hd_get_launches(const hd_state* st, int64_t* launches) {
+  if (!st || !launches) return HD_ERR_ARG;
+  *launches = st->launches;
+  return HD_OK;
+}
+
+HD_API int hd_sync(hd_state* st) {
+  if (!st) return HD_ERR_ARG;
+  if (cudaSetDevice(st->device) != cudaSuccess) return cuda_fail(st, cudaErrorInvalidDevice);
+  unsigned int err = 0;
+  cudaError_t e = cudaMemcpyAsync(&err, st->ws.err, sizeof(err), cudaMemcpyDeviceToHost, st->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st->stream);
+  if (e != cudaSuccess) {
+    set_error("hd_sync", e);
+    return cuda_fail(st, e);
+  }
+  if (err) {
+    snprintf(g_last_error, sizeof(g_last_error), "device error word 0x%x (bounded wait expired)", err);
+    st->poisoned = HD_ERR_TIMEOUT;
+    return HD_ERR_TIMEOUT;
+  }
+  return st->poisoned;
+}
+
 HD_API int hd_reset(hd_state* st, uint64_t seed) {
   if (!st) return HD_ERR_ARG;
+  if (cudaSetDevice(st->device) == cudaSuccess) {
+    // clear election counters and the error word left by an aborted step
+    cudaMemsetAsync(st->ws.cnt, 0, (size_t)3 * (kMaxGroups + 1) * sizeof(unsigned int), st->stream);
+    cudaMemsetAsync(st->ws.err, 0, 16, st->stream);
+  }
   st->seed = seed;
   st->t = st->r = st->l = 0;
   st->drawn = 0;
@@ -430,6 +726,10 @@ HD_API void hd_destroy(hd_state* st) {
   if (!st) return;
   cudaSetDevice(st->device);
   if (st->stream) cudaStreamSynchronize(st->stream); else cudaDeviceSynchronize();
+  if (st->gexec) cudaGraphExecDestroy(st->gexec);
+  if (st->own_stream) cudaStreamDestroy(st->own_stream);
+  for (auto& ev : st->prof_ev)
+    if (ev) cudaEventDestroy(ev);
   free_all(st);
   delete st;
 }

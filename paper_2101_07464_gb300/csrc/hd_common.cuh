@@ -10,8 +10,7 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kChunkMax = 4;           // 16-byte vectors per thread per sweep (registers)
 constexpr int kColBlock = 8;           // stack columns per register block in a sweep
 constexpr int kFinThreads = 256;       // threads of the single-CTA finalisation
-constexpr int kColsPerThread = 4;      // K2 column owners: T_max <= kColsPerThread * kThreads
-constexpr int kTmaxLimit = kColsPerThread * kThreads;
+constexpr int kTmaxLimit = 256;        // column owners hold at most 8 columns per lane
 
 // ---------------------------------------------------------------------------------
 // 16-byte vectors: 4 floats or 2 doubles per thread access.

@@ -41,8 +41,8 @@ __device__ __forceinline__ void block_sum_to(const T (&a)[NV], double* red, doub
   __syncthreads();
   if (threadIdx.x < nvalid) {
     double s = 0.0;
-#pragma unroll
-    for (int w = 0; w < kWarps; w++) s += red[w * NV + threadIdx.x];
+    const int nw = blockDim.x >> 5;
+    for (int w = 0; w < nw; w++) s += red[w * NV + threadIdx.x];
     out[threadIdx.x] = s;
   }
   __syncthreads();
@@ -75,12 +75,14 @@ __device__ bool reduce_partials(const Ws& ws, int set, int P, const Grid& g, dou
   if (!elect_last(&cnt[grp], gcount)) return false;
   for (int j = threadIdx.x; j < P; j += blockDim.x) {
     double s = 0.0;
+#pragma unroll 8
     for (int c = 0; c < gcount; c++) s += ld_cg(&ws.part[(int64_t)(gfirst + c) * P + j]);
     ws.gpart[(int64_t)grp * P + j] = s;
   }
   if (!elect_last(&cnt[kMaxGroups], g.ngroups)) return false;
   for (int j = threadIdx.x; j < P; j += blockDim.x) {
     double s = 0.0;
+#pragma unroll 8
     for (int q = 0; q < g.ngroups; q++) s += ld_cg(&ws.gpart[(int64_t)q * P + j]);
     out[j] = s;
   }
@@ -132,59 +134,6 @@ __global__ void __launch_bounds__(kThreads) k_first_draw(StackDev X, int64_t cou
   double* out = ws.scr(0);
   if (!reduce_partials(ws, set, 1, g, out)) return;
   if (threadIdx.x == 0) X.gg[0] = out[0];
-}
-
-// ------------------------------------------------------------------------------------
-// K1: z = V_D^T x over k_D columns, then (Ginibre) the data-space basis columns.
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_dots(StepPlan<T> p) {
-  constexpr int N = Vec<T>::N;
-  __shared__ double red[kWarps * kColBlock];
-  const int64_t dim = p.D.dim;
-  const int na = p.kD, nb = (p.ens == 0) ? p.kN : 0, nc = na + nb;
-  const T* A = (const T*)p.D.V;
-  const T* B = (const T*)p.Bd;
-  Rows rw(p.g1, dim, N);
-  Vec<T> xr[kChunkMax];
-#pragma unroll
-  for (int c = 0; c < kChunkMax; c++) {
-    if (rw.active(c)) {
-      ld_caller(p.x, rw.vec(c) * N, dim, p.xal != 0, xr[c]);
-    } else {
-#pragma unroll
-      for (int e = 0; e < N; e++) xr[c].e[e] = T(0);
-    }
-  }
-  double* part = p.ws.part + (int64_t)blockIdx.x * nc;
-  for (int jb = 0; jb < nc; jb += kColBlock) {
-    T acc[kColBlock];
-#pragma unroll
-    for (int q = 0; q < kColBlock; q++) acc[q] = T(0);
-#pragma unroll
-    for (int c = 0; c < kChunkMax; c++) {
-      if (!rw.active(c)) continue;
-      const int64_t row = rw.vec(c) * N;
-#pragma unroll
-      for (int q = 0; q < kColBlock; q++) {
-        const int j = jb + q;
-        if (j < nc) {
-          const T* col = (j < na) ? A + (int64_t)j * p.D.ld : B + (int64_t)(j - na) * p.ldBd;
-          Vec<T> v;
-          ld_stream(col + row, v);
-          acc[q] = dot_vec(v, xr[c], acc[q]);
-        }
-      }
-    }
-    block_sum_to<kColBlock>(acc, red, part + jb, min(kColBlock, nc - jb));
-  }
-  if (!reduce_partials(p.ws, 0, nc, p.g1, p.ws.z)) return;
-  // w = S_D^T z (S upper triangular).
-  const int Tm = p.Tm;
-  for (int j = threadIdx.x; j < na; j += blockDim.x) {
-    double s = 0.0;
-    for (int i = 0; i <= j; i++) s = fma(p.D.S[i + (int64_t)j * Tm], p.ws.z[i], s);
-    p.ws.w[j] = s;
-  }
 }
 
 // ------------------------------------------------------------------------------------
@@ -314,151 +263,406 @@ __device__ void fin_update(const StepPlan<T>& p, const double* r) {
   }
 }
 
-// K2: p = Delta_D (x - V_D w); new column k of V_D; next draw; exact dots of p[k:] and of
-// the next draw with the old columns of V_D.
+// ------------------------------------------------------------------------------------
+// Warp sub-tile engine shared by the three sweeps.
 //
-// The dots of p need p final, i.e. after all k columns of a row were applied, so the sweep
-// stages a tile of R rows x k columns of V_D in shared memory (one HBM read):
-//   loop 1, row owners:    p_i = Delta_i (x_i - sum_j V_ij w_j)  (256/R threads per row);
-//   loop 2, column owners: thread j accumulates sum_i V_ij p_i and sum_i V_ij g_i.
-// The tile has row stride R + 1 so that both loops are free of bank conflicts.
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
-}
-__device__ __forceinline__ void cp_async_elem(float* s, const float* g) { cp_async4(s, g); }
-__device__ __forceinline__ void cp_async_elem(double* s, const double* g) { cp_async8(s, g); }
+// Every warp walks its own 32-row sub-tiles (lane = row) of the stack, grid-strided over
+// all warps of the launch, with no CTA-wide synchronisation inside the walk.  A sub-tile
+// (32 rows x ncol columns) is copied by 16-byte cp.async into the warp's shared-memory
+// slice, column-major with the 16-byte chunk q of column j stored at slot (q + j) mod NCH.
+// On it two access patterns run without bank conflicts:
+//   row owner:    lane i computes out[i] = sum_j V[i, j] coef[j]   (4-byte reads, one row
+//                 per lane, coefficients read 16 bytes at a time);
+//   column owner: lane l owns columns l, l + 32, ... and adds sum_i V[i, j] rhs[i] (16-byte
+//                 reads of its column's rotated chunks, the rhs chunk is a broadcast) to
+//                 FP64 accumulators that persist across sub-tiles.
+// At the end the warps of a CTA add their column sums in shared memory and the CTA joins
+// the two-level last-block reduction.
 
+template <typename T>
+struct ColSrc {
+  const T* A;
+  int64_t ldA;
+  int nA;
+  const T* B;
+  int64_t ldB;
+  __device__ __forceinline__ const T* col(int j) const {
+    return (j < nA) ? A + (int64_t)j * ldA : B + (int64_t)(j - nA) * ldB;
+  }
+};
+
+template <typename T>
+struct WT {
+  static constexpr int ROWS = 32;
+  static constexpr int VEC = 16 / (int)sizeof(T);  // elements per 16-byte chunk
+  static constexpr int NCH = ROWS / VEC;           // chunks per column: 8 (FP32), 16 (FP64)
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* ptr) {
+  return (uint32_t)__cvta_generic_to_shared(ptr);
+}
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Copy rows [r0, r0 + 32) of ncol columns into a warp stage (no commit).
+template <typename T>
+__device__ __forceinline__ void wt_load_cols(T* buf, const ColSrc<T>& src, int ncol, int64_t r0) {
+  constexpr int NCH = WT<T>::NCH, VEC = WT<T>::VEC;
+  const int lane = threadIdx.x & 31;
+  for (int c = lane; c < ncol * NCH; c += 32) {
+    const int j = c / NCH, q = c & (NCH - 1);
+    cp_async16(buf + j * 32 + ((q + j) & (NCH - 1)) * VEC, src.col(j) + r0 + q * VEC);
+  }
+}
+__device__ __forceinline__ void cp_async16_zfill(void* smem, const void* gmem, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(smem)), "l"(gmem),
+               "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async4_zfill(void* smem, const void* gmem, int src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(smem_u32(smem)), "l"(gmem),
+               "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async8_zfill(void* smem, const void* gmem, int src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(smem_u32(smem)), "l"(gmem),
+               "r"(src_bytes) : "memory");
+}
+// Copy rows [r0, r0 + 32) of a vector of length dim into dst (32 elements), zero beyond
+// dim; 16-byte copies when the vector is 16-byte aligned, element copies otherwise.
+template <typename T>
+__device__ __forceinline__ void wt_load_vec(T* dst, const T* v, int64_t r0, int64_t dim, bool al) {
+  constexpr int VEC = WT<T>::VEC, NCH = WT<T>::NCH;
+  const int lane = threadIdx.x & 31;
+  if (al) {
+    if (lane < NCH) {
+      const int64_t row = r0 + lane * VEC;
+      const int64_t avail = dim - row;
+      const int bytes = (avail <= 0) ? 0 : (avail >= VEC ? 16 : (int)(avail * sizeof(T)));
+      cp_async16_zfill(dst + lane * VEC, bytes > 0 ? (const void*)(v + row) : (const void*)v, bytes);
+    }
+  } else {
+    const int64_t row = r0 + lane;
+    const int bytes = (row < dim) ? (int)sizeof(T) : 0;
+    if (sizeof(T) == 4) cp_async4_zfill(dst + lane, bytes ? (const void*)(v + row) : (const void*)v, bytes);
+    else cp_async8_zfill(dst + lane, bytes ? (const void*)(v + row) : (const void*)v, bytes);
+  }
+}
+// cp.async.wait_group with a run-time count of groups allowed to stay pending (0..7).
+__device__ __forceinline__ void cp_async_wait_dyn(int pending) {
+  switch (pending) {
+    case 0: cp_async_wait<0>(); break;
+    case 1: cp_async_wait<1>(); break;
+    case 2: cp_async_wait<2>(); break;
+    case 3: cp_async_wait<3>(); break;
+    case 4: cp_async_wait<4>(); break;
+    case 5: cp_async_wait<5>(); break;
+    case 6: cp_async_wait<6>(); break;
+    default: cp_async_wait<7>(); break;
+  }
+}
+
+// Row owner: out[o] = sum_j V[lane, j] coef_o[j], o < NO (coef arrays padded to VEC).
+template <typename T, int NO>
+__device__ __forceinline__ void wt_rows(const T* buf, int ncol, const T* coef0, const T* coef1,
+                                        T (&out)[NO]) {
+  constexpr int NCH = WT<T>::NCH, VEC = WT<T>::VEC;
+  const int lane = threadIdx.x & 31;
+  const int qi = lane / VEC, ri = lane & (VEC - 1);
+#pragma unroll
+  for (int o = 0; o < NO; o++) out[o] = T(0);
+  int j = 0;
+  for (; j + VEC <= ncol; j += VEC) {
+    const Vec<T> c0 = *reinterpret_cast<const Vec<T>*>(coef0 + j);
+    Vec<T> c1;
+    if (NO > 1) c1 = *reinterpret_cast<const Vec<T>*>(coef1 + j);
+#pragma unroll
+    for (int e = 0; e < VEC; e++) {
+      const int jj = j + e;
+      const T v = buf[jj * 32 + ((qi + jj) & (NCH - 1)) * VEC + ri];
+      out[0] = fma(v, c0.e[e], out[0]);
+      if (NO > 1) out[NO - 1] = fma(v, c1.e[e], out[NO - 1]);
+    }
+  }
+  for (; j < ncol; j++) {
+    const T v = buf[j * 32 + ((qi + j) & (NCH - 1)) * VEC + ri];
+    out[0] = fma(v, coef0[j], out[0]);
+    if (NO > 1) out[NO - 1] = fma(v, coef1[j], out[NO - 1]);
+  }
+}
+
+constexpr int kColsPerLane = 8;   // column owner: up to 8 * 32 = 256 columns
+
+// Column owner: acc[r][m] += sum_i V[i, lane + 32 m] rhs_r[i] over the 32 rows, m < 8.
+template <typename T, int NR>
+__device__ __forceinline__ void wt_cols(const T* buf, int ncol, const T* rhs0, const T* rhs1,
+                                        double (&acc)[NR][kColsPerLane]) {
+  constexpr int NCH = WT<T>::NCH, VEC = WT<T>::VEC;
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int m = 0; m < kColsPerLane; m++) {
+    const int j = lane + 32 * m;
+    if (32 * m >= ncol) break;
+    if (j < ncol) {
+      T s[NR];
+#pragma unroll
+      for (int r = 0; r < NR; r++) s[r] = T(0);
+      const T* col = buf + j * 32;
+#pragma unroll
+      for (int c = 0; c < NCH; c++) {
+        const Vec<T> v = *reinterpret_cast<const Vec<T>*>(col + ((c + j) & (NCH - 1)) * VEC);
+        const Vec<T> b0 = *reinterpret_cast<const Vec<T>*>(rhs0 + c * VEC);
+#pragma unroll
+        for (int e = 0; e < VEC; e++) s[0] = fma(v.e[e], b0.e[e], s[0]);
+        if (NR > 1) {
+          const Vec<T> b1 = *reinterpret_cast<const Vec<T>*>(rhs1 + c * VEC);
+#pragma unroll
+          for (int e = 0; e < VEC; e++) s[NR - 1] = fma(v.e[e], b1.e[e], s[NR - 1]);
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < NR; r++) acc[r][m] += (double)s[r];
+    }
+  }
+}
+
+// Shared-memory layout of a sweep launch with W warps, each with nb pipeline stages of ncolT
+// staged columns and NRV staged row vectors (32 elements each), plus two scratch row vectors
+// per warp, two coefficient arrays (padded to 16 bytes) and the W x NR x ncolC FP64 column
+// sums.
+template <typename T>
+struct WtSmem {
+  T* stages;         // W * nb * sstride
+  T* scratch;        // W * 2 * 32
+  T* coef;           // 2 * cpad
+  double* comb;      // W * NR * ncolC
+  int sstride;       // elements per stage: (ncolT + NRV) * 32
+  int ncolT;
+  int nb;
+  int cpad;
+  __device__ WtSmem(unsigned char* base, int W, int nbuf, int ncolT_, int NRV, int ncolC, int NR) {
+    constexpr int VEC = WT<T>::VEC;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+      unsigned char* p = base + off;
+      off += (bytes + 15) & ~(size_t)15;
+      return p;
+    };
+    ncolT = ncolT_;
+    nb = nbuf;
+    sstride = (ncolT + NRV) * 32;
+    stages = (T*)take((size_t)W * nb * sstride * sizeof(T));
+    scratch = (T*)take((size_t)W * 2 * 32 * sizeof(T));
+    cpad = (ncolT + VEC - 1) / VEC * VEC;
+    coef = (T*)take((size_t)2 * cpad * sizeof(T));
+    comb = (double*)take((size_t)W * NR * (ncolC > 0 ? ncolC : 1) * sizeof(double));
+  }
+  __device__ __forceinline__ T* stage(int warp, int b) const {
+    return stages + ((size_t)warp * nb + b) * sstride;
+  }
+  // staged row vector q of a stage (after the ncolT columns)
+  __device__ __forceinline__ T* srow(T* st, int q) const { return st + (size_t)(ncolT + q) * 32; }
+  __device__ __forceinline__ T* scr(int warp, int q) const { return scratch + ((size_t)warp * 2 + q) * 32; }
+};
+
+// Sum the warps' column-owner accumulators and store this CTA's partials part[off_r + j].
+template <int NR>
+__device__ __forceinline__ void wt_store_cols(double* comb, int ncolC, const double (&acc)[NR][kColsPerLane],
+                                              double* part, const int (&off)[NR]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
+#pragma unroll
+  for (int m = 0; m < kColsPerLane; m++) {
+    const int j = lane + 32 * m;
+    if (j < ncolC) {
+#pragma unroll
+      for (int r = 0; r < NR; r++) comb[((size_t)warp * NR + r) * ncolC + j] = acc[r][m];
+    }
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < ncolC; j += blockDim.x) {
+#pragma unroll
+    for (int r = 0; r < NR; r++) {
+      double s = 0.0;
+      for (int w = 0; w < W; w++) s += comb[((size_t)w * NR + r) * ncolC + j];
+      part[off[r] + j] = s;
+    }
+  }
+}
+
+// Per-lane pair sharing of the Gaussian draw: even lanes draw normals (2j, 2j+1), odd lanes
+// receive the second one; rows outside [first, dim) get 0; scaled by sigma.
+template <typename T>
+__device__ __forceinline__ T wt_draw(const DrawKey& key, int64_t row, int64_t first, int64_t dim, T sigma) {
+  const int lane = threadIdx.x & 31;
+  T a = T(0), b = T(0);
+  const int64_t r0 = row & ~(int64_t)1;
+  if (!(lane & 1) && r0 + 1 >= first && r0 < dim) normal_pair(key, (uint64_t)(r0 >> 1), a, b);
+  const T other = __shfl_up_sync(0xffffffffu, b, 1);
+  const T g = (lane & 1) ? other : a;
+  return (row >= first && row < dim) ? sigma * g : T(0);
+}
+
+// Walk of a warp over its sub-tiles: first sub-tile gw, stride GW.
+struct WarpWalk {
+  int64_t first, stride, nsub;
+  __device__ WarpWalk(int64_t dim) {
+    const int W = blockDim.x >> 5;
+    first = (int64_t)blockIdx.x * W + (threadIdx.x >> 5);
+    stride = (int64_t)gridDim.x * W;
+    nsub = (dim + 31) / 32;
+  }
+  __device__ __forceinline__ int64_t sub(int it) const { return first + (int64_t)it * stride; }
+  __device__ __forceinline__ int count() const {
+    return (first < nsub) ? (int)((nsub - 1 - first) / stride + 1) : 0;
+  }
+};
+
+// The walk of one warp as an nb-stage cp.async pipeline: load(it, stage) must issue the
+// copies of local sub-tile it into the stage; body(it, stage) runs once its data is ready.
+template <typename Load, typename Body>
+__device__ __forceinline__ void wt_pipeline(int count, int nb, Load&& load, Body&& body) {
+  for (int q = 0; q < nb - 1; q++) {
+    if (q < count) load(q, q);
+    cp_async_commit();
+  }
+  for (int it = 0; it < count; it++) {
+    const int nxt = it + nb - 1;
+    if (nxt < count) load(nxt, nxt % nb);
+    cp_async_commit();
+    cp_async_wait_dyn(nb - 1);
+    __syncwarp();
+    body(it, it % nb);
+    __syncwarp();
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// K1: z = V_D^T x over k_D columns (and, for Ginibre, x . the k_N data-space basis
+// columns); last CTA: w = S_D^T z.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_dots(StepPlan<T> p) {
+  extern __shared__ __align__(16) unsigned char dsm_raw[];
+  const int na = p.kD, nb = (p.ens == 0) ? p.kN : 0, nc = na + nb;
+  const SweepCfg& cfg = p.c1;
+  const int warp = threadIdx.x >> 5;
+  WtSmem<T> sm(dsm_raw, blockDim.x >> 5, cfg.nbuf, nc, 1, nc, 1);
+  const ColSrc<T> src{(const T*)p.D.V, p.D.ld, na, (const T*)p.Bd, p.ldBd};
+  const int64_t dim = p.D.dim;
+  double acc[1][kColsPerLane];
+#pragma unroll
+  for (int m = 0; m < kColsPerLane; m++) acc[0][m] = 0.0;
+  const WarpWalk ww(dim);
+  const bool xal = p.xal != 0;
+  wt_pipeline(ww.count(), cfg.nbuf,
+      [&](int it, int b) {
+        T* st = sm.stage(warp, b);
+        const int64_t r0 = ww.sub(it) * 32;
+        wt_load_cols(st, src, nc, r0);
+        wt_load_vec(sm.srow(st, 0), p.x, r0, dim, xal);
+      },
+      [&](int it, int b) {
+        T* st = sm.stage(warp, b);
+        wt_cols<T, 1>(st, nc, sm.srow(st, 0), nullptr, acc);
+      });
+  const int off[1] = {0};
+  wt_store_cols<1>(sm.comb, nc, acc, p.ws.part + (int64_t)blockIdx.x * nc, off);
+  if (!reduce_partials(p.ws, 0, nc, cfg.g, p.ws.z)) return;
+  const int Tm = p.Tm;
+  for (int j = threadIdx.x; j < na; j += blockDim.x) {
+    double s = 0.0;
+#pragma unroll 4
+    for (int i = 0; i <= j; i++) s = fma(p.D.S[i + (int64_t)j * Tm], p.ws.z[i], s);
+    p.ws.w[j] = s;
+  }
+}
+
+// K2: p = Delta_D (x - V_D w); writes p[k:] as the new column k of V_D; draws g_{t+1}
+// (rows > k) into the data stack's buffer; exact V_D^T p[k:] and V_D^T g_{t+1}.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_update(StepPlan<T> p) {
   extern __shared__ __align__(16) unsigned char dsm_raw[];
   __shared__ double red[kWarps * 4];
-  const int k = p.kD, R = p.R2, Rs = R + 1;
-  const int G1 = kThreads / R;               // threads per row in loop 1
-  T* Vt = reinterpret_cast<T*>(dsm_raw);     // k x Rs
-  T* pv = Vt + (size_t)k * Rs;               // R: p[k:] (zero above row k)
-  T* gv = pv + R;                            // R: next draw
-  T* ps = gv + R;                            // kThreads: loop-1 partial sums
-  T* wsm = ps + kThreads;                    // k: w
-  const int tid = threadIdx.x;
+  const int k = p.kD;
+  const SweepCfg& cfg = p.c2;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  WtSmem<T> sm(dsm_raw, blockDim.x >> 5, cfg.nbuf, k, 1, k, 2);
+  for (int j = threadIdx.x; j < sm.cpad; j += blockDim.x) sm.coef[j] = (j < k) ? (T)p.ws.w[j] : T(0);
+  __syncthreads();
+  const ColSrc<T> src{(const T*)p.D.V, p.D.ld, k, nullptr, 0};
   const int64_t dim = p.D.dim;
-  for (int j = tid; j < k; j += kThreads) wsm[j] = (T)p.ws.w[j];
-  T* V = (T*)p.D.V;
-  const int64_t ld = p.D.ld;
+  T* col = (T*)p.D.V + (int64_t)k * p.D.ld;
   T* gb = (T*)p.D.gbuf;
-  T* col = V + (int64_t)k * ld;
   const T dconst = (T)p.D.dpre[k];
-  const int ri = tid % R, rq = tid / R;
-  double accp[kColsPerThread], accg[kColsPerThread];  // columns tid + c*kThreads
+  double acc[2][kColsPerLane];
 #pragma unroll
-  for (int c = 0; c < kColsPerThread; c++) accp[c] = accg[c] = 0.0;
-  T ex[3] = {T(0), T(0), T(0)};              // p . g_next, ||p[k+1:]||^2, ||g_next[k+2:]||^2
-  for (int64_t tile = blockIdx.x; tile < p.ntiles2; tile += gridDim.x) {
-    const int64_t r0 = tile * R;
-    for (int idx = tid; idx < k * R; idx += kThreads) {
-      const int j = idx / R, i = idx - j * R;
-      if (r0 + i < ld) cp_async_elem(&Vt[j * Rs + i], V + (int64_t)j * ld + r0 + i);
-      else Vt[j * Rs + i] = T(0);
-    }
-    if (tid < R / 2) {
-      T a, b;
-      const int64_t row = r0 + 2 * tid;
-      if (row + 1 >= (int64_t)k + 1 && row < dim) {
-        normal_pair(p.key_next, (uint64_t)(row >> 1), a, b);
-        a = (row >= (int64_t)k + 1 && row < dim) ? p.sigma * a : T(0);
-        b = (row + 1 >= (int64_t)k + 1 && row + 1 < dim) ? p.sigma * b : T(0);
-      } else {
-        a = b = T(0);
-      }
-      gv[2 * tid] = a;
-      gv[2 * tid + 1] = b;
-    }
-    cp_async_wait_all();
-    __syncthreads();
-    {
-      T s = T(0);
-      for (int j = rq; j < k; j += G1) s = fma(Vt[j * Rs + ri], wsm[j], s);
-      ps[rq * R + ri] = s;
-    }
-    __syncthreads();
-    if (tid < R) {
-      const int64_t i = r0 + tid;
-      T xi = T(0);
-      if (i < dim) xi = p.x[i];
-      T acc = xi;
-      for (int q = 0; q < G1; q++) acc -= ps[q * R + tid];
-      const T d = (i < k) ? (T)p.D.dpre[i + 1] : dconst;
-      const T pvv = acc * d;
-      const T g = gv[tid];
-      if (i < dim) {
-        if (i < k) p.ws.phead[i] = (double)pvv;
-        else {
-          col[i] = pvv;
-          if (i == k) p.ws.scal[kPpiv] = (double)pvv;
-          else ex[1] = fma(pvv, pvv, ex[1]);
-          ex[0] = fma(pvv, g, ex[0]);
+  for (int m = 0; m < kColsPerLane; m++) acc[0][m] = acc[1][m] = 0.0;
+  T ex[3] = {T(0), T(0), T(0)};   // p . g_next, ||p[k+1:]||^2, ||g_next[k+2:]||^2
+  T* pv = sm.scr(warp, 0);
+  T* gv = sm.scr(warp, 1);
+  const WarpWalk ww(dim);
+  const bool xal = p.xal != 0;
+  wt_pipeline(ww.count(), cfg.nbuf,
+      [&](int it, int b) {
+        T* st = sm.stage(warp, b);
+        const int64_t r0 = ww.sub(it) * 32;
+        wt_load_cols(st, src, k, r0);
+        wt_load_vec(sm.srow(st, 0), p.x, r0, dim, xal);
+      },
+      [&](int it, int b) {
+        T* st = sm.stage(warp, b);
+        const int64_t r = ww.sub(it) * 32 + lane;
+        const T g = wt_draw(p.key_next, r, (int64_t)k + 1, dim, p.sigma);
+        T out[1];
+        wt_rows<T, 1>(st, k, sm.coef, nullptr, out);
+        const T d = (r < k) ? (T)p.D.dpre[r + 1] : dconst;
+        const T pvv = (sm.srow(st, 0)[lane] - out[0]) * d;
+        if (r < dim) {
+          if (r < k) {
+            p.ws.phead[r] = (double)pvv;
+          } else {
+            col[r] = pvv;
+            if (r == k) p.ws.scal[kPpiv] = (double)pvv;
+            else ex[1] = fma(pvv, pvv, ex[1]);
+            ex[0] = fma(pvv, g, ex[0]);
+          }
+          if (r >= (int64_t)k + 2) ex[2] = fma(g, g, ex[2]);
         }
-        if (i >= (int64_t)k + 2) ex[2] = fma(g, g, ex[2]);
-      }
-      if (i < ld) gb[i] = g;
-      pv[tid] = (i >= k && i < dim) ? pvv : T(0);
-    }
-    __syncthreads();
-#pragma unroll
-    for (int c = 0; c < kColsPerThread; c++) {
-      const int j = tid + c * kThreads;
-      if (j < k) {
-        T sp = T(0), sg = T(0);
-        const T* vc = Vt + j * Rs;
-        for (int i = 0; i < R; i++) {
-          const T v = vc[i];
-          sp = fma(v, pv[i], sp);
-          sg = fma(v, gv[i], sg);
-        }
-        accp[c] += (double)sp;
-        accg[c] += (double)sg;
-      }
-    }
-    __syncthreads();
-  }
+        gb[r] = g;   // the buffer has ld >= 32 * nsub entries
+        pv[lane] = (r >= k && r < dim) ? pvv : T(0);
+        gv[lane] = g;
+        __syncwarp();
+        wt_cols<T, 2>(st, k, pv, gv, acc);
+      });
   const int P = 2 * k + 3;
   double* part = p.ws.part + (int64_t)blockIdx.x * P;
-#pragma unroll
-  for (int c = 0; c < kColsPerThread; c++) {
-    const int j = tid + c * kThreads;
-    if (j < k) {
-      part[j] = accg[c];
-      part[k + 3 + j] = accp[c];
-    }
-  }
+  const int off[2] = {k + 3, 0};   // p-dots after the three extras, draw dots first
+  wt_store_cols<2>(sm.comb, k, acc, part, off);
   block_sum_to<3>(ex, red, part + k, 3);
-  double* r = p.ws.scr(3);
-  if (!reduce_partials(p.ws, 1, P, p.g2, r)) return;
-  fin_update<T>(p, r);
+  double* rr = p.ws.scr(3);
+  if (!reduce_partials(p.ws, 1, P, cfg.g, rr)) return;
+  fin_update<T>(p, rr);
 }
 
-// ------------------------------------------------------------------------------------
-// K3 (Haar): y = Delta_N c - V_N w', appends the random reflector column, and dots of the
-// next draw (copied from the data stack's buffer) with V_N.
+// K3 (Haar): y = Delta_N c - V_N w' with c = [p_head; coef g_t[k:]]; appends the random
+// reflector column (g_t[k:] with the pivot entry replaced); the next draw (read from the
+// data stack's buffer) replaces g_t in this stack's buffer; dots of it with V_N.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_out_haar(StepPlan<T> p) {
-  constexpr int N = Vec<T>::N;
-  extern __shared__ unsigned char dsm_raw[];
-  T* wsm = reinterpret_cast<T*>(dsm_raw);
-  __shared__ double red[kWarps * kColBlock];
+  extern __shared__ __align__(16) unsigned char dsm_raw[];
+  __shared__ double red[kWarps * 4];
   const int k = p.kN;
-  const int64_t dim = p.N.dim;
-  for (int j = threadIdx.x; j < k; j += kThreads) wsm[j] = (T)p.ws.wout[j];
+  const SweepCfg& cfg = p.c3;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  WtSmem<T> sm(dsm_raw, blockDim.x >> 5, cfg.nbuf, k, 2, k, 1);
+  for (int j = threadIdx.x; j < sm.cpad; j += blockDim.x) sm.coef[j] = (j < k) ? (T)p.ws.wout[j] : T(0);
   __syncthreads();
-  T* V = (T*)p.N.V;
-  const int64_t ld = p.N.ld;
+  const ColSrc<T> src{(const T*)p.N.V, p.N.ld, k, nullptr, 0};
+  const int64_t dim = p.N.dim;
+  T* col = (T*)p.N.V + (int64_t)k * p.N.ld;
   T* gcur = (T*)p.N.gbuf;
   const T* gnext = (const T*)p.D.gbuf;
   const T coef = (T)p.ws.scal[kCoef];
@@ -466,191 +670,123 @@ __global__ void __launch_bounds__(kThreads) k_out_haar(StepPlan<T> p) {
   const T usg = (T)p.ws.scal[kUpivG];
   const bool flag = p.ws.scal[kGFlag] != 0.0;
   const T dconst = (T)p.N.dpre[k];
-  Rows rw(p.g3, dim, N);
-  Vec<T> yr[kChunkMax], gn[kChunkMax];
+  double acc[1][kColsPerLane];
+#pragma unroll
+  for (int m = 0; m < kColsPerLane; m++) acc[0][m] = 0.0;
   T ex[1] = {T(0)};
-#pragma unroll
-  for (int c = 0; c < kChunkMax; c++) {
-    if (!rw.active(c)) {
-#pragma unroll
-      for (int e = 0; e < N; e++) yr[c].e[e] = gn[c].e[e] = T(0);
-      continue;
-    }
-    const int64_t row = rw.vec(c) * N;
-    Vec<T> g, ncol;
-    ld_stream(gcur + row, g);
-    ld_stream(gnext + row, gn[c]);
-#pragma unroll
-    for (int e = 0; e < N; e++) {
-      const int64_t i = row + e;
-      T ci;
-      if (i < k) ci = (T)p.ws.phead[i];
-      else if (flag) ci = (i == k) ? alpha : T(0);
-      else ci = coef * g.e[e];
-      const T d = (i < k) ? (T)p.N.dpre[i + 1] : dconst;
-      yr[c].e[e] = d * ci;
-      ncol.e[e] = (i > k) ? g.e[e] : ((i == k) ? usg : T(0));
-      ex[0] = fma(ncol.e[e], gn[c].e[e], ex[0]);
-    }
-    T* col = V + (int64_t)k * ld;
-    if (row >= k && row + N <= dim) {
-      st_vec(col + row, ncol);
-    } else {
-#pragma unroll
-      for (int e = 0; e < N; e++)
-        if (row + e >= k && row + e < dim) col[row + e] = ncol.e[e];
-    }
-    st_vec(gcur + row, gn[c]);
-  }
+  const WarpWalk ww(dim);
+  const int64_t ld = p.N.ld;
+  wt_pipeline(ww.count(), cfg.nbuf,
+      [&](int it, int b) {
+        T* st = sm.stage(warp, b);
+        const int64_t r0 = ww.sub(it) * 32;
+        wt_load_cols(st, src, k, r0);
+        wt_load_vec(sm.srow(st, 0), (const T*)gcur, r0, ld, true);
+        wt_load_vec(sm.srow(st, 1), gnext, r0, ld, true);
+      },
+      [&](int it, int b) {
+        T* st = sm.stage(warp, b);
+        const int64_t r = ww.sub(it) * 32 + lane;
+        const T g = sm.srow(st, 0)[lane];
+        const T gn = sm.srow(st, 1)[lane];
+        T out[1];
+        wt_rows<T, 1>(st, k, sm.coef, nullptr, out);
+        T ci;
+        if (r < k) ci = (T)p.ws.phead[r];
+        else if (flag) ci = (r == k) ? alpha : T(0);
+        else ci = coef * g;
+        const T d = (r < k) ? (T)p.N.dpre[r + 1] : dconst;
+        const T yi = d * ci - out[0];
+        const T nc = (r > k) ? g : ((r == k) ? usg : T(0));
+        if (r < dim) {
+          p.y[r] = yi;
+          if (r >= k) col[r] = nc;
+        }
+        ex[0] = fma(nc, gn, ex[0]);
+        gcur[r] = gn;
+        wt_cols<T, 1>(st, k, sm.srow(st, 1), nullptr, acc);
+      });
   const int P = k + 1;
   double* part = p.ws.part + (int64_t)blockIdx.x * P;
-  for (int jb = 0; jb < k; jb += kColBlock) {
-    T acc[kColBlock];
-#pragma unroll
-    for (int q = 0; q < kColBlock; q++) acc[q] = T(0);
-#pragma unroll
-    for (int c = 0; c < kChunkMax; c++) {
-      if (!rw.active(c)) continue;
-      const int64_t row = rw.vec(c) * N;
-#pragma unroll
-      for (int q = 0; q < kColBlock; q++) {
-        const int j = jb + q;
-        if (j < k) {
-          Vec<T> v;
-          ld_stream(V + (int64_t)j * ld + row, v);
-          const T wj = wsm[j];
-#pragma unroll
-          for (int e = 0; e < N; e++) yr[c].e[e] = fma(-v.e[e], wj, yr[c].e[e]);
-          acc[q] = dot_vec(v, gn[c], acc[q]);
-        }
-      }
-    }
-    block_sum_to<kColBlock>(acc, red, part + jb, min(kColBlock, k - jb));
-  }
-#pragma unroll
-  for (int c = 0; c < kChunkMax; c++)
-    if (rw.active(c)) st_caller(p.y, rw.vec(c) * N, dim, p.yal != 0, yr[c]);
+  const int off[1] = {0};
+  wt_store_cols<1>(sm.comb, k, acc, part, off);
   block_sum_to<1>(ex, red, part + k, 1);
-  double* r = p.ws.scr(3);
-  if (!reduce_partials(p.ws, 2, P, p.g3, r)) return;
-  for (int j = threadIdx.x; j <= k; j += blockDim.x) p.N.gdot[j] = r[j];
+  double* rr = p.ws.scr(3);
+  if (!reduce_partials(p.ws, 2, P, cfg.g, rr)) return;
+  for (int j = threadIdx.x; j <= k; j += blockDim.x) p.N.gdot[j] = rr[j];
   if (threadIdx.x == 0) p.N.gg[0] = p.D.gg[0];
 }
 
-// K3 (Ginibre): u = Delta_N g - V_N w_2 (= L_1..L_l Z g), y = alpha u + Delta_N h - V_N w_h
-// + B_n c, appends u to the other-space basis, draws g_{t+1} and its dots with V_N.
+// K3 (Ginibre): u = Delta_N g - V_N w_2 (= L_1..L_l Z_{1:l} g), y = alpha u + Delta_N h
+// - V_N w_h + B_n c; u becomes the new basis column; the next draw (rows >= k_N) replaces g
+// in this stack's buffer, with its dots with V_N.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_out_gin(StepPlan<T> p) {
-  constexpr int N = Vec<T>::N;
-  extern __shared__ unsigned char dsm_raw[];
-  const int kN = p.kN, kD = p.kD;
-  T* w2 = reinterpret_cast<T*>(dsm_raw);
-  T* wh = w2 + kN;
-  T* cb = wh + kN;
-  __shared__ double red[kWarps * kColBlock];
-  const int64_t dim = p.N.dim;
-  for (int j = threadIdx.x; j < kN; j += kThreads) {
-    w2[j] = (T)p.ws.wout2[j];
-    wh[j] = (T)p.ws.wout[j];
+  extern __shared__ __align__(16) unsigned char dsm_raw[];
+  const int kN = p.kN, kD = p.kD, nc = kN + kD;
+  const SweepCfg& cfg = p.c3;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  WtSmem<T> sm(dsm_raw, blockDim.x >> 5, cfg.nbuf, nc, 1, kN, 1);
+  for (int j = threadIdx.x; j < sm.cpad; j += blockDim.x) {
+    T c0 = T(0), c1 = T(0);
+    if (j < kN) {
+      c0 = (T)p.ws.wout2[j];
+      c1 = (T)p.ws.wout[j];
+    } else if (j < nc) {
+      c1 = -(T)p.ws.phead[j - kN];
+    }
+    sm.coef[j] = c0;
+    sm.coef[sm.cpad + j] = c1;
   }
-  for (int j = threadIdx.x; j < kD; j += kThreads) cb[j] = (T)p.ws.phead[j];
   __syncthreads();
-  const T* V = (const T*)p.N.V;
-  const int64_t ld = p.N.ld;
-  T* Bn = (T*)p.Bn;
+  const ColSrc<T> src{(const T*)p.N.V, p.N.ld, kN, (const T*)p.Bn, p.ldBn};
+  const int64_t dim = p.N.dim;
+  T* ucol = (T*)p.Bn + (int64_t)kD * p.ldBn;
   T* gcur = (T*)p.N.gbuf;
   const double* h = p.ws.z + kD;
   const T alpha = (T)p.ws.scal[kAlpha];
   const T dconst = (T)p.N.dpre[kN];
-  Rows rw(p.g3, dim, N);
-  Vec<T> ur[kChunkMax], yr[kChunkMax], gn[kChunkMax];
+  double acc[1][kColsPerLane];
 #pragma unroll
-  for (int c = 0; c < kChunkMax; c++) {
-    if (!rw.active(c)) {
-#pragma unroll
-      for (int e = 0; e < N; e++) ur[c].e[e] = yr[c].e[e] = gn[c].e[e] = T(0);
-      continue;
-    }
-    const int64_t row = rw.vec(c) * N;
-    Vec<T> g;
-    ld_stream(gcur + row, g);
-    draw_vec(p.key_next, row, (int64_t)kN, dim, p.sigma, gn[c]);
-#pragma unroll
-    for (int e = 0; e < N; e++) {
-      const int64_t i = row + e;
-      const T d = (i < kN) ? (T)p.N.dpre[i + 1] : dconst;
-      ur[c].e[e] = d * g.e[e];
-      yr[c].e[e] = (i < kN) ? d * (T)h[i] : T(0);
-    }
-    st_vec(gcur + row, gn[c]);
-  }
+  for (int m = 0; m < kColsPerLane; m++) acc[0][m] = 0.0;
+  T* gv = sm.scr(warp, 0);
+  const WarpWalk ww(dim);
+  const int64_t ld = p.N.ld;
+  wt_pipeline(ww.count(), cfg.nbuf,
+      [&](int it, int b) {
+        T* st = sm.stage(warp, b);
+        const int64_t r0 = ww.sub(it) * 32;
+        wt_load_cols(st, src, nc, r0);
+        wt_load_vec(sm.srow(st, 0), (const T*)gcur, r0, ld, true);
+      },
+      [&](int it, int b) {
+        T* st = sm.stage(warp, b);
+        const int64_t r = ww.sub(it) * 32 + lane;
+        const T g = sm.srow(st, 0)[lane];
+        const T hi = (r < kN) ? (T)h[r] : T(0);
+        const T gn = wt_draw(p.key_next, r, (int64_t)kN, dim, p.sigma);
+        T out[2];
+        wt_rows<T, 2>(st, nc, sm.coef, sm.coef + sm.cpad, out);
+        const T d = (r < kN) ? (T)p.N.dpre[r + 1] : dconst;
+        const T u = d * g - out[0];
+        const T yi = fma(alpha, u, d * hi) - out[1];
+        if (r < dim) {
+          ucol[r] = u;
+          p.y[r] = yi;
+        }
+        gcur[r] = gn;
+        gv[lane] = gn;
+        __syncwarp();
+        wt_cols<T, 1>(st, kN, gv, nullptr, acc);
+      });
+  if (kN == 0) return;   // no dots to form
   const int P = kN;
   double* part = p.ws.part + (int64_t)blockIdx.x * P;
-  for (int jb = 0; jb < kN; jb += kColBlock) {
-    T acc[kColBlock];
-#pragma unroll
-    for (int q = 0; q < kColBlock; q++) acc[q] = T(0);
-#pragma unroll
-    for (int c = 0; c < kChunkMax; c++) {
-      if (!rw.active(c)) continue;
-      const int64_t row = rw.vec(c) * N;
-#pragma unroll
-      for (int q = 0; q < kColBlock; q++) {
-        const int j = jb + q;
-        if (j < kN) {
-          Vec<T> v;
-          ld_stream(V + (int64_t)j * ld + row, v);
-          const T a2 = w2[j], ah = wh[j];
-#pragma unroll
-          for (int e = 0; e < N; e++) {
-            ur[c].e[e] = fma(-v.e[e], a2, ur[c].e[e]);
-            yr[c].e[e] = fma(-v.e[e], ah, yr[c].e[e]);
-          }
-          acc[q] = dot_vec(v, gn[c], acc[q]);
-        }
-      }
-    }
-    block_sum_to<kColBlock>(acc, red, part + jb, min(kColBlock, kN - jb));
-  }
-  for (int jb = 0; jb < kD; jb += kColBlock) {
-#pragma unroll
-    for (int c = 0; c < kChunkMax; c++) {
-      if (!rw.active(c)) continue;
-      const int64_t row = rw.vec(c) * N;
-#pragma unroll
-      for (int q = 0; q < kColBlock; q++) {
-        const int j = jb + q;
-        if (j < kD) {
-          Vec<T> v;
-          ld_stream(Bn + (int64_t)j * p.ldBn + row, v);
-          const T cj = cb[j];
-#pragma unroll
-          for (int e = 0; e < N; e++) yr[c].e[e] = fma(v.e[e], cj, yr[c].e[e]);
-        }
-      }
-    }
-  }
-  T* ucol = Bn + (int64_t)kD * p.ldBn;
-#pragma unroll
-  for (int c = 0; c < kChunkMax; c++) {
-    if (!rw.active(c)) continue;
-    const int64_t row = rw.vec(c) * N;
-    Vec<T> yv;
-#pragma unroll
-    for (int e = 0; e < N; e++) {
-      yv.e[e] = fma(alpha, ur[c].e[e], yr[c].e[e]);
-      if (row + e >= dim) ur[c].e[e] = T(0);
-    }
-    st_vec(ucol + row, ur[c]);
-    st_caller(p.y, row, dim, p.yal != 0, yv);
-  }
-  if (kN == 0) {
-    // no partial sums: still elect nothing; the next draw needs no dots
-    return;
-  }
-  double* r = p.ws.scr(3);
-  if (!reduce_partials(p.ws, 2, P, p.g3, r)) return;
-  for (int j = threadIdx.x; j < kN; j += blockDim.x) p.N.gdot[j] = r[j];
+  const int off[1] = {0};
+  wt_store_cols<1>(sm.comb, kN, acc, part, off);
+  double* rr = p.ws.scr(3);
+  if (!reduce_partials(p.ws, 2, P, cfg.g, rr)) return;
+  for (int j = threadIdx.x; j < kN; j += blockDim.x) p.N.gdot[j] = rr[j];
 }
 
 // ------------------------------------------------------------------------------------
@@ -662,27 +798,52 @@ cudaError_t launch_first_draw(StackDev X, int64_t count, DrawKey key, T sigma, W
 }
 
 template <typename T>
-cudaError_t launch_step(const StepPlan<T>& p, cudaStream_t s) {
+cudaError_t launch_step(const StepPlan<T>& p, cudaStream_t s, cudaEvent_t* ev, int* launched) {
+  auto rec = [&](int i) {
+    // External: inside a stream capture this becomes an event-record node of the graph
+    if (ev && ev[i]) cudaEventRecordWithFlags(ev[i], s, cudaEventRecordExternal);
+  };
   const int nc1 = p.kD + ((p.ens == 0) ? p.kN : 0);
-  if (nc1 > 0) k_dots<T><<<p.g1.ctas, kThreads, 0, s>>>(p);
-  k_update<T><<<p.g2.ctas, kThreads, update_smem_bytes<T>(p.kD, p.R2), s>>>(p);
+  if (nc1 > 0) {
+    rec(0);
+    k_dots<T><<<p.c1.g.ctas, 32 * p.c1.W, sweep_smem_bytes<T>(p.c1.W, p.c1.nbuf, nc1, 1, nc1, 1), s>>>(p);
+    rec(1);
+    if (launched) launched[0] = 1;
+  }
+  rec(2);
+  k_update<T><<<p.c2.g.ctas, 32 * p.c2.W, sweep_smem_bytes<T>(p.c2.W, p.c2.nbuf, p.kD, 1, p.kD, 2), s>>>(p);
+  rec(3);
+  if (launched) launched[1] = 1;
+  rec(4);
   if (p.ens == 1)
-    k_out_haar<T><<<p.g3.ctas, kThreads, (size_t)p.kN * sizeof(T), s>>>(p);
+    k_out_haar<T><<<p.c3.g.ctas, 32 * p.c3.W, sweep_smem_bytes<T>(p.c3.W, p.c3.nbuf, p.kN, 2, p.kN, 1), s>>>(p);
   else
-    k_out_gin<T><<<p.g3.ctas, kThreads, (size_t)(2 * p.kN + p.kD) * sizeof(T), s>>>(p);
+    k_out_gin<T><<<p.c3.g.ctas, 32 * p.c3.W,
+                   sweep_smem_bytes<T>(p.c3.W, p.c3.nbuf, p.kN + p.kD, 1, p.kN, 1), s>>>(p);
+  rec(5);
+  if (launched) launched[2] = 1;
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t set_update_smem_limit(int bytes) {
-  cudaFuncAttributes fa;
-  cudaError_t e = cudaFuncGetAttributes(&fa, k_update<T>);
-  if (e != cudaSuccess) return e;
-  const int dyn = bytes - (int)fa.sharedSizeBytes;
-  return cudaFuncSetAttribute(k_update<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+cudaError_t set_sweep_smem_limit(int bytes) {
+  cudaError_t e = cudaSuccess;
+  auto one = [&](const void* fn) {
+    cudaFuncAttributes fa;
+    cudaError_t r = cudaFuncGetAttributes(&fa, fn);
+    if (r == cudaSuccess)
+      r = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               bytes - (int)fa.sharedSizeBytes);
+    if (r != cudaSuccess) e = r;
+  };
+  one((const void*)k_dots<T>);
+  one((const void*)k_update<T>);
+  one((const void*)k_out_haar<T>);
+  one((const void*)k_out_gin<T>);
+  return e;
 }
-template cudaError_t set_update_smem_limit<float>(int);
-template cudaError_t set_update_smem_limit<double>(int);
+template cudaError_t set_sweep_smem_limit<float>(int);
+template cudaError_t set_sweep_smem_limit<double>(int);
 
 template <typename T>
 int kernel_occupancy(int which, size_t dynsmem) {
@@ -701,8 +862,8 @@ template int kernel_occupancy<double>(int, size_t);
 
 template cudaError_t launch_first_draw<float>(StackDev, int64_t, DrawKey, float, Ws, int, Grid, cudaStream_t);
 template cudaError_t launch_first_draw<double>(StackDev, int64_t, DrawKey, double, Ws, int, Grid, cudaStream_t);
-template cudaError_t launch_step<float>(const StepPlan<float>&, cudaStream_t);
-template cudaError_t launch_step<double>(const StepPlan<double>&, cudaStream_t);
+template cudaError_t launch_step<float>(const StepPlan<float>&, cudaStream_t, cudaEvent_t*, int*);
+template cudaError_t launch_step<double>(const StepPlan<double>&, cudaStream_t, cudaEvent_t*, int*);
 
 // ------------------------------------------------------------------------------------
 // Consistency probe (not on the hot path): y = Q^(t) x from the revealed part only.
@@ -767,7 +928,8 @@ __global__ void k_probe_out(StepPlan<T> p, const double* q) {
 template <typename T>
 cudaError_t launch_probe(const StepPlan<T>& p, double* q, double* unrev, cudaStream_t s) {
   const int nc1 = p.kD + ((p.ens == 0) ? p.kN : 0);
-  if (nc1 > 0) k_dots<T><<<p.g1.ctas, kThreads, 0, s>>>(p);
+  if (nc1 > 0)
+    k_dots<T><<<p.c1.g.ctas, 32 * p.c1.W, sweep_smem_bytes<T>(p.c1.W, p.c1.nbuf, nc1, 1, nc1, 1), s>>>(p);
   const int thr = 256;
   k_probe_q<T><<<(unsigned)((p.D.dim + thr - 1) / thr), thr, 0, s>>>(p, q, unrev);
   k_probe_coef<T><<<1, thr, 0, s>>>(p, q);

@@ -55,6 +55,7 @@ struct Ws {
   double* part;   // per-CTA partial sums
   double* gpart;  // per-group partial sums
   unsigned int* cnt;  // election counters: [3][kMaxGroups + 1]
+  unsigned int* err;  // device error word: bit 0 = a bounded mbarrier wait expired
   __device__ __forceinline__ double* scr(int i) const { return scrb + i * scr_stride; }
 };
 constexpr int kMaxGroups = 512;
@@ -65,6 +66,26 @@ struct Grid {
   int gsize;        // CTAs per election group
   int ngroups;
 };
+
+// Launch shape of one sweep: W warps per CTA (each walking 32-row sub-tiles), nbuf
+// sub-tile buffers per warp, persistent grid.
+struct SweepCfg {
+  int W;
+  int nbuf;
+  Grid g;
+};
+
+// Dynamic shared memory of a sweep (the carve of WtSmem: W * nbuf stages of ncolT columns and
+// NRV row vectors of 32 elements, W * 2 scratch row vectors, two coefficient arrays padded to
+// 16 bytes, and the W * NR * ncolC FP64 column sums; every section rounded up to 16 bytes).
+template <typename T>
+inline size_t sweep_smem_bytes(int W, int nbuf, int ncolT, int NRV, int ncolC, int NR) {
+  constexpr int VEC = 16 / (int)sizeof(T);
+  auto r16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
+  const size_t cpad = (size_t)(ncolT + VEC - 1) / VEC * VEC;
+  return r16((size_t)W * nbuf * (ncolT + NRV) * 32 * sizeof(T)) + r16((size_t)W * 2 * 32 * sizeof(T)) +
+         r16(2 * cpad * sizeof(T)) + r16((size_t)W * NR * (ncolC > 0 ? ncolC : 1) * sizeof(double));
+}
 
 // The three sweeps of one step plus the first draw; T = float or double.
 template <typename T>
@@ -84,29 +105,24 @@ struct StepPlan {
   Ws ws;
   DrawKey key_next;     // the next step's draw (t + 1)
   T sigma;              // entry scale of the draws (Ginibre), 1 for Haar
-  Grid g1, g2, g3;      // launch shapes of the three sweeps
-  int R2;               // rows per shared-memory tile of K2
-  int64_t ntiles2;      // tiles of K2
+  SweepCfg c1, c2, c3;  // launch shapes of the three sweeps
 };
-
-// Dynamic shared memory of K2 for k columns and R-row tiles.
-template <typename T>
-inline size_t update_smem_bytes(int k, int R) {
-  return ((size_t)k * (R + 1) + 2 * (size_t)R + kThreads + (size_t)k) * sizeof(T);
-}
 
 template <typename T>
 cudaError_t launch_first_draw(StackDev X, int64_t count, DrawKey key, T sigma, Ws ws,
                               int cnt_set, Grid g, cudaStream_t s);
+// ev (optional): start/stop event pairs recorded around K1, K2, K3 (ev[2*kind], ev[2*kind+1]);
+// a null entry skips the record.  launched[kind] is set to 1 for each sweep launched.
 template <typename T>
-cudaError_t launch_step(const StepPlan<T>& p, cudaStream_t s);
+cudaError_t launch_step(const StepPlan<T>& p, cudaStream_t s, cudaEvent_t* ev = nullptr,
+                        int* launched = nullptr);
 template <typename T>
 cudaError_t launch_probe(const StepPlan<T>& p, double* q, double* unrevealed, cudaStream_t s);
 
 template <typename T>
 int kernel_occupancy(int which, size_t dynsmem);
 template <typename T>
-cudaError_t set_update_smem_limit(int bytes);
+cudaError_t set_sweep_smem_limit(int bytes);
 
 cudaError_t launch_philox_normals(DrawKey key, int64_t start, int64_t count, int dtype, void* out,
                                   cudaStream_t s);

@@ -36,7 +36,9 @@ struct hd_state {
   Ws ws;
   Grid grid[2];          // launch shape for each space (0: n, 1: m)
   int nsm = 1;
+  int pdl = 1;           // programmatic dependent launch of the sweeps (HD_DISABLE_PDL=1: off)
   int occ_regs[4] = {1, 1, 1, 1};  // CTAs per SM allowed by registers: K1, K2, K3 Haar, K3 Gin
+  int static_smem[4] = {0, 0, 0, 0};  // static shared memory of each sweep kernel
   int smem_sm = 0;       // shared memory per SM usable by CTAs
   int smem_blk_max = 0;  // opt-in dynamic shared memory per CTA
   int64_t bytes = 0;
@@ -160,7 +162,8 @@ SweepCfg make_sweep(const hd_state* st, int which, int ncolT, int NRV, int ncolC
   SweepCfg c;
   c.W = 8;
   c.nbuf = 1;
-  const int blk = st->smem_blk_max - 1024;
+  const int stat = st->static_smem[which] + 1024;   // static + per-CTA reserve
+  const int blk = st->smem_blk_max - stat;
   const double stage = (double)(ncolT + NRV) * 32.0 * sizeof(T);
   double best = -1.0;
   for (int W = 8; W >= 1; W /= 2) {
@@ -168,7 +171,7 @@ SweepCfg make_sweep(const hd_state* st, int which, int ncolT, int NRV, int ncolC
       const size_t b = sweep_smem_bytes<T>(W, nb, ncolT, NRV, ncolC, NR);
       if ((int)b > blk) continue;
       const int by_regs = std::max(1, st->occ_regs[which] * 8 / W);
-      const int ctas = std::min(by_regs, (int)(st->smem_sm / (b + 1024)));
+      const int ctas = std::min(by_regs, (int)(st->smem_sm / (b + stat)));
       if (ctas < 1) continue;
       const int warps = std::min(64, ctas * W);
       const double inflight = std::min(warps * nb * stage, 131072.0);
@@ -182,7 +185,7 @@ SweepCfg make_sweep(const hd_state* st, int which, int ncolT, int NRV, int ncolC
   }
   const size_t bytes = sweep_smem_bytes<T>(c.W, c.nbuf, ncolT, NRV, ncolC, NR);
   const int by_regs = std::max(1, st->occ_regs[which] * 8 / c.W);
-  const int occ = std::max(1, std::min(by_regs, (int)(st->smem_sm / (bytes + 1024))));
+  const int occ = std::max(1, std::min(by_regs, (int)(st->smem_sm / (bytes + stat))));
   const int64_t nsub = (dim + 31) / 32;
   int64_t ctas = std::min<int64_t>((nsub + c.W - 1) / c.W, (int64_t)occ * st->nsm);
   if (ctas < 1) ctas = 1;
@@ -235,6 +238,7 @@ int do_step(hd_state* st, const void* x, int transpose, void* y) {
   p.key_next = key_for(st, st->t + 2);
   p.sigma = (st->ens == HD_GINIBRE) ? (T)st->sigma : T(1);
   set_sweeps<T>(st, &p);
+  p.pdl = st->pdl;
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   int slot0 = -1;
   if (st->prof_on && st->prof_used + 3 <= st->prof_cap) {
@@ -294,6 +298,7 @@ int do_probe(hd_state* st, const void* x, int transpose, void* y, double* unreve
   p.ws = st->ws;
   p.sigma = T(1);
   set_sweeps<T>(st, &p);
+  p.pdl = 0;
   double* q = nullptr;
   if (cudaMalloc(&q, (size_t)(p.D.dim + 1) * 8) != cudaSuccess) {
     set_error("hd_probe cudaMalloc", cudaGetLastError());
@@ -324,7 +329,7 @@ int run_steps(hd_state* st, const hd_run_spec* sp) {
     const int64_t nout = tr ? st->n : st->m;
     cudaError_t e = launch_dynamics<T>(sp->dynamics, sp->a, (const T*)st->yw, (const T*)st->xw[cur],
                                        (const T*)st->xw[1 - cur], (T*)st->xw[1 - cur], nout,
-                                       st->sumsq, st->stream);
+                                       st->sumsq, st->stream, st->pdl != 0);
     if (e != cudaSuccess) return cuda_fail(st, e);
     st->launches += (sp->dynamics == HD_DYN_NORM_TANH) ? 2 : 1;
     cur = 1 - cur;
@@ -501,6 +506,10 @@ HD_API int hd_create(int ensemble, int64_t m, int64_t n, int32_t T_max, uint64_t
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, st->device);
   if (nsm <= 0) nsm = 1;
   st->nsm = nsm;
+  {
+    const char* env = getenv("HD_DISABLE_PDL");
+    st->pdl = (env && env[0] == '1') ? 0 : 1;
+  }
   int smem_sm = 0, smem_blk = 0;
   cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, st->device);
   cudaDeviceGetAttribute(&smem_blk, cudaDevAttrMaxSharedMemoryPerBlockOptin, st->device);
@@ -526,8 +535,10 @@ HD_API int hd_create(int ensemble, int64_t m, int64_t n, int32_t T_max, uint64_t
   int occ;
   const size_t dsm = (size_t)3 * T_max * st->esz;
   (void)dsm;
-  for (int q = 0; q < 4; q++)
+  for (int q = 0; q < 4; q++) {
     st->occ_regs[q] = (dtype == HD_F64) ? kernel_occupancy<double>(q, 0) : kernel_occupancy<float>(q, 0);
+    st->static_smem[q] = (dtype == HD_F64) ? kernel_static_smem<double>(q) : kernel_static_smem<float>(q);
+  }
   occ = 4;
   const int64_t dims[2] = {n, m};
   int64_t maxctas = (int64_t)nsm * 8;

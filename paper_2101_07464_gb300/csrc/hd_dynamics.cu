@@ -19,6 +19,10 @@ __device__ __forceinline__ T sgn(T v) {
 template <typename T>
 __global__ void k_dyn(int kind, T a, const T* __restrict__ y, const T* xcur, const T* xprev, T* out,
                       int64_t n, double* sumsq) {
+  // y comes from the preceding kernel (programmatic dependent launch): wait, then let the
+  // next kernel start
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double s = 0.0;
   if (i < n) {
@@ -47,21 +51,32 @@ __global__ void k_scale_rsqrt(T* x, int64_t n, const double* sumsq) {
 
 template <typename T>
 cudaError_t launch_dynamics(int kind, double a, const T* y, const T* xcur, const T* xprev, T* out,
-                            int64_t n, double* sumsq, cudaStream_t s) {
+                            int64_t n, double* sumsq, cudaStream_t s, bool pdl) {
   const int thr = 256;
   const unsigned blocks = (unsigned)((n + thr - 1) / thr);
   if (kind == kDynNormTanh) {
     cudaError_t e = cudaMemsetAsync(sumsq, 0, sizeof(double), s);
     if (e != cudaSuccess) return e;
+    pdl = false;   // the memset sits between the sweep and this kernel
   }
-  k_dyn<T><<<blocks, thr, 0, s>>>(kind, (T)a, y, xcur, xprev, out, n, sumsq);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(thr);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = pdl ? attr : nullptr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k_dyn<T>, kind, (T)a, y, xcur, xprev, out, n, sumsq);
+  if (e != cudaSuccess) return e;
   if (kind == kDynNormTanh) k_scale_rsqrt<T><<<blocks, thr, 0, s>>>(out, n, sumsq);
   return cudaGetLastError();
 }
 
 template cudaError_t launch_dynamics<float>(int, double, const float*, const float*, const float*,
-                                            float*, int64_t, double*, cudaStream_t);
+                                            float*, int64_t, double*, cudaStream_t, bool);
 template cudaError_t launch_dynamics<double>(int, double, const double*, const double*,
-                                             const double*, double*, int64_t, double*, cudaStream_t);
+                                             const double*, double*, int64_t, double*, cudaStream_t, bool);
 
 }  // namespace hd

@@ -140,16 +140,18 @@ __global__ void __launch_bounds__(kThreads) k_first_draw(StackDev X, int64_t cou
 // Finalisation after K2 (one CTA).  r[0..k) = dots of the next draw with the old columns of
 // V_D, r[k] = with the new column, r[k+1] = ||p[k+1:]||^2, r[k+2] = ||g_{t+1}[k+2:]||^2,
 // r[k+3+j] = V_D[k:, j] . p[k:] for the old columns j < k.
+// Small vectors are staged in shared memory; the O(k^2) loops read S and V columns with
+// eight independent loads in flight per thread.
 template <typename T>
 __device__ void fin_update(const StepPlan<T>& p, const double* r) {
   const int k = p.kD, Tm = p.Tm;
   const int tid = threadIdx.x, nt = blockDim.x;
   __shared__ double sh[16];
+  __shared__ double f_a[kTmaxLimit + 1];   // vtu (data side), later zt
+  __shared__ double f_b[kTmaxLimit + 1];   // y_top = Delta_N phead (Haar) / h (Ginibre)
+  __shared__ double f_c[kTmaxLimit + 1];   // vtg (random side) / g-dots
   T* VD = (T*)p.D.V;
   const int64_t ldD = p.D.ld;
-  double* vtu = p.ws.scr(0);
-  double* vtg = p.ws.scr(1);
-  double* zt = p.ws.scr(2);
 
   for (int j = tid; j <= k; j += nt) p.D.gdot[j] = r[j];
   if (tid == 0) {
@@ -173,12 +175,15 @@ __device__ void fin_update(const StepPlan<T>& p, const double* r) {
   const double alpha = sh[0], tau = sh[1], us = sh[2], dsign = sh[3], ppiv = sh[5];
   // V_D^T u with u = p[k:] + (u_k - p_k) e_k, from the exact dots of the sweep.
   for (int j = tid; j < k; j += nt)
-    vtu[j] = r[k + 3 + j] + (us - ppiv) * (double)VD[k + (int64_t)j * ldD];
+    f_a[j] = r[k + 3 + j] + (us - ppiv) * (double)VD[k + (int64_t)j * ldD];
   __syncthreads();
   for (int j = tid; j < k; j += nt) {
     double s = 0.0;
-    if (alpha != 0.0)
-      for (int i = j; i < k; i++) s = fma(p.D.S[j + (int64_t)i * Tm], vtu[i], s);
+    if (alpha != 0.0) {
+      const double* Sj = p.D.S + j;
+#pragma unroll 8
+      for (int i = j; i < k; i++) s = fma(Sj[(int64_t)i * Tm], f_a[i], s);
+    }
     p.D.S[j + (int64_t)k * Tm] = -tau * s;
   }
   if (tid == 0) {
@@ -198,37 +203,42 @@ __device__ void fin_update(const StepPlan<T>& p, const double* r) {
       const double ag = sqrt(gg + gpiv * gpiv);
       const double sg = (gpiv >= 0.0) ? 1.0 : -1.0;
       if (ag == 0.0) {
-        sh[8] = 0.0; sh[9] = 0.0; sh[10] = 1.0; sh[11] = 0.0; sh[12] = 0.0; sh[13] = 1.0;
+        sh[8] = 0.0; sh[9] = 0.0; sh[10] = 1.0; sh[12] = 0.0; sh[13] = 1.0;
       } else {
         const double usg = (double)(T)(gpiv + sg * ag);
         const double uug = gg + usg * usg;
-        sh[8] = 2.0 / uug; sh[9] = usg; sh[10] = -sg; sh[11] = uug; sh[12] = alpha / ag; sh[13] = 0.0;
+        sh[8] = 2.0 / uug; sh[9] = usg; sh[10] = -sg; sh[12] = alpha / ag; sh[13] = 0.0;
       }
       sh[14] = gpiv;
       p.ws.scal[kCoef] = sh[12];
       p.ws.scal[kUpivG] = sh[9];
       p.ws.scal[kGFlag] = sh[13];
     }
+    for (int i = tid; i < k; i += nt) f_b[i] = p.N.dpre[i + 1] * ld_cg(&p.ws.phead[i]);
     __syncthreads();
     const double taug = sh[8], usg = sh[9], dg = sh[10], coef = sh[12];
     const bool flag = sh[13] != 0.0;
     const double gpiv = sh[14];
     const double deltaN = p.N.dpre[k];
     for (int j = tid; j < k; j += nt) {
-      const double vk = (double)VN[k + (int64_t)j * ldN];
-      vtg[j] = flag ? 0.0 : p.N.gdot[j] + (usg - gpiv) * vk;
+      const T* Vj = VN + (int64_t)j * ldN;
+      const double vk = (double)Vj[k];
+      const double gd = p.N.gdot[j];
+      f_c[j] = flag ? 0.0 : gd + (usg - gpiv) * vk;
       double tz = 0.0;
-      for (int i = j; i < k; i++)
-        tz = fma((double)VN[i + (int64_t)j * ldN], p.N.dpre[i + 1] * ld_cg(&p.ws.phead[i]), tz);
-      zt[j] = tz + deltaN * (flag ? alpha * vk : coef * p.N.gdot[j]);
+#pragma unroll 8
+      for (int i = j; i < k; i++) tz = fma((double)Vj[i], f_b[i], tz);
+      f_a[j] = tz + deltaN * (flag ? alpha * vk : coef * gd);
     }
     __syncthreads();
     for (int j = tid; j < k; j += nt) {
       double sw = 0.0, sc = 0.0;
+      const double* Sj = p.N.S + j;
+#pragma unroll 8
       for (int i = j; i < k; i++) {
-        const double sji = p.N.S[j + (int64_t)i * Tm];
-        sw = fma(sji, zt[i], sw);
-        sc = fma(sji, vtg[i], sc);
+        const double sji = Sj[(int64_t)i * Tm];
+        sw = fma(sji, f_a[i], sw);
+        sc = fma(sji, f_c[i], sc);
       }
       p.ws.wout[j] = sw;
       p.N.S[j + (int64_t)k * Tm] = -taug * sc;
@@ -241,21 +251,28 @@ __device__ void fin_update(const StepPlan<T>& p, const double* r) {
     // Ginibre: h = x . (data-space basis), w_h = S_N V_N^T Delta_N h (top block),
     // w_2 = S_N V_N^T Delta_N g (g on rows >= k_N where Delta_N is constant).
     const int kN = p.kN;
-    const double* h = p.ws.z + p.kD;
     const double deltaN = p.N.dpre[kN];
+    for (int i = tid; i < kN; i += nt) {
+      f_b[i] = p.N.dpre[i + 1] * p.ws.z[p.kD + i];
+      f_c[i] = p.N.gdot[i];
+    }
+    __syncthreads();
     for (int j = tid; j < kN; j += nt) {
+      const T* Vj = VN + (int64_t)j * ldN;
       double tz = 0.0;
-      for (int i = j; i < kN; i++)
-        tz = fma((double)VN[i + (int64_t)j * ldN], p.N.dpre[i + 1] * h[i], tz);
-      zt[j] = tz;
+#pragma unroll 8
+      for (int i = j; i < kN; i++) tz = fma((double)Vj[i], f_b[i], tz);
+      f_a[j] = tz;
     }
     __syncthreads();
     for (int j = tid; j < kN; j += nt) {
       double sw = 0.0, s2 = 0.0;
+      const double* Sj = p.N.S + j;
+#pragma unroll 8
       for (int i = j; i < kN; i++) {
-        const double sji = p.N.S[j + (int64_t)i * Tm];
-        sw = fma(sji, zt[i], sw);
-        s2 = fma(sji, p.N.gdot[i], s2);
+        const double sji = Sj[(int64_t)i * Tm];
+        sw = fma(sji, f_a[i], sw);
+        s2 = fma(sji, f_c[i], s2);
       }
       p.ws.wout[j] = sw;
       p.ws.wout2[j] = deltaN * s2;
@@ -310,14 +327,24 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// Copy rows [r0, r0 + 32) of ncol columns into a warp stage (no commit).
+// Copy rows [r0, r0 + 32) of ncol columns into a warp stage (no commit).  Lane l always
+// copies chunk q = l mod NCH of the columns l / NCH, l / NCH + 32 / NCH, ...
 template <typename T>
 __device__ __forceinline__ void wt_load_cols(T* buf, const ColSrc<T>& src, int ncol, int64_t r0) {
-  constexpr int NCH = WT<T>::NCH, VEC = WT<T>::VEC;
+  constexpr int NCH = WT<T>::NCH, VEC = WT<T>::VEC, CPI = 32 / NCH;
   const int lane = threadIdx.x & 31;
-  for (int c = lane; c < ncol * NCH; c += 32) {
-    const int j = c / NCH, q = c & (NCH - 1);
-    cp_async16(buf + j * 32 + ((q + j) & (NCH - 1)) * VEC, src.col(j) + r0 + q * VEC);
+  const int q = lane & (NCH - 1);
+  int j = lane / NCH;
+  const int nA = min(ncol, src.nA);
+  {
+    const T* g = src.A + (int64_t)j * src.ldA + r0 + q * VEC;
+    const int64_t gstep = (int64_t)CPI * src.ldA;
+    for (; j < nA; j += CPI, g += gstep) cp_async16(buf + j * 32 + ((q + j) & (NCH - 1)) * VEC, g);
+  }
+  if (j < ncol) {
+    const T* g = src.B + (int64_t)(j - src.nA) * src.ldB + r0 + q * VEC;
+    const int64_t gstep = (int64_t)CPI * src.ldB;
+    for (; j < ncol; j += CPI, g += gstep) cp_async16(buf + j * 32 + ((q + j) & (NCH - 1)) * VEC, g);
   }
 }
 __device__ __forceinline__ void cp_async16_zfill(void* smem, const void* gmem, int src_bytes) {
@@ -366,66 +393,100 @@ __device__ __forceinline__ void cp_async_wait_dyn(int pending) {
   }
 }
 
-// Row owner: out[o] = sum_j V[lane, j] coef_o[j], o < NO (coef arrays padded to VEC).
+// Row owner: out[o] = sum_j V[lane, j] coef_o[j], o < NO (coef arrays padded to NCH).
+// Column j = NCH g + u of the lane's row sits at NCH * 32 * g + off[u]; the NCH offsets of one
+// rotation period depend only on the lane.
 template <typename T, int NO>
 __device__ __forceinline__ void wt_rows(const T* buf, int ncol, const T* coef0, const T* coef1,
                                         T (&out)[NO]) {
   constexpr int NCH = WT<T>::NCH, VEC = WT<T>::VEC;
   const int lane = threadIdx.x & 31;
   const int qi = lane / VEC, ri = lane & (VEC - 1);
+  int off[NCH];
+#pragma unroll
+  for (int u = 0; u < NCH; u++) off[u] = u * 32 + ((qi + u) & (NCH - 1)) * VEC + ri;
 #pragma unroll
   for (int o = 0; o < NO; o++) out[o] = T(0);
-  int j = 0;
-  for (; j + VEC <= ncol; j += VEC) {
-    const Vec<T> c0 = *reinterpret_cast<const Vec<T>*>(coef0 + j);
-    Vec<T> c1;
-    if (NO > 1) c1 = *reinterpret_cast<const Vec<T>*>(coef1 + j);
+  const int ng = ncol / NCH;
+  const T* base = buf;
+  for (int g = 0; g < ng; g++, base += NCH * 32) {
+    const T* c0 = coef0 + g * NCH;
+    const T* c1 = coef1 + g * NCH;
 #pragma unroll
-    for (int e = 0; e < VEC; e++) {
-      const int jj = j + e;
-      const T v = buf[jj * 32 + ((qi + jj) & (NCH - 1)) * VEC + ri];
-      out[0] = fma(v, c0.e[e], out[0]);
-      if (NO > 1) out[NO - 1] = fma(v, c1.e[e], out[NO - 1]);
+    for (int u0 = 0; u0 < NCH; u0 += VEC) {
+      const Vec<T> a0 = *reinterpret_cast<const Vec<T>*>(c0 + u0);
+      Vec<T> a1;
+      if (NO > 1) a1 = *reinterpret_cast<const Vec<T>*>(c1 + u0);
+#pragma unroll
+      for (int e = 0; e < VEC; e++) {
+        const T v = base[off[u0 + e]];
+        out[0] = fma(v, a0.e[e], out[0]);
+        if (NO > 1) out[NO - 1] = fma(v, a1.e[e], out[NO - 1]);
+      }
     }
   }
-  for (; j < ncol; j++) {
-    const T v = buf[j * 32 + ((qi + j) & (NCH - 1)) * VEC + ri];
-    out[0] = fma(v, coef0[j], out[0]);
-    if (NO > 1) out[NO - 1] = fma(v, coef1[j], out[NO - 1]);
+  const int rem = ncol - ng * NCH;
+  if (rem > 0) {
+    const T* c0 = coef0 + ng * NCH;
+    const T* c1 = coef1 + ng * NCH;
+#pragma unroll
+    for (int u = 0; u < NCH; u++) {
+      if (u < rem) {
+        const T v = base[off[u]];
+        out[0] = fma(v, c0[u], out[0]);
+        if (NO > 1) out[NO - 1] = fma(v, c1[u], out[NO - 1]);
+      }
+    }
   }
 }
 
 constexpr int kColsPerLane = 8;   // column owner: up to 8 * 32 = 256 columns
 
 // Column owner: acc[r][m] += sum_i V[i, lane + 32 m] rhs_r[i] over the 32 rows, m < 8.
+// Logical chunk c of column j sits at slot (c + j) mod NCH, and j mod NCH = lane mod NCH for
+// every m, so the NCH chunk offsets are per-lane constants.
 template <typename T, int NR>
 __device__ __forceinline__ void wt_cols(const T* buf, int ncol, const T* rhs0, const T* rhs1,
                                         double (&acc)[NR][kColsPerLane]) {
   constexpr int NCH = WT<T>::NCH, VEC = WT<T>::VEC;
   const int lane = threadIdx.x & 31;
+  int coff[NCH];
 #pragma unroll
-  for (int m = 0; m < kColsPerLane; m++) {
-    const int j = lane + 32 * m;
+  for (int c = 0; c < NCH; c++) coff[c] = ((c + lane) & (NCH - 1)) * VEC;
+#pragma unroll
+  for (int m = 0; m < kColsPerLane; m += 2) {
     if (32 * m >= ncol) break;
-    if (j < ncol) {
-      T s[NR];
+    const int j0 = lane + 32 * m, j1 = j0 + 32;
+    const bool h0 = j0 < ncol, h1 = j1 < ncol;
+    if (!h0) continue;
+    T s0[NR], s1[NR];
 #pragma unroll
-      for (int r = 0; r < NR; r++) s[r] = T(0);
-      const T* col = buf + j * 32;
+    for (int r = 0; r < NR; r++) s0[r] = s1[r] = T(0);
+    const T* col0 = buf + j0 * 32;
+    const T* col1 = buf + (h1 ? j1 : j0) * 32;
 #pragma unroll
-      for (int c = 0; c < NCH; c++) {
-        const Vec<T> v = *reinterpret_cast<const Vec<T>*>(col + ((c + j) & (NCH - 1)) * VEC);
-        const Vec<T> b0 = *reinterpret_cast<const Vec<T>*>(rhs0 + c * VEC);
+    for (int c = 0; c < NCH; c++) {
+      const Vec<T> v0 = *reinterpret_cast<const Vec<T>*>(col0 + coff[c]);
+      const Vec<T> v1 = *reinterpret_cast<const Vec<T>*>(col1 + coff[c]);
+      const Vec<T> b0 = *reinterpret_cast<const Vec<T>*>(rhs0 + c * VEC);
 #pragma unroll
-        for (int e = 0; e < VEC; e++) s[0] = fma(v.e[e], b0.e[e], s[0]);
-        if (NR > 1) {
-          const Vec<T> b1 = *reinterpret_cast<const Vec<T>*>(rhs1 + c * VEC);
+      for (int e = 0; e < VEC; e++) {
+        s0[0] = fma(v0.e[e], b0.e[e], s0[0]);
+        s1[0] = fma(v1.e[e], b0.e[e], s1[0]);
+      }
+      if (NR > 1) {
+        const Vec<T> b1 = *reinterpret_cast<const Vec<T>*>(rhs1 + c * VEC);
 #pragma unroll
-          for (int e = 0; e < VEC; e++) s[NR - 1] = fma(v.e[e], b1.e[e], s[NR - 1]);
+        for (int e = 0; e < VEC; e++) {
+          s0[NR - 1] = fma(v0.e[e], b1.e[e], s0[NR - 1]);
+          s1[NR - 1] = fma(v1.e[e], b1.e[e], s1[NR - 1]);
         }
       }
+    }
 #pragma unroll
-      for (int r = 0; r < NR; r++) acc[r][m] += (double)s[r];
+    for (int r = 0; r < NR; r++) {
+      acc[r][m] += (double)s0[r];
+      if (h1) acc[r][m + 1] += (double)s1[r];
     }
   }
 }
@@ -457,7 +518,9 @@ struct WtSmem {
     sstride = (ncolT + NRV) * 32;
     stages = (T*)take((size_t)W * nb * sstride * sizeof(T));
     scratch = (T*)take((size_t)W * 2 * 32 * sizeof(T));
-    cpad = (ncolT + VEC - 1) / VEC * VEC;
+    constexpr int NCH = WT<T>::NCH;
+    (void)VEC;
+    cpad = (ncolT + NCH - 1) / NCH * NCH;
     coef = (T*)take((size_t)2 * cpad * sizeof(T));
     comb = (double*)take((size_t)W * NR * (ncolC > 0 ? ncolC : 1) * sizeof(double));
   }
@@ -521,19 +584,44 @@ struct WarpWalk {
   }
 };
 
-// The walk of one warp as an nb-stage cp.async pipeline: load(it, stage) must issue the
-// copies of local sub-tile it into the stage; body(it, stage) runs once its data is ready.
-template <typename Load, typename Body>
-__device__ __forceinline__ void wt_pipeline(int count, int nb, Load&& load, Body&& body) {
+// Programmatic dependent launch: wait until the preceding kernel of the stream has completed
+// and its writes are visible (no-op when launched without the attribute); then allow the next
+// kernel to be scheduled.  A kernel triggers only after its own wait, so every kernel that
+// starts early knows that everything before its predecessor has completed.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
+// The walk of one warp as an nb-stage cp.async pipeline.  pre(it, stage) issues the copies of
+// local sub-tile it that do not depend on the preceding kernel (stack columns written by
+// earlier kernels), post(it, stage) the rest; the prologue issues pre for the first nb - 1
+// stages, then waits for the preceding kernel (pdl_wait), then issues their post part.
+// setup() runs in every thread of the CTA right after the wait (then one CTA barrier): it
+// stages what the preceding kernel produced (coefficients).  body(it, stage) runs once the
+// stage is complete.
+template <typename Pre, typename Setup, typename Post, typename Body>
+__device__ __forceinline__ void wt_pipeline(int count, int nb, Pre&& pre, Setup&& setup, Post&& post,
+                                            Body&& body) {
   for (int q = 0; q < nb - 1; q++) {
-    if (q < count) load(q, q);
+    if (q < count) pre(q, q);
     cp_async_commit();
   }
+  pdl_wait();
+  pdl_trigger();
+  setup();
+  __syncthreads();
+  for (int q = 0; q < nb - 1; q++)
+    if (q < count) post(q, q);
+  cp_async_commit();
   for (int it = 0; it < count; it++) {
     const int nxt = it + nb - 1;
-    if (nxt < count) load(nxt, nxt % nb);
+    if (nxt < count) {
+      pre(nxt, nxt % nb);
+      post(nxt, nxt % nb);
+    }
     cp_async_commit();
-    cp_async_wait_dyn(nb - 1);
+    cp_async_wait_dyn(it + 1 < nb - 1 ? it + 1 : nb - 1);
     __syncwarp();
     body(it, it % nb);
     __syncwarp();
@@ -558,12 +646,9 @@ __global__ void __launch_bounds__(kThreads) k_dots(StepPlan<T> p) {
   const WarpWalk ww(dim);
   const bool xal = p.xal != 0;
   wt_pipeline(ww.count(), cfg.nbuf,
-      [&](int it, int b) {
-        T* st = sm.stage(warp, b);
-        const int64_t r0 = ww.sub(it) * 32;
-        wt_load_cols(st, src, nc, r0);
-        wt_load_vec(sm.srow(st, 0), p.x, r0, dim, xal);
-      },
+      [&](int it, int b) { wt_load_cols(sm.stage(warp, b), src, nc, ww.sub(it) * 32); },
+      [&]() {},
+      [&](int it, int b) { wt_load_vec(sm.srow(sm.stage(warp, b), 0), p.x, ww.sub(it) * 32, dim, xal); },
       [&](int it, int b) {
         T* st = sm.stage(warp, b);
         wt_cols<T, 1>(st, nc, sm.srow(st, 0), nullptr, acc);
@@ -571,11 +656,15 @@ __global__ void __launch_bounds__(kThreads) k_dots(StepPlan<T> p) {
   const int off[1] = {0};
   wt_store_cols<1>(sm.comb, nc, acc, p.ws.part + (int64_t)blockIdx.x * nc, off);
   if (!reduce_partials(p.ws, 0, nc, cfg.g, p.ws.z)) return;
+  __shared__ double zs[kTmaxLimit];
+  for (int i = threadIdx.x; i < na; i += blockDim.x) zs[i] = p.ws.z[i];
+  __syncthreads();
   const int Tm = p.Tm;
   for (int j = threadIdx.x; j < na; j += blockDim.x) {
     double s = 0.0;
-#pragma unroll 4
-    for (int i = 0; i <= j; i++) s = fma(p.D.S[i + (int64_t)j * Tm], p.ws.z[i], s);
+    const double* Sj = p.D.S + (int64_t)j * Tm;
+#pragma unroll 8
+    for (int i = 0; i <= j; i++) s = fma(Sj[i], zs[i], s);
     p.ws.w[j] = s;
   }
 }
@@ -590,8 +679,6 @@ __global__ void __launch_bounds__(kThreads) k_update(StepPlan<T> p) {
   const SweepCfg& cfg = p.c2;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   WtSmem<T> sm(dsm_raw, blockDim.x >> 5, cfg.nbuf, k, 1, k, 2);
-  for (int j = threadIdx.x; j < sm.cpad; j += blockDim.x) sm.coef[j] = (j < k) ? (T)p.ws.w[j] : T(0);
-  __syncthreads();
   const ColSrc<T> src{(const T*)p.D.V, p.D.ld, k, nullptr, 0};
   const int64_t dim = p.D.dim;
   T* col = (T*)p.D.V + (int64_t)k * p.D.ld;
@@ -612,6 +699,10 @@ __global__ void __launch_bounds__(kThreads) k_update(StepPlan<T> p) {
         wt_load_cols(st, src, k, r0);
         wt_load_vec(sm.srow(st, 0), p.x, r0, dim, xal);
       },
+      [&]() {   // w comes from the preceding kernel
+        for (int j = threadIdx.x; j < sm.cpad; j += blockDim.x) sm.coef[j] = (j < k) ? (T)p.ws.w[j] : T(0);
+      },
+      [&](int, int) {},
       [&](int it, int b) {
         T* st = sm.stage(warp, b);
         const int64_t r = ww.sub(it) * 32 + lane;
@@ -658,18 +749,13 @@ __global__ void __launch_bounds__(kThreads) k_out_haar(StepPlan<T> p) {
   const SweepCfg& cfg = p.c3;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   WtSmem<T> sm(dsm_raw, blockDim.x >> 5, cfg.nbuf, k, 2, k, 1);
-  for (int j = threadIdx.x; j < sm.cpad; j += blockDim.x) sm.coef[j] = (j < k) ? (T)p.ws.wout[j] : T(0);
-  __syncthreads();
   const ColSrc<T> src{(const T*)p.N.V, p.N.ld, k, nullptr, 0};
   const int64_t dim = p.N.dim;
   T* col = (T*)p.N.V + (int64_t)k * p.N.ld;
   T* gcur = (T*)p.N.gbuf;
   const T* gnext = (const T*)p.D.gbuf;
-  const T coef = (T)p.ws.scal[kCoef];
-  const T alpha = (T)p.ws.scal[kAlpha];
-  const T usg = (T)p.ws.scal[kUpivG];
-  const bool flag = p.ws.scal[kGFlag] != 0.0;
-  const T dconst = (T)p.N.dpre[k];
+  T coef = T(0), alpha = T(0), usg = T(0), dconst = T(0);
+  bool flag = false;
   double acc[1][kColsPerLane];
 #pragma unroll
   for (int m = 0; m < kColsPerLane; m++) acc[0][m] = 0.0;
@@ -682,8 +768,16 @@ __global__ void __launch_bounds__(kThreads) k_out_haar(StepPlan<T> p) {
         const int64_t r0 = ww.sub(it) * 32;
         wt_load_cols(st, src, k, r0);
         wt_load_vec(sm.srow(st, 0), (const T*)gcur, r0, ld, true);
-        wt_load_vec(sm.srow(st, 1), gnext, r0, ld, true);
       },
+      [&]() {   // outputs of the preceding kernel's finalisation
+        for (int j = threadIdx.x; j < sm.cpad; j += blockDim.x) sm.coef[j] = (j < k) ? (T)p.ws.wout[j] : T(0);
+        coef = (T)p.ws.scal[kCoef];
+        alpha = (T)p.ws.scal[kAlpha];
+        usg = (T)p.ws.scal[kUpivG];
+        flag = p.ws.scal[kGFlag] != 0.0;
+        dconst = (T)p.N.dpre[k];
+      },
+      [&](int it, int b) { wt_load_vec(sm.srow(sm.stage(warp, b), 1), gnext, ww.sub(it) * 32, ld, true); },
       [&](int it, int b) {
         T* st = sm.stage(warp, b);
         const int64_t r = ww.sub(it) * 32 + lane;
@@ -727,25 +821,12 @@ __global__ void __launch_bounds__(kThreads) k_out_gin(StepPlan<T> p) {
   const SweepCfg& cfg = p.c3;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   WtSmem<T> sm(dsm_raw, blockDim.x >> 5, cfg.nbuf, nc, 1, kN, 1);
-  for (int j = threadIdx.x; j < sm.cpad; j += blockDim.x) {
-    T c0 = T(0), c1 = T(0);
-    if (j < kN) {
-      c0 = (T)p.ws.wout2[j];
-      c1 = (T)p.ws.wout[j];
-    } else if (j < nc) {
-      c1 = -(T)p.ws.phead[j - kN];
-    }
-    sm.coef[j] = c0;
-    sm.coef[sm.cpad + j] = c1;
-  }
-  __syncthreads();
   const ColSrc<T> src{(const T*)p.N.V, p.N.ld, kN, (const T*)p.Bn, p.ldBn};
   const int64_t dim = p.N.dim;
   T* ucol = (T*)p.Bn + (int64_t)kD * p.ldBn;
   T* gcur = (T*)p.N.gbuf;
   const double* h = p.ws.z + kD;
-  const T alpha = (T)p.ws.scal[kAlpha];
-  const T dconst = (T)p.N.dpre[kN];
+  T alpha = T(0), dconst = T(0);
   double acc[1][kColsPerLane];
 #pragma unroll
   for (int m = 0; m < kColsPerLane; m++) acc[0][m] = 0.0;
@@ -759,6 +840,22 @@ __global__ void __launch_bounds__(kThreads) k_out_gin(StepPlan<T> p) {
         wt_load_cols(st, src, nc, r0);
         wt_load_vec(sm.srow(st, 0), (const T*)gcur, r0, ld, true);
       },
+      [&]() {   // outputs of the preceding kernel's finalisation
+        for (int j = threadIdx.x; j < sm.cpad; j += blockDim.x) {
+          T c0 = T(0), c1 = T(0);
+          if (j < kN) {
+            c0 = (T)p.ws.wout2[j];
+            c1 = (T)p.ws.wout[j];
+          } else if (j < nc) {
+            c1 = -(T)p.ws.phead[j - kN];
+          }
+          sm.coef[j] = c0;
+          sm.coef[sm.cpad + j] = c1;
+        }
+        alpha = (T)p.ws.scal[kAlpha];
+        dconst = (T)p.N.dpre[kN];
+      },
+      [&](int, int) {},
       [&](int it, int b) {
         T* st = sm.stage(warp, b);
         const int64_t r = ww.sub(it) * 32 + lane;
@@ -797,29 +894,53 @@ cudaError_t launch_first_draw(StackDev X, int64_t count, DrawKey key, T sigma, W
   return cudaGetLastError();
 }
 
+// Launch with programmatic stream serialisation (the kernel may start while its predecessor
+// drains; it synchronises through griddepcontrol.wait) when pdl is set.
+template <typename T>
+cudaError_t launch_sweep(void (*kern)(StepPlan<T>), const SweepCfg& c, size_t smem, cudaStream_t s,
+                         bool pdl, const StepPlan<T>& p) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)c.g.ctas);
+  cfg.blockDim = dim3((unsigned)(32 * c.W));
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = pdl ? attr : nullptr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, p);
+}
+
 template <typename T>
 cudaError_t launch_step(const StepPlan<T>& p, cudaStream_t s, cudaEvent_t* ev, int* launched) {
   auto rec = [&](int i) {
     // External: inside a stream capture this becomes an event-record node of the graph
     if (ev && ev[i]) cudaEventRecordWithFlags(ev[i], s, cudaEventRecordExternal);
   };
+  const bool pdl = p.pdl != 0;
+  cudaError_t e = cudaSuccess;
   const int nc1 = p.kD + ((p.ens == 0) ? p.kN : 0);
   if (nc1 > 0) {
     rec(0);
-    k_dots<T><<<p.c1.g.ctas, 32 * p.c1.W, sweep_smem_bytes<T>(p.c1.W, p.c1.nbuf, nc1, 1, nc1, 1), s>>>(p);
+    e = launch_sweep<T>(k_dots<T>, p.c1, sweep_smem_bytes<T>(p.c1.W, p.c1.nbuf, nc1, 1, nc1, 1), s, pdl, p);
+    if (e != cudaSuccess) return e;
     rec(1);
     if (launched) launched[0] = 1;
   }
   rec(2);
-  k_update<T><<<p.c2.g.ctas, 32 * p.c2.W, sweep_smem_bytes<T>(p.c2.W, p.c2.nbuf, p.kD, 1, p.kD, 2), s>>>(p);
+  e = launch_sweep<T>(k_update<T>, p.c2, sweep_smem_bytes<T>(p.c2.W, p.c2.nbuf, p.kD, 1, p.kD, 2), s, pdl, p);
+  if (e != cudaSuccess) return e;
   rec(3);
   if (launched) launched[1] = 1;
   rec(4);
   if (p.ens == 1)
-    k_out_haar<T><<<p.c3.g.ctas, 32 * p.c3.W, sweep_smem_bytes<T>(p.c3.W, p.c3.nbuf, p.kN, 2, p.kN, 1), s>>>(p);
+    e = launch_sweep<T>(k_out_haar<T>, p.c3, sweep_smem_bytes<T>(p.c3.W, p.c3.nbuf, p.kN, 2, p.kN, 1), s,
+                        pdl, p);
   else
-    k_out_gin<T><<<p.c3.g.ctas, 32 * p.c3.W,
-                   sweep_smem_bytes<T>(p.c3.W, p.c3.nbuf, p.kN + p.kD, 1, p.kN, 1), s>>>(p);
+    e = launch_sweep<T>(k_out_gin<T>, p.c3,
+                        sweep_smem_bytes<T>(p.c3.W, p.c3.nbuf, p.kN + p.kD, 1, p.kN, 1), s, pdl, p);
+  if (e != cudaSuccess) return e;
   rec(5);
   if (launched) launched[2] = 1;
   return cudaGetLastError();
@@ -844,6 +965,21 @@ cudaError_t set_sweep_smem_limit(int bytes) {
 }
 template cudaError_t set_sweep_smem_limit<float>(int);
 template cudaError_t set_sweep_smem_limit<double>(int);
+
+template <typename T>
+int kernel_static_smem(int which) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaErrorInvalidValue;
+  switch (which) {
+    case 0: e = cudaFuncGetAttributes(&fa, k_dots<T>); break;
+    case 1: e = cudaFuncGetAttributes(&fa, k_update<T>); break;
+    case 2: e = cudaFuncGetAttributes(&fa, k_out_haar<T>); break;
+    default: e = cudaFuncGetAttributes(&fa, k_out_gin<T>); break;
+  }
+  return (e == cudaSuccess) ? (int)fa.sharedSizeBytes : 8192;
+}
+template int kernel_static_smem<float>(int);
+template int kernel_static_smem<double>(int);
 
 template <typename T>
 int kernel_occupancy(int which, size_t dynsmem) {

@@ -80,9 +80,9 @@ struct SweepCfg {
 // 16 bytes, and the W * NR * ncolC FP64 column sums; every section rounded up to 16 bytes).
 template <typename T>
 inline size_t sweep_smem_bytes(int W, int nbuf, int ncolT, int NRV, int ncolC, int NR) {
-  constexpr int VEC = 16 / (int)sizeof(T);
+  constexpr int NCH = 32 * (int)sizeof(T) / 16;   // 16-byte chunks per 32-row column
   auto r16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
-  const size_t cpad = (size_t)(ncolT + VEC - 1) / VEC * VEC;
+  const size_t cpad = (size_t)(ncolT + NCH - 1) / NCH * NCH;
   return r16((size_t)W * nbuf * (ncolT + NRV) * 32 * sizeof(T)) + r16((size_t)W * 2 * 32 * sizeof(T)) +
          r16(2 * cpad * sizeof(T)) + r16((size_t)W * NR * (ncolC > 0 ? ncolC : 1) * sizeof(double));
 }
@@ -106,6 +106,7 @@ struct StepPlan {
   DrawKey key_next;     // the next step's draw (t + 1)
   T sigma;              // entry scale of the draws (Ginibre), 1 for Haar
   SweepCfg c1, c2, c3;  // launch shapes of the three sweeps
+  int pdl;              // launch with programmatic dependent launch
 };
 
 template <typename T>
@@ -121,6 +122,8 @@ cudaError_t launch_probe(const StepPlan<T>& p, double* q, double* unrevealed, cu
 
 template <typename T>
 int kernel_occupancy(int which, size_t dynsmem);
+template <typename T>
+int kernel_static_smem(int which);
 template <typename T>
 cudaError_t set_sweep_smem_limit(int bytes);
 

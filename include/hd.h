@@ -70,6 +70,22 @@ typedef enum { HD_F64 = 0, HD_F32 = 1 } hd_dtype;
 HD_API int hd_create(int ensemble, int64_t m, int64_t n, int32_t T_max, uint64_t seed,
                      int dtype, hd_state** out);
 
+/* A batch of `count` independent trials in one state (the paper's Monte-Carlo use: many
+ * trajectories of the same dynamics): trial i is Q_i ~ Gin(m[i], n[i]) or Haar(n[i])
+ * (m[i] == n[i]), with its own draws (Philox trial word = the state's trial option + i) and
+ * its own reflector stacks; every step of the batch is one launch per sweep for all trials.
+ * Vectors passed to hd_apply / hd_run are packed: trial i's entries of an n-space vector
+ * occupy [off_n[i], off_n[i+1]) and of an m-space vector [off_m[i], off_m[i+1]) (no padding;
+ * hd_get_batch_layout).  All trials share T_max (bounded by every trial's dimensions, as in
+ * hd_create), the schedule of Q / Q^T and the options.
+ * hd_probe is for single-trial states only. */
+HD_API int hd_create_batched(int ensemble, int32_t count, const int64_t* m, const int64_t* n,
+                             int32_t T_max, uint64_t seed, int dtype, hd_state** out);
+
+/* Packed layout of a state's vectors: *count trials; off_n and off_m (either may be NULL)
+ * receive count + 1 offsets each (prefix sums of n[i] and m[i]). */
+HD_API int hd_get_batch_layout(const hd_state* st, int32_t* count, int64_t* off_n, int64_t* off_m);
+
 /* Options; take effect from the next step.  sigma: entry standard deviation of the
  * Ginibre ensemble (> 0, finite; ignored for Haar, whose reflector H(g) does not depend on
  * the scale of g).  trial: the Philox counter word that separates independent trials

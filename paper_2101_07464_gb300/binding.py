@@ -34,6 +34,9 @@ _PROTOS = {
     "hd_create": (_c.c_int, [_c.c_int, _c.c_int64, _c.c_int64, _c.c_int32, _c.c_uint64, _c.c_int,
                              _c.POINTER(_P)]),
     "hd_set_options": (_c.c_int, [_P, _c.c_double, _c.c_uint32, _P]),
+    "hd_create_batched": (_c.c_int, [_c.c_int, _c.c_int32, _P, _P, _c.c_int32, _c.c_uint64, _c.c_int,
+                                     _c.POINTER(_P)]),
+    "hd_get_batch_layout": (_c.c_int, [_P, _c.POINTER(_c.c_int32), _P, _P]),
     "hd_apply": (_c.c_int, [_P, _P, _c.c_int, _P]),
     "hd_probe": (_c.c_int, [_P, _P, _c.c_int, _P, _c.POINTER(_c.c_double)]),
     "hd_reset": (_c.c_int, [_P, _c.c_uint64]),
@@ -123,6 +126,32 @@ def hd_create(ensemble, m, n, T_max, seed, dtype):
     _check(lib().hd_create(ens, m, n, T_max, seed & 0xFFFFFFFFFFFFFFFF, dt, ctypes.byref(h)),
            "hd_create")
     return h
+
+
+def hd_create_batched(ensemble, ms, ns, T_max, seed, dtype):
+    import numpy as np
+    ens = ENSEMBLES.get(ensemble, ensemble)
+    dt = DTYPES.get(dtype, dtype)
+    m = np.ascontiguousarray(ms, dtype=np.int64)
+    n = np.ascontiguousarray(ns, dtype=np.int64)
+    if m.shape != n.shape:
+        raise ValueError("m and n must have the same length")
+    h = _P()
+    _check(lib().hd_create_batched(ens, len(m), m.ctypes.data, n.ctypes.data, T_max,
+                                   seed & 0xFFFFFFFFFFFFFFFF, dt, ctypes.byref(h)), "hd_create_batched")
+    return h
+
+
+def hd_get_batch_layout(state):
+    """Returns (off_n, off_m) as numpy int64 arrays of count + 1 packed offsets."""
+    import numpy as np
+    c = ctypes.c_int32()
+    _check(lib().hd_get_batch_layout(state, ctypes.byref(c), None, None), "hd_get_batch_layout")
+    on = np.zeros(c.value + 1, dtype=np.int64)
+    om = np.zeros(c.value + 1, dtype=np.int64)
+    _check(lib().hd_get_batch_layout(state, ctypes.byref(c), on.ctypes.data, om.ctypes.data),
+           "hd_get_batch_layout")
+    return on, om
 
 
 def hd_set_options(state, sigma=1.0, trial=0, stream=None):
@@ -217,6 +246,45 @@ def hd_philox_normals(seed, trial, step, stream_id, start, count, dtype, out, st
 def hd_philox_words(seed, counters, nblocks, out, stream=None):
     _check(lib().hd_philox_words(seed & 0xFFFFFFFFFFFFFFFF, _ptr(counters, what="counters"), nblocks,
                                  _ptr(out, what="out"), _stream_ptr(stream)), "hd_philox_words")
+
+
+class HDBatch:
+    """Owner of a batched hd_state: `count` independent trials, packed vectors."""
+
+    def __init__(self, ensemble, ms, ns, T_max, seed, dtype="f32", sigma=1.0, trial=0, stream=None):
+        import torch
+        self.dtype_code = DTYPES.get(dtype, dtype)
+        self.torch_dtype = torch.float64 if self.dtype_code == HD_F64 else torch.float32
+        self.h = hd_create_batched(ensemble, ms, ns, T_max, seed, self.dtype_code)
+        self.off_n, self.off_m = hd_get_batch_layout(self.h)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        hd_set_options(self.h, sigma, trial, stream)
+
+    def apply(self, x, transpose=False, out=None):
+        import torch
+        dim_in = int(self.off_m[-1] if transpose else self.off_n[-1])
+        dim_out = int(self.off_n[-1] if transpose else self.off_m[-1])
+        _ptr(x, self.dtype_code, dim_in, "x")
+        if out is None:
+            out = torch.empty(dim_out, dtype=self.torch_dtype, device=x.device)
+        hd_apply(self.h, x, transpose, out)
+        return out
+
+    def reset(self, seed):
+        hd_reset(self.h, seed)
+
+    def close(self):
+        if self.h:
+            hd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class HD:

@@ -1,5 +1,6 @@
-// Host side of libhd.so: the hd_state, its device memory, launch shapes, and the C ABI
-// declared in include/hd.h.
+// Host side of libhd.so: the hd_state (a batch of independent trials; one for the
+// single-trial API), its device memory, launch shapes, and the C ABI declared in
+// include/hd.h.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -19,31 +20,34 @@ using namespace hd;
 
 struct hd_state {
   int ens = 0, dtype = 0;
-  int64_t m = 0, n = 0;
+  int count = 1;                 // trials
+  std::vector<int64_t> dims[2];  // per trial: dims[0] = n_i (space of R), dims[1] = m_i (space of L)
+  std::vector<int64_t> off[2];   // packed vector offsets per space (count + 1)
   int Tm = 0;
   uint64_t seed = 0;
-  uint32_t trial = 0;
+  uint32_t trial = 0;            // Philox trial word of trial 0 (trial i uses trial + i)
   double sigma = 1.0;
   cudaStream_t stream = nullptr;
   int device = 0;
   int t = 0, r = 0, l = 0;
-  int drawn = 0;         // first draws made since create/reset
-  int poisoned = 0;      // sticky error code
-  size_t esz = 8;        // element size of vectors and stacks
-  StackDev st[2];        // 0: R (acts on R^n), 1: L (acts on R^m)
-  void* basis[2] = {nullptr, nullptr};  // Ginibre: 0 = Q^T-step v_i (n-space), 1 = Q-step u_i (m-space)
-  int64_t ldb[2] = {0, 0};
-  Ws ws;
-  Grid grid[2];          // launch shape for each space (0: n, 1: m)
+  int drawn = 0;                 // first draws made since create/reset
+  int poisoned = 0;              // sticky error code
+  size_t esz = 8;                // element size of vectors and stacks
+  std::vector<TrialDesc> hdesc;  // host copy of the per-trial descriptors
+  TrialDesc* ddesc = nullptr;
+  CtaMap map[2];
+  int maxncta = 1;
+  unsigned int* err = nullptr;
+  unsigned int* cnt = nullptr;
+  size_t cnt_bytes = 0;
   int nsm = 1;
-  int pdl = 1;           // programmatic dependent launch of the sweeps (HD_DISABLE_PDL=1: off)
-  int occ_regs[4] = {1, 1, 1, 1};  // CTAs per SM allowed by registers: K1, K2, K3 Haar, K3 Gin
-  int static_smem[4] = {0, 0, 0, 0};  // static shared memory of each sweep kernel
-  int smem_sm = 0;       // shared memory per SM usable by CTAs
-  int smem_blk_max = 0;  // opt-in dynamic shared memory per CTA
+  int pdl = 1;                   // programmatic dependent launch of the sweeps (HD_DISABLE_PDL=1: off)
+  int occ_regs[4] = {1, 1, 1, 1};  // CTAs of 256 threads per SM allowed by registers per sweep
+  int static_smem[4] = {0, 0, 0, 0};
+  int smem_sm = 0;
+  int smem_blk_max = 0;
   int64_t bytes = 0;
-  void* allocs[40];
-  int nalloc = 0;
+  std::vector<void*> allocs;
   // hd_run: work vectors and the cached trajectory graph
   void* xw[2] = {nullptr, nullptr};
   void* yw = nullptr;
@@ -60,13 +64,12 @@ struct hd_state {
   int g_final = 0;
   int g_launches = 0;
   int g_prof = 0;
-  // kernel launches issued (graph replays count the captured launches)
-  int64_t launches = 0;
+  int64_t launches = 0;          // kernel launches issued (graph replays count their kernels)
   // profiling: event pairs around each sweep, algorithmic bytes of each recorded launch
   int prof_on = 0;
   int prof_cap = 0;
   int prof_used = 0;
-  std::vector<cudaEvent_t> prof_ev;   // 2 per slot
+  std::vector<cudaEvent_t> prof_ev;
   std::vector<int> prof_kind;
   std::vector<double> prof_bytes;
   double prof_ms[3] = {0, 0, 0};
@@ -82,46 +85,30 @@ void set_error(const char* where, cudaError_t e) {
   snprintf(g_last_error, sizeof(g_last_error), "%s: %s", where, cudaGetErrorString(e));
 }
 
-int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
-
 int cuda_fail(hd_state* st, cudaError_t e) {
   set_error("kernel launch", e);
   if (st) st->poisoned = HD_ERR_CUDA;
   return HD_ERR_CUDA;
 }
 
+int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
 void* dalloc(hd_state* st, size_t bytes) {
   void* p = nullptr;
   if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) & ~(size_t)255;
   if (cudaMalloc(&p, bytes) != cudaSuccess) {
     cudaGetLastError();
     return nullptr;
   }
-  st->allocs[st->nalloc++] = p;
+  st->allocs.push_back(p);
   st->bytes += (int64_t)bytes;
   return p;
 }
 
 void free_all(hd_state* st) {
-  for (int i = 0; i < st->nalloc; i++) cudaFree(st->allocs[i]);
-  st->nalloc = 0;
-}
-
-Grid make_grid(int64_t dim, int vec, int occ, int nsm) {
-  Grid g;
-  const int64_t nvec = (dim + vec - 1) / vec;
-  const int64_t cap = (int64_t)kThreads * kChunkMax;
-  int64_t ctas = std::max<int64_t>((nvec + cap - 1) / cap,
-                                   std::min<int64_t>((int64_t)occ * nsm, (nvec + kThreads - 1) / kThreads));
-  if (ctas < 1) ctas = 1;
-  g.vpc = (nvec + ctas - 1) / ctas;
-  ctas = (nvec + g.vpc - 1) / g.vpc;
-  g.ctas = (int)ctas;
-  int gs = (int)std::ceil(std::sqrt((double)ctas));
-  if (gs < 1) gs = 1;
-  g.gsize = gs;
-  g.ngroups = (int)((ctas + gs - 1) / gs);
-  return g;
+  for (void* p : st->allocs) cudaFree(p);
+  st->allocs.clear();
 }
 
 DrawKey key_for(const hd_state* st, int step) {
@@ -129,40 +116,21 @@ DrawKey key_for(const hd_state* st, int step) {
   k.k0 = (uint32_t)(st->seed & 0xFFFFFFFFu);
   k.k1 = (uint32_t)(st->seed >> 32);
   k.step = (uint32_t)step;
-  k.trial = st->trial;
+  k.trial = st->trial;   // replaced per trial by the kernels (desc.trial)
   k.stream = 0;
   return k;
 }
 
-bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
-
+// Shape of a sweep over ncolT staged columns and NRV staged row vectors (ncolC column-owner
+// columns, NR right-hand sides): the (warps per CTA, pipeline stages per warp) pair that puts
+// the most bytes in flight per SM (capped at 128 KB; then more resident warps, then fewer
+// stages).  The CTA count comes from the space's CTA map.
 template <typename T>
-int first_draws(hd_state* st) {
-  const T sigma = (st->ens == HD_GINIBRE) ? (T)st->sigma : T(1);
-  for (int s = 0; s < 2; s++) {
-    cudaError_t e = launch_first_draw<T>(st->st[s], 0, key_for(st, 1), sigma, st->ws, 0,
-                                         st->grid[s], st->stream);
-    if (e != cudaSuccess) return cuda_fail(st, e);
-  }
-  st->drawn = 1;
-  return HD_OK;
-}
-
-// Launch shape of a tiled sweep over ncol columns of a dim-row stack: the largest tile
-// height R in {256, 128, 64, 32} whose two-stage footprint leaves room for two CTAs per
-// SM; else one CTA per SM with two stages; else one stage.  Persistent grid of
-// min(tiles, resident CTAs).
-// Launch shape of a sweep over ncolT staged columns and NRV staged row vectors (ncolC
-// column-owner columns, NR right-hand sides) of a dim-row stack: the (warps per CTA, pipeline
-// stages per warp) pair that puts the most bytes in flight per SM (capped at 128 KB; then
-// more resident warps, then fewer stages), and a persistent grid of min(sub-tile groups,
-// resident CTAs).
-template <typename T>
-SweepCfg make_sweep(const hd_state* st, int which, int ncolT, int NRV, int ncolC, int NR, int64_t dim) {
+SweepCfg make_sweep(const hd_state* st, int which, int ncolT, int NRV, int ncolC, int NR) {
   SweepCfg c;
   c.W = 8;
   c.nbuf = 1;
-  const int stat = st->static_smem[which] + 1024;   // static + per-CTA reserve
+  const int stat = st->static_smem[which] + 1024;
   const int blk = st->smem_blk_max - stat;
   const double stage = (double)(ncolT + NRV) * 32.0 * sizeof(T);
   double best = -1.0;
@@ -183,28 +151,54 @@ SweepCfg make_sweep(const hd_state* st, int which, int ncolT, int NRV, int ncolC
       }
     }
   }
-  const size_t bytes = sweep_smem_bytes<T>(c.W, c.nbuf, ncolT, NRV, ncolC, NR);
-  const int by_regs = std::max(1, st->occ_regs[which] * 8 / c.W);
-  const int occ = std::max(1, std::min(by_regs, (int)(st->smem_sm / (bytes + stat))));
-  const int64_t nsub = (dim + 31) / 32;
-  int64_t ctas = std::min<int64_t>((nsub + c.W - 1) / c.W, (int64_t)occ * st->nsm);
-  if (ctas < 1) ctas = 1;
-  c.g.ctas = (int)ctas;
+  c.g.ctas = 0;
   c.g.vpc = 0;
-  c.g.gsize = std::max(1, (int)std::ceil(std::sqrt((double)ctas)));
-  c.g.ngroups = (int)((ctas + c.g.gsize - 1) / c.g.gsize);
+  c.g.gsize = 1;
+  c.g.ngroups = 1;
   return c;
 }
 
 template <typename T>
-void set_sweeps(const hd_state* st, StepPlan<T>* p) {
-  const int nc1 = p->kD + ((p->ens == 0) ? p->kN : 0);
-  p->c1 = make_sweep<T>(st, 0, nc1, 1, nc1, 1, p->D.dim);
-  p->c2 = make_sweep<T>(st, 1, p->kD, 1, p->kD, 2, p->D.dim);
-  if (p->ens == 1)
-    p->c3 = make_sweep<T>(st, 2, p->kN, 2, p->kN, 1, p->N.dim);
+BatchStep<T> make_batch(const hd_state* st, int d, int kD, int kN, const void* x, void* y) {
+  BatchStep<T> b;
+  memset(&b, 0, sizeof(b));
+  StepPlan<T>& p = b.base;
+  p.ens = st->ens;
+  p.Tm = st->Tm;
+  p.kD = kD;
+  p.kN = kN;
+  p.x = (const T*)x;
+  p.y = (T*)y;
+  p.sigma = (st->ens == HD_GINIBRE) ? (T)st->sigma : T(1);
+  const int nc1 = kD + ((st->ens == 0) ? kN : 0);
+  p.c1 = make_sweep<T>(st, 0, nc1, 1, nc1, 1);
+  p.c2 = make_sweep<T>(st, 1, kD, 1, kD, 2);
+  if (st->ens == HD_HAAR)
+    p.c3 = make_sweep<T>(st, 2, kN, 2, kN, 1);
   else
-    p->c3 = make_sweep<T>(st, 3, p->kN + p->kD, 1, p->kN, 1, p->N.dim);
+    p.c3 = make_sweep<T>(st, 3, kN + kD, 1, kN, 1);
+  p.pdl = st->pdl;
+  // trial 0's stacks give the host-side launch code its dimensions (probe)
+  p.D = st->hdesc[0].st[d];
+  p.N = st->hdesc[0].st[1 - d];
+  b.d = d;
+  b.desc = st->ddesc;
+  b.map[0] = st->map[0];
+  b.map[1] = st->map[1];
+  return b;
+}
+
+template <typename T>
+int first_draws(hd_state* st) {
+  const T sigma = (st->ens == HD_GINIBRE) ? (T)st->sigma : T(1);
+  BatchStep<T> b = make_batch<T>(st, 0, 0, 0, nullptr, nullptr);
+  for (int s = 0; s < 2; s++) {
+    cudaError_t e = launch_first_draw<T>(b, s, key_for(st, 1), sigma, st->stream);
+    if (e != cudaSuccess) return cuda_fail(st, e);
+  }
+  st->drawn = 1;
+  st->launches += 2;
+  return HD_OK;
 }
 
 template <typename T>
@@ -214,31 +208,11 @@ int do_step(hd_state* st, const void* x, int transpose, void* y) {
     if (rc) return rc;
   }
   const int d = transpose ? 1 : 0;  // data-side stack: R for Q, L for Q^T
-  StepPlan<T> p;
-  p.ens = st->ens;
-  p.Tm = st->Tm;
   const int cnt[2] = {st->r, st->l};
-  if (st->ens == HD_HAAR) {
-    p.kD = p.kN = st->t;
-  } else {
-    p.kD = cnt[d];
-    p.kN = cnt[1 - d];
-  }
-  p.D = st->st[d];
-  p.N = st->st[1 - d];
-  p.Bd = st->basis[d];
-  p.ldBd = st->ldb[d];
-  p.Bn = st->basis[1 - d];
-  p.ldBn = st->ldb[1 - d];
-  p.x = (const T*)x;
-  p.xal = aligned16(x);
-  p.y = (T*)y;
-  p.yal = aligned16(y);
-  p.ws = st->ws;
-  p.key_next = key_for(st, st->t + 2);
-  p.sigma = (st->ens == HD_GINIBRE) ? (T)st->sigma : T(1);
-  set_sweeps<T>(st, &p);
-  p.pdl = st->pdl;
+  const int kD = (st->ens == HD_HAAR) ? st->t : cnt[d];
+  const int kN = (st->ens == HD_HAAR) ? st->t : cnt[1 - d];
+  BatchStep<T> b = make_batch<T>(st, d, kD, kN, x, y);
+  b.base.key_next = key_for(st, st->t + 2);
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   int slot0 = -1;
   if (st->prof_on && st->prof_used + 3 <= st->prof_cap) {
@@ -249,21 +223,20 @@ int do_step(hd_state* st, const void* x, int transpose, void* y) {
     }
   }
   int launched[3] = {0, 0, 0};
-  cudaError_t e = launch_step<T>(p, st->stream, ev, launched);
+  cudaError_t e = launch_step<T>(b, st->stream, ev, launched);
   if (e != cudaSuccess) return cuda_fail(st, e);
   st->launches += launched[0] + launched[1] + launched[2];
   if (slot0 >= 0) {
-    // algorithmic bytes: each sweep reads its stack once plus its vectors
+    // algorithmic bytes: each sweep reads its stack once plus the vectors it reads/writes
     const double es = (double)sizeof(T);
-    const double nD = (double)p.D.dim, nN = (double)p.N.dim;
-    const double bd = (st->ens == HD_GINIBRE) ? (double)p.kN * nD : 0.0;  // data-space basis
-    const double bn = (st->ens == HD_GINIBRE) ? (double)(p.kD + 1) * nN : 0.0;
-    const double b[3] = {es * (nD * p.kD + bd + nD),
-                         es * (nD * p.kD + 3.0 * nD),
-                         es * (nN * p.kN + bn + 4.0 * nN)};
+    const double nD = (double)(st->off[d][st->count]), nN = (double)(st->off[1 - d][st->count]);
+    const double bd = (st->ens == HD_GINIBRE) ? (double)kN * nD : 0.0;
+    const double bn = (st->ens == HD_GINIBRE) ? (double)(kD + 1) * nN : 0.0;
+    const double bb[3] = {es * (nD * kD + bd + nD), es * (nD * kD + 3.0 * nD),
+                          es * (nN * kN + bn + 4.0 * nN)};
     for (int q = 0; q < 3; q++) {
       st->prof_kind[slot0 + q] = launched[q] ? q : -1;
-      st->prof_bytes[slot0 + q] = b[q];
+      st->prof_bytes[slot0 + q] = bb[q];
     }
     st->prof_used += 3;
   }
@@ -275,38 +248,20 @@ int do_step(hd_state* st, const void* x, int transpose, void* y) {
 template <typename T>
 int do_probe(hd_state* st, const void* x, int transpose, void* y, double* unrevealed_host) {
   const int d = transpose ? 1 : 0;
-  StepPlan<T> p;
-  p.ens = st->ens;
-  p.Tm = st->Tm;
   const int cnt[2] = {st->r, st->l};
-  if (st->ens == HD_HAAR) {
-    p.kD = p.kN = st->t;
-  } else {
-    p.kD = cnt[d];
-    p.kN = cnt[1 - d];
-  }
-  p.D = st->st[d];
-  p.N = st->st[1 - d];
-  p.Bd = st->basis[d];
-  p.ldBd = st->ldb[d];
-  p.Bn = st->basis[1 - d];
-  p.ldBn = st->ldb[1 - d];
-  p.x = (const T*)x;
-  p.xal = aligned16(x);
-  p.y = (T*)y;
-  p.yal = aligned16(y);
-  p.ws = st->ws;
-  p.sigma = T(1);
-  set_sweeps<T>(st, &p);
-  p.pdl = 0;
+  const int kD = (st->ens == HD_HAAR) ? st->t : cnt[d];
+  const int kN = (st->ens == HD_HAAR) ? st->t : cnt[1 - d];
+  BatchStep<T> b = make_batch<T>(st, d, kD, kN, x, y);
+  b.base.pdl = 0;
+  const int64_t dimD = st->dims[d][0];
   double* q = nullptr;
-  if (cudaMalloc(&q, (size_t)(p.D.dim + 1) * 8) != cudaSuccess) {
+  if (cudaMalloc(&q, (size_t)(dimD + 1) * 8) != cudaSuccess) {
     set_error("hd_probe cudaMalloc", cudaGetLastError());
     return HD_ERR_OOM;
   }
-  double* unrev = q + p.D.dim;
+  double* unrev = q + dimD;
   cudaError_t e = cudaMemsetAsync(unrev, 0, 8, st->stream);
-  if (e == cudaSuccess) e = launch_probe<T>(p, q, unrev, st->stream);
+  if (e == cudaSuccess) e = launch_probe<T>(b, q, unrev, st->stream);
   double u2 = 0.0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&u2, unrev, 8, cudaMemcpyDeviceToHost, st->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st->stream);
@@ -326,7 +281,7 @@ int run_steps(hd_state* st, const hd_run_spec* sp) {
     const int tr = sp->transpose[t] ? 1 : 0;
     int rc = do_step<T>(st, st->xw[cur], tr, st->yw);
     if (rc) return rc;
-    const int64_t nout = tr ? st->n : st->m;
+    const int64_t nout = st->off[tr ? 0 : 1][st->count];   // packed length of the output space
     cudaError_t e = launch_dynamics<T>(sp->dynamics, sp->a, (const T*)st->yw, (const T*)st->xw[cur],
                                        (const T*)st->xw[1 - cur], (T*)st->xw[1 - cur], nout,
                                        st->sumsq, st->stream, st->pdl != 0);
@@ -347,9 +302,293 @@ bool graph_matches(const hd_state* st, const hd_run_spec* sp) {
   return true;
 }
 
+// CTA map of one space: every trial gets ceil(nsub_i / spc) CTAs of spc 32-row sub-tiles,
+// spc chosen so that a single large trial fills about two CTAs per SM.
+bool build_map(hd_state* st, int s) {
+  const int count = st->count;
+  std::vector<int64_t> nsub(count);
+  int64_t total = 0;
+  for (int i = 0; i < count; i++) {
+    nsub[i] = (st->dims[s][i] + 31) / 32;
+    total += nsub[i];
+  }
+  const int64_t spc = std::max<int64_t>(16, (total + 2 * st->nsm - 1) / (2 * st->nsm));
+  std::vector<int> cta0(count + 1), spcv(count);
+  std::vector<int> ct;
+  cta0[0] = 0;
+  for (int i = 0; i < count; i++) {
+    const int n_i = (int)((nsub[i] + spc - 1) / spc);
+    spcv[i] = (int)spc;
+    for (int c = 0; c < n_i; c++) ct.push_back(i);
+    cta0[i + 1] = cta0[i] + n_i;
+    st->maxncta = std::max(st->maxncta, n_i);
+  }
+  int* d_ct = (int*)dalloc(st, ct.size() * sizeof(int));
+  int* d_c0 = (int*)dalloc(st, cta0.size() * sizeof(int));
+  int* d_sp = (int*)dalloc(st, spcv.size() * sizeof(int));
+  if (!d_ct || !d_c0 || !d_sp) return false;
+  if (cudaMemcpy(d_ct, ct.data(), ct.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(d_c0, cta0.data(), cta0.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(d_sp, spcv.data(), spcv.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+    return false;
+  st->map[s].cta_trial = d_ct;
+  st->map[s].cta0 = d_c0;
+  st->map[s].spc = d_sp;
+  st->map[s].ctas = cta0[count];
+  return true;
+}
+
+int create_common(int ensemble, int count, const int64_t* m, const int64_t* n, int32_t T_max,
+                  uint64_t seed, int dtype, hd_state** out) {
+  if (!out || !m || !n) return HD_ERR_ARG;
+  *out = nullptr;
+  if (count < 1) return HD_ERR_DIM;
+  if (ensemble != HD_GINIBRE && ensemble != HD_HAAR) return HD_ERR_ARG;
+  if (dtype != HD_F64 && dtype != HD_F32) return HD_ERR_ARG;
+  if (T_max <= 0 || T_max > kTmaxLimit) return HD_ERR_TMAX;
+  for (int i = 0; i < count; i++) {
+    if (m[i] <= 0 || n[i] <= 0) return HD_ERR_DIM;
+    if (ensemble == HD_HAAR && m[i] != n[i]) return HD_ERR_DIM;
+    if (m[i] > ((int64_t)1 << 40) || n[i] > ((int64_t)1 << 40)) return HD_ERR_DIM;
+    if (ensemble == HD_GINIBRE && T_max > std::min(m[i], n[i])) return HD_ERR_TMAX;
+    if (ensemble == HD_HAAR && T_max > n[i]) return HD_ERR_TMAX;
+  }
+  hd_state* st = new (std::nothrow) hd_state();
+  if (!st) return HD_ERR_OOM;
+  auto fail = [&](int code) {
+    free_all(st);
+    delete st;
+    return code;
+  };
+  st->ens = ensemble;
+  st->dtype = dtype;
+  st->count = count;
+  st->Tm = T_max;
+  st->seed = seed;
+  st->esz = (dtype == HD_F64) ? 8 : 4;
+  for (int i = 0; i < count; i++) {
+    st->dims[0].push_back(n[i]);
+    st->dims[1].push_back(m[i]);
+  }
+  for (int s = 0; s < 2; s++) {
+    st->off[s].assign(count + 1, 0);
+    for (int i = 0; i < count; i++) st->off[s][i + 1] = st->off[s][i] + st->dims[s][i];
+  }
+  if (cudaGetDevice(&st->device) != cudaSuccess) {
+    set_error("cudaGetDevice", cudaGetLastError());
+    return fail(HD_ERR_CUDA);
+  }
+  cudaDeviceGetAttribute(&st->nsm, cudaDevAttrMultiProcessorCount, st->device);
+  if (st->nsm <= 0) st->nsm = 1;
+  {
+    const char* env = getenv("HD_DISABLE_PDL");
+    st->pdl = (env && env[0] == '1') ? 0 : 1;
+  }
+  cudaDeviceGetAttribute(&st->smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, st->device);
+  cudaDeviceGetAttribute(&st->smem_blk_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, st->device);
+  {
+    const size_t need = (dtype == HD_F64) ? sweep_smem_bytes<double>(1, 1, T_max, 2, T_max, 2)
+                                          : sweep_smem_bytes<float>(1, 1, T_max, 2, T_max, 2);
+    if ((int)need > st->smem_blk_max - 8192) return fail(HD_ERR_TMAX);
+    cudaError_t e = (dtype == HD_F64) ? set_sweep_smem_limit<double>(st->smem_blk_max - 1024)
+                                      : set_sweep_smem_limit<float>(st->smem_blk_max - 1024);
+    if (e != cudaSuccess) {
+      set_error("cudaFuncSetAttribute", e);
+      cudaGetLastError();
+      return fail(HD_ERR_CUDA);
+    }
+  }
+  for (int q = 0; q < 4; q++) {
+    st->occ_regs[q] = (dtype == HD_F64) ? kernel_occupancy<double>(q, 0) : kernel_occupancy<float>(q, 0);
+    st->static_smem[q] = (dtype == HD_F64) ? kernel_static_smem<double>(q) : kernel_static_smem<float>(q);
+  }
+  for (int s = 0; s < 2; s++)
+    if (!build_map(st, s)) return fail(HD_ERR_OOM);
+  const int64_t Tm = T_max;
+  const size_t es = st->esz;
+  // per-space packed stacks: trial i at element offset voff[s][i] (ld_i = round_up(dim, 256))
+  std::vector<int64_t> ld[2], voff[2], goff[2];
+  int64_t vtot[2] = {0, 0}, gtot[2] = {0, 0};
+  for (int s = 0; s < 2; s++) {
+    for (int i = 0; i < count; i++) {
+      const int64_t L = round_up(st->dims[s][i], 256);
+      ld[s].push_back(L);
+      voff[s].push_back(vtot[s]);
+      goff[s].push_back(gtot[s]);
+      vtot[s] += L * Tm;
+      gtot[s] += L;
+    }
+  }
+  void* V[2];
+  void* G[2];
+  void* B[2] = {nullptr, nullptr};
+  double* S[2];
+  double* DP[2];
+  double* GD[2];
+  double* GG[2];
+  for (int s = 0; s < 2; s++) {
+    V[s] = dalloc(st, (size_t)vtot[s] * es);
+    G[s] = dalloc(st, (size_t)gtot[s] * es);
+    S[s] = (double*)dalloc(st, (size_t)count * Tm * Tm * 8);
+    DP[s] = (double*)dalloc(st, (size_t)count * (Tm + 1) * 8);
+    GD[s] = (double*)dalloc(st, (size_t)count * (Tm + 1) * 8);
+    GG[s] = (double*)dalloc(st, (size_t)count * 8);
+    if (!V[s] || !G[s] || !S[s] || !DP[s] || !GD[s] || !GG[s]) return fail(HD_ERR_OOM);
+    if (ensemble == HD_GINIBRE) {
+      B[s] = dalloc(st, (size_t)vtot[s] * es);
+      if (!B[s]) return fail(HD_ERR_OOM);
+    }
+  }
+  // per-trial FP64 workspace (vectors, scratch, partial sums) and election counters
+  const int64_t vs = 2 * Tm + 8;                 // length of the longest small vector
+  const int64_t gmax = (int64_t)std::ceil(std::sqrt((double)st->maxncta)) + 1;
+  const int64_t per_trial = vs /*z*/ + 4 * vs /*w phead wout wout2*/ + 4 * vs /*scr*/ + kNumScal +
+                            (int64_t)st->maxncta * vs /*part*/ + gmax * vs /*gpart*/;
+  double* wsb = (double*)dalloc(st, (size_t)count * per_trial * 8);
+  st->cnt_bytes = (size_t)count * 3 * (kMaxGroups + 1) * sizeof(unsigned int);
+  st->cnt = (unsigned int*)dalloc(st, st->cnt_bytes);
+  st->err = (unsigned int*)dalloc(st, 16);
+  if (!wsb || !st->cnt || !st->err) return fail(HD_ERR_OOM);
+  st->hdesc.resize(count);
+  for (int i = 0; i < count; i++) {
+    TrialDesc& td = st->hdesc[i];
+    memset(&td, 0, sizeof(td));
+    for (int s = 0; s < 2; s++) {
+      StackDev& X = td.st[s];
+      X.V = (char*)V[s] + (size_t)voff[s][i] * es;
+      X.ld = ld[s][i];
+      X.dim = st->dims[s][i];
+      X.S = S[s] + (size_t)i * Tm * Tm;
+      X.dpre = DP[s] + (size_t)i * (Tm + 1);
+      X.gbuf = (char*)G[s] + (size_t)goff[s][i] * es;
+      X.gdot = GD[s] + (size_t)i * (Tm + 1);
+      X.gg = GG[s] + i;
+      td.basis[s] = B[s] ? (char*)B[s] + (size_t)voff[s][i] * es : nullptr;
+      td.ldb[s] = ld[s][i];
+      td.off[s] = st->off[s][i];
+    }
+    double* w = wsb + (size_t)i * per_trial;
+    Ws& ws = td.ws;
+    ws.z = w; w += vs;
+    ws.w = w; w += vs;
+    ws.phead = w; w += vs;
+    ws.wout = w; w += vs;
+    ws.wout2 = w; w += vs;
+    ws.scrb = w; w += 4 * vs;
+    ws.scr_stride = vs;
+    ws.scal = w; w += kNumScal;
+    ws.part = w; w += (int64_t)st->maxncta * vs;
+    ws.gpart = w; w += gmax * vs;
+    ws.cnt = st->cnt + (size_t)i * 3 * (kMaxGroups + 1);
+    ws.err = st->err;
+    td.trial = (uint32_t)i;
+  }
+  st->ddesc = (TrialDesc*)dalloc(st, (size_t)count * sizeof(TrialDesc));
+  if (!st->ddesc) return fail(HD_ERR_OOM);
+  // zero everything: reflector columns must be zero above their pivot, padding rows zero
+  bool ok = true;
+  for (int s = 0; s < 2 && ok; s++) {
+    ok = cudaMemset(V[s], 0, (size_t)vtot[s] * es) == cudaSuccess &&
+         cudaMemset(G[s], 0, (size_t)gtot[s] * es) == cudaSuccess &&
+         cudaMemset(S[s], 0, (size_t)count * Tm * Tm * 8) == cudaSuccess &&
+         cudaMemset(GD[s], 0, (size_t)count * (Tm + 1) * 8) == cudaSuccess &&
+         cudaMemset(GG[s], 0, (size_t)count * 8) == cudaSuccess;
+    if (ok && B[s]) ok = cudaMemset(B[s], 0, (size_t)vtot[s] * es) == cudaSuccess;
+    if (ok) {
+      std::vector<double> dp((size_t)count * (Tm + 1), 0.0);
+      for (int i = 0; i < count; i++) dp[(size_t)i * (Tm + 1)] = 1.0;   // dpre[0] = 1
+      ok = cudaMemcpy(DP[s], dp.data(), dp.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess;
+    }
+  }
+  if (ok) ok = cudaMemset(wsb, 0, (size_t)count * per_trial * 8) == cudaSuccess;
+  if (ok) ok = cudaMemset(st->cnt, 0, st->cnt_bytes) == cudaSuccess;
+  if (ok) ok = cudaMemset(st->err, 0, 16) == cudaSuccess;
+  if (ok) ok = cudaMemcpy(st->ddesc, st->hdesc.data(), (size_t)count * sizeof(TrialDesc),
+                          cudaMemcpyHostToDevice) == cudaSuccess;
+  if (ok) ok = cudaDeviceSynchronize() == cudaSuccess;
+  if (!ok) {
+    set_error("hd_create initialisation", cudaGetLastError());
+    return fail(HD_ERR_CUDA);
+  }
+  *out = st;
+  return HD_OK;
+}
+
+// Philox trial words of the trials: base + i.
+int upload_trials(hd_state* st) {
+  for (int i = 0; i < st->count; i++) st->hdesc[i].trial = st->trial + (uint32_t)i;
+  if (cudaMemcpy(st->ddesc, st->hdesc.data(), (size_t)st->count * sizeof(TrialDesc),
+                 cudaMemcpyHostToDevice) != cudaSuccess) {
+    set_error("trial upload", cudaGetLastError());
+    return HD_ERR_CUDA;
+  }
+  return HD_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+HD_API const char* hd_last_error(void) { return g_last_error; }
+
+HD_API const char* hd_status_string(int status) {
+  switch (status) {
+    case HD_OK: return "HD_OK";
+    case HD_ERR_ARG: return "HD_ERR_ARG: invalid argument";
+    case HD_ERR_DIM: return "HD_ERR_DIM: invalid dimensions";
+    case HD_ERR_TMAX: return "HD_ERR_TMAX: step limit exceeded";
+    case HD_ERR_OOM: return "HD_ERR_OOM: device allocation failed";
+    case HD_ERR_CUDA: return "HD_ERR_CUDA: CUDA error";
+    case HD_ERR_TIMEOUT: return "HD_ERR_TIMEOUT: device wait expired";
+    case HD_ERR_STATE: return "HD_ERR_STATE: state poisoned by an earlier error";
+    default: return "unknown status";
+  }
+}
+
+HD_API int hd_create(int ensemble, int64_t m, int64_t n, int32_t T_max, uint64_t seed, int dtype,
+                     hd_state** out) {
+  return create_common(ensemble, 1, &m, &n, T_max, seed, dtype, out);
+}
+
+HD_API int hd_create_batched(int ensemble, int32_t count, const int64_t* m, const int64_t* n,
+                             int32_t T_max, uint64_t seed, int dtype, hd_state** out) {
+  return create_common(ensemble, count, m, n, T_max, seed, dtype, out);
+}
+
+HD_API int hd_get_batch_layout(const hd_state* st, int32_t* count, int64_t* off_n, int64_t* off_m) {
+  if (!st) return HD_ERR_ARG;
+  if (count) *count = st->count;
+  for (int i = 0; i <= st->count; i++) {
+    if (off_n) off_n[i] = st->off[0][i];
+    if (off_m) off_m[i] = st->off[1][i];
+  }
+  return HD_OK;
+}
+
+HD_API int hd_set_options(hd_state* st, double sigma, uint32_t trial, void* stream) {
+  if (!st) return HD_ERR_ARG;
+  if (!(sigma > 0.0) || !std::isfinite(sigma)) return HD_ERR_ARG;
+  if (st->t > 0 && (sigma != st->sigma || trial != st->trial)) return HD_ERR_ARG;
+  st->sigma = sigma;
+  st->stream = (cudaStream_t)stream;
+  if (trial != st->hdesc[0].trial) {
+    st->trial = trial;
+    if (cudaSetDevice(st->device) != cudaSuccess) return cuda_fail(st, cudaErrorInvalidDevice);
+    return upload_trials(st);
+  }
+  st->trial = trial;
+  return HD_OK;
+}
+
+HD_API int hd_apply(hd_state* st, const void* x, int transpose, void* y) {
+  if (!st || !x || !y) return HD_ERR_ARG;
+  if (transpose != 0 && transpose != 1) return HD_ERR_ARG;
+  if (st->poisoned) return st->poisoned;
+  if (st->t >= st->Tm) return HD_ERR_TMAX;
+  if (cudaSetDevice(st->device) != cudaSuccess) return cuda_fail(st, cudaErrorInvalidDevice);
+  return (st->dtype == HD_F64) ? do_step<double>(st, x, transpose, y)
+                               : do_step<float>(st, x, transpose, y);
+}
 
 HD_API int hd_run(hd_state* st, const hd_run_spec* sp, const void* x1, void* x_out) {
   if (!st || !sp || !sp->transpose || !x1 || !x_out) return HD_ERR_ARG;
@@ -357,25 +596,26 @@ HD_API int hd_run(hd_state* st, const hd_run_spec* sp, const void* x1, void* x_o
   if (sp->T < 1 || sp->T > st->Tm) return HD_ERR_TMAX;
   if (sp->dynamics != HD_DYN_TANH && sp->dynamics != HD_DYN_SIGN_MEM && sp->dynamics != HD_DYN_NORM_TANH)
     return HD_ERR_ARG;
+  if (sp->dynamics == HD_DYN_NORM_TANH && st->count != 1) return HD_ERR_ARG;
   if (!std::isfinite(sp->a)) return HD_ERR_ARG;
-  // dimensions: input of step t+1 = output of step t; x_{t-1} (sign_mem) matches y_t
+  // dimensions: input of step t+1 = output of step t for every trial
   for (int t = 0; t + 1 < sp->T; t++) {
-    const int64_t out_t = sp->transpose[t] ? st->n : st->m;
-    const int64_t in_next = sp->transpose[t + 1] ? st->m : st->n;
-    if (out_t != in_next) return HD_ERR_DIM;
+    const int so = sp->transpose[t] ? 0 : 1, si = sp->transpose[t + 1] ? 1 : 0;
+    for (int i = 0; i < st->count; i++)
+      if (st->dims[so][i] != st->dims[si][i]) return HD_ERR_DIM;
   }
   if (cudaSetDevice(st->device) != cudaSuccess) return cuda_fail(st, cudaErrorInvalidDevice);
-  const int64_t dmax = std::max(st->m, st->n);
+  const int64_t dmax = std::max(st->off[0][st->count], st->off[1][st->count]);
   if (!st->yw) {
-    const int64_t ld = round_up(dmax, 64);
-    st->xw[0] = dalloc(st, (size_t)ld * st->esz);
-    st->xw[1] = dalloc(st, (size_t)ld * st->esz);
-    st->yw = dalloc(st, (size_t)ld * st->esz);
+    const int64_t L = round_up(dmax, 64);
+    st->xw[0] = dalloc(st, (size_t)L * st->esz);
+    st->xw[1] = dalloc(st, (size_t)L * st->esz);
+    st->yw = dalloc(st, (size_t)L * st->esz);
     st->sumsq = (double*)dalloc(st, 64);
     if (!st->xw[0] || !st->xw[1] || !st->yw || !st->sumsq) return HD_ERR_OOM;
   }
-  const int64_t nin = sp->transpose[0] ? st->m : st->n;
-  const int64_t nfin = sp->transpose[sp->T - 1] ? st->n : st->m;
+  const int64_t nin = st->off[sp->transpose[0] ? 1 : 0][st->count];
+  const int64_t nfin = st->off[sp->transpose[sp->T - 1] ? 0 : 1][st->count];
   cudaError_t e = cudaMemcpyAsync(st->xw[0], x1, (size_t)nin * st->esz, cudaMemcpyDefault, st->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(st->xw[1], 0, (size_t)dmax * st->esz, st->stream);
   if (e != cudaSuccess) {
@@ -457,190 +697,10 @@ HD_API int hd_run(hd_state* st, const hd_run_spec* sp, const void* x1, void* x_o
   return HD_OK;
 }
 
-
-HD_API const char* hd_last_error(void) { return g_last_error; }
-
-HD_API const char* hd_status_string(int status) {
-  switch (status) {
-    case HD_OK: return "HD_OK";
-    case HD_ERR_ARG: return "HD_ERR_ARG: invalid argument";
-    case HD_ERR_DIM: return "HD_ERR_DIM: invalid dimensions";
-    case HD_ERR_TMAX: return "HD_ERR_TMAX: step limit exceeded";
-    case HD_ERR_OOM: return "HD_ERR_OOM: device allocation failed";
-    case HD_ERR_CUDA: return "HD_ERR_CUDA: CUDA error";
-    case HD_ERR_TIMEOUT: return "HD_ERR_TIMEOUT: device wait expired";
-    case HD_ERR_STATE: return "HD_ERR_STATE: state poisoned by an earlier error";
-    default: return "unknown status";
-  }
-}
-
-HD_API int hd_create(int ensemble, int64_t m, int64_t n, int32_t T_max, uint64_t seed, int dtype,
-                     hd_state** out) {
-  if (!out) return HD_ERR_ARG;
-  *out = nullptr;
-  if (ensemble != HD_GINIBRE && ensemble != HD_HAAR) return HD_ERR_ARG;
-  if (dtype != HD_F64 && dtype != HD_F32) return HD_ERR_ARG;
-  if (m <= 0 || n <= 0) return HD_ERR_DIM;
-  if (ensemble == HD_HAAR && m != n) return HD_ERR_DIM;
-  if (m > ((int64_t)1 << 40) || n > ((int64_t)1 << 40)) return HD_ERR_DIM;
-  if (T_max <= 0) return HD_ERR_TMAX;
-  if (ensemble == HD_GINIBRE && T_max > std::min(m, n)) return HD_ERR_TMAX;
-  if (ensemble == HD_HAAR && T_max > n) return HD_ERR_TMAX;
-  if (T_max > kTmaxLimit) return HD_ERR_TMAX;
-
-  hd_state* st = new (std::nothrow) hd_state();
-  if (!st) return HD_ERR_OOM;
-  st->ens = ensemble;
-  st->dtype = dtype;
-  st->m = m;
-  st->n = n;
-  st->Tm = T_max;
-  st->seed = seed;
-  st->esz = (dtype == HD_F64) ? 8 : 4;
-  if (cudaGetDevice(&st->device) != cudaSuccess) {
-    set_error("cudaGetDevice", cudaGetLastError());
-    delete st;
-    return HD_ERR_CUDA;
-  }
-  int nsm = 0;
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, st->device);
-  if (nsm <= 0) nsm = 1;
-  st->nsm = nsm;
-  {
-    const char* env = getenv("HD_DISABLE_PDL");
-    st->pdl = (env && env[0] == '1') ? 0 : 1;
-  }
-  int smem_sm = 0, smem_blk = 0;
-  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, st->device);
-  cudaDeviceGetAttribute(&smem_blk, cudaDevAttrMaxSharedMemoryPerBlockOptin, st->device);
-  st->smem_sm = smem_sm;
-  st->smem_blk_max = smem_blk;
-  {
-    const size_t need = (dtype == HD_F64) ? sweep_smem_bytes<double>(1, 1, T_max, 2, T_max, 2)
-                                          : sweep_smem_bytes<float>(1, 1, T_max, 2, T_max, 2);
-    if ((int)need > smem_blk - 1024) {
-      delete st;
-      return HD_ERR_TMAX;
-    }
-    cudaError_t e = (dtype == HD_F64) ? set_sweep_smem_limit<double>(smem_blk - 1024)
-                                      : set_sweep_smem_limit<float>(smem_blk - 1024);
-    if (e != cudaSuccess) {
-      set_error("cudaFuncSetAttribute", e);
-      cudaGetLastError();
-      delete st;
-      return HD_ERR_CUDA;
-    }
-  }
-  const int vec = (dtype == HD_F64) ? 2 : 4;
-  int occ;
-  const size_t dsm = (size_t)3 * T_max * st->esz;
-  (void)dsm;
-  for (int q = 0; q < 4; q++) {
-    st->occ_regs[q] = (dtype == HD_F64) ? kernel_occupancy<double>(q, 0) : kernel_occupancy<float>(q, 0);
-    st->static_smem[q] = (dtype == HD_F64) ? kernel_static_smem<double>(q) : kernel_static_smem<float>(q);
-  }
-  occ = 4;
-  const int64_t dims[2] = {n, m};
-  int64_t maxctas = (int64_t)nsm * 8;
-  for (int s = 0; s < 2; s++) {
-    st->grid[s] = make_grid(dims[s], vec, occ, nsm);
-    maxctas = std::max<int64_t>(maxctas, st->grid[s].ctas);
-    if (st->grid[s].ngroups > kMaxGroups) {
-      delete st;
-      return HD_ERR_DIM;
-    }
-  }
-  const int64_t Tm = T_max;
-  bool ok = true;
-  for (int s = 0; s < 2 && ok; s++) {
-    StackDev& X = st->st[s];
-    X.dim = dims[s];
-    X.ld = round_up(dims[s], 256);
-    X.V = dalloc(st, (size_t)X.ld * Tm * st->esz);
-    X.S = (double*)dalloc(st, (size_t)Tm * Tm * 8);
-    X.dpre = (double*)dalloc(st, (size_t)(Tm + 1) * 8);
-    X.gbuf = dalloc(st, (size_t)X.ld * st->esz);
-    X.gdot = (double*)dalloc(st, (size_t)(Tm + 1) * 8);
-    X.gg = (double*)dalloc(st, 8);
-    ok = X.V && X.S && X.dpre && X.gbuf && X.gdot && X.gg;
-    if (ok && ensemble == HD_GINIBRE) {
-      st->ldb[s] = X.ld;
-      st->basis[s] = dalloc(st, (size_t)X.ld * Tm * st->esz);
-      ok = st->basis[s] != nullptr;
-    }
-  }
-  const int64_t stride = Tm + 8;
-  if (ok) {
-    Ws& w = st->ws;
-    w.z = (double*)dalloc(st, (size_t)(2 * Tm + 8) * 8);
-    w.w = (double*)dalloc(st, (size_t)stride * 8);
-    w.phead = (double*)dalloc(st, (size_t)stride * 8);
-    w.wout = (double*)dalloc(st, (size_t)stride * 8);
-    w.wout2 = (double*)dalloc(st, (size_t)stride * 8);
-    w.scr_stride = 2 * Tm + 8;
-    w.scrb = (double*)dalloc(st, (size_t)4 * w.scr_stride * 8);
-    w.scal = (double*)dalloc(st, (size_t)kNumScal * 8);
-    w.part = (double*)dalloc(st, (size_t)maxctas * (2 * Tm + 8) * 8);
-    w.gpart = (double*)dalloc(st, (size_t)kMaxGroups * (2 * Tm + 8) * 8);
-    w.cnt = (unsigned int*)dalloc(st, (size_t)3 * (kMaxGroups + 1) * sizeof(unsigned int));
-    w.err = (unsigned int*)dalloc(st, 16);
-    ok = w.z && w.w && w.phead && w.wout && w.wout2 && w.scrb && w.scal && w.part &&
-         w.gpart && w.cnt && w.err;
-  }
-  if (!ok) {
-    free_all(st);
-    delete st;
-    return HD_ERR_OOM;
-  }
-  // Zero everything (reflector columns must be zero above their pivot; padding rows zero).
-  bool zok = true;
-  for (int s = 0; s < 2 && zok; s++) {
-    StackDev& X = st->st[s];
-    zok = cudaMemset(X.V, 0, (size_t)X.ld * Tm * st->esz) == cudaSuccess &&
-          cudaMemset(X.gbuf, 0, (size_t)X.ld * st->esz) == cudaSuccess &&
-          cudaMemset(X.S, 0, (size_t)Tm * Tm * 8) == cudaSuccess &&
-          cudaMemset(X.gdot, 0, (size_t)(Tm + 1) * 8) == cudaSuccess;
-    if (zok && st->basis[s]) zok = cudaMemset(st->basis[s], 0, (size_t)st->ldb[s] * Tm * st->esz) == cudaSuccess;
-    const double one = 1.0;
-    if (zok) zok = cudaMemcpy(X.dpre, &one, 8, cudaMemcpyHostToDevice) == cudaSuccess;
-  }
-  if (zok) zok = cudaMemset(st->ws.cnt, 0, (size_t)3 * (kMaxGroups + 1) * sizeof(unsigned int)) == cudaSuccess;
-  if (zok) zok = cudaMemset(st->ws.err, 0, 16) == cudaSuccess;
-  if (zok) zok = cudaMemset(st->ws.scal, 0, kNumScal * 8) == cudaSuccess;
-  if (zok) zok = cudaDeviceSynchronize() == cudaSuccess;
-  if (!zok) {
-    set_error("hd_create initialisation", cudaGetLastError());
-    free_all(st);
-    delete st;
-    return HD_ERR_CUDA;
-  }
-  *out = st;
-  return HD_OK;
-}
-
-HD_API int hd_set_options(hd_state* st, double sigma, uint32_t trial, void* stream) {
-  if (!st) return HD_ERR_ARG;
-  if (!(sigma > 0.0) || !std::isfinite(sigma)) return HD_ERR_ARG;
-  if (st->t > 0 && (sigma != st->sigma || trial != st->trial)) return HD_ERR_ARG;
-  st->sigma = sigma;
-  st->trial = trial;
-  st->stream = (cudaStream_t)stream;
-  return HD_OK;
-}
-
-HD_API int hd_apply(hd_state* st, const void* x, int transpose, void* y) {
-  if (!st || !x || !y) return HD_ERR_ARG;
-  if (transpose != 0 && transpose != 1) return HD_ERR_ARG;
-  if (st->poisoned) return st->poisoned;
-  if (st->t >= st->Tm) return HD_ERR_TMAX;
-  if (cudaSetDevice(st->device) != cudaSuccess) return cuda_fail(st, cudaErrorInvalidDevice);
-  return (st->dtype == HD_F64) ? do_step<double>(st, x, transpose, y)
-                               : do_step<float>(st, x, transpose, y);
-}
-
 HD_API int hd_probe(hd_state* st, const void* x, int transpose, void* y, double* unrevealed_host) {
   if (!st || !x || !y || !unrevealed_host) return HD_ERR_ARG;
   if (transpose != 0 && transpose != 1) return HD_ERR_ARG;
+  if (st->count != 1) return HD_ERR_ARG;
   if (st->poisoned) return st->poisoned;
   if (cudaSetDevice(st->device) != cudaSuccess) return cuda_fail(st, cudaErrorInvalidDevice);
   return (st->dtype == HD_F64) ? do_probe<double>(st, x, transpose, y, unrevealed_host)
@@ -705,7 +765,7 @@ HD_API int hd_sync(hd_state* st) {
   if (!st) return HD_ERR_ARG;
   if (cudaSetDevice(st->device) != cudaSuccess) return cuda_fail(st, cudaErrorInvalidDevice);
   unsigned int err = 0;
-  cudaError_t e = cudaMemcpyAsync(&err, st->ws.err, sizeof(err), cudaMemcpyDeviceToHost, st->stream);
+  cudaError_t e = cudaMemcpyAsync(&err, st->err, sizeof(err), cudaMemcpyDeviceToHost, st->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st->stream);
   if (e != cudaSuccess) {
     set_error("hd_sync", e);
@@ -723,8 +783,8 @@ HD_API int hd_reset(hd_state* st, uint64_t seed) {
   if (!st) return HD_ERR_ARG;
   if (cudaSetDevice(st->device) == cudaSuccess) {
     // clear election counters and the error word left by an aborted step
-    cudaMemsetAsync(st->ws.cnt, 0, (size_t)3 * (kMaxGroups + 1) * sizeof(unsigned int), st->stream);
-    cudaMemsetAsync(st->ws.err, 0, 16, st->stream);
+    cudaMemsetAsync(st->cnt, 0, st->cnt_bytes, st->stream);
+    cudaMemsetAsync(st->err, 0, 16, st->stream);
   }
   st->seed = seed;
   st->t = st->r = st->l = 0;

@@ -64,14 +64,21 @@ __device__ __forceinline__ bool elect_last(unsigned int* counter, int expected) 
   return last;
 }
 
-// Two-level reduction of P partial sums per CTA (part[b * P + j]).  Returns true in the one
-// CTA that finishes last; there out[j] holds the grand totals (FP64, fixed order).
-__device__ bool reduce_partials(const Ws& ws, int set, int P, const Grid& g, double* out) {
+// Two-level reduction of P partial sums per CTA of one trial (part[local * P + j]): the last
+// CTA of each group of ~sqrt(ncta) CTAs sums its group, the last group-finisher sums the
+// groups.  Returns true in that one CTA; there out[j] holds the totals (FP64, fixed order).
+__device__ __forceinline__ int group_size(int ncta) {
+  int g = (int)sqrtf((float)ncta);
+  while (g * g < ncta) g++;
+  return g < 1 ? 1 : g;
+}
+__device__ bool reduce_partials(const Ws& ws, int set, int P, int local, int ncta, double* out) {
   unsigned int* cnt = ws.cnt + set * (kMaxGroups + 1);
-  const int b = blockIdx.x;
-  const int grp = b / g.gsize;
-  const int gfirst = grp * g.gsize;
-  const int gcount = min(g.gsize, g.ctas - gfirst);
+  const int gsize = group_size(ncta);
+  const int ngroups = (ncta + gsize - 1) / gsize;
+  const int grp = local / gsize;
+  const int gfirst = grp * gsize;
+  const int gcount = min(gsize, ncta - gfirst);
   if (!elect_last(&cnt[grp], gcount)) return false;
   for (int j = threadIdx.x; j < P; j += blockDim.x) {
     double s = 0.0;
@@ -79,15 +86,43 @@ __device__ bool reduce_partials(const Ws& ws, int set, int P, const Grid& g, dou
     for (int c = 0; c < gcount; c++) s += ld_cg(&ws.part[(int64_t)(gfirst + c) * P + j]);
     ws.gpart[(int64_t)grp * P + j] = s;
   }
-  if (!elect_last(&cnt[kMaxGroups], g.ngroups)) return false;
+  if (!elect_last(&cnt[kMaxGroups], ngroups)) return false;
   for (int j = threadIdx.x; j < P; j += blockDim.x) {
     double s = 0.0;
 #pragma unroll 8
-    for (int q = 0; q < g.ngroups; q++) s += ld_cg(&ws.gpart[(int64_t)q * P + j]);
+    for (int q = 0; q < ngroups; q++) s += ld_cg(&ws.gpart[(int64_t)q * P + j]);
     out[j] = s;
   }
   __syncthreads();
   return true;
+}
+
+// The CTA's trial and place within it, and the trial's view of a batched step.
+struct CtaCtx {
+  int trial, local, ncta, spc;
+};
+template <typename T>
+__device__ __forceinline__ StepPlan<T> make_plan(const BatchStep<T>& b, int space, CtaCtx& c) {
+  const CtaMap& m = b.map[space];
+  c.trial = m.cta_trial[blockIdx.x];
+  const int c0 = m.cta0[c.trial];
+  c.ncta = m.cta0[c.trial + 1] - c0;
+  c.local = (int)blockIdx.x - c0;
+  c.spc = m.spc[c.trial];
+  const TrialDesc& td = b.desc[c.trial];
+  const int d = b.d;
+  StepPlan<T> p = b.base;
+  p.D = td.st[d];
+  p.N = td.st[1 - d];
+  p.Bd = td.basis[d];
+  p.ldBd = td.ldb[d];
+  p.Bn = td.basis[1 - d];
+  p.ldBn = td.ldb[1 - d];
+  p.ws = td.ws;
+  p.key_next.trial = td.trial;
+  p.x = b.base.x ? b.base.x + td.off[d] : nullptr;
+  p.y = b.base.y ? b.base.y + td.off[1 - d] : nullptr;
+  return p;
 }
 
 // Rows of this thread: vectors v0 + tid + c * kThreads, c < kChunkMax, inside [v0, v1).
@@ -110,29 +145,40 @@ __device__ __forceinline__ T dot_vec(const Vec<T>& a, const Vec<T>& b, T acc) {
 }
 
 // ------------------------------------------------------------------------------------
-// First draw g_1 of a stack's space (rows >= count), its squared norm over rows > count.
+// First draw g_1 of a space (rows >= 0) into the buffer of the stack acting on that space,
+// for every trial, with its squared norm over rows > 0.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_first_draw(StackDev X, int64_t count, DrawKey key,
-                                                         T sigma, Ws ws, int set, Grid g) {
-  constexpr int N = Vec<T>::N;
+__global__ void __launch_bounds__(kThreads) k_first_draw(BatchStep<T> b, int space, DrawKey key, T sigma) {
   __shared__ double red[kWarps];
-  Rows rw(g, X.dim, N);
+  CtaCtx c;
+  const CtaMap& m = b.map[space];
+  c.trial = m.cta_trial[blockIdx.x];
+  const int c0 = m.cta0[c.trial];
+  c.ncta = m.cta0[c.trial + 1] - c0;
+  c.local = (int)blockIdx.x - c0;
+  c.spc = m.spc[c.trial];
+  const TrialDesc& td = b.desc[c.trial];
+  const StackDev X = td.st[space];
+  key.trial = td.trial;
+  const int64_t nsub = (X.dim + 31) / 32;
+  const int64_t s0 = (int64_t)c.local * c.spc, s1 = min(nsub, s0 + c.spc);
   T* gb = (T*)X.gbuf;
+  const int lane = threadIdx.x & 31, W = blockDim.x >> 5;
   T a[1] = {T(0)};
-#pragma unroll
-  for (int c = 0; c < kChunkMax; c++) {
-    if (!rw.active(c)) continue;
-    const int64_t row = rw.vec(c) * N;
-    Vec<T> v;
-    draw_vec(key, row, count, X.dim, sigma, v);
-    st_vec(gb + row, v);
-#pragma unroll
-    for (int e = 0; e < N; e++)
-      if (row + e > count) a[0] = fma(v.e[e], v.e[e], a[0]);
+  for (int64_t s = s0 + (threadIdx.x >> 5); s < s1; s += W) {
+    const int64_t r = s * 32 + lane;
+    T g = T(0), h = T(0);
+    const int64_t r2 = r & ~(int64_t)1;
+    if (!(lane & 1) && r2 < X.dim) normal_pair(key, (uint64_t)(r2 >> 1), g, h);
+    const T other = __shfl_up_sync(0xffffffffu, h, 1);
+    T v = (lane & 1) ? other : g;
+    v = (r < X.dim) ? sigma * v : T(0);
+    gb[r] = v;
+    if (r > 0) a[0] = fma(v, v, a[0]);
   }
-  block_sum_to<1>(a, red, ws.part + blockIdx.x, 1);
-  double* out = ws.scr(0);
-  if (!reduce_partials(ws, set, 1, g, out)) return;
+  block_sum_to<1>(a, red, td.ws.part + c.local, 1);
+  double* out = td.ws.scr(0);
+  if (!reduce_partials(td.ws, 0, 1, c.local, c.ncta, out)) return;
   if (threadIdx.x == 0) X.gg[0] = out[0];
 }
 
@@ -571,12 +617,14 @@ __device__ __forceinline__ T wt_draw(const DrawKey& key, int64_t row, int64_t fi
 
 // Walk of a warp over its sub-tiles: first sub-tile gw, stride GW.
 struct WarpWalk {
-  int64_t first, stride, nsub;
-  __device__ WarpWalk(int64_t dim) {
+  int64_t first, stride, nsub;   // nsub: end of the CTA's sub-tile range
+  __device__ WarpWalk(int64_t dim, const CtaCtx& c) {
     const int W = blockDim.x >> 5;
-    first = (int64_t)blockIdx.x * W + (threadIdx.x >> 5);
-    stride = (int64_t)gridDim.x * W;
-    nsub = (dim + 31) / 32;
+    const int64_t total = (dim + 31) / 32;
+    const int64_t s0 = (int64_t)c.local * c.spc;
+    first = s0 + (threadIdx.x >> 5);
+    stride = W;
+    nsub = min(total, s0 + c.spc);
   }
   __device__ __forceinline__ int64_t sub(int it) const { return first + (int64_t)it * stride; }
   __device__ __forceinline__ int count() const {
@@ -632,7 +680,9 @@ __device__ __forceinline__ void wt_pipeline(int count, int nb, Pre&& pre, Setup&
 // K1: z = V_D^T x over k_D columns (and, for Ginibre, x . the k_N data-space basis
 // columns); last CTA: w = S_D^T z.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_dots(StepPlan<T> p) {
+__global__ void __launch_bounds__(kThreads) k_dots(BatchStep<T> bs) {
+  CtaCtx cc;
+  const StepPlan<T> p = make_plan(bs, bs.d, cc);
   extern __shared__ __align__(16) unsigned char dsm_raw[];
   const int na = p.kD, nb = (p.ens == 0) ? p.kN : 0, nc = na + nb;
   const SweepCfg& cfg = p.c1;
@@ -643,8 +693,8 @@ __global__ void __launch_bounds__(kThreads) k_dots(StepPlan<T> p) {
   double acc[1][kColsPerLane];
 #pragma unroll
   for (int m = 0; m < kColsPerLane; m++) acc[0][m] = 0.0;
-  const WarpWalk ww(dim);
-  const bool xal = p.xal != 0;
+  const WarpWalk ww(dim, cc);
+  const bool xal = ((uintptr_t)p.x & 15u) == 0;   // per-trial offsets may break alignment
   wt_pipeline(ww.count(), cfg.nbuf,
       [&](int it, int b) { wt_load_cols(sm.stage(warp, b), src, nc, ww.sub(it) * 32); },
       [&]() {},
@@ -654,8 +704,8 @@ __global__ void __launch_bounds__(kThreads) k_dots(StepPlan<T> p) {
         wt_cols<T, 1>(st, nc, sm.srow(st, 0), nullptr, acc);
       });
   const int off[1] = {0};
-  wt_store_cols<1>(sm.comb, nc, acc, p.ws.part + (int64_t)blockIdx.x * nc, off);
-  if (!reduce_partials(p.ws, 0, nc, cfg.g, p.ws.z)) return;
+  wt_store_cols<1>(sm.comb, nc, acc, p.ws.part + (int64_t)cc.local * nc, off);
+  if (!reduce_partials(p.ws, 0, nc, cc.local, cc.ncta, p.ws.z)) return;
   __shared__ double zs[kTmaxLimit];
   for (int i = threadIdx.x; i < na; i += blockDim.x) zs[i] = p.ws.z[i];
   __syncthreads();
@@ -672,7 +722,9 @@ __global__ void __launch_bounds__(kThreads) k_dots(StepPlan<T> p) {
 // K2: p = Delta_D (x - V_D w); writes p[k:] as the new column k of V_D; draws g_{t+1}
 // (rows > k) into the data stack's buffer; exact V_D^T p[k:] and V_D^T g_{t+1}.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_update(StepPlan<T> p) {
+__global__ void __launch_bounds__(kThreads) k_update(BatchStep<T> bs) {
+  CtaCtx cc;
+  const StepPlan<T> p = make_plan(bs, bs.d, cc);
   extern __shared__ __align__(16) unsigned char dsm_raw[];
   __shared__ double red[kWarps * 4];
   const int k = p.kD;
@@ -690,8 +742,8 @@ __global__ void __launch_bounds__(kThreads) k_update(StepPlan<T> p) {
   T ex[3] = {T(0), T(0), T(0)};   // p . g_next, ||p[k+1:]||^2, ||g_next[k+2:]||^2
   T* pv = sm.scr(warp, 0);
   T* gv = sm.scr(warp, 1);
-  const WarpWalk ww(dim);
-  const bool xal = p.xal != 0;
+  const WarpWalk ww(dim, cc);
+  const bool xal = ((uintptr_t)p.x & 15u) == 0;   // per-trial offsets may break alignment
   wt_pipeline(ww.count(), cfg.nbuf,
       [&](int it, int b) {
         T* st = sm.stage(warp, b);
@@ -729,12 +781,12 @@ __global__ void __launch_bounds__(kThreads) k_update(StepPlan<T> p) {
         wt_cols<T, 2>(st, k, pv, gv, acc);
       });
   const int P = 2 * k + 3;
-  double* part = p.ws.part + (int64_t)blockIdx.x * P;
+  double* part = p.ws.part + (int64_t)cc.local * P;
   const int off[2] = {k + 3, 0};   // p-dots after the three extras, draw dots first
   wt_store_cols<2>(sm.comb, k, acc, part, off);
   block_sum_to<3>(ex, red, part + k, 3);
   double* rr = p.ws.scr(3);
-  if (!reduce_partials(p.ws, 1, P, cfg.g, rr)) return;
+  if (!reduce_partials(p.ws, 1, P, cc.local, cc.ncta, rr)) return;
   fin_update<T>(p, rr);
 }
 
@@ -742,7 +794,9 @@ __global__ void __launch_bounds__(kThreads) k_update(StepPlan<T> p) {
 // reflector column (g_t[k:] with the pivot entry replaced); the next draw (read from the
 // data stack's buffer) replaces g_t in this stack's buffer; dots of it with V_N.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_out_haar(StepPlan<T> p) {
+__global__ void __launch_bounds__(kThreads) k_out_haar(BatchStep<T> bs) {
+  CtaCtx cc;
+  const StepPlan<T> p = make_plan(bs, 1 - bs.d, cc);
   extern __shared__ __align__(16) unsigned char dsm_raw[];
   __shared__ double red[kWarps * 4];
   const int k = p.kN;
@@ -760,7 +814,7 @@ __global__ void __launch_bounds__(kThreads) k_out_haar(StepPlan<T> p) {
 #pragma unroll
   for (int m = 0; m < kColsPerLane; m++) acc[0][m] = 0.0;
   T ex[1] = {T(0)};
-  const WarpWalk ww(dim);
+  const WarpWalk ww(dim, cc);
   const int64_t ld = p.N.ld;
   wt_pipeline(ww.count(), cfg.nbuf,
       [&](int it, int b) {
@@ -801,12 +855,12 @@ __global__ void __launch_bounds__(kThreads) k_out_haar(StepPlan<T> p) {
         wt_cols<T, 1>(st, k, sm.srow(st, 1), nullptr, acc);
       });
   const int P = k + 1;
-  double* part = p.ws.part + (int64_t)blockIdx.x * P;
+  double* part = p.ws.part + (int64_t)cc.local * P;
   const int off[1] = {0};
   wt_store_cols<1>(sm.comb, k, acc, part, off);
   block_sum_to<1>(ex, red, part + k, 1);
   double* rr = p.ws.scr(3);
-  if (!reduce_partials(p.ws, 2, P, cfg.g, rr)) return;
+  if (!reduce_partials(p.ws, 2, P, cc.local, cc.ncta, rr)) return;
   for (int j = threadIdx.x; j <= k; j += blockDim.x) p.N.gdot[j] = rr[j];
   if (threadIdx.x == 0) p.N.gg[0] = p.D.gg[0];
 }
@@ -815,7 +869,9 @@ __global__ void __launch_bounds__(kThreads) k_out_haar(StepPlan<T> p) {
 // - V_N w_h + B_n c; u becomes the new basis column; the next draw (rows >= k_N) replaces g
 // in this stack's buffer, with its dots with V_N.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_out_gin(StepPlan<T> p) {
+__global__ void __launch_bounds__(kThreads) k_out_gin(BatchStep<T> bs) {
+  CtaCtx cc;
+  const StepPlan<T> p = make_plan(bs, 1 - bs.d, cc);
   extern __shared__ __align__(16) unsigned char dsm_raw[];
   const int kN = p.kN, kD = p.kD, nc = kN + kD;
   const SweepCfg& cfg = p.c3;
@@ -831,7 +887,7 @@ __global__ void __launch_bounds__(kThreads) k_out_gin(StepPlan<T> p) {
 #pragma unroll
   for (int m = 0; m < kColsPerLane; m++) acc[0][m] = 0.0;
   T* gv = sm.scr(warp, 0);
-  const WarpWalk ww(dim);
+  const WarpWalk ww(dim, cc);
   const int64_t ld = p.N.ld;
   wt_pipeline(ww.count(), cfg.nbuf,
       [&](int it, int b) {
@@ -878,29 +934,28 @@ __global__ void __launch_bounds__(kThreads) k_out_gin(StepPlan<T> p) {
       });
   if (kN == 0) return;   // no dots to form
   const int P = kN;
-  double* part = p.ws.part + (int64_t)blockIdx.x * P;
+  double* part = p.ws.part + (int64_t)cc.local * P;
   const int off[1] = {0};
   wt_store_cols<1>(sm.comb, kN, acc, part, off);
   double* rr = p.ws.scr(3);
-  if (!reduce_partials(p.ws, 2, P, cfg.g, rr)) return;
+  if (!reduce_partials(p.ws, 2, P, cc.local, cc.ncta, rr)) return;
   for (int j = threadIdx.x; j < kN; j += blockDim.x) p.N.gdot[j] = rr[j];
 }
 
 // ------------------------------------------------------------------------------------
 template <typename T>
-cudaError_t launch_first_draw(StackDev X, int64_t count, DrawKey key, T sigma, Ws ws, int set,
-                              Grid g, cudaStream_t s) {
-  k_first_draw<T><<<g.ctas, kThreads, 0, s>>>(X, count, key, sigma, ws, set, g);
+cudaError_t launch_first_draw(const BatchStep<T>& b, int space, DrawKey key, T sigma, cudaStream_t s) {
+  k_first_draw<T><<<b.map[space].ctas, kThreads, 0, s>>>(b, space, key, sigma);
   return cudaGetLastError();
 }
 
 // Launch with programmatic stream serialisation (the kernel may start while its predecessor
 // drains; it synchronises through griddepcontrol.wait) when pdl is set.
 template <typename T>
-cudaError_t launch_sweep(void (*kern)(StepPlan<T>), const SweepCfg& c, size_t smem, cudaStream_t s,
-                         bool pdl, const StepPlan<T>& p) {
+cudaError_t launch_sweep(void (*kern)(BatchStep<T>), const SweepCfg& c, int ctas, size_t smem,
+                         cudaStream_t s, bool pdl, const BatchStep<T>& b) {
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)c.g.ctas);
+  cfg.gridDim = dim3((unsigned)ctas);
   cfg.blockDim = dim3((unsigned)(32 * c.W));
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
@@ -909,37 +964,41 @@ cudaError_t launch_sweep(void (*kern)(StepPlan<T>), const SweepCfg& c, size_t sm
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = pdl ? attr : nullptr;
   cfg.numAttrs = pdl ? 1 : 0;
-  return cudaLaunchKernelEx(&cfg, kern, p);
+  return cudaLaunchKernelEx(&cfg, kern, b);
 }
 
 template <typename T>
-cudaError_t launch_step(const StepPlan<T>& p, cudaStream_t s, cudaEvent_t* ev, int* launched) {
+cudaError_t launch_step(const BatchStep<T>& b, cudaStream_t s, cudaEvent_t* ev, int* launched) {
   auto rec = [&](int i) {
     // External: inside a stream capture this becomes an event-record node of the graph
     if (ev && ev[i]) cudaEventRecordWithFlags(ev[i], s, cudaEventRecordExternal);
   };
+  const StepPlan<T>& p = b.base;
   const bool pdl = p.pdl != 0;
+  const int dspace = b.d, ospace = 1 - b.d;
   cudaError_t e = cudaSuccess;
   const int nc1 = p.kD + ((p.ens == 0) ? p.kN : 0);
   if (nc1 > 0) {
     rec(0);
-    e = launch_sweep<T>(k_dots<T>, p.c1, sweep_smem_bytes<T>(p.c1.W, p.c1.nbuf, nc1, 1, nc1, 1), s, pdl, p);
+    e = launch_sweep<T>(k_dots<T>, p.c1, b.map[dspace].ctas,
+                        sweep_smem_bytes<T>(p.c1.W, p.c1.nbuf, nc1, 1, nc1, 1), s, pdl, b);
     if (e != cudaSuccess) return e;
     rec(1);
     if (launched) launched[0] = 1;
   }
   rec(2);
-  e = launch_sweep<T>(k_update<T>, p.c2, sweep_smem_bytes<T>(p.c2.W, p.c2.nbuf, p.kD, 1, p.kD, 2), s, pdl, p);
+  e = launch_sweep<T>(k_update<T>, p.c2, b.map[dspace].ctas,
+                      sweep_smem_bytes<T>(p.c2.W, p.c2.nbuf, p.kD, 1, p.kD, 2), s, pdl, b);
   if (e != cudaSuccess) return e;
   rec(3);
   if (launched) launched[1] = 1;
   rec(4);
   if (p.ens == 1)
-    e = launch_sweep<T>(k_out_haar<T>, p.c3, sweep_smem_bytes<T>(p.c3.W, p.c3.nbuf, p.kN, 2, p.kN, 1), s,
-                        pdl, p);
+    e = launch_sweep<T>(k_out_haar<T>, p.c3, b.map[ospace].ctas,
+                        sweep_smem_bytes<T>(p.c3.W, p.c3.nbuf, p.kN, 2, p.kN, 1), s, pdl, b);
   else
-    e = launch_sweep<T>(k_out_gin<T>, p.c3,
-                        sweep_smem_bytes<T>(p.c3.W, p.c3.nbuf, p.kN + p.kD, 1, p.kN, 1), s, pdl, p);
+    e = launch_sweep<T>(k_out_gin<T>, p.c3, b.map[ospace].ctas,
+                        sweep_smem_bytes<T>(p.c3.W, p.c3.nbuf, p.kN + p.kD, 1, p.kN, 1), s, pdl, b);
   if (e != cudaSuccess) return e;
   rec(5);
   if (launched) launched[2] = 1;
@@ -996,10 +1055,10 @@ int kernel_occupancy(int which, size_t dynsmem) {
 template int kernel_occupancy<float>(int, size_t);
 template int kernel_occupancy<double>(int, size_t);
 
-template cudaError_t launch_first_draw<float>(StackDev, int64_t, DrawKey, float, Ws, int, Grid, cudaStream_t);
-template cudaError_t launch_first_draw<double>(StackDev, int64_t, DrawKey, double, Ws, int, Grid, cudaStream_t);
-template cudaError_t launch_step<float>(const StepPlan<float>&, cudaStream_t, cudaEvent_t*, int*);
-template cudaError_t launch_step<double>(const StepPlan<double>&, cudaStream_t, cudaEvent_t*, int*);
+template cudaError_t launch_first_draw<float>(const BatchStep<float>&, int, DrawKey, float, cudaStream_t);
+template cudaError_t launch_first_draw<double>(const BatchStep<double>&, int, DrawKey, double, cudaStream_t);
+template cudaError_t launch_step<float>(const BatchStep<float>&, cudaStream_t, cudaEvent_t*, int*);
+template cudaError_t launch_step<double>(const BatchStep<double>&, cudaStream_t, cudaEvent_t*, int*);
 
 // ------------------------------------------------------------------------------------
 // Consistency probe (not on the hot path): y = Q^(t) x from the revealed part only.
@@ -1008,7 +1067,22 @@ template cudaError_t launch_step<double>(const StepPlan<double>&, cudaStream_t, 
 //   Haar:    y = B_N [q[:t]; 0]              (eq. H_t: the hidden block never sees q[:t])
 //   Ginibre: y = B_N [h; 0] + B_n q[:k_D]    (h = x . data-space basis), eq. Gaussian_t.
 template <typename T>
-__global__ void k_probe_q(StepPlan<T> p, double* q, double* unrev) {
+__device__ __forceinline__ StepPlan<T> trial0_plan(const BatchStep<T>& b) {
+  const TrialDesc& td = b.desc[0];
+  StepPlan<T> p = b.base;
+  p.D = td.st[b.d];
+  p.N = td.st[1 - b.d];
+  p.Bd = td.basis[b.d];
+  p.ldBd = td.ldb[b.d];
+  p.Bn = td.basis[1 - b.d];
+  p.ldBn = td.ldb[1 - b.d];
+  p.ws = td.ws;
+  return p;
+}
+
+template <typename T>
+__global__ void k_probe_q(BatchStep<T> b, double* q, double* unrev) {
+  const StepPlan<T> p = trial0_plan(b);
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int k = p.kD;
   double u2 = 0.0;
@@ -1025,7 +1099,8 @@ __global__ void k_probe_q(StepPlan<T> p, double* q, double* unrev) {
 }
 
 template <typename T>
-__global__ void k_probe_coef(StepPlan<T> p, const double* q) {
+__global__ void k_probe_coef(BatchStep<T> b, const double* q) {
+  const StepPlan<T> p = trial0_plan(b);
   // one CTA: zt = V_N[top]^T Delta_N c_top, w' = S_N zt  (c_top = q[:t] for Haar, h for Ginibre)
   const int kN = p.kN, Tm = p.Tm;
   const T* VN = (const T*)p.N.V;
@@ -1045,7 +1120,8 @@ __global__ void k_probe_coef(StepPlan<T> p, const double* q) {
 }
 
 template <typename T>
-__global__ void k_probe_out(StepPlan<T> p, const double* q) {
+__global__ void k_probe_out(BatchStep<T> b, const double* q) {
+  const StepPlan<T> p = trial0_plan(b);
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= p.N.dim) return;
   const int kN = p.kN;
@@ -1062,18 +1138,23 @@ __global__ void k_probe_out(StepPlan<T> p, const double* q) {
 }
 
 template <typename T>
-cudaError_t launch_probe(const StepPlan<T>& p, double* q, double* unrev, cudaStream_t s) {
+cudaError_t launch_probe(const BatchStep<T>& b, double* q, double* unrev, cudaStream_t s) {
+  const StepPlan<T>& p = b.base;
   const int nc1 = p.kD + ((p.ens == 0) ? p.kN : 0);
+  cudaError_t e = cudaSuccess;
   if (nc1 > 0)
-    k_dots<T><<<p.c1.g.ctas, 32 * p.c1.W, sweep_smem_bytes<T>(p.c1.W, p.c1.nbuf, nc1, 1, nc1, 1), s>>>(p);
+    e = launch_sweep<T>(k_dots<T>, p.c1, b.map[b.d].ctas,
+                        sweep_smem_bytes<T>(p.c1.W, p.c1.nbuf, nc1, 1, nc1, 1), s, false, b);
+  if (e != cudaSuccess) return e;
   const int thr = 256;
-  k_probe_q<T><<<(unsigned)((p.D.dim + thr - 1) / thr), thr, 0, s>>>(p, q, unrev);
-  k_probe_coef<T><<<1, thr, 0, s>>>(p, q);
-  k_probe_out<T><<<(unsigned)((p.N.dim + thr - 1) / thr), thr, 0, s>>>(p, q);
+  const int64_t dD = b.map[b.d].ctas > 0 ? p.D.dim : 0, dN = p.N.dim;
+  k_probe_q<T><<<(unsigned)((dD + thr - 1) / thr), thr, 0, s>>>(b, q, unrev);
+  k_probe_coef<T><<<1, thr, 0, s>>>(b, q);
+  k_probe_out<T><<<(unsigned)((dN + thr - 1) / thr), thr, 0, s>>>(b, q);
   return cudaGetLastError();
 }
-template cudaError_t launch_probe<float>(const StepPlan<float>&, double*, double*, cudaStream_t);
-template cudaError_t launch_probe<double>(const StepPlan<double>&, double*, double*, cudaStream_t);
+template cudaError_t launch_probe<float>(const BatchStep<float>&, double*, double*, cudaStream_t);
+template cudaError_t launch_probe<double>(const BatchStep<double>&, double*, double*, cudaStream_t);
 
 // ------------------------------------------------------------------------------------
 // Generator checks.

@@ -99,9 +99,7 @@ struct StepPlan {
   void* Bn;             // Ginibre: basis columns living in the other space (kD + 1 after)
   int64_t ldBn;
   const T* x;
-  int xal;
   T* y;
-  int yal;
   Ws ws;
   DrawKey key_next;     // the next step's draw (t + 1)
   T sigma;              // entry scale of the draws (Ginibre), 1 for Haar
@@ -109,16 +107,46 @@ struct StepPlan {
   int pdl;              // launch with programmatic dependent launch
 };
 
+// ------------------------------------------------------------------------------------
+// Batches.  A state holds `count` independent trials (one for the single-trial API); every
+// trial has its own stacks, basis stores and workspace, packed in shared allocations.  A
+// launch covers all trials: the CTA map of a space (0: the n-dimensional space of R, 1: the
+// m-dimensional space of L) gives each CTA its trial and a contiguous range of 32-row
+// sub-tiles; elections and finalisations are per trial.
+struct TrialDesc {
+  StackDev st[2];
+  void* basis[2];
+  int64_t ldb[2];
+  Ws ws;
+  uint32_t trial;       // Philox trial word
+  int64_t off[2];       // offset of the trial's vector in packed n-space / m-space buffers
+};
+
+struct CtaMap {
+  const int* cta_trial; // [ctas]: trial of each CTA
+  const int* cta0;      // [count + 1]: first CTA of each trial
+  const int* spc;       // [count]: sub-tiles per CTA of each trial
+  int ctas;             // CTAs of a launch over this space
+};
+
 template <typename T>
-cudaError_t launch_first_draw(StackDev X, int64_t count, DrawKey key, T sigma, Ws ws,
-                              int cnt_set, Grid g, cudaStream_t s);
+struct BatchStep {
+  StepPlan<T> base;     // fields shared by all trials (pointers filled per trial)
+  int d;                // data-side stack index (0 for M_t = Q, 1 for Q^T)
+  const TrialDesc* desc;
+  CtaMap map[2];
+};
+
+template <typename T>
+cudaError_t launch_first_draw(const BatchStep<T>& b, int space, DrawKey key, T sigma,
+                              cudaStream_t s);
 // ev (optional): start/stop event pairs recorded around K1, K2, K3 (ev[2*kind], ev[2*kind+1]);
 // a null entry skips the record.  launched[kind] is set to 1 for each sweep launched.
 template <typename T>
-cudaError_t launch_step(const StepPlan<T>& p, cudaStream_t s, cudaEvent_t* ev = nullptr,
+cudaError_t launch_step(const BatchStep<T>& b, cudaStream_t s, cudaEvent_t* ev = nullptr,
                         int* launched = nullptr);
 template <typename T>
-cudaError_t launch_probe(const StepPlan<T>& p, double* q, double* unrevealed, cudaStream_t s);
+cudaError_t launch_probe(const BatchStep<T>& b, double* q, double* unrevealed, cudaStream_t s);
 
 template <typename T>
 int kernel_occupancy(int which, size_t dynsmem);

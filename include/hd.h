@@ -191,6 +191,38 @@ HD_API int hd_philox_normals(uint64_t seed, uint32_t trial, uint32_t step, uint3
 HD_API int hd_philox_words(uint64_t seed, const uint32_t* counters, int64_t nblocks,
                            uint32_t* out, void* stream);
 
+/* Allocation-free first product of a fresh matrix.  The paper has no counterpart of this
+ * entry point: it is a library convenience for callers that must not allocate device
+ * memory, such as code whose framework already holds the device memory in its own pool
+ * (a cudaMalloc outside that pool can fail or fragment it) or code on a latency-critical
+ * stream (cudaMalloc / cudaFree may synchronise the whole device).
+ *
+ * Computes y = Q x (transpose == 0: x has n entries, y has m) or y = Q^T x (transpose != 0:
+ * x has m, y has n) for the matrix that hd_create(ensemble, m, n, T_max, seed, dtype) with
+ * options (sigma, trial) would sample, at its step 1: the result equals that state's first
+ * hd_apply up to rounding.  By Algorithm 2's first step y = ||x|| g / ||g|| for Haar(n), and
+ * by Algorithm 1's first step y = ||x|| g for Gin(m, n), g the step-1 Philox draw (entry
+ * scale sigma for Gin; sigma is ignored for Haar).  x and y are device buffers of dtype on
+ * the calling thread's current device, not overlapping; work is enqueued on `stream`
+ * (NULL = the legacy default stream).
+ *
+ * Scratch: one file-scope device array of 66,048 bytes per device holds the per-tile partial
+ * sums, a tile counter and the coefficient, which bounds max(m, n) at 16,777,216 entries.
+ * The counter must be zero when the norm kernel starts: every call clears it on `stream`
+ * first.  Calls that overlap on one device (on different streams, or from different host
+ * threads without ordering) share that array and race on it, giving wrong results: order
+ * them on one stream.  The first call on a device does set-up (it looks up the array's
+ * device address, which can load the library's device code); a caller that captures the
+ * call into a CUDA graph should make one call before beginning the capture.  The call
+ * allocates no device or host memory.
+ *
+ * Errors: HD_ERR_ARG (bad ensemble or dtype, NULL x or y, m or n <= 0, Gin sigma not finite
+ * and positive), HD_ERR_DIM (Haar with m != n; max(m, n) above 16,777,216, with the limit in
+ * hd_last_error), HD_ERR_CUDA (set-up or launch failure, text in hd_last_error). */
+HD_API int hd_first_product_noalloc(int ensemble, int dtype, int64_t m, int64_t n, int transpose,
+                                    uint64_t seed, uint32_t trial, double sigma, const void* x,
+                                    void* y, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

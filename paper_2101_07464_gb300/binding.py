@@ -37,6 +37,8 @@ _PROTOS = {
     "hd_create_batched": (_c.c_int, [_c.c_int, _c.c_int32, _P, _P, _c.c_int32, _c.c_uint64, _c.c_int,
                                      _c.POINTER(_P)]),
     "hd_get_batch_layout": (_c.c_int, [_P, _c.POINTER(_c.c_int32), _P, _P]),
+    "hd_first_product_noalloc": (_c.c_int, [_c.c_int, _c.c_int, _c.c_int64, _c.c_int64, _c.c_int,
+                                            _c.c_uint64, _c.c_uint32, _c.c_double, _P, _P, _P]),
     "hd_apply": (_c.c_int, [_P, _P, _c.c_int, _P]),
     "hd_probe": (_c.c_int, [_P, _P, _c.c_int, _P, _c.POINTER(_c.c_double)]),
     "hd_reset": (_c.c_int, [_P, _c.c_uint64]),
@@ -152,6 +154,18 @@ def hd_get_batch_layout(state):
     _check(lib().hd_get_batch_layout(state, ctypes.byref(c), on.ctypes.data, om.ctypes.data),
            "hd_get_batch_layout")
     return on, om
+
+
+def hd_first_product_noalloc(ensemble, dtype, m, n, transpose, seed, trial, sigma, x, y,
+                             stream=None):
+    """y = Q x (or Q^T x) for a fresh matrix, as a new state's step 1; allocates nothing.
+    x and y are preallocated CUDA tensors (or raw device addresses) of the dtype."""
+    dt = DTYPES.get(dtype, dtype)
+    nx, ny = (m, n) if transpose else (n, m)
+    _check(lib().hd_first_product_noalloc(ENSEMBLES.get(ensemble, ensemble), dt, m, n,
+                                          1 if transpose else 0, seed & 0xFFFFFFFFFFFFFFFF, trial,
+                                          float(sigma), _ptr(x, dt, nx, "x"), _ptr(y, dt, ny, "y"),
+                                          _stream_ptr(stream)), "hd_first_product_noalloc")
 
 
 def hd_set_options(state, sigma=1.0, trial=0, stream=None):

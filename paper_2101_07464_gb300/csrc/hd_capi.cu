@@ -527,6 +527,11 @@ int upload_trials(hd_state* st) {
 
 }  // namespace
 
+namespace hd {
+// Lets other translation units of the library set hd_last_error's text.
+void record_error_text(const char* msg) { snprintf(g_last_error, sizeof(g_last_error), "%s", msg); }
+}  // namespace hd
+
 extern "C" {
 
 HD_API const char* hd_last_error(void) { return g_last_error; }

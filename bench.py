@@ -163,6 +163,11 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# DRAM bytes / algorithmic bytes of one k_update launch (k = 60, n = 10^6, FP32) from an
+# ncu --set full capture of the current kernel; reset to None when the kernel changes.
+UPDATE_TRAFFIC_RATIO = 254.366 / 252.0
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -284,7 +289,11 @@ def run_ours(args):
     roofline = {"bound": "hbm", "kernel": {"dots": "k_dots", "update": "k_update",
                                             "output": "k_out_haar"}[dom],
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "peak_source": peak_kind, "traffic": None,
+                "peak_source": peak_kind,
+                "traffic": (by / nl) * UPDATE_TRAFFIC_RATIO if (nl and dom == "update") else None,
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_update "
+                                  "launch at k = 60 (254.37 MB for 252.0 MB algorithmic), scaled to "
+                                  "the average launch by algorithmic bytes",
                 "timing": "CUDA events on the launching stream around every sweep, recorded "
                           "in a second pass of the same trajectories (events inside the graph "
                           "would perturb the headline timing)",

@@ -139,7 +139,8 @@ SweepCfg make_sweep(const hd_state* st, int which, int ncolT, int NRV, int ncolC
       const size_t b = sweep_smem_bytes<T>(W, nb, ncolT, NRV, ncolC, NR);
       if ((int)b > blk) continue;
       const int by_regs = std::max(1, st->occ_regs[which] * 8 / W);
-      const int ctas = std::min(by_regs, (int)(st->smem_sm / (b + stat)));
+      // the CTA maps give each SM at most kSweepCtasPerSm CTAs
+      const int ctas = std::min(std::min(by_regs, (int)(st->smem_sm / (b + stat))), kSweepCtasPerSm);
       if (ctas < 1) continue;
       const int warps = std::min(64, ctas * W);
       const double inflight = std::min(warps * nb * stage, 131072.0);
@@ -303,7 +304,7 @@ bool graph_matches(const hd_state* st, const hd_run_spec* sp) {
 }
 
 // CTA map of one space: every trial gets ceil(nsub_i / spc) CTAs of spc 32-row sub-tiles,
-// spc chosen so that a single large trial fills about two CTAs per SM.
+// spc chosen so that a single large trial fills kSweepCtasPerSm CTAs per SM (one wave).
 bool build_map(hd_state* st, int s) {
   const int count = st->count;
   std::vector<int64_t> nsub(count);
@@ -312,7 +313,8 @@ bool build_map(hd_state* st, int s) {
     nsub[i] = (st->dims[s][i] + 31) / 32;
     total += nsub[i];
   }
-  const int64_t spc = std::max<int64_t>(16, (total + 2 * st->nsm - 1) / (2 * st->nsm));
+  const int64_t per = (int64_t)kSweepCtasPerSm * st->nsm;
+  const int64_t spc = std::max<int64_t>(16, (total + per - 1) / per);
   std::vector<int> cta0(count + 1), spcv(count);
   std::vector<int> ct;
   cta0[0] = 0;

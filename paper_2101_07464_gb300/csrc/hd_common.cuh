@@ -8,6 +8,9 @@ namespace hd {
 constexpr int kThreads = 256;          // threads per CTA of every streaming kernel
 constexpr int kWarps = kThreads / 32;
 constexpr int kChunkMax = 4;           // 16-byte vectors per thread per sweep (registers)
+// Resident CTAs per SM that every sweep kernel is compiled for (registers capped to fit) and
+// that the CTA maps are sized to: one wave of kSweepCtasPerSm CTAs of up to 8 warps per SM.
+constexpr int kSweepCtasPerSm = 2;
 constexpr int kColBlock = 8;           // stack columns per register block in a sweep
 constexpr int kFinThreads = 256;       // threads of the single-CTA finalisation
 constexpr int kTmaxLimit = 256;        // column owners hold at most 8 columns per lane

@@ -680,7 +680,7 @@ __device__ __forceinline__ void wt_pipeline(int count, int nb, Pre&& pre, Setup&
 // K1: z = V_D^T x over k_D columns (and, for Ginibre, x . the k_N data-space basis
 // columns); last CTA: w = S_D^T z.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_dots(BatchStep<T> bs) {
+__global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_dots(BatchStep<T> bs) {
   CtaCtx cc;
   const StepPlan<T> p = make_plan(bs, bs.d, cc);
   extern __shared__ __align__(16) unsigned char dsm_raw[];
@@ -722,7 +722,7 @@ __global__ void __launch_bounds__(kThreads) k_dots(BatchStep<T> bs) {
 // K2: p = Delta_D (x - V_D w); writes p[k:] as the new column k of V_D; draws g_{t+1}
 // (rows > k) into the data stack's buffer; exact V_D^T p[k:] and V_D^T g_{t+1}.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_update(BatchStep<T> bs) {
+__global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_update(BatchStep<T> bs) {
   CtaCtx cc;
   const StepPlan<T> p = make_plan(bs, bs.d, cc);
   extern __shared__ __align__(16) unsigned char dsm_raw[];
@@ -794,7 +794,7 @@ __global__ void __launch_bounds__(kThreads) k_update(BatchStep<T> bs) {
 // reflector column (g_t[k:] with the pivot entry replaced); the next draw (read from the
 // data stack's buffer) replaces g_t in this stack's buffer; dots of it with V_N.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_out_haar(BatchStep<T> bs) {
+__global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_out_haar(BatchStep<T> bs) {
   CtaCtx cc;
   const StepPlan<T> p = make_plan(bs, 1 - bs.d, cc);
   extern __shared__ __align__(16) unsigned char dsm_raw[];
@@ -869,7 +869,7 @@ __global__ void __launch_bounds__(kThreads) k_out_haar(BatchStep<T> bs) {
 // - V_N w_h + B_n c; u becomes the new basis column; the next draw (rows >= k_N) replaces g
 // in this stack's buffer, with its dots with V_N.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_out_gin(BatchStep<T> bs) {
+__global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_out_gin(BatchStep<T> bs) {
   CtaCtx cc;
   const StepPlan<T> p = make_plan(bs, 1 - bs.d, cc);
   extern __shared__ __align__(16) unsigned char dsm_raw[];

@@ -191,6 +191,45 @@ HD_API int hd_philox_normals(uint64_t seed, uint32_t trial, uint32_t step, uint3
 HD_API int hd_philox_words(uint64_t seed, const uint32_t* counters, int64_t nblocks,
                            uint32_t* out, void* stream);
 
+/* ---- Reverse mode (adjoint) ---------------------------------------------------------
+ * With the Gaussian draws held fixed, y_1..y_T of Algorithms 1 and 2 are a deterministic,
+ * almost everywhere differentiable function of the step inputs x_1..x_T.  y_t depends on x_t
+ * directly and on earlier inputs through the data-side reflectors they built (R_s = H_s(p_s),
+ * eq. Householder_e) and, for Gin, through the basis vectors built with them (Alg. 1).  The
+ * paper has no gradients; this is the pathwise derivative of the sampler, so it is an
+ * unbiased estimator of the derivative of an expectation, not the derivative for a fixed
+ * dense Q.  The sign choices of the reflectors are piecewise constant and pass no
+ * derivative; an identity reflector (zero tail) passes none either.  Single-trial states only.
+ *
+ * hd_adjoint_enable(st, flags): call on a fresh or just-reset state (no step taken).  From
+ * then on every forward step is recorded; with HD_ADJ_RECORD_X the library also keeps a copy
+ * of each x_t (T_max vectors of the longer dimension, state dtype), otherwise the caller
+ * passes x_t back to hd_adjoint_step (recomputing them, e.g. from checkpoints with hd_probe).
+ * Allocates the accumulators once: per stack dim x T_max FP64 (dV) and T_max^2 FP64 (dS), per
+ * Gin basis store dim x T_max FP64, plus 7 FP64 work vectors.  hd_run on a recording state
+ * runs without its CUDA graph.  Errors: HD_ERR_ARG (batched state, unknown flag),
+ * HD_ERR_STATE (steps already taken), HD_ERR_OOM, HD_ERR_CUDA. */
+#define HD_ADJ_RECORD_X 1
+HD_API int hd_adjoint_enable(hd_state* st, int flags);
+
+/* Reverse the latest forward step not yet reversed (step t, counting down from the last).
+ * ybar: dLoss/dy_t, a device buffer of y_t's length (state dtype).  x_t: the step's input
+ * (device, x_t's length) or NULL to use the recorded copy.  xbar (device, x_t's length)
+ * receives dLoss/dx_t through y_t and through every later product that used a reflector or
+ * basis vector built from x_t (their contributions were accumulated when those later steps
+ * were reversed).  It does not include the caller's own f_t: the caller adds
+ * d x_{t+1} / d x_t terms itself.  Enqueued on the state's stream.  Once a reverse pass has
+ * started, hd_apply returns HD_ERR_STATE until hd_reset or hd_adjoint_restart.
+ * Errors: HD_ERR_STATE (not enabled, or every step reversed), HD_ERR_ARG, HD_ERR_CUDA. */
+HD_API int hd_adjoint_step(hd_state* st, const void* ybar, const void* x_t, void* xbar);
+
+/* Zero the accumulators and set the reverse pass back to the last forward step, so that
+ * another loss can be differentiated through the same forward trajectory. */
+HD_API int hd_adjoint_restart(hd_state* st);
+
+/* Number of forward steps not yet reversed. */
+HD_API int hd_adjoint_position(const hd_state* st, int32_t* remaining);
+
 /* Allocation-free first product of a fresh matrix.  The paper has no counterpart of this
  * entry point: it is a library convenience for callers that must not allocate device
  * memory, such as code whose framework already holds the device memory in its own pool

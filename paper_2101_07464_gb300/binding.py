@@ -37,6 +37,10 @@ _PROTOS = {
     "hd_create_batched": (_c.c_int, [_c.c_int, _c.c_int32, _P, _P, _c.c_int32, _c.c_uint64, _c.c_int,
                                      _c.POINTER(_P)]),
     "hd_get_batch_layout": (_c.c_int, [_P, _c.POINTER(_c.c_int32), _P, _P]),
+    "hd_adjoint_enable": (_c.c_int, [_P, _c.c_int]),
+    "hd_adjoint_step": (_c.c_int, [_P, _P, _P, _P]),
+    "hd_adjoint_restart": (_c.c_int, [_P]),
+    "hd_adjoint_position": (_c.c_int, [_P, _c.POINTER(_c.c_int32)]),
     "hd_first_product_noalloc": (_c.c_int, [_c.c_int, _c.c_int, _c.c_int64, _c.c_int64, _c.c_int,
                                             _c.c_uint64, _c.c_uint32, _c.c_double, _P, _P, _P]),
     "hd_apply": (_c.c_int, [_P, _P, _c.c_int, _P]),
@@ -166,6 +170,29 @@ def hd_first_product_noalloc(ensemble, dtype, m, n, transpose, seed, trial, sigm
                                           1 if transpose else 0, seed & 0xFFFFFFFFFFFFFFFF, trial,
                                           float(sigma), _ptr(x, dt, nx, "x"), _ptr(y, dt, ny, "y"),
                                           _stream_ptr(stream)), "hd_first_product_noalloc")
+
+
+HD_ADJ_RECORD_X = 1
+
+
+def hd_adjoint_enable(state, record_x=True):
+    _check(lib().hd_adjoint_enable(state, HD_ADJ_RECORD_X if record_x else 0), "hd_adjoint_enable")
+
+
+def hd_adjoint_step(state, ybar, x_t, xbar):
+    """ybar, xbar: CUDA tensors (or addresses); x_t: CUDA tensor, address or None (recorded)."""
+    _check(lib().hd_adjoint_step(state, _ptr(ybar, what="ybar"), None if x_t is None else _ptr(x_t, what="x_t"),
+                                 _ptr(xbar, what="xbar")), "hd_adjoint_step")
+
+
+def hd_adjoint_restart(state):
+    _check(lib().hd_adjoint_restart(state), "hd_adjoint_restart")
+
+
+def hd_adjoint_position(state):
+    v = ctypes.c_int32()
+    _check(lib().hd_adjoint_position(state, ctypes.byref(v)), "hd_adjoint_position")
+    return v.value
 
 
 def hd_set_options(state, sigma=1.0, trial=0, stream=None):
@@ -311,6 +338,7 @@ class HD:
     def __init__(self, ensemble, m, n, T_max, seed, dtype="f64", sigma=1.0, trial=0, stream=None):
         import torch
         self.ensemble, self.m, self.n, self.T_max = ensemble, m, n, T_max
+        self.seed = seed
         self.dtype_code = DTYPES.get(dtype, dtype)
         self.torch_dtype = torch.float64 if self.dtype_code == HD_F64 else torch.float32
         self.h = hd_create(ensemble, m, n, T_max, seed, self.dtype_code)
@@ -337,11 +365,32 @@ class HD:
         u = hd_probe(self.h, x, transpose, out)
         return out, u
 
-    def reset(self, seed):
-        hd_reset(self.h, seed)
+    def reset(self, seed=None):
+        if seed is not None:
+            self.seed = seed
+        hd_reset(self.h, self.seed)
 
     def counts(self):
         return hd_get_counts(self.h)
+
+    def adjoint_enable(self, record_x=True):
+        """Record the following forward steps for hd_adjoint_step (call on a fresh or reset state)."""
+        hd_adjoint_enable(self.h, record_x)
+
+    def adjoint_step(self, ybar, transpose, x_t=None):
+        """Reverse the latest unreversed step (a Q^T step when `transpose`): returns dLoss/dx_t
+        through y_t and every later product; x_t=None uses the recorded input."""
+        import torch
+        n_in, n_out = (self.m, self.n) if transpose else (self.n, self.m)
+        _ptr(ybar, self.dtype_code, n_out, "ybar")
+        if x_t is not None:
+            _ptr(x_t, self.dtype_code, n_in, "x_t")
+        xbar = torch.empty(n_in, dtype=self.torch_dtype, device=ybar.device)
+        hd_adjoint_step(self.h, ybar, x_t, xbar)
+        return xbar
+
+    def adjoint_restart(self):
+        hd_adjoint_restart(self.h)
 
     def close(self):
         if self.h:

@@ -1,0 +1,569 @@
+// Reverse mode of Householder Dice: the adjoint of a recorded single-trial trajectory.
+//
+// With the Gaussian draws held fixed, the outputs y_1..y_T of Algorithms 1 and 2 are a
+// deterministic function of the step inputs x_1..x_T.  y_t depends on x_t directly and on the
+// earlier inputs through the data-side reflectors they created (R_s = H_s(p_s), eq.
+// Householder_e) and, for Ginibre, through the basis vectors built with those reflectors.
+// hd_adjoint_step reverses the forward steps one at a time, last first.  Given ybar_t =
+// dLoss/dy_t it returns xbar_t = dLoss/dx_t through every product that x_t reaches, i.e. y_t
+// itself and all later steps through the reflector built from x_t.
+//
+// The forward steps are composed of three kinds of operation on the compact WY form
+// (I - V S V^T = P_0 ... P_{K-1}, Delta the prefix signs of the reflectors' scalar factors):
+//   data product     p = Delta (I - V S^T V^T) x            (z = V^T x, w = S^T z)
+//   output product   y = (I - V S V^T) Delta c              (a = V^T Delta c, b = S a)
+//   new reflector    u = p[k:] + s alpha e_k, alpha = ||p[k:]||, s = sign(p_k)
+//   and S = (strict_upper(G) + diag(G)/2)^{-1} with G = V^T V.
+// Their adjoints are accumulated into Vbar (per stack, like V), Sbar (upper triangle only),
+// and for Ginibre Bbar (per basis store).  When the reverse pass reaches the step that created
+// column j of a stack, every later use of that column has been accounted for: the explicit
+// terms are in Vbar[:, j], and the terms through S (Gbar = upper(-S^T Sbar S^T) with half
+// diagonal, Vbar += V (Gbar + Gbar^T)) depend only on entries of Sbar in columns >= j, which
+// are complete.  The column's adjoint then goes back into p and, through the data product,
+// into x and into the older columns.  Forward quantities (z, w, p, alpha) are recomputed from
+// the recorded x_t and the final stacks, whose leading blocks are the stacks of step t.
+// The sign s and the prefix signs are piecewise constant and carry no derivative; an identity
+// reflector (alpha = 0) passes no derivative to p.
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+
+#include <cuda_runtime.h>
+
+#include "../../include/hd.h"
+#include "hd_common.cuh"
+#include "hd_state.cuh"
+
+namespace hd {
+namespace {
+
+constexpr int kAT = 256;   // threads of every adjoint kernel
+
+enum AdjVec { kVx, kVyb, kVp, kVub, kVqb, kVxb, kVg, kAdjVecs };
+enum AdjSmall {
+  kSz, kSw, kSh, kSbb, kSb, kScb, kSzb, kSwb, kSE, kSc, kShb, kSau, kSbu, kSbbu, kSabu, kSscal,
+  kAdjSmall
+};
+
+__device__ __forceinline__ double a_block_sum(double v, double* red) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += red[w];
+  return s;
+}
+
+template <typename T>
+__global__ void k_to_double(const T* __restrict__ in, double* __restrict__ out, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (double)in[i];
+}
+template <typename T>
+__global__ void k_from_double(const double* __restrict__ in, T* __restrict__ out, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (T)in[i];
+}
+
+// Partial column dots over one row chunk per CTA: part[(b K + j) 2 + v] = sum_r A[r, j] v_v[r].
+template <typename T>
+__global__ void __launch_bounds__(kAT) k_colpass(const T* __restrict__ A, int64_t ld, int K, int64_t dim,
+                                                 const double* __restrict__ v1,
+                                                 const double* __restrict__ v2, double* part) {
+  const int64_t per = ((dim + gridDim.x - 1) / gridDim.x + 31) / 32 * 32;
+  const int64_t r0 = (int64_t)blockIdx.x * per, r1 = min(dim, r0 + per);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = warp; j < K; j += nw) {
+    const T* Aj = A + (int64_t)j * ld;
+    double s1 = 0.0, s2 = 0.0;
+    for (int64_t r = r0 + lane; r < r1; r += 32) {
+      const double a = (double)Aj[r];
+      s1 = fma(a, v1[r], s1);
+      if (v2) s2 = fma(a, v2[r], s2);
+    }
+    s1 = warp_sum(s1);
+    s2 = warp_sum(s2);
+    if (lane == 0) {
+      part[((int64_t)blockIdx.x * K + j) * 2] = s1;
+      part[((int64_t)blockIdx.x * K + j) * 2 + 1] = s2;
+    }
+  }
+}
+
+// out_v[j] = scale_v * sum over CTAs of the partials (fixed order: deterministic).
+__global__ void __launch_bounds__(kAT) k_colreduce(const double* __restrict__ part, int nblk, int K,
+                                                   double s1, double* out1, double s2, double* out2) {
+  for (int j = threadIdx.x; j < K; j += blockDim.x) {
+    double a = 0.0, b = 0.0;
+    for (int q = 0; q < nblk; q++) {
+      a += part[((int64_t)q * K + j) * 2];
+      b += part[((int64_t)q * K + j) * 2 + 1];
+    }
+    out1[j] = s1 * a;
+    if (out2) out2[j] = s2 * b;
+  }
+}
+
+// out[r] (+)= sgn(r) (s_in in[r] + c_scale sum_{j<K} A[r, j] c[j]), sgn(r) = dpre[min(r+1, Kd)]
+// (or 1); optionally per-CTA partial sums of out[r]^2 over r >= rnorm.
+template <typename T>
+__global__ void __launch_bounds__(kAT) k_rowpass(double* out, const double* in, double s_in, const T* __restrict__ A,
+                                                 int64_t ld, int K, const double* __restrict__ c, double c_scale,
+                                                 int64_t dim, const double* __restrict__ dpre, int Kd,
+                                                 int accumulate, int64_t rnorm, double* npart) {
+  __shared__ double cs[kTmaxLimit + 1];
+  __shared__ double red[kAT / 32];
+  for (int j = threadIdx.x; j < K; j += blockDim.x) cs[j] = c_scale * c[j];
+  __syncthreads();
+  double ns = 0.0;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < dim; r += (int64_t)gridDim.x * blockDim.x) {
+    double v = in ? s_in * in[r] : 0.0;
+    const T* Ar = A + r;
+    int j = 0;
+    for (; j + 4 <= K; j += 4) {
+      v = fma((double)Ar[(int64_t)j * ld], cs[j], v);
+      v = fma((double)Ar[(int64_t)(j + 1) * ld], cs[j + 1], v);
+      v = fma((double)Ar[(int64_t)(j + 2) * ld], cs[j + 2], v);
+      v = fma((double)Ar[(int64_t)(j + 3) * ld], cs[j + 3], v);
+    }
+    for (; j < K; j++) v = fma((double)Ar[(int64_t)j * ld], cs[j], v);
+    if (dpre) v *= dpre[min(r + 1, (int64_t)Kd)];
+    if (accumulate) v += out[r];
+    out[r] = v;
+    if (r >= rnorm) ns = fma(v, v, ns);
+  }
+  if (npart) {
+    ns = a_block_sum(ns, red);
+    if (threadIdx.x == 0) npart[blockIdx.x] = ns;
+  }
+}
+
+// Ab[r, j] += sb a[r] b[j] + sd c[r] d[j] for r < dim, j < K (column-major, leading dim ld).
+__global__ void __launch_bounds__(kAT) k_rank(double* Ab, int64_t ld, int K, int64_t dim,
+                                              const double* __restrict__ a, const double* __restrict__ b, double sb,
+                                              const double* __restrict__ c, const double* __restrict__ d, double sd) {
+  const int j0 = blockIdx.y * 8;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < dim; r += (int64_t)gridDim.x * blockDim.x) {
+    const double ar = sb * a[r];
+    const double cr = c ? sd * c[r] : 0.0;
+    for (int j = j0; j < min(K, j0 + 8); j++) {
+      double v = ar * b[j];
+      if (c) v = fma(cr, d[j], v);
+      Ab[r + (int64_t)j * ld] += v;
+    }
+  }
+}
+
+// out = scale S v (trans = 0) or scale S^T v (trans = 1), leading K x K block of the upper
+// triangular S (column-major, leading dim Tm).
+__global__ void __launch_bounds__(kAT) k_tri(const double* __restrict__ S, int Tm, int K, const double* __restrict__ v,
+                                             double scale, int trans, double* out) {
+  for (int i = threadIdx.x; i < K; i += blockDim.x) {
+    double s = 0.0;
+    if (!trans) {
+      for (int j = i; j < K; j++) s = fma(S[i + (int64_t)j * Tm], v[j], s);
+    } else {
+      for (int q = 0; q <= i; q++) s = fma(S[q + (int64_t)i * Tm], v[q], s);
+    }
+    out[i] = scale * s;
+  }
+}
+
+// Sb[i, j] += a[i] b[j] on the upper triangle i <= j < K (S has no free entries below).
+__global__ void __launch_bounds__(kAT) k_outer_upper(double* Sb, int Tm, int K, const double* __restrict__ a,
+                                                     const double* __restrict__ b) {
+  for (int idx = threadIdx.x; idx < K * K; idx += blockDim.x) {
+    const int i = idx % K, j = idx / K;
+    if (i <= j) Sb[i + (int64_t)j * Tm] += a[i] * b[j];
+  }
+}
+
+// E = Gbar[:, j] + Gbar[j, :]^T with Gbar = upper(M) (half diagonal), M = -S^T Sbar S^T, over
+// the K columns of the stack: E[i] = M[i, j] for i <= j, M[j, i] for i > j.
+__global__ void __launch_bounds__(kAT) k_gbar(const double* __restrict__ S, const double* __restrict__ Sb, int Tm,
+                                              int K, int j, double* E) {
+  __shared__ double r1[kTmaxLimit + 1], r2[kTmaxLimit + 1];
+  const bool ident = S[j + (int64_t)j * Tm] == 0.0;   // identity reflector: no free column
+  for (int a = threadIdx.x; a < K; a += blockDim.x) {
+    double s1 = 0.0, s2 = 0.0;
+    for (int b = j; b < K; b++) s1 = fma(Sb[a + (int64_t)b * Tm], S[j + (int64_t)b * Tm], s1);   // (Sbar S[j, :]^T)_a
+    for (int q = 0; q <= j; q++) s2 = fma(S[q + (int64_t)j * Tm], Sb[q + (int64_t)a * Tm], s2);   // (Sbar^T S[:, j])_a
+    r1[a] = s1;
+    r2[a] = s2;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < K; i += blockDim.x) {
+    double s = 0.0;
+    if (!ident) {
+      if (i <= j) {
+        for (int a = 0; a <= i; a++) s = fma(S[a + (int64_t)i * Tm], r1[a], s);
+      } else {
+        for (int b = i; b < K; b++) s = fma(S[i + (int64_t)b * Tm], r2[b], s);
+      }
+    }
+    E[i] = -s;
+  }
+}
+
+// alpha = ||p[kD:]|| from the row-pass partials, s = sign(p[kD]) (+1 at 0).
+__global__ void k_alpha(const double* __restrict__ npart, int nb, const double* __restrict__ p, int kD, double* scal) {
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int q = 0; q < nb; q++) s += npart[q];
+    scal[0] = sqrt(s);
+    scal[1] = (p[kD] >= 0.0) ? 1.0 : -1.0;
+  }
+}
+
+// c = [p[0:k]; alpha]
+__global__ void k_head_alpha(const double* __restrict__ p, int k, const double* __restrict__ scal, double* c) {
+  for (int i = threadIdx.x; i <= k; i += blockDim.x) c[i] = (i < k) ? p[i] : scal[0];
+}
+
+// Adjoint of the output product y = (I - V S V^T) Delta c for c supported on rows < nc <= Ke
+// (Ke reflectors).  Given bb = -V^T ybar (from a column pass) and the head of ybar: writes
+// b = S a (for Vbar += -ybar b^T, done by the caller), cbar = Delta (ybar + V S^T bb) on the
+// first nc rows, and adds Sbar += bb a^T and Vbar[:nc, :] += (Delta c) (S^T bb)^T.
+template <typename T>
+__global__ void __launch_bounds__(kAT) k_out_small(const T* __restrict__ V, int64_t ld, int Ke, int nc,
+                                                   const double* __restrict__ S, int Tm,
+                                                   const double* __restrict__ dpre, const double* __restrict__ c,
+                                                   const double* __restrict__ bb, const double* __restrict__ ybd,
+                                                   double* Sb, double* Vb, double* b_out, double* cbar) {
+  __shared__ double cp[kTmaxLimit + 1], a[kTmaxLimit + 1], ab[kTmaxLimit + 1];
+  for (int i = threadIdx.x; i < nc; i += blockDim.x) cp[i] = dpre[i + 1] * c[i];
+  __syncthreads();
+  for (int j = threadIdx.x; j < Ke; j += blockDim.x) {
+    double s = 0.0;
+    for (int i = j; i < nc; i++) s = fma((double)V[i + (int64_t)j * ld], cp[i], s);
+    a[j] = s;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < Ke; i += blockDim.x) {
+    double sb = 0.0, sa = 0.0;
+    for (int j = i; j < Ke; j++) sb = fma(S[i + (int64_t)j * Tm], a[j], sb);
+    for (int q = 0; q <= i; q++) sa = fma(S[q + (int64_t)i * Tm], bb[q], sa);
+    b_out[i] = sb;
+    ab[i] = sa;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < Ke * Ke; idx += blockDim.x) {
+    const int i = idx % Ke, j = idx / Ke;
+    if (i <= j) Sb[i + (int64_t)j * Tm] += bb[i] * a[j];
+  }
+  for (int i = threadIdx.x; i < nc; i += blockDim.x) {
+    double s = ybd[i];
+    const int jm = min(i, Ke - 1);
+    for (int j = 0; j <= jm; j++) {
+      s = fma((double)V[i + (int64_t)j * ld], ab[j], s);
+      Vb[i + (int64_t)j * ld] += cp[i] * ab[j];
+    }
+    cbar[i] = dpre[i + 1] * s;
+  }
+}
+
+// qbar = Delta_D pbar with pbar[r] = cb[r] (r < kD) and, on the tail, the adjoint of the new
+// column u = p[kD:] + s alpha e_kD and of alpha: (cb[kD] + s ub[kD]) p[r] / alpha + ub[r].
+__global__ void __launch_bounds__(kAT) k_pbar(double* __restrict__ qbar, const double* __restrict__ p,
+                                              const double* __restrict__ ub, const double* __restrict__ cb,
+                                              const double* __restrict__ scal, int kD,
+                                              const double* __restrict__ dpre, int64_t dim) {
+  const double alpha = scal[0], s = scal[1];
+  const double coef = (alpha > 0.0) ? (cb[kD] + s * ub[kD]) / alpha : 0.0;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < dim; r += (int64_t)gridDim.x * blockDim.x) {
+    double pb;
+    if (r < kD) pb = cb[r];
+    else pb = (alpha > 0.0) ? fma(coef, p[r], ub[r]) : 0.0;
+    qbar[r] = dpre[min(r + 1, (int64_t)kD)] * pb;
+  }
+}
+
+// out[r] = sgn * (sigma g_r) for first <= r < dim (the step's draw, in the state's precision),
+// 0 elsewhere; sgn = *sgnp.
+template <typename T>
+__global__ void __launch_bounds__(kAT) k_draw_d(DrawKey key, int64_t first, int64_t dim, T sigma,
+                                                const double* __restrict__ sgnp, double* out) {
+  const double sg = *sgnp;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < dim; r += (int64_t)gridDim.x * blockDim.x) {
+    double v = 0.0;
+    if (r >= first) {
+      T a, b;
+      normal_pair(key, (uint64_t)(r >> 1), a, b);
+      v = sg * (double)(sigma * ((r & 1) ? b : a));
+    }
+    out[r] = v;
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// Host side
+struct Ctx {
+  hd_state* st;
+  cudaStream_t s;
+  unsigned grid;
+};
+
+unsigned rows_grid(const hd_state* st, int64_t dim) {
+  const int64_t want = (dim + kAT - 1) / kAT;
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)st->nsm * 8));
+}
+
+template <typename T>
+void colpass(const Ctx& c, const T* A, int64_t ld, int K, int64_t dim, const double* v1, double s1, double* o1,
+             const double* v2 = nullptr, double s2 = 0.0, double* o2 = nullptr) {
+  if (K <= 0) return;
+  AdjState& A_ = *c.st->adj;
+  k_colpass<T><<<A_.nblk, kAT, 0, c.s>>>(A, ld, K, dim, v1, v2, A_.part);
+  k_colreduce<<<1, kAT, 0, c.s>>>(A_.part, A_.nblk, K, s1, o1, s2, o2);
+}
+
+template <typename T>
+void rowpass(const Ctx& c, double* out, const double* in, double s_in, const T* A, int64_t ld, int K,
+             const double* coef, double cscale, int64_t dim, const double* dpre, int Kd, int acc,
+             int64_t rnorm = INT64_MAX, double* npart = nullptr, unsigned grid = 0) {
+  const unsigned g = grid ? grid : rows_grid(c.st, dim);
+  k_rowpass<T><<<g, kAT, 0, c.s>>>(out, in, s_in, A, ld, K, coef, cscale, dim, dpre, Kd, acc, rnorm, npart);
+}
+
+void rank(const Ctx& c, double* Ab, int64_t ld, int K, int64_t dim, const double* a, const double* b, double sb,
+          const double* cc = nullptr, const double* d = nullptr, double sd = 0.0) {
+  if (K <= 0) return;
+  dim3 g(rows_grid(c.st, dim), (unsigned)((K + 7) / 8));
+  k_rank<<<g, kAT, 0, c.s>>>(Ab, ld, K, dim, a, b, sb, cc, d, sd);
+}
+
+template <typename T>
+int adj_step(hd_state* st, const void* ybar, const void* x_in, void* xbar) {
+  AdjState& A = *st->adj;
+  const int t = A.rev;                 // 1-based forward step being reversed
+  const int tr = A.flag[t - 1], kD = A.kD[t - 1], kN = A.kN[t - 1];
+  const int d = tr ? 1 : 0, e = 1 - d;
+  const TrialDesc& td = st->hdesc[0];
+  const StackDev& Sd = td.st[d];
+  const StackDev& Se = td.st[e];
+  const int64_t nd = st->dims[d][0], ne = st->dims[e][0];
+  const bool haar = st->ens == HD_HAAR;
+  const int Kfin_d = haar ? st->t : (d == 0 ? st->r : st->l);
+  const T* Vd = (const T*)Sd.V;
+  const T* Ve = (const T*)Se.V;
+  const int Tm = st->Tm;
+  const Ctx c{st, st->stream, 0};
+  const int64_t L = A.dmax;
+  double* xd = A.vec + kVx * L;
+  double* ybd = A.vec + kVyb * L;
+  double* p = A.vec + kVp * L;
+  double* ub = A.vec + kVub * L;
+  double* qb = A.vec + kVqb * L;
+  double* xb = A.vec + kVxb * L;
+  double* gd = A.vec + kVg * L;
+  auto sm = [&](int slot) { return A.small + (int64_t)slot * A.small_ld; };
+  double* z = sm(kSz);
+  double* w = sm(kSw);
+  double* h = sm(kSh);
+  double* bb = sm(kSbb);
+  double* bo = sm(kSb);
+  double* cb = sm(kScb);
+  double* zb = sm(kSzb);
+  double* wb = sm(kSwb);
+  double* E = sm(kSE);
+  double* cv = sm(kSc);
+  double* hb = sm(kShb);
+  double* au = sm(kSau);
+  double* bu = sm(kSbu);
+  double* bbu = sm(kSbbu);
+  double* abu = sm(kSabu);
+  double* scal = sm(kSscal);
+  const unsigned gv = rows_grid(st, std::max(nd, ne));
+
+  // forward quantities of step t: z = V_D^T x, (Gin) h = B_D^T x, w = S_D^T z, p, alpha, s
+  const void* xsrc = x_in ? x_in : (const void*)((const char*)A.X + (size_t)(t - 1) * A.ldx * sizeof(T));
+  k_to_double<T><<<gv, kAT, 0, c.s>>>((const T*)xsrc, xd, nd);
+  k_to_double<T><<<gv, kAT, 0, c.s>>>((const T*)ybar, ybd, ne);
+  colpass<T>(c, Vd, Sd.ld, kD, nd, xd, 1.0, z);
+  if (!haar) colpass<T>(c, (const T*)td.basis[d], td.ldb[d], kN, nd, xd, 1.0, h);
+  if (kD > 0) k_tri<<<1, kAT, 0, c.s>>>(Sd.S, Tm, kD, z, 1.0, 1, w);
+  const unsigned gp = rows_grid(st, nd);
+  rowpass<T>(c, p, xd, 1.0, Vd, Sd.ld, kD, w, -1.0, nd, Sd.dpre, kD, 0, kD, A.part, gp);
+  k_alpha<<<1, 32, 0, c.s>>>(A.part, (int)gp, p, kD, scal);
+
+  // output product
+  if (haar) {
+    const int Ke = kD + 1;   // the other stack including this step's random reflector
+    colpass<T>(c, Ve, Se.ld, Ke, ne, ybd, -1.0, bb);
+    k_head_alpha<<<1, kAT, 0, c.s>>>(p, kD, scal, cv);
+    k_out_small<T><<<1, kAT, 0, c.s>>>(Ve, Se.ld, Ke, kD + 1, Se.S, Tm, Se.dpre, cv, bb, ybd, A.Sbar[e],
+                                      A.Vbar[e], bo, cb);
+    rank(c, A.Vbar[e], Se.ld, Ke, ne, ybd, bo, -1.0);
+  } else {
+    if (kN > 0) {
+      colpass<T>(c, Ve, Se.ld, kN, ne, ybd, -1.0, bb);
+      k_out_small<T><<<1, kAT, 0, c.s>>>(Ve, Se.ld, kN, kN, Se.S, Tm, Se.dpre, h, bb, ybd, A.Sbar[e],
+                                        A.Vbar[e], bo, hb);
+      rank(c, A.Vbar[e], Se.ld, kN, ne, ybd, bo, -1.0);
+    }
+    const T* Be = (const T*)td.basis[e];
+    const int64_t lde = td.ldb[e];
+    colpass<T>(c, Be, lde, kD + 1, ne, ybd, 1.0, cb);         // [pbar_head; alphabar]
+    k_head_alpha<<<1, kAT, 0, c.s>>>(p, kD, scal, cv);          // [p_head; alpha]
+    rank(c, A.Bbar[e], lde, kD + 1, ne, ybd, cv, 1.0);
+    if (kN > 0) {
+      // the basis column built at this step, u = (I - V_N S_N V_N^T) Delta_N g: its adjoint
+      // is complete; g is constant
+      const double* ubar_b = A.Bbar[e] + (int64_t)kD * lde;
+      DrawKey key = key_for(st, t);
+      k_draw_d<T><<<gv, kAT, 0, c.s>>>(key, kN, ne, (T)st->sigma, Se.dpre + kN, gd);
+      colpass<T>(c, Ve, Se.ld, kN, ne, ubar_b, -1.0, bbu, gd, 1.0, au);
+      k_tri<<<1, kAT, 0, c.s>>>(Se.S, Tm, kN, au, 1.0, 0, bu);
+      k_tri<<<1, kAT, 0, c.s>>>(Se.S, Tm, kN, bbu, 1.0, 1, abu);
+      k_outer_upper<<<1, kAT, 0, c.s>>>(A.Sbar[e], Tm, kN, bbu, au);
+      rank(c, A.Vbar[e], Se.ld, kN, ne, ubar_b, bu, -1.0, gd, abu, 1.0);
+    }
+  }
+
+  // the data-side reflector of this step (column kD of V_D)
+  k_gbar<<<1, kAT, 0, c.s>>>(Sd.S, A.Sbar[d], Tm, Kfin_d, kD, E);
+  rowpass<T>(c, ub, A.Vbar[d] + (int64_t)kD * Sd.ld, 1.0, Vd, Sd.ld, Kfin_d, E, 1.0, nd, nullptr, 0, 0);
+  k_pbar<<<gp, kAT, 0, c.s>>>(qb, p, ub, cb, scal, kD, Sd.dpre, nd);
+
+  // the data product p = Delta (I - V S^T V^T) x
+  colpass<T>(c, Vd, Sd.ld, kD, nd, qb, -1.0, wb);
+  if (kD > 0) {
+    k_tri<<<1, kAT, 0, c.s>>>(Sd.S, Tm, kD, wb, 1.0, 0, zb);
+    k_outer_upper<<<1, kAT, 0, c.s>>>(A.Sbar[d], Tm, kD, z, wb);
+  }
+  rowpass<T>(c, xb, qb, 1.0, Vd, Sd.ld, kD, zb, 1.0, nd, nullptr, 0, 0);
+  if (!haar && kN > 0) {
+    const T* Bd = (const T*)td.basis[d];
+    rowpass<T>(c, xb, nullptr, 0.0, Bd, td.ldb[d], kN, hb, 1.0, nd, nullptr, 0, 1);
+    rank(c, A.Bbar[d], td.ldb[d], kN, nd, xd, hb, 1.0);
+  }
+  rank(c, A.Vbar[d], Sd.ld, kD, nd, qb, w, -1.0, xd, zb, 1.0);
+  k_from_double<T><<<gv, kAT, 0, c.s>>>(xb, (T*)xbar, nd);
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return cuda_fail(st, err);
+  A.rev -= 1;
+  return HD_OK;
+}
+
+int adj_zero(hd_state* st) {
+  AdjState& A = *st->adj;
+  const TrialDesc& td = st->hdesc[0];
+  for (int s = 0; s < 2; s++) {
+    if (cudaMemsetAsync(A.Vbar[s], 0, (size_t)td.st[s].ld * st->Tm * sizeof(double), st->stream) != cudaSuccess ||
+        cudaMemsetAsync(A.Sbar[s], 0, (size_t)st->Tm * st->Tm * sizeof(double), st->stream) != cudaSuccess)
+      return cuda_fail(st, cudaGetLastError());
+    if (A.Bbar[s] && cudaMemsetAsync(A.Bbar[s], 0, (size_t)td.ldb[s] * st->Tm * sizeof(double), st->stream) != cudaSuccess)
+      return cuda_fail(st, cudaGetLastError());
+  }
+  return HD_OK;
+}
+
+}  // namespace
+
+// Called by the forward step when reverse mode is on: record the step and its input.
+int adj_record_step(hd_state* st, const void* x, int transpose, int kD, int kN) {
+  AdjState& A = *st->adj;
+  if (A.rev != st->t) return HD_ERR_STATE;   // a reverse pass has started: no more forward steps
+  A.flag.push_back((int8_t)(transpose ? 1 : 0));
+  A.kD.push_back(kD);
+  A.kN.push_back(kN);
+  if (A.record_x) {
+    const int64_t nin = st->dims[transpose ? 1 : 0][0];
+    cudaError_t e = cudaMemcpyAsync((char*)A.X + (size_t)st->t * A.ldx * st->esz, x, (size_t)nin * st->esz,
+                                    cudaMemcpyDeviceToDevice, st->stream);
+    if (e != cudaSuccess) return cuda_fail(st, e);
+  }
+  A.rev = st->t + 1;
+  return HD_OK;
+}
+
+// Called by hd_reset: forget the recorded steps and clear the accumulators.
+int adj_on_reset(hd_state* st) {
+  if (!st->adj || !st->adj->on) return HD_OK;
+  AdjState& A = *st->adj;
+  A.flag.clear();
+  A.kD.clear();
+  A.kN.clear();
+  A.rev = 0;
+  return adj_zero(st);
+}
+
+}  // namespace hd
+
+using namespace hd;
+
+HD_API int hd_adjoint_enable(hd_state* st, int flags) {
+  if (!st) return HD_ERR_ARG;
+  if (st->poisoned) return st->poisoned;
+  if (st->count != 1) return HD_ERR_ARG;
+  if (st->t != 0) return HD_ERR_STATE;
+  if (flags & ~(HD_ADJ_RECORD_X)) return HD_ERR_ARG;
+  if (cudaSetDevice(st->device) != cudaSuccess) return cuda_fail(st, cudaErrorInvalidDevice);
+  if (!st->adj) {
+    AdjState* A = new (std::nothrow) AdjState();
+    if (!A) return HD_ERR_OOM;
+    st->adj = A;
+    const TrialDesc& td = st->hdesc[0];
+    const int Tm = st->Tm;
+    for (int s = 0; s < 2; s++) {
+      A->Vbar[s] = (double*)dalloc(st, (size_t)td.st[s].ld * Tm * sizeof(double));
+      A->Sbar[s] = (double*)dalloc(st, (size_t)Tm * Tm * sizeof(double));
+      if (!A->Vbar[s] || !A->Sbar[s]) return HD_ERR_OOM;
+      if (st->ens == HD_GINIBRE) {
+        A->Bbar[s] = (double*)dalloc(st, (size_t)td.ldb[s] * Tm * sizeof(double));
+        if (!A->Bbar[s]) return HD_ERR_OOM;
+      }
+    }
+    A->dmax = round_up(std::max(st->dims[0][0], st->dims[1][0]), 256);
+    A->ldx = A->dmax;
+    A->vec = (double*)dalloc(st, (size_t)kAdjVecs * A->dmax * sizeof(double));
+    A->small_ld = Tm + 8;
+    A->small = (double*)dalloc(st, (size_t)kAdjSmall * A->small_ld * sizeof(double));
+    A->nblk = std::max(1, 2 * st->nsm);
+    const int64_t gmax = (int64_t)st->nsm * 8;
+    A->part = (double*)dalloc(st, (size_t)std::max<int64_t>((int64_t)A->nblk * (Tm + 1) * 2, gmax) * sizeof(double));
+    if (!A->vec || !A->small || !A->part) return HD_ERR_OOM;
+  }
+  AdjState& A = *st->adj;
+  A.record_x = (flags & HD_ADJ_RECORD_X) ? 1 : 0;
+  if (A.record_x && !A.X) {
+    A.X = dalloc(st, (size_t)A.ldx * st->Tm * st->esz);
+    if (!A.X) return HD_ERR_OOM;
+  }
+  A.on = 1;
+  A.flag.clear();
+  A.kD.clear();
+  A.kN.clear();
+  A.rev = 0;
+  return adj_zero(st);
+}
+
+HD_API int hd_adjoint_step(hd_state* st, const void* ybar, const void* x_t, void* xbar) {
+  if (!st || !ybar || !xbar) return HD_ERR_ARG;
+  if (st->poisoned) return st->poisoned;
+  if (!st->adj || !st->adj->on) return HD_ERR_STATE;
+  AdjState& A = *st->adj;
+  if (A.rev < 1) return HD_ERR_STATE;
+  if (!x_t && !A.record_x) return HD_ERR_ARG;
+  if (cudaSetDevice(st->device) != cudaSuccess) return cuda_fail(st, cudaErrorInvalidDevice);
+  return st->dtype == HD_F64 ? adj_step<double>(st, ybar, x_t, xbar) : adj_step<float>(st, ybar, x_t, xbar);
+}
+
+HD_API int hd_adjoint_restart(hd_state* st) {
+  if (!st) return HD_ERR_ARG;
+  if (st->poisoned) return st->poisoned;
+  if (!st->adj || !st->adj->on) return HD_ERR_STATE;
+  if (cudaSetDevice(st->device) != cudaSuccess) return cuda_fail(st, cudaErrorInvalidDevice);
+  st->adj->rev = st->t;
+  return adj_zero(st);
+}
+
+HD_API int hd_adjoint_position(const hd_state* st, int32_t* remaining) {
+  if (!st || !remaining) return HD_ERR_ARG;
+  *remaining = (st->adj && st->adj->on) ? st->adj->rev : 0;
+  return HD_OK;
+}

@@ -15,111 +15,14 @@
 #include "../../include/hd.h"
 #include "hd_dynamics.cuh"
 #include "hd_kernels.cuh"
+#include "hd_state.cuh"
 
 using namespace hd;
-
-struct hd_state {
-  int ens = 0, dtype = 0;
-  int count = 1;                 // trials
-  std::vector<int64_t> dims[2];  // per trial: dims[0] = n_i (space of R), dims[1] = m_i (space of L)
-  std::vector<int64_t> off[2];   // packed vector offsets per space (count + 1)
-  int Tm = 0;
-  uint64_t seed = 0;
-  uint32_t trial = 0;            // Philox trial word of trial 0 (trial i uses trial + i)
-  double sigma = 1.0;
-  cudaStream_t stream = nullptr;
-  int device = 0;
-  int t = 0, r = 0, l = 0;
-  int drawn = 0;                 // first draws made since create/reset
-  int poisoned = 0;              // sticky error code
-  size_t esz = 8;                // element size of vectors and stacks
-  std::vector<TrialDesc> hdesc;  // host copy of the per-trial descriptors
-  TrialDesc* ddesc = nullptr;
-  CtaMap map[2];
-  int maxncta = 1;
-  unsigned int* err = nullptr;
-  unsigned int* cnt = nullptr;
-  size_t cnt_bytes = 0;
-  int nsm = 1;
-  int pdl = 1;                   // programmatic dependent launch of the sweeps (HD_DISABLE_PDL=1: off)
-  int occ_regs[4] = {1, 1, 1, 1};  // CTAs of 256 threads per SM allowed by registers per sweep
-  int static_smem[4] = {0, 0, 0, 0};
-  int smem_sm = 0;
-  int smem_blk_max = 0;
-  int64_t bytes = 0;
-  std::vector<void*> allocs;
-  // hd_run: work vectors and the cached trajectory graph
-  void* xw[2] = {nullptr, nullptr};
-  void* yw = nullptr;
-  double* sumsq = nullptr;
-  int run_final = 0;
-  cudaStream_t own_stream = nullptr;
-  cudaGraphExec_t gexec = nullptr;
-  std::vector<uint8_t> g_flags;
-  int g_T = 0, g_dyn = 0;
-  double g_a = 0.0, g_sigma = 0.0;
-  uint64_t g_seed = 0;
-  uint32_t g_trial = 0;
-  cudaStream_t g_stream = nullptr;
-  int g_final = 0;
-  int g_launches = 0;
-  int g_prof = 0;
-  int64_t launches = 0;          // kernel launches issued (graph replays count their kernels)
-  // profiling: event pairs around each sweep, algorithmic bytes of each recorded launch
-  int prof_on = 0;
-  int prof_cap = 0;
-  int prof_used = 0;
-  std::vector<cudaEvent_t> prof_ev;
-  std::vector<int> prof_kind;
-  std::vector<double> prof_bytes;
-  double prof_ms[3] = {0, 0, 0};
-  int64_t prof_n[3] = {0, 0, 0};
-  double prof_b[3] = {0, 0, 0};
-};
 
 namespace {
 
 thread_local char g_last_error[256] = "";
 
-void set_error(const char* where, cudaError_t e) {
-  snprintf(g_last_error, sizeof(g_last_error), "%s: %s", where, cudaGetErrorString(e));
-}
-
-int cuda_fail(hd_state* st, cudaError_t e) {
-  set_error("kernel launch", e);
-  if (st) st->poisoned = HD_ERR_CUDA;
-  return HD_ERR_CUDA;
-}
-
-int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
-
-void* dalloc(hd_state* st, size_t bytes) {
-  void* p = nullptr;
-  if (bytes == 0) bytes = 16;
-  bytes = (bytes + 255) & ~(size_t)255;
-  if (cudaMalloc(&p, bytes) != cudaSuccess) {
-    cudaGetLastError();
-    return nullptr;
-  }
-  st->allocs.push_back(p);
-  st->bytes += (int64_t)bytes;
-  return p;
-}
-
-void free_all(hd_state* st) {
-  for (void* p : st->allocs) cudaFree(p);
-  st->allocs.clear();
-}
-
-DrawKey key_for(const hd_state* st, int step) {
-  DrawKey k;
-  k.k0 = (uint32_t)(st->seed & 0xFFFFFFFFu);
-  k.k1 = (uint32_t)(st->seed >> 32);
-  k.step = (uint32_t)step;
-  k.trial = st->trial;   // replaced per trial by the kernels (desc.trial)
-  k.stream = 0;
-  return k;
-}
 
 // Shape of a sweep over ncolT staged columns and NRV staged row vectors (ncolC column-owner
 // columns, NR right-hand sides): the (warps per CTA, pipeline stages per warp) pair that puts
@@ -212,6 +115,10 @@ int do_step(hd_state* st, const void* x, int transpose, void* y) {
   const int cnt[2] = {st->r, st->l};
   const int kD = (st->ens == HD_HAAR) ? st->t : cnt[d];
   const int kN = (st->ens == HD_HAAR) ? st->t : cnt[1 - d];
+  if (st->adj && st->adj->on) {
+    const int rc = adj_record_step(st, x, transpose, kD, kN);
+    if (rc) return rc;
+  }
   BatchStep<T> b = make_batch<T>(st, d, kD, kN, x, y);
   b.base.key_next = key_for(st, st->t + 2);
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -277,6 +184,7 @@ int run_steps(hd_state* st, const hd_run_spec* sp) {
   if (st->prof_on) st->prof_used = 0;
   st->t = st->r = st->l = 0;
   st->drawn = 0;
+  if (int rc = adj_on_reset(st)) return rc;
   int cur = 0;
   for (int t = 0; t < sp->T; t++) {
     const int tr = sp->transpose[t] ? 1 : 0;
@@ -530,6 +438,47 @@ int upload_trials(hd_state* st) {
 }  // namespace
 
 namespace hd {
+
+void set_error(const char* where, cudaError_t e) {
+  snprintf(g_last_error, sizeof(g_last_error), "%s: %s", where, cudaGetErrorString(e));
+}
+
+int cuda_fail(hd_state* st, cudaError_t e) {
+  set_error("kernel launch", e);
+  if (st) st->poisoned = HD_ERR_CUDA;
+  return HD_ERR_CUDA;
+}
+
+int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+void* dalloc(hd_state* st, size_t bytes) {
+  void* p = nullptr;
+  if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) & ~(size_t)255;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  st->allocs.push_back(p);
+  st->bytes += (int64_t)bytes;
+  return p;
+}
+
+void free_all(hd_state* st) {
+  for (void* p : st->allocs) cudaFree(p);
+  st->allocs.clear();
+}
+
+DrawKey key_for(const hd_state* st, int step) {
+  DrawKey k;
+  k.k0 = (uint32_t)(st->seed & 0xFFFFFFFFu);
+  k.k1 = (uint32_t)(st->seed >> 32);
+  k.step = (uint32_t)step;
+  k.trial = st->trial;   // replaced per trial by the kernels (desc.trial)
+  k.stream = 0;
+  return k;
+}
+
 // Lets other translation units of the library set hd_last_error's text.
 void record_error_text(const char* msg) { snprintf(g_last_error, sizeof(g_last_error), "%s", msg); }
 }  // namespace hd
@@ -630,7 +579,8 @@ HD_API int hd_run(hd_state* st, const hd_run_spec* sp, const void* x1, void* x_o
     return cuda_fail(st, e);
   }
   int rc = HD_OK;
-  if (sp->use_graph) {
+  // reverse mode records every step on the host, so a recording state runs without the graph
+  if (sp->use_graph && !(st->adj && st->adj->on)) {
     if (!graph_matches(st, sp)) {
       if (st->gexec) {
         cudaGraphExecDestroy(st->gexec);
@@ -797,7 +747,7 @@ HD_API int hd_reset(hd_state* st, uint64_t seed) {
   st->t = st->r = st->l = 0;
   st->drawn = 0;
   st->poisoned = 0;
-  return HD_OK;
+  return adj_on_reset(st);
 }
 
 HD_API void hd_destroy(hd_state* st) {
@@ -809,6 +759,7 @@ HD_API void hd_destroy(hd_state* st) {
   for (auto& ev : st->prof_ev)
     if (ev) cudaEventDestroy(ev);
   free_all(st);
+  delete st->adj;
   delete st;
 }
 

@@ -1,0 +1,108 @@
+// The library's state object (host side) and the helpers shared by its translation units.
+#pragma once
+#include <cstdint>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "hd_kernels.cuh"
+
+namespace hd {
+
+// Reverse-mode record and accumulators of a single-trial state (hd_adjoint_*).
+struct AdjState {
+  int on = 0;
+  int record_x = 0;
+  std::vector<int8_t> flag;      // per forward step: transpose flag
+  std::vector<int> kD, kN;       // per forward step: reflectors in the data / other stack before it
+  int rev = 0;                   // forward steps not yet reversed
+  double* Vbar[2] = {nullptr, nullptr};   // d loss / d V per stack (dim x T_max, ld of the stack)
+  double* Bbar[2] = {nullptr, nullptr};   // d loss / d basis store per space (Ginibre)
+  double* Sbar[2] = {nullptr, nullptr};   // d loss / d S per stack (T_max x T_max)
+  void* X = nullptr;             // recorded step inputs x_t (state dtype), column t-1
+  int64_t ldx = 0;
+  int64_t dmax = 0;              // longest vector (rounded)
+  double* vec = nullptr;         // FP64 work vectors, kAdjVecs x dmax
+  double* small = nullptr;       // FP64 small arena, kAdjSmall x (T_max + 8)
+  int64_t small_ld = 0;
+  double* part = nullptr;        // column-pass partial sums
+  int nblk = 1;
+};
+
+}  // namespace hd
+
+using hd::TrialDesc;
+using hd::CtaMap;
+
+struct hd_state {
+  int ens = 0, dtype = 0;
+  int count = 1;                 // trials
+  std::vector<int64_t> dims[2];  // per trial: dims[0] = n_i (space of R), dims[1] = m_i (space of L)
+  std::vector<int64_t> off[2];   // packed vector offsets per space (count + 1)
+  int Tm = 0;
+  uint64_t seed = 0;
+  uint32_t trial = 0;            // Philox trial word of trial 0 (trial i uses trial + i)
+  double sigma = 1.0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int t = 0, r = 0, l = 0;
+  int drawn = 0;                 // first draws made since create/reset
+  int poisoned = 0;              // sticky error code
+  size_t esz = 8;                // element size of vectors and stacks
+  std::vector<TrialDesc> hdesc;  // host copy of the per-trial descriptors
+  TrialDesc* ddesc = nullptr;
+  CtaMap map[2];
+  int maxncta = 1;
+  unsigned int* err = nullptr;
+  unsigned int* cnt = nullptr;
+  size_t cnt_bytes = 0;
+  int nsm = 1;
+  int pdl = 1;                   // programmatic dependent launch of the sweeps (HD_DISABLE_PDL=1: off)
+  int occ_regs[4] = {1, 1, 1, 1};  // CTAs of 256 threads per SM allowed by registers per sweep
+  int static_smem[4] = {0, 0, 0, 0};
+  int smem_sm = 0;
+  int smem_blk_max = 0;
+  int64_t bytes = 0;
+  std::vector<void*> allocs;
+  // hd_run: work vectors and the cached trajectory graph
+  void* xw[2] = {nullptr, nullptr};
+  void* yw = nullptr;
+  double* sumsq = nullptr;
+  int run_final = 0;
+  cudaStream_t own_stream = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<uint8_t> g_flags;
+  int g_T = 0, g_dyn = 0;
+  double g_a = 0.0, g_sigma = 0.0;
+  uint64_t g_seed = 0;
+  uint32_t g_trial = 0;
+  cudaStream_t g_stream = nullptr;
+  int g_final = 0;
+  int g_launches = 0;
+  int g_prof = 0;
+  int64_t launches = 0;          // kernel launches issued (graph replays count their kernels)
+  // profiling: event pairs around each sweep, algorithmic bytes of each recorded launch
+  int prof_on = 0;
+  int prof_cap = 0;
+  int prof_used = 0;
+  std::vector<cudaEvent_t> prof_ev;
+  std::vector<int> prof_kind;
+  std::vector<double> prof_bytes;
+  double prof_ms[3] = {0, 0, 0};
+  int64_t prof_n[3] = {0, 0, 0};
+  double prof_b[3] = {0, 0, 0};
+  hd::AdjState* adj = nullptr;   // reverse mode (hd_adjoint_enable)
+};
+
+namespace hd {
+void set_error(const char* where, cudaError_t e);
+int cuda_fail(hd_state* st, cudaError_t e);
+int64_t round_up(int64_t a, int64_t b);
+void* dalloc(hd_state* st, size_t bytes);
+void free_all(hd_state* st);
+DrawKey key_for(const hd_state* st, int step);
+void record_error_text(const char* msg);
+// reverse mode hooks of the forward path (hd_adjoint.cu)
+int adj_record_step(hd_state* st, const void* x, int transpose, int kD, int kN);
+int adj_on_reset(hd_state* st);
+}  // namespace hd

@@ -82,6 +82,12 @@ HD_API int hd_create(int ensemble, int64_t m, int64_t n, int32_t T_max, uint64_t
 HD_API int hd_create_batched(int ensemble, int32_t count, const int64_t* m, const int64_t* n,
                              int32_t T_max, uint64_t seed, int dtype, hd_state** out);
 
+/* Per-trial entry scales of a Gin batch (count values, each finite and > 0): trial i's draws
+ * are sigma[i] N(0, 1), i.e. Q_i has entry variance sigma[i]^2 (e.g. 1/m_i for the AMP
+ * workload).  Before the first step only (HD_ERR_STATE otherwise); hd_set_options sets every
+ * trial back to its single sigma.  Haar states ignore the scales. */
+HD_API int hd_set_trial_sigmas(hd_state* st, const double* sigma);
+
 /* Packed layout of a state's vectors: *count trials; off_n and off_m (either may be NULL)
  * receive count + 1 offsets each (prefix sums of n[i] and m[i]). */
 HD_API int hd_get_batch_layout(const hd_state* st, int32_t* count, int64_t* off_n, int64_t* off_m);
@@ -111,11 +117,21 @@ HD_API int hd_apply(hd_state* st, const void* x, int transpose, void* y);
 HD_API int hd_probe(hd_state* st, const void* x, int transpose, void* y,
                     double* unrevealed_host);
 
-/* Built-in dynamics f_t for hd_run (elementwise, run in the library's kernels):
+/* Built-in dynamics f_t for hd_run (run in the library's kernels):
  *   HD_DYN_TANH       x_{t+1} = tanh(y_t)
  *   HD_DYN_SIGN_MEM   x_{t+1} = sign(y_t) + a x_{t-1}   (sign(0) = 0; x_0 = 0)
- *   HD_DYN_NORM_TANH  x_{t+1} = v/||v||, v = tanh(y_t) + a x_t                        */
-typedef enum { HD_DYN_TANH = 1, HD_DYN_SIGN_MEM = 2, HD_DYN_NORM_TANH = 3 } hd_dynamics;
+ *   HD_DYN_NORM_TANH  x_{t+1} = v/||v||, v = tanh(y_t) + a x_t      (single-trial states)
+ *   HD_DYN_AMP        approximate message passing for y = Q beta + w, per trial (one of the
+ *                     iterative algorithms eq. dynamics covers, Section 1).  Product 1 is
+ *                     Q beta (x1 = beta, n-space); then y = Q beta + w, z^0 = y, x^0 = 0, and
+ *                     the products alternate Q^T z^k (even t) and Q x^{k+1} (odd t):
+ *                       x^{k+1} = eta(x^k + Q^T z^k; a ||z^k|| / sqrt(m)),
+ *                       z^{k+1} = y - Q x^{k+1} + z^k ||x^{k+1}||_0 / m,
+ *                     eta the soft threshold, a the threshold multiplier (1.1 in the batched
+ *                     AMP workload), norms and counts per trial.  spec.aux = w (m-space);
+ *                     x_out receives the last x^k (n-space).  The schedule must be Q, Q^T,
+ *                     Q, ... (HD_ERR_ARG otherwise).                                       */
+typedef enum { HD_DYN_TANH = 1, HD_DYN_SIGN_MEM = 2, HD_DYN_NORM_TANH = 3, HD_DYN_AMP = 4 } hd_dynamics;
 
 typedef struct {
   int32_t T;                 /* number of products, 1 <= T <= T_max                      */
@@ -126,6 +142,9 @@ typedef struct {
                                 replay it on later calls with the same (T, flags,
                                 dynamics, a); the first call with use_graph must not
                                 happen while the state's stream is being captured       */
+  const void* aux;           /* HD_DYN_AMP: the noise w (packed m-space vector, device or
+                                page-locked host, copied at the start of every call);
+                                ignored otherwise                                       */
 } hd_run_spec;
 
 /* A whole trajectory of eq. (dynamics): resets the state (same seed, trial and sigma),
@@ -135,7 +154,8 @@ typedef struct {
  * with cudaMemcpyAsync, cudaMemcpyDefault); they are read/written on the stream.  Every
  * step's input dimension must match the previous output (HD_ERR_DIM otherwise: for a
  * rectangular Gin, Q and Q^T must alternate).  Work vectors are allocated by the state
- * on the first call (3 x max(m, n) elements). */
+ * on the first call (3 x max(m, n) elements; HD_DYN_AMP adds 3 x m + 2 x n).  Batched
+ * states: every vector is packed (hd_get_batch_layout). */
 HD_API int hd_run(hd_state* st, const hd_run_spec* spec, const void* x1, void* x_out);
 
 /* Synchronise the state's stream and check the device error word: returns HD_ERR_TIMEOUT

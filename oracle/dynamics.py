@@ -7,6 +7,8 @@ them and shares nothing with this file.
   tanh       x_{t+1} = tanh(y_t)                                (Ginibre, all Q)
   sign_mem   x_{t+1} = sign(y_t) + 0.5 x_{t-1}, x_0 = 0, sign(0) = 0   (Haar, Q / Q^T alternating)
   norm_tanh  x_{t+1} = normalize(tanh(y_t) + 0.1 x_t)          (Haar, all Q)
+  amp        approximate message passing for y = Q beta + w (the AMP family the paper
+             lists among its target dynamics in Section 1), soft threshold 1.1 sigma_t
 The schedule helpers return the transpose flag of step t (1-based).
 """
 import numpy as np
@@ -53,3 +55,36 @@ def run(state, x1, T, f, schedule, x0=None):
         x_prev, x = x, x_next
         xs.append(x)
     return xs, ys
+
+
+def soft_threshold(r, theta):
+    return np.sign(r) * np.maximum(np.abs(r) - theta, 0.0)
+
+
+def amp(state, beta, w, T, thr=1.1):
+    """T products of AMP for the linear model y = Q beta + w, Q in R^{m x n}.
+
+    Product 1 is Q beta (then y = Q beta + w, z^0 = y, x^0 = 0); after that the products
+    alternate Q^T z^k (even t) and Q x^{k+1} (odd t):
+        x^{k+1} = eta(x^k + Q^T z^k; theta_k),  theta_k = thr * ||z^k|| / sqrt(m)
+        z^{k+1} = y - Q x^{k+1} + z^k ||x^{k+1}||_0 / m      (the Onsager term)
+    with eta the soft threshold.  Returns (xs, zs): the x^k after each Q^T product and the
+    z^k (z^0 first).
+    """
+    beta = np.asarray(beta, dtype=np.float64)
+    w = np.asarray(w, dtype=np.float64)
+    m = w.shape[0]
+    y = np.asarray(state.apply(beta, transpose=False), dtype=np.float64) + w
+    z = y.copy()
+    x = np.zeros_like(beta)
+    xs, zs = [], [z]
+    for t in range(2, T + 1):
+        if t % 2 == 0:
+            r = x + np.asarray(state.apply(z, transpose=True), dtype=np.float64)
+            x = soft_threshold(r, thr * np.linalg.norm(z) / np.sqrt(m))
+            xs.append(x)
+        else:
+            q = np.asarray(state.apply(x, transpose=False), dtype=np.float64)
+            z = y - q + z * (np.count_nonzero(x) / m)
+            zs.append(z)
+    return xs, zs

@@ -20,13 +20,14 @@ DTYPES = {"f64": HD_F64, "f32": HD_F32}
 
 _LIB = None
 
-HD_DYN_TANH, HD_DYN_SIGN_MEM, HD_DYN_NORM_TANH = 1, 2, 3
-DYNAMICS = {"tanh": HD_DYN_TANH, "sign_mem": HD_DYN_SIGN_MEM, "norm_tanh": HD_DYN_NORM_TANH}
+HD_DYN_TANH, HD_DYN_SIGN_MEM, HD_DYN_NORM_TANH, HD_DYN_AMP = 1, 2, 3, 4
+DYNAMICS = {"tanh": HD_DYN_TANH, "sign_mem": HD_DYN_SIGN_MEM, "norm_tanh": HD_DYN_NORM_TANH, "amp": HD_DYN_AMP}
 
 
 class hd_run_spec(ctypes.Structure):
     _fields_ = [("T", ctypes.c_int32), ("transpose", ctypes.POINTER(ctypes.c_uint8)),
-                ("dynamics", ctypes.c_int32), ("a", ctypes.c_double), ("use_graph", ctypes.c_int32)]
+                ("dynamics", ctypes.c_int32), ("a", ctypes.c_double), ("use_graph", ctypes.c_int32),
+                ("aux", ctypes.c_void_p)]
 
 _c = ctypes
 _P = _c.c_void_p
@@ -37,6 +38,7 @@ _PROTOS = {
     "hd_create_batched": (_c.c_int, [_c.c_int, _c.c_int32, _P, _P, _c.c_int32, _c.c_uint64, _c.c_int,
                                      _c.POINTER(_P)]),
     "hd_get_batch_layout": (_c.c_int, [_P, _c.POINTER(_c.c_int32), _P, _P]),
+    "hd_set_trial_sigmas": (_c.c_int, [_P, _P]),
     "hd_adjoint_enable": (_c.c_int, [_P, _c.c_int]),
     "hd_adjoint_step": (_c.c_int, [_P, _P, _P, _P]),
     "hd_adjoint_restart": (_c.c_int, [_P]),
@@ -210,12 +212,17 @@ def hd_probe(state, x, transpose, y):
     return u.value
 
 
-def make_run_spec(transpose_flags, dynamics, a=0.0, use_graph=True):
-    """hd_run_spec for a schedule (sequence of 0/1 flags) and a built-in dynamics name/code."""
+def make_run_spec(transpose_flags, dynamics, a=0.0, use_graph=True, aux=None):
+    """hd_run_spec for a schedule (sequence of 0/1 flags) and a built-in dynamics name/code.
+    aux: HD_DYN_AMP's noise vector w (CUDA or page-locked tensor, or an address)."""
     flags = (ctypes.c_uint8 * len(transpose_flags))(*[1 if f else 0 for f in transpose_flags])
+    aux_addr = None
+    if aux is not None:
+        aux_addr = aux if isinstance(aux, int) else aux.data_ptr()
     spec = hd_run_spec(len(transpose_flags), ctypes.cast(flags, ctypes.POINTER(ctypes.c_uint8)),
-                       DYNAMICS.get(dynamics, dynamics), float(a), 1 if use_graph else 0)
+                       DYNAMICS.get(dynamics, dynamics), float(a), 1 if use_graph else 0, aux_addr)
     spec._flags = flags  # keep the array alive with the struct
+    spec._aux = aux
     return spec
 
 
@@ -289,6 +296,12 @@ def hd_philox_words(seed, counters, nblocks, out, stream=None):
                                  _ptr(out, what="out"), _stream_ptr(stream)), "hd_philox_words")
 
 
+def hd_set_trial_sigmas(state, sigmas):
+    import numpy as np
+    a = np.ascontiguousarray(sigmas, dtype=np.float64)
+    _check(lib().hd_set_trial_sigmas(state, a.ctypes.data), "hd_set_trial_sigmas")
+
+
 class HDBatch:
     """Owner of a batched hd_state: `count` independent trials, packed vectors."""
 
@@ -315,6 +328,9 @@ class HDBatch:
 
     def reset(self, seed):
         hd_reset(self.h, seed)
+
+    def set_trial_sigmas(self, sigmas):
+        hd_set_trial_sigmas(self.h, sigmas)
 
     def close(self):
         if self.h:

@@ -415,7 +415,7 @@ int adj_step(hd_state* st, const void* ybar, const void* x_in, void* xbar) {
       // is complete; g is constant
       const double* ubar_b = A.Bbar[e] + (int64_t)kD * lde;
       DrawKey key = key_for(st, t);
-      k_draw_d<T><<<gv, kAT, 0, c.s>>>(key, kN, ne, (T)st->sigma, Se.dpre + kN, gd);
+      k_draw_d<T><<<gv, kAT, 0, c.s>>>(key, kN, ne, (T)td.sigma, Se.dpre + kN, gd);
       colpass<T>(c, Ve, Se.ld, kN, ne, ubar_b, -1.0, bbu, gd, 1.0, au);
       k_tri<<<1, kAT, 0, c.s>>>(Se.S, Tm, kN, au, 1.0, 0, bu);
       k_tri<<<1, kAT, 0, c.s>>>(Se.S, Tm, kN, bbu, 1.0, 1, abu);

@@ -94,10 +94,9 @@ BatchStep<T> make_batch(const hd_state* st, int d, int kD, int kN, const void* x
 
 template <typename T>
 int first_draws(hd_state* st) {
-  const T sigma = (st->ens == HD_GINIBRE) ? (T)st->sigma : T(1);
   BatchStep<T> b = make_batch<T>(st, 0, 0, 0, nullptr, nullptr);
   for (int s = 0; s < 2; s++) {
-    cudaError_t e = launch_first_draw<T>(b, s, key_for(st, 1), sigma, st->stream);
+    cudaError_t e = launch_first_draw<T>(b, s, key_for(st, 1), st->stream);
     if (e != cudaSuccess) return cuda_fail(st, e);
   }
   st->drawn = 1;
@@ -202,9 +201,72 @@ int run_steps(hd_state* st, const hd_run_spec* sp) {
   return HD_OK;
 }
 
+// HD_DYN_AMP: product 1 is Q beta, then Q^T z^k and Q x^{k+1} alternate (flags checked by
+// hd_run); the AMP updates run per trial between the products.
+template <typename T>
+int run_amp(hd_state* st, const hd_run_spec* sp) {
+  if (st->prof_on) st->prof_used = 0;
+  st->t = st->r = st->l = 0;
+  st->drawn = 0;
+  if (int rc = adj_on_reset(st)) return rc;
+  const int cnt = st->count;
+  const int64_t ntot = st->off[0][cnt];
+  cudaError_t e = cudaMemsetAsync(st->amp_x, 0, (size_t)ntot * st->esz, st->stream);
+  if (e != cudaSuccess) return cuda_fail(st, e);
+  for (int t = 1; t <= sp->T; t++) {
+    int rc;
+    if (t == 1) {
+      rc = do_step<T>(st, st->xw[0], 0, st->yw);
+      if (!rc) e = launch_amp_init<T>(cnt, st->d_off[1], (const T*)st->yw, (const T*)st->amp_w,
+                                      (T*)st->amp_y, (T*)st->amp_z, st->amp_zsq, st->stream);
+    } else if (t % 2 == 0) {
+      rc = do_step<T>(st, st->amp_z, 1, st->yw);
+      if (!rc) e = launch_amp_x<T>(cnt, st->d_off[0], st->d_off[1], (const T*)st->yw, (T*)st->amp_x,
+                                   st->amp_zsq, sp->a, st->amp_nnz, st->stream);
+    } else {
+      rc = do_step<T>(st, st->amp_x, 0, st->yw);
+      if (!rc) e = launch_amp_z<T>(cnt, st->d_off[1], (const T*)st->amp_y, (const T*)st->yw, (T*)st->amp_z,
+                                   st->amp_nnz, st->amp_zsq, st->stream);
+    }
+    if (rc) return rc;
+    if (e != cudaSuccess) return cuda_fail(st, e);
+    st->launches += 1;
+  }
+  return HD_OK;
+}
+
+int amp_buffers(hd_state* st) {
+  if (st->amp_y) return HD_OK;
+  const int cnt = st->count;
+  const size_t bm = (size_t)round_up(st->off[1][cnt], 64) * st->esz;
+  const size_t bn = (size_t)round_up(st->off[0][cnt], 64) * st->esz;
+  st->amp_y = dalloc(st, bm);
+  st->amp_z = dalloc(st, bm);
+  st->amp_w = dalloc(st, bm);
+  st->amp_x = dalloc(st, bn);
+  st->amp_zsq = (double*)dalloc(st, (size_t)cnt * sizeof(double));
+  st->amp_nnz = (int*)dalloc(st, (size_t)cnt * sizeof(int));
+  for (int s = 0; s < 2; s++) {
+    st->d_off[s] = (int64_t*)dalloc(st, (size_t)(cnt + 1) * sizeof(int64_t));
+    if (!st->d_off[s]) return HD_ERR_OOM;
+    if (cudaMemcpy(st->d_off[s], st->off[s].data(), (size_t)(cnt + 1) * sizeof(int64_t),
+                   cudaMemcpyHostToDevice) != cudaSuccess)
+      return cuda_fail(st, cudaGetLastError());
+  }
+  if (!st->amp_y || !st->amp_z || !st->amp_w || !st->amp_x || !st->amp_zsq || !st->amp_nnz) return HD_ERR_OOM;
+  return HD_OK;
+}
+
+int run_any(hd_state* st, const hd_run_spec* sp) {
+  if (sp->dynamics == HD_DYN_AMP)
+    return (st->dtype == HD_F64) ? run_amp<double>(st, sp) : run_amp<float>(st, sp);
+  return (st->dtype == HD_F64) ? run_steps<double>(st, sp) : run_steps<float>(st, sp);
+}
+
 bool graph_matches(const hd_state* st, const hd_run_spec* sp) {
   if (!st->gexec || st->g_T != sp->T || st->g_dyn != sp->dynamics || st->g_a != sp->a) return false;
   if (st->g_seed != st->seed || st->g_trial != st->trial || st->g_sigma != st->sigma) return false;
+  if (st->g_sigma_gen != st->sigma_gen) return false;
   if (st->g_stream != st->stream || st->g_prof != st->prof_on) return false;
   for (int t = 0; t < sp->T; t++)
     if (st->g_flags[t] != (sp->transpose[t] ? 1 : 0)) return false;
@@ -392,6 +454,7 @@ int create_common(int ensemble, int count, const int64_t* m, const int64_t* n, i
     ws.cnt = st->cnt + (size_t)i * 3 * (kMaxGroups + 1);
     ws.err = st->err;
     td.trial = (uint32_t)i;
+    td.sigma = 1.0;
   }
   st->ddesc = (TrialDesc*)dalloc(st, (size_t)count * sizeof(TrialDesc));
   if (!st->ddesc) return fail(HD_ERR_OOM);
@@ -426,7 +489,10 @@ int create_common(int ensemble, int count, const int64_t* m, const int64_t* n, i
 
 // Philox trial words of the trials: base + i.
 int upload_trials(hd_state* st) {
-  for (int i = 0; i < st->count; i++) st->hdesc[i].trial = st->trial + (uint32_t)i;
+  for (int i = 0; i < st->count; i++) {
+    st->hdesc[i].trial = st->trial + (uint32_t)i;
+    st->hdesc[i].sigma = (st->ens == HD_HAAR) ? 1.0 : (st->sigmas.empty() ? st->sigma : st->sigmas[i]);
+  }
   if (cudaMemcpy(st->ddesc, st->hdesc.data(), (size_t)st->count * sizeof(TrialDesc),
                  cudaMemcpyHostToDevice) != cudaSuccess) {
     set_error("trial upload", cudaGetLastError());
@@ -525,15 +591,28 @@ HD_API int hd_set_options(hd_state* st, double sigma, uint32_t trial, void* stre
   if (!st) return HD_ERR_ARG;
   if (!(sigma > 0.0) || !std::isfinite(sigma)) return HD_ERR_ARG;
   if (st->t > 0 && (sigma != st->sigma || trial != st->trial)) return HD_ERR_ARG;
+  const bool changed = trial != st->hdesc[0].trial || sigma != st->sigma || !st->sigmas.empty();
   st->sigma = sigma;
+  st->sigmas.clear();
   st->stream = (cudaStream_t)stream;
-  if (trial != st->hdesc[0].trial) {
-    st->trial = trial;
+  st->trial = trial;
+  if (changed) {
+    st->sigma_gen += 1;
     if (cudaSetDevice(st->device) != cudaSuccess) return cuda_fail(st, cudaErrorInvalidDevice);
     return upload_trials(st);
   }
-  st->trial = trial;
   return HD_OK;
+}
+
+HD_API int hd_set_trial_sigmas(hd_state* st, const double* sigma) {
+  if (!st || !sigma) return HD_ERR_ARG;
+  if (st->t > 0) return HD_ERR_STATE;
+  for (int i = 0; i < st->count; i++)
+    if (!(sigma[i] > 0.0) || !std::isfinite(sigma[i])) return HD_ERR_ARG;
+  st->sigmas.assign(sigma, sigma + st->count);
+  st->sigma_gen += 1;
+  if (cudaSetDevice(st->device) != cudaSuccess) return cuda_fail(st, cudaErrorInvalidDevice);
+  return upload_trials(st);
 }
 
 HD_API int hd_apply(hd_state* st, const void* x, int transpose, void* y) {
@@ -550,9 +629,16 @@ HD_API int hd_run(hd_state* st, const hd_run_spec* sp, const void* x1, void* x_o
   if (!st || !sp || !sp->transpose || !x1 || !x_out) return HD_ERR_ARG;
   if (st->poisoned) return st->poisoned;
   if (sp->T < 1 || sp->T > st->Tm) return HD_ERR_TMAX;
-  if (sp->dynamics != HD_DYN_TANH && sp->dynamics != HD_DYN_SIGN_MEM && sp->dynamics != HD_DYN_NORM_TANH)
+  if (sp->dynamics != HD_DYN_TANH && sp->dynamics != HD_DYN_SIGN_MEM && sp->dynamics != HD_DYN_NORM_TANH &&
+      sp->dynamics != HD_DYN_AMP)
     return HD_ERR_ARG;
   if (sp->dynamics == HD_DYN_NORM_TANH && st->count != 1) return HD_ERR_ARG;
+  const bool amp = sp->dynamics == HD_DYN_AMP;
+  if (amp) {
+    if (!sp->aux || st->ens != HD_GINIBRE) return HD_ERR_ARG;
+    for (int t = 0; t < sp->T; t++)
+      if ((sp->transpose[t] ? 1 : 0) != (t % 2)) return HD_ERR_ARG;   // Q, Q^T, Q, ...
+  }
   if (!std::isfinite(sp->a)) return HD_ERR_ARG;
   // dimensions: input of step t+1 = output of step t for every trial
   for (int t = 0; t + 1 < sp->T; t++) {
@@ -571,9 +657,15 @@ HD_API int hd_run(hd_state* st, const hd_run_spec* sp, const void* x1, void* x_o
     if (!st->xw[0] || !st->xw[1] || !st->yw || !st->sumsq) return HD_ERR_OOM;
   }
   const int64_t nin = st->off[sp->transpose[0] ? 1 : 0][st->count];
-  const int64_t nfin = st->off[sp->transpose[sp->T - 1] ? 0 : 1][st->count];
+  const int64_t nfin = amp ? st->off[0][st->count] : st->off[sp->transpose[sp->T - 1] ? 0 : 1][st->count];
+  if (amp) {
+    if (int rc0 = amp_buffers(st)) return rc0;
+  }
   cudaError_t e = cudaMemcpyAsync(st->xw[0], x1, (size_t)nin * st->esz, cudaMemcpyDefault, st->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(st->xw[1], 0, (size_t)dmax * st->esz, st->stream);
+  if (e == cudaSuccess && amp)
+    e = cudaMemcpyAsync(st->amp_w, sp->aux, (size_t)st->off[1][st->count] * st->esz, cudaMemcpyDefault,
+                        st->stream);
   if (e != cudaSuccess) {
     set_error("hd_run input copy", e);
     return cuda_fail(st, e);
@@ -603,7 +695,7 @@ HD_API int hd_run(hd_state* st, const hd_run_spec* sp, const void* x1, void* x_o
       }
       st->stream = cap;
       const int64_t l0 = st->launches;
-      rc = (st->dtype == HD_F64) ? run_steps<double>(st, sp) : run_steps<float>(st, sp);
+      rc = run_any(st, sp);
       st->g_launches = (int)(st->launches - l0);
       st->launches = l0;
       st->stream = user;
@@ -625,6 +717,7 @@ HD_API int hd_run(hd_state* st, const hd_run_spec* sp, const void* x1, void* x_o
       st->g_seed = st->seed;
       st->g_trial = st->trial;
       st->g_sigma = st->sigma;
+      st->g_sigma_gen = st->sigma_gen;
       st->g_stream = st->stream;
       st->g_flags.assign(sp->transpose, sp->transpose + sp->T);
       for (auto& f : st->g_flags) f = f ? 1 : 0;
@@ -643,10 +736,11 @@ HD_API int hd_run(hd_state* st, const hd_run_spec* sp, const void* x1, void* x_o
     st->drawn = 1;
     st->run_final = st->g_final;
   } else {
-    rc = (st->dtype == HD_F64) ? run_steps<double>(st, sp) : run_steps<float>(st, sp);
+    rc = run_any(st, sp);
     if (rc) return rc;
   }
-  e = cudaMemcpyAsync(x_out, st->xw[st->run_final], (size_t)nfin * st->esz, cudaMemcpyDefault, st->stream);
+  e = cudaMemcpyAsync(x_out, amp ? st->amp_x : st->xw[st->run_final], (size_t)nfin * st->esz, cudaMemcpyDefault,
+                      st->stream);
   if (e != cudaSuccess) {
     set_error("hd_run output copy", e);
     return cuda_fail(st, e);

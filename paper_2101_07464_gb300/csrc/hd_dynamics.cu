@@ -74,6 +74,111 @@ cudaError_t launch_dynamics(int kind, double a, const T* y, const T* xcur, const
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------------------------
+// AMP (one CTA per trial)
+constexpr int kAmpThreads = 256;
+
+__device__ __forceinline__ double amp_block_sum(double v, double* red) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double s = 0.0;
+#pragma unroll
+  for (int w = 0; w < kAmpThreads / 32; w++) s += red[w];
+  return s;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kAmpThreads) k_amp_init(const int64_t* offm, const T* __restrict__ q,
+                                                          const T* __restrict__ w, T* ymeas, T* z, double* zsq) {
+  __shared__ double red[kAmpThreads / 32];
+  const int i = blockIdx.x;
+  const int64_t r0 = offm[i], r1 = offm[i + 1];
+  double s = 0.0;
+  for (int64_t r = r0 + threadIdx.x; r < r1; r += kAmpThreads) {
+    const T v = q[r] + w[r];
+    ymeas[r] = v;
+    z[r] = v;
+    s = fma((double)v, (double)v, s);
+  }
+  s = amp_block_sum(s, red);
+  if (threadIdx.x == 0) zsq[i] = s;
+}
+
+template <typename T>
+__device__ __forceinline__ T soft_thr(T r, T theta) {
+  const T a = fabs(r) - theta;
+  return (a > T(0)) ? copysign(a, r) : T(0);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kAmpThreads) k_amp_x(const int64_t* offn, const int64_t* offm,
+                                                       const T* __restrict__ sv, T* x, const double* zsq,
+                                                       double a, int* nnz) {
+  __shared__ double red[kAmpThreads / 32];
+  const int i = blockIdx.x;
+  const int64_t r0 = offn[i], r1 = offn[i + 1];
+  const double mi = (double)(offm[i + 1] - offm[i]);
+  const T theta = (T)(a * sqrt(zsq[i] / mi));
+  double c = 0.0;
+  for (int64_t r = r0 + threadIdx.x; r < r1; r += kAmpThreads) {
+    const T v = soft_thr(x[r] + sv[r], theta);
+    x[r] = v;
+    c += (v != T(0)) ? 1.0 : 0.0;
+  }
+  c = amp_block_sum(c, red);
+  if (threadIdx.x == 0) nnz[i] = (int)c;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kAmpThreads) k_amp_z(const int64_t* offm, const T* __restrict__ ymeas,
+                                                       const T* __restrict__ q, T* z, const int* nnz, double* zsq) {
+  __shared__ double red[kAmpThreads / 32];
+  const int i = blockIdx.x;
+  const int64_t r0 = offm[i], r1 = offm[i + 1];
+  const T ons = (T)((double)nnz[i] / (double)(r1 - r0));
+  double s = 0.0;
+  for (int64_t r = r0 + threadIdx.x; r < r1; r += kAmpThreads) {
+    const T v = fma(z[r], ons, ymeas[r] - q[r]);
+    z[r] = v;
+    s = fma((double)v, (double)v, s);
+  }
+  s = amp_block_sum(s, red);
+  if (threadIdx.x == 0) zsq[i] = s;
+}
+
+template <typename T>
+cudaError_t launch_amp_init(int count, const int64_t* offm, const T* q, const T* w, T* ymeas, T* z,
+                            double* zsq, cudaStream_t s) {
+  k_amp_init<T><<<count, kAmpThreads, 0, s>>>(offm, q, w, ymeas, z, zsq);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_amp_x(int count, const int64_t* offn, const int64_t* offm, const T* sv, T* x,
+                         const double* zsq, double a, int* nnz, cudaStream_t s) {
+  k_amp_x<T><<<count, kAmpThreads, 0, s>>>(offn, offm, sv, x, zsq, a, nnz);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_amp_z(int count, const int64_t* offm, const T* ymeas, const T* q, T* z, const int* nnz,
+                         double* zsq, cudaStream_t s) {
+  k_amp_z<T><<<count, kAmpThreads, 0, s>>>(offm, ymeas, q, z, nnz, zsq);
+  return cudaGetLastError();
+}
+
+#define HD_AMP_INST(T)                                                                               \
+  template cudaError_t launch_amp_init<T>(int, const int64_t*, const T*, const T*, T*, T*, double*,  \
+                                          cudaStream_t);                                             \
+  template cudaError_t launch_amp_x<T>(int, const int64_t*, const int64_t*, const T*, T*,            \
+                                       const double*, double, int*, cudaStream_t);                   \
+  template cudaError_t launch_amp_z<T>(int, const int64_t*, const T*, const T*, T*, const int*,      \
+                                       double*, cudaStream_t);
+HD_AMP_INST(float)
+HD_AMP_INST(double)
+#undef HD_AMP_INST
+
 template cudaError_t launch_dynamics<float>(int, double, const float*, const float*, const float*,
                                             float*, int64_t, double*, cudaStream_t, bool);
 template cudaError_t launch_dynamics<double>(int, double, const double*, const double*,

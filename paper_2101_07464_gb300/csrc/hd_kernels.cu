@@ -118,6 +118,7 @@ __device__ __forceinline__ StepPlan<T> make_plan(const BatchStep<T>& b, int spac
   p.ldBd = td.ldb[d];
   p.Bn = td.basis[1 - d];
   p.ldBn = td.ldb[1 - d];
+  p.sigma = (T)td.sigma;
   p.ws = td.ws;
   p.key_next.trial = td.trial;
   p.x = b.base.x ? b.base.x + td.off[d] : nullptr;
@@ -148,7 +149,7 @@ __device__ __forceinline__ T dot_vec(const Vec<T>& a, const Vec<T>& b, T acc) {
 // First draw g_1 of a space (rows >= 0) into the buffer of the stack acting on that space,
 // for every trial, with its squared norm over rows > 0.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_first_draw(BatchStep<T> b, int space, DrawKey key, T sigma) {
+__global__ void __launch_bounds__(kThreads) k_first_draw(BatchStep<T> b, int space, DrawKey key) {
   __shared__ double red[kWarps];
   CtaCtx c;
   const CtaMap& m = b.map[space];
@@ -160,6 +161,7 @@ __global__ void __launch_bounds__(kThreads) k_first_draw(BatchStep<T> b, int spa
   const TrialDesc& td = b.desc[c.trial];
   const StackDev X = td.st[space];
   key.trial = td.trial;
+  const T sigma = (T)td.sigma;
   const int64_t nsub = (X.dim + 31) / 32;
   const int64_t s0 = (int64_t)c.local * c.spc, s1 = min(nsub, s0 + c.spc);
   T* gb = (T*)X.gbuf;
@@ -944,8 +946,8 @@ __global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_out_gin(BatchStep
 
 // ------------------------------------------------------------------------------------
 template <typename T>
-cudaError_t launch_first_draw(const BatchStep<T>& b, int space, DrawKey key, T sigma, cudaStream_t s) {
-  k_first_draw<T><<<b.map[space].ctas, kThreads, 0, s>>>(b, space, key, sigma);
+cudaError_t launch_first_draw(const BatchStep<T>& b, int space, DrawKey key, cudaStream_t s) {
+  k_first_draw<T><<<b.map[space].ctas, kThreads, 0, s>>>(b, space, key);
   return cudaGetLastError();
 }
 
@@ -1055,8 +1057,8 @@ int kernel_occupancy(int which, size_t dynsmem) {
 template int kernel_occupancy<float>(int, size_t);
 template int kernel_occupancy<double>(int, size_t);
 
-template cudaError_t launch_first_draw<float>(const BatchStep<float>&, int, DrawKey, float, cudaStream_t);
-template cudaError_t launch_first_draw<double>(const BatchStep<double>&, int, DrawKey, double, cudaStream_t);
+template cudaError_t launch_first_draw<float>(const BatchStep<float>&, int, DrawKey, cudaStream_t);
+template cudaError_t launch_first_draw<double>(const BatchStep<double>&, int, DrawKey, cudaStream_t);
 template cudaError_t launch_step<float>(const BatchStep<float>&, cudaStream_t, cudaEvent_t*, int*);
 template cudaError_t launch_step<double>(const BatchStep<double>&, cudaStream_t, cudaEvent_t*, int*);
 

@@ -120,6 +120,7 @@ struct TrialDesc {
   Ws ws;
   uint32_t trial;       // Philox trial word
   int64_t off[2];       // offset of the trial's vector in packed n-space / m-space buffers
+  double sigma;         // entry scale of the trial's draws (Ginibre), 1 for Haar
 };
 
 struct CtaMap {
@@ -138,7 +139,7 @@ struct BatchStep {
 };
 
 template <typename T>
-cudaError_t launch_first_draw(const BatchStep<T>& b, int space, DrawKey key, T sigma,
+cudaError_t launch_first_draw(const BatchStep<T>& b, int space, DrawKey key,
                               cudaStream_t s);
 // ev (optional): start/stop event pairs recorded around K1, K2, K3 (ev[2*kind], ev[2*kind+1]);
 // a null entry skips the record.  launched[kind] is set to 1 for each sweep launched.

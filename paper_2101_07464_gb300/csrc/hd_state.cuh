@@ -43,6 +43,8 @@ struct hd_state {
   uint64_t seed = 0;
   uint32_t trial = 0;            // Philox trial word of trial 0 (trial i uses trial + i)
   double sigma = 1.0;
+  std::vector<double> sigmas;    // per-trial entry scales (hd_set_trial_sigmas); empty: all sigma
+  int64_t sigma_gen = 0;         // bumped whenever the draw scales change
   cudaStream_t stream = nullptr;
   int device = 0;
   int t = 0, r = 0, l = 0;
@@ -74,6 +76,7 @@ struct hd_state {
   std::vector<uint8_t> g_flags;
   int g_T = 0, g_dyn = 0;
   double g_a = 0.0, g_sigma = 0.0;
+  int64_t g_sigma_gen = -1;
   uint64_t g_seed = 0;
   uint32_t g_trial = 0;
   cudaStream_t g_stream = nullptr;
@@ -92,6 +95,14 @@ struct hd_state {
   int64_t prof_n[3] = {0, 0, 0};
   double prof_b[3] = {0, 0, 0};
   hd::AdjState* adj = nullptr;   // reverse mode (hd_adjoint_enable)
+  // hd_run with HD_DYN_AMP: packed per-trial vectors and scalars (allocated on first use)
+  void* amp_y = nullptr;         // y = Q beta + w (m-space)
+  void* amp_z = nullptr;         // z^k (m-space)
+  void* amp_x = nullptr;         // x^k (n-space)
+  void* amp_w = nullptr;         // the caller's w, copied (m-space)
+  double* amp_zsq = nullptr;     // ||z^k||^2 per trial
+  int* amp_nnz = nullptr;        // ||x^k||_0 per trial
+  int64_t* d_off[2] = {nullptr, nullptr};   // packed offsets per space on the device
 };
 
 namespace hd {

@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 side measurement")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--no-amp", action="store_true", help="skip the batched AMP measurement")
+    ap.add_argument("--amp-trials", type=int, default=4096)
     return ap.parse_args()
 
 
@@ -222,6 +224,56 @@ def profile_kernels(st, spec, x1, xout, steps):
     return prof
 
 
+def measure_amp_batch(args, rank, world, dist):
+    """Batched AMP workload: `amp_trials` independent Gin(m_i, n_i) trials in one state,
+    n_i ~ U{1000..100000}, m_i = n_i / 2, entries N(0, 1/m_i), beta ~ Bernoulli(0.1) N(0, 1),
+    w ~ N(0, 0.1^2), T = 30 products (Q beta, then Q^T z / Q x alternating), soft threshold
+    1.1 ||z|| / sqrt(m), FP32 storage; one hd_run call (one CUDA graph) per trajectory."""
+    import numpy as np
+    import torch
+    import synth
+    import paper_2101_07464_gb300 as hd
+    count, T = args.amp_trials, 30
+    ns = synth.batch_sizes(count, 1000, 100000, args.seed + rank)
+    ms = ns // 2
+    b = hd.HDBatch("ginibre", ms, ns, T, args.seed, "f32", trial=rank * count)
+    b.set_trial_sigmas(1.0 / np.sqrt(ms.astype(np.float64)))
+    beta = np.concatenate([synth.bernoulli_gauss(int(n), args.seed, trial=i, dtype=np.float32)
+                           for i, n in enumerate(ns)])
+    w = np.concatenate([synth.noise(int(m), args.seed, trial=i, dtype=np.float32) for i, m in enumerate(ms)])
+    bt = torch.from_numpy(beta).cuda()
+    wt = torch.from_numpy(w).cuda()
+    out = torch.empty_like(bt)
+    spec = hd.make_run_spec([t % 2 == 0 for t in range(1, T + 1)], "amp", 1.1, use_graph=True, aux=wt)
+    for _ in range(2):
+        hd.hd_run(b.h, spec, bt, out)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    steps = 3
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        hd.hd_run(b.h, spec, bt, out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    secs = e0.elapsed_time(e1) / 1e3 / steps
+    if dist is not None:
+        tt = torch.tensor([secs], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        secs = float(tt.item())
+    mse = float(((out.double() - bt.double()) ** 2).sum().item() / float(ns.sum()))
+    sum_n, sum_mn = float(ns.sum()), float((ns + ms).sum())
+    credited = sum_mn * 4.0 * T * (T + 1) / 2.0
+    b.close()
+    return {"metric": "trials*n*T^2/s", "value": sum_n * T * T * world / secs,
+            "ms_per_trajectory": secs * 1e3, "trials": count * world, "sum_n": sum_n * world, "T": T,
+            "dtype": "f32 (FP64 coefficients)", "graph": "one CUDA graph per trajectory",
+            "credited_GBps": credited / secs / 1e9, "mse": mse,
+            "config": "Gin(m_i, n_i), n_i ~ U{1000..100000}, m_i = n_i/2, AMP soft threshold 1.1 sigma_t"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -312,6 +364,10 @@ def run_ours(args):
         fp64 = {"value": units / (secs64 / args.steps), "ms_per_step": secs64 / args.steps * 1e3,
                 "unit": UNIT}
 
+    amp = None
+    if not args.no_amp:
+        amp = measure_amp_batch(args, rank, world, dist)
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         done, csecs, thr = oracle_sample(n, T, args.seed, budget_s=15.0)
@@ -333,7 +389,7 @@ def run_ours(args):
                 "roofline": roofline,
                 "step_credited_GBps": step_gbps,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk, "fp64": fp64}
+                "clocks": clk, "fp64": fp64, "batched_amp": amp}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

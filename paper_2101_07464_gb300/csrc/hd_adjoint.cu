@@ -350,7 +350,7 @@ int adj_step(hd_state* st, const void* ybar, const void* x_in, void* xbar) {
   const int Kfin_d = haar ? st->t : (d == 0 ? st->r : st->l);
   const T* Vd = (const T*)Sd.V;
   const T* Ve = (const T*)Se.V;
-  const int Tm = st->Tm;
+  const int Tm = st->Sld;   // leading dimension of S and Sbar
   const Ctx c{st, st->stream, 0};
   const int64_t L = A.dmax;
   double* xd = A.vec + kVx * L;
@@ -454,7 +454,7 @@ int adj_zero(hd_state* st) {
   const TrialDesc& td = st->hdesc[0];
   for (int s = 0; s < 2; s++) {
     if (cudaMemsetAsync(A.Vbar[s], 0, (size_t)td.st[s].ld * st->Tm * sizeof(double), st->stream) != cudaSuccess ||
-        cudaMemsetAsync(A.Sbar[s], 0, (size_t)st->Tm * st->Tm * sizeof(double), st->stream) != cudaSuccess)
+        cudaMemsetAsync(A.Sbar[s], 0, (size_t)st->Sld * st->Sld * sizeof(double), st->stream) != cudaSuccess)
       return cuda_fail(st, cudaGetLastError());
     if (A.Bbar[s] && cudaMemsetAsync(A.Bbar[s], 0, (size_t)td.ldb[s] * st->Tm * sizeof(double), st->stream) != cudaSuccess)
       return cuda_fail(st, cudaGetLastError());
@@ -511,7 +511,7 @@ HD_API int hd_adjoint_enable(hd_state* st, int flags) {
     const int Tm = st->Tm;
     for (int s = 0; s < 2; s++) {
       A->Vbar[s] = (double*)dalloc(st, (size_t)td.st[s].ld * Tm * sizeof(double));
-      A->Sbar[s] = (double*)dalloc(st, (size_t)Tm * Tm * sizeof(double));
+      A->Sbar[s] = (double*)dalloc(st, (size_t)st->Sld * st->Sld * sizeof(double));
       if (!A->Vbar[s] || !A->Sbar[s]) return HD_ERR_OOM;
       if (st->ens == HD_GINIBRE) {
         A->Bbar[s] = (double*)dalloc(st, (size_t)td.ldb[s] * Tm * sizeof(double));

@@ -68,7 +68,7 @@ BatchStep<T> make_batch(const hd_state* st, int d, int kD, int kN, const void* x
   memset(&b, 0, sizeof(b));
   StepPlan<T>& p = b.base;
   p.ens = st->ens;
-  p.Tm = st->Tm;
+  p.Tm = st->Sld;   // leading dimension of S
   p.kD = kD;
   p.kN = kN;
   p.x = (const T*)x;
@@ -377,6 +377,8 @@ int create_common(int ensemble, int count, const int64_t* m, const int64_t* n, i
   for (int s = 0; s < 2; s++)
     if (!build_map(st, s)) return fail(HD_ERR_OOM);
   const int64_t Tm = T_max;
+  const int64_t Sld = (T_max + 1) / 2 * 2;   // even: every column of S starts 16-byte aligned
+  st->Sld = (int)Sld;
   const size_t es = st->esz;
   // per-space packed stacks: trial i at element offset voff[s][i] (ld_i = round_up(dim, 256))
   std::vector<int64_t> ld[2], voff[2], goff[2];
@@ -401,7 +403,7 @@ int create_common(int ensemble, int count, const int64_t* m, const int64_t* n, i
   for (int s = 0; s < 2; s++) {
     V[s] = dalloc(st, (size_t)vtot[s] * es);
     G[s] = dalloc(st, (size_t)gtot[s] * es);
-    S[s] = (double*)dalloc(st, (size_t)count * Tm * Tm * 8);
+    S[s] = (double*)dalloc(st, (size_t)count * Sld * Sld * 8);
     DP[s] = (double*)dalloc(st, (size_t)count * (Tm + 1) * 8);
     GD[s] = (double*)dalloc(st, (size_t)count * (Tm + 1) * 8);
     GG[s] = (double*)dalloc(st, (size_t)count * 8);
@@ -430,7 +432,7 @@ int create_common(int ensemble, int count, const int64_t* m, const int64_t* n, i
       X.V = (char*)V[s] + (size_t)voff[s][i] * es;
       X.ld = ld[s][i];
       X.dim = st->dims[s][i];
-      X.S = S[s] + (size_t)i * Tm * Tm;
+      X.S = S[s] + (size_t)i * Sld * Sld;
       X.dpre = DP[s] + (size_t)i * (Tm + 1);
       X.gbuf = (char*)G[s] + (size_t)goff[s][i] * es;
       X.gdot = GD[s] + (size_t)i * (Tm + 1);
@@ -463,7 +465,7 @@ int create_common(int ensemble, int count, const int64_t* m, const int64_t* n, i
   for (int s = 0; s < 2 && ok; s++) {
     ok = cudaMemset(V[s], 0, (size_t)vtot[s] * es) == cudaSuccess &&
          cudaMemset(G[s], 0, (size_t)gtot[s] * es) == cudaSuccess &&
-         cudaMemset(S[s], 0, (size_t)count * Tm * Tm * 8) == cudaSuccess &&
+         cudaMemset(S[s], 0, (size_t)count * Sld * Sld * 8) == cudaSuccess &&
          cudaMemset(GD[s], 0, (size_t)count * (Tm + 1) * 8) == cudaSuccess &&
          cudaMemset(GG[s], 0, (size_t)count * 8) == cudaSuccess;
     if (ok && B[s]) ok = cudaMemset(B[s], 0, (size_t)vtot[s] * es) == cudaSuccess;

@@ -185,21 +185,192 @@ __global__ void __launch_bounds__(kThreads) k_first_draw(BatchStep<T> b, int spa
 }
 
 // ------------------------------------------------------------------------------------
+// CTA-wide helpers of the finalisations (every thread of the CTA calls them).  The small
+// matrices they read (S, the head block of V) are in L2 or DRAM.  They are copied into shared
+// memory with one bulk copy per column, all in flight at once on one mbarrier (a single
+// memory round trip); when a matrix does not fit in the free shared memory the product reads
+// it from global memory instead.
+
+__device__ __forceinline__ uint32_t smem_u32(const void* ptr) {
+  return (uint32_t)__cvta_generic_to_shared(ptr);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, unsigned parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+// One staging round: the CTA's threads issue bulk copies (issue(tid) returns nothing), thread 0
+// posts the byte count; everyone waits, at most kStageSpins polls, for the copies.  On a
+// timeout the error word is set and false returned (the caller then skips the product).
+constexpr unsigned kStageSpins = 1u << 22;
+struct Stager {
+  uint64_t* bar;
+  unsigned parity;
+  unsigned* err;
+  template <typename Issue>
+  __device__ bool run(unsigned bytes, Issue issue) {
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0) mbar_arrive_tx(bar, bytes);
+    issue();
+    unsigned spins = 0;
+    bool ok = true;
+    while (!mbar_test(bar, parity)) {
+      if (++spins > kStageSpins) {
+        ok = false;
+        if (threadIdx.x == 0 && err) atomicOr(err, 1u);
+        break;
+      }
+    }
+    parity ^= 1u;
+    __syncthreads();
+    return ok;
+  }
+};
+
+// Packed upper triangle: column c holds rows 0..c, padded to an even count (16-byte copies).
+__device__ __forceinline__ int64_t up_off(int c) {
+  return (c & 1) ? (int64_t)(c + 1) * (c + 1) / 2 : (int64_t)c * c / 2 + c;
+}
+__device__ __forceinline__ bool stage_upper(Stager& sg, const double* S, int Sld, int k, double* dst) {
+  return sg.run((unsigned)(up_off(k) * 8), [&]() {
+    for (int c = threadIdx.x; c < k; c += blockDim.x)
+      bulk_g2s(dst + up_off(c), S + (int64_t)c * Sld, (unsigned)(((c + 2) & ~1) * 8), sg.bar);
+  });
+}
+// Columns 0..ncol-1, rows 0..rows-1 of a stack, padded to 16 bytes: column j at j * Lv.
+template <typename T>
+__device__ __forceinline__ int stage_lv(int rows) {
+  return (rows * (int)sizeof(T) + 15) / 16 * (16 / (int)sizeof(T));
+}
+template <typename T>
+__device__ __forceinline__ bool stage_cols(Stager& sg, const T* V, int64_t ld, int rows, int ncol, T* dst) {
+  const int Lv = stage_lv<T>(rows);
+  return sg.run((unsigned)((int64_t)Lv * ncol * sizeof(T)), [&]() {
+    for (int j = threadIdx.x; j < ncol; j += blockDim.x)
+      bulk_g2s(dst + (int64_t)j * Lv, V + (int64_t)j * ld, (unsigned)(Lv * sizeof(T)), sg.bar);
+  });
+}
+
+// FP64 on this GPU has a long dependent latency (about 65 cycles per FMA), so the products below
+// split every row or column sum over a group of G lanes (G a power of two, G * rows <= CTA
+// threads), each lane with two interleaved accumulators, and add the group's lanes with
+// shuffles in a fixed order (deterministic).
+__device__ __forceinline__ int lanes_per_item(int items) {
+  int G = 32;
+  while (G > 1 && G * items > (int)blockDim.x) G >>= 1;
+  return G;
+}
+__device__ __forceinline__ double group_sum(double s, int G) {
+  for (int o = G >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
+// o_r[j] = sc_r sum_{i >= j} S[j, i] f_r[i] (j < k) from the packed upper triangle Su (or, when
+// Su is null, from S in global memory).
+template <int NR>
+__device__ void upper_mv(const double* Su, const double* S, int Sld, int k, const double* f1, const double* f2,
+                         double* o1, double sc1, double* o2, double sc2) {
+  const int G = lanes_per_item(k);
+  const int groups = blockDim.x / G, g = threadIdx.x % G;
+  const int iters = (k + groups - 1) / groups;
+  for (int it = 0; it < iters; it++) {
+    const int j = it * groups + (int)threadIdx.x / G;
+    double a0 = 0.0, a1 = 0.0, b0 = 0.0, b1 = 0.0;
+    if (j < k) {
+      int i = j + g;
+      for (; i + G < k; i += 2 * G) {
+        const double s0 = Su ? Su[up_off(i) + j] : S[j + (int64_t)i * Sld];
+        const double s1 = Su ? Su[up_off(i + G) + j] : S[j + (int64_t)(i + G) * Sld];
+        a0 = fma(s0, f1[i], a0);
+        a1 = fma(s1, f1[i + G], a1);
+        if (NR > 1) {
+          b0 = fma(s0, f2[i], b0);
+          b1 = fma(s1, f2[i + G], b1);
+        }
+      }
+      if (i < k) {
+        const double s0 = Su ? Su[up_off(i) + j] : S[j + (int64_t)i * Sld];
+        a0 = fma(s0, f1[i], a0);
+        if (NR > 1) b0 = fma(s0, f2[i], b0);
+      }
+    }
+    const double r1 = group_sum(a0 + a1, G);
+    const double r2 = (NR > 1) ? group_sum(b0 + b1, G) : 0.0;
+    if (j < k && g == 0) {
+      o1[j] = sc1 * r1;
+      if (NR > 1) o2[j] = sc2 * r2;
+    }
+  }
+  __syncthreads();
+}
+
+// out[j] = sum_{lo_j <= i <= hi_j} A[i, j] v[i] (j < ncol), A with leading dim lda (staged or
+// global).
+template <typename TA, typename LoHi>
+__device__ void col_dots(const TA* A, int64_t lda, int ncol, const double* v, LoHi lohi, double* out) {
+  const int G = lanes_per_item(ncol);
+  const int groups = blockDim.x / G, g = threadIdx.x % G;
+  const int iters = (ncol + groups - 1) / groups;
+  for (int it = 0; it < iters; it++) {
+    const int j = it * groups + (int)threadIdx.x / G;
+    double a0 = 0.0, a1 = 0.0;
+    if (j < ncol) {
+      int lo, hi;
+      lohi(j, lo, hi);
+      const TA* Aj = A + (int64_t)j * lda;
+      int i = lo + g;
+      for (; i + G <= hi; i += 2 * G) {
+        a0 = fma((double)Aj[i], v[i], a0);
+        a1 = fma((double)Aj[i + G], v[i + G], a1);
+      }
+      if (i <= hi) a0 = fma((double)Aj[i], v[i], a0);
+    }
+    const double r = group_sum(a0 + a1, G);
+    if (j < ncol && g == 0) out[j] = r;
+  }
+  __syncthreads();
+}
+
 // Finalisation after K2 (one CTA).  r[0..k) = dots of the next draw with the old columns of
 // V_D, r[k] = with the new column, r[k+1] = ||p[k+1:]||^2, r[k+2] = ||g_{t+1}[k+2:]||^2,
-// r[k+3+j] = V_D[k:, j] . p[k:] for the old columns j < k.
-// Small vectors are staged in shared memory; the O(k^2) loops read S and V columns with
-// eight independent loads in flight per thread.
+// r[k+3+j] = V_D[k:, j] . p[k:] for the old columns j < k.  Small vectors are staged in
+// shared memory; the O(k^2) products read S and V columns coalesced, spread over the CTA's
+// warps (scr: the sweep's dynamic shared memory, free at this point).
 template <typename T>
-__device__ void fin_update(const StepPlan<T>& p, const double* r) {
+__device__ void fin_update(const StepPlan<T>& p, const double* r, double* scr, int cap) {
   const int k = p.kD, Tm = p.Tm;
   const int tid = threadIdx.x, nt = blockDim.x;
   __shared__ double sh[16];
-  __shared__ double f_a[kTmaxLimit + 1];   // vtu (data side), later zt
-  __shared__ double f_b[kTmaxLimit + 1];   // y_top = Delta_N phead (Haar) / h (Ginibre)
-  __shared__ double f_c[kTmaxLimit + 1];   // vtg (random side) / g-dots
+  __shared__ double f_a[kTmaxLimit + 1];
+  __shared__ double f_b[kTmaxLimit + 1];
+  __shared__ double f_c[kTmaxLimit + 1];
+  __shared__ uint64_t fbar;
   T* VD = (T*)p.D.V;
   const int64_t ldD = p.D.ld;
+  if (tid == 0) mbar_init(&fbar);
+  Stager sg{&fbar, 0u, p.ws.err};
+  const int64_t capb = (int64_t)cap * 8;   // free shared memory in bytes
 
   for (int j = tid; j <= k; j += nt) p.D.gdot[j] = r[j];
   if (tid == 0) {
@@ -221,18 +392,15 @@ __device__ void fin_update(const StepPlan<T>& p, const double* r) {
   }
   __syncthreads();
   const double alpha = sh[0], tau = sh[1], us = sh[2], dsign = sh[3], ppiv = sh[5];
-  // V_D^T u with u = p[k:] + (u_k - p_k) e_k, from the exact dots of the sweep.
+  // V_D^T u with u = p[k:] + (u_k - p_k) e_k, from the exact dots of the sweep; then the new
+  // column of S: S[:k, k] = -tau S V_D^T u
   for (int j = tid; j < k; j += nt)
     f_a[j] = r[k + 3 + j] + (us - ppiv) * (double)VD[k + (int64_t)j * ldD];
   __syncthreads();
-  for (int j = tid; j < k; j += nt) {
-    double s = 0.0;
-    if (alpha != 0.0) {
-      const double* Sj = p.D.S + j;
-#pragma unroll 8
-      for (int i = j; i < k; i++) s = fma(Sj[(int64_t)i * Tm], f_a[i], s);
-    }
-    p.D.S[j + (int64_t)k * Tm] = -tau * s;
+  {
+    const bool st = k > 0 && up_off(k) * 8 <= capb && stage_upper(sg, p.D.S, Tm, k, scr);
+    upper_mv<1>(st ? scr : nullptr, p.D.S, Tm, k, f_a, nullptr, p.D.S + (int64_t)k * Tm,
+                (alpha != 0.0) ? -tau : 0.0, nullptr, 0.0);
   }
   if (tid == 0) {
     p.D.S[k + (int64_t)k * Tm] = tau;
@@ -268,28 +436,25 @@ __device__ void fin_update(const StepPlan<T>& p, const double* r) {
     const bool flag = sh[13] != 0.0;
     const double gpiv = sh[14];
     const double deltaN = p.N.dpre[k];
-    for (int j = tid; j < k; j += nt) {
-      const T* Vj = VN + (int64_t)j * ldN;
-      const double vk = (double)Vj[k];
-      const double gd = p.N.gdot[j];
-      f_c[j] = flag ? 0.0 : gd + (usg - gpiv) * vk;
-      double tz = 0.0;
-#pragma unroll 8
-      for (int i = j; i < k; i++) tz = fma((double)Vj[i], f_b[i], tz);
-      f_a[j] = tz + deltaN * (flag ? alpha * vk : coef * gd);
+    // tz_j = V_N[j:k, j] . (Delta_N p_head)[j:k]
+    {
+      const int Lv = stage_lv<T>(k);
+      const bool st = k > 0 && (int64_t)Lv * k * (int64_t)sizeof(T) <= capb &&
+                      stage_cols(sg, VN, ldN, k, k, (T*)scr);
+      col_dots(st ? (const T*)scr : VN, st ? (int64_t)Lv : ldN, k, f_b,
+               [k](int j, int& lo, int& hi) { lo = j; hi = k - 1; }, f_a);
     }
     __syncthreads();
     for (int j = tid; j < k; j += nt) {
-      double sw = 0.0, sc = 0.0;
-      const double* Sj = p.N.S + j;
-#pragma unroll 8
-      for (int i = j; i < k; i++) {
-        const double sji = Sj[(int64_t)i * Tm];
-        sw = fma(sji, f_a[i], sw);
-        sc = fma(sji, f_c[i], sc);
-      }
-      p.ws.wout[j] = sw;
-      p.N.S[j + (int64_t)k * Tm] = -taug * sc;
+      const double vk = (double)VN[k + (int64_t)j * ldN];
+      const double gd = p.N.gdot[j];
+      f_c[j] = flag ? 0.0 : gd + (usg - gpiv) * vk;
+      f_a[j] += deltaN * (flag ? alpha * vk : coef * gd);
+    }
+    __syncthreads();
+    {
+      const bool st = k > 0 && up_off(k) * 8 <= capb && stage_upper(sg, p.N.S, Tm, k, scr);
+      upper_mv<2>(st ? scr : nullptr, p.N.S, Tm, k, f_a, f_c, p.ws.wout, 1.0, p.N.S + (int64_t)k * Tm, -taug);
     }
     if (tid == 0) {
       p.N.S[k + (int64_t)k * Tm] = taug;
@@ -305,25 +470,16 @@ __device__ void fin_update(const StepPlan<T>& p, const double* r) {
       f_c[i] = p.N.gdot[i];
     }
     __syncthreads();
-    for (int j = tid; j < kN; j += nt) {
-      const T* Vj = VN + (int64_t)j * ldN;
-      double tz = 0.0;
-#pragma unroll 8
-      for (int i = j; i < kN; i++) tz = fma((double)Vj[i], f_b[i], tz);
-      f_a[j] = tz;
+    {
+      const int Lv = stage_lv<T>(kN);
+      const bool st = kN > 0 && (int64_t)Lv * kN * (int64_t)sizeof(T) <= capb &&
+                      stage_cols(sg, VN, ldN, kN, kN, (T*)scr);
+      col_dots(st ? (const T*)scr : VN, st ? (int64_t)Lv : ldN, kN, f_b,
+               [kN](int j, int& lo, int& hi) { lo = j; hi = kN - 1; }, f_a);
     }
-    __syncthreads();
-    for (int j = tid; j < kN; j += nt) {
-      double sw = 0.0, s2 = 0.0;
-      const double* Sj = p.N.S + j;
-#pragma unroll 8
-      for (int i = j; i < kN; i++) {
-        const double sji = Sj[(int64_t)i * Tm];
-        sw = fma(sji, f_a[i], sw);
-        s2 = fma(sji, f_c[i], s2);
-      }
-      p.ws.wout[j] = sw;
-      p.ws.wout2[j] = deltaN * s2;
+    {
+      const bool st = kN > 0 && up_off(kN) * 8 <= capb && stage_upper(sg, p.N.S, Tm, kN, scr);
+      upper_mv<2>(st ? scr : nullptr, p.N.S, Tm, kN, f_a, f_c, p.ws.wout, 1.0, p.ws.wout2, deltaN);
     }
   }
 }
@@ -363,11 +519,19 @@ struct WT {
   static constexpr int NCH = ROWS / VEC;           // chunks per column: 8 (FP32), 16 (FP64)
 };
 
-__device__ __forceinline__ uint32_t smem_u32(const void* ptr) {
-  return (uint32_t)__cvta_generic_to_shared(ptr);
-}
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
+}
+// L2 policy for the stack columns the sweeps stream once per launch: evict first, so that the
+// small per-step data (S, coefficients, partial sums, vectors) stays resident in L2.
+__device__ __forceinline__ uint64_t l2_evict_first() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ void cp_async16_stream(void* smem, const void* gmem, uint64_t pol) {
+  asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;\n" ::"r"(smem_u32(smem)), "l"(gmem),
+               "l"(pol) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
@@ -384,15 +548,16 @@ __device__ __forceinline__ void wt_load_cols(T* buf, const ColSrc<T>& src, int n
   const int q = lane & (NCH - 1);
   int j = lane / NCH;
   const int nA = min(ncol, src.nA);
+  const uint64_t pol = l2_evict_first();
   {
     const T* g = src.A + (int64_t)j * src.ldA + r0 + q * VEC;
     const int64_t gstep = (int64_t)CPI * src.ldA;
-    for (; j < nA; j += CPI, g += gstep) cp_async16(buf + j * 32 + ((q + j) & (NCH - 1)) * VEC, g);
+    for (; j < nA; j += CPI, g += gstep) cp_async16_stream(buf + j * 32 + ((q + j) & (NCH - 1)) * VEC, g, pol);
   }
   if (j < ncol) {
     const T* g = src.B + (int64_t)(j - src.nA) * src.ldB + r0 + q * VEC;
     const int64_t gstep = (int64_t)CPI * src.ldB;
-    for (; j < ncol; j += CPI, g += gstep) cp_async16(buf + j * 32 + ((q + j) & (NCH - 1)) * VEC, g);
+    for (; j < ncol; j += CPI, g += gstep) cp_async16_stream(buf + j * 32 + ((q + j) & (NCH - 1)) * VEC, g, pol);
   }
 }
 __device__ __forceinline__ void cp_async16_zfill(void* smem, const void* gmem, int src_bytes) {
@@ -553,6 +718,8 @@ struct WtSmem {
   int ncolT;
   int nb;
   int cpad;
+  size_t total;      // bytes of the layout (the launch's dynamic shared memory)
+  __device__ size_t bytes() const { return total; }
   __device__ WtSmem(unsigned char* base, int W, int nbuf, int ncolT_, int NRV, int ncolC, int NR) {
     constexpr int VEC = WT<T>::VEC;
     size_t off = 0;
@@ -571,6 +738,7 @@ struct WtSmem {
     cpad = (ncolT + NCH - 1) / NCH * NCH;
     coef = (T*)take((size_t)2 * cpad * sizeof(T));
     comb = (double*)take((size_t)W * NR * (ncolC > 0 ? ncolC : 1) * sizeof(double));
+    total = off;
   }
   __device__ __forceinline__ T* stage(int warp, int b) const {
     return stages + ((size_t)warp * nb + b) * sstride;
@@ -711,13 +879,34 @@ __global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_dots(BatchStep<T>
   __shared__ double zs[kTmaxLimit];
   for (int i = threadIdx.x; i < na; i += blockDim.x) zs[i] = p.ws.z[i];
   __syncthreads();
-  const int Tm = p.Tm;
-  for (int j = threadIdx.x; j < na; j += blockDim.x) {
-    double s = 0.0;
-    const double* Sj = p.D.S + (int64_t)j * Tm;
-#pragma unroll 8
-    for (int i = 0; i <= j; i++) s = fma(Sj[i], zs[i], s);
-    p.ws.w[j] = s;
+  // w = S_D^T z: w_j = S[0:j+1, j] . z[0:j+1]
+  __shared__ uint64_t dbar;
+  if (threadIdx.x == 0) mbar_init(&dbar);
+  Stager sg{&dbar, 0u, p.ws.err};
+  double* scr = (double*)dsm_raw;
+  const bool st = na > 0 && up_off(na) * 8 <= (int64_t)sm.bytes() && stage_upper(sg, p.D.S, p.Tm, na, scr);
+  // w_j = S[0:j+1, j] . z[0:j+1]: column j of the packed triangle starts at up_off(j)
+  if (st) {
+    const int G = lanes_per_item(na);
+    const int groups = blockDim.x / G, g = threadIdx.x % G;
+    const int iters = (na + groups - 1) / groups;
+    for (int it = 0; it < iters; it++) {
+      const int j = it * groups + (int)threadIdx.x / G;
+      double a0 = 0.0, a1 = 0.0;
+      if (j < na) {
+        const double* Sj = scr + up_off(j);
+        int i = g;
+        for (; i + G <= j; i += 2 * G) {
+          a0 = fma(Sj[i], zs[i], a0);
+          a1 = fma(Sj[i + G], zs[i + G], a1);
+        }
+        if (i <= j) a0 = fma(Sj[i], zs[i], a0);
+      }
+      const double r = group_sum(a0 + a1, G);
+      if (j < na && g == 0) p.ws.w[j] = r;
+    }
+  } else {
+    col_dots(p.D.S, (int64_t)p.Tm, na, zs, [](int j, int& lo, int& hi) { lo = 0; hi = j; }, p.ws.w);
   }
 }
 
@@ -789,7 +978,7 @@ __global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_update(BatchStep<
   block_sum_to<3>(ex, red, part + k, 3);
   double* rr = p.ws.scr(3);
   if (!reduce_partials(p.ws, 1, P, cc.local, cc.ncta, rr)) return;
-  fin_update<T>(p, rr);
+  fin_update<T>(p, rr, (double*)dsm_raw, (int)(sm.bytes() / sizeof(double)));
 }
 
 // K3 (Haar): y = Delta_N c - V_N w' with c = [p_head; coef g_t[k:]]; appends the random

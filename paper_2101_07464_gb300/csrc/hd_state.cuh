@@ -40,6 +40,7 @@ struct hd_state {
   std::vector<int64_t> dims[2];  // per trial: dims[0] = n_i (space of R), dims[1] = m_i (space of L)
   std::vector<int64_t> off[2];   // packed vector offsets per space (count + 1)
   int Tm = 0;
+  int Sld = 0;                   // leading dimension of the S matrices (T_max rounded up to even)
   uint64_t seed = 0;
   uint32_t trial = 0;            // Philox trial word of trial 0 (trial i uses trial + i)
   double sigma = 1.0;

@@ -167,7 +167,7 @@ class ClockSampler:
 
 # DRAM bytes / algorithmic bytes of one k_update launch (k = 60, n = 10^6, FP32) from an
 # ncu --set full capture of the current kernel; reset to None when the kernel changes.
-UPDATE_TRAFFIC_RATIO = 254.366 / 252.0
+UPDATE_TRAFFIC_RATIO = None
 
 
 def measured_peaks():
@@ -342,7 +342,8 @@ def run_ours(args):
                                             "output": "k_out_haar"}[dom],
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_source": peak_kind,
-                "traffic": (by / nl) * UPDATE_TRAFFIC_RATIO if (nl and dom == "update") else None,
+                "traffic": ((by / nl) * UPDATE_TRAFFIC_RATIO
+                            if (nl and dom == "update" and UPDATE_TRAFFIC_RATIO) else None),
                 "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_update "
                                   "launch at k = 60 (254.37 MB for 252.0 MB algorithmic), scaled to "
                                   "the average launch by algorithmic bytes",

@@ -104,8 +104,19 @@ int first_draws(hd_state* st) {
   return HD_OK;
 }
 
+// A step of a fused trajectory (hd_run): K3 applies the dynamics and forms the next step's
+// K1 results (fuse), and/or this step's K1 was formed by the previous step (skip_dots).
+struct FuseSpec {
+  int fuse = 0;
+  int skip_dots = 0;
+  int dyn = 0;
+  double a = 0.0;
+  void* xnext = nullptr;
+  const void* xprev = nullptr;
+};
+
 template <typename T>
-int do_step(hd_state* st, const void* x, int transpose, void* y) {
+int do_step(hd_state* st, const void* x, int transpose, void* y, const FuseSpec* fs = nullptr) {
   if (!st->drawn) {
     int rc = first_draws<T>(st);
     if (rc) return rc;
@@ -120,6 +131,21 @@ int do_step(hd_state* st, const void* x, int transpose, void* y) {
   }
   BatchStep<T> b = make_batch<T>(st, d, kD, kN, x, y);
   b.base.key_next = key_for(st, st->t + 2);
+  if (fs) {
+    b.base.skip_dots = fs->skip_dots;
+    if (fs->fuse) {
+      b.base.fuse = 1;
+      b.base.dyn = fs->dyn;
+      b.base.dyn_a = (T)fs->a;
+      b.base.xnext = (T*)fs->xnext;
+      b.base.xprev = (const T*)fs->xprev;
+      b.base.y = nullptr;
+      if (st->ens == HD_HAAR)
+        b.base.c3 = make_sweep<T>(st, 4, kN, 3, kN, 2);
+      else
+        b.base.c3 = make_sweep<T>(st, 5, kN + kD, 2, kN + kD, 2);
+    }
+  }
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   int slot0 = -1;
   if (st->prof_on && st->prof_used + 3 <= st->prof_cap) {
@@ -139,8 +165,9 @@ int do_step(hd_state* st, const void* x, int transpose, void* y) {
     const double nD = (double)(st->off[d][st->count]), nN = (double)(st->off[1 - d][st->count]);
     const double bd = (st->ens == HD_GINIBRE) ? (double)kN * nD : 0.0;
     const double bn = (st->ens == HD_GINIBRE) ? (double)(kD + 1) * nN : 0.0;
+    const bool fz = fs && fs->fuse;
     const double bb[3] = {es * (nD * kD + bd + nD), es * (nD * kD + 3.0 * nD),
-                          es * (nN * kN + bn + 4.0 * nN)};
+                          es * (nN * kN + bn + (fz ? 5.0 : 4.0) * nN)};
     for (int q = 0; q < 3; q++) {
       st->prof_kind[slot0 + q] = launched[q] ? q : -1;
       st->prof_bytes[slot0 + q] = bb[q];
@@ -185,10 +212,26 @@ int run_steps(hd_state* st, const hd_run_spec* sp) {
   st->drawn = 0;
   if (int rc = adj_on_reset(st)) return rc;
   int cur = 0;
+  // elementwise dynamics of a Q / Q^T alternating schedule: the output sweep of step t applies
+  // f_t and forms step t+1's dot sweep (HD_DISABLE_FUSE=1 turns this off)
+  const bool fusable = (sp->dynamics == HD_DYN_TANH || sp->dynamics == HD_DYN_SIGN_MEM) && st->fuse;
+  int prev_fused = 0;
   for (int t = 0; t < sp->T; t++) {
     const int tr = sp->transpose[t] ? 1 : 0;
-    int rc = do_step<T>(st, st->xw[cur], tr, st->yw);
+    FuseSpec fs;
+    fs.skip_dots = prev_fused;
+    fs.fuse = fusable && t + 1 < sp->T && ((sp->transpose[t + 1] ? 1 : 0) != tr);
+    fs.dyn = sp->dynamics;
+    fs.a = sp->a;
+    fs.xnext = st->xw[1 - cur];
+    fs.xprev = st->xw[1 - cur];
+    int rc = do_step<T>(st, st->xw[cur], tr, st->yw, &fs);
     if (rc) return rc;
+    prev_fused = fs.fuse;
+    if (fs.fuse) {
+      cur = 1 - cur;
+      continue;
+    }
     const int64_t nout = st->off[tr ? 0 : 1][st->count];   // packed length of the output space
     cudaError_t e = launch_dynamics<T>(sp->dynamics, sp->a, (const T*)st->yw, (const T*)st->xw[cur],
                                        (const T*)st->xw[1 - cur], (T*)st->xw[1 - cur], nout,
@@ -355,6 +398,8 @@ int create_common(int ensemble, int count, const int64_t* m, const int64_t* n, i
   {
     const char* env = getenv("HD_DISABLE_PDL");
     st->pdl = (env && env[0] == '1') ? 0 : 1;
+    const char* envf = getenv("HD_DISABLE_FUSE");
+    st->fuse = (envf && envf[0] == '1') ? 0 : 1;
   }
   cudaDeviceGetAttribute(&st->smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, st->device);
   cudaDeviceGetAttribute(&st->smem_blk_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, st->device);
@@ -370,7 +415,7 @@ int create_common(int ensemble, int count, const int64_t* m, const int64_t* n, i
       return fail(HD_ERR_CUDA);
     }
   }
-  for (int q = 0; q < 4; q++) {
+  for (int q = 0; q < 6; q++) {
     st->occ_regs[q] = (dtype == HD_F64) ? kernel_occupancy<double>(q, 0) : kernel_occupancy<float>(q, 0);
     st->static_smem[q] = (dtype == HD_F64) ? kernel_static_smem<double>(q) : kernel_static_smem<float>(q);
   }

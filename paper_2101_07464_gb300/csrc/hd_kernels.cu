@@ -123,6 +123,8 @@ __device__ __forceinline__ StepPlan<T> make_plan(const BatchStep<T>& b, int spac
   p.key_next.trial = td.trial;
   p.x = b.base.x ? b.base.x + td.off[d] : nullptr;
   p.y = b.base.y ? b.base.y + td.off[1 - d] : nullptr;
+  p.xnext = b.base.xnext ? b.base.xnext + td.off[1 - d] : nullptr;
+  p.xprev = b.base.xprev ? b.base.xprev + td.off[1 - d] : nullptr;
   return p;
 }
 
@@ -350,6 +352,39 @@ __device__ void col_dots(const TA* A, int64_t lda, int ncol, const double* v, Lo
     if (j < ncol && g == 0) out[j] = r;
   }
   __syncthreads();
+}
+
+
+// Finalisation of the dot sweep (one CTA): w = S^T z over n columns (w_j = S[0:j+1, j] . z),
+// S staged as a packed upper triangle when it fits in the free shared memory.
+__device__ void fin_dots(const double* S, int Sld, int na, const double* zs, double* w, double* scr, int64_t capb,
+                         unsigned* err) {
+  __shared__ uint64_t dbar;
+  if (threadIdx.x == 0) mbar_init(&dbar);
+  Stager sg{&dbar, 0u, err};
+  const bool st = na > 0 && up_off(na) * 8 <= capb && stage_upper(sg, S, Sld, na, scr);
+  if (st) {
+    const int G = lanes_per_item(na);
+    const int groups = blockDim.x / G, g = threadIdx.x % G;
+    const int iters = (na + groups - 1) / groups;
+    for (int it = 0; it < iters; it++) {
+      const int j = it * groups + (int)threadIdx.x / G;
+      double a0 = 0.0, a1 = 0.0;
+      if (j < na) {
+        const double* Sj = scr + up_off(j);
+        int i = g;
+        for (; i + G <= j; i += 2 * G) {
+          a0 = fma(Sj[i], zs[i], a0);
+          a1 = fma(Sj[i + G], zs[i + G], a1);
+        }
+        if (i <= j) a0 = fma(Sj[i], zs[i], a0);
+      }
+      const double r = group_sum(a0 + a1, G);
+      if (j < na && g == 0) w[j] = r;
+    }
+  } else {
+    col_dots(S, (int64_t)Sld, na, zs, [](int j, int& lo, int& hi) { lo = 0; hi = j; }, w);
+  }
 }
 
 // Finalisation after K2 (one CTA).  r[0..k) = dots of the next draw with the old columns of
@@ -880,34 +915,7 @@ __global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_dots(BatchStep<T>
   for (int i = threadIdx.x; i < na; i += blockDim.x) zs[i] = p.ws.z[i];
   __syncthreads();
   // w = S_D^T z: w_j = S[0:j+1, j] . z[0:j+1]
-  __shared__ uint64_t dbar;
-  if (threadIdx.x == 0) mbar_init(&dbar);
-  Stager sg{&dbar, 0u, p.ws.err};
-  double* scr = (double*)dsm_raw;
-  const bool st = na > 0 && up_off(na) * 8 <= (int64_t)sm.bytes() && stage_upper(sg, p.D.S, p.Tm, na, scr);
-  // w_j = S[0:j+1, j] . z[0:j+1]: column j of the packed triangle starts at up_off(j)
-  if (st) {
-    const int G = lanes_per_item(na);
-    const int groups = blockDim.x / G, g = threadIdx.x % G;
-    const int iters = (na + groups - 1) / groups;
-    for (int it = 0; it < iters; it++) {
-      const int j = it * groups + (int)threadIdx.x / G;
-      double a0 = 0.0, a1 = 0.0;
-      if (j < na) {
-        const double* Sj = scr + up_off(j);
-        int i = g;
-        for (; i + G <= j; i += 2 * G) {
-          a0 = fma(Sj[i], zs[i], a0);
-          a1 = fma(Sj[i + G], zs[i + G], a1);
-        }
-        if (i <= j) a0 = fma(Sj[i], zs[i], a0);
-      }
-      const double r = group_sum(a0 + a1, G);
-      if (j < na && g == 0) p.ws.w[j] = r;
-    }
-  } else {
-    col_dots(p.D.S, (int64_t)p.Tm, na, zs, [](int j, int& lo, int& hi) { lo = 0; hi = j; }, p.ws.w);
-  }
+  fin_dots(p.D.S, p.Tm, na, zs, p.ws.w, (double*)dsm_raw, (int64_t)sm.bytes(), p.ws.err);
 }
 
 // K2: p = Delta_D (x - V_D w); writes p[k:] as the new column k of V_D; draws g_{t+1}
@@ -981,10 +989,21 @@ __global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_update(BatchStep<
   fin_update<T>(p, rr, (double*)dsm_raw, (int)(sm.bytes() / sizeof(double)));
 }
 
+// Elementwise dynamics of the fused K3 (the same arithmetic as the stand-alone kernel).
+template <typename T>
+__device__ __forceinline__ T fused_dyn(int kind, T a, T y, T xprev) {
+  if (kind == 1) return tanh(y);
+  const T sg = (y > T(0)) ? T(1) : ((y < T(0)) ? T(-1) : T(0));
+  return sg + a * xprev;
+}
+
 // K3 (Haar): y = Delta_N c - V_N w' with c = [p_head; coef g_t[k:]]; appends the random
 // reflector column (g_t[k:] with the pivot entry replaced); the next draw (read from the
 // data stack's buffer) replaces g_t in this stack's buffer; dots of it with V_N.
-template <typename T>
+// FUSE: instead of storing y, applies the dynamics x_{t+1} = f(y, x_{t-1}) and adds the dots
+// of x_{t+1} with V_N and the new column, i.e. the next step's K1 (this stack is the next
+// step's data stack), finished by w = S_N^T z in the last CTA.
+template <typename T, bool FUSE>
 __global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_out_haar(BatchStep<T> bs) {
   CtaCtx cc;
   const StepPlan<T> p = make_plan(bs, 1 - bs.d, cc);
@@ -993,7 +1012,8 @@ __global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_out_haar(BatchSte
   const int k = p.kN;
   const SweepCfg& cfg = p.c3;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  WtSmem<T> sm(dsm_raw, blockDim.x >> 5, cfg.nbuf, k, 2, k, 1);
+  constexpr int NR = FUSE ? 2 : 1;
+  WtSmem<T> sm(dsm_raw, blockDim.x >> 5, cfg.nbuf, k, FUSE ? 3 : 2, k, NR);
   const ColSrc<T> src{(const T*)p.N.V, p.N.ld, k, nullptr, 0};
   const int64_t dim = p.N.dim;
   T* col = (T*)p.N.V + (int64_t)k * p.N.ld;
@@ -1001,10 +1021,15 @@ __global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_out_haar(BatchSte
   const T* gnext = (const T*)p.D.gbuf;
   T coef = T(0), alpha = T(0), usg = T(0), dconst = T(0);
   bool flag = false;
-  double acc[1][kColsPerLane];
+  double acc[NR][kColsPerLane];
 #pragma unroll
-  for (int m = 0; m < kColsPerLane; m++) acc[0][m] = 0.0;
-  T ex[1] = {T(0)};
+  for (int m = 0; m < kColsPerLane; m++) {
+    acc[0][m] = 0.0;
+    if (FUSE) acc[NR - 1][m] = 0.0;
+  }
+  T ex[2] = {T(0), T(0)};   // new column . g_{t+1}; (FUSE) new column . x_{t+1}
+  T* xv = sm.scr(warp, 0);
+  const bool need_prev = FUSE && p.dyn != 1;
   const WarpWalk ww(dim, cc);
   const int64_t ld = p.N.ld;
   wt_pipeline(ww.count(), cfg.nbuf,
@@ -1013,6 +1038,7 @@ __global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_out_haar(BatchSte
         const int64_t r0 = ww.sub(it) * 32;
         wt_load_cols(st, src, k, r0);
         wt_load_vec(sm.srow(st, 0), (const T*)gcur, r0, ld, true);
+        if (need_prev) wt_load_vec(sm.srow(st, 2), p.xprev, r0, dim, ((uintptr_t)p.xprev & 15u) == 0);
       },
       [&]() {   // outputs of the preceding kernel's finalisation
         for (int j = threadIdx.x; j < sm.cpad; j += blockDim.x) sm.coef[j] = (j < k) ? (T)p.ws.wout[j] : T(0);
@@ -1038,46 +1064,86 @@ __global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_out_haar(BatchSte
         const T yi = d * ci - out[0];
         const T nc = (r > k) ? g : ((r == k) ? usg : T(0));
         if (r < dim) {
-          p.y[r] = yi;
+          if (!FUSE) p.y[r] = yi;
           if (r >= k) col[r] = nc;
         }
         ex[0] = fma(nc, gn, ex[0]);
         gcur[r] = gn;
-        wt_cols<T, 1>(st, k, sm.srow(st, 1), nullptr, acc);
+        if (FUSE) {
+          T xn = T(0);
+          if (r < dim) {
+            xn = fused_dyn<T>(p.dyn, p.dyn_a, yi, need_prev ? sm.srow(st, 2)[lane] : T(0));
+            p.xnext[r] = xn;
+          }
+          xv[lane] = xn;
+          ex[1] = fma(nc, xn, ex[1]);
+          __syncwarp();
+        }
+        wt_cols<T, NR>(st, k, sm.srow(st, 1), FUSE ? xv : nullptr, acc);
+        if (FUSE) __syncwarp();
       });
-  const int P = k + 1;
+  // partial sums: [0, k) V_N . g_{t+1}, [k] new . g_{t+1}, (FUSE) [k+1] new . x_{t+1},
+  // [k+2, 2k+2) V_N . x_{t+1}
+  const int P = FUSE ? 2 * k + 2 : k + 1;
   double* part = p.ws.part + (int64_t)cc.local * P;
-  const int off[1] = {0};
-  wt_store_cols<1>(sm.comb, k, acc, part, off);
-  block_sum_to<1>(ex, red, part + k, 1);
+  {
+    int off[NR];
+    off[0] = 0;
+    if (FUSE) off[NR - 1] = k + 2;
+    wt_store_cols<NR>(sm.comb, k, acc, part, off);
+  }
+  block_sum_to<2>(ex, red, part + k, NR);
   double* rr = p.ws.scr(3);
   if (!reduce_partials(p.ws, 2, P, cc.local, cc.ncta, rr)) return;
   for (int j = threadIdx.x; j <= k; j += blockDim.x) p.N.gdot[j] = rr[j];
   if (threadIdx.x == 0) p.N.gg[0] = p.D.gg[0];
+  if (FUSE) {
+    // the next step's K1: z = V_N^T x_{t+1} over the k + 1 columns, w = S_N^T z
+    __shared__ double zs[kTmaxLimit + 1];
+    for (int j = threadIdx.x; j <= k; j += blockDim.x) {
+      const double zj = (j < k) ? rr[k + 2 + j] : rr[k + 1];
+      zs[j] = zj;
+      p.ws.z[j] = zj;
+    }
+    __syncthreads();
+    fin_dots(p.N.S, p.Tm, k + 1, zs, p.ws.w, (double*)dsm_raw, (int64_t)sm.bytes(), p.ws.err);
+  }
 }
 
 // K3 (Ginibre): u = Delta_N g - V_N w_2 (= L_1..L_l Z_{1:l} g), y = alpha u + Delta_N h
 // - V_N w_h + B_n c; u becomes the new basis column; the next draw (rows >= k_N) replaces g
 // in this stack's buffer, with its dots with V_N.
-template <typename T>
+// FUSE: applies the dynamics instead of storing y and adds the next step's K1: the dots of
+// x_{t+1} with V_N (the next data stack) and with B_n including u (the next step's data-space
+// basis), then w = S_N^T z in the last CTA.
+template <typename T, bool FUSE>
 __global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_out_gin(BatchStep<T> bs) {
   CtaCtx cc;
   const StepPlan<T> p = make_plan(bs, 1 - bs.d, cc);
   extern __shared__ __align__(16) unsigned char dsm_raw[];
+  __shared__ double red[kWarps * 4];
   const int kN = p.kN, kD = p.kD, nc = kN + kD;
   const SweepCfg& cfg = p.c3;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  WtSmem<T> sm(dsm_raw, blockDim.x >> 5, cfg.nbuf, nc, 1, kN, 1);
+  constexpr int NR = FUSE ? 2 : 1;
+  const int ncc = FUSE ? nc : kN;   // column-owner columns
+  WtSmem<T> sm(dsm_raw, blockDim.x >> 5, cfg.nbuf, nc, FUSE ? 2 : 1, ncc, NR);
   const ColSrc<T> src{(const T*)p.N.V, p.N.ld, kN, (const T*)p.Bn, p.ldBn};
   const int64_t dim = p.N.dim;
   T* ucol = (T*)p.Bn + (int64_t)kD * p.ldBn;
   T* gcur = (T*)p.N.gbuf;
   const double* h = p.ws.z + kD;
   T alpha = T(0), dconst = T(0);
-  double acc[1][kColsPerLane];
+  double acc[NR][kColsPerLane];
 #pragma unroll
-  for (int m = 0; m < kColsPerLane; m++) acc[0][m] = 0.0;
+  for (int m = 0; m < kColsPerLane; m++) {
+    acc[0][m] = 0.0;
+    if (FUSE) acc[NR - 1][m] = 0.0;
+  }
+  T ex[1] = {T(0)};   // (FUSE) u . x_{t+1}
   T* gv = sm.scr(warp, 0);
+  T* xv = sm.scr(warp, 1);
+  const bool need_prev = FUSE && p.dyn != 1;
   const WarpWalk ww(dim, cc);
   const int64_t ld = p.N.ld;
   wt_pipeline(ww.count(), cfg.nbuf,
@@ -1086,6 +1152,7 @@ __global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_out_gin(BatchStep
         const int64_t r0 = ww.sub(it) * 32;
         wt_load_cols(st, src, nc, r0);
         wt_load_vec(sm.srow(st, 0), (const T*)gcur, r0, ld, true);
+        if (need_prev) wt_load_vec(sm.srow(st, 1), p.xprev, r0, dim, ((uintptr_t)p.xprev & 15u) == 0);
       },
       [&]() {   // outputs of the preceding kernel's finalisation
         for (int j = threadIdx.x; j < sm.cpad; j += blockDim.x) {
@@ -1116,21 +1183,51 @@ __global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_out_gin(BatchStep
         const T yi = fma(alpha, u, d * hi) - out[1];
         if (r < dim) {
           ucol[r] = u;
-          p.y[r] = yi;
+          if (!FUSE) p.y[r] = yi;
         }
         gcur[r] = gn;
         gv[lane] = gn;
+        if (FUSE) {
+          T xn = T(0);
+          if (r < dim) {
+            xn = fused_dyn<T>(p.dyn, p.dyn_a, yi, need_prev ? sm.srow(st, 1)[lane] : T(0));
+            p.xnext[r] = xn;
+          }
+          xv[lane] = xn;
+          ex[0] = fma(u, xn, ex[0]);
+        }
         __syncwarp();
-        wt_cols<T, 1>(st, kN, gv, nullptr, acc);
+        wt_cols<T, NR>(st, ncc, gv, FUSE ? xv : nullptr, acc);
+        if (FUSE) __syncwarp();
       });
-  if (kN == 0) return;   // no dots to form
-  const int P = kN;
+  if (!FUSE && kN == 0) return;   // no dots to form
+  // partial sums: [0, ncc) columns . g_{t+1} (V_N's first kN are used); (FUSE) [nc] u . x_{t+1},
+  // [nc + 1, 2 nc + 1) columns . x_{t+1}
+  const int P = FUSE ? 2 * nc + 1 : kN;
   double* part = p.ws.part + (int64_t)cc.local * P;
-  const int off[1] = {0};
-  wt_store_cols<1>(sm.comb, kN, acc, part, off);
+  {
+    int off[NR];
+    off[0] = 0;
+    if (FUSE) off[NR - 1] = nc + 1;
+    wt_store_cols<NR>(sm.comb, ncc, acc, part, off);
+  }
+  if (FUSE) block_sum_to<1>(ex, red, part + nc, 1);
   double* rr = p.ws.scr(3);
   if (!reduce_partials(p.ws, 2, P, cc.local, cc.ncta, rr)) return;
   for (int j = threadIdx.x; j < kN; j += blockDim.x) p.N.gdot[j] = rr[j];
+  if (FUSE) {
+    // the next step's K1 (its data stack is V_N, k_D' = kN; its data-space basis is B_n with
+    // kD + 1 columns): z = V_N^T x_{t+1}, h = B_n^T x_{t+1}, w = S_N^T z
+    __shared__ double zs[kTmaxLimit + 1];
+    for (int j = threadIdx.x; j < kN; j += blockDim.x) {
+      const double zj = rr[nc + 1 + j];
+      zs[j] = zj;
+      p.ws.z[j] = zj;
+    }
+    for (int i = threadIdx.x; i <= kD; i += blockDim.x) p.ws.z[kN + i] = (i < kD) ? rr[nc + 1 + kN + i] : rr[nc];
+    __syncthreads();
+    fin_dots(p.N.S, p.Tm, kN, zs, p.ws.w, (double*)dsm_raw, (int64_t)sm.bytes(), p.ws.err);
+  }
 }
 
 // ------------------------------------------------------------------------------------
@@ -1169,7 +1266,7 @@ cudaError_t launch_step(const BatchStep<T>& b, cudaStream_t s, cudaEvent_t* ev, 
   const int dspace = b.d, ospace = 1 - b.d;
   cudaError_t e = cudaSuccess;
   const int nc1 = p.kD + ((p.ens == 0) ? p.kN : 0);
-  if (nc1 > 0) {
+  if (nc1 > 0 && !p.skip_dots) {
     rec(0);
     e = launch_sweep<T>(k_dots<T>, p.c1, b.map[dspace].ctas,
                         sweep_smem_bytes<T>(p.c1.W, p.c1.nbuf, nc1, 1, nc1, 1), s, pdl, b);
@@ -1178,18 +1275,27 @@ cudaError_t launch_step(const BatchStep<T>& b, cudaStream_t s, cudaEvent_t* ev, 
     if (launched) launched[0] = 1;
   }
   rec(2);
+  // K2 prefetches x and its stack columns before waiting for the preceding kernel; after a
+  // fused K3 (which writes x and the newest column) it is launched without the early start
   e = launch_sweep<T>(k_update<T>, p.c2, b.map[dspace].ctas,
-                      sweep_smem_bytes<T>(p.c2.W, p.c2.nbuf, p.kD, 1, p.kD, 2), s, pdl, b);
+                      sweep_smem_bytes<T>(p.c2.W, p.c2.nbuf, p.kD, 1, p.kD, 2), s, pdl && !p.skip_dots, b);
   if (e != cudaSuccess) return e;
   rec(3);
   if (launched) launched[1] = 1;
   rec(4);
-  if (p.ens == 1)
-    e = launch_sweep<T>(k_out_haar<T>, p.c3, b.map[ospace].ctas,
+  const int ncg = p.kN + p.kD;
+  if (p.ens == 1 && p.fuse)
+    e = launch_sweep<T>(k_out_haar<T, true>, p.c3, b.map[ospace].ctas,
+                        sweep_smem_bytes<T>(p.c3.W, p.c3.nbuf, p.kN, 3, p.kN, 2), s, pdl, b);
+  else if (p.ens == 1)
+    e = launch_sweep<T>(k_out_haar<T, false>, p.c3, b.map[ospace].ctas,
                         sweep_smem_bytes<T>(p.c3.W, p.c3.nbuf, p.kN, 2, p.kN, 1), s, pdl, b);
+  else if (p.fuse)
+    e = launch_sweep<T>(k_out_gin<T, true>, p.c3, b.map[ospace].ctas,
+                        sweep_smem_bytes<T>(p.c3.W, p.c3.nbuf, ncg, 2, ncg, 2), s, pdl, b);
   else
-    e = launch_sweep<T>(k_out_gin<T>, p.c3, b.map[ospace].ctas,
-                        sweep_smem_bytes<T>(p.c3.W, p.c3.nbuf, p.kN + p.kD, 1, p.kN, 1), s, pdl, b);
+    e = launch_sweep<T>(k_out_gin<T, false>, p.c3, b.map[ospace].ctas,
+                        sweep_smem_bytes<T>(p.c3.W, p.c3.nbuf, ncg, 1, p.kN, 1), s, pdl, b);
   if (e != cudaSuccess) return e;
   rec(5);
   if (launched) launched[2] = 1;
@@ -1209,8 +1315,10 @@ cudaError_t set_sweep_smem_limit(int bytes) {
   };
   one((const void*)k_dots<T>);
   one((const void*)k_update<T>);
-  one((const void*)k_out_haar<T>);
-  one((const void*)k_out_gin<T>);
+  one((const void*)k_out_haar<T, false>);
+  one((const void*)k_out_gin<T, false>);
+  one((const void*)k_out_haar<T, true>);
+  one((const void*)k_out_gin<T, true>);
   return e;
 }
 template cudaError_t set_sweep_smem_limit<float>(int);
@@ -1223,8 +1331,10 @@ int kernel_static_smem(int which) {
   switch (which) {
     case 0: e = cudaFuncGetAttributes(&fa, k_dots<T>); break;
     case 1: e = cudaFuncGetAttributes(&fa, k_update<T>); break;
-    case 2: e = cudaFuncGetAttributes(&fa, k_out_haar<T>); break;
-    default: e = cudaFuncGetAttributes(&fa, k_out_gin<T>); break;
+    case 2: e = cudaFuncGetAttributes(&fa, k_out_haar<T, false>); break;
+    case 3: e = cudaFuncGetAttributes(&fa, k_out_gin<T, false>); break;
+    case 4: e = cudaFuncGetAttributes(&fa, k_out_haar<T, true>); break;
+    default: e = cudaFuncGetAttributes(&fa, k_out_gin<T, true>); break;
   }
   return (e == cudaSuccess) ? (int)fa.sharedSizeBytes : 8192;
 }
@@ -1238,8 +1348,10 @@ int kernel_occupancy(int which, size_t dynsmem) {
   switch (which) {
     case 0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_dots<T>, kThreads, dynsmem); break;
     case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_update<T>, kThreads, dynsmem); break;
-    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_out_haar<T>, kThreads, dynsmem); break;
-    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_out_gin<T>, kThreads, dynsmem); break;
+    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_out_haar<T, false>, kThreads, dynsmem); break;
+    case 3: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_out_gin<T, false>, kThreads, dynsmem); break;
+    case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_out_haar<T, true>, kThreads, dynsmem); break;
+    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_out_gin<T, true>, kThreads, dynsmem); break;
   }
   return (e == cudaSuccess && nb > 0) ? nb : 1;
 }

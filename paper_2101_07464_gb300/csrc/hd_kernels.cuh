@@ -105,6 +105,15 @@ struct StepPlan {
   T sigma;              // entry scale of the draws (Ginibre), 1 for Haar
   SweepCfg c1, c2, c3;  // launch shapes of the three sweeps
   int pdl;              // launch with programmatic dependent launch
+  // Fused trajectories (hd_run, Q / Q^T alternating, elementwise f_t): K3 also applies the
+  // dynamics x_{t+1} = f(y_t, x_{t-1}) and forms the next step's K1 results (z, h, w), so the
+  // next step skips K1.
+  int fuse;             // this step's K3 is the fused one
+  int skip_dots;        // this step's K1 was done by the previous step's fused K3
+  int dyn;              // kDynTanh or kDynSignMem
+  T dyn_a;
+  T* xnext;             // x_{t+1} (output space, packed base); written by the fused K3
+  const T* xprev;       // x_{t-1} (output space, packed base); may alias xnext
 };
 
 // ------------------------------------------------------------------------------------

@@ -61,8 +61,9 @@ struct hd_state {
   size_t cnt_bytes = 0;
   int nsm = 1;
   int pdl = 1;                   // programmatic dependent launch of the sweeps (HD_DISABLE_PDL=1: off)
-  int occ_regs[4] = {1, 1, 1, 1};  // CTAs of 256 threads per SM allowed by registers per sweep
-  int static_smem[4] = {0, 0, 0, 0};
+  int fuse = 1;                  // fused output + dynamics + dot sweeps in hd_run (HD_DISABLE_FUSE=1: off)
+  int occ_regs[6] = {1, 1, 1, 1, 1, 1};  // CTAs of 256 threads per SM allowed by registers, per sweep kernel
+  int static_smem[6] = {0, 0, 0, 0, 0, 0};   // (dots, update, out Haar, out Gin, fused out Haar, fused out Gin)
   int smem_sm = 0;
   int smem_blk_max = 0;
   int64_t bytes = 0;

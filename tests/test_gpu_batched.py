@@ -97,8 +97,9 @@ def test_batch_of_one_is_single_state(ens):
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 @pytest.mark.parametrize("graph", [False, True])
-def test_batched_run_matches_apply(dtype, graph):
+def test_batched_run_matches_apply(dtype, graph, monkeypatch):
     import paper_2101_07464_gb300 as hd
+    monkeypatch.setenv("HD_DISABLE_FUSE", "1")   # bit-exact comparison: the unfused path
     tdt = torch.float64 if dtype == "f64" else torch.float32
     ns = [10_007, 31, 65_536, 4099]
     T, a = 14, 0.5
@@ -139,4 +140,29 @@ def test_batched_argument_checks():
         hd.hd_run(b.h, nt, torch.zeros(70, dtype=torch.float64, device="cuda"),
                   torch.zeros(70, dtype=torch.float64, device="cuda"))
     assert ei.value.code == 1
+    b.close()
+
+
+def test_batched_fused_run_matches_apply():
+    """Fused alternating trajectory on a batch (FP64, sign dynamics): per trial equal to the
+    step-by-step products up to the dots' summation order."""
+    import paper_2101_07464_gb300 as hd
+    ns = [10_007, 31, 65_536, 4099]
+    T, a = 14, 0.5
+    flags = [ALT(t) for t in range(1, T + 1)]
+    x1 = torch.tensor(np.concatenate([synth.x1(n, 9, trial=i) for i, n in enumerate(ns)]),
+                      dtype=torch.float64, device="cuda")
+    b = hd.HDBatch("haar", ns, ns, T, 9, "f64", trial=3)
+    x, xp = x1.clone(), torch.zeros_like(x1)
+    for t in range(T):
+        y = b.apply(x, flags[t])
+        x, xp = torch.sign(y) + a * xp, x
+    b.reset(9)
+    out = torch.empty_like(x1)
+    hd.hd_run(b.h, hd.make_run_spec(flags, "sign_mem", a, use_graph=True), x1, out)
+    torch.cuda.synchronize()
+    off = b.off_n
+    for i in range(len(ns)):
+        xo, xr = out[off[i]:off[i + 1]].double(), x[off[i]:off[i + 1]].double()
+        assert (xo - xr).norm().item() <= 1e-12 * xr.norm().item(), i
     b.close()

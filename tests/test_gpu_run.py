@@ -44,13 +44,15 @@ def _manual(ens, m, n, T, seed, dtype, flags, dyn, a, sigma):
     ("haar", 4099, 4099, "norm_tanh", 0.1, "allq"),
     ("ginibre", 3001, 3001, "tanh", 0.0, "allq"),
     ("ginibre", 2001, 5003, "tanh", 0.0, "alt")])
-def test_run_matches_apply(dtype, graph, ens, m, n, dyn, a, pattern):
+def test_run_matches_apply(dtype, graph, ens, m, n, dyn, a, pattern, monkeypatch):
+    """The unfused trajectory path: bit for bit the same kernels as hd_apply."""
     import paper_2101_07464_gb300 as hd
     T = 16
     flags = [(t % 2 == 0) if pattern == "alt" else False for t in range(1, T + 1)]
     sigma = 1.0 if ens == "haar" else m ** -0.5
     ref = _manual(ens, m, n, T, 5, dtype, flags, dyn, a, sigma)
     tdt = torch.float64 if dtype == "f64" else torch.float32
+    monkeypatch.setenv("HD_DISABLE_FUSE", "1")
     st = hd.HD(ens, m, n, T, 5, dtype, sigma=sigma)
     spec = hd.make_run_spec(flags, dyn, a, use_graph=graph)
     x1 = torch.tensor(synth.x1(m if flags[0] else n, 5), dtype=tdt, device="cuda")
@@ -89,3 +91,38 @@ def test_run_host_buffers_and_dim_check():
                   torch.zeros(500, dtype=torch.float64, device="cuda"))
     assert ei.value.code == 2
     g.close()
+
+
+@pytest.mark.parametrize("graph", [False, True])
+@pytest.mark.parametrize("ens,m,n,dyn,a,dtype", [
+    ("haar", 10007, 10007, "sign_mem", 0.5, "f64"),
+    ("haar", 65_536, 65_536, "tanh", 0.0, "f32"),
+    ("haar", 4099, 4099, "tanh", 0.0, "f64"),
+    ("ginibre", 2001, 5003, "tanh", 0.0, "f64"),
+    ("ginibre", 30_011, 20_011, "tanh", 0.0, "f32"),
+    ("ginibre", 3001, 3001, "sign_mem", 0.5, "f64")])
+def test_fused_run_matches_apply(graph, ens, m, n, dyn, a, dtype):
+    """Q / Q^T alternating with an elementwise f_t: the output sweep of every step but the last
+    applies f_t and forms the next step's dot sweep.  The products are the same up to the
+    summation order of the dots (FP64 to 1e-12, FP32 to 1e-5 relative)."""
+    import paper_2101_07464_gb300 as hd
+    T = 16
+    flags = [t % 2 == 0 for t in range(1, T + 1)]
+    sigma = 1.0 if ens == "haar" else m ** -0.5
+    ref = _manual(ens, m, n, T, 7, dtype, flags, dyn, a, sigma)
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    st = hd.HD(ens, m, n, T, 7, dtype, sigma=sigma)
+    spec = hd.make_run_spec(flags, dyn, a, use_graph=graph)
+    x1 = torch.tensor(synth.x1(m if flags[0] else n, 7), dtype=tdt, device="cuda")
+    out = torch.empty(ref.numel(), dtype=tdt, device="cuda")
+    l0 = hd.hd_get_launches(st.h)
+    for rep in range(2):
+        hd.hd_run(st.h, spec, x1, out)
+        torch.cuda.synchronize()
+        rel = ((out.double() - ref.double()).norm() / ref.double().norm()).item()
+        assert rel <= (1e-12 if dtype == "f64" else 1e-5), rel
+    # two first-draw kernels, then two sweeps per step (the dot sweep of steps 2..T is done by
+    # the previous output sweep; step 1 has none) and one dynamics kernel after the last step
+    per_run = (hd.hd_get_launches(st.h) - l0) // 2
+    assert per_run == 2 + 2 * T + 1, per_run
+    st.close()

@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-amp", action="store_true", help="skip the batched AMP measurement")
     ap.add_argument("--amp-trials", type=int, default=4096)
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the reverse-mode measurement")
     return ap.parse_args()
 
 
@@ -167,7 +168,7 @@ class ClockSampler:
 
 # DRAM bytes / algorithmic bytes of one k_update launch (k = 60, n = 10^6, FP32) from an
 # ncu --set full capture of the current kernel; reset to None when the kernel changes.
-UPDATE_TRAFFIC_RATIO = None
+UPDATE_TRAFFIC_RATIO = 249.31 / 252.0
 
 
 def measured_peaks():
@@ -274,6 +275,60 @@ def measure_amp_batch(args, rank, world, dist):
             "config": "Gin(m_i, n_i), n_i ~ U{1000..100000}, m_i = n_i/2, AMP soft threshold 1.1 sigma_t"}
 
 
+def measure_adjoint(args, rank, world, dist):
+    """Reverse mode: gradient of <c, x_{T+1}> with respect to x_1 and the per-step parameters
+    theta_t of x_{t+1} = tanh(theta_t y_t) + 0.3 x_{t-1} on Haar(n), n = 10^6, T = 32 products
+    Q / Q^T alternating, FP32 storage (paper_2101_07464_gb300.autograd.trajectory: forward with
+    the library's steps recorded, backward through hd_adjoint_step).  Units n T^2 per
+    forward + backward."""
+    import numpy as np
+    import torch
+    import synth
+    import paper_2101_07464_gb300 as hd
+    from paper_2101_07464_gb300.autograd import trajectory
+    n, T = 10 ** 6, 32
+    sched = [t % 2 == 0 for t in range(1, T + 1)]
+    st = hd.HD("haar", n, n, T, args.seed, "f32", trial=rank)
+    x1 = torch.tensor(synth.x1(n, args.seed, trial=rank), dtype=torch.float32, device="cuda")
+    c = torch.tensor(synth.x1(n, args.seed + 1, trial=rank), dtype=torch.float32, device="cuda")
+    theta0 = torch.full((T,), 0.8, dtype=torch.float32, device="cuda")
+
+    def f(t, y, x, xprev, theta):
+        v = torch.tanh(theta[t - 1] * y)
+        return v if xprev is None else v + 0.3 * xprev
+
+    def one(backward):
+        x = x1.clone().requires_grad_(backward)
+        th = theta0.clone().requires_grad_(backward)
+        out = trajectory(st, x, sched, f, (th,))
+        L = torch.dot(c, out)
+        if backward:
+            L.backward()
+        return L
+
+    for _ in range(2):
+        one(True)
+    torch.cuda.synchronize()
+    steps = 3
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        one(True)
+    torch.cuda.synchronize()
+    fb = (time.perf_counter() - t0) / steps
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        with torch.no_grad():
+            one(False)
+    torch.cuda.synchronize()
+    fw = (time.perf_counter() - t0) / steps
+    st.close()
+    return {"metric": "n*T^2/s (forward + backward)", "value": float(n) * T * T * world / fb,
+            "ms_forward_backward": fb * 1e3, "ms_forward": fw * 1e3, "n": n, "T": T, "dtype": "f32",
+            "timing": "wall clock around synchronised whole calls (host-driven steps, torch f_t)",
+            "config": "Haar n=1e6, T=32, Q/Q^T alternating, x_{t+1} = tanh(theta_t y_t) + 0.3 x_{t-1}, "
+                      "d<c, x_{T+1}>/d(x_1, theta)"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -345,7 +400,7 @@ def run_ours(args):
                 "traffic": ((by / nl) * UPDATE_TRAFFIC_RATIO
                             if (nl and dom == "update" and UPDATE_TRAFFIC_RATIO) else None),
                 "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_update "
-                                  "launch at k = 60 (254.37 MB for 252.0 MB algorithmic), scaled to "
+                                  "launch at k = 60 (249.31 MB for 252.0 MB algorithmic), scaled to "
                                   "the average launch by algorithmic bytes",
                 "timing": "CUDA events on the launching stream around every sweep, recorded "
                           "in a second pass of the same trajectories (events inside the graph "
@@ -368,6 +423,9 @@ def run_ours(args):
     amp = None
     if not args.no_amp:
         amp = measure_amp_batch(args, rank, world, dist)
+    adj = None
+    if not args.no_adjoint:
+        adj = measure_adjoint(args, rank, world, dist)
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -390,7 +448,7 @@ def run_ours(args):
                 "roofline": roofline,
                 "step_credited_GBps": step_gbps,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk, "fp64": fp64, "batched_amp": amp}
+                "clocks": clk, "fp64": fp64, "batched_amp": amp, "adjoint": adj}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

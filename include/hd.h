@@ -225,8 +225,10 @@ HD_API int hd_philox_words(uint64_t seed, const uint32_t* counters, int64_t nblo
  * then on every forward step is recorded; with HD_ADJ_RECORD_X the library also keeps a copy
  * of each x_t (T_max vectors of the longer dimension, state dtype), otherwise the caller
  * passes x_t back to hd_adjoint_step (recomputing them, e.g. from checkpoints with hd_probe).
- * Allocates the accumulators once: per stack dim x T_max FP64 (dV) and T_max^2 FP64 (dS), per
- * Gin basis store dim x T_max FP64, plus 7 FP64 work vectors.  hd_run on a recording state
+ * Allocates the accumulators once: per stack dim x T_max elements of the state dtype (dV) and
+ * T_max^2 FP64 (dS), per Gin basis store dim x T_max of the state dtype, plus 4 work vectors.
+ * The streaming passes compute in the state's precision with FP64 cross-thread sums, as the
+ * forward sweeps do.  hd_run on a recording state
  * runs without its CUDA graph.  Errors: HD_ERR_ARG (batched state, unknown flag),
  * HD_ERR_STATE (steps already taken), HD_ERR_OOM, HD_ERR_CUDA. */
 #define HD_ADJ_RECORD_X 1

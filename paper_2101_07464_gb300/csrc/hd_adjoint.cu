@@ -41,11 +41,15 @@ namespace {
 
 constexpr int kAT = 256;   // threads of every adjoint kernel
 
-enum AdjVec { kVx, kVyb, kVp, kVub, kVqb, kVxb, kVg, kAdjVecs };
+enum AdjVec { kVp, kVub, kVqb, kVg, kAdjVecs };
 enum AdjSmall {
   kSz, kSw, kSh, kSbb, kSb, kScb, kSzb, kSwb, kSE, kSc, kShb, kSau, kSbu, kSbbu, kSabu, kSscal,
   kAdjSmall
 };
+
+// Precision: the streaming passes over the stacks run in the state's precision T (FP32 for an
+// FP32 state, as the forward sweeps do: GB300's FP64 rate would bound them otherwise); every
+// sum across threads or CTAs, the small coefficient vectors and Sbar are FP64.
 
 __device__ __forceinline__ double a_block_sum(double v, double* red) {
   v = warp_sum(v);
@@ -58,83 +62,93 @@ __device__ __forceinline__ double a_block_sum(double v, double* red) {
   return s;
 }
 
-template <typename T>
-__global__ void k_to_double(const T* __restrict__ in, double* __restrict__ out, int64_t n) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    out[i] = (double)in[i];
-}
-template <typename T>
-__global__ void k_from_double(const double* __restrict__ in, T* __restrict__ out, int64_t n) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    out[i] = (T)in[i];
-}
-
-// Partial column dots over one row chunk per CTA: part[(b K + j) 2 + v] = sum_r A[r, j] v_v[r].
+// Partial column dots: CTA (x, y) covers row chunk x and the 8 columns 8y..8y+7, one warp per
+// column; part[(x K + j) 2 + v] = sum over the chunk of A[r, j] v_v[r] (per-lane sums in T over
+// at most ~100 rows, eight loads in flight per lane, FP64 across lanes).
 template <typename T>
 __global__ void __launch_bounds__(kAT) k_colpass(const T* __restrict__ A, int64_t ld, int K, int64_t dim,
-                                                 const double* __restrict__ v1,
-                                                 const double* __restrict__ v2, double* part) {
+                                                 const T* __restrict__ v1, const T* __restrict__ v2,
+                                                 double* part) {
   const int64_t per = ((dim + gridDim.x - 1) / gridDim.x + 31) / 32 * 32;
   const int64_t r0 = (int64_t)blockIdx.x * per, r1 = min(dim, r0 + per);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int j = warp; j < K; j += nw) {
-    const T* Aj = A + (int64_t)j * ld;
-    double s1 = 0.0, s2 = 0.0;
-    for (int64_t r = r0 + lane; r < r1; r += 32) {
-      const double a = (double)Aj[r];
-      s1 = fma(a, v1[r], s1);
-      if (v2) s2 = fma(a, v2[r], s2);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int j = blockIdx.y * 8 + warp;
+  if (j >= K) return;
+  const T* Aj = A + (int64_t)j * ld;
+  T s1 = T(0), s2 = T(0), t1 = T(0), t2 = T(0);
+  int64_t r = r0 + lane;
+#pragma unroll 4
+  for (; r + 32 < r1; r += 64) {
+    const T a0 = Aj[r], a1 = Aj[r + 32];
+    s1 = fma(a0, v1[r], s1);
+    t1 = fma(a1, v1[r + 32], t1);
+    if (v2) {
+      s2 = fma(a0, v2[r], s2);
+      t2 = fma(a1, v2[r + 32], t2);
     }
-    s1 = warp_sum(s1);
-    s2 = warp_sum(s2);
-    if (lane == 0) {
-      part[((int64_t)blockIdx.x * K + j) * 2] = s1;
-      part[((int64_t)blockIdx.x * K + j) * 2 + 1] = s2;
-    }
+  }
+  if (r < r1) {
+    const T a0 = Aj[r];
+    s1 = fma(a0, v1[r], s1);
+    if (v2) s2 = fma(a0, v2[r], s2);
+  }
+  const double d1 = warp_sum((double)s1 + (double)t1);
+  const double d2 = warp_sum((double)s2 + (double)t2);
+  if (lane == 0) {
+    part[((int64_t)blockIdx.x * K + j) * 2] = d1;
+    part[((int64_t)blockIdx.x * K + j) * 2 + 1] = d2;
   }
 }
 
-// out_v[j] = scale_v * sum over CTAs of the partials (fixed order: deterministic).
+// out_v[j] = scale_v * sum over the nblk row chunks of the partials: one warp per column, the
+// lanes over the chunks, then a shuffle reduction (fixed order: deterministic).
 __global__ void __launch_bounds__(kAT) k_colreduce(const double* __restrict__ part, int nblk, int K,
                                                    double s1, double* out1, double s2, double* out2) {
-  for (int j = threadIdx.x; j < K; j += blockDim.x) {
-    double a = 0.0, b = 0.0;
-    for (int q = 0; q < nblk; q++) {
-      a += part[((int64_t)q * K + j) * 2];
-      b += part[((int64_t)q * K + j) * 2 + 1];
-    }
+  const int lane = threadIdx.x & 31;
+  const int j = blockIdx.x * (kAT / 32) + (threadIdx.x >> 5);
+  if (j >= K) return;
+  double a = 0.0, b = 0.0;
+  for (int q = lane; q < nblk; q += 32) {
+    a += part[((int64_t)q * K + j) * 2];
+    b += part[((int64_t)q * K + j) * 2 + 1];
+  }
+  a = warp_sum(a);
+  b = warp_sum(b);
+  if (lane == 0) {
     out1[j] = s1 * a;
     if (out2) out2[j] = s2 * b;
   }
 }
 
 // out[r] (+)= sgn(r) (s_in in[r] + c_scale sum_{j<K} A[r, j] c[j]), sgn(r) = dpre[min(r+1, Kd)]
-// (or 1); optionally per-CTA partial sums of out[r]^2 over r >= rnorm.
+// (or 1); optionally per-CTA FP64 partial sums of out[r]^2 over r >= rnorm.
 template <typename T>
-__global__ void __launch_bounds__(kAT) k_rowpass(double* out, const double* in, double s_in, const T* __restrict__ A,
+__global__ void __launch_bounds__(kAT) k_rowpass(T* out, const T* in, double s_in, const T* __restrict__ A,
                                                  int64_t ld, int K, const double* __restrict__ c, double c_scale,
                                                  int64_t dim, const double* __restrict__ dpre, int Kd,
                                                  int accumulate, int64_t rnorm, double* npart) {
-  __shared__ double cs[kTmaxLimit + 1];
+  __shared__ T cs[kTmaxLimit + 1];
   __shared__ double red[kAT / 32];
-  for (int j = threadIdx.x; j < K; j += blockDim.x) cs[j] = c_scale * c[j];
+  for (int j = threadIdx.x; j < K; j += blockDim.x) cs[j] = (T)(c_scale * c[j]);
   __syncthreads();
+  const T si = (T)s_in;
   double ns = 0.0;
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < dim; r += (int64_t)gridDim.x * blockDim.x) {
-    double v = in ? s_in * in[r] : 0.0;
+    T v0 = in ? si * in[r] : T(0), v1 = T(0), v2 = T(0), v3 = T(0);
     const T* Ar = A + r;
     int j = 0;
     for (; j + 4 <= K; j += 4) {
-      v = fma((double)Ar[(int64_t)j * ld], cs[j], v);
-      v = fma((double)Ar[(int64_t)(j + 1) * ld], cs[j + 1], v);
-      v = fma((double)Ar[(int64_t)(j + 2) * ld], cs[j + 2], v);
-      v = fma((double)Ar[(int64_t)(j + 3) * ld], cs[j + 3], v);
+      v0 = fma(Ar[(int64_t)j * ld], cs[j], v0);
+      v1 = fma(Ar[(int64_t)(j + 1) * ld], cs[j + 1], v1);
+      v2 = fma(Ar[(int64_t)(j + 2) * ld], cs[j + 2], v2);
+      v3 = fma(Ar[(int64_t)(j + 3) * ld], cs[j + 3], v3);
     }
-    for (; j < K; j++) v = fma((double)Ar[(int64_t)j * ld], cs[j], v);
-    if (dpre) v *= dpre[min(r + 1, (int64_t)Kd)];
+    for (; j < K; j++) v0 = fma(Ar[(int64_t)j * ld], cs[j], v0);
+    T v = (v0 + v1) + (v2 + v3);
+    if (dpre) v *= (T)dpre[min(r + 1, (int64_t)Kd)];
     if (accumulate) v += out[r];
     out[r] = v;
-    if (r >= rnorm) ns = fma(v, v, ns);
+    if (r >= rnorm) ns = fma((double)v, (double)v, ns);
   }
   if (npart) {
     ns = a_block_sum(ns, red);
@@ -143,33 +157,46 @@ __global__ void __launch_bounds__(kAT) k_rowpass(double* out, const double* in, 
 }
 
 // Ab[r, j] += sb a[r] b[j] + sd c[r] d[j] for r < dim, j < K (column-major, leading dim ld).
-__global__ void __launch_bounds__(kAT) k_rank(double* Ab, int64_t ld, int K, int64_t dim,
-                                              const double* __restrict__ a, const double* __restrict__ b, double sb,
-                                              const double* __restrict__ c, const double* __restrict__ d, double sd) {
+template <typename T>
+__global__ void __launch_bounds__(kAT) k_rank(T* Ab, int64_t ld, int K, int64_t dim, const T* __restrict__ a,
+                                              const double* __restrict__ b, double sb, const T* __restrict__ c,
+                                              const double* __restrict__ d, double sd) {
+  __shared__ T bs[8], ds[8];
   const int j0 = blockIdx.y * 8;
+  if (threadIdx.x < 8) {
+    const int j = j0 + threadIdx.x;
+    bs[threadIdx.x] = (j < K) ? (T)(sb * b[j]) : T(0);
+    ds[threadIdx.x] = (j < K && c) ? (T)(sd * d[j]) : T(0);
+  }
+  __syncthreads();
+  const int jn = min(K, j0 + 8) - j0;
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < dim; r += (int64_t)gridDim.x * blockDim.x) {
-    const double ar = sb * a[r];
-    const double cr = c ? sd * c[r] : 0.0;
-    for (int j = j0; j < min(K, j0 + 8); j++) {
-      double v = ar * b[j];
-      if (c) v = fma(cr, d[j], v);
-      Ab[r + (int64_t)j * ld] += v;
+    const T ar = a[r];
+    const T cr = c ? c[r] : T(0);
+    for (int q = 0; q < jn; q++) {
+      T v = ar * bs[q];
+      if (c) v = fma(cr, ds[q], v);
+      Ab[r + (int64_t)(j0 + q) * ld] += v;
     }
   }
 }
 
 // out = scale S v (trans = 0) or scale S^T v (trans = 1), leading K x K block of the upper
-// triangular S (column-major, leading dim Tm).
-__global__ void __launch_bounds__(kAT) k_tri(const double* __restrict__ S, int Tm, int K, const double* __restrict__ v,
-                                             double scale, int trans, double* out) {
-  for (int i = threadIdx.x; i < K; i += blockDim.x) {
+// triangular S (column-major, leading dim Tm): one warp per output, lanes over the sum.
+constexpr int kSmallT = 1024;   // threads of the small FP64 kernels (FP64 latency wants many warps)
+__global__ void __launch_bounds__(kSmallT) k_tri(const double* __restrict__ S, int Tm, int K,
+                                                 const double* __restrict__ v, double scale, int trans,
+                                                 double* out) {
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int i = threadIdx.x >> 5; i < K; i += nw) {
     double s = 0.0;
     if (!trans) {
-      for (int j = i; j < K; j++) s = fma(S[i + (int64_t)j * Tm], v[j], s);
+      for (int j = i + lane; j < K; j += 32) s = fma(S[i + (int64_t)j * Tm], v[j], s);
     } else {
-      for (int q = 0; q <= i; q++) s = fma(S[q + (int64_t)i * Tm], v[q], s);
+      for (int q = lane; q <= i; q += 32) s = fma(S[q + (int64_t)i * Tm], v[q], s);
     }
-    out[i] = scale * s;
+    s = warp_sum(s);
+    if (lane == 0) out[i] = scale * s;
   }
 }
 
@@ -183,102 +210,111 @@ __global__ void __launch_bounds__(kAT) k_outer_upper(double* Sb, int Tm, int K, 
 }
 
 // E = Gbar[:, j] + Gbar[j, :]^T with Gbar = upper(M) (half diagonal), M = -S^T Sbar S^T, over
-// the K columns of the stack: E[i] = M[i, j] for i <= j, M[j, i] for i > j.
-__global__ void __launch_bounds__(kAT) k_gbar(const double* __restrict__ S, const double* __restrict__ Sb, int Tm,
-                                              int K, int j, double* E) {
+// the K columns of the stack: E[i] = M[i, j] for i <= j, M[j, i] for i > j.  One warp per
+// output, lanes over the sums.
+__global__ void __launch_bounds__(kSmallT) k_gbar(const double* __restrict__ S, const double* __restrict__ Sb,
+                                                  int Tm, int K, int j, double* E) {
   __shared__ double r1[kTmaxLimit + 1], r2[kTmaxLimit + 1];
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const bool ident = S[j + (int64_t)j * Tm] == 0.0;   // identity reflector: no free column
-  for (int a = threadIdx.x; a < K; a += blockDim.x) {
+  for (int a = threadIdx.x >> 5; a < K; a += nw) {
     double s1 = 0.0, s2 = 0.0;
-    for (int b = j; b < K; b++) s1 = fma(Sb[a + (int64_t)b * Tm], S[j + (int64_t)b * Tm], s1);   // (Sbar S[j, :]^T)_a
-    for (int q = 0; q <= j; q++) s2 = fma(S[q + (int64_t)j * Tm], Sb[q + (int64_t)a * Tm], s2);   // (Sbar^T S[:, j])_a
-    r1[a] = s1;
-    r2[a] = s2;
+    for (int b = j + lane; b < K; b += 32) s1 = fma(Sb[a + (int64_t)b * Tm], S[j + (int64_t)b * Tm], s1);
+    for (int q = lane; q <= j; q += 32) s2 = fma(S[q + (int64_t)j * Tm], Sb[q + (int64_t)a * Tm], s2);
+    s1 = warp_sum(s1);
+    s2 = warp_sum(s2);
+    if (lane == 0) {
+      r1[a] = s1;   // (Sbar S[j, :]^T)_a
+      r2[a] = s2;   // (Sbar^T S[:, j])_a
+    }
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < K; i += blockDim.x) {
+  for (int i = threadIdx.x >> 5; i < K; i += nw) {
     double s = 0.0;
     if (!ident) {
       if (i <= j) {
-        for (int a = 0; a <= i; a++) s = fma(S[a + (int64_t)i * Tm], r1[a], s);
+        for (int a = lane; a <= i; a += 32) s = fma(S[a + (int64_t)i * Tm], r1[a], s);
       } else {
-        for (int b = i; b < K; b++) s = fma(S[i + (int64_t)b * Tm], r2[b], s);
+        for (int b = i + lane; b < K; b += 32) s = fma(S[i + (int64_t)b * Tm], r2[b], s);
       }
     }
-    E[i] = -s;
+    s = warp_sum(s);
+    if (lane == 0) E[i] = -s;
   }
 }
 
-// alpha = ||p[kD:]|| from the row-pass partials, s = sign(p[kD]) (+1 at 0).
-__global__ void k_alpha(const double* __restrict__ npart, int nb, const double* __restrict__ p, int kD, double* scal) {
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int q = 0; q < nb; q++) s += npart[q];
-    scal[0] = sqrt(s);
-    scal[1] = (p[kD] >= 0.0) ? 1.0 : -1.0;
-  }
-}
-
-// c = [p[0:k]; alpha]
-__global__ void k_head_alpha(const double* __restrict__ p, int k, const double* __restrict__ scal, double* c) {
-  for (int i = threadIdx.x; i <= k; i += blockDim.x) c[i] = (i < k) ? p[i] : scal[0];
+// c = [p_head[0:k]; alpha] from the step's record
+__global__ void k_head_alpha(const double* __restrict__ phead, int k, const double* __restrict__ rs, double* c) {
+  for (int i = threadIdx.x; i <= k; i += blockDim.x) c[i] = (i < k) ? phead[i] : rs[1];
 }
 
 // Adjoint of the output product y = (I - V S V^T) Delta c for c supported on rows < nc <= Ke
 // (Ke reflectors).  Given bb = -V^T ybar (from a column pass) and the head of ybar: writes
 // b = S a (for Vbar += -ybar b^T, done by the caller), cbar = Delta (ybar + V S^T bb) on the
-// first nc rows, and adds Sbar += bb a^T and Vbar[:nc, :] += (Delta c) (S^T bb)^T.
+// first nc rows, and adds Sbar += bb a^T and Vbar[:nc, :] += (Delta c) (S^T bb)^T.  One warp
+// per output, lanes over the sums.
 template <typename T>
-__global__ void __launch_bounds__(kAT) k_out_small(const T* __restrict__ V, int64_t ld, int Ke, int nc,
-                                                   const double* __restrict__ S, int Tm,
-                                                   const double* __restrict__ dpre, const double* __restrict__ c,
-                                                   const double* __restrict__ bb, const double* __restrict__ ybd,
-                                                   double* Sb, double* Vb, double* b_out, double* cbar) {
+__global__ void __launch_bounds__(kSmallT) k_out_small(const T* __restrict__ V, int64_t ld, int Ke, int nc,
+                                                       const double* __restrict__ S, int Tm,
+                                                       const double* __restrict__ dpre, const double* __restrict__ c,
+                                                       const double* __restrict__ bb, const T* __restrict__ ybd,
+                                                       double* Sb, T* Vb, double* b_out, double* cbar) {
   __shared__ double cp[kTmaxLimit + 1], a[kTmaxLimit + 1], ab[kTmaxLimit + 1];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int i = threadIdx.x; i < nc; i += blockDim.x) cp[i] = dpre[i + 1] * c[i];
   __syncthreads();
-  for (int j = threadIdx.x; j < Ke; j += blockDim.x) {
+  for (int j = wid; j < Ke; j += nw) {   // a = V^T Delta c (rows j..nc-1 of column j)
     double s = 0.0;
-    for (int i = j; i < nc; i++) s = fma((double)V[i + (int64_t)j * ld], cp[i], s);
-    a[j] = s;
+    for (int i = j + lane; i < nc; i += 32) s = fma((double)V[i + (int64_t)j * ld], cp[i], s);
+    s = warp_sum(s);
+    if (lane == 0) a[j] = s;
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < Ke; i += blockDim.x) {
+  for (int i = wid; i < Ke; i += nw) {   // b = S a, abar = S^T bb
     double sb = 0.0, sa = 0.0;
-    for (int j = i; j < Ke; j++) sb = fma(S[i + (int64_t)j * Tm], a[j], sb);
-    for (int q = 0; q <= i; q++) sa = fma(S[q + (int64_t)i * Tm], bb[q], sa);
-    b_out[i] = sb;
-    ab[i] = sa;
+    for (int j = i + lane; j < Ke; j += 32) sb = fma(S[i + (int64_t)j * Tm], a[j], sb);
+    for (int q = lane; q <= i; q += 32) sa = fma(S[q + (int64_t)i * Tm], bb[q], sa);
+    sb = warp_sum(sb);
+    sa = warp_sum(sa);
+    if (lane == 0) {
+      b_out[i] = sb;
+      ab[i] = sa;
+    }
   }
   __syncthreads();
   for (int idx = threadIdx.x; idx < Ke * Ke; idx += blockDim.x) {
     const int i = idx % Ke, j = idx / Ke;
     if (i <= j) Sb[i + (int64_t)j * Tm] += bb[i] * a[j];
   }
-  for (int i = threadIdx.x; i < nc; i += blockDim.x) {
-    double s = ybd[i];
+  for (int i = wid; i < nc; i += nw) {   // cbar = Delta (ybar + V abar) on rows < nc
     const int jm = min(i, Ke - 1);
-    for (int j = 0; j <= jm; j++) {
+    double s = 0.0;
+    for (int j = lane; j <= jm; j += 32) {
       s = fma((double)V[i + (int64_t)j * ld], ab[j], s);
-      Vb[i + (int64_t)j * ld] += cp[i] * ab[j];
+      Vb[i + (int64_t)j * ld] += (T)(cp[i] * ab[j]);
     }
-    cbar[i] = dpre[i + 1] * s;
+    s = warp_sum(s);
+    if (lane == 0) cbar[i] = dpre[i + 1] * ((double)ybd[i] + s);
   }
 }
 
 // qbar = Delta_D pbar with pbar[r] = cb[r] (r < kD) and, on the tail, the adjoint of the new
-// column u = p[kD:] + s alpha e_kD and of alpha: (cb[kD] + s ub[kD]) p[r] / alpha + ub[r].
-__global__ void __launch_bounds__(kAT) k_pbar(double* __restrict__ qbar, const double* __restrict__ p,
-                                              const double* __restrict__ ub, const double* __restrict__ cb,
-                                              const double* __restrict__ scal, int kD,
+// column u = p[kD:] + s alpha e_kD and of alpha: (cb[kD] + s ub[kD]) p[r] / alpha + ub[r].  The
+// tail of p is read back from the stored column (p[r] = u[r] for r > kD, p[kD] recorded).
+// rs = the step's record: rs[0] = p[kD], rs[1] = alpha.
+template <typename T>
+__global__ void __launch_bounds__(kAT) k_pbar(T* __restrict__ qbar, const T* __restrict__ u,
+                                              const T* __restrict__ ub, const double* __restrict__ cb,
+                                              const double* __restrict__ rs, int kD,
                                               const double* __restrict__ dpre, int64_t dim) {
-  const double alpha = scal[0], s = scal[1];
-  const double coef = (alpha > 0.0) ? (cb[kD] + s * ub[kD]) / alpha : 0.0;
+  const double ppiv = rs[0], alpha = rs[1];
+  const double s = (ppiv >= 0.0) ? 1.0 : -1.0;
+  const T coef = (alpha > 0.0) ? (T)((cb[kD] + s * (double)ub[kD]) / alpha) : T(0);
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < dim; r += (int64_t)gridDim.x * blockDim.x) {
-    double pb;
-    if (r < kD) pb = cb[r];
-    else pb = (alpha > 0.0) ? fma(coef, p[r], ub[r]) : 0.0;
-    qbar[r] = dpre[min(r + 1, (int64_t)kD)] * pb;
+    T pb;
+    if (r < kD) pb = (T)cb[r];
+    else pb = (alpha > 0.0) ? fma(coef, (r == kD) ? (T)ppiv : u[r], ub[r]) : T(0);
+    qbar[r] = (T)dpre[min(r + 1, (int64_t)kD)] * pb;
   }
 }
 
@@ -286,14 +322,14 @@ __global__ void __launch_bounds__(kAT) k_pbar(double* __restrict__ qbar, const d
 // 0 elsewhere; sgn = *sgnp.
 template <typename T>
 __global__ void __launch_bounds__(kAT) k_draw_d(DrawKey key, int64_t first, int64_t dim, T sigma,
-                                                const double* __restrict__ sgnp, double* out) {
-  const double sg = *sgnp;
+                                                const double* __restrict__ sgnp, T* out) {
+  const T sg = (T)*sgnp;
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < dim; r += (int64_t)gridDim.x * blockDim.x) {
-    double v = 0.0;
+    T v = T(0);
     if (r >= first) {
       T a, b;
       normal_pair(key, (uint64_t)(r >> 1), a, b);
-      v = sg * (double)(sigma * ((r & 1) ? b : a));
+      v = sg * (sigma * ((r & 1) ? b : a));
     }
     out[r] = v;
   }
@@ -304,7 +340,6 @@ __global__ void __launch_bounds__(kAT) k_draw_d(DrawKey key, int64_t first, int6
 struct Ctx {
   hd_state* st;
   cudaStream_t s;
-  unsigned grid;
 };
 
 unsigned rows_grid(const hd_state* st, int64_t dim) {
@@ -313,27 +348,28 @@ unsigned rows_grid(const hd_state* st, int64_t dim) {
 }
 
 template <typename T>
-void colpass(const Ctx& c, const T* A, int64_t ld, int K, int64_t dim, const double* v1, double s1, double* o1,
-             const double* v2 = nullptr, double s2 = 0.0, double* o2 = nullptr) {
+void colpass(const Ctx& c, const T* A, int64_t ld, int K, int64_t dim, const T* v1, double s1, double* o1,
+             const T* v2 = nullptr, double s2 = 0.0, double* o2 = nullptr) {
   if (K <= 0) return;
   AdjState& A_ = *c.st->adj;
-  k_colpass<T><<<A_.nblk, kAT, 0, c.s>>>(A, ld, K, dim, v1, v2, A_.part);
-  k_colreduce<<<1, kAT, 0, c.s>>>(A_.part, A_.nblk, K, s1, o1, s2, o2);
+  k_colpass<T><<<dim3(A_.nblk, (K + 7) / 8), kAT, 0, c.s>>>(A, ld, K, dim, v1, v2, A_.part);
+  k_colreduce<<<(K + kAT / 32 - 1) / (kAT / 32), kAT, 0, c.s>>>(A_.part, A_.nblk, K, s1, o1, s2, o2);
 }
 
 template <typename T>
-void rowpass(const Ctx& c, double* out, const double* in, double s_in, const T* A, int64_t ld, int K,
-             const double* coef, double cscale, int64_t dim, const double* dpre, int Kd, int acc,
-             int64_t rnorm = INT64_MAX, double* npart = nullptr, unsigned grid = 0) {
+void rowpass(const Ctx& c, T* out, const T* in, double s_in, const T* A, int64_t ld, int K, const double* coef,
+             double cscale, int64_t dim, const double* dpre, int Kd, int acc, int64_t rnorm = INT64_MAX,
+             double* npart = nullptr, unsigned grid = 0) {
   const unsigned g = grid ? grid : rows_grid(c.st, dim);
   k_rowpass<T><<<g, kAT, 0, c.s>>>(out, in, s_in, A, ld, K, coef, cscale, dim, dpre, Kd, acc, rnorm, npart);
 }
 
-void rank(const Ctx& c, double* Ab, int64_t ld, int K, int64_t dim, const double* a, const double* b, double sb,
-          const double* cc = nullptr, const double* d = nullptr, double sd = 0.0) {
+template <typename T>
+void rank(const Ctx& c, T* Ab, int64_t ld, int K, int64_t dim, const T* a, const double* b, double sb,
+          const T* cc = nullptr, const double* d = nullptr, double sd = 0.0) {
   if (K <= 0) return;
   dim3 g(rows_grid(c.st, dim), (unsigned)((K + 7) / 8));
-  k_rank<<<g, kAT, 0, c.s>>>(Ab, ld, K, dim, a, b, sb, cc, d, sd);
+  k_rank<T><<<g, kAT, 0, c.s>>>(Ab, ld, K, dim, a, b, sb, cc, d, sd);
 }
 
 template <typename T>
@@ -350,20 +386,19 @@ int adj_step(hd_state* st, const void* ybar, const void* x_in, void* xbar) {
   const int Kfin_d = haar ? st->t : (d == 0 ? st->r : st->l);
   const T* Vd = (const T*)Sd.V;
   const T* Ve = (const T*)Se.V;
+  T* Vbd = (T*)A.Vbar[d];
+  T* Vbe = (T*)A.Vbar[e];
   const int Tm = st->Sld;   // leading dimension of S and Sbar
-  const Ctx c{st, st->stream, 0};
+  const Ctx c{st, st->stream};
   const int64_t L = A.dmax;
-  double* xd = A.vec + kVx * L;
-  double* ybd = A.vec + kVyb * L;
-  double* p = A.vec + kVp * L;
-  double* ub = A.vec + kVub * L;
-  double* qb = A.vec + kVqb * L;
-  double* xb = A.vec + kVxb * L;
-  double* gd = A.vec + kVg * L;
+  T* vec = (T*)A.vec;
+  T* ub = vec + kVub * L;
+  T* qb = vec + kVqb * L;
+  T* gd = vec + kVg * L;
+  const T* xd = x_in ? (const T*)x_in : (const T*)((const char*)A.X + (size_t)(t - 1) * A.ldx * sizeof(T));
+  const T* ybd = (const T*)ybar;
+  T* xb = (T*)xbar;
   auto sm = [&](int slot) { return A.small + (int64_t)slot * A.small_ld; };
-  double* z = sm(kSz);
-  double* w = sm(kSw);
-  double* h = sm(kSh);
   double* bb = sm(kSbb);
   double* bo = sm(kSb);
   double* cb = sm(kScb);
@@ -376,73 +411,72 @@ int adj_step(hd_state* st, const void* ybar, const void* x_in, void* xbar) {
   double* bu = sm(kSbu);
   double* bbu = sm(kSbbu);
   double* abu = sm(kSabu);
-  double* scal = sm(kSscal);
   const unsigned gv = rows_grid(st, std::max(nd, ne));
 
-  // forward quantities of step t: z = V_D^T x, (Gin) h = B_D^T x, w = S_D^T z, p, alpha, s
-  const void* xsrc = x_in ? x_in : (const void*)((const char*)A.X + (size_t)(t - 1) * A.ldx * sizeof(T));
-  k_to_double<T><<<gv, kAT, 0, c.s>>>((const T*)xsrc, xd, nd);
-  k_to_double<T><<<gv, kAT, 0, c.s>>>((const T*)ybar, ybd, ne);
-  colpass<T>(c, Vd, Sd.ld, kD, nd, xd, 1.0, z);
-  if (!haar) colpass<T>(c, (const T*)td.basis[d], td.ldb[d], kN, nd, xd, 1.0, h);
-  if (kD > 0) k_tri<<<1, kAT, 0, c.s>>>(Sd.S, Tm, kD, z, 1.0, 1, w);
+  // forward quantities of step t, recorded after it: z = V_D^T x, (Gin) h = B_D^T x, w, p_head,
+  // p's pivot entry and alpha; p's tail is the stored column u of V_D (minus s alpha at the pivot)
+  const double* rz = A.rec + (int64_t)(t - 1) * A.rec_ld;
+  const double* z = rz;
+  const double* h = rz + kD;
+  const double* w = rz + st->Sld;
+  const double* phead = rz + 2 * (int64_t)st->Sld;
+  const double* rs = rz + 3 * (int64_t)st->Sld;
+  const T* ucol = Vd + (int64_t)kD * Sd.ld;
   const unsigned gp = rows_grid(st, nd);
-  rowpass<T>(c, p, xd, 1.0, Vd, Sd.ld, kD, w, -1.0, nd, Sd.dpre, kD, 0, kD, A.part, gp);
-  k_alpha<<<1, 32, 0, c.s>>>(A.part, (int)gp, p, kD, scal);
 
   // output product
   if (haar) {
     const int Ke = kD + 1;   // the other stack including this step's random reflector
     colpass<T>(c, Ve, Se.ld, Ke, ne, ybd, -1.0, bb);
-    k_head_alpha<<<1, kAT, 0, c.s>>>(p, kD, scal, cv);
-    k_out_small<T><<<1, kAT, 0, c.s>>>(Ve, Se.ld, Ke, kD + 1, Se.S, Tm, Se.dpre, cv, bb, ybd, A.Sbar[e],
-                                      A.Vbar[e], bo, cb);
-    rank(c, A.Vbar[e], Se.ld, Ke, ne, ybd, bo, -1.0);
+    k_head_alpha<<<1, kAT, 0, c.s>>>(phead, kD, rs, cv);
+    k_out_small<T><<<1, kSmallT, 0, c.s>>>(Ve, Se.ld, Ke, kD + 1, Se.S, Tm, Se.dpre, cv, bb, ybd, A.Sbar[e], Vbe,
+                                      bo, cb);
+    rank<T>(c, Vbe, Se.ld, Ke, ne, ybd, bo, -1.0);
   } else {
     if (kN > 0) {
       colpass<T>(c, Ve, Se.ld, kN, ne, ybd, -1.0, bb);
-      k_out_small<T><<<1, kAT, 0, c.s>>>(Ve, Se.ld, kN, kN, Se.S, Tm, Se.dpre, h, bb, ybd, A.Sbar[e],
-                                        A.Vbar[e], bo, hb);
-      rank(c, A.Vbar[e], Se.ld, kN, ne, ybd, bo, -1.0);
+      k_out_small<T><<<1, kSmallT, 0, c.s>>>(Ve, Se.ld, kN, kN, Se.S, Tm, Se.dpre, h, bb, ybd, A.Sbar[e], Vbe, bo,
+                                        hb);
+      rank<T>(c, Vbe, Se.ld, kN, ne, ybd, bo, -1.0);
     }
     const T* Be = (const T*)td.basis[e];
     const int64_t lde = td.ldb[e];
+    T* Bbe = (T*)A.Bbar[e];
     colpass<T>(c, Be, lde, kD + 1, ne, ybd, 1.0, cb);         // [pbar_head; alphabar]
-    k_head_alpha<<<1, kAT, 0, c.s>>>(p, kD, scal, cv);          // [p_head; alpha]
-    rank(c, A.Bbar[e], lde, kD + 1, ne, ybd, cv, 1.0);
+    k_head_alpha<<<1, kAT, 0, c.s>>>(phead, kD, rs, cv);        // [p_head; alpha]
+    rank<T>(c, Bbe, lde, kD + 1, ne, ybd, cv, 1.0);
     if (kN > 0) {
       // the basis column built at this step, u = (I - V_N S_N V_N^T) Delta_N g: its adjoint
       // is complete; g is constant
-      const double* ubar_b = A.Bbar[e] + (int64_t)kD * lde;
+      const T* ubar_b = Bbe + (int64_t)kD * lde;
       DrawKey key = key_for(st, t);
       k_draw_d<T><<<gv, kAT, 0, c.s>>>(key, kN, ne, (T)td.sigma, Se.dpre + kN, gd);
       colpass<T>(c, Ve, Se.ld, kN, ne, ubar_b, -1.0, bbu, gd, 1.0, au);
-      k_tri<<<1, kAT, 0, c.s>>>(Se.S, Tm, kN, au, 1.0, 0, bu);
-      k_tri<<<1, kAT, 0, c.s>>>(Se.S, Tm, kN, bbu, 1.0, 1, abu);
+      k_tri<<<1, kSmallT, 0, c.s>>>(Se.S, Tm, kN, au, 1.0, 0, bu);
+      k_tri<<<1, kSmallT, 0, c.s>>>(Se.S, Tm, kN, bbu, 1.0, 1, abu);
       k_outer_upper<<<1, kAT, 0, c.s>>>(A.Sbar[e], Tm, kN, bbu, au);
-      rank(c, A.Vbar[e], Se.ld, kN, ne, ubar_b, bu, -1.0, gd, abu, 1.0);
+      rank<T>(c, Vbe, Se.ld, kN, ne, ubar_b, bu, -1.0, gd, abu, 1.0);
     }
   }
 
   // the data-side reflector of this step (column kD of V_D)
-  k_gbar<<<1, kAT, 0, c.s>>>(Sd.S, A.Sbar[d], Tm, Kfin_d, kD, E);
-  rowpass<T>(c, ub, A.Vbar[d] + (int64_t)kD * Sd.ld, 1.0, Vd, Sd.ld, Kfin_d, E, 1.0, nd, nullptr, 0, 0);
-  k_pbar<<<gp, kAT, 0, c.s>>>(qb, p, ub, cb, scal, kD, Sd.dpre, nd);
+  k_gbar<<<1, kSmallT, 0, c.s>>>(Sd.S, A.Sbar[d], Tm, Kfin_d, kD, E);
+  rowpass<T>(c, ub, Vbd + (int64_t)kD * Sd.ld, 1.0, Vd, Sd.ld, Kfin_d, E, 1.0, nd, nullptr, 0, 0);
+  k_pbar<T><<<gp, kAT, 0, c.s>>>(qb, ucol, ub, cb, rs, kD, Sd.dpre, nd);
 
   // the data product p = Delta (I - V S^T V^T) x
   colpass<T>(c, Vd, Sd.ld, kD, nd, qb, -1.0, wb);
   if (kD > 0) {
-    k_tri<<<1, kAT, 0, c.s>>>(Sd.S, Tm, kD, wb, 1.0, 0, zb);
-    k_outer_upper<<<1, kAT, 0, c.s>>>(A.Sbar[d], Tm, kD, z, wb);
+    k_tri<<<1, kSmallT, 0, c.s>>>(Sd.S, Tm, kD, wb, 1.0, 0, zb);
+    k_outer_upper<<<1, kAT, 0, c.s>>>(A.Sbar[d], Tm, kD, z, wb);   // Sbar += z wbar^T
   }
   rowpass<T>(c, xb, qb, 1.0, Vd, Sd.ld, kD, zb, 1.0, nd, nullptr, 0, 0);
   if (!haar && kN > 0) {
     const T* Bd = (const T*)td.basis[d];
     rowpass<T>(c, xb, nullptr, 0.0, Bd, td.ldb[d], kN, hb, 1.0, nd, nullptr, 0, 1);
-    rank(c, A.Bbar[d], td.ldb[d], kN, nd, xd, hb, 1.0);
+    rank<T>(c, (T*)A.Bbar[d], td.ldb[d], kN, nd, xd, hb, 1.0);
   }
-  rank(c, A.Vbar[d], Sd.ld, kD, nd, qb, w, -1.0, xd, zb, 1.0);
-  k_from_double<T><<<gv, kAT, 0, c.s>>>(xb, (T*)xbar, nd);
+  rank<T>(c, Vbd, Sd.ld, kD, nd, qb, w, -1.0, xd, zb, 1.0);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return cuda_fail(st, err);
   A.rev -= 1;
@@ -453,10 +487,10 @@ int adj_zero(hd_state* st) {
   AdjState& A = *st->adj;
   const TrialDesc& td = st->hdesc[0];
   for (int s = 0; s < 2; s++) {
-    if (cudaMemsetAsync(A.Vbar[s], 0, (size_t)td.st[s].ld * st->Tm * sizeof(double), st->stream) != cudaSuccess ||
+    if (cudaMemsetAsync(A.Vbar[s], 0, (size_t)td.st[s].ld * st->Tm * st->esz, st->stream) != cudaSuccess ||
         cudaMemsetAsync(A.Sbar[s], 0, (size_t)st->Sld * st->Sld * sizeof(double), st->stream) != cudaSuccess)
       return cuda_fail(st, cudaGetLastError());
-    if (A.Bbar[s] && cudaMemsetAsync(A.Bbar[s], 0, (size_t)td.ldb[s] * st->Tm * sizeof(double), st->stream) != cudaSuccess)
+    if (A.Bbar[s] && cudaMemsetAsync(A.Bbar[s], 0, (size_t)td.ldb[s] * st->Tm * st->esz, st->stream) != cudaSuccess)
       return cuda_fail(st, cudaGetLastError());
   }
   return HD_OK;
@@ -478,6 +512,26 @@ int adj_record_step(hd_state* st, const void* x, int transpose, int kD, int kN) 
     if (e != cudaSuccess) return cuda_fail(st, e);
   }
   A.rev = st->t + 1;
+  return HD_OK;
+}
+
+// Called by the forward step after its launches: copy the step's small vectors from the
+// workspace (they are overwritten by the next step).
+int adj_record_after(hd_state* st, int kD, int kN) {
+  AdjState& A = *st->adj;
+  const Ws& ws = st->hdesc[0].ws;
+  double* r = A.rec + (int64_t)(st->t) * A.rec_ld;   // st->t is still this step's index
+  const int64_t L = st->Sld;
+  cudaError_t e = cudaSuccess;
+  const int nz = (st->ens == HD_GINIBRE) ? kD + kN : kD;   // Haar's K1 forms no basis dots
+  if (nz > 0) e = cudaMemcpyAsync(r, ws.z, (size_t)nz * 8, cudaMemcpyDeviceToDevice, st->stream);
+  if (e == cudaSuccess && kD > 0)
+    e = cudaMemcpyAsync(r + L, ws.w, (size_t)kD * 8, cudaMemcpyDeviceToDevice, st->stream);
+  if (e == cudaSuccess && kD > 0)
+    e = cudaMemcpyAsync(r + 2 * L, ws.phead, (size_t)kD * 8, cudaMemcpyDeviceToDevice, st->stream);
+  if (e == cudaSuccess)   // scal[kPpiv], scal[kAlpha]
+    e = cudaMemcpyAsync(r + 3 * L, ws.scal, 2 * 8, cudaMemcpyDeviceToDevice, st->stream);
+  if (e != cudaSuccess) return cuda_fail(st, e);
   return HD_OK;
 }
 
@@ -510,23 +564,25 @@ HD_API int hd_adjoint_enable(hd_state* st, int flags) {
     const TrialDesc& td = st->hdesc[0];
     const int Tm = st->Tm;
     for (int s = 0; s < 2; s++) {
-      A->Vbar[s] = (double*)dalloc(st, (size_t)td.st[s].ld * Tm * sizeof(double));
+      A->Vbar[s] = dalloc(st, (size_t)td.st[s].ld * Tm * st->esz);
       A->Sbar[s] = (double*)dalloc(st, (size_t)st->Sld * st->Sld * sizeof(double));
       if (!A->Vbar[s] || !A->Sbar[s]) return HD_ERR_OOM;
       if (st->ens == HD_GINIBRE) {
-        A->Bbar[s] = (double*)dalloc(st, (size_t)td.ldb[s] * Tm * sizeof(double));
+        A->Bbar[s] = dalloc(st, (size_t)td.ldb[s] * Tm * st->esz);
         if (!A->Bbar[s]) return HD_ERR_OOM;
       }
     }
     A->dmax = round_up(std::max(st->dims[0][0], st->dims[1][0]), 256);
     A->ldx = A->dmax;
-    A->vec = (double*)dalloc(st, (size_t)kAdjVecs * A->dmax * sizeof(double));
+    A->vec = dalloc(st, (size_t)kAdjVecs * A->dmax * st->esz);
     A->small_ld = Tm + 8;
     A->small = (double*)dalloc(st, (size_t)kAdjSmall * A->small_ld * sizeof(double));
     A->nblk = std::max(1, 2 * st->nsm);
     const int64_t gmax = (int64_t)st->nsm * 8;
     A->part = (double*)dalloc(st, (size_t)std::max<int64_t>((int64_t)A->nblk * (Tm + 1) * 2, gmax) * sizeof(double));
-    if (!A->vec || !A->small || !A->part) return HD_ERR_OOM;
+    A->rec_ld = 3 * (int64_t)st->Sld + 8;
+    A->rec = (double*)dalloc(st, (size_t)A->rec_ld * Tm * sizeof(double));
+    if (!A->vec || !A->small || !A->part || !A->rec) return HD_ERR_OOM;
   }
   AdjState& A = *st->adj;
   A.record_x = (flags & HD_ADJ_RECORD_X) ? 1 : 0;

@@ -158,6 +158,10 @@ int do_step(hd_state* st, const void* x, int transpose, void* y, const FuseSpec*
   int launched[3] = {0, 0, 0};
   cudaError_t e = launch_step<T>(b, st->stream, ev, launched);
   if (e != cudaSuccess) return cuda_fail(st, e);
+  if (st->adj && st->adj->on) {
+    const int rc = adj_record_after(st, kD, kN);
+    if (rc) return rc;
+  }
   st->launches += launched[0] + launched[1] + launched[2];
   if (slot0 >= 0) {
     // algorithmic bytes: each sweep reads its stack once plus the vectors it reads/writes
@@ -214,7 +218,10 @@ int run_steps(hd_state* st, const hd_run_spec* sp) {
   int cur = 0;
   // elementwise dynamics of a Q / Q^T alternating schedule: the output sweep of step t applies
   // f_t and forms step t+1's dot sweep (HD_DISABLE_FUSE=1 turns this off)
-  const bool fusable = (sp->dynamics == HD_DYN_TANH || sp->dynamics == HD_DYN_SIGN_MEM) && st->fuse;
+  // (a state recording for reverse mode keeps the unfused steps: their workspace holds each
+  // step's own dots when the step is recorded)
+  const bool fusable = (sp->dynamics == HD_DYN_TANH || sp->dynamics == HD_DYN_SIGN_MEM) && st->fuse &&
+                       !(st->adj && st->adj->on);
   int prev_fused = 0;
   for (int t = 0; t < sp->T; t++) {
     const int tr = sp->transpose[t] ? 1 : 0;

@@ -16,17 +16,21 @@ struct AdjState {
   std::vector<int8_t> flag;      // per forward step: transpose flag
   std::vector<int> kD, kN;       // per forward step: reflectors in the data / other stack before it
   int rev = 0;                   // forward steps not yet reversed
-  double* Vbar[2] = {nullptr, nullptr};   // d loss / d V per stack (dim x T_max, ld of the stack)
-  double* Bbar[2] = {nullptr, nullptr};   // d loss / d basis store per space (Ginibre)
+  void* Vbar[2] = {nullptr, nullptr};     // d loss / d V per stack (state dtype, dim x T_max, ld of the stack)
+  void* Bbar[2] = {nullptr, nullptr};     // d loss / d basis store per space (Ginibre; state dtype)
   double* Sbar[2] = {nullptr, nullptr};   // d loss / d S per stack (T_max x T_max)
   void* X = nullptr;             // recorded step inputs x_t (state dtype), column t-1
   int64_t ldx = 0;
   int64_t dmax = 0;              // longest vector (rounded)
-  double* vec = nullptr;         // FP64 work vectors, kAdjVecs x dmax
+  void* vec = nullptr;           // work vectors (state dtype), kAdjVecs x dmax
   double* small = nullptr;       // FP64 small arena, kAdjSmall x (T_max + 8)
   int64_t small_ld = 0;
   double* part = nullptr;        // column-pass partial sums
   int nblk = 1;
+  // per forward step: z (k_D + k_N: data-stack dots, then Gin basis dots), w (k_D), p_head
+  // (k_D), then p's pivot entry and alpha, copied from the workspace after the step
+  double* rec = nullptr;
+  int64_t rec_ld = 0;
 };
 
 }  // namespace hd
@@ -117,5 +121,6 @@ DrawKey key_for(const hd_state* st, int step);
 void record_error_text(const char* msg);
 // reverse mode hooks of the forward path (hd_adjoint.cu)
 int adj_record_step(hd_state* st, const void* x, int transpose, int kD, int kN);
+int adj_record_after(hd_state* st, int kD, int kN);
 int adj_on_reset(hd_state* st);
 }  // namespace hd

@@ -277,7 +277,7 @@ def measure_amp_batch(args, rank, world, dist):
 
 def measure_adjoint(args, rank, world, dist):
     """Reverse mode: gradient of <c, x_{T+1}> with respect to x_1 and the per-step parameters
-    theta_t of x_{t+1} = tanh(theta_t y_t) + 0.3 x_{t-1} on Haar(n), n = 10^6, T = 32 products
+    theta_t of x_{t+1} = tanh(theta_t y_t) + 0.3 x_{t-1} on Haar(n), n = 10^6, T = 100 products
     Q / Q^T alternating, FP32 storage (paper_2101_07464_gb300.autograd.trajectory: forward with
     the library's steps recorded, backward through hd_adjoint_step).  Units n T^2 per
     forward + backward."""
@@ -286,7 +286,7 @@ def measure_adjoint(args, rank, world, dist):
     import synth
     import paper_2101_07464_gb300 as hd
     from paper_2101_07464_gb300.autograd import trajectory
-    n, T = 10 ** 6, 32
+    n, T = 10 ** 6, 100
     sched = [t % 2 == 0 for t in range(1, T + 1)]
     st = hd.HD("haar", n, n, T, args.seed, "f32", trial=rank)
     x1 = torch.tensor(synth.x1(n, args.seed, trial=rank), dtype=torch.float32, device="cuda")
@@ -325,7 +325,7 @@ def measure_adjoint(args, rank, world, dist):
     return {"metric": "n*T^2/s (forward + backward)", "value": float(n) * T * T * world / fb,
             "ms_forward_backward": fb * 1e3, "ms_forward": fw * 1e3, "n": n, "T": T, "dtype": "f32",
             "timing": "wall clock around synchronised whole calls (host-driven steps, torch f_t)",
-            "config": "Haar n=1e6, T=32, Q/Q^T alternating, x_{t+1} = tanh(theta_t y_t) + 0.3 x_{t-1}, "
+            "config": "Haar n=1e6, T=100, Q/Q^T alternating, x_{t+1} = tanh(theta_t y_t) + 0.3 x_{t-1}, "
                       "d<c, x_{T+1}>/d(x_1, theta)"}
 
 

@@ -40,6 +40,7 @@ namespace hd {
 namespace {
 
 constexpr int kAT = 256;   // threads of every adjoint kernel
+constexpr int kSmallT = 1024;   // threads of the small FP64 kernels (FP64 latency wants many warps)
 
 enum AdjVec { kVp, kVub, kVqb, kVg, kAdjVecs };
 enum AdjSmall {
@@ -156,34 +157,72 @@ __global__ void __launch_bounds__(kAT) k_rowpass(T* out, const T* in, double s_i
   }
 }
 
-// Ab[r, j] += sb a[r] b[j] + sd c[r] d[j] for r < dim, j < K (column-major, leading dim ld).
+// Ab[r, j] += a[r] b[j] + c[r] d[j] + e[r] f[j] for r < dim, j < K (column-major, leading dim
+// ld; b, d, f are FP64 coefficient vectors with the scales sb, sd, sf; c, e may be null).
 template <typename T>
 __global__ void __launch_bounds__(kAT) k_rank(T* Ab, int64_t ld, int K, int64_t dim, const T* __restrict__ a,
                                               const double* __restrict__ b, double sb, const T* __restrict__ c,
-                                              const double* __restrict__ d, double sd) {
-  __shared__ T bs[8], ds[8];
+                                              const double* __restrict__ d, double sd, const T* __restrict__ e,
+                                              const double* __restrict__ f, double sf, int Kf) {
+  __shared__ T bs[8], ds[8], fs[8];
   const int j0 = blockIdx.y * 8;
   if (threadIdx.x < 8) {
     const int j = j0 + threadIdx.x;
     bs[threadIdx.x] = (j < K) ? (T)(sb * b[j]) : T(0);
     ds[threadIdx.x] = (j < K && c) ? (T)(sd * d[j]) : T(0);
+    fs[threadIdx.x] = (j < Kf && e) ? (T)(sf * f[j]) : T(0);
   }
   __syncthreads();
   const int jn = min(K, j0 + 8) - j0;
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < dim; r += (int64_t)gridDim.x * blockDim.x) {
     const T ar = a[r];
     const T cr = c ? c[r] : T(0);
+    const T er = e ? e[r] : T(0);
     for (int q = 0; q < jn; q++) {
       T v = ar * bs[q];
       if (c) v = fma(cr, ds[q], v);
+      if (e) v = fma(er, fs[q], v);
       Ab[r + (int64_t)(j0 + q) * ld] += v;
     }
   }
 }
 
+// Adjoint of the S-column recurrence of column k of a stack: S[:k, k] = c = -tau S_k a with
+// a = V_k^T u (recorded) and S[k, k] = tau = 2 / u^T u.  With cbar = Sbar[:k, k] and
+// taubar = Sbar[k, k] + cbar . c / tau:  abar = -tau S_k^T cbar (a = V^T u passes it on as
+// Vbar_k += u abar^T and ubar += V_k abar), Sbar_k += -tau cbar a^T (upper triangle), and
+// tau = 2 / u^T u gives ubar += -tau^2 taubar u.  Writes coef[0..k) = abar, coef[k] =
+// -tau^2 taubar (the coefficients of ubar += V[:, 0..k] coef).  An identity column (tau = 0)
+// passes nothing.
+__global__ void __launch_bounds__(kSmallT) k_rec_col(const double* __restrict__ S, double* Sb, int Tm, int k,
+                                                     const double* __restrict__ a, double* coef) {
+  __shared__ double cb[kTmaxLimit + 1];
+  __shared__ double tb;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const double tau = S[k + (int64_t)k * Tm];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) cb[i] = (tau != 0.0) ? Sb[i + (int64_t)k * Tm] : 0.0;
+  if (wid == 0) {
+    double s = 0.0;
+    for (int i = lane; i < k; i += 32) s = fma(Sb[i + (int64_t)k * Tm], S[i + (int64_t)k * Tm], s);
+    s = warp_sum(s);
+    if (lane == 0) tb = (tau != 0.0) ? Sb[k + (int64_t)k * Tm] + s / tau : 0.0;
+  }
+  __syncthreads();
+  for (int j = wid; j < k; j += nw) {   // abar_j = -tau sum_{i <= j} S[i, j] cbar_i
+    double s = 0.0;
+    for (int i = lane; i <= j; i += 32) s = fma(S[i + (int64_t)j * Tm], cb[i], s);
+    s = warp_sum(s);
+    if (lane == 0) coef[j] = -tau * s;
+  }
+  if (threadIdx.x == 0) coef[k] = -tau * tau * tb;
+  for (int idx = threadIdx.x; idx < k * k; idx += blockDim.x) {
+    const int i = idx % k, j = idx / k;
+    if (i <= j) Sb[i + (int64_t)j * Tm] += -tau * cb[i] * a[j];
+  }
+}
+
 // out = scale S v (trans = 0) or scale S^T v (trans = 1), leading K x K block of the upper
 // triangular S (column-major, leading dim Tm): one warp per output, lanes over the sum.
-constexpr int kSmallT = 1024;   // threads of the small FP64 kernels (FP64 latency wants many warps)
 __global__ void __launch_bounds__(kSmallT) k_tri(const double* __restrict__ S, int Tm, int K,
                                                  const double* __restrict__ v, double scale, int trans,
                                                  double* out) {
@@ -206,40 +245,6 @@ __global__ void __launch_bounds__(kAT) k_outer_upper(double* Sb, int Tm, int K, 
   for (int idx = threadIdx.x; idx < K * K; idx += blockDim.x) {
     const int i = idx % K, j = idx / K;
     if (i <= j) Sb[i + (int64_t)j * Tm] += a[i] * b[j];
-  }
-}
-
-// E = Gbar[:, j] + Gbar[j, :]^T with Gbar = upper(M) (half diagonal), M = -S^T Sbar S^T, over
-// the K columns of the stack: E[i] = M[i, j] for i <= j, M[j, i] for i > j.  One warp per
-// output, lanes over the sums.
-__global__ void __launch_bounds__(kSmallT) k_gbar(const double* __restrict__ S, const double* __restrict__ Sb,
-                                                  int Tm, int K, int j, double* E) {
-  __shared__ double r1[kTmaxLimit + 1], r2[kTmaxLimit + 1];
-  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  const bool ident = S[j + (int64_t)j * Tm] == 0.0;   // identity reflector: no free column
-  for (int a = threadIdx.x >> 5; a < K; a += nw) {
-    double s1 = 0.0, s2 = 0.0;
-    for (int b = j + lane; b < K; b += 32) s1 = fma(Sb[a + (int64_t)b * Tm], S[j + (int64_t)b * Tm], s1);
-    for (int q = lane; q <= j; q += 32) s2 = fma(S[q + (int64_t)j * Tm], Sb[q + (int64_t)a * Tm], s2);
-    s1 = warp_sum(s1);
-    s2 = warp_sum(s2);
-    if (lane == 0) {
-      r1[a] = s1;   // (Sbar S[j, :]^T)_a
-      r2[a] = s2;   // (Sbar^T S[:, j])_a
-    }
-  }
-  __syncthreads();
-  for (int i = threadIdx.x >> 5; i < K; i += nw) {
-    double s = 0.0;
-    if (!ident) {
-      if (i <= j) {
-        for (int a = lane; a <= i; a += 32) s = fma(S[a + (int64_t)i * Tm], r1[a], s);
-      } else {
-        for (int b = i + lane; b < K; b += 32) s = fma(S[i + (int64_t)b * Tm], r2[b], s);
-      }
-    }
-    s = warp_sum(s);
-    if (lane == 0) E[i] = -s;
   }
 }
 
@@ -366,10 +371,11 @@ void rowpass(const Ctx& c, T* out, const T* in, double s_in, const T* A, int64_t
 
 template <typename T>
 void rank(const Ctx& c, T* Ab, int64_t ld, int K, int64_t dim, const T* a, const double* b, double sb,
-          const T* cc = nullptr, const double* d = nullptr, double sd = 0.0) {
+          const T* cc = nullptr, const double* d = nullptr, double sd = 0.0, const T* e = nullptr,
+          const double* f = nullptr, double sf = 0.0, int Kf = 0) {
   if (K <= 0) return;
   dim3 g(rows_grid(c.st, dim), (unsigned)((K + 7) / 8));
-  k_rank<T><<<g, kAT, 0, c.s>>>(Ab, ld, K, dim, a, b, sb, cc, d, sd);
+  k_rank<T><<<g, kAT, 0, c.s>>>(Ab, ld, K, dim, a, b, sb, cc, d, sd, e, f, sf, Kf);
 }
 
 template <typename T>
@@ -383,7 +389,6 @@ int adj_step(hd_state* st, const void* ybar, const void* x_in, void* xbar) {
   const StackDev& Se = td.st[e];
   const int64_t nd = st->dims[d][0], ne = st->dims[e][0];
   const bool haar = st->ens == HD_HAAR;
-  const int Kfin_d = haar ? st->t : (d == 0 ? st->r : st->l);
   const T* Vd = (const T*)Sd.V;
   const T* Ve = (const T*)Se.V;
   T* Vbd = (T*)A.Vbar[d];
@@ -421,6 +426,8 @@ int adj_step(hd_state* st, const void* ybar, const void* x_in, void* xbar) {
   const double* w = rz + st->Sld;
   const double* phead = rz + 2 * (int64_t)st->Sld;
   const double* rs = rz + 3 * (int64_t)st->Sld;
+  const double* ra = rz + 3 * (int64_t)st->Sld + 8;    // V_D^T u (new data column)
+  const double* rag = rz + 4 * (int64_t)st->Sld + 8;   // V_N^T u_g (Haar: new random column)
   const T* ucol = Vd + (int64_t)kD * Sd.ld;
   const unsigned gp = rows_grid(st, nd);
 
@@ -431,7 +438,9 @@ int adj_step(hd_state* st, const void* ybar, const void* x_in, void* xbar) {
     k_head_alpha<<<1, kAT, 0, c.s>>>(phead, kD, rs, cv);
     k_out_small<T><<<1, kSmallT, 0, c.s>>>(Ve, Se.ld, Ke, kD + 1, Se.S, Tm, Se.dpre, cv, bb, ybd, A.Sbar[e], Vbe,
                                       bo, cb);
-    rank<T>(c, Vbe, Se.ld, Ke, ne, ybd, bo, -1.0);
+    // the random column of this step (L_t = H_t(g_t), column kD of V_N): its S recurrence
+    k_rec_col<<<1, kSmallT, 0, c.s>>>(Se.S, A.Sbar[e], Tm, kD, rag, au);
+    rank<T>(c, Vbe, Se.ld, Ke, ne, ybd, bo, -1.0, Ve + (int64_t)kD * Se.ld, au, 1.0, nullptr, nullptr, 0.0, 0);
   } else {
     if (kN > 0) {
       colpass<T>(c, Ve, Se.ld, kN, ne, ybd, -1.0, bb);
@@ -459,9 +468,10 @@ int adj_step(hd_state* st, const void* ybar, const void* x_in, void* xbar) {
     }
   }
 
-  // the data-side reflector of this step (column kD of V_D)
-  k_gbar<<<1, kSmallT, 0, c.s>>>(Sd.S, A.Sbar[d], Tm, Kfin_d, kD, E);
-  rowpass<T>(c, ub, Vbd + (int64_t)kD * Sd.ld, 1.0, Vd, Sd.ld, Kfin_d, E, 1.0, nd, nullptr, 0, 0);
+  // the data-side reflector of this step (column kD of V_D): ubar = Vbar[:, kD] + the S
+  // recurrence's V[:, 0..kD] coef (E = [abar; -tau^2 taubar])
+  k_rec_col<<<1, kSmallT, 0, c.s>>>(Sd.S, A.Sbar[d], Tm, kD, ra, E);
+  rowpass<T>(c, ub, Vbd + (int64_t)kD * Sd.ld, 1.0, Vd, Sd.ld, kD + 1, E, 1.0, nd, nullptr, 0, 0);
   k_pbar<T><<<gp, kAT, 0, c.s>>>(qb, ucol, ub, cb, rs, kD, Sd.dpre, nd);
 
   // the data product p = Delta (I - V S^T V^T) x
@@ -476,7 +486,7 @@ int adj_step(hd_state* st, const void* ybar, const void* x_in, void* xbar) {
     rowpass<T>(c, xb, nullptr, 0.0, Bd, td.ldb[d], kN, hb, 1.0, nd, nullptr, 0, 1);
     rank<T>(c, (T*)A.Bbar[d], td.ldb[d], kN, nd, xd, hb, 1.0);
   }
-  rank<T>(c, Vbd, Sd.ld, kD, nd, qb, w, -1.0, xd, zb, 1.0);
+  rank<T>(c, Vbd, Sd.ld, kD, nd, qb, w, -1.0, xd, zb, 1.0, ucol, E, 1.0, kD);   // + u abar^T
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return cuda_fail(st, err);
   A.rev -= 1;
@@ -531,6 +541,10 @@ int adj_record_after(hd_state* st, int kD, int kN) {
     e = cudaMemcpyAsync(r + 2 * L, ws.phead, (size_t)kD * 8, cudaMemcpyDeviceToDevice, st->stream);
   if (e == cudaSuccess)   // scal[kPpiv], scal[kAlpha]
     e = cudaMemcpyAsync(r + 3 * L, ws.scal, 2 * 8, cudaMemcpyDeviceToDevice, st->stream);
+  if (e == cudaSuccess && kD > 0)   // V_D^T u of the new data-side column
+    e = cudaMemcpyAsync(r + 3 * L + 8, ws.scrb + ws.scr_stride * 1, (size_t)kD * 8, cudaMemcpyDeviceToDevice, st->stream);
+  if (e == cudaSuccess && st->ens == HD_HAAR && kN > 0)   // V_N^T u_g of the new random column
+    e = cudaMemcpyAsync(r + 4 * L + 8, ws.scrb + ws.scr_stride * 2, (size_t)kN * 8, cudaMemcpyDeviceToDevice, st->stream);
   if (e != cudaSuccess) return cuda_fail(st, e);
   return HD_OK;
 }
@@ -580,7 +594,7 @@ HD_API int hd_adjoint_enable(hd_state* st, int flags) {
     A->nblk = std::max(1, 2 * st->nsm);
     const int64_t gmax = (int64_t)st->nsm * 8;
     A->part = (double*)dalloc(st, (size_t)std::max<int64_t>((int64_t)A->nblk * (Tm + 1) * 2, gmax) * sizeof(double));
-    A->rec_ld = 3 * (int64_t)st->Sld + 8;
+    A->rec_ld = 5 * (int64_t)st->Sld + 8;
     A->rec = (double*)dalloc(st, (size_t)A->rec_ld * Tm * sizeof(double));
     if (!A->vec || !A->small || !A->part || !A->rec) return HD_ERR_OOM;
   }

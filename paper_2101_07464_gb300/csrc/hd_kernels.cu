@@ -429,8 +429,11 @@ __device__ void fin_update(const StepPlan<T>& p, const double* r, double* scr, i
   const double alpha = sh[0], tau = sh[1], us = sh[2], dsign = sh[3], ppiv = sh[5];
   // V_D^T u with u = p[k:] + (u_k - p_k) e_k, from the exact dots of the sweep; then the new
   // column of S: S[:k, k] = -tau S V_D^T u
-  for (int j = tid; j < k; j += nt)
+  double* ua_out = p.ws.scr(1);   // V_D^T u, kept for the reverse mode
+  for (int j = tid; j < k; j += nt) {
     f_a[j] = r[k + 3 + j] + (us - ppiv) * (double)VD[k + (int64_t)j * ldD];
+    ua_out[j] = f_a[j];
+  }
   __syncthreads();
   {
     const bool st = k > 0 && up_off(k) * 8 <= capb && stage_upper(sg, p.D.S, Tm, k, scr);
@@ -480,10 +483,12 @@ __device__ void fin_update(const StepPlan<T>& p, const double* r, double* scr, i
                [k](int j, int& lo, int& hi) { lo = j; hi = k - 1; }, f_a);
     }
     __syncthreads();
+    double* ug_out = p.ws.scr(2);   // V_N^T u_g, kept for the reverse mode
     for (int j = tid; j < k; j += nt) {
       const double vk = (double)VN[k + (int64_t)j * ldN];
       const double gd = p.N.gdot[j];
       f_c[j] = flag ? 0.0 : gd + (usg - gpiv) * vk;
+      ug_out[j] = f_c[j];
       f_a[j] += deltaN * (flag ? alpha * vk : coef * gd);
     }
     __syncthreads();

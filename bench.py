@@ -30,7 +30,7 @@ METRIC = "HD throughput n*T^2/s (Haar n=1e6, T=100, Q/Q^T alternating)"
 UNIT = "n*T^2/s"
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
@@ -45,16 +45,36 @@ def parse():
     ap.add_argument("--no-amp", action="store_true", help="skip the batched AMP measurement")
     ap.add_argument("--amp-trials", type=int, default=4096)
     ap.add_argument("--no-adjoint", action="store_true", help="skip the reverse-mode measurement")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def schedule(T):
     return [1 if t % 2 == 0 else 0 for t in range(1, T + 1)]
 
 
+def parse_args_for_test(argv):
+    return parse(argv)
+
+
 def dist_info():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), \
         int(os.environ.get("LOCAL_RANK", 0))
+
+
+def max_over_ranks(secs, dist, device="cuda"):
+    """The slowest rank's time (every rank gets it); `dist` is torch.distributed or None."""
+    if dist is None:
+        return secs
+    import torch
+    t = torch.tensor([float(secs)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, world, secs):
+    """Whole-job throughput: every rank processed units_per_rank in at most secs (weak scaling:
+    one independent trial per rank, Philox trial word = rank)."""
+    return float(units_per_rank) * world / secs
 
 
 # ----------------------------------------------------------------------------------------
@@ -92,14 +112,14 @@ def run_reference(args):
     if world > 1 and rank != 0:
         return
     n, T = args.n, args.T
-    k_sample = 10
+    k_sample = min(10, T)
     times = []
     for i in range(args.warmup + args.steps):
         done, secs, thr = oracle_sample(n, T, args.seed, budget_s=1e9, max_products=k_sample)
         if i >= args.warmup:
             times.append(secs)
     mean = statistics.mean(times)
-    value = cpu_units(n, k_sample) / mean
+    value = cpu_units(n, done) / mean
     sample = "first %d of %d products at n=%d (Haar, Q/Q^T alternating, sign dynamics), FP64" % (
         k_sample, T, n)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
@@ -200,11 +220,7 @@ def time_trajectories(st, spec, x1, xout, steps, warmup, dist):
     e1.record(stream)
     torch.cuda.synchronize()
     launches = hd.hd_get_launches(st.h) - l0
-    secs = e0.elapsed_time(e1) / 1e3
-    if dist is not None:
-        t = torch.tensor([secs], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        secs = float(t.item())
+    secs = max_over_ranks(e0.elapsed_time(e1) / 1e3, dist)
     return secs, launches
 
 
@@ -259,16 +275,12 @@ def measure_amp_batch(args, rank, world, dist):
         hd.hd_run(b.h, spec, bt, out)
     e1.record(stream)
     torch.cuda.synchronize()
-    secs = e0.elapsed_time(e1) / 1e3 / steps
-    if dist is not None:
-        tt = torch.tensor([secs], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        secs = float(tt.item())
+    secs = max_over_ranks(e0.elapsed_time(e1) / 1e3 / steps, dist)
     mse = float(((out.double() - bt.double()) ** 2).sum().item() / float(ns.sum()))
     sum_n, sum_mn = float(ns.sum()), float((ns + ms).sum())
     credited = sum_mn * 4.0 * T * (T + 1) / 2.0
     b.close()
-    return {"metric": "trials*n*T^2/s", "value": sum_n * T * T * world / secs,
+    return {"metric": "trials*n*T^2/s", "value": job_throughput(sum_n * T * T, world, secs),
             "ms_per_trajectory": secs * 1e3, "trials": count * world, "sum_n": sum_n * world, "T": T,
             "dtype": "f32 (FP64 coefficients)", "graph": "one CUDA graph per trajectory",
             "credited_GBps": credited / secs / 1e9, "mse": mse,
@@ -321,8 +333,9 @@ def measure_adjoint(args, rank, world, dist):
             one(False)
     torch.cuda.synchronize()
     fw = (time.perf_counter() - t0) / steps
+    fb, fw = max_over_ranks(fb, dist), max_over_ranks(fw, dist)
     st.close()
-    return {"metric": "n*T^2/s (forward + backward)", "value": float(n) * T * T * world / fb,
+    return {"metric": "n*T^2/s (forward + backward)", "value": job_throughput(float(n) * T * T, world, fb),
             "ms_forward_backward": fb * 1e3, "ms_forward": fw * 1e3, "n": n, "T": T, "dtype": "f32",
             "timing": "wall clock around synchronised whole calls (host-driven steps, torch f_t)",
             "config": "Haar n=1e6, T=100, Q/Q^T alternating, x_{t+1} = tanh(theta_t y_t) + 0.3 x_{t-1}, "
@@ -363,7 +376,7 @@ def run_ours(args):
     clk = clocks.stop()
     per_step = secs / args.steps
     units = float(n) * T * T * world
-    value = units / per_step
+    value = job_throughput(float(n) * T * T, world, per_step)
 
     # end to end through the public API: pinned host x_1 in, x_{T+1} back, every step
     tdt = torch.float32 if args.dtype == "f32" else torch.float64
@@ -379,11 +392,7 @@ def run_ours(args):
         hd.hd_run(st.h, spec, x1h, xouth)
         torch.cuda.current_stream().synchronize()   # the result is on the host
         float(xouth[0])
-    e2e_secs = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_secs], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_secs = float(t.item())
+    e2e_secs = max_over_ranks(time.perf_counter() - t0, dist)
     e2e = {"value": units / (e2e_secs / args.steps), "unit": UNIT,
            "h2d_bytes_per_step": n * x1h.element_size(), "d2h_bytes_per_step": n * xouth.element_size()}
     st.close()

@@ -141,9 +141,9 @@ int do_step(hd_state* st, const void* x, int transpose, void* y, const FuseSpec*
       b.base.xprev = (const T*)fs->xprev;
       b.base.y = nullptr;
       if (st->ens == HD_HAAR)
-        b.base.c3 = make_sweep<T>(st, 4, kN, 3, kN, 2);
+        b.base.c3 = make_sweep<T>(st, 4, kN, 2, kN, 1);
       else
-        b.base.c3 = make_sweep<T>(st, 5, kN + kD, 2, kN + kD, 2);
+        b.base.c3 = make_sweep<T>(st, 5, kN + kD, 2, kN + kD, 1);
     }
   }
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};

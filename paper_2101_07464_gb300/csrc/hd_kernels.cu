@@ -1017,8 +1017,10 @@ __global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_out_haar(BatchSte
   const int k = p.kN;
   const SweepCfg& cfg = p.c3;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  constexpr int NR = FUSE ? 2 : 1;
-  WtSmem<T> sm(dsm_raw, blockDim.x >> 5, cfg.nbuf, k, FUSE ? 3 : 2, k, NR);
+  // FUSE (the next step is the other product): the next draw's dots with this stack and its
+  // copy into this stack's buffer are not needed (the next step's kernels redo or overwrite
+  // them); the column pass forms the dots of x_{t+1} instead
+  WtSmem<T> sm(dsm_raw, blockDim.x >> 5, cfg.nbuf, k, 2, k, 1);
   const ColSrc<T> src{(const T*)p.N.V, p.N.ld, k, nullptr, 0};
   const int64_t dim = p.N.dim;
   T* col = (T*)p.N.V + (int64_t)k * p.N.ld;
@@ -1026,13 +1028,10 @@ __global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_out_haar(BatchSte
   const T* gnext = (const T*)p.D.gbuf;
   T coef = T(0), alpha = T(0), usg = T(0), dconst = T(0);
   bool flag = false;
-  double acc[NR][kColsPerLane];
+  double acc[1][kColsPerLane];
 #pragma unroll
-  for (int m = 0; m < kColsPerLane; m++) {
-    acc[0][m] = 0.0;
-    if (FUSE) acc[NR - 1][m] = 0.0;
-  }
-  T ex[2] = {T(0), T(0)};   // new column . g_{t+1}; (FUSE) new column . x_{t+1}
+  for (int m = 0; m < kColsPerLane; m++) acc[0][m] = 0.0;
+  T ex[1] = {T(0)};   // new column . g_{t+1}, or (FUSE) new column . x_{t+1}
   T* xv = sm.scr(warp, 0);
   const bool need_prev = FUSE && p.dyn != 1;
   const WarpWalk ww(dim, cc);
@@ -1043,7 +1042,7 @@ __global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_out_haar(BatchSte
         const int64_t r0 = ww.sub(it) * 32;
         wt_load_cols(st, src, k, r0);
         wt_load_vec(sm.srow(st, 0), (const T*)gcur, r0, ld, true);
-        if (need_prev) wt_load_vec(sm.srow(st, 2), p.xprev, r0, dim, ((uintptr_t)p.xprev & 15u) == 0);
+        if (need_prev) wt_load_vec(sm.srow(st, 1), p.xprev, r0, dim, ((uintptr_t)p.xprev & 15u) == 0);
       },
       [&]() {   // outputs of the preceding kernel's finalisation
         for (int j = threadIdx.x; j < sm.cpad; j += blockDim.x) sm.coef[j] = (j < k) ? (T)p.ws.wout[j] : T(0);
@@ -1053,12 +1052,13 @@ __global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_out_haar(BatchSte
         flag = p.ws.scal[kGFlag] != 0.0;
         dconst = (T)p.N.dpre[k];
       },
-      [&](int it, int b) { wt_load_vec(sm.srow(sm.stage(warp, b), 1), gnext, ww.sub(it) * 32, ld, true); },
+      [&](int it, int b) {
+        if (!FUSE) wt_load_vec(sm.srow(sm.stage(warp, b), 1), gnext, ww.sub(it) * 32, ld, true);
+      },
       [&](int it, int b) {
         T* st = sm.stage(warp, b);
         const int64_t r = ww.sub(it) * 32 + lane;
         const T g = sm.srow(st, 0)[lane];
-        const T gn = sm.srow(st, 1)[lane];
         T out[1];
         wt_rows<T, 1>(st, k, sm.coef, nullptr, out);
         T ci;
@@ -1072,43 +1072,41 @@ __global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_out_haar(BatchSte
           if (!FUSE) p.y[r] = yi;
           if (r >= k) col[r] = nc;
         }
-        ex[0] = fma(nc, gn, ex[0]);
-        gcur[r] = gn;
         if (FUSE) {
           T xn = T(0);
           if (r < dim) {
-            xn = fused_dyn<T>(p.dyn, p.dyn_a, yi, need_prev ? sm.srow(st, 2)[lane] : T(0));
+            xn = fused_dyn<T>(p.dyn, p.dyn_a, yi, need_prev ? sm.srow(st, 1)[lane] : T(0));
             p.xnext[r] = xn;
           }
           xv[lane] = xn;
-          ex[1] = fma(nc, xn, ex[1]);
+          ex[0] = fma(nc, xn, ex[0]);
           __syncwarp();
+          wt_cols<T, 1>(st, k, xv, nullptr, acc);
+          __syncwarp();
+        } else {
+          const T gn = sm.srow(st, 1)[lane];
+          ex[0] = fma(nc, gn, ex[0]);
+          gcur[r] = gn;
+          wt_cols<T, 1>(st, k, sm.srow(st, 1), nullptr, acc);
         }
-        wt_cols<T, NR>(st, k, sm.srow(st, 1), FUSE ? xv : nullptr, acc);
-        if (FUSE) __syncwarp();
       });
-  // partial sums: [0, k) V_N . g_{t+1}, [k] new . g_{t+1}, (FUSE) [k+1] new . x_{t+1},
-  // [k+2, 2k+2) V_N . x_{t+1}
-  const int P = FUSE ? 2 * k + 2 : k + 1;
+  // partial sums: [0, k) V_N . r, [k] new column . r, r = g_{t+1} or (FUSE) x_{t+1}
+  const int P = k + 1;
   double* part = p.ws.part + (int64_t)cc.local * P;
-  {
-    int off[NR];
-    off[0] = 0;
-    if (FUSE) off[NR - 1] = k + 2;
-    wt_store_cols<NR>(sm.comb, k, acc, part, off);
-  }
-  block_sum_to<2>(ex, red, part + k, NR);
+  const int off[1] = {0};
+  wt_store_cols<1>(sm.comb, k, acc, part, off);
+  block_sum_to<1>(ex, red, part + k, 1);
   double* rr = p.ws.scr(3);
   if (!reduce_partials(p.ws, 2, P, cc.local, cc.ncta, rr)) return;
-  for (int j = threadIdx.x; j <= k; j += blockDim.x) p.N.gdot[j] = rr[j];
-  if (threadIdx.x == 0) p.N.gg[0] = p.D.gg[0];
-  if (FUSE) {
+  if (!FUSE) {
+    for (int j = threadIdx.x; j <= k; j += blockDim.x) p.N.gdot[j] = rr[j];
+    if (threadIdx.x == 0) p.N.gg[0] = p.D.gg[0];
+  } else {
     // the next step's K1: z = V_N^T x_{t+1} over the k + 1 columns, w = S_N^T z
     __shared__ double zs[kTmaxLimit + 1];
     for (int j = threadIdx.x; j <= k; j += blockDim.x) {
-      const double zj = (j < k) ? rr[k + 2 + j] : rr[k + 1];
-      zs[j] = zj;
-      p.ws.z[j] = zj;
+      zs[j] = rr[j];
+      p.ws.z[j] = rr[j];
     }
     __syncthreads();
     fin_dots(p.N.S, p.Tm, k + 1, zs, p.ws.w, (double*)dsm_raw, (int64_t)sm.bytes(), p.ws.err);
@@ -1130,24 +1128,21 @@ __global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_out_gin(BatchStep
   const int kN = p.kN, kD = p.kD, nc = kN + kD;
   const SweepCfg& cfg = p.c3;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  constexpr int NR = FUSE ? 2 : 1;
+  // FUSE (the next step is the other product): the next draw in this space and its dots are
+  // not needed; the column pass forms the dots of x_{t+1} with V_N and B_n instead
   const int ncc = FUSE ? nc : kN;   // column-owner columns
-  WtSmem<T> sm(dsm_raw, blockDim.x >> 5, cfg.nbuf, nc, FUSE ? 2 : 1, ncc, NR);
+  WtSmem<T> sm(dsm_raw, blockDim.x >> 5, cfg.nbuf, nc, FUSE ? 2 : 1, ncc, 1);
   const ColSrc<T> src{(const T*)p.N.V, p.N.ld, kN, (const T*)p.Bn, p.ldBn};
   const int64_t dim = p.N.dim;
   T* ucol = (T*)p.Bn + (int64_t)kD * p.ldBn;
   T* gcur = (T*)p.N.gbuf;
   const double* h = p.ws.z + kD;
   T alpha = T(0), dconst = T(0);
-  double acc[NR][kColsPerLane];
+  double acc[1][kColsPerLane];
 #pragma unroll
-  for (int m = 0; m < kColsPerLane; m++) {
-    acc[0][m] = 0.0;
-    if (FUSE) acc[NR - 1][m] = 0.0;
-  }
+  for (int m = 0; m < kColsPerLane; m++) acc[0][m] = 0.0;
   T ex[1] = {T(0)};   // (FUSE) u . x_{t+1}
-  T* gv = sm.scr(warp, 0);
-  T* xv = sm.scr(warp, 1);
+  T* rv = sm.scr(warp, 0);
   const bool need_prev = FUSE && p.dyn != 1;
   const WarpWalk ww(dim, cc);
   const int64_t ld = p.N.ld;
@@ -1180,7 +1175,6 @@ __global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_out_gin(BatchStep
         const int64_t r = ww.sub(it) * 32 + lane;
         const T g = sm.srow(st, 0)[lane];
         const T hi = (r < kN) ? (T)h[r] : T(0);
-        const T gn = wt_draw(p.key_next, r, (int64_t)kN, dim, p.sigma);
         T out[2];
         wt_rows<T, 2>(st, nc, sm.coef, sm.coef + sm.cpad, out);
         const T d = (r < kN) ? (T)p.N.dpre[r + 1] : dconst;
@@ -1190,46 +1184,43 @@ __global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_out_gin(BatchStep
           ucol[r] = u;
           if (!FUSE) p.y[r] = yi;
         }
-        gcur[r] = gn;
-        gv[lane] = gn;
         if (FUSE) {
           T xn = T(0);
           if (r < dim) {
             xn = fused_dyn<T>(p.dyn, p.dyn_a, yi, need_prev ? sm.srow(st, 1)[lane] : T(0));
             p.xnext[r] = xn;
           }
-          xv[lane] = xn;
+          rv[lane] = xn;
           ex[0] = fma(u, xn, ex[0]);
+        } else {
+          const T gn = wt_draw(p.key_next, r, (int64_t)kN, dim, p.sigma);
+          gcur[r] = gn;
+          rv[lane] = gn;
         }
         __syncwarp();
-        wt_cols<T, NR>(st, ncc, gv, FUSE ? xv : nullptr, acc);
-        if (FUSE) __syncwarp();
+        wt_cols<T, 1>(st, ncc, rv, nullptr, acc);
+        __syncwarp();
       });
   if (!FUSE && kN == 0) return;   // no dots to form
-  // partial sums: [0, ncc) columns . g_{t+1} (V_N's first kN are used); (FUSE) [nc] u . x_{t+1},
-  // [nc + 1, 2 nc + 1) columns . x_{t+1}
-  const int P = FUSE ? 2 * nc + 1 : kN;
+  // partial sums: [0, ncc) columns . r (r = g_{t+1}, or (FUSE) x_{t+1}), (FUSE) [nc] u . x_{t+1}
+  const int P = FUSE ? nc + 1 : kN;
   double* part = p.ws.part + (int64_t)cc.local * P;
-  {
-    int off[NR];
-    off[0] = 0;
-    if (FUSE) off[NR - 1] = nc + 1;
-    wt_store_cols<NR>(sm.comb, ncc, acc, part, off);
-  }
+  const int off[1] = {0};
+  wt_store_cols<1>(sm.comb, ncc, acc, part, off);
   if (FUSE) block_sum_to<1>(ex, red, part + nc, 1);
   double* rr = p.ws.scr(3);
   if (!reduce_partials(p.ws, 2, P, cc.local, cc.ncta, rr)) return;
-  for (int j = threadIdx.x; j < kN; j += blockDim.x) p.N.gdot[j] = rr[j];
-  if (FUSE) {
+  if (!FUSE) {
+    for (int j = threadIdx.x; j < kN; j += blockDim.x) p.N.gdot[j] = rr[j];
+  } else {
     // the next step's K1 (its data stack is V_N, k_D' = kN; its data-space basis is B_n with
     // kD + 1 columns): z = V_N^T x_{t+1}, h = B_n^T x_{t+1}, w = S_N^T z
     __shared__ double zs[kTmaxLimit + 1];
     for (int j = threadIdx.x; j < kN; j += blockDim.x) {
-      const double zj = rr[nc + 1 + j];
-      zs[j] = zj;
-      p.ws.z[j] = zj;
+      zs[j] = rr[j];
+      p.ws.z[j] = rr[j];
     }
-    for (int i = threadIdx.x; i <= kD; i += blockDim.x) p.ws.z[kN + i] = (i < kD) ? rr[nc + 1 + kN + i] : rr[nc];
+    for (int i = threadIdx.x; i <= kD; i += blockDim.x) p.ws.z[kN + i] = (i < kD) ? rr[kN + i] : rr[nc];
     __syncthreads();
     fin_dots(p.N.S, p.Tm, kN, zs, p.ws.w, (double*)dsm_raw, (int64_t)sm.bytes(), p.ws.err);
   }
@@ -1291,13 +1282,13 @@ cudaError_t launch_step(const BatchStep<T>& b, cudaStream_t s, cudaEvent_t* ev, 
   const int ncg = p.kN + p.kD;
   if (p.ens == 1 && p.fuse)
     e = launch_sweep<T>(k_out_haar<T, true>, p.c3, b.map[ospace].ctas,
-                        sweep_smem_bytes<T>(p.c3.W, p.c3.nbuf, p.kN, 3, p.kN, 2), s, pdl, b);
+                        sweep_smem_bytes<T>(p.c3.W, p.c3.nbuf, p.kN, 2, p.kN, 1), s, pdl, b);
   else if (p.ens == 1)
     e = launch_sweep<T>(k_out_haar<T, false>, p.c3, b.map[ospace].ctas,
                         sweep_smem_bytes<T>(p.c3.W, p.c3.nbuf, p.kN, 2, p.kN, 1), s, pdl, b);
   else if (p.fuse)
     e = launch_sweep<T>(k_out_gin<T, true>, p.c3, b.map[ospace].ctas,
-                        sweep_smem_bytes<T>(p.c3.W, p.c3.nbuf, ncg, 2, ncg, 2), s, pdl, b);
+                        sweep_smem_bytes<T>(p.c3.W, p.c3.nbuf, ncg, 2, ncg, 1), s, pdl, b);
   else
     e = launch_sweep<T>(k_out_gin<T, false>, p.c3, b.map[ospace].ctas,
                         sweep_smem_bytes<T>(p.c3.W, p.c3.nbuf, ncg, 1, p.kN, 1), s, pdl, b);

@@ -79,19 +79,30 @@ __device__ bool reduce_partials(const Ws& ws, int set, int P, int local, int nct
   const int grp = local / gsize;
   const int gfirst = grp * gsize;
   const int gcount = min(gsize, ncta - gfirst);
+  // (two interleaved FP64 sums per value: dependent FP64 adds are slow on this GPU)
   if (!elect_last(&cnt[grp], gcount)) return false;
   for (int j = threadIdx.x; j < P; j += blockDim.x) {
-    double s = 0.0;
-#pragma unroll 8
-    for (int c = 0; c < gcount; c++) s += ld_cg(&ws.part[(int64_t)(gfirst + c) * P + j]);
-    ws.gpart[(int64_t)grp * P + j] = s;
+    double s0 = 0.0, s1 = 0.0;
+    int c = 0;
+#pragma unroll 4
+    for (; c + 1 < gcount; c += 2) {
+      s0 += ld_cg(&ws.part[(int64_t)(gfirst + c) * P + j]);
+      s1 += ld_cg(&ws.part[(int64_t)(gfirst + c + 1) * P + j]);
+    }
+    if (c < gcount) s0 += ld_cg(&ws.part[(int64_t)(gfirst + c) * P + j]);
+    ws.gpart[(int64_t)grp * P + j] = s0 + s1;
   }
   if (!elect_last(&cnt[kMaxGroups], ngroups)) return false;
   for (int j = threadIdx.x; j < P; j += blockDim.x) {
-    double s = 0.0;
-#pragma unroll 8
-    for (int q = 0; q < ngroups; q++) s += ld_cg(&ws.gpart[(int64_t)q * P + j]);
-    out[j] = s;
+    double s0 = 0.0, s1 = 0.0;
+    int q = 0;
+#pragma unroll 4
+    for (; q + 1 < ngroups; q += 2) {
+      s0 += ld_cg(&ws.gpart[(int64_t)q * P + j]);
+      s1 += ld_cg(&ws.gpart[(int64_t)(q + 1) * P + j]);
+    }
+    if (q < ngroups) s0 += ld_cg(&ws.gpart[(int64_t)q * P + j]);
+    out[j] = s0 + s1;
   }
   __syncthreads();
   return true;
@@ -229,12 +240,15 @@ struct Stager {
   uint64_t* bar;
   unsigned parity;
   unsigned* err;
+  // begin(): issue the copies (every thread calls it); finish(): wait for them (bounded).
   template <typename Issue>
-  __device__ bool run(unsigned bytes, Issue issue) {
+  __device__ void begin(unsigned bytes, Issue issue) {
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     __syncthreads();
     if (threadIdx.x == 0) mbar_arrive_tx(bar, bytes);
     issue();
+  }
+  __device__ bool finish() {
     unsigned spins = 0;
     bool ok = true;
     while (!mbar_test(bar, parity)) {
@@ -247,6 +261,11 @@ struct Stager {
     parity ^= 1u;
     __syncthreads();
     return ok;
+  }
+  template <typename Issue>
+  __device__ bool run(unsigned bytes, Issue issue) {
+    begin(bytes, issue);
+    return finish();
   }
 };
 
@@ -403,9 +422,32 @@ __device__ void fin_update(const StepPlan<T>& p, const double* r, double* scr, i
   __shared__ uint64_t fbar;
   T* VD = (T*)p.D.V;
   const int64_t ldD = p.D.ld;
+  const T* VN = (const T*)p.N.V;
+  const int64_t ldN = p.N.ld;
   if (tid == 0) mbar_init(&fbar);
   Stager sg{&fbar, 0u, p.ws.err};
   const int64_t capb = (int64_t)cap * 8;   // free shared memory in bytes
+
+  // The three small matrices of this finalisation (S_D, the head block of V_N, S_N), staged in
+  // one round while the scalars are formed, when they fit together.
+  const int kNs = (p.ens == 1) ? k : p.kN;
+  const int Lv = stage_lv<T>(kNs);
+  const int64_t bSD = (k > 0) ? up_off(k) * 8 : 0;
+  const int64_t bVN = (int64_t)Lv * kNs * (int64_t)sizeof(T);
+  const int64_t bSN = (kNs > 0) ? up_off(kNs) * 8 : 0;
+  const bool all = bSD + bVN + bSN > 0 && bSD + bVN + bSN <= capb;
+  double* sSD = scr;
+  T* sVN = (T*)((char*)scr + bSD);
+  double* sSN = (double*)((char*)scr + bSD + bVN);
+  if (all)
+    sg.begin((unsigned)(bSD + bVN + bSN), [&]() {
+      for (int c = tid; c < k; c += nt)
+        bulk_g2s(sSD + up_off(c), p.D.S + (int64_t)c * Tm, (unsigned)(((c + 2) & ~1) * 8), sg.bar);
+      for (int j = tid; j < kNs; j += nt)
+        bulk_g2s(sVN + (int64_t)j * Lv, VN + (int64_t)j * ldN, (unsigned)(Lv * sizeof(T)), sg.bar);
+      for (int c = tid; c < kNs; c += nt)
+        bulk_g2s(sSN + up_off(c), p.N.S + (int64_t)c * Tm, (unsigned)(((c + 2) & ~1) * 8), sg.bar);
+    });
 
   for (int j = tid; j <= k; j += nt) p.D.gdot[j] = r[j];
   if (tid == 0) {
@@ -425,6 +467,21 @@ __device__ void fin_update(const StepPlan<T>& p, const double* r, double* scr, i
     sh[5] = ppiv;
     p.ws.scal[kAlpha] = alpha;
   }
+  if (p.ens == 1 && tid == (nt > 32 ? 32 : 0)) {
+    // Haar: L_t = H_t(g_t) from the stored draw (formed beside the data-side scalars)
+    const double gpiv = (double)((const T*)p.N.gbuf)[k];
+    const double gg = p.N.gg[0];
+    const double ag = sqrt(gg + gpiv * gpiv);
+    const double sg2 = (gpiv >= 0.0) ? 1.0 : -1.0;
+    if (ag == 0.0) {
+      sh[8] = 0.0; sh[9] = 0.0; sh[10] = 1.0; sh[11] = 0.0; sh[13] = 1.0;
+    } else {
+      const double usg = (double)(T)(gpiv + sg2 * ag);
+      const double uug = gg + usg * usg;
+      sh[8] = 2.0 / uug; sh[9] = usg; sh[10] = -sg2; sh[11] = ag; sh[13] = 0.0;
+    }
+    sh[14] = gpiv;
+  }
   __syncthreads();
   const double alpha = sh[0], tau = sh[1], us = sh[2], dsign = sh[3], ppiv = sh[5];
   // V_D^T u with u = p[k:] + (u_k - p_k) e_k, from the exact dots of the sweep; then the new
@@ -435,9 +492,10 @@ __device__ void fin_update(const StepPlan<T>& p, const double* r, double* scr, i
     ua_out[j] = f_a[j];
   }
   __syncthreads();
+  const bool staged = all && sg.finish();
   {
-    const bool st = k > 0 && up_off(k) * 8 <= capb && stage_upper(sg, p.D.S, Tm, k, scr);
-    upper_mv<1>(st ? scr : nullptr, p.D.S, Tm, k, f_a, nullptr, p.D.S + (int64_t)k * Tm,
+    const bool st = staged || (k > 0 && !all && up_off(k) * 8 <= capb && stage_upper(sg, p.D.S, Tm, k, scr));
+    upper_mv<1>(st ? sSD : nullptr, p.D.S, Tm, k, f_a, nullptr, p.D.S + (int64_t)k * Tm,
                 (alpha != 0.0) ? -tau : 0.0, nullptr, 0.0);
   }
   if (tid == 0) {
@@ -446,24 +504,11 @@ __device__ void fin_update(const StepPlan<T>& p, const double* r, double* scr, i
     VD[k + (int64_t)k * ldD] = (T)us;
   }
 
-  const T* VN = (const T*)p.N.V;
-  const int64_t ldN = p.N.ld;
   if (p.ens == 1) {
-    // Haar: L_t = H_t(g_t) from the stored draw, and the output coefficients
-    // c = L_t R_t p = [p_head; alpha g[k:]/||g[k:]||]  (H(v) e_1 = v/||v||).
+    // Haar: the output coefficients c = L_t R_t p = [p_head; alpha g[k:]/||g[k:]||]
+    // (H(v) e_1 = v/||v||)
     if (tid == 0) {
-      const double gpiv = (double)((const T*)p.N.gbuf)[k];
-      const double gg = p.N.gg[0];
-      const double ag = sqrt(gg + gpiv * gpiv);
-      const double sg = (gpiv >= 0.0) ? 1.0 : -1.0;
-      if (ag == 0.0) {
-        sh[8] = 0.0; sh[9] = 0.0; sh[10] = 1.0; sh[12] = 0.0; sh[13] = 1.0;
-      } else {
-        const double usg = (double)(T)(gpiv + sg * ag);
-        const double uug = gg + usg * usg;
-        sh[8] = 2.0 / uug; sh[9] = usg; sh[10] = -sg; sh[12] = alpha / ag; sh[13] = 0.0;
-      }
-      sh[14] = gpiv;
+      sh[12] = (sh[13] != 0.0) ? 0.0 : alpha / sh[11];
       p.ws.scal[kCoef] = sh[12];
       p.ws.scal[kUpivG] = sh[9];
       p.ws.scal[kGFlag] = sh[13];
@@ -476,11 +521,10 @@ __device__ void fin_update(const StepPlan<T>& p, const double* r, double* scr, i
     const double deltaN = p.N.dpre[k];
     // tz_j = V_N[j:k, j] . (Delta_N p_head)[j:k]
     {
-      const int Lv = stage_lv<T>(k);
-      const bool st = k > 0 && (int64_t)Lv * k * (int64_t)sizeof(T) <= capb &&
-                      stage_cols(sg, VN, ldN, k, k, (T*)scr);
-      col_dots(st ? (const T*)scr : VN, st ? (int64_t)Lv : ldN, k, f_b,
-               [k](int j, int& lo, int& hi) { lo = j; hi = k - 1; }, f_a);
+      const bool st = staged || (k > 0 && !all && (int64_t)Lv * k * (int64_t)sizeof(T) <= capb &&
+                                 stage_cols(sg, VN, ldN, k, k, (T*)scr));
+      const T* vsrc = staged ? sVN : (st ? (const T*)scr : VN);
+      col_dots(vsrc, st ? (int64_t)Lv : ldN, k, f_b, [k](int j, int& lo, int& hi) { lo = j; hi = k - 1; }, f_a);
     }
     __syncthreads();
     double* ug_out = p.ws.scr(2);   // V_N^T u_g, kept for the reverse mode
@@ -493,8 +537,9 @@ __device__ void fin_update(const StepPlan<T>& p, const double* r, double* scr, i
     }
     __syncthreads();
     {
-      const bool st = k > 0 && up_off(k) * 8 <= capb && stage_upper(sg, p.N.S, Tm, k, scr);
-      upper_mv<2>(st ? scr : nullptr, p.N.S, Tm, k, f_a, f_c, p.ws.wout, 1.0, p.N.S + (int64_t)k * Tm, -taug);
+      const bool st = staged || (k > 0 && !all && up_off(k) * 8 <= capb && stage_upper(sg, p.N.S, Tm, k, scr));
+      upper_mv<2>(st ? (staged ? sSN : scr) : nullptr, p.N.S, Tm, k, f_a, f_c, p.ws.wout, 1.0,
+                  p.N.S + (int64_t)k * Tm, -taug);
     }
     if (tid == 0) {
       p.N.S[k + (int64_t)k * Tm] = taug;
@@ -511,15 +556,16 @@ __device__ void fin_update(const StepPlan<T>& p, const double* r, double* scr, i
     }
     __syncthreads();
     {
-      const int Lv = stage_lv<T>(kN);
-      const bool st = kN > 0 && (int64_t)Lv * kN * (int64_t)sizeof(T) <= capb &&
-                      stage_cols(sg, VN, ldN, kN, kN, (T*)scr);
-      col_dots(st ? (const T*)scr : VN, st ? (int64_t)Lv : ldN, kN, f_b,
-               [kN](int j, int& lo, int& hi) { lo = j; hi = kN - 1; }, f_a);
+      const bool st = staged || (kN > 0 && !all && (int64_t)Lv * kN * (int64_t)sizeof(T) <= capb &&
+                                 stage_cols(sg, VN, ldN, kN, kN, (T*)scr));
+      const T* vsrc = staged ? sVN : (st ? (const T*)scr : VN);
+      col_dots(vsrc, st ? (int64_t)Lv : ldN, kN, f_b, [kN](int j, int& lo, int& hi) { lo = j; hi = kN - 1; },
+               f_a);
     }
     {
-      const bool st = kN > 0 && up_off(kN) * 8 <= capb && stage_upper(sg, p.N.S, Tm, kN, scr);
-      upper_mv<2>(st ? scr : nullptr, p.N.S, Tm, kN, f_a, f_c, p.ws.wout, 1.0, p.ws.wout2, deltaN);
+      const bool st = staged || (kN > 0 && !all && up_off(kN) * 8 <= capb && stage_upper(sg, p.N.S, Tm, kN, scr));
+      upper_mv<2>(st ? (staged ? sSN : scr) : nullptr, p.N.S, Tm, kN, f_a, f_c, p.ws.wout, 1.0, p.ws.wout2,
+                  deltaN);
     }
   }
 }

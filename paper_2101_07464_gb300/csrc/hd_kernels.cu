@@ -858,18 +858,31 @@ __device__ __forceinline__ void wt_store_cols(double* comb, int ncolC, const dou
   }
 }
 
-// Per-lane pair sharing of the Gaussian draw: even lanes draw normals (2j, 2j+1), odd lanes
-// receive the second one; rows outside [first, dim) get 0; scaled by sigma.
+// Draws for a warp's walk, two sub-tiles per Philox round: at even local iterations lane l
+// forms the normal pair (2j, 2j+1) of sub-tile it (l < 16) or of sub-tile it + 1 (l >= 16);
+// each iteration then hands every lane its row's normal by shuffle.  Rows outside
+// [first, dim) get 0; scaled by sigma.
 template <typename T>
-__device__ __forceinline__ T wt_draw(const DrawKey& key, int64_t row, int64_t first, int64_t dim, T sigma) {
-  const int lane = threadIdx.x & 31;
+struct PairDraws {
   T a = T(0), b = T(0);
-  const int64_t r0 = row & ~(int64_t)1;
-  if (!(lane & 1) && r0 + 1 >= first && r0 < dim) normal_pair(key, (uint64_t)(r0 >> 1), a, b);
-  const T other = __shfl_up_sync(0xffffffffu, b, 1);
-  const T g = (lane & 1) ? other : a;
-  return (row >= first && row < dim) ? sigma * g : T(0);
-}
+  // cur0: first row of this iteration's sub-tile; nxt0: first row of the next one (used at
+  // even iterations when has_next).
+  __device__ __forceinline__ T next(const DrawKey& key, int it, int64_t cur0, int64_t nxt0, bool has_next,
+                                    int64_t first, int64_t dim, T sigma) {
+    const int lane = threadIdx.x & 31;
+    if (!(it & 1)) {
+      const int64_t row = ((lane < 16) ? cur0 : nxt0) + 2 * (lane & 15);
+      a = b = T(0);
+      if ((lane < 16 || has_next) && row + 1 >= first && row < dim) normal_pair(key, (uint64_t)(row >> 1), a, b);
+    }
+    const int src = ((it & 1) ? 16 : 0) + (lane >> 1);
+    const T va = __shfl_sync(0xffffffffu, a, src);
+    const T vb = __shfl_sync(0xffffffffu, b, src);
+    const T g = (lane & 1) ? vb : va;
+    const int64_t r = cur0 + lane;
+    return (r >= first && r < dim) ? sigma * g : T(0);
+  }
+};
 
 // Walk of a warp over its sub-tiles: first sub-tile gw, stride GW.
 struct WarpWalk {
@@ -992,6 +1005,7 @@ __global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_update(BatchStep<
   T ex[3] = {T(0), T(0), T(0)};   // p . g_next, ||p[k+1:]||^2, ||g_next[k+2:]||^2
   T* pv = sm.scr(warp, 0);
   T* gv = sm.scr(warp, 1);
+  PairDraws<T> draws;
   const WarpWalk ww(dim, cc);
   const bool xal = ((uintptr_t)p.x & 15u) == 0;   // per-trial offsets may break alignment
   wt_pipeline(ww.count(), cfg.nbuf,
@@ -1008,7 +1022,9 @@ __global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_update(BatchStep<
       [&](int it, int b) {
         T* st = sm.stage(warp, b);
         const int64_t r = ww.sub(it) * 32 + lane;
-        const T g = wt_draw(p.key_next, r, (int64_t)k + 1, dim, p.sigma);
+        const bool has_next = it + 1 < ww.count();
+        const T g = draws.next(p.key_next, it, ww.sub(it) * 32, has_next ? ww.sub(it + 1) * 32 : 0, has_next,
+                               (int64_t)k + 1, dim, p.sigma);
         T out[1];
         wt_rows<T, 1>(st, k, sm.coef, nullptr, out);
         const T d = (r < k) ? (T)p.D.dpre[r + 1] : dconst;
@@ -1190,6 +1206,7 @@ __global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_out_gin(BatchStep
   T ex[1] = {T(0)};   // (FUSE) u . x_{t+1}
   T* rv = sm.scr(warp, 0);
   const bool need_prev = FUSE && p.dyn != 1;
+  PairDraws<T> draws;
   const WarpWalk ww(dim, cc);
   const int64_t ld = p.N.ld;
   wt_pipeline(ww.count(), cfg.nbuf,
@@ -1239,7 +1256,9 @@ __global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_out_gin(BatchStep
           rv[lane] = xn;
           ex[0] = fma(u, xn, ex[0]);
         } else {
-          const T gn = wt_draw(p.key_next, r, (int64_t)kN, dim, p.sigma);
+          const bool has_next = it + 1 < ww.count();
+          const T gn = draws.next(p.key_next, it, ww.sub(it) * 32, has_next ? ww.sub(it + 1) * 32 : 0, has_next,
+                                  (int64_t)kN, dim, p.sigma);
           gcur[r] = gn;
           rv[lane] = gn;
         }

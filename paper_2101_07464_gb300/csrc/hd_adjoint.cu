@@ -187,6 +187,97 @@ __global__ void __launch_bounds__(kAT) k_rank(T* Ab, int64_t ld, int K, int64_t 
   }
 }
 
+// FP32 with 16-byte aligned vectors: the same passes four rows per thread (float4 accesses).
+__host__ __device__ __forceinline__ bool al16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+__global__ void __launch_bounds__(kAT) k_rank4(float* Ab, int64_t ld, int K, int64_t dim4, const float* __restrict__ a,
+                                               const double* __restrict__ b, double sb, const float* __restrict__ c,
+                                               const double* __restrict__ d, double sd, const float* __restrict__ e,
+                                               const double* __restrict__ f, double sf, int Kf) {
+  __shared__ float bs[8], ds[8], fs[8];
+  const int j0 = blockIdx.y * 8;
+  if (threadIdx.x < 8) {
+    const int j = j0 + threadIdx.x;
+    bs[threadIdx.x] = (j < K) ? (float)(sb * b[j]) : 0.f;
+    ds[threadIdx.x] = (j < K && c) ? (float)(sd * d[j]) : 0.f;
+    fs[threadIdx.x] = (j < Kf && e) ? (float)(sf * f[j]) : 0.f;
+  }
+  __syncthreads();
+  const int jn = min(K, j0 + 8) - j0;
+  for (int64_t q4 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q4 < dim4; q4 += (int64_t)gridDim.x * blockDim.x) {
+    const float4 ar = reinterpret_cast<const float4*>(a)[q4];
+    const float4 cr = c ? reinterpret_cast<const float4*>(c)[q4] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 er = e ? reinterpret_cast<const float4*>(e)[q4] : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int q = 0; q < jn; q++) {
+      float4* col = reinterpret_cast<float4*>(Ab + (int64_t)(j0 + q) * ld);
+      float4 v = col[q4];
+      const float bq = bs[q], dq = ds[q], fq = fs[q];
+      v.x = fmaf(er.x, fq, fmaf(cr.x, dq, fmaf(ar.x, bq, v.x)));
+      v.y = fmaf(er.y, fq, fmaf(cr.y, dq, fmaf(ar.y, bq, v.y)));
+      v.z = fmaf(er.z, fq, fmaf(cr.z, dq, fmaf(ar.z, bq, v.z)));
+      v.w = fmaf(er.w, fq, fmaf(cr.w, dq, fmaf(ar.w, bq, v.w)));
+      col[q4] = v;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kAT) k_rowpass4(float* out, const float* in, double s_in, const float* __restrict__ A,
+                                                  int64_t ld, int K, const double* __restrict__ c, double c_scale,
+                                                  int64_t dim4, int accumulate) {
+  __shared__ float cs[kTmaxLimit + 1];
+  for (int j = threadIdx.x; j < K; j += blockDim.x) cs[j] = (float)(c_scale * c[j]);
+  __syncthreads();
+  const float si = (float)s_in;
+  for (int64_t q4 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q4 < dim4; q4 += (int64_t)gridDim.x * blockDim.x) {
+    float4 v = in ? reinterpret_cast<const float4*>(in)[q4] : make_float4(0.f, 0.f, 0.f, 0.f);
+    v.x *= si; v.y *= si; v.z *= si; v.w *= si;
+    for (int j = 0; j < K; j++) {
+      const float4 aj = reinterpret_cast<const float4*>(A + (int64_t)j * ld)[q4];
+      const float cj = cs[j];
+      v.x = fmaf(aj.x, cj, v.x);
+      v.y = fmaf(aj.y, cj, v.y);
+      v.z = fmaf(aj.z, cj, v.z);
+      v.w = fmaf(aj.w, cj, v.w);
+    }
+    if (accumulate) {
+      const float4 o = reinterpret_cast<const float4*>(out)[q4];
+      v.x += o.x; v.y += o.y; v.z += o.z; v.w += o.w;
+    }
+    reinterpret_cast<float4*>(out)[q4] = v;
+  }
+}
+
+// Column pass, float4: CTA (x, y) = row chunk x (a multiple of 128 rows) and columns 8y..8y+7.
+__global__ void __launch_bounds__(kAT) k_colpass4(const float* __restrict__ A, int64_t ld, int K, int64_t dim4,
+                                                  const float* __restrict__ v1, const float* __restrict__ v2,
+                                                  double* part) {
+  const int64_t per = ((dim4 + gridDim.x - 1) / gridDim.x + 31) / 32 * 32;
+  const int64_t q0 = (int64_t)blockIdx.x * per, q1 = min(dim4, q0 + per);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int j = blockIdx.y * 8 + warp;
+  if (j >= K) return;
+  const float4* Aj = reinterpret_cast<const float4*>(A + (int64_t)j * ld);
+  const float4* w1 = reinterpret_cast<const float4*>(v1);
+  const float4* w2 = reinterpret_cast<const float4*>(v2);
+  float s1 = 0.f, s2 = 0.f;
+#pragma unroll 4
+  for (int64_t q = q0 + lane; q < q1; q += 32) {
+    const float4 a = Aj[q];
+    const float4 x = w1[q];
+    s1 = fmaf(a.x, x.x, fmaf(a.y, x.y, fmaf(a.z, x.z, fmaf(a.w, x.w, s1))));
+    if (v2) {
+      const float4 y = w2[q];
+      s2 = fmaf(a.x, y.x, fmaf(a.y, y.y, fmaf(a.z, y.z, fmaf(a.w, y.w, s2))));
+    }
+  }
+  const double d1 = warp_sum((double)s1);
+  const double d2 = warp_sum((double)s2);
+  if (lane == 0) {
+    part[((int64_t)blockIdx.x * K + j) * 2] = d1;
+    part[((int64_t)blockIdx.x * K + j) * 2 + 1] = d2;
+  }
+}
+
 // Adjoint of the S-column recurrence of column k of a stack: S[:k, k] = c = -tau S_k a with
 // a = V_k^T u (recorded) and S[k, k] = tau = 2 / u^T u.  With cbar = Sbar[:k, k] and
 // taubar = Sbar[k, k] + cbar . c / tau:  abar = -tau S_k^T cbar (a = V^T u passes it on as
@@ -357,7 +448,11 @@ void colpass(const Ctx& c, const T* A, int64_t ld, int K, int64_t dim, const T* 
              const T* v2 = nullptr, double s2 = 0.0, double* o2 = nullptr) {
   if (K <= 0) return;
   AdjState& A_ = *c.st->adj;
-  k_colpass<T><<<dim3(A_.nblk, (K + 7) / 8), kAT, 0, c.s>>>(A, ld, K, dim, v1, v2, A_.part);
+  if (sizeof(T) == 4 && dim % 4 == 0 && al16(A) && al16(v1) && (!v2 || al16(v2)))
+    k_colpass4<<<dim3(A_.nblk, (K + 7) / 8), kAT, 0, c.s>>>((const float*)A, ld, K, dim / 4, (const float*)v1,
+                                                            (const float*)v2, A_.part);
+  else
+    k_colpass<T><<<dim3(A_.nblk, (K + 7) / 8), kAT, 0, c.s>>>(A, ld, K, dim, v1, v2, A_.part);
   k_colreduce<<<(K + kAT / 32 - 1) / (kAT / 32), kAT, 0, c.s>>>(A_.part, A_.nblk, K, s1, o1, s2, o2);
 }
 
@@ -366,6 +461,11 @@ void rowpass(const Ctx& c, T* out, const T* in, double s_in, const T* A, int64_t
              double cscale, int64_t dim, const double* dpre, int Kd, int acc, int64_t rnorm = INT64_MAX,
              double* npart = nullptr, unsigned grid = 0) {
   const unsigned g = grid ? grid : rows_grid(c.st, dim);
+  if (sizeof(T) == 4 && !dpre && !npart && dim % 4 == 0 && al16(out) && (!in || al16(in)) && al16(A)) {
+    k_rowpass4<<<rows_grid(c.st, dim / 4), kAT, 0, c.s>>>((float*)out, (const float*)in, s_in, (const float*)A, ld, K,
+                                                          coef, cscale, dim / 4, acc);
+    return;
+  }
   k_rowpass<T><<<g, kAT, 0, c.s>>>(out, in, s_in, A, ld, K, coef, cscale, dim, dpre, Kd, acc, rnorm, npart);
 }
 
@@ -374,6 +474,12 @@ void rank(const Ctx& c, T* Ab, int64_t ld, int K, int64_t dim, const T* a, const
           const T* cc = nullptr, const double* d = nullptr, double sd = 0.0, const T* e = nullptr,
           const double* f = nullptr, double sf = 0.0, int Kf = 0) {
   if (K <= 0) return;
+  if (sizeof(T) == 4 && dim % 4 == 0 && al16(Ab) && al16(a) && (!cc || al16(cc)) && (!e || al16(e))) {
+    dim3 g4(rows_grid(c.st, dim / 4), (unsigned)((K + 7) / 8));
+    k_rank4<<<g4, kAT, 0, c.s>>>((float*)Ab, ld, K, dim / 4, (const float*)a, b, sb, (const float*)cc, d, sd,
+                                 (const float*)e, f, sf, Kf);
+    return;
+  }
   dim3 g(rows_grid(c.st, dim), (unsigned)((K + 7) / 8));
   k_rank<T><<<g, kAT, 0, c.s>>>(Ab, ld, K, dim, a, b, sb, cc, d, sd, e, f, sf, Kf);
 }

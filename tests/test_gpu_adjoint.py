@@ -133,7 +133,8 @@ def test_fp64_adjoint_matches_finite_differences(ens, m, n, T, schedf, f):
 
 
 @pytest.mark.parametrize("ens,m,n,T,schedf,f", [
-    ("haar", 100_003, 100_003, 16, ALT, f_theta),
+    ("haar", 100_003, 100_003, 16, ALT, f_theta),    # rows not a multiple of 4: scalar passes
+    ("haar", 100_000, 100_000, 16, ALT, f_theta),    # 16-byte vector passes
     ("ginibre", 40_000, 70_001, 12, ALT, f_theta)])
 def test_fp32_adjoint_matches_fp64(ens, m, n, T, schedf, f):
     sched, x1, theta, beta, c = _case(ens, m, n, T, schedf, seed=4)

@@ -166,3 +166,29 @@ def test_batched_fused_run_matches_apply():
         xo, xr = out[off[i]:off[i + 1]].double(), x[off[i]:off[i + 1]].double()
         assert (xo - xr).norm().item() <= 1e-12 * xr.norm().item(), i
     b.close()
+
+
+def test_batched_fused_ginibre_run_matches_apply():
+    """Fused alternating trajectory on a batch of rectangular Ginibre trials (FP64, tanh):
+    per trial equal to the step-by-step products up to the dots' summation order."""
+    import paper_2101_07464_gb300 as hd
+    ms = [3001, 40, 20_000]
+    ns = [5003, 64, 12_011]
+    T = 12
+    flags = [ALT(t) for t in range(1, T + 1)]
+    x1 = torch.tensor(np.concatenate([synth.x1(n, 4, trial=i) for i, n in enumerate(ns)]),
+                      dtype=torch.float64, device="cuda")
+    b = hd.HDBatch("ginibre", ms, ns, T, 4, "f64", trial=1)
+    b.set_trial_sigmas([m ** -0.5 for m in ms])
+    x = x1.clone()
+    for t in range(T):
+        x = torch.tanh(b.apply(x, flags[t]))
+    b.reset(4)
+    out = torch.empty(int(b.off_m[-1]) if not flags[-1] else int(b.off_n[-1]), dtype=torch.float64, device="cuda")
+    hd.hd_run(b.h, hd.make_run_spec(flags, "tanh", 0.0, use_graph=True), x1, out)
+    torch.cuda.synchronize()
+    off = b.off_n if flags[-1] else b.off_m
+    for i in range(len(ns)):
+        xo, xr = out[off[i]:off[i + 1]], x[off[i]:off[i + 1]]
+        assert (xo - xr).norm().item() <= 1e-12 * xr.norm().item(), i
+    b.close()

@@ -113,6 +113,10 @@ struct FuseSpec {
   double a = 0.0;
   void* xnext = nullptr;
   const void* xprev = nullptr;
+  int amp_mode = 0;          // HD_DYN_AMP: 1 after Q beta, 2 after Q^T z, 3 after Q x
+  void* amp_v = nullptr;
+  void* amp_y = nullptr;
+  const void* amp_w = nullptr;
 };
 
 template <typename T>
@@ -139,11 +143,17 @@ int do_step(hd_state* st, const void* x, int transpose, void* y, const FuseSpec*
       b.base.dyn_a = (T)fs->a;
       b.base.xnext = (T*)fs->xnext;
       b.base.xprev = (const T*)fs->xprev;
+      b.base.amp_mode = fs->amp_mode;
+      b.base.amp_v = (T*)fs->amp_v;
+      b.base.amp_y = (T*)fs->amp_y;
+      b.base.amp_w = (const T*)fs->amp_w;
+      b.base.amp_zsq = st->amp_zsq;
+      b.base.amp_nnz = st->amp_nnz;
       b.base.y = nullptr;
       if (st->ens == HD_HAAR)
         b.base.c3 = make_sweep<T>(st, 4, kN, 2, kN, 1);
       else
-        b.base.c3 = make_sweep<T>(st, 5, kN + kD, 2, kN + kD, 1);
+        b.base.c3 = make_sweep<T>(st, 5, kN + kD, 3, kN + kD, 1);
     }
   }
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -263,22 +273,34 @@ int run_amp(hd_state* st, const hd_run_spec* sp) {
   const int64_t ntot = st->off[0][cnt];
   cudaError_t e = cudaMemsetAsync(st->amp_x, 0, (size_t)ntot * st->esz, st->stream);
   if (e != cudaSuccess) return cuda_fail(st, e);
+  // every step but the last runs its AMP update inside the fused output sweep, which also forms
+  // the next step's dot sweep; the last step uses the stand-alone AMP kernel
+  int prev_fused = 0;
   for (int t = 1; t <= sp->T; t++) {
-    int rc;
-    if (t == 1) {
-      rc = do_step<T>(st, st->xw[0], 0, st->yw);
-      if (!rc) e = launch_amp_init<T>(cnt, st->d_off[1], (const T*)st->yw, (const T*)st->amp_w,
-                                      (T*)st->amp_y, (T*)st->amp_z, st->amp_zsq, st->stream);
-    } else if (t % 2 == 0) {
-      rc = do_step<T>(st, st->amp_z, 1, st->yw);
-      if (!rc) e = launch_amp_x<T>(cnt, st->d_off[0], st->d_off[1], (const T*)st->yw, (T*)st->amp_x,
-                                   st->amp_zsq, sp->a, st->amp_nnz, st->stream);
-    } else {
-      rc = do_step<T>(st, st->amp_x, 0, st->yw);
-      if (!rc) e = launch_amp_z<T>(cnt, st->d_off[1], (const T*)st->amp_y, (const T*)st->yw, (T*)st->amp_z,
-                                   st->amp_nnz, st->amp_zsq, st->stream);
-    }
+    const int mode = (t == 1) ? 1 : ((t % 2 == 0) ? 2 : 3);
+    FuseSpec fs;
+    fs.skip_dots = prev_fused;
+    fs.fuse = st->fuse && t < sp->T && !(st->adj && st->adj->on);
+    fs.dyn = HD_DYN_AMP;
+    fs.a = sp->a;
+    fs.amp_mode = mode;
+    fs.amp_v = (mode == 2) ? st->amp_x : st->amp_z;
+    fs.amp_y = st->amp_y;
+    fs.amp_w = st->amp_w;
+    const void* xin = (mode == 1) ? st->xw[0] : ((mode == 2) ? st->amp_z : st->amp_x);
+    int rc = do_step<T>(st, xin, mode == 2 ? 1 : 0, st->yw, &fs);
     if (rc) return rc;
+    prev_fused = fs.fuse;
+    if (fs.fuse) continue;
+    if (mode == 1)
+      e = launch_amp_init<T>(cnt, st->d_off[1], (const T*)st->yw, (const T*)st->amp_w, (T*)st->amp_y,
+                             (T*)st->amp_z, st->amp_zsq, st->stream);
+    else if (mode == 2)
+      e = launch_amp_x<T>(cnt, st->d_off[0], st->d_off[1], (const T*)st->yw, (T*)st->amp_x, st->amp_zsq, sp->a,
+                          st->amp_nnz, st->stream);
+    else
+      e = launch_amp_z<T>(cnt, st->d_off[1], (const T*)st->amp_y, (const T*)st->yw, (T*)st->amp_z, st->amp_nnz,
+                          st->amp_zsq, st->stream);
     if (e != cudaSuccess) return cuda_fail(st, e);
     st->launches += 1;
   }

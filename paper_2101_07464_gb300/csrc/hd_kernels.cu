@@ -136,6 +136,9 @@ __device__ __forceinline__ StepPlan<T> make_plan(const BatchStep<T>& b, int spac
   p.y = b.base.y ? b.base.y + td.off[1 - d] : nullptr;
   p.xnext = b.base.xnext ? b.base.xnext + td.off[1 - d] : nullptr;
   p.xprev = b.base.xprev ? b.base.xprev + td.off[1 - d] : nullptr;
+  p.amp_v = b.base.amp_v ? b.base.amp_v + td.off[1 - d] : nullptr;
+  p.amp_y = b.base.amp_y ? b.base.amp_y + td.off[1 - d] : nullptr;
+  p.amp_w = b.base.amp_w ? b.base.amp_w + td.off[1 - d] : nullptr;
   return p;
 }
 
@@ -1193,7 +1196,9 @@ __global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_out_gin(BatchStep
   // FUSE (the next step is the other product): the next draw in this space and its dots are
   // not needed; the column pass forms the dots of x_{t+1} with V_N and B_n instead
   const int ncc = FUSE ? nc : kN;   // column-owner columns
-  WtSmem<T> sm(dsm_raw, blockDim.x >> 5, cfg.nbuf, nc, FUSE ? 2 : 1, ncc, 1);
+  WtSmem<T> sm(dsm_raw, blockDim.x >> 5, cfg.nbuf, nc, FUSE ? 3 : 1, ncc, 1);
+  const bool amp = FUSE && p.dyn == 4;
+  const int amode = amp ? p.amp_mode : 0;
   const ColSrc<T> src{(const T*)p.N.V, p.N.ld, kN, (const T*)p.Bn, p.ldBn};
   const int64_t dim = p.N.dim;
   T* ucol = (T*)p.Bn + (int64_t)kD * p.ldBn;
@@ -1203,9 +1208,10 @@ __global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_out_gin(BatchStep
   double acc[1][kColsPerLane];
 #pragma unroll
   for (int m = 0; m < kColsPerLane; m++) acc[0][m] = 0.0;
-  T ex[1] = {T(0)};   // (FUSE) u . x_{t+1}
+  T ex[2] = {T(0), T(0)};   // (FUSE) u . x_{t+1}; (AMP) ||z||^2 or ||x||_0 of this CTA's rows
   T* rv = sm.scr(warp, 0);
-  const bool need_prev = FUSE && p.dyn != 1;
+  const bool need_prev = FUSE && !amp && p.dyn != 1;
+  T amp_s = T(0);   // (AMP) threshold (mode 2) or Onsager factor (mode 3) of this trial
   PairDraws<T> draws;
   const WarpWalk ww(dim, cc);
   const int64_t ld = p.N.ld;
@@ -1216,8 +1222,16 @@ __global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_out_gin(BatchStep
         wt_load_cols(st, src, nc, r0);
         wt_load_vec(sm.srow(st, 0), (const T*)gcur, r0, ld, true);
         if (need_prev) wt_load_vec(sm.srow(st, 1), p.xprev, r0, dim, ((uintptr_t)p.xprev & 15u) == 0);
+        if (amode == 1) wt_load_vec(sm.srow(st, 1), p.amp_w, r0, dim, ((uintptr_t)p.amp_w & 15u) == 0);
+        if (amode == 2 || amode == 3)
+          wt_load_vec(sm.srow(st, 1), (const T*)p.amp_v, r0, dim, ((uintptr_t)p.amp_v & 15u) == 0);
+        if (amode == 3) wt_load_vec(sm.srow(st, 2), (const T*)p.amp_y, r0, dim, ((uintptr_t)p.amp_y & 15u) == 0);
       },
       [&]() {   // outputs of the preceding kernel's finalisation
+        if (amode == 2 || amode == 3) {
+          const double mi = (double)bs.desc[cc.trial].st[1].dim;
+          amp_s = (amode == 2) ? (T)(p.dyn_a * sqrt(p.amp_zsq[cc.trial] / mi)) : (T)((double)p.amp_nnz[cc.trial] / mi);
+        }
         for (int j = threadIdx.x; j < sm.cpad; j += blockDim.x) {
           T c0 = T(0), c1 = T(0);
           if (j < kN) {
@@ -1250,8 +1264,25 @@ __global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_out_gin(BatchStep
         if (FUSE) {
           T xn = T(0);
           if (r < dim) {
-            xn = fused_dyn<T>(p.dyn, p.dyn_a, yi, need_prev ? sm.srow(st, 1)[lane] : T(0));
-            p.xnext[r] = xn;
+            if (amode == 1) {          // y = Q beta + w; z = y
+              xn = yi + sm.srow(st, 1)[lane];
+              p.amp_y[r] = xn;
+              p.amp_v[r] = xn;
+              ex[1] = fma(xn, xn, ex[1]);
+            } else if (amode == 2) {   // x = eta(x + Q^T z; theta)
+              const T v = sm.srow(st, 1)[lane] + yi;
+              const T m = fabs(v) - amp_s;
+              xn = (m > T(0)) ? copysign(m, v) : T(0);
+              p.amp_v[r] = xn;
+              ex[1] += (xn != T(0)) ? T(1) : T(0);
+            } else if (amode == 3) {   // z = y - Q x + z ||x||_0 / m
+              xn = fma(sm.srow(st, 1)[lane], amp_s, sm.srow(st, 2)[lane] - yi);
+              p.amp_v[r] = xn;
+              ex[1] = fma(xn, xn, ex[1]);
+            } else {
+              xn = fused_dyn<T>(p.dyn, p.dyn_a, yi, need_prev ? sm.srow(st, 1)[lane] : T(0));
+              p.xnext[r] = xn;
+            }
           }
           rv[lane] = xn;
           ex[0] = fma(u, xn, ex[0]);
@@ -1268,11 +1299,11 @@ __global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_out_gin(BatchStep
       });
   if (!FUSE && kN == 0) return;   // no dots to form
   // partial sums: [0, ncc) columns . r (r = g_{t+1}, or (FUSE) x_{t+1}), (FUSE) [nc] u . x_{t+1}
-  const int P = FUSE ? nc + 1 : kN;
+  const int P = FUSE ? nc + 1 + (amp ? 1 : 0) : kN;
   double* part = p.ws.part + (int64_t)cc.local * P;
   const int off[1] = {0};
   wt_store_cols<1>(sm.comb, ncc, acc, part, off);
-  if (FUSE) block_sum_to<1>(ex, red, part + nc, 1);
+  if (FUSE) block_sum_to<2>(ex, red, part + nc, amp ? 2 : 1);
   double* rr = p.ws.scr(3);
   if (!reduce_partials(p.ws, 2, P, cc.local, cc.ncta, rr)) return;
   if (!FUSE) {
@@ -1286,6 +1317,10 @@ __global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_out_gin(BatchStep
       p.ws.z[j] = rr[j];
     }
     for (int i = threadIdx.x; i <= kD; i += blockDim.x) p.ws.z[kN + i] = (i < kD) ? rr[kN + i] : rr[nc];
+    if (amp && threadIdx.x == 0) {   // the trial's AMP scalar for the following steps
+      if (amode == 2) p.amp_nnz[cc.trial] = (int)(rr[nc + 1] + 0.5);
+      else p.amp_zsq[cc.trial] = rr[nc + 1];
+    }
     __syncthreads();
     fin_dots(p.N.S, p.Tm, kN, zs, p.ws.w, (double*)dsm_raw, (int64_t)sm.bytes(), p.ws.err);
   }
@@ -1353,7 +1388,7 @@ cudaError_t launch_step(const BatchStep<T>& b, cudaStream_t s, cudaEvent_t* ev, 
                         sweep_smem_bytes<T>(p.c3.W, p.c3.nbuf, p.kN, 2, p.kN, 1), s, pdl, b);
   else if (p.fuse)
     e = launch_sweep<T>(k_out_gin<T, true>, p.c3, b.map[ospace].ctas,
-                        sweep_smem_bytes<T>(p.c3.W, p.c3.nbuf, ncg, 2, ncg, 1), s, pdl, b);
+                        sweep_smem_bytes<T>(p.c3.W, p.c3.nbuf, ncg, 3, ncg, 1), s, pdl, b);
   else
     e = launch_sweep<T>(k_out_gin<T, false>, p.c3, b.map[ospace].ctas,
                         sweep_smem_bytes<T>(p.c3.W, p.c3.nbuf, ncg, 1, p.kN, 1), s, pdl, b);

@@ -114,6 +114,15 @@ struct StepPlan {
   T dyn_a;
   T* xnext;             // x_{t+1} (output space, packed base); written by the fused K3
   const T* xprev;       // x_{t-1} (output space, packed base); may alias xnext
+  // AMP in the fused Ginibre K3 (dyn == kDynAmp), per trial: amp_mode 1 = after Q beta
+  // (y = Q beta + w, z = y), 2 = after Q^T z (x = eta(x + s; a ||z|| / sqrt(m))), 3 = after Q x
+  // (z = y - q + z ||x||_0 / m).  Vectors in the output space (packed bases).
+  int amp_mode;
+  T* amp_v;             // updated in place: z (modes 1, 3) or x (mode 2)
+  T* amp_y;             // y = Q beta + w: written in mode 1, read in mode 3
+  const T* amp_w;       // the noise w (mode 1)
+  double* amp_zsq;      // per trial ||z||^2: written in modes 1 and 3, read in mode 2
+  int* amp_nnz;         // per trial ||x||_0: written in mode 2, read in mode 3
 };
 
 // ------------------------------------------------------------------------------------

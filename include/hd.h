@@ -192,6 +192,41 @@ HD_API int hd_profile_enable(hd_state* st, int on);
 HD_API int hd_profile_read(hd_state* st, double* ms3, int64_t* launches3, double* bytes3,
                            int clear);
 
+/* Launch shapes of the sweeps (the paper fixes none: these are the engine's own choices for
+ * streaming the reflector stacks of Algorithms 1 and 2; results depend on them only through
+ * the order of floating-point sums).  Two choices are tunable:
+ *   - per sweep kernel (dots, update, output Haar, output Ginibre, and the fused output
+ *     sweeps of both) and per range of column counts (bit width of the count: 0, 1, 2-3,
+ *     4-7, ..., >= 512), the pair (warps per CTA, pipeline stages per warp), each 1, 2, 4
+ *     or 8; 0 means the built-in rule (the pair with the most bytes in flight per SM);
+ *   - the CTA split, one of hd_get_map_options' candidates: sub-tiles of 32 rows per CTA in
+ *     the n-space and in the m-space (option 0, the built-in rule: one wave of CTAs over the
+ *     whole batch; later options split large trials over more CTAs).
+ * A shape that does not fit the shared memory at some column count falls back to the rule.
+ *
+ * hd_autotune measures them on the caller's trajectory: it runs `spec` as hd_run (without a
+ * graph, from x1, writing x_out; reps >= 1 timed runs per candidate, at most 64) under every
+ * (warps, stages) pair with CUDA events around each sweep, keeps per kernel and column range
+ * the pair of least device time, then times each CTA split over whole trajectories and keeps
+ * the fastest.  About 16 * reps + nmaps * (reps + 1) + 1 trajectories.  The result applies to
+ * this state and is cached for the process under the state's shape (ensemble, dtype, trials
+ * and their dimensions, T_max, device); hd_create / hd_create_batched of the same shape
+ * start from it.  The state is left reset (hd_reset with its seed); profiling totals are
+ * kept, unread profiling records dropped.  Errors: those of hd_run; HD_ERR_ARG (reps out of
+ * range), HD_ERR_STATE (reverse mode on).
+ *
+ * hd_get_tuning writes the state's choices as HD_TUNE_WORDS int32 words (nwords >= that):
+ * [1, split option, then for kernel q = 0..5 and range b = 0..10: warps, stages]; the words
+ * can be stored and handed to hd_set_tuning on a state of the same shape (HD_ERR_ARG for a
+ * bad version, split option or value).  hd_set_tuning with nwords = 0 restores the rules.
+ * hd_get_map_options returns the number of candidate splits and, when spc is non-null,
+ * their sub-tiles per CTA (2 x count int32: n-space, m-space). */
+#define HD_TUNE_WORDS 134
+HD_API int hd_autotune(hd_state* st, const hd_run_spec* spec, const void* x1, void* x_out, int32_t reps);
+HD_API int hd_get_tuning(const hd_state* st, int32_t* words, int32_t nwords);
+HD_API int hd_set_tuning(hd_state* st, const int32_t* words, int32_t nwords);
+HD_API int hd_get_map_options(const hd_state* st, int32_t* count, int32_t* spc);
+
 /* Number of kernels this state has launched (graph replays count their kernels). */
 HD_API int hd_get_launches(const hd_state* st, int64_t* launches);
 

@@ -50,6 +50,10 @@ _PROTOS = {
     "hd_reset": (_c.c_int, [_P, _c.c_uint64]),
     "hd_sync": (_c.c_int, [_P]),
     "hd_run": (_c.c_int, [_P, _P, _P, _P]),
+    "hd_autotune": (_c.c_int, [_P, _P, _P, _P, _c.c_int32]),
+    "hd_get_tuning": (_c.c_int, [_P, _P, _c.c_int32]),
+    "hd_set_tuning": (_c.c_int, [_P, _P, _c.c_int32]),
+    "hd_get_map_options": (_c.c_int, [_P, _c.POINTER(_c.c_int32), _P]),
     "hd_profile_enable": (_c.c_int, [_P, _c.c_int]),
     "hd_profile_read": (_c.c_int, [_P, _c.POINTER(_c.c_double), _c.POINTER(_c.c_int64),
                                    _c.POINTER(_c.c_double), _c.c_int]),
@@ -228,15 +232,48 @@ def make_run_spec(transpose_flags, dynamics, a=0.0, use_graph=True, aux=None):
 
 def hd_run(state, spec, x1, x_out):
     """x1 / x_out: CUDA tensors, page-locked CPU tensors, or raw addresses."""
-    def addr(t, what):
-        if isinstance(t, int):
-            return t
-        if not t.is_contiguous():
-            raise ValueError("%s must be contiguous" % what)
-        if not t.is_cuda and not t.is_pinned():
-            raise ValueError("%s must be a CUDA tensor or page-locked host memory" % what)
-        return t.data_ptr()
-    _check(lib().hd_run(state, ctypes.byref(spec), addr(x1, "x1"), addr(x_out, "x_out")), "hd_run")
+    _check(lib().hd_run(state, ctypes.byref(spec), _run_addr(x1, "x1"), _run_addr(x_out, "x_out")),
+           "hd_run")
+
+
+HD_TUNE_WORDS = 134
+
+
+def _run_addr(t, what):
+    if isinstance(t, int):
+        return t
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % what)
+    if not t.is_cuda and not t.is_pinned():
+        raise ValueError("%s must be a CUDA tensor or page-locked host memory" % what)
+    return t.data_ptr()
+
+
+def hd_autotune(state, spec, x1, x_out, reps=2):
+    """Measure and keep the fastest launch shapes and CTA split for trajectory `spec`."""
+    _check(lib().hd_autotune(state, ctypes.byref(spec), _run_addr(x1, "x1"), _run_addr(x_out, "x_out"),
+                             int(reps)), "hd_autotune")
+
+
+def hd_get_tuning(state):
+    w = (ctypes.c_int32 * HD_TUNE_WORDS)()
+    _check(lib().hd_get_tuning(state, w, HD_TUNE_WORDS), "hd_get_tuning")
+    return list(w)
+
+
+def hd_set_tuning(state, words):
+    """words: a list from hd_get_tuning (same shape of state), or [] for the built-in rules."""
+    w = (ctypes.c_int32 * max(1, len(words)))(*[int(v) for v in words])
+    _check(lib().hd_set_tuning(state, w, len(words)), "hd_set_tuning")
+
+
+def hd_get_map_options(state):
+    """[(sub-tiles per CTA in the n-space, in the m-space)] of the candidate CTA splits."""
+    cnt = ctypes.c_int32()
+    _check(lib().hd_get_map_options(state, ctypes.byref(cnt), None), "hd_get_map_options")
+    spc = (ctypes.c_int32 * (2 * cnt.value))()
+    _check(lib().hd_get_map_options(state, ctypes.byref(cnt), spc), "hd_get_map_options")
+    return [(spc[2 * o], spc[2 * o + 1]) for o in range(cnt.value)]
 
 
 def hd_profile_enable(state, on=True):
@@ -332,6 +369,26 @@ class HDBatch:
     def set_trial_sigmas(self, sigmas):
         hd_set_trial_sigmas(self.h, sigmas)
 
+    def _dims(self):
+        return (int(self.off_n[-1]), int(self.off_m[-1]))
+
+    def autotune(self, schedule, dynamics, x1, a=0.0, reps=2, aux=None):
+        """hd_autotune on the trajectory (schedule, dynamics, a) from x1; leaves the state reset."""
+        import torch
+        spec = make_run_spec(schedule, dynamics, a, use_graph=False, aux=aux)
+        dmax = int(max(self._dims()))
+        out = torch.empty(dmax, dtype=self.torch_dtype, device=x1.device)
+        hd_autotune(self.h, spec, x1, out, reps)
+
+    def tuning(self):
+        return hd_get_tuning(self.h)
+
+    def set_tuning(self, words):
+        hd_set_tuning(self.h, words)
+
+    def map_options(self):
+        return hd_get_map_options(self.h)
+
     def close(self):
         if self.h:
             hd_destroy(self.h)
@@ -407,6 +464,26 @@ class HD:
 
     def adjoint_restart(self):
         hd_adjoint_restart(self.h)
+
+    def _dims(self):
+        return (self.n, self.m)
+
+    def autotune(self, schedule, dynamics, x1, a=0.0, reps=2, aux=None):
+        """hd_autotune on the trajectory (schedule, dynamics, a) from x1; leaves the state reset."""
+        import torch
+        spec = make_run_spec(schedule, dynamics, a, use_graph=False, aux=aux)
+        dmax = int(max(self._dims()))
+        out = torch.empty(dmax, dtype=self.torch_dtype, device=x1.device)
+        hd_autotune(self.h, spec, x1, out, reps)
+
+    def tuning(self):
+        return hd_get_tuning(self.h)
+
+    def set_tuning(self, words):
+        hd_set_tuning(self.h, words)
+
+    def map_options(self):
+        return hd_get_map_options(self.h)
 
     def close(self):
         if self.h:

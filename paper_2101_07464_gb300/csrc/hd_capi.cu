@@ -27,7 +27,8 @@ thread_local char g_last_error[256] = "";
 // Shape of a sweep over ncolT staged columns and NRV staged row vectors (ncolC column-owner
 // columns, NR right-hand sides): the (warps per CTA, pipeline stages per warp) pair that puts
 // the most bytes in flight per SM (capped at 128 KB; then more resident warps, then fewer
-// stages).  The CTA count comes from the space's CTA map.
+// stages), unless the state carries a measured shape for this kernel and column range
+// (hd_autotune, hd_set_tuning).  The CTA count comes from the space's CTA map.
 template <typename T>
 SweepCfg make_sweep(const hd_state* st, int which, int ncolT, int NRV, int ncolC, int NR) {
   SweepCfg c;
@@ -36,14 +37,17 @@ SweepCfg make_sweep(const hd_state* st, int which, int ncolT, int NRV, int ncolC
   const int stat = st->static_smem[which] + 1024;
   const int blk = st->smem_blk_max - stat;
   const double stage = (double)(ncolT + NRV) * 32.0 * sizeof(T);
+  auto ctas_of = [&](int W, int nb) {
+    const size_t b = sweep_smem_bytes<T>(W, nb, ncolT, NRV, ncolC, NR);
+    if ((int)b > blk) return 0;
+    const int by_regs = std::max(1, st->occ_regs[which] * 8 / W);
+    // the CTA maps give each SM at most kSweepCtasPerSm CTAs
+    return std::min(std::min(by_regs, (int)(st->smem_sm / (b + stat))), kSweepCtasPerSm);
+  };
   double best = -1.0;
   for (int W = 8; W >= 1; W /= 2) {
     for (int nb = 1; nb <= 8; nb *= 2) {
-      const size_t b = sweep_smem_bytes<T>(W, nb, ncolT, NRV, ncolC, NR);
-      if ((int)b > blk) continue;
-      const int by_regs = std::max(1, st->occ_regs[which] * 8 / W);
-      // the CTA maps give each SM at most kSweepCtasPerSm CTAs
-      const int ctas = std::min(std::min(by_regs, (int)(st->smem_sm / (b + stat))), kSweepCtasPerSm);
+      const int ctas = ctas_of(W, nb);
       if (ctas < 1) continue;
       const int warps = std::min(64, ctas * W);
       const double inflight = std::min(warps * nb * stage, 131072.0);
@@ -55,6 +59,18 @@ SweepCfg make_sweep(const hd_state* st, int which, int ncolT, int NRV, int ncolC
       }
     }
   }
+  // a shape forced by the autotuner, else the tuned one of this column range, when it fits
+  const int bucket = hd::tune_bucket(ncolT);
+  int tW = st->force_W, tnb = st->force_nb;
+  if (!tW) {
+    tW = st->tuneW[which][bucket];
+    tnb = st->tuneNb[which][bucket];
+  }
+  if (tW > 0 && tnb > 0 && ctas_of(tW, tnb) >= 1) {
+    c.W = tW;
+    c.nbuf = tnb;
+  }
+  c.tag = which | (bucket << 4);
   c.g.ctas = 0;
   c.g.vpc = 0;
   c.g.gsize = 1;
@@ -182,9 +198,11 @@ int do_step(hd_state* st, const void* x, int transpose, void* y, const FuseSpec*
     const bool fz = fs && fs->fuse;
     const double bb[3] = {es * (nD * kD + bd + nD), es * (nD * kD + 3.0 * nD),
                           es * (nN * kN + bn + (fz ? 5.0 : 4.0) * nN)};
+    const SweepCfg* cs[3] = {&b.base.c1, &b.base.c2, &b.base.c3};
     for (int q = 0; q < 3; q++) {
       st->prof_kind[slot0 + q] = launched[q] ? q : -1;
       st->prof_bytes[slot0 + q] = bb[q];
+      st->prof_tag[slot0 + q] = cs[q]->tag | (cs[q]->W << 8) | (cs[q]->nbuf << 12);
     }
     st->prof_used += 3;
   }
@@ -339,29 +357,22 @@ bool graph_matches(const hd_state* st, const hd_run_spec* sp) {
   if (!st->gexec || st->g_T != sp->T || st->g_dyn != sp->dynamics || st->g_a != sp->a) return false;
   if (st->g_seed != st->seed || st->g_trial != st->trial || st->g_sigma != st->sigma) return false;
   if (st->g_sigma_gen != st->sigma_gen) return false;
+  if (st->g_tune_gen != st->tune_gen) return false;
   if (st->g_stream != st->stream || st->g_prof != st->prof_on) return false;
   for (int t = 0; t < sp->T; t++)
     if (st->g_flags[t] != (sp->transpose[t] ? 1 : 0)) return false;
   return true;
 }
 
-// CTA map of one space: every trial gets ceil(nsub_i / spc) CTAs of spc 32-row sub-tiles,
-// spc chosen so that a single large trial fills kSweepCtasPerSm CTAs per SM (one wave).
-bool build_map(hd_state* st, int s) {
+// CTA map of one space: every trial gets ceil(nsub_i / spc) CTAs of spc 32-row sub-tiles.
+bool build_map(hd_state* st, int s, int64_t spc, CtaMap* out) {
   const int count = st->count;
-  std::vector<int64_t> nsub(count);
-  int64_t total = 0;
-  for (int i = 0; i < count; i++) {
-    nsub[i] = (st->dims[s][i] + 31) / 32;
-    total += nsub[i];
-  }
-  const int64_t per = (int64_t)kSweepCtasPerSm * st->nsm;
-  const int64_t spc = std::max<int64_t>(16, (total + per - 1) / per);
   std::vector<int> cta0(count + 1), spcv(count);
   std::vector<int> ct;
   cta0[0] = 0;
   for (int i = 0; i < count; i++) {
-    const int n_i = (int)((nsub[i] + spc - 1) / spc);
+    const int64_t nsub = (st->dims[s][i] + 31) / 32;
+    const int n_i = (int)((nsub + spc - 1) / spc);
     spcv[i] = (int)spc;
     for (int c = 0; c < n_i; c++) ct.push_back(i);
     cta0[i + 1] = cta0[i] + n_i;
@@ -375,10 +386,50 @@ bool build_map(hd_state* st, int s) {
       cudaMemcpy(d_c0, cta0.data(), cta0.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(d_sp, spcv.data(), spcv.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
     return false;
-  st->map[s].cta_trial = d_ct;
-  st->map[s].cta0 = d_c0;
-  st->map[s].spc = d_sp;
-  st->map[s].ctas = cta0[count];
+  out->cta_trial = d_ct;
+  out->cta0 = d_c0;
+  out->spc = d_sp;
+  out->ctas = cta0[count];
+  return true;
+}
+
+// The candidate CTA splits.  Option 0 (the built-in rule): spc chosen so that the whole batch
+// fills kSweepCtasPerSm CTAs per SM (one wave; at least 16 sub-tiles per CTA).  Options 1.. halve
+// the sub-tiles per CTA from min(that, the largest trial's sub-tiles), which splits the largest
+// trials over more CTAs (load balance of unequal trials, more waves); at least 16 sub-tiles.
+bool build_maps(hd_state* st) {
+  int64_t spc0[2], base[2];
+  for (int s = 0; s < 2; s++) {
+    int64_t total = 0, maxsub = 1;
+    for (int i = 0; i < st->count; i++) {
+      const int64_t nsub = (st->dims[s][i] + 31) / 32;
+      total += nsub;
+      maxsub = std::max(maxsub, nsub);
+    }
+    const int64_t per = (int64_t)kSweepCtasPerSm * st->nsm;
+    spc0[s] = std::max<int64_t>(16, (total + per - 1) / per);
+    base[s] = std::min(spc0[s], maxsub);
+  }
+  st->nmaps = 0;
+  for (int j = 0; j < kMapOpts; j++) {
+    int64_t spc[2];
+    for (int s = 0; s < 2; s++)
+      spc[s] = (j == 0) ? spc0[s] : std::max<int64_t>(16, (base[s] + (1 << j) - 1) >> j);
+    if (j > 0 && spc[0] >= std::min(spc0[0], base[0]) && spc[1] >= std::min(spc0[1], base[1])) continue;
+    bool dup = false;
+    for (int o = 0; o < st->nmaps; o++)
+      dup = dup || (st->map_spc[o][0] == spc[0] && st->map_spc[o][1] == spc[1]);
+    if (dup) continue;
+    const int o = st->nmaps;
+    for (int s = 0; s < 2; s++) {
+      st->map_spc[o][s] = (int)spc[s];
+      if (!build_map(st, s, spc[s], &st->maps[o][s])) return false;
+    }
+    st->nmaps++;
+  }
+  st->map_opt = 0;
+  st->map[0] = st->maps[0][0];
+  st->map[1] = st->maps[0][1];
   return true;
 }
 
@@ -448,8 +499,7 @@ int create_common(int ensemble, int count, const int64_t* m, const int64_t* n, i
     st->occ_regs[q] = (dtype == HD_F64) ? kernel_occupancy<double>(q, 0) : kernel_occupancy<float>(q, 0);
     st->static_smem[q] = (dtype == HD_F64) ? kernel_static_smem<double>(q) : kernel_static_smem<float>(q);
   }
-  for (int s = 0; s < 2; s++)
-    if (!build_map(st, s)) return fail(HD_ERR_OOM);
+  if (!build_maps(st)) return fail(HD_ERR_OOM);
   const int64_t Tm = T_max;
   const int64_t Sld = (T_max + 1) / 2 * 2;   // even: every column of S starts 16-byte aligned
   st->Sld = (int)Sld;
@@ -559,6 +609,7 @@ int create_common(int ensemble, int count, const int64_t* m, const int64_t* n, i
     set_error("hd_create initialisation", cudaGetLastError());
     return fail(HD_ERR_CUDA);
   }
+  tune_load_cached(st);
   *out = st;
   return HD_OK;
 }
@@ -794,6 +845,7 @@ HD_API int hd_run(hd_state* st, const hd_run_spec* sp, const void* x1, void* x_o
       st->g_trial = st->trial;
       st->g_sigma = st->sigma;
       st->g_sigma_gen = st->sigma_gen;
+      st->g_tune_gen = st->tune_gen;
       st->g_stream = st->stream;
       st->g_flags.assign(sp->transpose, sp->transpose + sp->T);
       for (auto& f : st->g_flags) f = f ? 1 : 0;
@@ -846,6 +898,7 @@ HD_API int hd_profile_enable(hd_state* st, int on) {
       }
     st->prof_kind.assign(slots, -1);
     st->prof_bytes.assign(slots, 0.0);
+    st->prof_tag.assign(slots, 0);
     st->prof_cap = slots;
   }
   st->prof_on = on ? 1 : 0;

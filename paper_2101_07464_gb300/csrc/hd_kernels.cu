@@ -1354,8 +1354,15 @@ cudaError_t launch_sweep(void (*kern)(BatchStep<T>), const SweepCfg& c, int ctas
 template <typename T>
 cudaError_t launch_step(const BatchStep<T>& b, cudaStream_t s, cudaEvent_t* ev, int* launched) {
   auto rec = [&](int i) {
-    // External: inside a stream capture this becomes an event-record node of the graph
-    if (ev && ev[i]) cudaEventRecordWithFlags(ev[i], s, cudaEventRecordExternal);
+    if (!ev || !ev[i]) return;
+    // inside a stream capture the record becomes an event-record node of the graph (the
+    // External flag); outside a capture that flag is not allowed
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) cs = cudaStreamCaptureStatusNone;
+    if (cs == cudaStreamCaptureStatusActive)
+      cudaEventRecordWithFlags(ev[i], s, cudaEventRecordExternal);
+    else
+      cudaEventRecord(ev[i], s);
   };
   const StepPlan<T>& p = b.base;
   const bool pdl = p.pdl != 0;

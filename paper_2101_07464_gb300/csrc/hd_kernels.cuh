@@ -73,6 +73,7 @@ struct SweepCfg {
   int W;
   int nbuf;
   Grid g;
+  int tag;          // host bookkeeping (profiling): kernel | column bucket << 4
 };
 
 // Dynamic shared memory of a sweep (the carve of WtSmem: W * nbuf stages of ncolT columns and

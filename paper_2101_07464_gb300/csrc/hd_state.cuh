@@ -1,6 +1,7 @@
 // The library's state object (host side) and the helpers shared by its translation units.
 #pragma once
 #include <cstdint>
+#include <string>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -8,6 +9,22 @@
 #include "hd_kernels.cuh"
 
 namespace hd {
+
+// Launch-shape tuning: per sweep kernel (dots, update, out Haar, out Gin, fused out Haar,
+// fused out Gin) and per range of column counts (bucket b holds counts c with bit width b:
+// 0, 1, 2-3, 4-7, ...), the tuned (warps per CTA, stages per warp); 0 = the built-in rule.
+constexpr int kSweepKinds = 6;
+constexpr int kTuneBuckets = 11;
+constexpr int kMapOpts = 5;            // CTA splits (sub-tiles per CTA) tried by the autotuner
+constexpr int kTuneWords = 2 + 2 * kSweepKinds * kTuneBuckets;
+inline int tune_bucket(int cols) {
+  int b = 0;
+  while (cols > 0 && b < kTuneBuckets - 1) {
+    cols >>= 1;
+    b++;
+  }
+  return b;
+}
 
 // Reverse-mode record and accumulators of a single-trial state (hd_adjoint_*).
 struct AdjState {
@@ -58,8 +75,18 @@ struct hd_state {
   size_t esz = 8;                // element size of vectors and stacks
   std::vector<TrialDesc> hdesc;  // host copy of the per-trial descriptors
   TrialDesc* ddesc = nullptr;
-  CtaMap map[2];
+  CtaMap map[2];                 // the CTA split in use (maps[map_opt])
+  CtaMap maps[hd::kMapOpts][2];  // candidate splits per space (option 0: the built-in rule)
+  int map_spc[hd::kMapOpts][2] = {};
+  int nmaps = 1;
+  int map_opt = 0;
   int maxncta = 1;
+  // launch shapes: tuned table, autotuner override, cache key of the state's shape
+  int8_t tuneW[hd::kSweepKinds][hd::kTuneBuckets] = {};
+  int8_t tuneNb[hd::kSweepKinds][hd::kTuneBuckets] = {};
+  int force_W = 0, force_nb = 0;
+  int64_t tune_gen = 0;
+  std::string tune_key;
   unsigned int* err = nullptr;
   unsigned int* cnt = nullptr;
   size_t cnt_bytes = 0;
@@ -89,6 +116,7 @@ struct hd_state {
   int g_final = 0;
   int g_launches = 0;
   int g_prof = 0;
+  int64_t g_tune_gen = -1;
   int64_t launches = 0;          // kernel launches issued (graph replays count their kernels)
   // profiling: event pairs around each sweep, algorithmic bytes of each recorded launch
   int prof_on = 0;
@@ -97,6 +125,7 @@ struct hd_state {
   std::vector<cudaEvent_t> prof_ev;
   std::vector<int> prof_kind;
   std::vector<double> prof_bytes;
+  std::vector<int> prof_tag;     // per slot: kernel | bucket << 4 | W << 8 | stages << 12
   double prof_ms[3] = {0, 0, 0};
   int64_t prof_n[3] = {0, 0, 0};
   double prof_b[3] = {0, 0, 0};
@@ -123,4 +152,8 @@ void record_error_text(const char* msg);
 int adj_record_step(hd_state* st, const void* x, int transpose, int kD, int kN);
 int adj_record_after(hd_state* st, int kD, int kN);
 int adj_on_reset(hd_state* st);
+// launch-shape tuning (hd_tune.cu)
+void tune_load_cached(hd_state* st);
+int tune_apply_words(hd_state* st, const int32_t* words);
+void set_map_option(hd_state* st, int opt);
 }  // namespace hd

@@ -17,12 +17,15 @@ def next_input(y, t_next, transpose_next, m, n, seed):
 
 
 def teacher_forced(ens, m, n, T, seed, dtype, schedule, sigma=1.0, x1=None, dynamics=None,
-                   trial=0):
+                   trial=0, setup=None):
+    """setup(state): called on the GPU state once, before its first product."""
     import torch
     from paper_2101_07464_gb300 import HD
     tdt = torch.float64 if dtype == "f64" else torch.float32
     ora = make_oracle(ens, m, n, T, seed, trial=trial, sigma=sigma)
     gpu = HD(ens, m, n, T, seed, dtype, sigma=sigma, trial=trial)
+    if setup is not None:
+        setup(gpu)
     x = synth.x1(m if schedule(1) else n, seed) if x1 is None else x1
     x_prev = None
     errs = []

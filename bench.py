@@ -45,6 +45,8 @@ def parse(argv=None):
     ap.add_argument("--no-amp", action="store_true", help="skip the batched AMP measurement")
     ap.add_argument("--amp-trials", type=int, default=4096)
     ap.add_argument("--no-adjoint", action="store_true", help="skip the reverse-mode measurement")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the built-in launch shapes (no hd_autotune before timing)")
     return ap.parse_args(argv)
 
 
@@ -261,7 +263,10 @@ def measure_amp_batch(args, rank, world, dist):
     bt = torch.from_numpy(beta).cuda()
     wt = torch.from_numpy(w).cuda()
     out = torch.empty_like(bt)
-    spec = hd.make_run_spec([t % 2 == 0 for t in range(1, T + 1)], "amp", 1.1, use_graph=True, aux=wt)
+    flags = [t % 2 == 0 for t in range(1, T + 1)]
+    spec = hd.make_run_spec(flags, "amp", 1.1, use_graph=True, aux=wt)
+    if not args.no_autotune:
+        b.autotune(flags, "amp", bt, a=1.1, reps=1, aux=wt)
     for _ in range(2):
         hd.hd_run(b.h, spec, bt, out)
     torch.cuda.synchronize()
@@ -284,6 +289,7 @@ def measure_amp_batch(args, rank, world, dist):
             "ms_per_trajectory": secs * 1e3, "trials": count * world, "sum_n": sum_n * world, "T": T,
             "dtype": "f32 (FP64 coefficients)", "graph": "one CUDA graph per trajectory",
             "credited_GBps": credited / secs / 1e9, "mse": mse,
+            "launch_shapes": "built-in" if args.no_autotune else "hd_autotune (untimed, before the runs)",
             "config": "Gin(m_i, n_i), n_i ~ U{1000..100000}, m_i = n_i/2, AMP soft threshold 1.1 sigma_t"}
 
 
@@ -366,6 +372,8 @@ def run_ours(args):
         spec = hd.make_run_spec(flags, "sign_mem", 0.5, use_graph=True)
         x1 = torch.tensor(synth.x1(n, args.seed, trial=rank), dtype=tdt, device="cuda")
         xout = torch.empty(n, dtype=tdt, device="cuda")
+        if not args.no_autotune:   # measured launch shapes, before the timed region
+            st.autotune(flags, "sign_mem", x1, a=0.5, reps=2)
         secs, launches = time_trajectories(st, spec, x1, xout, args.steps, args.warmup, dist)
         prof = profile_kernels(st, spec, x1, xout, args.steps) if profile else None
         return st, spec, secs, prof, launches
@@ -453,7 +461,9 @@ def run_ours(args):
                            else "FP64", "per_rank": "independent trial (Philox trial word = rank)",
                            "l2": "inputs larger than L2 (two reflector stacks of %.0f MB each)"
                            % (n * T * tdt.itemsize / 1e6),
-                           "graph": "one CUDA graph per trajectory"},
+                           "graph": "one CUDA graph per trajectory",
+                           "launch_shapes": "built-in" if args.no_autotune
+                           else "hd_autotune (untimed, before the timed region)"},
                 "roofline": roofline,
                 "step_credited_GBps": step_gbps,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,

@@ -746,10 +746,57 @@ constexpr int kColsPerLane = 8;   // column owner: up to 8 * 32 = 256 columns
 
 // Column owner: acc[r][m] += sum_i V[i, lane + 32 m] rhs_r[i] over the 32 rows, m < 8.
 // Logical chunk c of column j sits at slot (c + j) mod NCH, and j mod NCH = lane mod NCH for
-// every m, so the NCH chunk offsets are per-lane constants.
+// every m, so the NCH chunk offsets are per-lane constants.  acc is in the storage type and
+// covers at most kColFlush sub-tiles (wt_flush_cols).
+// Columns j0 = lane + 32 m and (TWO) j1 = j0 + 32 of the sub-tile against the right-hand sides.
+template <typename T, int NR, bool TWO>
+__device__ __forceinline__ void wt_col_pair(const T* buf, int ncol, int m, const int (&coff)[WT<T>::NCH],
+                                            const T* rhs0, const T* rhs1, T (&acc)[NR][kColsPerLane]) {
+  constexpr int NCH = WT<T>::NCH, VEC = WT<T>::VEC;
+  const int lane = threadIdx.x & 31;
+  const int j0 = lane + 32 * m, j1 = j0 + 32;
+  const bool h1 = TWO && j1 < ncol;
+  if (j0 >= ncol) return;
+  T s0[NR], s1[NR];
+#pragma unroll
+  for (int r = 0; r < NR; r++) s0[r] = s1[r] = T(0);
+  const T* col0 = buf + j0 * 32;
+  const T* col1 = buf + (h1 ? j1 : j0) * 32;
+#pragma unroll
+  for (int c = 0; c < NCH; c++) {
+    const Vec<T> v0 = *reinterpret_cast<const Vec<T>*>(col0 + coff[c]);
+    Vec<T> v1;
+    if (TWO) v1 = *reinterpret_cast<const Vec<T>*>(col1 + coff[c]);
+    const Vec<T> b0 = *reinterpret_cast<const Vec<T>*>(rhs0 + c * VEC);
+#pragma unroll
+    for (int e = 0; e < VEC; e++) {
+      s0[0] = fma(v0.e[e], b0.e[e], s0[0]);
+      if (TWO) s1[0] = fma(v1.e[e], b0.e[e], s1[0]);
+    }
+    if (NR > 1) {
+      const Vec<T> b1 = *reinterpret_cast<const Vec<T>*>(rhs1 + c * VEC);
+#pragma unroll
+      for (int e = 0; e < VEC; e++) {
+        s0[NR - 1] = fma(v0.e[e], b1.e[e], s0[NR - 1]);
+        if (TWO) s1[NR - 1] = fma(v1.e[e], b1.e[e], s1[NR - 1]);
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < NR; r++) {
+    acc[r][m] += s0[r];
+    if (TWO && h1) acc[r][m + 1] += s1[r];
+  }
+}
+
+// Column owner: acc[r][m] += sum_i V[i, lane + 32 m] rhs_r[i] over the 32 rows, m < 8.
+// Logical chunk c of column j sits at slot (c + j) mod NCH, and j mod NCH = lane mod NCH for
+// every m, so the NCH chunk offsets are per-lane constants.  Columns go two per lane while a
+// second one exists anywhere in the warp, then one.  acc is in the storage type and covers
+// at most kColFlush sub-tiles (wt_flush_cols).
 template <typename T, int NR>
 __device__ __forceinline__ void wt_cols(const T* buf, int ncol, const T* rhs0, const T* rhs1,
-                                        double (&acc)[NR][kColsPerLane]) {
+                                        T (&acc)[NR][kColsPerLane]) {
   constexpr int NCH = WT<T>::NCH, VEC = WT<T>::VEC;
   const int lane = threadIdx.x & 31;
   int coff[NCH];
@@ -758,37 +805,42 @@ __device__ __forceinline__ void wt_cols(const T* buf, int ncol, const T* rhs0, c
 #pragma unroll
   for (int m = 0; m < kColsPerLane; m += 2) {
     if (32 * m >= ncol) break;
-    const int j0 = lane + 32 * m, j1 = j0 + 32;
-    const bool h0 = j0 < ncol, h1 = j1 < ncol;
-    if (!h0) continue;
-    T s0[NR], s1[NR];
+    if (32 * (m + 1) < ncol)   // warp-uniform
+      wt_col_pair<T, NR, true>(buf, ncol, m, coff, rhs0, rhs1, acc);
+    else
+      wt_col_pair<T, NR, false>(buf, ncol, m, coff, rhs0, rhs1, acc);
+  }
+}
+
+// The column owners' running sums in the storage type cover at most kColFlush sub-tiles
+// (32 kColFlush products, FP32 in the mixed mode); wt_flush_cols then adds them into the
+// warp's FP64 sums in shared memory (comb[warp][r][j], zeroed by wt_zero_cols) and clears
+// them.  (FP64 adds are scarce on this GPU: one per column and right-hand side every
+// kColFlush sub-tiles instead of every sub-tile.)  In the FP64 mode the running sums are
+// already FP64 and are flushed once, after the warp's last sub-tile.
+constexpr int kColFlush = 4;
+template <int NR>
+__device__ __forceinline__ void wt_zero_cols(double* comb, int ncolC) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int q = lane; q < NR * ncolC; q += 32) comb[(size_t)warp * NR * ncolC + q] = 0.0;
+  __syncwarp();
+}
+template <typename T>
+__device__ __forceinline__ bool wt_flush_due(int it, int count) {
+  if (sizeof(T) == 8) return it + 1 == count;
+  return (it + 1) % kColFlush == 0 || it + 1 == count;
+}
+template <typename T, int NR>
+__device__ __forceinline__ void wt_flush_cols(T (&acc)[NR][kColsPerLane], double* comb, int ncolC) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int r = 0; r < NR; r++) s0[r] = s1[r] = T(0);
-    const T* col0 = buf + j0 * 32;
-    const T* col1 = buf + (h1 ? j1 : j0) * 32;
-#pragma unroll
-    for (int c = 0; c < NCH; c++) {
-      const Vec<T> v0 = *reinterpret_cast<const Vec<T>*>(col0 + coff[c]);
-      const Vec<T> v1 = *reinterpret_cast<const Vec<T>*>(col1 + coff[c]);
-      const Vec<T> b0 = *reinterpret_cast<const Vec<T>*>(rhs0 + c * VEC);
-#pragma unroll
-      for (int e = 0; e < VEC; e++) {
-        s0[0] = fma(v0.e[e], b0.e[e], s0[0]);
-        s1[0] = fma(v1.e[e], b0.e[e], s1[0]);
-      }
-      if (NR > 1) {
-        const Vec<T> b1 = *reinterpret_cast<const Vec<T>*>(rhs1 + c * VEC);
-#pragma unroll
-        for (int e = 0; e < VEC; e++) {
-          s0[NR - 1] = fma(v0.e[e], b1.e[e], s0[NR - 1]);
-          s1[NR - 1] = fma(v1.e[e], b1.e[e], s1[NR - 1]);
-        }
-      }
-    }
+  for (int m = 0; m < kColsPerLane; m++) {
+    if (32 * m >= ncolC) break;
+    const int j = lane + 32 * m;
 #pragma unroll
     for (int r = 0; r < NR; r++) {
-      acc[r][m] += (double)s0[r];
-      if (h1) acc[r][m + 1] += (double)s1[r];
+      if (j < ncolC) comb[((size_t)warp * NR + r) * ncolC + j] += (double)acc[r][m];
+      acc[r][m] = T(0);
     }
   }
 }
@@ -837,19 +889,11 @@ struct WtSmem {
   __device__ __forceinline__ T* scr(int warp, int q) const { return scratch + ((size_t)warp * 2 + q) * 32; }
 };
 
-// Sum the warps' column-owner accumulators and store this CTA's partials part[off_r + j].
+// Sum the warps' FP64 column sums (comb, after their last wt_flush_cols) and store this
+// CTA's partials part[off_r + j].
 template <int NR>
-__device__ __forceinline__ void wt_store_cols(double* comb, int ncolC, const double (&acc)[NR][kColsPerLane],
-                                              double* part, const int (&off)[NR]) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
-#pragma unroll
-  for (int m = 0; m < kColsPerLane; m++) {
-    const int j = lane + 32 * m;
-    if (j < ncolC) {
-#pragma unroll
-      for (int r = 0; r < NR; r++) comb[((size_t)warp * NR + r) * ncolC + j] = acc[r][m];
-    }
-  }
+__device__ __forceinline__ void wt_store_cols(double* comb, int ncolC, double* part, const int (&off)[NR]) {
+  const int W = blockDim.x >> 5;
   __syncthreads();
   for (int j = threadIdx.x; j < ncolC; j += blockDim.x) {
 #pragma unroll
@@ -962,21 +1006,24 @@ __global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_dots(BatchStep<T>
   WtSmem<T> sm(dsm_raw, blockDim.x >> 5, cfg.nbuf, nc, 1, nc, 1);
   const ColSrc<T> src{(const T*)p.D.V, p.D.ld, na, (const T*)p.Bd, p.ldBd};
   const int64_t dim = p.D.dim;
-  double acc[1][kColsPerLane];
+  T acc[1][kColsPerLane];
 #pragma unroll
-  for (int m = 0; m < kColsPerLane; m++) acc[0][m] = 0.0;
+  for (int m = 0; m < kColsPerLane; m++) acc[0][m] = T(0);
   const WarpWalk ww(dim, cc);
+  const int cnt = ww.count();
   const bool xal = ((uintptr_t)p.x & 15u) == 0;   // per-trial offsets may break alignment
-  wt_pipeline(ww.count(), cfg.nbuf,
+  wt_zero_cols<1>(sm.comb, nc);
+  wt_pipeline(cnt, cfg.nbuf,
       [&](int it, int b) { wt_load_cols(sm.stage(warp, b), src, nc, ww.sub(it) * 32); },
       [&]() {},
       [&](int it, int b) { wt_load_vec(sm.srow(sm.stage(warp, b), 0), p.x, ww.sub(it) * 32, dim, xal); },
       [&](int it, int b) {
         T* st = sm.stage(warp, b);
         wt_cols<T, 1>(st, nc, sm.srow(st, 0), nullptr, acc);
+        if (wt_flush_due<T>(it, cnt)) wt_flush_cols<T, 1>(acc, sm.comb, nc);
       });
   const int off[1] = {0};
-  wt_store_cols<1>(sm.comb, nc, acc, p.ws.part + (int64_t)cc.local * nc, off);
+  wt_store_cols<1>(sm.comb, nc, p.ws.part + (int64_t)cc.local * nc, off);
   if (!reduce_partials(p.ws, 0, nc, cc.local, cc.ncta, p.ws.z)) return;
   __shared__ double zs[kTmaxLimit];
   for (int i = threadIdx.x; i < na; i += blockDim.x) zs[i] = p.ws.z[i];
@@ -1002,16 +1049,18 @@ __global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_update(BatchStep<
   T* col = (T*)p.D.V + (int64_t)k * p.D.ld;
   T* gb = (T*)p.D.gbuf;
   const T dconst = (T)p.D.dpre[k];
-  double acc[2][kColsPerLane];
+  T acc[2][kColsPerLane];
 #pragma unroll
-  for (int m = 0; m < kColsPerLane; m++) acc[0][m] = acc[1][m] = 0.0;
+  for (int m = 0; m < kColsPerLane; m++) acc[0][m] = acc[1][m] = T(0);
   T ex[3] = {T(0), T(0), T(0)};   // p . g_next, ||p[k+1:]||^2, ||g_next[k+2:]||^2
   T* pv = sm.scr(warp, 0);
   T* gv = sm.scr(warp, 1);
   PairDraws<T> draws;
   const WarpWalk ww(dim, cc);
+  const int cnt = ww.count();
   const bool xal = ((uintptr_t)p.x & 15u) == 0;   // per-trial offsets may break alignment
-  wt_pipeline(ww.count(), cfg.nbuf,
+  wt_zero_cols<2>(sm.comb, k);
+  wt_pipeline(cnt, cfg.nbuf,
       [&](int it, int b) {
         T* st = sm.stage(warp, b);
         const int64_t r0 = ww.sub(it) * 32;
@@ -1025,7 +1074,7 @@ __global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_update(BatchStep<
       [&](int it, int b) {
         T* st = sm.stage(warp, b);
         const int64_t r = ww.sub(it) * 32 + lane;
-        const bool has_next = it + 1 < ww.count();
+        const bool has_next = it + 1 < cnt;
         const T g = draws.next(p.key_next, it, ww.sub(it) * 32, has_next ? ww.sub(it + 1) * 32 : 0, has_next,
                                (int64_t)k + 1, dim, p.sigma);
         T out[1];
@@ -1048,11 +1097,12 @@ __global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_update(BatchStep<
         gv[lane] = g;
         __syncwarp();
         wt_cols<T, 2>(st, k, pv, gv, acc);
+        if (wt_flush_due<T>(it, cnt)) wt_flush_cols<T, 2>(acc, sm.comb, k);
       });
   const int P = 2 * k + 3;
   double* part = p.ws.part + (int64_t)cc.local * P;
   const int off[2] = {k + 3, 0};   // p-dots after the three extras, draw dots first
-  wt_store_cols<2>(sm.comb, k, acc, part, off);
+  wt_store_cols<2>(sm.comb, k, part, off);
   block_sum_to<3>(ex, red, part + k, 3);
   double* rr = p.ws.scr(3);
   if (!reduce_partials(p.ws, 1, P, cc.local, cc.ncta, rr)) return;
@@ -1093,15 +1143,17 @@ __global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_out_haar(BatchSte
   const T* gnext = (const T*)p.D.gbuf;
   T coef = T(0), alpha = T(0), usg = T(0), dconst = T(0);
   bool flag = false;
-  double acc[1][kColsPerLane];
+  T acc[1][kColsPerLane];
 #pragma unroll
-  for (int m = 0; m < kColsPerLane; m++) acc[0][m] = 0.0;
+  for (int m = 0; m < kColsPerLane; m++) acc[0][m] = T(0);
   T ex[1] = {T(0)};   // new column . g_{t+1}, or (FUSE) new column . x_{t+1}
   T* xv = sm.scr(warp, 0);
   const bool need_prev = FUSE && p.dyn != 1;
   const WarpWalk ww(dim, cc);
+  const int cnt = ww.count();
   const int64_t ld = p.N.ld;
-  wt_pipeline(ww.count(), cfg.nbuf,
+  wt_zero_cols<1>(sm.comb, k);
+  wt_pipeline(cnt, cfg.nbuf,
       [&](int it, int b) {
         T* st = sm.stage(warp, b);
         const int64_t r0 = ww.sub(it) * 32;
@@ -1154,12 +1206,13 @@ __global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_out_haar(BatchSte
           gcur[r] = gn;
           wt_cols<T, 1>(st, k, sm.srow(st, 1), nullptr, acc);
         }
+        if (wt_flush_due<T>(it, cnt)) wt_flush_cols<T, 1>(acc, sm.comb, k);
       });
   // partial sums: [0, k) V_N . r, [k] new column . r, r = g_{t+1} or (FUSE) x_{t+1}
   const int P = k + 1;
   double* part = p.ws.part + (int64_t)cc.local * P;
   const int off[1] = {0};
-  wt_store_cols<1>(sm.comb, k, acc, part, off);
+  wt_store_cols<1>(sm.comb, k, part, off);
   block_sum_to<1>(ex, red, part + k, 1);
   double* rr = p.ws.scr(3);
   if (!reduce_partials(p.ws, 2, P, cc.local, cc.ncta, rr)) return;
@@ -1205,17 +1258,19 @@ __global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_out_gin(BatchStep
   T* gcur = (T*)p.N.gbuf;
   const double* h = p.ws.z + kD;
   T alpha = T(0), dconst = T(0);
-  double acc[1][kColsPerLane];
+  T acc[1][kColsPerLane];
 #pragma unroll
-  for (int m = 0; m < kColsPerLane; m++) acc[0][m] = 0.0;
+  for (int m = 0; m < kColsPerLane; m++) acc[0][m] = T(0);
   T ex[2] = {T(0), T(0)};   // (FUSE) u . x_{t+1}; (AMP) ||z||^2 or ||x||_0 of this CTA's rows
   T* rv = sm.scr(warp, 0);
   const bool need_prev = FUSE && !amp && p.dyn != 1;
   T amp_s = T(0);   // (AMP) threshold (mode 2) or Onsager factor (mode 3) of this trial
   PairDraws<T> draws;
   const WarpWalk ww(dim, cc);
+  const int cnt = ww.count();
   const int64_t ld = p.N.ld;
-  wt_pipeline(ww.count(), cfg.nbuf,
+  wt_zero_cols<1>(sm.comb, ncc);
+  wt_pipeline(cnt, cfg.nbuf,
       [&](int it, int b) {
         T* st = sm.stage(warp, b);
         const int64_t r0 = ww.sub(it) * 32;
@@ -1287,7 +1342,7 @@ __global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_out_gin(BatchStep
           rv[lane] = xn;
           ex[0] = fma(u, xn, ex[0]);
         } else {
-          const bool has_next = it + 1 < ww.count();
+          const bool has_next = it + 1 < cnt;
           const T gn = draws.next(p.key_next, it, ww.sub(it) * 32, has_next ? ww.sub(it + 1) * 32 : 0, has_next,
                                   (int64_t)kN, dim, p.sigma);
           gcur[r] = gn;
@@ -1296,13 +1351,14 @@ __global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_out_gin(BatchStep
         __syncwarp();
         wt_cols<T, 1>(st, ncc, rv, nullptr, acc);
         __syncwarp();
+        if (wt_flush_due<T>(it, cnt)) wt_flush_cols<T, 1>(acc, sm.comb, ncc);
       });
   if (!FUSE && kN == 0) return;   // no dots to form
   // partial sums: [0, ncc) columns . r (r = g_{t+1}, or (FUSE) x_{t+1}), (FUSE) [nc] u . x_{t+1}
   const int P = FUSE ? nc + 1 + (amp ? 1 : 0) : kN;
   double* part = p.ws.part + (int64_t)cc.local * P;
   const int off[1] = {0};
-  wt_store_cols<1>(sm.comb, ncc, acc, part, off);
+  wt_store_cols<1>(sm.comb, ncc, part, off);
   if (FUSE) block_sum_to<2>(ex, red, part + nc, amp ? 2 : 1);
   double* rr = p.ws.scr(3);
   if (!reduce_partials(p.ws, 2, P, cc.local, cc.ncta, rr)) return;

@@ -583,9 +583,11 @@ __device__ void fin_update(const StepPlan<T>& p, const double* r, double* scr, i
 // On it two access patterns run without bank conflicts:
 //   row owner:    lane i computes out[i] = sum_j V[i, j] coef[j]   (4-byte reads, one row
 //                 per lane, coefficients read 16 bytes at a time);
-//   column owner: lane l owns columns l, l + 32, ... and adds sum_i V[i, j] rhs[i] (16-byte
-//                 reads of its column's rotated chunks, the rhs chunk is a broadcast) to
-//                 FP64 accumulators that persist across sub-tiles.
+//   column owner: lane l owns columns l, l + 32, ... (or, for up to 16 columns, a group of
+//                 lanes shares a column) and adds sum_i V[i, j] rhs[i] (16-byte reads of its
+//                 column's rotated chunks, the rhs chunk is a broadcast) to running sums in
+//                 the storage type, which go into per-warp FP64 sums every kColFlush
+//                 sub-tiles.
 // At the end the warps of a CTA add their column sums in shared memory and the CTA joins
 // the two-level last-block reduction.
 
@@ -789,15 +791,56 @@ __device__ __forceinline__ void wt_col_pair(const T* buf, int ncol, int m, const
   }
 }
 
+// Few columns (ncol <= 16): Q = 32 / C lanes per column (C = 4, 8 or 16 column slots),
+// lane = j Q + q.  Lane (j, q) takes NCH / Q chunks of column j, chunk q D + (i mod D) +
+// 8 (i div D) at step i (D = 8 / Q), so that the 8 lanes of every quarter warp read 8
+// distinct 16-byte bank groups.  Its running sums stay in acc[r][0]; wt_flush_cols adds the
+// Q lanes of a column.
+__device__ __forceinline__ int wt_col_slots(int ncol) {
+  return ncol <= 4 ? 4 : (ncol <= 8 ? 8 : (ncol <= 16 ? 16 : 0));
+}
+template <typename T, int NR, int Q>
+__device__ __forceinline__ void wt_cols_grouped(const T* buf, int ncol, const T* rhs0, const T* rhs1,
+                                                T (&acc)[NR][kColsPerLane]) {
+  constexpr int NCH = WT<T>::NCH, VEC = WT<T>::VEC, S = NCH / Q, D = 8 / Q;
+  const int lane = threadIdx.x & 31, j = lane / Q, q = lane % Q;
+  if (j >= ncol) return;
+  const T* col = buf + j * 32;
+  T s[NR];
+#pragma unroll
+  for (int r = 0; r < NR; r++) s[r] = T(0);
+#pragma unroll
+  for (int i = 0; i < S; i++) {
+    const int c = q * D + (i % D) + 8 * (i / D);
+    const Vec<T> v = *reinterpret_cast<const Vec<T>*>(col + ((c + j) & (NCH - 1)) * VEC);
+    const Vec<T> b0 = *reinterpret_cast<const Vec<T>*>(rhs0 + c * VEC);
+#pragma unroll
+    for (int e = 0; e < VEC; e++) s[0] = fma(v.e[e], b0.e[e], s[0]);
+    if (NR > 1) {
+      const Vec<T> b1 = *reinterpret_cast<const Vec<T>*>(rhs1 + c * VEC);
+#pragma unroll
+      for (int e = 0; e < VEC; e++) s[NR - 1] = fma(v.e[e], b1.e[e], s[NR - 1]);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < NR; r++) acc[r][0] += s[r];
+}
+
 // Column owner: acc[r][m] += sum_i V[i, lane + 32 m] rhs_r[i] over the 32 rows, m < 8.
 // Logical chunk c of column j sits at slot (c + j) mod NCH, and j mod NCH = lane mod NCH for
 // every m, so the NCH chunk offsets are per-lane constants.  Columns go two per lane while a
-// second one exists anywhere in the warp, then one.  acc is in the storage type and covers
-// at most kColFlush sub-tiles (wt_flush_cols).
+// second one exists anywhere in the warp, then one; up to 16 columns use wt_cols_grouped.
+// acc is in the storage type and covers at most kColFlush sub-tiles (wt_flush_cols).
 template <typename T, int NR>
 __device__ __forceinline__ void wt_cols(const T* buf, int ncol, const T* rhs0, const T* rhs1,
                                         T (&acc)[NR][kColsPerLane]) {
   constexpr int NCH = WT<T>::NCH, VEC = WT<T>::VEC;
+  switch (wt_col_slots(ncol)) {   // uniform over the launch
+    case 4: wt_cols_grouped<T, NR, 8>(buf, ncol, rhs0, rhs1, acc); return;
+    case 8: wt_cols_grouped<T, NR, 4>(buf, ncol, rhs0, rhs1, acc); return;
+    case 16: wt_cols_grouped<T, NR, 2>(buf, ncol, rhs0, rhs1, acc); return;
+    default: break;
+  }
   const int lane = threadIdx.x & 31;
   int coff[NCH];
 #pragma unroll
@@ -833,6 +876,18 @@ __device__ __forceinline__ bool wt_flush_due(int it, int count) {
 template <typename T, int NR>
 __device__ __forceinline__ void wt_flush_cols(T (&acc)[NR][kColsPerLane], double* comb, int ncolC) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int C = wt_col_slots(ncolC);
+  if (C) {   // wt_cols_grouped: add the Q = 32 / C lanes of each column (fixed order)
+    const int Q = 32 / C, j = lane / Q;
+#pragma unroll
+    for (int r = 0; r < NR; r++) {
+      T v = acc[r][0];
+      for (int o = Q >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane % Q == 0 && j < ncolC) comb[((size_t)warp * NR + r) * ncolC + j] += (double)v;
+      acc[r][0] = T(0);
+    }
+    return;
+  }
 #pragma unroll
   for (int m = 0; m < kColsPerLane; m++) {
     if (32 * m >= ncolC) break;

@@ -103,11 +103,9 @@ __global__ void __launch_bounds__(kAT) k_colpass(const T* __restrict__ A, int64_
 
 // out_v[j] = scale_v * sum over the nblk row chunks of the partials: one warp per column, the
 // lanes over the chunks, then a shuffle reduction (fixed order: deterministic).
-__global__ void __launch_bounds__(kAT) k_colreduce(const double* __restrict__ part, int nblk, int K,
-                                                   double s1, double* out1, double s2, double* out2) {
+__device__ __forceinline__ void colreduce_col(const double* __restrict__ part, int nblk, int K, int j,
+                                              double s1, double* out1, double s2, double* out2) {
   const int lane = threadIdx.x & 31;
-  const int j = blockIdx.x * (kAT / 32) + (threadIdx.x >> 5);
-  if (j >= K) return;
   double a = 0.0, b = 0.0;
   for (int q = lane; q < nblk; q += 32) {
     a += part[((int64_t)q * K + j) * 2];
@@ -119,6 +117,11 @@ __global__ void __launch_bounds__(kAT) k_colreduce(const double* __restrict__ pa
     out1[j] = s1 * a;
     if (out2) out2[j] = s2 * b;
   }
+}
+__global__ void __launch_bounds__(kAT) k_colreduce(const double* __restrict__ part, int nblk, int K,
+                                                   double s1, double* out1, double s2, double* out2) {
+  const int j = blockIdx.x * (kAT / 32) + (threadIdx.x >> 5);
+  if (j < K) colreduce_col(part, nblk, K, j, s1, out1, s2, out2);
 }
 
 // out[r] (+)= sgn(r) (s_in in[r] + c_scale sum_{j<K} A[r, j] c[j]), sgn(r) = dpre[min(r+1, Kd)]
@@ -221,6 +224,67 @@ __global__ void __launch_bounds__(kAT) k_rank4(float* Ab, int64_t ld, int K, int
   }
 }
 
+// Up to five rank-one terms in one pass: Ab[:, j] += sum_q v_q (s_q c_q[j]) for j < min(K, K_q).
+struct RankTerms {
+  const void* v[5];
+  const double* c[5];
+  double s[5];
+  int K[5];
+  int n;
+};
+template <typename T>
+__global__ void __launch_bounds__(kAT) k_rankN(T* Ab, int64_t ld, int K, int64_t dim, RankTerms t) {
+  __shared__ T cs[5][8];
+  const int j0 = blockIdx.y * 8;
+  if (threadIdx.x < 40) {
+    const int q = threadIdx.x >> 3, jj = threadIdx.x & 7, j = j0 + jj;
+    cs[q][jj] = (q < t.n && j < K && j < t.K[q]) ? (T)(t.s[q] * t.c[q][j]) : T(0);
+  }
+  __syncthreads();
+  const int jn = min(K, j0 + 8) - j0;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < dim; r += (int64_t)gridDim.x * blockDim.x) {
+    T vr[5];
+#pragma unroll
+    for (int q = 0; q < 5; q++) vr[q] = (q < t.n) ? ((const T*)t.v[q])[r] : T(0);
+    for (int jj = 0; jj < jn; jj++) {
+      T* col = Ab + (int64_t)(j0 + jj) * ld;
+      T v = col[r];
+#pragma unroll
+      for (int q = 0; q < 5; q++) v = fma(vr[q], cs[q][jj], v);
+      col[r] = v;
+    }
+  }
+}
+__global__ void __launch_bounds__(kAT) k_rankN4(float* Ab, int64_t ld, int K, int64_t dim4, RankTerms t) {
+  __shared__ float cs[5][8];
+  const int j0 = blockIdx.y * 8;
+  if (threadIdx.x < 40) {
+    const int q = threadIdx.x >> 3, jj = threadIdx.x & 7, j = j0 + jj;
+    cs[q][jj] = (q < t.n && j < K && j < t.K[q]) ? (float)(t.s[q] * t.c[q][j]) : 0.f;
+  }
+  __syncthreads();
+  const int jn = min(K, j0 + 8) - j0;
+  for (int64_t q4 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q4 < dim4; q4 += (int64_t)gridDim.x * blockDim.x) {
+    float4 vr[5];
+#pragma unroll
+    for (int q = 0; q < 5; q++)
+      vr[q] = (q < t.n) ? reinterpret_cast<const float4*>(t.v[q])[q4] : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int jj = 0; jj < jn; jj++) {
+      float4* col = reinterpret_cast<float4*>(Ab + (int64_t)(j0 + jj) * ld);
+      float4 v = col[q4];
+#pragma unroll
+      for (int q = 0; q < 5; q++) {
+        const float cq = cs[q][jj];
+        v.x = fmaf(vr[q].x, cq, v.x);
+        v.y = fmaf(vr[q].y, cq, v.y);
+        v.z = fmaf(vr[q].z, cq, v.z);
+        v.w = fmaf(vr[q].w, cq, v.w);
+      }
+      col[q4] = v;
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kAT) k_rowpass4(float* out, const float* in, double s_in, const float* __restrict__ A,
                                                   int64_t ld, int K, const double* __restrict__ c, double c_scale,
                                                   int64_t dim4, int accumulate) {
@@ -285,8 +349,8 @@ __global__ void __launch_bounds__(kAT) k_colpass4(const float* __restrict__ A, i
 // tau = 2 / u^T u gives ubar += -tau^2 taubar u.  Writes coef[0..k) = abar, coef[k] =
 // -tau^2 taubar (the coefficients of ubar += V[:, 0..k] coef).  An identity column (tau = 0)
 // passes nothing.
-__global__ void __launch_bounds__(kSmallT) k_rec_col(const double* __restrict__ S, double* Sb, int Tm, int k,
-                                                     const double* __restrict__ a, double* coef) {
+__device__ void rec_col_dev(const double* __restrict__ S, double* Sb, int Tm, int k, const double* __restrict__ a,
+                            double* coef) {
   __shared__ double cb[kTmaxLimit + 1];
   __shared__ double tb;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -311,12 +375,15 @@ __global__ void __launch_bounds__(kSmallT) k_rec_col(const double* __restrict__ 
     if (i <= j) Sb[i + (int64_t)j * Tm] += -tau * cb[i] * a[j];
   }
 }
+__global__ void __launch_bounds__(kSmallT) k_rec_col(const double* __restrict__ S, double* Sb, int Tm, int k,
+                                                     const double* __restrict__ a, double* coef) {
+  rec_col_dev(S, Sb, Tm, k, a, coef);
+}
 
 // out = scale S v (trans = 0) or scale S^T v (trans = 1), leading K x K block of the upper
 // triangular S (column-major, leading dim Tm): one warp per output, lanes over the sum.
-__global__ void __launch_bounds__(kSmallT) k_tri(const double* __restrict__ S, int Tm, int K,
-                                                 const double* __restrict__ v, double scale, int trans,
-                                                 double* out) {
+__device__ void tri_dev(const double* __restrict__ S, int Tm, int K, const double* __restrict__ v, double scale,
+                        int trans, double* out) {
   const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int i = threadIdx.x >> 5; i < K; i += nw) {
     double s = 0.0;
@@ -329,14 +396,23 @@ __global__ void __launch_bounds__(kSmallT) k_tri(const double* __restrict__ S, i
     if (lane == 0) out[i] = scale * s;
   }
 }
+__global__ void __launch_bounds__(kSmallT) k_tri(const double* __restrict__ S, int Tm, int K,
+                                                 const double* __restrict__ v, double scale, int trans,
+                                                 double* out) {
+  tri_dev(S, Tm, K, v, scale, trans, out);
+}
 
 // Sb[i, j] += a[i] b[j] on the upper triangle i <= j < K (S has no free entries below).
-__global__ void __launch_bounds__(kAT) k_outer_upper(double* Sb, int Tm, int K, const double* __restrict__ a,
-                                                     const double* __restrict__ b) {
+__device__ __forceinline__ void outer_upper_dev(double* Sb, int Tm, int K, const double* __restrict__ a,
+                                                const double* __restrict__ b) {
   for (int idx = threadIdx.x; idx < K * K; idx += blockDim.x) {
     const int i = idx % K, j = idx / K;
     if (i <= j) Sb[i + (int64_t)j * Tm] += a[i] * b[j];
   }
+}
+__global__ void __launch_bounds__(kAT) k_outer_upper(double* Sb, int Tm, int K, const double* __restrict__ a,
+                                                     const double* __restrict__ b) {
+  outer_upper_dev(Sb, Tm, K, a, b);
 }
 
 // c = [p_head[0:k]; alpha] from the step's record
@@ -350,11 +426,10 @@ __global__ void k_head_alpha(const double* __restrict__ phead, int k, const doub
 // first nc rows, and adds Sbar += bb a^T and Vbar[:nc, :] += (Delta c) (S^T bb)^T.  One warp
 // per output, lanes over the sums.
 template <typename T>
-__global__ void __launch_bounds__(kSmallT) k_out_small(const T* __restrict__ V, int64_t ld, int Ke, int nc,
-                                                       const double* __restrict__ S, int Tm,
-                                                       const double* __restrict__ dpre, const double* __restrict__ c,
-                                                       const double* __restrict__ bb, const T* __restrict__ ybd,
-                                                       double* Sb, T* Vb, double* b_out, double* cbar) {
+__device__ void out_small_dev(const T* __restrict__ V, int64_t ld, int Ke, int nc, const double* __restrict__ S,
+                              int Tm, const double* __restrict__ dpre, const double* __restrict__ c,
+                              const double* __restrict__ bb, const T* __restrict__ ybd, double* Sb, T* Vb,
+                              double* b_out, double* cbar) {
   __shared__ double cp[kTmaxLimit + 1], a[kTmaxLimit + 1], ab[kTmaxLimit + 1];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int i = threadIdx.x; i < nc; i += blockDim.x) cp[i] = dpre[i + 1] * c[i];
@@ -393,6 +468,66 @@ __global__ void __launch_bounds__(kSmallT) k_out_small(const T* __restrict__ V, 
     if (lane == 0) cbar[i] = dpre[i + 1] * ((double)ybd[i] + s);
   }
 }
+template <typename T>
+__global__ void __launch_bounds__(kSmallT) k_out_small(const T* __restrict__ V, int64_t ld, int Ke, int nc,
+                                                       const double* __restrict__ S, int Tm,
+                                                       const double* __restrict__ dpre, const double* __restrict__ c,
+                                                       const double* __restrict__ bb, const T* __restrict__ ybd,
+                                                       double* Sb, T* Vb, double* b_out, double* cbar) {
+  out_small_dev<T>(V, ld, Ke, nc, S, Tm, dpre, c, bb, ybd, Sb, Vb, b_out, cbar);
+}
+
+// Haar output side in one CTA: bb = -V^T ybar from the column pass's partials, c = [p_head;
+// alpha], the output-product adjoint (k_out_small) and the S recurrence of the step's random
+// column (k_rec_col, after the Sbar update it depends on).
+template <typename T>
+__global__ void __launch_bounds__(kSmallT) k_out_haar_adj(const double* __restrict__ part, int nblk,
+                                                          const T* __restrict__ V, int64_t ld, int Ke,
+                                                          const double* __restrict__ S, int Tm,
+                                                          const double* __restrict__ dpre,
+                                                          const double* __restrict__ phead,
+                                                          const double* __restrict__ rs, double* cv, double* bb,
+                                                          const T* __restrict__ ybd, double* Sb, T* Vb, double* bo,
+                                                          double* cbar, const double* __restrict__ rag,
+                                                          double* au) {
+  const int wid = threadIdx.x >> 5, nw = blockDim.x >> 5, k = Ke - 1;
+  for (int j = wid; j < Ke; j += nw) colreduce_col(part, nblk, Ke, j, -1.0, bb, 0.0, nullptr);
+  for (int i = threadIdx.x; i <= k; i += blockDim.x) cv[i] = (i < k) ? phead[i] : rs[1];
+  __syncthreads();
+  out_small_dev<T>(V, ld, Ke, Ke, S, Tm, dpre, cv, bb, ybd, Sb, Vb, bo, cbar);
+  __syncthreads();
+  rec_col_dev(S, Sb, Tm, k, rag, au);
+}
+
+// The step's record (adj_record_after) in one launch: z (nz), w, p_head, V_D^T u (kD each),
+// p's pivot entry and alpha, and (Haar) V_N^T u_g (nug).
+__global__ void __launch_bounds__(kAT) k_adj_record(double* r, int64_t L, const double* __restrict__ z, int nz,
+                                                    const double* __restrict__ w, const double* __restrict__ ph,
+                                                    int kD, const double* __restrict__ scal,
+                                                    const double* __restrict__ ua, const double* __restrict__ ug,
+                                                    int nug) {
+  for (int i = threadIdx.x; i < nz; i += blockDim.x) r[i] = z[i];
+  for (int i = threadIdx.x; i < kD; i += blockDim.x) {
+    r[L + i] = w[i];
+    r[2 * L + i] = ph[i];
+    r[3 * L + 8 + i] = ua[i];
+  }
+  if (threadIdx.x < 2) r[3 * L + threadIdx.x] = scal[threadIdx.x];
+  for (int i = threadIdx.x; i < nug; i += blockDim.x) r[4 * L + 8 + i] = ug[i];
+}
+
+// Data side after the column pass of qbar in one CTA: wbar = -V^T qbar from the partials,
+// zbar = S wbar, Sbar += z wbar^T.
+__global__ void __launch_bounds__(kSmallT) k_data_small(const double* __restrict__ part, int nblk, int K,
+                                                        const double* __restrict__ S, int Tm,
+                                                        const double* __restrict__ z, double* wb, double* zb,
+                                                        double* Sb) {
+  const int wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = wid; j < K; j += nw) colreduce_col(part, nblk, K, j, -1.0, wb, 0.0, nullptr);
+  __syncthreads();
+  tri_dev(S, Tm, K, wb, 1.0, 0, zb);
+  outer_upper_dev(Sb, Tm, K, z, wb);
+}
 
 // qbar = Delta_D pbar with pbar[r] = cb[r] (r < kD) and, on the tail, the adjoint of the new
 // column u = p[kD:] + s alpha e_kD and of alpha: (cb[kD] + s ub[kD]) p[r] / alpha + ub[r].  The
@@ -403,9 +538,14 @@ __global__ void __launch_bounds__(kAT) k_pbar(T* __restrict__ qbar, const T* __r
                                               const T* __restrict__ ub, const double* __restrict__ cb,
                                               const double* __restrict__ rs, int kD,
                                               const double* __restrict__ dpre, int64_t dim) {
+  __shared__ T coef_s;
   const double ppiv = rs[0], alpha = rs[1];
-  const double s = (ppiv >= 0.0) ? 1.0 : -1.0;
-  const T coef = (alpha > 0.0) ? (T)((cb[kD] + s * (double)ub[kD]) / alpha) : T(0);
+  if (threadIdx.x == 0) {   // one FP64 division per CTA
+    const double s = (ppiv >= 0.0) ? 1.0 : -1.0;
+    coef_s = (alpha > 0.0) ? (T)((cb[kD] + s * (double)ub[kD]) / alpha) : T(0);
+  }
+  __syncthreads();
+  const T coef = coef_s;
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < dim; r += (int64_t)gridDim.x * blockDim.x) {
     T pb;
     if (r < kD) pb = (T)cb[r];
@@ -443,6 +583,8 @@ unsigned rows_grid(const hd_state* st, int64_t dim) {
   return (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)st->nsm * 8));
 }
 
+// Column pass o_v = s_v A^T v_v; with o1 null only the partial sums are formed (a following
+// single-CTA kernel reduces them).
 template <typename T>
 void colpass(const Ctx& c, const T* A, int64_t ld, int K, int64_t dim, const T* v1, double s1, double* o1,
              const T* v2 = nullptr, double s2 = 0.0, double* o2 = nullptr) {
@@ -453,7 +595,7 @@ void colpass(const Ctx& c, const T* A, int64_t ld, int K, int64_t dim, const T* 
                                                             (const float*)v2, A_.part);
   else
     k_colpass<T><<<dim3(A_.nblk, (K + 7) / 8), kAT, 0, c.s>>>(A, ld, K, dim, v1, v2, A_.part);
-  k_colreduce<<<(K + kAT / 32 - 1) / (kAT / 32), kAT, 0, c.s>>>(A_.part, A_.nblk, K, s1, o1, s2, o2);
+  if (o1) k_colreduce<<<(K + kAT / 32 - 1) / (kAT / 32), kAT, 0, c.s>>>(A_.part, A_.nblk, K, s1, o1, s2, o2);
 }
 
 template <typename T>
@@ -467,6 +609,20 @@ void rowpass(const Ctx& c, T* out, const T* in, double s_in, const T* A, int64_t
     return;
   }
   k_rowpass<T><<<g, kAT, 0, c.s>>>(out, in, s_in, A, ld, K, coef, cscale, dim, dpre, Kd, acc, rnorm, npart);
+}
+
+template <typename T>
+void rankN(const Ctx& c, T* Ab, int64_t ld, int K, int64_t dim, const RankTerms& t) {
+  if (K <= 0 || t.n <= 0) return;
+  bool al = sizeof(T) == 4 && dim % 4 == 0 && al16(Ab);
+  for (int q = 0; q < t.n; q++) al = al && al16(t.v[q]);
+  if (al) {
+    dim3 g4(rows_grid(c.st, dim / 4), (unsigned)((K + 7) / 8));
+    k_rankN4<<<g4, kAT, 0, c.s>>>((float*)Ab, ld, K, dim / 4, t);
+    return;
+  }
+  dim3 g(rows_grid(c.st, dim), (unsigned)((K + 7) / 8));
+  k_rankN<T><<<g, kAT, 0, c.s>>>(Ab, ld, K, dim, t);
 }
 
 template <typename T>
@@ -537,16 +693,42 @@ int adj_step(hd_state* st, const void* ybar, const void* x_in, void* xbar) {
   const T* ucol = Vd + (int64_t)kD * Sd.ld;
   const unsigned gp = rows_grid(st, nd);
 
+  // A data-side update held back by the previous call (the next-later step) joins this
+  // step's output-side update when that covers the same stack and columns; otherwise it is
+  // applied now, before anything here reads that stack's Vbar.
+  AdjState::Pending& pd = A.pend;
+  const bool join = haar && pd.on && pd.s == e && pd.K == kD + 1;
+  auto pending_terms = [&](RankTerms& rt) {
+    for (int q = 0; q < pd.n; q++) {
+      rt.v[rt.n] = pd.v[q];
+      rt.c[rt.n] = pd.c[q];
+      rt.s[rt.n] = pd.sc[q];
+      rt.K[rt.n] = pd.Kq[q];
+      rt.n++;
+    }
+    pd.on = 0;
+  };
+  if (pd.on && !join) {
+    RankTerms rt{};
+    const int s0 = pd.s, K0 = pd.K;
+    pending_terms(rt);
+    rankN<T>(c, (T*)A.Vbar[s0], td.st[s0].ld, K0, st->dims[s0][0], rt);
+  }
+
   // output product
   if (haar) {
     const int Ke = kD + 1;   // the other stack including this step's random reflector
-    colpass<T>(c, Ve, Se.ld, Ke, ne, ybd, -1.0, bb);
-    k_head_alpha<<<1, kAT, 0, c.s>>>(phead, kD, rs, cv);
-    k_out_small<T><<<1, kSmallT, 0, c.s>>>(Ve, Se.ld, Ke, kD + 1, Se.S, Tm, Se.dpre, cv, bb, ybd, A.Sbar[e], Vbe,
-                                      bo, cb);
-    // the random column of this step (L_t = H_t(g_t), column kD of V_N): its S recurrence
-    k_rec_col<<<1, kSmallT, 0, c.s>>>(Se.S, A.Sbar[e], Tm, kD, rag, au);
-    rank<T>(c, Vbe, Se.ld, Ke, ne, ybd, bo, -1.0, Ve + (int64_t)kD * Se.ld, au, 1.0, nullptr, nullptr, 0.0, 0);
+    // bb = -V_N^T ybar, the output-product adjoint, and the S recurrence of this step's random
+    // column (L_t = H_t(g_t), column kD of V_N)
+    colpass<T>(c, Ve, Se.ld, Ke, ne, ybd, -1.0, nullptr);
+    k_out_haar_adj<T><<<1, kSmallT, 0, c.s>>>(A.part, A.nblk, Ve, Se.ld, Ke, Se.S, Tm, Se.dpre, phead, rs, cv, bb,
+                                              ybd, A.Sbar[e], Vbe, bo, cb, rag, au);
+    RankTerms rt{};
+    rt.v[0] = ybd; rt.c[0] = bo; rt.s[0] = -1.0; rt.K[0] = Ke;
+    rt.v[1] = Ve + (int64_t)kD * Se.ld; rt.c[1] = au; rt.s[1] = 1.0; rt.K[1] = Ke;
+    rt.n = 2;
+    if (join) pending_terms(rt);
+    rankN<T>(c, Vbe, Se.ld, Ke, ne, rt);
   } else {
     if (kN > 0) {
       colpass<T>(c, Ve, Se.ld, kN, ne, ybd, -1.0, bb);
@@ -581,10 +763,9 @@ int adj_step(hd_state* st, const void* ybar, const void* x_in, void* xbar) {
   k_pbar<T><<<gp, kAT, 0, c.s>>>(qb, ucol, ub, cb, rs, kD, Sd.dpre, nd);
 
   // the data product p = Delta (I - V S^T V^T) x
-  colpass<T>(c, Vd, Sd.ld, kD, nd, qb, -1.0, wb);
-  if (kD > 0) {
-    k_tri<<<1, kSmallT, 0, c.s>>>(Sd.S, Tm, kD, wb, 1.0, 0, zb);
-    k_outer_upper<<<1, kAT, 0, c.s>>>(A.Sbar[d], Tm, kD, z, wb);   // Sbar += z wbar^T
+  if (kD > 0) {   // wbar = -V_D^T qbar, zbar = S wbar, Sbar += z wbar^T
+    colpass<T>(c, Vd, Sd.ld, kD, nd, qb, -1.0, nullptr);
+    k_data_small<<<1, kSmallT, 0, c.s>>>(A.part, A.nblk, kD, Sd.S, Tm, z, wb, zb, A.Sbar[d]);
   }
   rowpass<T>(c, xb, qb, 1.0, Vd, Sd.ld, kD, zb, 1.0, nd, nullptr, 0, 0);
   if (!haar && kN > 0) {
@@ -592,7 +773,20 @@ int adj_step(hd_state* st, const void* ybar, const void* x_in, void* xbar) {
     rowpass<T>(c, xb, nullptr, 0.0, Bd, td.ldb[d], kN, hb, 1.0, nd, nullptr, 0, 1);
     rank<T>(c, (T*)A.Bbar[d], td.ldb[d], kN, nd, xd, hb, 1.0);
   }
-  rank<T>(c, Vbd, Sd.ld, kD, nd, qb, w, -1.0, xd, zb, 1.0, ucol, E, 1.0, kD);   // + u abar^T
+  // Vbar_D += -qbar w^T + x zbar^T + u abar^T.  Haar with the recorded x_t and the next reverse
+  // step on the other product: held back for that step's output-side pass over this stack
+  // (qbar, w, x, zbar, u, abar stay in place until then).
+  if (haar && !x_in && t > 1 && A.flag[t - 2] != A.flag[t - 1] && kD > 0) {
+    pd.on = 1;
+    pd.s = d;
+    pd.K = kD;
+    pd.n = 3;
+    pd.v[0] = qb; pd.c[0] = w; pd.sc[0] = -1.0; pd.Kq[0] = kD;
+    pd.v[1] = xd; pd.c[1] = zb; pd.sc[1] = 1.0; pd.Kq[1] = kD;
+    pd.v[2] = ucol; pd.c[2] = E; pd.sc[2] = 1.0; pd.Kq[2] = kD;
+  } else {
+    rank<T>(c, Vbd, Sd.ld, kD, nd, qb, w, -1.0, xd, zb, 1.0, ucol, E, 1.0, kD);   // + u abar^T
+  }
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return cuda_fail(st, err);
   A.rev -= 1;
@@ -601,6 +795,7 @@ int adj_step(hd_state* st, const void* ybar, const void* x_in, void* xbar) {
 
 int adj_zero(hd_state* st) {
   AdjState& A = *st->adj;
+  A.pend.on = 0;
   const TrialDesc& td = st->hdesc[0];
   for (int s = 0; s < 2; s++) {
     if (cudaMemsetAsync(A.Vbar[s], 0, (size_t)td.st[s].ld * st->Tm * st->esz, st->stream) != cudaSuccess ||
@@ -637,20 +832,11 @@ int adj_record_after(hd_state* st, int kD, int kN) {
   AdjState& A = *st->adj;
   const Ws& ws = st->hdesc[0].ws;
   double* r = A.rec + (int64_t)(st->t) * A.rec_ld;   // st->t is still this step's index
-  const int64_t L = st->Sld;
-  cudaError_t e = cudaSuccess;
   const int nz = (st->ens == HD_GINIBRE) ? kD + kN : kD;   // Haar's K1 forms no basis dots
-  if (nz > 0) e = cudaMemcpyAsync(r, ws.z, (size_t)nz * 8, cudaMemcpyDeviceToDevice, st->stream);
-  if (e == cudaSuccess && kD > 0)
-    e = cudaMemcpyAsync(r + L, ws.w, (size_t)kD * 8, cudaMemcpyDeviceToDevice, st->stream);
-  if (e == cudaSuccess && kD > 0)
-    e = cudaMemcpyAsync(r + 2 * L, ws.phead, (size_t)kD * 8, cudaMemcpyDeviceToDevice, st->stream);
-  if (e == cudaSuccess)   // scal[kPpiv], scal[kAlpha]
-    e = cudaMemcpyAsync(r + 3 * L, ws.scal, 2 * 8, cudaMemcpyDeviceToDevice, st->stream);
-  if (e == cudaSuccess && kD > 0)   // V_D^T u of the new data-side column
-    e = cudaMemcpyAsync(r + 3 * L + 8, ws.scrb + ws.scr_stride * 1, (size_t)kD * 8, cudaMemcpyDeviceToDevice, st->stream);
-  if (e == cudaSuccess && st->ens == HD_HAAR && kN > 0)   // V_N^T u_g of the new random column
-    e = cudaMemcpyAsync(r + 4 * L + 8, ws.scrb + ws.scr_stride * 2, (size_t)kN * 8, cudaMemcpyDeviceToDevice, st->stream);
+  const int nug = (st->ens == HD_HAAR) ? kN : 0;            // V_N^T u_g of the new random column
+  k_adj_record<<<1, kAT, 0, st->stream>>>(r, st->Sld, ws.z, nz, ws.w, ws.phead, kD, ws.scal,
+                                          ws.scrb + ws.scr_stride * 1, ws.scrb + ws.scr_stride * 2, nug);
+  const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(st, e);
   return HD_OK;
 }

@@ -48,6 +48,19 @@ struct AdjState {
   // (k_D), then p's pivot entry and alpha, copied from the workspace after the step
   double* rec = nullptr;
   int64_t rec_ld = 0;
+  // A data-side update Vbar += sum_q v_q (s_q c_q)^T of one reverse step, held back so that
+  // the next reverse step adds it in the same pass over that stack as its own output-side
+  // update (Haar, Q and Q^T alternating: both cover the same columns).
+  struct Pending {
+    int on = 0;
+    int s = 0;                   // stack
+    int K = 0;                   // columns 0..K-1
+    int n = 0;                   // terms
+    const void* v[3] = {nullptr, nullptr, nullptr};
+    const double* c[3] = {nullptr, nullptr, nullptr};
+    double sc[3] = {0.0, 0.0, 0.0};
+    int Kq[3] = {0, 0, 0};       // columns each term covers
+  } pend;
 };
 
 }  // namespace hd

@@ -190,7 +190,7 @@ class ClockSampler:
 
 # DRAM bytes / algorithmic bytes of one k_update launch (k = 60, n = 10^6, FP32) from an
 # ncu --set full capture of the current kernel; reset to None when the kernel changes.
-UPDATE_TRAFFIC_RATIO = 249.39 / 252.0
+UPDATE_TRAFFIC_RATIO = 250.15 / 252.0
 
 
 def measured_peaks():
@@ -417,7 +417,7 @@ def run_ours(args):
                 "traffic": ((by / nl) * UPDATE_TRAFFIC_RATIO
                             if (nl and dom == "update" and UPDATE_TRAFFIC_RATIO) else None),
                 "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_update "
-                                  "launch at k = 60 (249.39 MB for 252.0 MB algorithmic), scaled to "
+                                  "launch at k = 60 (250.15 MB for 252.0 MB algorithmic), scaled to "
                                   "the average launch by algorithmic bytes",
                 "timing": "CUDA events on the launching stream around every sweep, recorded "
                           "in a second pass of the same trajectories (events inside the graph "

@@ -62,3 +62,23 @@ def test_argument_errors_need_no_gpu(libpath):
     assert L.hd_apply(None, None, 0, None) == hd.binding.HD_ERR_ARG
     assert L.hd_reset(None, 0) == hd.binding.HD_ERR_ARG
     L.hd_destroy(None)
+
+
+def test_tuning_entry_points_reject_null_state_without_gpu(libpath):
+    import paper_2101_07464_gb300 as hd
+    L = hd.lib()
+    words = (ctypes.c_int32 * hd.binding.HD_TUNE_WORDS)()
+    cnt = ctypes.c_int32()
+    ARG = hd.binding.HD_ERR_ARG
+    assert L.hd_autotune(None, None, None, None, 1) == ARG
+    assert L.hd_get_tuning(None, words, hd.binding.HD_TUNE_WORDS) == ARG
+    assert L.hd_set_tuning(None, words, hd.binding.HD_TUNE_WORDS) == ARG
+    assert L.hd_get_map_options(None, ctypes.byref(cnt), None) == ARG
+
+
+def test_tuning_word_count_matches_header():
+    """[version, split option] + (warps, stages) for 6 sweep kernels x 11 column ranges."""
+    import paper_2101_07464_gb300 as hd
+    txt = open(os.path.join(ROOT, "include", "hd.h")).read()
+    m = re.search(r"#define HD_TUNE_WORDS (\d+)", txt)
+    assert m and int(m.group(1)) == hd.binding.HD_TUNE_WORDS == 2 + 2 * 6 * 11

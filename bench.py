@@ -45,6 +45,8 @@ def parse(argv=None):
     ap.add_argument("--no-amp", action="store_true", help="skip the batched AMP measurement")
     ap.add_argument("--amp-trials", type=int, default=4096)
     ap.add_argument("--no-adjoint", action="store_true", help="skip the reverse-mode measurement")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the large configuration (Haar n = 2e7, T = 256, forward and reverse mode)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the built-in launch shapes (no hd_autotune before timing)")
     return ap.parse_args(argv)
@@ -348,6 +350,67 @@ def measure_adjoint(args, rank, world, dist):
                       "d<c, x_{T+1}>/d(x_1, theta)"}
 
 
+def measure_large(args, rank, world, dist):
+    """The large single-trial configuration: Haar(n), n = 2 * 10^7, T = 256 products, all Q,
+    x_{t+1} = normalize(tanh(y_t) + 0.1 x_t), FP32 stacks (2 x 20.5 GB).  Forward: one hd_run
+    graph per trajectory (built-in shapes), CUDA events, plus a second pass with events around
+    every sweep for the update sweep's algorithmic GB/s.  Reverse mode: d<x_{T+1}, x_1>/d(x_1,
+    a_1..a_T) (a_t the per-step mixing, 0.1) through autograd.trajectory with segments of 32
+    steps recomputed by hd_probe, wall clock around one whole synchronised call."""
+    import torch
+    import synth
+    import paper_2101_07464_gb300 as hd
+    from paper_2101_07464_gb300.autograd import trajectory
+    n, T, seg = 2 * 10 ** 7, 256, 32
+    free, _ = torch.cuda.mem_get_info()
+    if free < 120e9:
+        return {"skipped": "needs about 120 GB of free device memory, %.0f GB free" % (free / 1e9)}
+    flags = [False] * T
+    st = hd.HD("haar", n, n, T, args.seed, "f32", trial=rank)
+    x1 = torch.tensor(synth.x1(n, args.seed, trial=rank), dtype=torch.float32, device="cuda")
+    x1 = x1 / x1.norm()
+    out = torch.empty_like(x1)
+    spec = hd.make_run_spec(flags, "norm_tanh", 0.1, use_graph=True)
+    hd.hd_run(st.h, spec, x1, out)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    hd.hd_run(st.h, spec, x1, out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fw = max_over_ranks(e0.elapsed_time(e1) / 1e3, dist)
+    prof = profile_kernels(st, spec, x1, out, 1)
+    peak, _ = measured_peaks()
+    per = {k: (v[2] / (v[0] / 1e3) / 1e9 if v[0] else None) for k, v in prof.items()}
+
+    def f(t, y, x, xprev, a):
+        v = torch.tanh(y) + a[t - 1] * x
+        return v / torch.sqrt(torch.sum(v.double() * v.double())).to(v.dtype)
+
+    a = torch.full((T,), 0.1, dtype=torch.float32, device="cuda", requires_grad=True)
+    xg = x1.clone().requires_grad_(True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    xo = trajectory(st, xg, flags, f, (a,), checkpoint=seg)
+    L = torch.dot(xo, x1)
+    L.backward()
+    torch.cuda.synchronize()
+    fb = max_over_ranks(time.perf_counter() - t0, dist)
+    st.close()
+    units = float(n) * T * T
+    return {"config": "Haar n=2e7, T=256, all Q, x_{t+1} = normalize(tanh(y_t) + 0.1 x_t), FP32 stacks",
+            "forward": {"ms": fw * 1e3, "value": job_throughput(units, world, fw), "unit": UNIT,
+                        "update_GBps": per["update"], "update_frac": (per["update"] / peak) if per["update"] else None,
+                        "output_GBps": per["output"], "dots_GBps": per["dots"],
+                        "launch_shapes": "built-in", "timing": "CUDA events, one graph replay after one warm-up"},
+            "adjoint": {"ms_forward_backward": fb * 1e3, "value": job_throughput(units, world, fb), "unit": UNIT,
+                        "checkpoint_segment": seg, "loss": "<x_{T+1}, x_1>",
+                        "timing": "wall clock around one synchronised forward + backward"}}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -443,6 +506,12 @@ def run_ours(args):
     adj = None
     if not args.no_adjoint:
         adj = measure_adjoint(args, rank, world, dist)
+    large = None
+    if not args.no_large:
+        try:
+            large = measure_large(args, rank, world, dist)
+        except Exception as exc:   # reported in the line, the headline stands
+            large = {"error": "%s: %s" % (type(exc).__name__, exc)}
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -467,7 +536,7 @@ def run_ours(args):
                 "roofline": roofline,
                 "step_credited_GBps": step_gbps,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk, "fp64": fp64, "batched_amp": amp, "adjoint": adj}
+                "clocks": clk, "fp64": fp64, "batched_amp": amp, "adjoint": adj, "large": large}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -1,0 +1,154 @@
+"""The largest reflector counts the library accepts (T_max = 256): every column-pass form
+(lane groups, one and two columns per lane, up to four pairs of 32-column blocks), the
+finalisations' staging fallbacks and the four-warp shapes the update sweep takes at large k,
+checked against the oracle.
+
+Conditioning decides what can be compared.  Under schedules that alternate Q and Q^T
+(alternating, or the mixed schedule on Haar) the later outputs are very sensitive to the
+stored reflectors: the oracle against itself, with one rounding-sized relative change
+(1e-16) of x_1, drifts by about 1e-14 at step 32, 1e-9 at step 64 and 3e-6 at step 256
+(Haar, alternating, x_{t+1} = tanh(y_t)).  Two correct FP64 implementations with different
+summation orders therefore cannot agree to 1e-12 there, so:
+
+* well-conditioned cases (Haar all Q, Ginibre mixed) are compared per step to FP64 1e-12 /
+  FP32 1e-5 all the way to T = 256;
+* the alternating Haar case is compared to the oracle's own measured sensitivity (times 10^3
+  for roundings at every step), with the exact invariant ||y_t|| = ||x_t|| to 1e-13;
+* the fused trajectory path at T = 256 is compared to step-by-step hd_apply for gross
+  errors only (1e-2); at T = 48 to 1e-7 (FP64) and 1e-4 (FP32), free-running;
+* the reverse mode at T = 256 (Haar, all Q) against the oracle's torch float64 autograd.
+"""
+import numpy as np
+import pytest
+
+import synth
+from gpu_util import TOL, next_input, teacher_forced
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TMAX = 256
+ALT = lambda t: t % 2 == 0
+ALLQ = lambda t: False
+MIXED = lambda t: (t % 3 == 0) or (t % 7 == 1)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_haar_tmax_all_q_teacher_forced(dtype):
+    n = 2003
+    errs = teacher_forced("haar", n, n, TMAX, seed=41, dtype=dtype, schedule=ALLQ)
+    assert errs.max() <= TOL[dtype], (errs.argmax(), errs.max())
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_ginibre_tmax_mixed_teacher_forced(dtype):
+    m, n = 1501, 2003
+    errs = teacher_forced("ginibre", m, n, TMAX, seed=43, dtype=dtype, schedule=MIXED, sigma=m ** -0.5)
+    assert errs.max() <= TOL[dtype], (errs.argmax(), errs.max())
+
+
+def test_haar_tmax_alternating_within_oracle_sensitivity():
+    from oracle.hd import make_oracle
+    from paper_2101_07464_gb300 import HD
+    n, seed = 2003, 41
+    ora, ref = make_oracle("haar", n, n, TMAX, seed), make_oracle("haar", n, n, TMAX, seed)
+    gpu = HD("haar", n, n, TMAX, seed, "f64")
+    rng = np.random.default_rng(0)
+    x = synth.x1(n, seed)
+    err, sens, ndef = [], [], []
+    for t in range(1, TMAX + 1):
+        tr = ALT(t)
+        yo = ora.apply(x, tr).numpy()
+        xr = x * (1.0 + 1e-16 * rng.standard_normal(n)) if t == 1 else x
+        yr = ref.apply(xr, tr).numpy()
+        yg = gpu.apply(torch.tensor(x, dtype=torch.float64, device="cuda"), tr).cpu().numpy()
+        den = np.linalg.norm(yo)
+        err.append(np.linalg.norm(yg - yo) / den)
+        sens.append(np.linalg.norm(yr - yo) / den)
+        ndef.append(abs(np.linalg.norm(yg) / np.linalg.norm(x) - 1.0))
+        x = next_input(yo, t + 1, ALT(t + 1), n, n, seed)
+    gpu.close()
+    err, env = np.array(err), np.maximum.accumulate(np.array(sens))
+    bound = np.maximum(TOL["f64"], 1e3 * env)
+    assert (err <= bound).all(), [(t + 1, err[t], bound[t]) for t in np.nonzero(err > bound)[0][:5]]
+    assert err[:32].max() <= TOL["f64"], err[:32].max()
+    assert max(ndef) <= 1e-13, max(ndef)
+
+
+def test_fused_run_tmax_gross():
+    import paper_2101_07464_gb300 as hd
+    n, dtype = 3001, "f64"
+    flags = [ALT(t) for t in range(1, TMAX + 1)]
+    ref_st = hd.HD("haar", n, n, TMAX, 9, dtype)
+    x = torch.tensor(synth.x1(n, 9), dtype=torch.float64, device="cuda")
+    for t in range(1, TMAX + 1):
+        x = torch.tanh(ref_st.apply(x, flags[t - 1]))
+    ref_st.close()
+    st = hd.HD("haar", n, n, TMAX, 9, dtype)
+    out = torch.empty(n, dtype=torch.float64, device="cuda")
+    hd.hd_run(st.h, hd.make_run_spec(flags, "tanh", use_graph=True),
+              torch.tensor(synth.x1(n, 9), dtype=torch.float64, device="cuda"), out)
+    torch.cuda.synchronize()
+    rel = ((out - x).norm() / x.norm()).item()
+    assert rel <= 1e-2, rel
+    st.close()
+
+
+@pytest.mark.parametrize("ens,dtype,tol", [("haar", "f64", 1e-7), ("haar", "f32", 1e-4)])
+def test_fused_run_t48(ens, dtype, tol):
+    """Free-running: x_{t+1} comes from each path's own y_t, so the two summation orders
+    separate at the alternating schedule's sensitivity (measured 1.1e-9 in FP64 at T = 48)."""
+    import paper_2101_07464_gb300 as hd
+    n, T = 20_011, 48
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    flags = [ALT(t) for t in range(1, T + 1)]
+    ref_st = hd.HD(ens, n, n, T, 9, dtype)
+    x = torch.tensor(synth.x1(n, 9), dtype=tdt, device="cuda")
+    for t in range(1, T + 1):
+        x = torch.tanh(ref_st.apply(x, flags[t - 1]))
+    ref_st.close()
+    st = hd.HD(ens, n, n, T, 9, dtype)
+    out = torch.empty(n, dtype=tdt, device="cuda")
+    hd.hd_run(st.h, hd.make_run_spec(flags, "tanh", use_graph=True),
+              torch.tensor(synth.x1(n, 9), dtype=tdt, device="cuda"), out)
+    torch.cuda.synchronize()
+    rel = ((out.double() - x.double()).norm() / x.double().norm()).item()
+    assert rel <= tol, rel
+    st.close()
+
+
+def test_adjoint_tmax_matches_oracle_autograd():
+    from oracle.adjoint import trajectory as oracle_trajectory
+    from paper_2101_07464_gb300 import HD
+    from paper_2101_07464_gb300.autograd import trajectory
+    n, T = 517, TMAX
+    sched = [ALLQ(t) for t in range(1, T + 1)]
+    rng = np.random.default_rng(5)
+    x1 = rng.standard_normal(n)
+    theta = 0.6 + 0.4 * rng.random(T)
+    c = rng.standard_normal(n)
+
+    def f(t, y, x, xprev, th):
+        v = torch.tanh(th[t - 1] * y)
+        return v if xprev is None else v + 0.3 * xprev
+
+    hdst = HD("haar", n, n, T, 11, "f64")
+    xg = torch.tensor(x1, dtype=torch.float64, device="cuda", requires_grad=True)
+    tg = torch.tensor(theta, dtype=torch.float64, device="cuda", requires_grad=True)
+    L = torch.dot(torch.tensor(c, dtype=torch.float64, device="cuda"), trajectory(hdst, xg, sched, f, (tg,)))
+    L.backward()
+    hdst.close()
+    xo = torch.tensor(x1, dtype=torch.float64, requires_grad=True)
+    to = torch.tensor(theta, dtype=torch.float64, requires_grad=True)
+    Lo = torch.dot(torch.tensor(c, dtype=torch.float64), oracle_trajectory("haar", n, n, T, 11, sched, f, xo, (to,)))
+    Lo.backward()
+    rel = lambda a, b: (a - b).norm().item() / b.norm().item()
+    assert abs(L.item() - Lo.item()) <= 1e-11 * max(1.0, abs(Lo.item()))
+    assert rel(xg.grad.cpu(), xo.grad) <= 1e-9, rel(xg.grad.cpu(), xo.grad)
+    assert rel(tg.grad.cpu(), to.grad) <= 1e-9, rel(tg.grad.cpu(), to.grad)

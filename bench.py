@@ -45,6 +45,7 @@ def parse(argv=None):
     ap.add_argument("--no-amp", action="store_true", help="skip the batched AMP measurement")
     ap.add_argument("--amp-trials", type=int, default=4096)
     ap.add_argument("--no-adjoint", action="store_true", help="skip the reverse-mode measurement")
+    ap.add_argument("--no-ista", action="store_true", help="skip the differentiable ISTA workload")
     ap.add_argument("--no-large", action="store_true",
                     help="skip the large configuration (Haar n = 2e7, T = 256, forward and reverse mode)")
     ap.add_argument("--no-autotune", action="store_true",
@@ -350,6 +351,76 @@ def measure_adjoint(args, rank, world, dist):
                       "d<c, x_{T+1}>/d(x_1, theta)"}
 
 
+def measure_ista(args, rank, world, dist):
+    """The differentiable ISTA workload: 64 trials of Gin(n, n), n = 2 * 10^5, entries N(0, 1/n),
+    50 ISTA iterations x^{k+1} = eta(x^k + tau Q^T (y - Q x^k); theta_k) with y = Q beta* + w
+    (101 products: Q beta*, then Q x^k and Q^T r^k alternating), beta* ~ 0.2 delta_0 +
+    0.8 N(0, 2^2), w ~ N(0, 0.1^2), FP32 storage; the gradient of (1/n) ||x^50 - beta*||^2 with
+    respect to theta_1..theta_50 (0.6) and tau (0.3) through the library's reverse mode.  The
+    trials run one after another on one state (Philox trial word per trial); wall clock
+    around all of them, synchronised.  Units trials n T^2 per forward + backward, T = 101."""
+    import numpy as np
+    import torch
+    import synth
+    import paper_2101_07464_gb300 as hd
+    from paper_2101_07464_gb300.autograd import trajectory
+    n, K, trials = 200_000, 50, 64
+    T = 2 * K + 1
+    sched = [False] + [bool(t % 2) for t in range(2, T + 1)]
+    sigma = n ** -0.5
+    st = hd.HD("ginibre", n, n, T, args.seed, "f32", sigma=sigma, trial=rank * trials)
+
+    def make_f(w):
+        store = {}
+
+        def f(t, y, x, xprev, theta, tau):
+            if t == 1:
+                store["y"] = (y + w).detach()
+                return torch.zeros_like(y)
+            if t % 2 == 0:
+                return store["y"] - y
+            v = xprev + tau * y
+            return torch.sign(v) * torch.clamp(v.abs() - theta[(t - 3) // 2], min=0.0)
+        return f
+
+    data = []
+    for i in range(trials):
+        b = synth.bernoulli_gauss(n, args.seed, trial=rank * trials + i, p_nonzero=0.8, scale=2.0,
+                                  dtype=np.float32)
+        w = synth.noise(n, args.seed, trial=rank * trials + i, sigma=0.1, dtype=np.float32)
+        data.append((torch.from_numpy(b).cuda(), torch.from_numpy(w).cuda()))
+
+    def one(i):
+        st.reset()   # the trial word changes only on a reset state
+        hd.hd_set_options(st.h, sigma, rank * trials + i, st.stream)
+        bt, wt = data[i]
+        th = torch.full((K,), 0.6, dtype=torch.float32, device="cuda", requires_grad=True)
+        ta = torch.tensor(0.3, dtype=torch.float32, device="cuda", requires_grad=True)
+        xK = trajectory(st, bt, sched, make_f(wt), (th, ta))
+        L = torch.sum((xK - bt) ** 2) / n
+        L.backward()
+        return L.detach(), th.grad.norm(), ta.grad.detach()
+
+    one(0)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    t0 = time.perf_counter()
+    res = [one(i) for i in range(trials)]
+    torch.cuda.synchronize()
+    secs = max_over_ranks(time.perf_counter() - t0, dist)
+    st.close()
+    mse = float(torch.stack([r[0] for r in res]).mean().item())
+    gth = float(torch.stack([r[1] for r in res]).mean().item())
+    return {"metric": "trials*n*T^2/s (forward + backward)",
+            "value": job_throughput(float(trials) * n * T * T, world, secs),
+            "ms_per_trial": secs / trials * 1e3, "trials": trials * world, "n": n, "T": T, "dtype": "f32",
+            "mean_loss": mse, "mean_grad_theta_norm": gth,
+            "timing": "wall clock around the 64 trials (host-driven steps, torch f_t), synchronised",
+            "config": "Gin(n, n), n=2e5, ISTA 50 iterations (101 products), tau=0.3, theta_k=0.6, "
+                      "d MSE / d(theta_1..theta_50, tau)"}
+
+
 def measure_large(args, rank, world, dist):
     """The large single-trial configuration: Haar(n), n = 2 * 10^7, T = 256 products, all Q,
     x_{t+1} = normalize(tanh(y_t) + 0.1 x_t), FP32 stacks (2 x 20.5 GB).  Forward: one hd_run
@@ -506,6 +577,12 @@ def run_ours(args):
     adj = None
     if not args.no_adjoint:
         adj = measure_adjoint(args, rank, world, dist)
+    ista = None
+    if not args.no_ista:
+        try:
+            ista = measure_ista(args, rank, world, dist)
+        except Exception as exc:   # reported in the line, the headline stands
+            ista = {"error": "%s: %s" % (type(exc).__name__, exc)}
     large = None
     if not args.no_large:
         try:
@@ -536,7 +613,7 @@ def run_ours(args):
                 "roofline": roofline,
                 "step_credited_GBps": step_gbps,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk, "fp64": fp64, "batched_amp": amp, "adjoint": adj, "large": large}
+                "clocks": clk, "fp64": fp64, "batched_amp": amp, "adjoint": adj, "ista": ista, "large": large}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -71,7 +71,10 @@ class _Trajectory(torch.autograd.Function):
             with torch.enable_grad():
                 out = f(t, yl, xl, pl, *ql)
                 ins = [yl, xl] + ([pl] if pl is not None else []) + [q for q in ql if q.requires_grad]
-                g = torch.autograd.grad(out, ins, xbar.pop(t + 1), allow_unused=True)
+                gout_t = xbar.pop(t + 1)
+                # an f_t whose output does not depend on its inputs (e.g. a constant) passes nothing
+                g = (torch.autograd.grad(out, ins, gout_t, allow_unused=True) if out.requires_grad
+                     else [None] * len(ins))
             ybar = g[0] if g[0] is not None else torch.zeros_like(yl)
             add(t, g[1])
             k = 2

@@ -33,10 +33,22 @@ std::map<std::string, std::vector<int32_t>>& tune_cache() {
 
 // Cache key: ensemble, dtype, trials, T_max, device (name, SMs), fusion, and a hash of every
 // trial's dimensions (FNV-1a over their bytes).
-std::string shape_key(const hd_state* st) {
+// Device names, looked up once per device (cudaGetDeviceProperties is slow).
+std::string device_name(int dev) {
+  static std::mutex mu;
+  static std::map<int, std::string> names;
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = names.find(dev);
+  if (it != names.end()) return it->second;
   cudaDeviceProp prop;
   memset(&prop, 0, sizeof(prop));
-  if (cudaGetDeviceProperties(&prop, st->device) != cudaSuccess) cudaGetLastError();
+  if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) cudaGetLastError();
+  prop.name[sizeof(prop.name) - 1] = 0;
+  return names[dev] = std::string(prop.name);
+}
+
+std::string shape_key(const hd_state* st) {
+  const std::string name = device_name(st->device);
   uint64_t h = 1469598103934665603ull;
   for (int s = 0; s < 2; s++)
     for (int64_t d : st->dims[s])
@@ -46,7 +58,7 @@ std::string shape_key(const hd_state* st) {
       }
   char buf[384];
   snprintf(buf, sizeof(buf), "%d/%d/%d/%d/%d/%.200s/%d/%016llx", st->ens, st->dtype, st->count, st->Tm,
-           st->nsm, prop.name, st->fuse, (unsigned long long)h);
+           st->nsm, name.c_str(), st->fuse, (unsigned long long)h);
   return std::string(buf);
 }
 

@@ -1482,8 +1482,11 @@ cudaError_t launch_step(const BatchStep<T>& b, cudaStream_t s, cudaEvent_t* ev, 
   const int nc1 = p.kD + ((p.ens == 0) ? p.kN : 0);
   if (nc1 > 0 && !p.skip_dots) {
     rec(0);
+    // no early launch: its prologue copies the newest stack and basis columns, which the
+    // previous step's output sweep may still be writing when the two steps follow each
+    // other directly on the stream
     e = launch_sweep<T>(k_dots<T>, p.c1, b.map[dspace].ctas,
-                        sweep_smem_bytes<T>(p.c1.W, p.c1.nbuf, nc1, 1, nc1, 1), s, pdl, b);
+                        sweep_smem_bytes<T>(p.c1.W, p.c1.nbuf, nc1, 1, nc1, 1), s, false, b);
     if (e != cudaSuccess) return e;
     rec(1);
     if (launched) launched[0] = 1;

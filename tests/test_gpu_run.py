@@ -126,3 +126,35 @@ def test_fused_run_matches_apply(graph, ens, m, n, dyn, a, dtype):
     per_run = (hd.hd_get_launches(st.h) - l0) // 2
     assert per_run == 2 + 2 * T + 1, per_run
     st.close()
+
+
+@pytest.mark.parametrize("ens,dtype", [("haar", "f64"), ("ginibre", "f64"), ("ginibre", "f32")])
+def test_back_to_back_products_match_oracle(ens, dtype):
+    """Products issued directly one after another on the stream, no kernel or host wait in
+    between, at a size with one CTA per sweep (so the next product's sweeps could start on
+    idle SMs while the previous one finishes).  The inputs are fixed seeded vectors, so each
+    output is compared with the oracle's at the same step."""
+    from oracle.hd import make_oracle
+    from paper_2101_07464_gb300 import HD
+    from gpu_util import TOL
+    n, T, seed = 300, 12, 4
+    sched = [(t % 2 == 0) or (t % 5 == 0) for t in range(1, T + 1)]
+    sigma = 1.0 if ens == "haar" else n ** -0.5
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    xs = [synth.x1(n, seed, trial=t) for t in range(T)]
+    if dtype == "f32":
+        xs = [x.astype(np.float32).astype(np.float64) for x in xs]
+    xd = [torch.tensor(x, dtype=tdt, device="cuda") for x in xs]
+    ys = [torch.empty(n, dtype=tdt, device="cuda") for _ in range(T)]
+    st = HD(ens, n, n, T, seed, dtype, sigma=sigma)
+    torch.cuda.synchronize()
+    import paper_2101_07464_gb300 as hd
+    for t in range(T):
+        hd.hd_apply(st.h, xd[t], sched[t], ys[t])
+    torch.cuda.synchronize()
+    ora = make_oracle(ens, n, n, T, seed, sigma=sigma)
+    for t in range(T):
+        yo = ora.apply(xs[t], sched[t]).numpy()
+        err = np.linalg.norm(ys[t].double().cpu().numpy() - yo) / np.linalg.norm(yo)
+        assert err <= TOL[dtype], (t, err)
+    st.close()

@@ -227,6 +227,29 @@ HD_API int hd_get_tuning(const hd_state* st, int32_t* words, int32_t nwords);
 HD_API int hd_set_tuning(hd_state* st, const int32_t* words, int32_t nwords);
 HD_API int hd_get_map_options(const hd_state* st, int32_t* count, int32_t* spc);
 
+/* Other ensembles from the Gaussian and Haar ones (paper, section "Other Random Matrix
+ * Ensembles").
+ *
+ * hd_goe_apply: y = W x for W = (Q + Q^T)/sqrt(2) ~ GOE(n), Q the square Ginibre matrix of
+ * `st` (entries N(0, sigma^2); sigma = 1 gives GOE(n) with W_ii ~ N(0, 2), W_ij ~ N(0, 1)).
+ * Two products of the state, Q x then Q^T x, and their scaled sum, on the state's stream;
+ * T_max counts both.  Batched states: every trial square, vectors packed.  x, y: distinct
+ * device vectors of n (packed) elements in the state's dtype.  Errors: HD_ERR_ARG (not
+ * Ginibre, null or aliased vectors), HD_ERR_DIM (a trial with m != n), HD_ERR_TMAX (fewer than
+ * two products left), HD_ERR_OOM (the intermediate vector, allocated on first use), and those
+ * of hd_apply.
+ *
+ * hd_usv_apply: the product with Q = U Sigma V (eq. inv): U = the Haar(m) state `U`, V = the
+ * Haar(n) state `V`, Sigma the m x n rectangular diagonal matrix with s[0..min(m,n)) (device
+ * FP64 array) on its diagonal.  transpose = 0: y = U (Sigma (V x)), x of length n, y of m;
+ * transpose = 1: y = V^T (Sigma^T (U^T x)), x of length m, y of n.  One product of each state
+ * per call; both single-trial, same dtype, device and stream.  Intermediates live in U (two
+ * vectors of max(m, n), allocated on first use).  Errors: HD_ERR_ARG (wrong ensembles,
+ * batched, mismatched dtype / stream, null pointers, U == V), HD_ERR_TMAX, HD_ERR_OOM, and
+ * those of hd_apply. */
+HD_API int hd_goe_apply(hd_state* st, const void* x, void* y);
+HD_API int hd_usv_apply(hd_state* U, hd_state* V, const double* s, const void* x, int transpose, void* y);
+
 /* Number of kernels this state has launched (graph replays count their kernels). */
 HD_API int hd_get_launches(const hd_state* st, int64_t* launches);
 

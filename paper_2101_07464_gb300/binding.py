@@ -50,6 +50,8 @@ _PROTOS = {
     "hd_reset": (_c.c_int, [_P, _c.c_uint64]),
     "hd_sync": (_c.c_int, [_P]),
     "hd_run": (_c.c_int, [_P, _P, _P, _P]),
+    "hd_goe_apply": (_c.c_int, [_P, _P, _P]),
+    "hd_usv_apply": (_c.c_int, [_P, _P, _P, _P, _c.c_int, _P]),
     "hd_autotune": (_c.c_int, [_P, _P, _P, _P, _c.c_int32]),
     "hd_get_tuning": (_c.c_int, [_P, _P, _c.c_int32]),
     "hd_set_tuning": (_c.c_int, [_P, _P, _c.c_int32]),
@@ -237,6 +239,17 @@ def hd_run(state, spec, x1, x_out):
 
 
 HD_TUNE_WORDS = 134
+
+
+def hd_goe_apply(state, x, y):
+    """y = (Q + Q^T) x / sqrt(2) on a square Ginibre state (two of its products)."""
+    _check(lib().hd_goe_apply(state, _ptr(x, what="x"), _ptr(y, what="y")), "hd_goe_apply")
+
+
+def hd_usv_apply(U, V, s, x, transpose, y):
+    """y = U Sigma V x (transpose False) or V^T Sigma^T U^T x (True); s: CUDA float64 tensor."""
+    _check(lib().hd_usv_apply(U, V, _ptr(s, HD_F64, what="s"), _ptr(x, what="x"), int(bool(transpose)),
+                              _ptr(y, what="y")), "hd_usv_apply")
 
 
 def _run_addr(t, what):
@@ -465,6 +478,16 @@ class HD:
     def adjoint_restart(self):
         hd_adjoint_restart(self.h)
 
+    def goe(self, x, out=None):
+        """W x for W = (Q + Q^T)/sqrt(2) (square Ginibre state; two products)."""
+        import torch
+        if out is None:
+            out = torch.empty(self.n, dtype=self.torch_dtype, device=x.device)
+        _ptr(x, self.dtype_code, self.n, "x")
+        _ptr(out, self.dtype_code, self.n, "out")
+        hd_goe_apply(self.h, x, out)
+        return out
+
     def _dims(self):
         return (self.n, self.m)
 
@@ -495,3 +518,29 @@ class HD:
             self.close()
         except Exception:
             pass
+
+
+class USV:
+    """Q = U Sigma V (eq. inv) from two independent Haar states and singular values s."""
+
+    def __init__(self, m, n, T_max, seed_u, seed_v, s, dtype="f64", stream=None):
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.m, self.n = m, n
+        self.U = HD("haar", m, m, T_max, seed_u, dtype, stream=stream)
+        self.V = HD("haar", n, n, T_max, seed_v, dtype, stream=stream)
+        self.s = torch.as_tensor(s, dtype=torch.float64).to("cuda").contiguous()
+        if self.s.numel() < min(m, n):
+            raise ValueError("s needs min(m, n) = %d values" % min(m, n))
+        self.torch_dtype = self.U.torch_dtype
+
+    def apply(self, x, transpose=False):
+        import torch
+        out = torch.empty(self.n if transpose else self.m, dtype=self.torch_dtype, device=x.device)
+        hd_usv_apply(self.U.h, self.V.h, self.s, x, transpose, out)
+        return out
+
+    def close(self):
+        self.U.close()
+        self.V.close()

@@ -115,6 +115,7 @@ struct hd_state {
   // hd_run: work vectors and the cached trajectory graph
   void* xw[2] = {nullptr, nullptr};
   void* yw = nullptr;
+  void* ens_tmp[2] = {nullptr, nullptr};   // hd_goe_apply / hd_usv_apply intermediates
   double* sumsq = nullptr;
   int run_final = 0;
   cudaStream_t own_stream = nullptr;

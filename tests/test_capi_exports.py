@@ -42,6 +42,14 @@ def test_library_exports_every_declared_symbol(libpath):
         assert getattr(lib, n) is not None
 
 
+def test_library_exports_nothing_undeclared(libpath):
+    """Every hd_* symbol the library exports is declared (and documented) in include/*.h."""
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (hd_\w+)", out))
+    extra = sorted(exported - set(_declared()))
+    assert not extra, extra
+
+
 def test_binding_loads_and_maps_status_strings(libpath):
     import paper_2101_07464_gb300 as hd
     L = hd.lib()

@@ -28,24 +28,7 @@ def _cuda():
         pytest.skip("no CUDA device")
 
 
-def schedule(K):
-    return [False] + [bool(t % 2) for t in range(2, 2 * K + 2)]   # Q, Q, Q^T, Q, Q^T, ...
-
-
-def ista_f(w):
-    """f_t for the trajectory API; keeps y = Q beta* + w from the first product."""
-    store = {}
-
-    def f(t, y, x, xprev, theta, tau):
-        if t == 1:
-            store["y"] = (y + w).detach()
-            return torch.zeros_like(y)
-        if t % 2 == 0:                      # y = Q x^k: next input r^k = y_obs - Q x^k
-            return store["y"] - y
-        k = (t - 3) // 2                    # y = Q^T r^k, xprev = x^k
-        v = xprev + tau * y
-        return torch.sign(v) * torch.clamp(v.abs() - theta[k], min=0.0)
-    return f
+from dyn_util import ista_f, ista_schedule as schedule   # noqa: E402
 
 
 def inputs(n, seed, dtype):

@@ -163,6 +163,13 @@ HD_API int hd_run(hd_state* st, const hd_run_spec* spec, const void* x1, void* x
  * state's sticky status (HD_OK when healthy). */
 HD_API int hd_sync(hd_state* st);
 
+/* Check of the failure path of the kernels' bounded waits (no fault involved): launches one
+ * CTA that waits on a shared-memory barrier nothing will complete, gives up after `polls`
+ * polls (1..2^24), sets the state's device error word and exits.  The next hd_sync then
+ * returns HD_ERR_TIMEOUT and poisons the state, as after a real expired wait; hd_reset clears
+ * it.  Errors: HD_ERR_ARG (polls out of range), the state's sticky status, HD_ERR_CUDA. */
+HD_API int hd_check_bounded_wait(hd_state* st, uint32_t polls);
+
 /* Forget all steps (t = r = l = 0) and re-key the generator with seed; keeps the
  * allocations and options.  Clears a poisoned state. */
 HD_API int hd_reset(hd_state* st, uint64_t seed);

@@ -49,6 +49,7 @@ _PROTOS = {
     "hd_probe": (_c.c_int, [_P, _P, _c.c_int, _P, _c.POINTER(_c.c_double)]),
     "hd_reset": (_c.c_int, [_P, _c.c_uint64]),
     "hd_sync": (_c.c_int, [_P]),
+    "hd_check_bounded_wait": (_c.c_int, [_P, _c.c_uint32]),
     "hd_run": (_c.c_int, [_P, _P, _P, _P]),
     "hd_goe_apply": (_c.c_int, [_P, _P, _P]),
     "hd_usv_apply": (_c.c_int, [_P, _P, _P, _P, _c.c_int, _P]),
@@ -310,6 +311,11 @@ def hd_get_launches(state):
 
 def hd_sync(state):
     _check(lib().hd_sync(state), "hd_sync")
+
+
+def hd_check_bounded_wait(state, polls=4096):
+    """Launch the bounded-wait check (see include/hd.h); hd_sync afterwards reports the expiry."""
+    _check(lib().hd_check_bounded_wait(state, int(polls)), "hd_check_bounded_wait")
 
 
 def hd_reset(state, seed):

@@ -941,6 +941,16 @@ HD_API int hd_get_launches(const hd_state* st, int64_t* launches) {
   return HD_OK;
 }
 
+HD_API int hd_check_bounded_wait(hd_state* st, uint32_t polls) {
+  if (!st || polls < 1 || polls > (1u << 24)) return HD_ERR_ARG;
+  if (st->poisoned) return st->poisoned;
+  if (cudaSetDevice(st->device) != cudaSuccess) return cuda_fail(st, cudaErrorInvalidDevice);
+  const cudaError_t e = launch_wait_selftest(st->err, polls, st->stream);
+  if (e != cudaSuccess) return cuda_fail(st, e);
+  st->launches += 1;
+  return HD_OK;
+}
+
 HD_API int hd_sync(hd_state* st) {
   if (!st) return HD_ERR_ARG;
   if (cudaSetDevice(st->device) != cudaSuccess) return cuda_fail(st, cudaErrorInvalidDevice);

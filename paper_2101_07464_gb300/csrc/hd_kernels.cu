@@ -243,6 +243,7 @@ struct Stager {
   uint64_t* bar;
   unsigned parity;
   unsigned* err;
+  unsigned limit = kStageSpins;   // polls before the wait gives up
   // begin(): issue the copies (every thread calls it); finish(): wait for them (bounded).
   template <typename Issue>
   __device__ void begin(unsigned bytes, Issue issue) {
@@ -255,7 +256,7 @@ struct Stager {
     unsigned spins = 0;
     bool ok = true;
     while (!mbar_test(bar, parity)) {
-      if (++spins > kStageSpins) {
+      if (++spins > limit) {
         ok = false;
         if (threadIdx.x == 0 && err) atomicOr(err, 1u);
         break;
@@ -1675,6 +1676,22 @@ cudaError_t launch_probe(const BatchStep<T>& b, double* q, double* unrev, cudaSt
 }
 template cudaError_t launch_probe<float>(const BatchStep<float>&, double*, double*, cudaStream_t);
 template cudaError_t launch_probe<double>(const BatchStep<double>&, double*, double*, cudaStream_t);
+
+// ------------------------------------------------------------------------------------
+// Check of the bounded-wait path: one staging round that posts 16 expected bytes and issues
+// no copy, so the wait runs out after `limit` polls, sets the error word and returns (no copy
+// is ever in flight on the abandoned barrier).
+__global__ void k_wait_selftest(unsigned* err, unsigned limit) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) mbar_init(&bar);
+  Stager sg{&bar, 0u, err, limit};
+  sg.run(16u, []() {});
+}
+
+cudaError_t launch_wait_selftest(unsigned* err, unsigned limit, cudaStream_t s) {
+  k_wait_selftest<<<1, 64, 0, s>>>(err, limit);
+  return cudaGetLastError();
+}
 
 // ------------------------------------------------------------------------------------
 // Generator checks.

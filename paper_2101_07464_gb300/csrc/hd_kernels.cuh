@@ -177,6 +177,7 @@ cudaError_t set_sweep_smem_limit(int bytes);
 
 cudaError_t launch_philox_normals(DrawKey key, int64_t start, int64_t count, int dtype, void* out,
                                   cudaStream_t s);
+cudaError_t launch_wait_selftest(unsigned* err, unsigned limit, cudaStream_t s);
 cudaError_t launch_philox_words(uint32_t k0, uint32_t k1, const uint32_t* ctr, int64_t nblocks,
                                 uint32_t* out, cudaStream_t s);
 

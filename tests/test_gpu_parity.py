@@ -181,3 +181,28 @@ def test_probe_reproduces_earlier_queries(dtype, ens, m, n):
     _, unrev = st.probe(torch.tensor(synth.x1(n, 99), dtype=tdt, device="cuda"), False)
     assert unrev > 0.5 * np.sqrt(n)
     st.close()
+
+
+def test_expired_bounded_wait_poisons_until_reset():
+    """The kernels' bounded waits: a wait that runs out (on a barrier nothing completes) sets
+    the error word; hd_sync reports HD_ERR_TIMEOUT, later calls return it, hd_reset clears it
+    and the state computes the oracle's products again."""
+    import paper_2101_07464_gb300 as hd
+    import synth
+    n = 1000
+    st = hd.HD("haar", n, n, 4, 3, "f64")
+    x = torch.tensor(synth.x1(n, 3), dtype=torch.float64, device="cuda")
+    st.apply(x)
+    hd.hd_check_bounded_wait(st.h, 4096)
+    with pytest.raises(hd.HDError) as ei:
+        hd.hd_sync(st.h)
+    assert ei.value.code == 6
+    with pytest.raises(hd.HDError) as ei:   # sticky
+        st.apply(x)
+    assert ei.value.code == 6
+    st.reset()
+    hd.hd_sync(st.h)
+    st.close()
+    errs = teacher_forced("haar", n, n, 4, seed=3, dtype="f64", schedule=lambda t: t % 2 == 0,
+                          setup=lambda g: (hd.hd_check_bounded_wait(g.h, 64), g.reset()))
+    assert errs.max() <= 1e-12, errs

@@ -1,0 +1,90 @@
+"""Pins of the complex Householder Dice oracle (Haar measure on the unitary group; the
+paper's section "Other Random Matrix Ensembles", eq. Householder_c):
+
+* the complex reflector is unitary, maps v to ||v|| e_1, its adjoint maps e_1 to v/||v||, and
+  for real v it is the real reflector of eq. Householder;
+* step 1 gives y_1 = ||x_1|| g_1/||g_1|| for Q and for Q^H;
+* every product keeps norms; at n = 6, T = n the implied Q is unitary and reproduces every
+  earlier query (brute force);
+* law: |Q_11|^2 ~ Beta(1, n - 1), arg Q_11 uniform, |Q_11|^2 + |Q_12|^2 ~ Beta(2, n - 2)
+  (the first row of a Haar unitary matrix is uniform on the complex sphere).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+from scipy import stats
+
+from oracle.complex_hd import ComplexHaarOracle, ComplexReflector, complex_gaussian_vector, unit
+from oracle.hd import Reflector
+
+
+def crand(n, seed):
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal(n) + 1j * rng.standard_normal(n)
+
+
+@pytest.mark.parametrize("n,seed", [(1, 1), (5, 2), (17, 3)])
+def test_complex_reflector_identities(n, seed):
+    v = torch.tensor(crand(n, seed))
+    H = ComplexReflector(0, v).dense(n)
+    eye = torch.eye(n, dtype=torch.complex128)
+    assert torch.linalg.matrix_norm(H.conj().T @ H - eye) <= 1e-13
+    nv = torch.linalg.vector_norm(v)
+    assert torch.linalg.vector_norm(H @ v - nv * unit(n, 0)) <= 1e-13 * nv
+    assert torch.linalg.vector_norm(H.conj().T @ unit(n, 0) - v / nv) <= 1e-13
+
+
+def test_complex_reflector_reduces_to_real_and_handles_zero_pivot():
+    n = 9
+    v = np.random.default_rng(4).standard_normal(n)
+    for vv in (v, -v, np.concatenate([[0.0], v[1:]])):
+        Hc = ComplexReflector(0, vv).dense(n)
+        Hr = Reflector(0, torch.tensor(vv)).dense(n)
+        assert torch.linalg.matrix_norm(Hc - Hr.to(torch.complex128)) <= 1e-13
+    ident = ComplexReflector(3, np.concatenate([crand(3, 5), np.zeros(4)]))
+    z = torch.tensor(crand(7, 6))
+    assert torch.equal(ident.apply(z), z)
+
+
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_first_step_closed_form(adjoint):
+    n, seed = 11, 7
+    x = crand(n, 8)
+    y = ComplexHaarOracle(n, 3, seed).apply(x, adjoint).numpy()
+    g = complex_gaussian_vector(seed, 0, 1, n, 0)
+    np.testing.assert_allclose(y, np.linalg.norm(x) * g / np.linalg.norm(g), rtol=0, atol=1e-13 * np.linalg.norm(x))
+
+
+def test_norms_kept_and_brute_force_reconstruction():
+    n = 6
+    o = ComplexHaarOracle(n, n, 9)
+    sched = [False, True, True, False, True, False]
+    xs, ys = [], []
+    for t in range(n):
+        x = crand(n, 20 + t)
+        y = o.apply(x, sched[t]).numpy()
+        assert abs(np.linalg.norm(y) / np.linalg.norm(x) - 1.0) <= 1e-13
+        xs.append(x)
+        ys.append(y)
+    Q = o.matrix().numpy()
+    assert np.abs(Q.conj().T @ Q - np.eye(n)).max() <= 1e-13
+    for t in range(n):
+        M = Q.conj().T if sched[t] else Q
+        np.testing.assert_allclose(M @ xs[t], ys[t], rtol=0, atol=1e-12)
+
+
+def test_first_row_law():
+    n, trials = 5, 2000
+    a11, a12, ph = [], [], []
+    for s in range(trials):
+        o = ComplexHaarOracle(n, 2, 100 + s)
+        c1 = o.apply(unit(n, 0)).numpy()       # column 1: Q_11 = c1[0]
+        c2 = o.apply(unit(n, 1)).numpy()       # column 2: Q_12 = c2[0]
+        a11.append(abs(c1[0]) ** 2)
+        a12.append(abs(c1[0]) ** 2 + abs(c2[0]) ** 2)
+        ph.append(np.angle(c1[0]))
+    assert stats.kstest(a11, stats.beta(1, n - 1).cdf).pvalue > 1e-3
+    assert stats.kstest(a12, stats.beta(2, n - 2).cdf).pvalue > 1e-3
+    assert stats.kstest(ph, stats.uniform(-math.pi, 2 * math.pi).cdf).pvalue > 1e-3

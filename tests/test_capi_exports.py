@@ -90,3 +90,14 @@ def test_tuning_word_count_matches_header():
     txt = open(os.path.join(ROOT, "include", "hd.h")).read()
     m = re.search(r"#define HD_TUNE_WORDS (\d+)", txt)
     assert m and int(m.group(1)) == hd.binding.HD_TUNE_WORDS == 2 + 2 * 6 * 11
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """No fallback: without libhd.so every entry point raises instead of computing."""
+    import paper_2101_07464_gb300 as hd
+    monkeypatch.setattr(hd.binding, "_LIB", None)
+    monkeypatch.setattr(hd.binding._build, "LIB", str(tmp_path / "libhd.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        hd.lib()
+    with pytest.raises(RuntimeError, match="not built"):
+        hd.hd_create("haar", 8, 8, 2, 0, "f64")

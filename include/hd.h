@@ -49,7 +49,8 @@ typedef enum {
   HD_ERR_OOM = 4,      /* device allocation failed                                        */
   HD_ERR_CUDA = 5,     /* a CUDA call or kernel launch failed                             */
   HD_ERR_TIMEOUT = 6,  /* a bounded device-side wait expired                              */
-  HD_ERR_STATE = 7     /* the state was poisoned by an earlier error                     */
+  HD_ERR_STATE = 7     /* the call is not valid in the state's current phase (e.g. after
+                          the first step, or with reverse mode on or not enabled)         */
 } hd_status;
 
 typedef enum { HD_GINIBRE = 0, HD_HAAR = 1 } hd_ensemble;

@@ -689,7 +689,7 @@ HD_API const char* hd_status_string(int status) {
     case HD_ERR_OOM: return "HD_ERR_OOM: device allocation failed";
     case HD_ERR_CUDA: return "HD_ERR_CUDA: CUDA error";
     case HD_ERR_TIMEOUT: return "HD_ERR_TIMEOUT: device wait expired";
-    case HD_ERR_STATE: return "HD_ERR_STATE: state poisoned by an earlier error";
+    case HD_ERR_STATE: return "HD_ERR_STATE: call not valid in the state's current phase";
     default: return "unknown status";
   }
 }

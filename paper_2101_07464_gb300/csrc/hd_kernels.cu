@@ -1493,8 +1493,10 @@ cudaError_t launch_step(const BatchStep<T>& b, cudaStream_t s, cudaEvent_t* ev, 
     if (launched) launched[0] = 1;
   }
   rec(2);
-  // K2 prefetches x and its stack columns before waiting for the preceding kernel; after a
-  // fused K3 (which writes x and the newest column) it is launched without the early start
+  // K2 prefetches x and its stack columns before waiting for the preceding kernel.  That
+  // kernel is K1 or, at step 1, the first-draw kernel: both start only after everything
+  // before them on the stream has completed, so x and the older columns are final.  After a
+  // fused K3 (which writes x and the newest column) K2 is launched without the early start
   e = launch_sweep<T>(k_update<T>, p.c2, b.map[dspace].ctas,
                       sweep_smem_bytes<T>(p.c2.W, p.c2.nbuf, p.kD, 1, p.kD, 2), s, pdl && !p.skip_dots, b);
   if (e != cudaSuccess) return e;

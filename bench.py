@@ -26,6 +26,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 N_DEFAULT, T_DEFAULT = 10 ** 6, 100
+REFERENCE_BUDGET_S = 180.0   # bound on a whole --impl reference run (warm-up + timed steps)
 METRIC = "HD throughput n*T^2/s (Haar n=1e6, T=100, Q/Q^T alternating)"
 UNIT = "n*T^2/s"
 
@@ -89,7 +90,7 @@ def job_throughput(units_per_rank, world, secs):
 # CPU oracle (baseline and reference arm)
 def oracle_sample(n, T, seed, budget_s, max_products=None):
     """Run the oracle's first products of the workload until budget_s; returns
-    (products done, seconds, threads)."""
+    (products done, seconds, threads, seconds of each product including its dynamics)."""
     import numpy as np
     import torch
     import synth
@@ -99,20 +100,53 @@ def oracle_sample(n, T, seed, budget_s, max_products=None):
     x = synth.x1(n, seed)
     xp = np.zeros(n)
     sched = schedule(T)
+    per = []
     t0 = time.perf_counter()
-    done = 0
     for t in range(T):
+        t1 = time.perf_counter()
         y = ora.apply(x, bool(sched[t])).numpy()
         x, xp = f_sign_mem(y, x, xp), x
-        done += 1
-        if time.perf_counter() - t0 > budget_s or (max_products and done >= max_products):
+        per.append(time.perf_counter() - t1)
+        if time.perf_counter() - t0 > budget_s or (max_products and len(per) >= max_products):
             break
-    return done, time.perf_counter() - t0, torch.get_num_threads()
+    return len(per), time.perf_counter() - t0, torch.get_num_threads(), per
 
 
-def cpu_units(n, k):
-    """Work of the first k products in the n T^2 unit (work grows like n t for product t)."""
-    return float(n) * k * k
+def trajectory_seconds(T, samples):
+    """Seconds of a whole T-product trajectory from timed samples of its first products.
+
+    samples: lists of per-product seconds, each starting at product 1.  When every sample
+    covers all T products this is their mean total.  Otherwise product t costs a fixed part
+    (draws, norms, dynamics: O(n)) plus a part that grows with the t - 1 stored reflectors it
+    applies (O(n t)), so a least-squares fit of a + b t over all sampled products (a, b >= 0)
+    gives the whole trajectory as sum_{t<=T} (a + b t).  Returns (seconds, a, b, exact)."""
+    import numpy as np
+    if all(len(s) == T for s in samples):
+        return float(np.mean([sum(s) for s in samples])), None, None, True
+    t = np.concatenate([np.arange(1, len(s) + 1) for s in samples]).astype(np.float64)
+    y = np.concatenate([np.asarray(s, dtype=np.float64) for s in samples])
+    if len(np.unique(t)) > 1:
+        b, a = np.polyfit(t, y, 1)
+    else:
+        a, b = float(y.mean()), 0.0
+    if b < 0.0:
+        a, b = float(y.mean()), 0.0
+    if a < 0.0:
+        a, b = 0.0, float(np.dot(t, y) / np.dot(t, t))
+    return float(T * a + b * T * (T + 1) / 2.0), float(a), float(b), False
+
+
+def oracle_throughput(n, T, samples):
+    """n T^2 per second of the whole trajectory, and a description of how it was obtained."""
+    secs, a, b, exact = trajectory_seconds(T, samples)
+    k = min(len(s) for s in samples)
+    if exact:
+        how = "all %d of %d products at n=%d, mean of %d run(s)" % (T, T, n, len(samples))
+    else:
+        how = ("first %d of %d products at n=%d timed (%d run(s)); whole trajectory extrapolated "
+               "with product t costing a + b t, a = %.1f ms, b = %.2f ms, fitted to every "
+               "sampled product: %.1f s" % (k, T, n, len(samples), a * 1e3, b * 1e3, secs))
+    return float(n) * T * T / secs, secs, how
 
 
 def run_reference(args):
@@ -120,21 +154,30 @@ def run_reference(args):
     if world > 1 and rank != 0:
         return
     n, T = args.n, args.T
-    k_sample = min(10, T)
-    times = []
+    # the whole run (warm-up and timed steps) is bounded by about REFERENCE_BUDGET_S: the
+    # first warm-up run sets how many of the T products fit a step's share of it, and every
+    # later run times that many
+    share = REFERENCE_BUDGET_S / max(1, args.warmup + args.steps)
+    k, _, _, _ = oracle_sample(n, T, args.seed, budget_s=share)
+    times, samples = [], []
     for i in range(args.warmup + args.steps):
-        done, secs, thr = oracle_sample(n, T, args.seed, budget_s=1e9, max_products=k_sample)
+        if i == 0 and args.warmup > 0:
+            continue   # the calibration run above is the first warm-up
+        done, secs, thr, per = oracle_sample(n, T, args.seed, budget_s=1e9, max_products=k)
         if i >= args.warmup:
             times.append(secs)
+            samples.append(per)
+    value, traj_s, how = oracle_throughput(n, T, samples)
     mean = statistics.mean(times)
-    value = cpu_units(n, done) / mean
-    sample = "first %d of %d products at n=%d (Haar, Q/Q^T alternating, sign dynamics), FP64" % (
-        k_sample, T, n)
+    sample = how + " (Haar, Q/Q^T alternating, sign dynamics), FP64"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean * 1e3,
+            "trajectory_s": traj_s,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "haar_sign n=%d T=%d (sampled: first %d products)" % (n, T, k_sample),
+            "config": {"workload": "haar_sign n=%d T=%d (%s)" % (
+                           n, T, "whole trajectory per step" if k >= T else
+                           "per step: first %d products, throughput extrapolated" % k),
                        "n": n, "T": T},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": thr, "kind": "oracle",
                              "sample": sample},
@@ -704,9 +747,10 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and not args.no_cpu:
-        done, csecs, thr = oracle_sample(n, T, args.seed, budget_s=15.0)
-        cpu = {"value": cpu_units(n, done) / csecs, "unit": UNIT, "cores": thr, "kind": "oracle",
-               "sample": "first %d of %d products at n=%d, FP64, wall %.1f s" % (done, T, n, csecs)}
+        done, csecs, thr, per = oracle_sample(n, T, args.seed, budget_s=15.0)
+        cval, _, how = oracle_throughput(n, T, [per])
+        cpu = {"value": cval, "unit": UNIT, "cores": thr, "kind": "oracle",
+               "sample": "%s, FP64, wall %.1f s" % (how, csecs)}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,

@@ -746,7 +746,7 @@ def run_ours(args):
             large = {"error": "%s: %s" % (type(exc).__name__, exc)}
 
     cpu = None
-    if rank == 0 and not args.no_cpu:
+    if rank == 0 and world == 1 and not args.no_cpu:   # N = 1 only: the oracle is a single-host baseline
         done, csecs, thr, per = oracle_sample(n, T, args.seed, budget_s=15.0)
         cval, _, how = oracle_throughput(n, T, [per])
         cpu = {"value": cval, "unit": UNIT, "cores": thr, "kind": "oracle",

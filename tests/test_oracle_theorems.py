@@ -132,3 +132,50 @@ def test_a_wrong_sign_rule_is_caught():
     finally:
         hdmod.Reflector = orig
     assert np.max(np.abs(y - expect)) > 0.1
+
+
+def test_revealed_haar_matrix_trace_moments():
+    """The whole revealed Q at T = n against the trace moments of the Haar measure on O(n)
+    (Diaconis and Shahshahani, 1994): for sum_j j a_j <= n/2, E prod_j (tr Q^j)^{a_j} equals
+    the same moment of independent sqrt(j) Z_j + [j even].  At n = 8 that fixes
+    E tr Q = 0, E (tr Q)^2 = 1, E tr Q^2 = 1, E (tr Q)^4 = 3 and E (tr Q^2)^2 = 3.  The
+    trace mixes every diagonal entry, so it sees the joint law, not one entry's marginal.
+    A planted mistake (on the CPU, in a subclass of the oracle's reflector) that drops the
+    sign factor -s of eq. Householder fails it."""
+    import torch
+    from oracle import hd as hdmod
+
+    def gaps(trials):
+        rng = np.random.default_rng(8)
+        t1, t2 = [], []
+        for i in range(trials):
+            st = hdmod.HaarOracle(8, 8, seed=41, trial=i)
+            run(st, rng.standard_normal(8), 8, f_sign_mem, lambda t: t % 3 == 0)
+            Q = st.dense().numpy()
+            t1.append(np.trace(Q))
+            t2.append(np.trace(Q @ Q))
+        t1, t2 = np.array(t1), np.array(t2)
+        out = []
+        for sample, want in ((t1, 0.0), (t1 ** 2, 1.0), (t2, 1.0), (t1 ** 4, 3.0), (t2 ** 2, 3.0)):
+            out.append(abs(sample.mean() - want) / (sample.std(ddof=1) / np.sqrt(trials)))
+        return np.array(out)
+
+    g = gaps(1000)
+    assert (g <= 4.5).all(), g
+
+    class Unsigned(hdmod.Reflector):
+        def apply(self, w):
+            w = hdmod._vec(w)
+            if self.identity:
+                return w.clone()
+            seg = w[self.k:]
+            seg = seg - (2.0 * torch.dot(self.u, seg) / self.uu) * self.u
+            return torch.cat([w[:self.k], seg])
+
+    orig = hdmod.Reflector
+    hdmod.Reflector = Unsigned
+    try:
+        bad = gaps(400)
+    finally:
+        hdmod.Reflector = orig
+    assert bad.max() > 4.5, bad

@@ -88,3 +88,33 @@ def test_first_row_law():
     assert stats.kstest(a11, stats.beta(1, n - 1).cdf).pvalue > 1e-3
     assert stats.kstest(a12, stats.beta(2, n - 2).cdf).pvalue > 1e-3
     assert stats.kstest(ph, stats.uniform(-math.pi, 2 * math.pi).cdf).pvalue > 1e-3
+
+
+def test_revealed_unitary_trace_moments():
+    """The fully revealed Q at n = 6 against the trace moments of the Haar measure on U(n)
+    (Diaconis and Shahshahani, 1994): for sum_j j a_j <= n, E prod_j |tr Q^j|^{2 a_j} =
+    prod_j j^{a_j} a_j!, and E (tr Q)^2 = E tr Q = 0.  So E |tr Q|^2 = 1, E |tr Q|^4 = 2,
+    E |tr Q|^6 = 6 and E |tr Q^2|^2 = 2.  The queries mix Q and Q^H steps, so both reflector
+    stacks and their adjoints enter the reconstruction.  The queries are the same fixed
+    vectors in every trial, so all the randomness is the draws'; Theorem 2's complex analogue
+    says Q is Haar for any queries independent of it.  (These moments of order <= 6 do not
+    tell U(n) from a real orthogonal factor between fixed unitaries; the law of the draws
+    themselves is pinned by the uniform phase in test_first_row_law.)"""
+    n, trials = 6, 600
+    sched = [False, True, True, False, True, False]
+    rng = np.random.default_rng(3)
+    queries = [rng.standard_normal(n) + 1j * rng.standard_normal(n) for _ in range(n)]
+    t1, t2 = [], []
+    for i in range(trials):
+        o = ComplexHaarOracle(n, n, 500, trial=i)
+        for t in range(n):
+            o.apply(queries[t], sched[t])
+        Q = o.matrix().numpy()
+        t1.append(np.trace(Q))
+        t2.append(np.trace(Q @ Q))
+    t1, t2 = np.array(t1), np.array(t2)
+    a1 = np.abs(t1) ** 2
+    for sample, want in ((t1.real, 0.0), (t1.imag, 0.0), ((t1 ** 2).real, 0.0), (a1, 1.0),
+                         (a1 ** 2, 2.0), (a1 ** 3, 6.0), (np.abs(t2) ** 2, 2.0)):
+        se = sample.std(ddof=1) / np.sqrt(trials)
+        assert abs(sample.mean() - want) <= 4.5 * se, (sample.mean(), want, se)

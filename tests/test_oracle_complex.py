@@ -97,9 +97,9 @@ def test_revealed_unitary_trace_moments():
     E |tr Q|^6 = 6 and E |tr Q^2|^2 = 2.  The queries mix Q and Q^H steps, so both reflector
     stacks and their adjoints enter the reconstruction.  The queries are the same fixed
     vectors in every trial, so all the randomness is the draws'; Theorem 2's complex analogue
-    says Q is Haar for any queries independent of it.  (These moments of order <= 6 do not
-    tell U(n) from a real orthogonal factor between fixed unitaries; the law of the draws
-    themselves is pinned by the uniform phase in test_first_row_law.)"""
+    says Q is Haar for any queries independent of it.  (A planted mistake with real draws
+    still passed these moments at this sample size, so the law of the draws themselves is
+    left to the uniform phase in test_first_row_law.)"""
     n, trials = 6, 600
     sched = [False, True, True, False, True, False]
     rng = np.random.default_rng(3)

@@ -14,6 +14,11 @@ Workloads (sizes as in the paper's experiments and the synthetic benchmark set):
   ista_batch    64 trials of Gin(n, n), n = 200000, T = 50 ISTA iterations (101 products),
                 beta* ~ 0.2 delta_0 + 0.8 N(0, 2^2) (Section 2.1), noise N(0, 0.1^2)
   haar_large    Haar(n), n = 2*10^7, T = 256, all Q, x_1 ~ N(0, I)
+  lasso_ista    Gin(m, n), m = n/2, entries N(0, 1/m), n = 10^7, 50 ISTA iterations
+                (101 products), beta* ~ 0.2 delta_0 + 0.8 N(0, 2^2), noise N(0, 0.1^2)
+                (Section 2.1, the run the paper times)
+  spectral      A = [I_n 0] Q, Q ~ Haar(2n), n = 10^5, xi ~ N(0, I_n), start x ~ N(0, I_n),
+                100 power iterations (Section 2.2)
 """
 import numpy as np
 

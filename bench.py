@@ -10,8 +10,9 @@ headline line; the plain FP64 form is measured on the same workload and reported
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--dtype f32|f64] [--impl reference]
 
---impl reference times the CPU FP64 oracle on the machine's host cores on a bounded sample of
-the same workload (the first products of the trajectory at full n).
+--impl reference times the CPU FP64 oracle on the host cores over the same workload at full
+n: whole trajectories when they fit the run's time bound, else the first products of each,
+with the whole trajectory's time extrapolated from a fitted per-product cost.
 """
 import argparse
 import json

@@ -27,7 +27,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 N_DEFAULT, T_DEFAULT = 10 ** 6, 100
-REFERENCE_BUDGET_S = 180.0   # bound on a whole --impl reference run (warm-up + timed steps)
+REFERENCE_TIME_LIMIT_S = 180.0   # bound on a whole --impl reference run (warm-up + timed steps)
 METRIC = "HD throughput n*T^2/s (Haar n=1e6, T=100, Q/Q^T alternating)"
 UNIT = "n*T^2/s"
 
@@ -89,8 +89,8 @@ def job_throughput(units_per_rank, world, secs):
 
 # ----------------------------------------------------------------------------------------
 # CPU oracle (baseline and reference arm)
-def oracle_sample(n, T, seed, budget_s, max_products=None):
-    """Run the oracle's first products of the workload until budget_s; returns
+def oracle_sample(n, T, seed, time_limit_s, max_products=None):
+    """Run the oracle's first products of the workload until time_limit_s; returns
     (products done, seconds, threads, seconds of each product including its dynamics)."""
     import numpy as np
     import torch
@@ -108,7 +108,7 @@ def oracle_sample(n, T, seed, budget_s, max_products=None):
         y = ora.apply(x, bool(sched[t])).numpy()
         x, xp = f_sign_mem(y, x, xp), x
         per.append(time.perf_counter() - t1)
-        if time.perf_counter() - t0 > budget_s or (max_products and len(per) >= max_products):
+        if time.perf_counter() - t0 > time_limit_s or (max_products and len(per) >= max_products):
             break
     return len(per), time.perf_counter() - t0, torch.get_num_threads(), per
 
@@ -155,16 +155,16 @@ def run_reference(args):
     if world > 1 and rank != 0:
         return
     n, T = args.n, args.T
-    # the whole run (warm-up and timed steps) is bounded by about REFERENCE_BUDGET_S: the
+    # the whole run (warm-up and timed steps) is bounded by about REFERENCE_TIME_LIMIT_S: the
     # first warm-up run sets how many of the T products fit a step's share of it, and every
     # later run times that many
-    share = REFERENCE_BUDGET_S / max(1, args.warmup + args.steps)
-    k, _, _, _ = oracle_sample(n, T, args.seed, budget_s=share)
+    share = REFERENCE_TIME_LIMIT_S / max(1, args.warmup + args.steps)
+    k, _, _, _ = oracle_sample(n, T, args.seed, time_limit_s=share)
     times, samples = [], []
     for i in range(args.warmup + args.steps):
         if i == 0 and args.warmup > 0:
             continue   # the calibration run above is the first warm-up
-        done, secs, thr, per = oracle_sample(n, T, args.seed, budget_s=1e9, max_products=k)
+        done, secs, thr, per = oracle_sample(n, T, args.seed, time_limit_s=1e9, max_products=k)
         if i >= args.warmup:
             times.append(secs)
             samples.append(per)
@@ -748,7 +748,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:   # N = 1 only: the oracle is a single-host baseline
-        done, csecs, thr, per = oracle_sample(n, T, args.seed, budget_s=15.0)
+        done, csecs, thr, per = oracle_sample(n, T, args.seed, time_limit_s=15.0)
         cval, _, how = oracle_throughput(n, T, [per])
         cpu = {"value": cval, "unit": UNIT, "cores": thr, "kind": "oracle",
                "sample": "%s, FP64, wall %.1f s" % (how, csecs)}

@@ -112,12 +112,22 @@ __device__ __forceinline__ void normal_pair(const DrawKey& k, uint64_t j, double
   z1 = r * sn;
 }
 // The same words through 32-bit arithmetic: u = w_hi 2^-32 + ((w_lo >> 11) + 1) 2^-53 equals
-// the 53-bit uniform up to float rounding (relative 2^-24), then Box-Muller in FP32.
+// the 53-bit uniform up to float rounding (relative 2^-24), then Box-Muller in FP32.  Near
+// u1 = 1 the rounded u1 would lose the small quantity 1 - u1 that ln u1 depends on (a normal
+// near zero would then be off by up to about 2^-12), so for u1 >= 1 - 2^-10 ln u1 is formed
+// as log1p(-v) from v = 1 - u1 = (2^53 - 1 - k) 2^-53, which the words give exactly before
+// one float rounding.  That branch is taken by about 3% of warps.
 __device__ __forceinline__ void normal_pair(const DrawKey& k, uint64_t j, float& z0, float& z1) {
   PhiloxOut o = philox4x32_10((uint32_t)j, k.step, k.trial, k.stream, k.k0, k.k1);
-  const float u1 = fmaf((float)o.w[0], 0x1.0p-32f, (float)((o.w[1] >> 11) + 1u) * 0x1.0p-53f);
   const float u2 = fmaf((float)o.w[2], 0x1.0p-32f, (float)((o.w[3] >> 11) + 1u) * 0x1.0p-53f);
-  const float r = sqrtf(-2.0f * logf(u1));
+  float l;
+  if (o.w[0] >= 0xFFC00000u) {
+    const float v = fmaf((float)(0xFFFFFFFFu - o.w[0]), 0x1.0p-32f, (float)(0x1FFFFFu - (o.w[1] >> 11)) * 0x1.0p-53f);
+    l = log1pf(-v);
+  } else {
+    l = logf(fmaf((float)o.w[0], 0x1.0p-32f, (float)((o.w[1] >> 11) + 1u) * 0x1.0p-53f));
+  }
+  const float r = sqrtf(-2.0f * l);
   float sn, cs;
   sincospif(2.0f * u2, &sn, &cs);
   z0 = r * cs;

@@ -44,8 +44,10 @@ def test_philox_words_bit_exact():
     np.testing.assert_array_equal(got, ref.astype(np.uint32))
 
 
-@pytest.mark.parametrize("start,count", [(0, 1000), (1, 999), (77, 4097), (1_000_000, 3)])
+@pytest.mark.parametrize("start,count", [(0, 1000), (1, 999), (77, 4097), (1_000_000, 3), (5, 1 << 23)])
 def test_philox_normals(start, count):
+    """FP64 normals to rounding; FP32 normals within a few float ulps of |z| everywhere,
+    including near z = 0 where u1 is close to 1 (8M draws reach 1 - u1 below 1e-6)."""
     import paper_2101_07464_gb300 as hd
     ref = philox.normals(11, 3, 5, start, count, stream=0)
     o64 = torch.empty(count, dtype=torch.float64, device="cuda")
@@ -54,8 +56,10 @@ def test_philox_normals(start, count):
     hd.hd_philox_normals(11, 3, 5, 0, start, count, "f32", o32)
     torch.cuda.synchronize()
     np.testing.assert_allclose(o64.cpu().numpy(), ref, rtol=0, atol=1e-13)
-    # 32-bit Box-Muller of the same words: absolute error a few float ulps of |z| <= 9
-    np.testing.assert_allclose(o32.double().cpu().numpy(), ref, rtol=0, atol=5e-6)
+    # 32-bit Box-Muller of the same words: a few float ulps of |z|, plus the float rounding of
+    # u2 (up to 2e-7 rad of the angle, times r) and about 7e-7 where ln u1 is taken from the
+    # rounded u1 just below its complement branch
+    np.testing.assert_allclose(o32.double().cpu().numpy(), ref, rtol=6e-7, atol=2e-6)
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])

@@ -1,25 +1,24 @@
 // Allocation-free first product of a fresh matrix: hd_first_product_noalloc.
 //
-// The first product of Algorithm 1 / Algorithm 2 needs no stored reflectors.  For a fresh
-// Q ~ Haar(n), R_1 = H_1(x_1) sends x_1 to ||x_1|| e_1 and L_1 = H_1(g_1) sends e_1 to
-// g_1 / ||g_1|| (the reflector property of Section 3.1), so y_1 = ||x_1|| g_1 / ||g_1||, for
-// Q and for Q^T alike.  For a fresh Q ~ Gin(m, n), Algorithm 1's first step stores
-// v_1 = R_1 e_1 = x_1 / ||x_1|| and u_1 = g_1, so y_1 = (v_1^T x_1) u_1 = ||x_1|| g_1 (g_1 drawn
-// with entry scale sigma, in R^m for Q and R^n for Q^T).  g_1 is the same Philox draw that a
-// new state makes for its step 1, so the result equals hd_create + hd_apply at step 1 up to
-// rounding.
+// The first product of a fresh matrix needs no stored reflectors.  For Q ~ Haar(n) the
+// data-side reflector sends x_1 to ||x_1|| e_1 and the random-side reflector sends e_1 to
+// g_1 / ||g_1||, so y_1 = ||x_1|| g_1 / ||g_1||, for Q and for Q^T alike.  For Q ~ Gin(m, n)
+// the first basis pair is v_1 = x_1 / ||x_1|| and u_1 = g_1, so y_1 = (v_1^T x_1) u_1 =
+// ||x_1|| g_1 (g_1 drawn with entry scale sigma, in R^m for Q and R^n for Q^T).  g_1 is the
+// same Philox draw that a new state makes for its step 1, so the result equals hd_create +
+// hd_apply at step 1 up to rounding.
 //
 // Two kernels on the caller's stream: per-tile partial sums of ||x_1||^2 (and ||g_1||^2 for
 // Haar), the last tile to finish forming the coefficient; then y = coefficient * g_1 with
 // g_1 drawn again.  Their scratch (partials, tile counter, coefficient) is one file-scope
-// device array, found once per device with cudaGetSymbolAddress, so a call allocates no
-// device or host memory.  The scratch is shared by every call on a device: calls that
-// overlap on the device race on it.
+// device array whose device address is looked up on every call with cudaGetSymbolAddress
+// (cheap once the module is loaded, and never stale after a device reset), so a call
+// allocates no device or host memory.  The scratch is shared by every call on a device:
+// calls that overlap on the device race on it.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
-#include <mutex>
 
 #include <cuda_runtime.h>
 
@@ -45,10 +44,6 @@ constexpr int kNaCounter = 2 * kNaMaxTiles + 32;
 constexpr int kNaScratchDoubles = 2 * kNaMaxTiles + 64;    // 66,048 bytes
 
 static __device__ __align__(256) double g_na_scratch[kNaScratchDoubles];
-
-constexpr int kNaMaxDevices = 64;
-std::mutex g_na_mutex;
-double* g_na_ptr[kNaMaxDevices] = {};
 
 __device__ __forceinline__ double na_block_sum(double v, double* red) {
   v = warp_sum(v);
@@ -138,23 +133,13 @@ int na_fail(const char* where, cudaError_t e) {
   return HD_ERR_CUDA;
 }
 
-// Device address of the scratch for the current device, looked up on the first call.
+// Device address of the scratch on the current device.  Looked up on every call rather than
+// cached: the address belongs to the current context, which a device reset replaces.
 int na_scratch(double** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return na_fail("cudaGetDevice", e);
-  if (dev < 0 || dev >= kNaMaxDevices) {
-    record_error_text("hd_first_product_noalloc: device ordinal beyond the 64 supported");
-    return HD_ERR_ARG;
-  }
-  std::lock_guard<std::mutex> lock(g_na_mutex);
-  if (!g_na_ptr[dev]) {
-    double* p = nullptr;
-    e = cudaGetSymbolAddress((void**)&p, g_na_scratch);
-    if (e != cudaSuccess) return na_fail("set-up (cudaGetSymbolAddress)", e);
-    g_na_ptr[dev] = p;
-  }
-  *out = g_na_ptr[dev];
+  double* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress((void**)&p, g_na_scratch);
+  if (e != cudaSuccess) return na_fail("set-up (cudaGetSymbolAddress)", e);
+  *out = p;
   return HD_OK;
 }
 

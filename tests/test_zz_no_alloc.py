@@ -2,8 +2,8 @@
 
 It must give what a new state gives at its first hd_apply (same seed, trial, sigma) within
 the parity tolerances, on two calls in a row on one stream (the second call sees the
-scratch the first one left), allocate no device memory once set up, and reject sizes
-beyond its scratch with a clear error.  This file sorts last so that it also runs after
+scratch the first one left), match the oracle's first product, allocate no device memory,
+and reject sizes beyond its scratch with a clear error.  This file sorts last so that it also runs after
 every other test has used the device.
 """
 import pytest
@@ -75,19 +75,52 @@ def test_largest_size_and_zero_input():
     assert torch.count_nonzero(yz).item() == 0
 
 
+@pytest.mark.parametrize("ens,m,n,transpose", [("haar", 5003, 5003, False), ("ginibre", 3001, 7001, True)])
+def test_matches_oracle_first_product(ens, m, n, transpose):
+    """Directly against the oracle's first product (FP64, same seed and trial)."""
+    import numpy as np
+    import paper_2101_07464_gb300 as hd
+    from oracle.hd import make_oracle
+    nx, ny = (m, n) if transpose else (n, m)
+    sigma = 1.0 if ens == "haar" else m ** -0.5
+    x = synth.x1(nx, 31)
+    y = torch.empty(ny, dtype=torch.float64, device="cuda")
+    hd.hd_first_product_noalloc(ens, "f64", m, n, transpose, 77, 2, sigma, torch.tensor(x, device="cuda"), y)
+    yo = make_oracle(ens, m, n, 1, 77, trial=2, sigma=sigma).apply(x, transpose).numpy()
+    torch.cuda.synchronize()
+    yg = y.cpu().numpy()
+    assert np.abs(yg - yo).max() <= TOL["f64"] * np.abs(yo).max()
+    assert np.linalg.norm(yg - yo) <= TOL["f64"] * np.linalg.norm(yo)
+
+
+def _free_bytes():
+    """Free device memory, read until two readings agree (other users of the device can move
+    it between readings)."""
+    last = None
+    for _ in range(10):
+        torch.cuda.synchronize()
+        f, _ = torch.cuda.mem_get_info()
+        if f == last:
+            return f
+        last = f
+    return last
+
+
 def test_allocates_no_device_memory():
+    """Device memory only (host allocations are not measured here)."""
     import paper_2101_07464_gb300 as hd
     n = 1_000_003
     x = torch.tensor(synth.x1(n, 9), dtype=torch.float64, device="cuda")
     y = torch.empty(n, dtype=torch.float64, device="cuda")
-    hd.hd_first_product_noalloc("haar", "f64", n, n, False, 1, 0, 1.0, x, y)   # set-up call
+    hd.hd_first_product_noalloc("haar", "f64", n, n, False, 1, 0, 1.0, x, y)   # first call on the device
     torch.cuda.synchronize()
-    free0, _ = torch.cuda.mem_get_info()
+    alloc0, res0 = torch.cuda.memory_allocated(), torch.cuda.memory_reserved()
+    free0 = _free_bytes()
     for k in range(20):
         hd.hd_first_product_noalloc("haar", "f64", n, n, k % 2 == 1, k, k, 1.0, x, y)
     torch.cuda.synchronize()
-    free1, _ = torch.cuda.mem_get_info()
-    assert free1 == free0
+    assert torch.cuda.memory_allocated() == alloc0 and torch.cuda.memory_reserved() == res0
+    assert _free_bytes() == free0
 
 
 def test_rejects_oversize_and_bad_arguments():

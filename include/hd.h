@@ -83,6 +83,18 @@ HD_API int hd_create(int ensemble, int64_t m, int64_t n, int32_t T_max, uint64_t
 HD_API int hd_create_batched(int ensemble, int32_t count, const int64_t* m, const int64_t* n,
                              int32_t T_max, uint64_t seed, int dtype, hd_state** out);
 
+/* Engine switches of a state (both off by default), for measurement and for checking one
+ * code path against another; results differ only in the order of floating-point sums.
+ *   HD_ENGINE_NO_FUSE  hd_run keeps the three separate sweeps of every step instead of
+ *                      folding f_t and the next step's dot sweep into the output sweep
+ *   HD_ENGINE_NO_PDL   launch the sweeps without programmatic dependent launch (no early
+ *                      start of a sweep's prologue while its predecessor drains)
+ * Take effect from the next step; a cached hd_run graph is recaptured.  HD_ERR_ARG for an
+ * unknown bit. */
+#define HD_ENGINE_NO_FUSE 1
+#define HD_ENGINE_NO_PDL 2
+HD_API int hd_set_engine(hd_state* st, int flags);
+
 /* Per-trial entry scales of a Gin batch (count values, each finite and > 0): trial i's draws
  * are sigma[i] N(0, 1), i.e. Q_i has entry variance sigma[i]^2 (e.g. 1/m_i for the AMP
  * workload).  Before the first step only (HD_ERR_STATE otherwise); hd_set_options sets every
@@ -114,7 +126,9 @@ HD_API int hd_apply(hd_state* st, const void* x, int transpose, void* y);
  * and *unrevealed_host = the norm of the component of x that the hidden block would see
  * (||Z_{1:r} R_r...R_1 x|| for Q); y equals M x exactly when it is zero, e.g. for any
  * earlier input x_s of the same direction, or Q^T applied to an earlier output.
- * Synchronises the state's stream (the norm is returned on the host). */
+ * Synchronises the state's stream (the norm is returned on the host).  The first probe of a
+ * state allocates a workspace of max(m, n) + 1 doubles that the state keeps (HD_ERR_OOM if
+ * that fails); later probes allocate nothing. */
 HD_API int hd_probe(hd_state* st, const void* x, int transpose, void* y,
                     double* unrevealed_host);
 
@@ -146,6 +160,23 @@ typedef struct {
   const void* aux;           /* HD_DYN_AMP: the noise w (packed m-space vector, device or
                                 page-locked host, copied at the start of every call);
                                 ignored otherwise                                       */
+  /* Trajectory records, all optional (NULL = off).  Each is a device buffer of the state's
+   * dtype holding T rows of ld_rows elements; row t-1 belongs to step t and holds a packed
+   * vector of step t's output space (rows are not padded or cleared beyond that length).
+   * They exist to check the trajectory path step by step: the fused sweeps that hd_run uses
+   * for Q / Q^T alternating schedules never store y_t otherwise.                          */
+  void* y_record;            /* receives y_t = M_t x_t                                   */
+  void* x_record;            /* receives f_t's result as the library computed it: x_{t+1}
+                                (HD_DYN_AMP: z^0, x^1, z^1, ... as each step updates them) */
+  const void* x_given;       /* teacher forcing: row t-1 (t < T) replaces f_t's result as
+                                the input of product t+1 and as the value later steps of
+                                f read (x_{t-1} of sign_mem, x^k / z^k of AMP, whose norm
+                                or nonzero count is then taken of the given vector); row
+                                T-1 is not read, so x_out is f_T's own result.  With
+                                HD_DYN_AMP it needs the fused sweeps (HD_ERR_STATE under
+                                HD_ENGINE_NO_FUSE or reverse-mode recording)            */
+  int64_t ld_rows;           /* elements between rows; >= the longest packed vector of the
+                                state when any record is given (HD_ERR_ARG otherwise)     */
 } hd_run_spec;
 
 /* A whole trajectory of eq. (dynamics): resets the state (same seed, trial and sigma),
@@ -258,6 +289,16 @@ HD_API int hd_get_map_options(const hd_state* st, int32_t* count, int32_t* spc);
 HD_API int hd_goe_apply(hd_state* st, const void* x, void* y);
 HD_API int hd_usv_apply(hd_state* U, hd_state* V, const double* s, const void* x, int transpose, void* y);
 
+/* Measured rate of the FP64 fused multiply-add pipe of the current device, in TFLOP/s (2 flops
+ * per FMA): the roofline of the FP64 form, whose streaming passes are bound by this pipe rather
+ * than by HBM on this GPU.  A measurement helper with no counterpart in the paper.  Runs
+ * reps + 1 launches (the first untimed) of a kernel in which every thread advances 8
+ * independent FMA chains for `iters` iterations over 8 CTAs of 256 threads per SM, timed with
+ * CUDA events on `stream` (NULL = legacy default stream); *tflops_host receives the best
+ * timed launch.  Synchronises the stream; allocates no device memory.  Errors: HD_ERR_ARG
+ * (iters or reps < 1, null output), HD_ERR_CUDA. */
+HD_API int hd_fp64_fma_rate(int32_t iters, int32_t reps, double* tflops_host, void* stream);
+
 /* Number of kernels this state has launched (graph replays count their kernels). */
 HD_API int hd_get_launches(const hd_state* st, int64_t* launches);
 
@@ -327,21 +368,20 @@ HD_API int hd_adjoint_position(const hd_state* st, int32_t* remaining);
  * Computes y = Q x (transpose == 0: x has n entries, y has m) or y = Q^T x (transpose != 0:
  * x has m, y has n) for the matrix that hd_create(ensemble, m, n, T_max, seed, dtype) with
  * options (sigma, trial) would sample, at its step 1: the result equals that state's first
- * hd_apply up to rounding.  By Algorithm 2's first step y = ||x|| g / ||g|| for Haar(n), and
- * by Algorithm 1's first step y = ||x|| g for Gin(m, n), g the step-1 Philox draw (entry
- * scale sigma for Gin; sigma is ignored for Haar).  x and y are device buffers of dtype on
- * the calling thread's current device, not overlapping; work is enqueued on `stream`
- * (NULL = the legacy default stream).
+ * hd_apply up to rounding, namely y = ||x|| g / ||g|| for Haar(n) and y = ||x|| g for
+ * Gin(m, n), g the step-1 Philox draw of the output space (entry scale sigma for Gin; sigma
+ * is ignored for Haar).  x and y are device buffers of dtype on the calling thread's current
+ * device, not overlapping; work is enqueued on `stream` (NULL = the legacy default stream).
  *
  * Scratch: one file-scope device array of 66,048 bytes per device holds the per-tile partial
  * sums, a tile counter and the coefficient, which bounds max(m, n) at 16,777,216 entries.
  * The counter must be zero when the norm kernel starts: every call clears it on `stream`
  * first.  Calls that overlap on one device (on different streams, or from different host
  * threads without ordering) share that array and race on it, giving wrong results: order
- * them on one stream.  The first call on a device does set-up (it looks up the array's
- * device address, which can load the library's device code); a caller that captures the
- * call into a CUDA graph should make one call before beginning the capture.  The call
- * allocates no device or host memory.
+ * them on one stream.  Every call looks up the array's device address on the current device
+ * (cudaGetSymbolAddress); the first lookup on a device can load the library's device code,
+ * so a caller that captures the call into a CUDA graph should make one call before beginning
+ * the capture.  The call allocates no device memory.
  *
  * Errors: HD_ERR_ARG (bad ensemble or dtype, NULL x or y, m or n <= 0, Gin sigma not finite
  * and positive), HD_ERR_DIM (Haar with m != n; max(m, n) above 16,777,216, with the limit in

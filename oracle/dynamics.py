@@ -57,34 +57,77 @@ def run(state, x1, T, f, schedule, x0=None):
     return xs, ys
 
 
+def run_trace(state, x1, T, f, schedule, cast=None):
+    """Iterate eq. (dynamics) for T steps, x_0 = 0, recording what each product consumed.
+
+    cast (optional) rounds x_1 and every result of f before the next product uses it, so that
+    a lower-precision implementation can be handed exactly the same inputs (teacher forcing).
+    Returns (xs, ys, fs): xs[t-1] = x_t as fed to product t, ys[t-1] = M_t x_t and
+    fs[t-1] = f's result after step t, before rounding.  x_{t-1} enters f as the zero vector
+    of y_t's space when its own dimension differs (first step of a rectangular schedule).
+    """
+    c = cast if cast is not None else (lambda v: np.asarray(v, dtype=np.float64))
+    x = c(x1)
+    x_prev = np.zeros_like(x)
+    xs, ys, fs = [], [], []
+    for t in range(1, T + 1):
+        y = np.asarray(state.apply(x, transpose=schedule(t)), dtype=np.float64)
+        xp = x_prev if x_prev.shape == y.shape else np.zeros_like(y)
+        fx = f(y, x, xp)
+        xs.append(x)
+        ys.append(y)
+        fs.append(fx)
+        x_prev, x = x, c(fx)
+    return xs, ys, fs
+
+
 def soft_threshold(r, theta):
     return np.sign(r) * np.maximum(np.abs(r) - theta, 0.0)
 
 
-def amp(state, beta, w, T, thr=1.1):
-    """T products of AMP for the linear model y = Q beta + w, Q in R^{m x n}.
+def amp_trace(state, beta, w, T, thr=1.1, cast=None):
+    """T products of AMP for the linear model y = Q beta + w, Q in R^{m x n}, step by step.
 
     Product 1 is Q beta (then y = Q beta + w, z^0 = y, x^0 = 0); after that the products
     alternate Q^T z^k (even t) and Q x^{k+1} (odd t):
         x^{k+1} = eta(x^k + Q^T z^k; theta_k),  theta_k = thr * ||z^k|| / sqrt(m)
         z^{k+1} = y - Q x^{k+1} + z^k ||x^{k+1}||_0 / m      (the Onsager term)
-    with eta the soft threshold.  Returns (xs, zs): the x^k after each Q^T product and the
-    z^k (z^0 first).
+    with eta the soft threshold.  cast (optional) rounds each updated vector before anything
+    uses it (teacher forcing of a lower-precision implementation); y keeps full precision.
+    Returns a dict of per-step lists: products[t-1] = the t-th product, updates[t-1] = the
+    vector step t updates (z^0, x^1, z^1, x^2, ...) and used[t-1] = that vector after cast.
     """
+    c = cast if cast is not None else (lambda v: v)
     beta = np.asarray(beta, dtype=np.float64)
     w = np.asarray(w, dtype=np.float64)
     m = w.shape[0]
-    y = np.asarray(state.apply(beta, transpose=False), dtype=np.float64) + w
-    z = y.copy()
+    q = np.asarray(state.apply(beta, transpose=False), dtype=np.float64)
+    y = q + w
+    z = c(y.copy())
     x = np.zeros_like(beta)
-    xs, zs = [], [z]
+    tr = {"products": [q], "updates": [y.copy()], "used": [z]}
     for t in range(2, T + 1):
         if t % 2 == 0:
-            r = x + np.asarray(state.apply(z, transpose=True), dtype=np.float64)
-            x = soft_threshold(r, thr * np.linalg.norm(z) / np.sqrt(m))
-            xs.append(x)
+            s = np.asarray(state.apply(z, transpose=True), dtype=np.float64)
+            x_new = soft_threshold(x + s, thr * np.linalg.norm(z) / np.sqrt(m))
+            tr["products"].append(s)
+            tr["updates"].append(x_new)
+            x = c(x_new)
+            tr["used"].append(x)
         else:
             q = np.asarray(state.apply(x, transpose=False), dtype=np.float64)
-            z = y - q + z * (np.count_nonzero(x) / m)
-            zs.append(z)
+            z_new = y - q + z * (np.count_nonzero(x) / m)
+            tr["products"].append(q)
+            tr["updates"].append(z_new)
+            z = c(z_new)
+            tr["used"].append(z)
+    return tr
+
+
+def amp(state, beta, w, T, thr=1.1):
+    """T products of AMP (amp_trace without rounding).  Returns (xs, zs): the x^k after each
+    Q^T product and the z^k (z^0 first)."""
+    tr = amp_trace(state, beta, w, T, thr)
+    xs = [v for t, v in enumerate(tr["used"], start=1) if t % 2 == 0]
+    zs = [v for t, v in enumerate(tr["used"], start=1) if t % 2 == 1]
     return xs, zs

@@ -27,7 +27,10 @@ DYNAMICS = {"tanh": HD_DYN_TANH, "sign_mem": HD_DYN_SIGN_MEM, "norm_tanh": HD_DY
 class hd_run_spec(ctypes.Structure):
     _fields_ = [("T", ctypes.c_int32), ("transpose", ctypes.POINTER(ctypes.c_uint8)),
                 ("dynamics", ctypes.c_int32), ("a", ctypes.c_double), ("use_graph", ctypes.c_int32),
-                ("aux", ctypes.c_void_p)]
+                ("aux", ctypes.c_void_p), ("y_record", ctypes.c_void_p), ("x_record", ctypes.c_void_p),
+                ("x_given", ctypes.c_void_p), ("ld_rows", ctypes.c_int64)]
+
+HD_ENGINE_NO_FUSE, HD_ENGINE_NO_PDL = 1, 2
 
 _c = ctypes
 _P = _c.c_void_p
@@ -39,6 +42,8 @@ _PROTOS = {
                                      _c.POINTER(_P)]),
     "hd_get_batch_layout": (_c.c_int, [_P, _c.POINTER(_c.c_int32), _P, _P]),
     "hd_set_trial_sigmas": (_c.c_int, [_P, _P]),
+    "hd_set_engine": (_c.c_int, [_P, _c.c_int]),
+    "hd_fp64_fma_rate": (_c.c_int, [_c.c_int32, _c.c_int32, _c.POINTER(_c.c_double), _P]),
     "hd_adjoint_enable": (_c.c_int, [_P, _c.c_int]),
     "hd_adjoint_step": (_c.c_int, [_P, _P, _P, _P]),
     "hd_adjoint_restart": (_c.c_int, [_P]),
@@ -219,18 +224,60 @@ def hd_probe(state, x, transpose, y):
     return u.value
 
 
-def make_run_spec(transpose_flags, dynamics, a=0.0, use_graph=True, aux=None):
+def _rows_addr(t, what):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if not t.is_cuda or not t.is_contiguous() or t.dim() != 2:
+        raise ValueError("%s must be a contiguous 2-D CUDA tensor (T rows)" % what)
+    return t.data_ptr()
+
+
+def make_run_spec(transpose_flags, dynamics, a=0.0, use_graph=True, aux=None, y_record=None,
+                  x_record=None, x_given=None):
     """hd_run_spec for a schedule (sequence of 0/1 flags) and a built-in dynamics name/code.
-    aux: HD_DYN_AMP's noise vector w (CUDA or page-locked tensor, or an address)."""
+    aux: HD_DYN_AMP's noise vector w (CUDA or page-locked tensor, or an address).
+    y_record / x_record / x_given: optional T x L CUDA tensors of the state's dtype (row t-1
+    for step t; L >= the longest packed vector): records of y_t and of f_t's result, and
+    teacher-forced replacements of f_t's result (hd_run_spec)."""
     flags = (ctypes.c_uint8 * len(transpose_flags))(*[1 if f else 0 for f in transpose_flags])
     aux_addr = None
     if aux is not None:
         aux_addr = aux if isinstance(aux, int) else aux.data_ptr()
+    rows = [r for r in (y_record, x_record, x_given) if r is not None]
+    ld = 0
+    for r in rows:
+        if isinstance(r, int):
+            raise ValueError("record buffers must be tensors")
+        if r.shape[0] < len(transpose_flags):
+            raise ValueError("record buffers need one row per step")
+        if ld and r.stride(0) != ld:
+            raise ValueError("record buffers must share one row length")
+        ld = r.stride(0)
     spec = hd_run_spec(len(transpose_flags), ctypes.cast(flags, ctypes.POINTER(ctypes.c_uint8)),
-                       DYNAMICS.get(dynamics, dynamics), float(a), 1 if use_graph else 0, aux_addr)
+                       DYNAMICS.get(dynamics, dynamics), float(a), 1 if use_graph else 0, aux_addr,
+                       _rows_addr(y_record, "y_record"), _rows_addr(x_record, "x_record"),
+                       _rows_addr(x_given, "x_given"), int(ld))
     spec._flags = flags  # keep the array alive with the struct
     spec._aux = aux
+    spec._rows = rows
     return spec
+
+
+def hd_fp64_fma_rate(iters=1 << 16, reps=5, stream=None):
+    """Measured FP64 FMA pipe rate of the current device in TFLOP/s (hd_fp64_fma_rate)."""
+    out = ctypes.c_double()
+    _check(lib().hd_fp64_fma_rate(int(iters), int(reps), ctypes.byref(out), _stream_ptr(stream)),
+           "hd_fp64_fma_rate")
+    return out.value
+
+
+def hd_set_engine(state, no_fuse=False, no_pdl=False):
+    """Engine switches (hd_set_engine): keep hd_run's separate sweeps, or launch without
+    programmatic dependent launch."""
+    flags = (HD_ENGINE_NO_FUSE if no_fuse else 0) | (HD_ENGINE_NO_PDL if no_pdl else 0)
+    _check(lib().hd_set_engine(state, flags), "hd_set_engine")
 
 
 def hd_run(state, spec, x1, x_out):

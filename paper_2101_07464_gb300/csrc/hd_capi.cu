@@ -108,6 +108,12 @@ BatchStep<T> make_batch(const hd_state* st, int d, int kD, int kN, const void* x
   return b;
 }
 
+// Row t (0-based) of one of hd_run's optional trajectory buffers (null when not given).
+void* run_row(const hd_state* st, void* base, const hd_run_spec* sp, int t) {
+  if (!base) return nullptr;
+  return (char*)base + (size_t)t * (size_t)sp->ld_rows * st->esz;
+}
+
 template <typename T>
 int first_draws(hd_state* st) {
   BatchStep<T> b = make_batch<T>(st, 0, 0, 0, nullptr, nullptr);
@@ -133,6 +139,9 @@ struct FuseSpec {
   void* amp_v = nullptr;
   void* amp_y = nullptr;
   const void* amp_w = nullptr;
+  void* yrec = nullptr;        // trajectory records of this step's row (hd_run_spec)
+  void* xrec = nullptr;
+  const void* xgiven = nullptr;
 };
 
 template <typename T>
@@ -165,6 +174,9 @@ int do_step(hd_state* st, const void* x, int transpose, void* y, const FuseSpec*
       b.base.amp_w = (const T*)fs->amp_w;
       b.base.amp_zsq = st->amp_zsq;
       b.base.amp_nnz = st->amp_nnz;
+      b.base.yrec = (T*)fs->yrec;
+      b.base.xrec = (T*)fs->xrec;
+      b.base.xgiven = (const T*)fs->xgiven;
       b.base.y = nullptr;
       if (st->ens == HD_HAAR)
         b.base.c3 = make_sweep<T>(st, 4, kN, 2, kN, 1);
@@ -219,19 +231,23 @@ int do_probe(hd_state* st, const void* x, int transpose, void* y, double* unreve
   const int kN = (st->ens == HD_HAAR) ? st->t : cnt[1 - d];
   BatchStep<T> b = make_batch<T>(st, d, kD, kN, x, y);
   b.base.pdl = 0;
-  const int64_t dimD = st->dims[d][0];
-  double* q = nullptr;
-  if (cudaMalloc(&q, (size_t)(dimD + 1) * 8) != cudaSuccess) {
-    set_error("hd_probe cudaMalloc", cudaGetLastError());
-    return HD_ERR_OOM;
+  // workspace of max(m, n) + 1 doubles, allocated by the first probe and kept by the state
+  if (!st->probe_ws) {
+    const int64_t dmax = std::max(st->dims[0][0], st->dims[1][0]);
+    st->probe_ws = (double*)dalloc(st, (size_t)(dmax + 1) * 8);
+    if (!st->probe_ws) {
+      set_error("hd_probe workspace", cudaErrorMemoryAllocation);
+      return HD_ERR_OOM;
+    }
   }
+  const int64_t dimD = st->dims[d][0];
+  double* q = st->probe_ws;
   double* unrev = q + dimD;
   cudaError_t e = cudaMemsetAsync(unrev, 0, 8, st->stream);
   if (e == cudaSuccess) e = launch_probe<T>(b, q, unrev, st->stream);
   double u2 = 0.0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&u2, unrev, 8, cudaMemcpyDeviceToHost, st->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st->stream);
-  cudaFree(q);
   if (e != cudaSuccess) return cuda_fail(st, e);
   *unrevealed_host = std::sqrt(u2);
   return HD_OK;
@@ -245,7 +261,7 @@ int run_steps(hd_state* st, const hd_run_spec* sp) {
   if (int rc = adj_on_reset(st)) return rc;
   int cur = 0;
   // elementwise dynamics of a Q / Q^T alternating schedule: the output sweep of step t applies
-  // f_t and forms step t+1's dot sweep (HD_DISABLE_FUSE=1 turns this off)
+  // f_t and forms step t+1's dot sweep (HD_ENGINE_NO_FUSE turns this off)
   // (a state recording for reverse mode keeps the unfused steps: their workspace holds each
   // step's own dots when the step is recorded)
   const bool fusable = (sp->dynamics == HD_DYN_TANH || sp->dynamics == HD_DYN_SIGN_MEM) && st->fuse &&
@@ -260,6 +276,9 @@ int run_steps(hd_state* st, const hd_run_spec* sp) {
     fs.a = sp->a;
     fs.xnext = st->xw[1 - cur];
     fs.xprev = st->xw[1 - cur];
+    fs.yrec = run_row(st, sp->y_record, sp, t);
+    fs.xrec = run_row(st, sp->x_record, sp, t);
+    fs.xgiven = (t + 1 < sp->T) ? run_row(st, const_cast<void*>(sp->x_given), sp, t) : nullptr;
     int rc = do_step<T>(st, st->xw[cur], tr, st->yw, &fs);
     if (rc) return rc;
     prev_fused = fs.fuse;
@@ -273,6 +292,14 @@ int run_steps(hd_state* st, const hd_run_spec* sp) {
                                        st->sumsq, st->stream, st->pdl != 0);
     if (e != cudaSuccess) return cuda_fail(st, e);
     st->launches += (sp->dynamics == HD_DYN_NORM_TANH) ? 2 : 1;
+    // records and teacher forcing of an unfused step: plain stream-ordered copies
+    const size_t bytes = (size_t)nout * st->esz;
+    if (fs.yrec) e = cudaMemcpyAsync(fs.yrec, st->yw, bytes, cudaMemcpyDeviceToDevice, st->stream);
+    if (e == cudaSuccess && fs.xrec)
+      e = cudaMemcpyAsync(fs.xrec, st->xw[1 - cur], bytes, cudaMemcpyDeviceToDevice, st->stream);
+    if (e == cudaSuccess && fs.xgiven)
+      e = cudaMemcpyAsync(st->xw[1 - cur], fs.xgiven, bytes, cudaMemcpyDeviceToDevice, st->stream);
+    if (e != cudaSuccess) return cuda_fail(st, e);
     cur = 1 - cur;
   }
   st->run_final = cur;
@@ -305,11 +332,22 @@ int run_amp(hd_state* st, const hd_run_spec* sp) {
     fs.amp_v = (mode == 2) ? st->amp_x : st->amp_z;
     fs.amp_y = st->amp_y;
     fs.amp_w = st->amp_w;
+    fs.yrec = run_row(st, sp->y_record, sp, t - 1);
+    fs.xrec = run_row(st, sp->x_record, sp, t - 1);
+    fs.xgiven = (t < sp->T) ? run_row(st, const_cast<void*>(sp->x_given), sp, t - 1) : nullptr;
+    // teacher forcing replaces the AMP vector inside the fused sweep, which also forms the
+    // per-trial norm or count of the replacement; the stand-alone AMP kernels do not
+    if (fs.xgiven && !fs.fuse) return HD_ERR_STATE;
     const void* xin = (mode == 1) ? st->xw[0] : ((mode == 2) ? st->amp_z : st->amp_x);
     int rc = do_step<T>(st, xin, mode == 2 ? 1 : 0, st->yw, &fs);
     if (rc) return rc;
     prev_fused = fs.fuse;
     if (fs.fuse) continue;
+    const int64_t nout = st->off[mode == 2 ? 0 : 1][cnt];
+    if (fs.yrec) {
+      e = cudaMemcpyAsync(fs.yrec, st->yw, (size_t)nout * st->esz, cudaMemcpyDeviceToDevice, st->stream);
+      if (e != cudaSuccess) return cuda_fail(st, e);
+    }
     if (mode == 1)
       e = launch_amp_init<T>(cnt, st->d_off[1], (const T*)st->yw, (const T*)st->amp_w, (T*)st->amp_y,
                              (T*)st->amp_z, st->amp_zsq, st->stream);
@@ -321,6 +359,11 @@ int run_amp(hd_state* st, const hd_run_spec* sp) {
                           st->amp_zsq, st->stream);
     if (e != cudaSuccess) return cuda_fail(st, e);
     st->launches += 1;
+    if (fs.xrec) {
+      e = cudaMemcpyAsync(fs.xrec, mode == 2 ? st->amp_x : st->amp_z, (size_t)nout * st->esz,
+                          cudaMemcpyDeviceToDevice, st->stream);
+      if (e != cudaSuccess) return cuda_fail(st, e);
+    }
   }
   return HD_OK;
 }
@@ -359,6 +402,9 @@ bool graph_matches(const hd_state* st, const hd_run_spec* sp) {
   if (st->g_sigma_gen != st->sigma_gen) return false;
   if (st->g_tune_gen != st->tune_gen) return false;
   if (st->g_stream != st->stream || st->g_prof != st->prof_on) return false;
+  if (st->g_rows[0] != sp->y_record || st->g_rows[1] != sp->x_record || st->g_rows[2] != sp->x_given ||
+      st->g_ld_rows != sp->ld_rows)
+    return false;
   for (int t = 0; t < sp->T; t++)
     if (st->g_flags[t] != (sp->transpose[t] ? 1 : 0)) return false;
   return true;
@@ -475,12 +521,6 @@ int create_common(int ensemble, int count, const int64_t* m, const int64_t* n, i
   }
   cudaDeviceGetAttribute(&st->nsm, cudaDevAttrMultiProcessorCount, st->device);
   if (st->nsm <= 0) st->nsm = 1;
-  {
-    const char* env = getenv("HD_DISABLE_PDL");
-    st->pdl = (env && env[0] == '1') ? 0 : 1;
-    const char* envf = getenv("HD_DISABLE_FUSE");
-    st->fuse = (envf && envf[0] == '1') ? 0 : 1;
-  }
   cudaDeviceGetAttribute(&st->smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, st->device);
   cudaDeviceGetAttribute(&st->smem_blk_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, st->device);
   {
@@ -731,6 +771,15 @@ HD_API int hd_set_options(hd_state* st, double sigma, uint32_t trial, void* stre
   return HD_OK;
 }
 
+HD_API int hd_set_engine(hd_state* st, int flags) {
+  if (!st) return HD_ERR_ARG;
+  if (flags & ~(HD_ENGINE_NO_FUSE | HD_ENGINE_NO_PDL)) return HD_ERR_ARG;
+  st->fuse = (flags & HD_ENGINE_NO_FUSE) ? 0 : 1;
+  st->pdl = (flags & HD_ENGINE_NO_PDL) ? 0 : 1;
+  st->tune_gen += 1;   // a cached trajectory graph was captured with the old launches
+  return HD_OK;
+}
+
 HD_API int hd_set_trial_sigmas(hd_state* st, const double* sigma) {
   if (!st || !sigma) return HD_ERR_ARG;
   if (st->t > 0) return HD_ERR_STATE;
@@ -767,6 +816,13 @@ HD_API int hd_run(hd_state* st, const hd_run_spec* sp, const void* x1, void* x_o
       if ((sp->transpose[t] ? 1 : 0) != (t % 2)) return HD_ERR_ARG;   // Q, Q^T, Q, ...
   }
   if (!std::isfinite(sp->a)) return HD_ERR_ARG;
+  if (sp->y_record || sp->x_record || sp->x_given) {
+    const int64_t need = std::max(st->off[0][st->count], st->off[1][st->count]);
+    if (sp->ld_rows < need) return HD_ERR_ARG;
+    const void* rows[3] = {sp->y_record, sp->x_record, sp->x_given};
+    for (int i = 0; i < 3; i++)
+      if (rows[i] && ((uintptr_t)rows[i] % st->esz) != 0) return HD_ERR_ARG;
+  }
   // dimensions: input of step t+1 = output of step t for every trial
   for (int t = 0; t + 1 < sp->T; t++) {
     const int so = sp->transpose[t] ? 0 : 1, si = sp->transpose[t + 1] ? 1 : 0;
@@ -851,6 +907,10 @@ HD_API int hd_run(hd_state* st, const hd_run_spec* sp, const void* x1, void* x_o
       for (auto& f : st->g_flags) f = f ? 1 : 0;
       st->g_final = st->run_final;
       st->g_prof = st->prof_on;
+      st->g_rows[0] = sp->y_record;
+      st->g_rows[1] = sp->x_record;
+      st->g_rows[2] = sp->x_given;
+      st->g_ld_rows = sp->ld_rows;
     }
     e = cudaGraphLaunch(st->gexec, st->stream);
     if (e != cudaSuccess) {

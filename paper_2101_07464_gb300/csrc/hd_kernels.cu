@@ -139,6 +139,9 @@ __device__ __forceinline__ StepPlan<T> make_plan(const BatchStep<T>& b, int spac
   p.amp_v = b.base.amp_v ? b.base.amp_v + td.off[1 - d] : nullptr;
   p.amp_y = b.base.amp_y ? b.base.amp_y + td.off[1 - d] : nullptr;
   p.amp_w = b.base.amp_w ? b.base.amp_w + td.off[1 - d] : nullptr;
+  p.yrec = b.base.yrec ? b.base.yrec + td.off[1 - d] : nullptr;
+  p.xrec = b.base.xrec ? b.base.xrec + td.off[1 - d] : nullptr;
+  p.xgiven = b.base.xgiven ? b.base.xgiven + td.off[1 - d] : nullptr;
   return p;
 }
 
@@ -236,8 +239,11 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
 }
 
 // One staging round: the CTA's threads issue bulk copies (issue(tid) returns nothing), thread 0
-// posts the byte count; everyone waits, at most kStageSpins polls, for the copies.  On a
-// timeout the error word is set and false returned (the caller then skips the product).
+// posts the byte count and waits, at most kStageSpins polls, for the copies; the outcome is
+// one decision for the whole CTA.  On a timeout the error word is set, thread 0 gives the
+// copies still in flight a second bounded wait (a CTA must not exit with bulk copies into its
+// shared memory outstanding), and false is returned: the caller skips the product, and the
+// state is poisoned (its outputs are undefined) until hd_reset.
 constexpr unsigned kStageSpins = 1u << 22;
 struct Stager {
   uint64_t* bar;
@@ -253,17 +259,28 @@ struct Stager {
     issue();
   }
   __device__ bool finish() {
-    unsigned spins = 0;
-    bool ok = true;
-    while (!mbar_test(bar, parity)) {
-      if (++spins > limit) {
-        ok = false;
-        if (threadIdx.x == 0 && err) atomicOr(err, 1u);
-        break;
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
+      unsigned spins = 0;
+      bool ok = true;
+      while (!mbar_test(bar, parity)) {
+        if (++spins > limit) {
+          ok = false;
+          break;
+        }
       }
+      if (!ok) {
+        if (err) atomicOr(err, 1u);
+        unsigned drain = 0;
+        while (!mbar_test(bar, parity) && ++drain <= limit) {
+        }
+      }
+      s_ok = ok ? 1 : 0;
     }
-    parity ^= 1u;
     __syncthreads();
+    const bool ok = s_ok != 0;
+    parity ^= 1u;
+    __syncthreads();   // s_ok is reused by the next round
     return ok;
   }
   template <typename Issue>
@@ -1249,6 +1266,9 @@ __global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_out_haar(BatchSte
           T xn = T(0);
           if (r < dim) {
             xn = fused_dyn<T>(p.dyn, p.dyn_a, yi, need_prev ? sm.srow(st, 1)[lane] : T(0));
+            if (p.yrec) p.yrec[r] = yi;
+            if (p.xrec) p.xrec[r] = xn;
+            if (p.xgiven) xn = p.xgiven[r];
             p.xnext[r] = xn;
           }
           xv[lane] = xn;
@@ -1378,20 +1398,22 @@ __global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_out_gin(BatchStep
             if (amode == 1) {          // y = Q beta + w; z = y
               xn = yi + sm.srow(st, 1)[lane];
               p.amp_y[r] = xn;
-              p.amp_v[r] = xn;
-              ex[1] = fma(xn, xn, ex[1]);
             } else if (amode == 2) {   // x = eta(x + Q^T z; theta)
               const T v = sm.srow(st, 1)[lane] + yi;
               const T m = fabs(v) - amp_s;
               xn = (m > T(0)) ? copysign(m, v) : T(0);
-              p.amp_v[r] = xn;
-              ex[1] += (xn != T(0)) ? T(1) : T(0);
             } else if (amode == 3) {   // z = y - Q x + z ||x||_0 / m
               xn = fma(sm.srow(st, 1)[lane], amp_s, sm.srow(st, 2)[lane] - yi);
-              p.amp_v[r] = xn;
-              ex[1] = fma(xn, xn, ex[1]);
             } else {
               xn = fused_dyn<T>(p.dyn, p.dyn_a, yi, need_prev ? sm.srow(st, 1)[lane] : T(0));
+            }
+            if (p.yrec) p.yrec[r] = yi;
+            if (p.xrec) p.xrec[r] = xn;
+            if (p.xgiven) xn = p.xgiven[r];
+            if (amp) {
+              p.amp_v[r] = xn;
+              ex[1] = (amode == 2) ? ex[1] + ((xn != T(0)) ? T(1) : T(0)) : fma(xn, xn, ex[1]);
+            } else {
               p.xnext[r] = xn;
             }
           }

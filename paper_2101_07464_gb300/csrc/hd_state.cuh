@@ -104,8 +104,8 @@ struct hd_state {
   unsigned int* cnt = nullptr;
   size_t cnt_bytes = 0;
   int nsm = 1;
-  int pdl = 1;                   // programmatic dependent launch of the sweeps (HD_DISABLE_PDL=1: off)
-  int fuse = 1;                  // fused output + dynamics + dot sweeps in hd_run (HD_DISABLE_FUSE=1: off)
+  int pdl = 1;                   // programmatic dependent launch of the sweeps (hd_set_engine)
+  int fuse = 1;                  // fused output + dynamics + dot sweeps in hd_run (hd_set_engine)
   int occ_regs[6] = {1, 1, 1, 1, 1, 1};  // CTAs of 256 threads per SM allowed by registers, per sweep kernel
   int static_smem[6] = {0, 0, 0, 0, 0, 0};   // (dots, update, out Haar, out Gin, fused out Haar, fused out Gin)
   int smem_sm = 0;
@@ -117,6 +117,7 @@ struct hd_state {
   void* yw = nullptr;
   void* ens_tmp[2] = {nullptr, nullptr};   // hd_goe_apply / hd_usv_apply intermediates
   double* sumsq = nullptr;
+  double* probe_ws = nullptr;    // hd_probe: max(m, n) + 1 doubles (allocated by the first probe)
   int run_final = 0;
   cudaStream_t own_stream = nullptr;
   cudaGraphExec_t gexec = nullptr;
@@ -131,6 +132,8 @@ struct hd_state {
   int g_launches = 0;
   int g_prof = 0;
   int64_t g_tune_gen = -1;
+  const void* g_rows[3] = {nullptr, nullptr, nullptr};   // hd_run_spec record / teacher buffers
+  int64_t g_ld_rows = 0;
   int64_t launches = 0;          // kernel launches issued (graph replays count their kernels)
   // profiling: event pairs around each sweep, algorithmic bytes of each recorded launch
   int prof_on = 0;

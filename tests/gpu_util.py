@@ -47,3 +47,41 @@ def teacher_forced(ens, m, n, T, seed, dtype, schedule, sigma=1.0, x1=None, dyna
     finally:
         gpu.close()
     return np.array(errs)
+
+
+def f32_cast(v):
+    """Round a float64 vector to the nearest FP32 values (kept as float64)."""
+    return np.asarray(v, dtype=np.float64).astype(np.float32).astype(np.float64)
+
+
+def oracle_trajectory(ens, m, n, T, seed, schedule, f, x1, sigma=1.0, cast=None, trial=0):
+    """The oracle's own trajectory (oracle.dynamics.run_trace on a fresh oracle state):
+    (xs, ys, fs) with xs[t-1] = x_t as fed to product t, ys[t-1] = y_t and fs[t-1] = f's
+    result after step t before rounding by cast."""
+    from oracle.dynamics import run_trace
+    ora = make_oracle(ens, m, n, T, seed, trial=trial, sigma=sigma)
+    return run_trace(ora, x1, T, f, schedule, cast=cast)
+
+
+def elem_err(a, b, head):
+    """Element-wise error of one step's output: rows below `head` (the pivot rows that the
+    step's reflectors have fixed, t of them after step t) relative to ||b||_2, the other rows
+    relative to max_i |b_i|.  The oracle forms each pivot row by applying eq. Householder
+    literally, as the difference of two terms of the size of ||x_t|| (H(a) a = ||a|| e_1), so
+    its own rounding there scales with the vector norm and the length of its dot products
+    (1.2e-11 absolute at n = 10^6, ||x|| = 10^3, with the GPU host's BLAS); the other rows
+    carry rounding on the scale of the entries."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    d = np.abs(a - b)
+    h = min(int(head), b.shape[0])
+    tail = d[h:].max() / np.abs(b).max() if h < b.shape[0] else 0.0
+    hd_ = d[:h].max() / np.linalg.norm(b) if h > 0 else 0.0
+    return float(max(tail, hd_))
+
+
+def max_rel(a, b):
+    """max_i |a_i - b_i| / max_i |b_i| (element-wise error on the scale of the vector)."""
+    b = np.asarray(b, dtype=np.float64)
+    s = np.abs(b).max()
+    return float(np.abs(np.asarray(a, dtype=np.float64) - b).max() / s) if s > 0 else float(np.abs(a).max())

@@ -4,7 +4,8 @@
   the oracle's torch float64 autograd on the same seed (relative 1e-9): Haar and Ginibre, Q /
   Q^T alternating, all Q, mixed schedules, rectangular both ways, several CTAs.
 * They equal central finite differences of the GPU FP64 forward (relative 1e-6).
-* The FP32 reverse mode agrees with the FP64 one to 1e-4 (relative).
+* The FP32 reverse mode agrees with the oracle's FP64 autograd and with the FP64 reverse mode
+  to 1e-4 (relative).
 * Segment checkpointing (recompute with hd_probe) gives the recorded result.
 """
 import numpy as np
@@ -99,6 +100,27 @@ def test_fp64_adjoint_matches_oracle_autograd(ens, m, n, T, schedf, f):
     assert rel(gx, ox) <= 1e-9, rel(gx, ox)
     assert rel(gt, ot) <= 1e-9, rel(gt, ot)
     assert rel(gb, ob) <= 1e-9, (gb, ob)
+
+
+def _f32(v):
+    return np.asarray(v, dtype=np.float64).astype(np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("ens,m,n,T,schedf,f", CASES + [
+    ("haar", 100_003, 100_003, 16, ALT, f_theta),
+    ("ginibre", 40_000, 70_001, 12, ALT, f_theta)])
+def test_fp32_adjoint_matches_oracle_autograd(ens, m, n, T, schedf, f):
+    """The FP32 reverse mode (FP32 stacks and passes, FP64 sums and coefficients) against the
+    oracle's FP64 autograd on the same FP32-representable inputs, relative 1e-4."""
+    sched, x1, theta, beta, c = _case(ens, m, n, T, schedf, seed=5)
+    x1, theta, c = _f32(x1), _f32(theta), _f32(c)
+    beta = float(np.float32(beta))
+    Lg, gx, gt, gb = gpu_grads(ens, m, n, T, sched, f, x1, theta, beta, c, "f32")
+    Lo, ox, ot, ob = oracle_grads(ens, m, n, T, sched, f, x1, theta, beta, c)
+    assert abs(Lg - Lo) <= 1e-4 * max(1.0, abs(Lo)), (Lg, Lo)
+    assert rel(gx, ox) <= 1e-4, rel(gx, ox)
+    assert rel(gt, ot) <= 1e-4, rel(gt, ot)
+    assert rel(gb, ob) <= 1e-4, (gb, ob)
 
 
 @pytest.mark.parametrize("ens,m,n,T,schedf,f", [CASES[0], CASES[3], CASES[6]])

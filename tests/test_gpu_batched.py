@@ -97,9 +97,8 @@ def test_batch_of_one_is_single_state(ens):
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 @pytest.mark.parametrize("graph", [False, True])
-def test_batched_run_matches_apply(dtype, graph, monkeypatch):
+def test_batched_run_matches_apply(dtype, graph):
     import paper_2101_07464_gb300 as hd
-    monkeypatch.setenv("HD_DISABLE_FUSE", "1")   # bit-exact comparison: the unfused path
     tdt = torch.float64 if dtype == "f64" else torch.float32
     ns = [10_007, 31, 65_536, 4099]
     T, a = 14, 0.5
@@ -107,6 +106,7 @@ def test_batched_run_matches_apply(dtype, graph, monkeypatch):
     x1 = torch.tensor(np.concatenate([synth.x1(n, 8, trial=i) for i, n in enumerate(ns)]),
                       dtype=tdt, device="cuda")
     b = hd.HDBatch("haar", ns, ns, T, 8, dtype, trial=2)
+    hd.hd_set_engine(b.h, no_fuse=True)   # bit-exact comparison: the unfused path
     x, xp = x1.clone(), torch.zeros_like(x1)
     for t in range(T):
         y = b.apply(x, flags[t])

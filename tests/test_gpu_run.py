@@ -44,7 +44,7 @@ def _manual(ens, m, n, T, seed, dtype, flags, dyn, a, sigma):
     ("haar", 4099, 4099, "norm_tanh", 0.1, "allq"),
     ("ginibre", 3001, 3001, "tanh", 0.0, "allq"),
     ("ginibre", 2001, 5003, "tanh", 0.0, "alt")])
-def test_run_matches_apply(dtype, graph, ens, m, n, dyn, a, pattern, monkeypatch):
+def test_run_matches_apply(dtype, graph, ens, m, n, dyn, a, pattern):
     """The unfused trajectory path: bit for bit the same kernels as hd_apply."""
     import paper_2101_07464_gb300 as hd
     T = 16
@@ -52,8 +52,8 @@ def test_run_matches_apply(dtype, graph, ens, m, n, dyn, a, pattern, monkeypatch
     sigma = 1.0 if ens == "haar" else m ** -0.5
     ref = _manual(ens, m, n, T, 5, dtype, flags, dyn, a, sigma)
     tdt = torch.float64 if dtype == "f64" else torch.float32
-    monkeypatch.setenv("HD_DISABLE_FUSE", "1")
     st = hd.HD(ens, m, n, T, 5, dtype, sigma=sigma)
+    hd.hd_set_engine(st.h, no_fuse=True)
     spec = hd.make_run_spec(flags, dyn, a, use_graph=graph)
     x1 = torch.tensor(synth.x1(m if flags[0] else n, 5), dtype=tdt, device="cuda")
     out = torch.empty(ref.numel(), dtype=tdt, device="cuda")

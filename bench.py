@@ -5,10 +5,16 @@ T = 100 products alternating Q and Q^T, dynamics x_{t+1} = sign(M_t x_t) + 0.5 x
 x_1 ~ N(0, I_n) (seeded, synthetic).  One bench "step" is one whole trajectory: T products
 (every row of the hot path: draws, the data-side reflector products, the new reflectors,
 the outputs) plus the dynamics, all in libhd.so kernels, replayed from one CUDA graph.
-Metric: n T^2 / s (the O(nT^2) work unit of the method).  The FP32-storage form is the
-headline line; the plain FP64 form is measured on the same workload and reported beside it.
+Metric: n T^2 / s (the O(nT^2) work unit of the method).  The headline line is the FP64
+form (the paper's precision); the FP32-storage form of the same workload is reported beside
+it under "fp32" with its own roofline, and the other workloads under their own keys.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--dtype f32|f64] [--impl reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--dtype f64|f32] [--impl reference]
+
+Accuracy: every result carries its error against the FP64 oracle (per-step teacher-forced
+error, free-running trajectory error, orthogonality defect ||Q^T Q x - x|| / ||x|| per T, or
+gradient error).  The oracle runs only in the CPU-baseline leg (cpu_baseline_leg), which
+times it for the baseline and computes the reference values these fields compare against.
 
 --impl reference times the CPU FP64 oracle on the host cores over the same workload at full
 n: whole trajectories when they fit the run's time bound, else the first products of each,
@@ -37,12 +43,16 @@ def parse(argv=None):
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--dtype", default="f64", choices=["f32", "f64"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--T", type=int, default=T_DEFAULT)
     ap.add_argument("--seed", type=int, default=1)
-    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 side measurement")
+    ap.add_argument("--no-side", action="store_true",
+                    help="skip the other-precision form of the headline workload")
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="skip the accuracy fields (and the oracle reference values they need)")
+    ap.add_argument("--no-c1", action="store_true", help="skip the small Ginibre configuration")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-amp", action="store_true", help="skip the batched AMP measurement")
     ap.add_argument("--amp-trials", type=int, default=4096)
@@ -238,9 +248,19 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-# DRAM bytes / algorithmic bytes of one k_update launch (k = 60, n = 10^6, FP32) from an
-# ncu --set full capture of the current kernel; reset to None when the kernel changes.
-UPDATE_TRAFFIC_RATIO = 250.15 / 252.0
+# DRAM bytes / algorithmic bytes of one k_update launch, from ncu --set full captures of the
+# current kernel at k = 60, n = 10^6 (FP32: 250.15 MB for 252.0 MB; FP64: 494.3 MB for 504.0 MB);
+# None once the kernel has changed since the capture.
+TRAFFIC_RATIO = {"f32": 250.15 / 252.0, "f64": 494.30 / 504.0}
+TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_update launch "
+                  "(k = 60, n = 10^6, same dtype), scaled to the average launch by algorithmic bytes")
+
+# Algorithmic FP64 flops per stack element of each sweep in the fused Q / Q^T alternating
+# trajectory (2 per FMA): the update sweep forms p = Delta (x - V w) and the two column
+# products V^T p~ and V^T g_{t+1}; the fused output sweep forms y = c - V w' and the next
+# step's V^T x_{t+1}; the dot sweep V^T x.
+FLOPS_PER_ELEMENT = {"dots": 2.0, "update": 6.0, "output": 4.0}
+KERNEL_NAME = {"dots": "k_dots", "update": "k_update", "output": "k_out_haar"}
 
 
 def measured_peaks():
@@ -250,6 +270,19 @@ def measured_peaks():
         return float(d["hbm_gbs"]), "measured"
     except (OSError, KeyError, ValueError):
         return 6800.0, "fallback"
+
+
+def fp64_peak():
+    """The FP64 FMA pipe rate of this GPU, measured now (hd_fp64_fma_rate), TFLOP/s."""
+    import paper_2101_07464_gb300 as hd
+    return hd.hd_fp64_fma_rate(iters=1 << 14, reps=5)
+
+
+def haar_columns(T):
+    """Columns each sweep kind streams over one Haar trajectory of T products: before step t
+    both stacks hold t - 1 reflectors; every step has one update and one output sweep."""
+    k = float(T * (T - 1) / 2)
+    return {"update": k, "output": k, "dots": 0.0}
 
 
 def time_trajectories(st, spec, x1, xout, steps, warmup, dist):
@@ -345,10 +378,13 @@ def measure_amp_batch(args, rank, world, dist):
 
 def measure_adjoint(args, rank, world, dist):
     """Reverse mode: gradient of <c, x_{T+1}> with respect to x_1 and the per-step parameters
-    theta_t of x_{t+1} = tanh(theta_t y_t) + 0.3 x_{t-1} on Haar(n), n = 10^6, T = 100 products
-    Q / Q^T alternating, FP32 storage (paper_2101_07464_gb300.autograd.trajectory: forward with
-    the library's steps recorded, backward through hd_adjoint_step).  Units n T^2 per
-    forward + backward."""
+    theta_t (2.0) of x_{t+1} = tanh(theta_t y_t) + 0.3 x_{t-1} on Haar(n), n = 10^6, T = 100
+    products Q / Q^T alternating, FP32 storage (paper_2101_07464_gb300.autograd.trajectory:
+    forward with the library's steps recorded, backward through hd_adjoint_step).  Units n T^2
+    per forward + backward.  theta = 2 keeps the trajectory well conditioned under the
+    alternating schedule: with theta = 0.8 most of x_{t+1} lies in the span the earlier
+    reflectors fix, and FP32 rounding of the inputs alone moves the trajectory by 5e-5 at
+    step 32 (oracle, n = 20000), against 7e-8 with theta = 2."""
     import numpy as np
     import torch
     import synth
@@ -359,7 +395,7 @@ def measure_adjoint(args, rank, world, dist):
     st = hd.HD("haar", n, n, T, args.seed, "f32", trial=rank)
     x1 = torch.tensor(synth.x1(n, args.seed, trial=rank), dtype=torch.float32, device="cuda")
     c = torch.tensor(synth.x1(n, args.seed + 1, trial=rank), dtype=torch.float32, device="cuda")
-    theta0 = torch.full((T,), 0.8, dtype=torch.float32, device="cuda")
+    theta0 = torch.full((T,), 2.0, dtype=torch.float32, device="cuda")
 
     def f(t, y, x, xprev, theta):
         v = torch.tanh(theta[t - 1] * y)
@@ -395,7 +431,7 @@ def measure_adjoint(args, rank, world, dist):
             "ms_forward_backward": fb * 1e3, "ms_forward": fw * 1e3, "n": n, "T": T, "dtype": "f32",
             "timing": "wall clock around synchronised whole calls (host-driven steps, torch f_t)",
             "config": "Haar n=1e6, T=100, Q/Q^T alternating, x_{t+1} = tanh(theta_t y_t) + 0.3 x_{t-1}, "
-                      "d<c, x_{T+1}>/d(x_1, theta)"}
+                      "theta_t = 2, d<c, x_{T+1}>/d(x_1, theta)"}
 
 
 def measure_ista(args, rank, world, dist):
@@ -626,6 +662,511 @@ def measure_large(args, rank, world, dist):
                         "timing": "wall clock around one synchronised forward + backward"}}
 
 
+# ----------------------------------------------------------------------------------------
+# The CPU-baseline leg: the only place (besides the reference arm) that runs the oracle.  It
+# times the oracle on the headline workload (cpu_baseline) and computes the reference values
+# of every accuracy field at the sizes below (full size where the oracle finishes in seconds).
+N_ACC_FP32 = 200_000          # Haar workload in FP32: teacher-forced at this n
+N_ACC_LARGE, T_LARGE = 10_000, 256
+N_ACC_GRAD = 10_000           # reverse-mode gradients against the oracle's float64 autograd
+K_ACC_ISTA = 10               # ISTA iterations within the converging residuals' conditioning
+N_ACC_ISTA = 20_000           # lasso ISTA, Gin(n/2, n)
+N_ACC_SPECTRAL = 3_000
+AMP_ACC_TRIALS = 4
+
+
+def alt(t):
+    return t % 2 == 0
+
+
+# Smallest alpha_t / ||x_t|| (the part of the step input that the revealed reflectors do not
+# already fix) at which per-step parity is meaningful: the unit roundoff over the tolerance.
+# Below it the new reflector is built from a tail dominated by rounding (reading A13(i)).
+COND_MIN = {"f64": 1.1e-16 / 1e-12, "f32": 6.0e-8 / 1e-5}
+
+
+def unrevealed_fraction(ora, x, transpose):
+    """alpha of the data-side reflector the oracle's last product built, over ||x||."""
+    import numpy as np
+    r = (ora.L if transpose else ora.R)[-1]
+    nx = float(np.linalg.norm(np.asarray(x, dtype=np.float64)))
+    return float(r.alpha) / nx if nx > 0 else 0.0
+
+
+def f32_cast(v):
+    import numpy as np
+    return np.asarray(v, dtype=np.float64).astype(np.float32).astype(np.float64)
+
+
+def cpu_baseline_leg(args, n, T, want_accuracy):
+    """Returns (cpu_baseline, refs): the oracle timed on the headline trajectory at full n
+    (FP64, every product) and the oracle's reference values of the accuracy fields."""
+    import numpy as np
+    import torch
+    import synth
+    from oracle.adjoint import trajectory as oracle_grad_trajectory
+    from oracle.dynamics import amp_trace, f_norm_tanh, f_sign_mem, f_tanh, run_trace
+    from oracle.hd import make_oracle
+    refs = {}
+    x1 = synth.x1(n, args.seed)
+    t0 = time.perf_counter()
+    ora = make_oracle("haar", n, n, T, args.seed)
+    xs, ys, fs = run_trace(ora, x1, T, f_sign_mem, alt)
+    secs = time.perf_counter() - t0
+    cpu = {"value": float(n) * T * T / secs, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+           "sample": "all %d of %d products of one trajectory at n=%d (Haar, Q/Q^T alternating, sign "
+                     "dynamics), FP64, wall %.1f s" % (T, T, n, secs)}
+    refs["headline"] = {"xs": xs, "ys": ys, "fs": fs}
+    if not want_accuracy:
+        return cpu, refs
+    na = min(n, N_ACC_FP32)
+    xa = synth.x1(na, args.seed)
+    refs["fp32"] = {"n": na,
+                    "teacher": run_trace(make_oracle("haar", na, na, T, args.seed), xa, T, f_sign_mem, alt,
+                                         cast=f32_cast),
+                    "free": run_trace(make_oracle("haar", na, na, T, args.seed), xa, T, f_sign_mem, alt)}
+    # small Ginibre configuration, full size
+    nc, Tc = 1000, 10
+    oc = make_oracle("ginibre", nc, nc, Tc, args.seed, sigma=nc ** -0.5)
+    refs["c1"] = run_trace(oc, synth.x1(nc, args.seed), Tc, f_tanh, lambda t: False)
+    # batched AMP: the workload's first trials, FP32 inputs
+    ns = synth.batch_sizes(args.amp_trials, 1000, 100000, args.seed)[:AMP_ACC_TRIALS]
+    amp = []
+    for i, nn in enumerate(ns):
+        nn = int(nn)
+        mm = nn // 2
+        beta = f32_cast(synth.bernoulli_gauss(nn, args.seed, trial=i))
+        w = f32_cast(synth.noise(mm, args.seed, trial=i))
+        oa = make_oracle("ginibre", mm, nn, 30, args.seed, trial=i, sigma=mm ** -0.5)
+        amp.append({"n": nn, "m": mm, "beta": beta, "w": w, "trace": amp_trace(oa, beta, w, 30, cast=f32_cast)})
+    refs["amp"] = amp
+    # large configuration at reduced n, FP32 inputs
+    xl = synth.x1(N_ACC_LARGE, args.seed)
+    ol = make_oracle("haar", N_ACC_LARGE, N_ACC_LARGE, T_LARGE, args.seed)
+    tl = run_trace(ol, f32_cast(xl / np.linalg.norm(xl)), T_LARGE, f_norm_tanh, lambda t: False, cast=f32_cast)
+    # alpha_t / ||x_t||: the part of x_t that the revealed reflectors do not already fix
+    frac = [float(r.alpha) / float(np.linalg.norm(x)) for r, x in zip(ol.R, tl[0])]
+    refs["large"] = {"n": N_ACC_LARGE, "teacher": tl, "unrevealed_fraction": frac}
+    # reverse mode: the adjoint workload's gradients at reduced n (oracle float64 autograd)
+    refs["adjoint"] = grad_reference(oracle_grad_trajectory, "adjoint", args.seed)
+    refs["ista"] = grad_reference(oracle_grad_trajectory, "ista", args.seed)
+    # lasso ISTA (the paper's timed run) and the spectral method at reduced n: every product's
+    # input, transpose flag and output
+    refs["paper_ista"] = lasso_reference(make_oracle, N_ACC_ISTA, args.seed)
+    refs["spectral"] = spectral_reference(make_oracle, N_ACC_SPECTRAL, args.seed)
+    return cpu, refs
+
+
+def adjoint_problem(kind, n, seed):
+    """The reduced-size instance of a reverse-mode workload shared by the oracle reference and
+    the GPU check: (ensemble, m, n, T, schedule, f, x1, params, c or None, sigma)."""
+    import numpy as np
+    import synth
+    if kind == "adjoint":
+        T = 100
+        sched = [alt(t) for t in range(1, T + 1)]
+
+        def f(t, y, x, xprev, theta):
+            import torch
+            v = torch.tanh(theta[t - 1] * y)
+            return v if xprev is None else v + 0.3 * xprev
+        x1 = f32_cast(synth.x1(n, seed))
+        c = f32_cast(synth.x1(n, seed + 1))
+        return "haar", n, n, T, sched, f, x1, [np.full(T, 2.0)], c, 1.0
+    K = K_ACC_ISTA
+    T = 2 * K + 1
+    sched = [False] + [bool(t % 2) for t in range(2, T + 1)]
+    beta = f32_cast(synth.bernoulli_gauss(n, seed, trial=0, p_nonzero=0.8, scale=2.0))
+    w = f32_cast(synth.noise(n, seed, trial=0, sigma=0.1))
+
+    def make_f(wt):
+        store = {}
+
+        def f(t, y, x, xprev, theta, tau):
+            import torch
+            if t == 1:
+                store["y"] = (y + wt).detach()
+                return torch.zeros_like(y)
+            if t % 2 == 0:
+                return store["y"] - y
+            v = xprev + tau * y
+            return torch.sign(v) * torch.clamp(v.abs() - theta[(t - 3) // 2], min=0.0)
+        return f
+    return "ginibre", n, n, T, sched, make_f, beta, [np.full(K, 0.6), np.float64(0.3)], w, n ** -0.5
+
+
+def grad_reference(oracle_grad_trajectory, kind, seed):
+    import numpy as np
+    import torch
+    n = N_ACC_GRAD
+    ens, m, n, T, sched, f, x1, params, extra, sigma = adjoint_problem(kind, n, seed)
+    xt = torch.tensor(x1, dtype=torch.float64, requires_grad=True)
+    ps = [torch.tensor(p, dtype=torch.float64, requires_grad=True) for p in params]
+    if kind == "adjoint":
+        out = oracle_grad_trajectory(ens, m, n, T, seed, sched, f, xt, tuple(ps), sigma=sigma)
+        L = torch.dot(torch.tensor(extra, dtype=torch.float64), out)
+    else:
+        fw = f(torch.tensor(extra, dtype=torch.float64))
+        out = oracle_grad_trajectory(ens, m, n, T, seed, sched, fw, xt, tuple(ps), sigma=sigma)
+        L = torch.sum((out - xt.detach()) ** 2) / n
+    L.backward()
+    return {"n": n, "T": T, "loss": float(L.item()), "grad_x1": xt.grad.numpy().copy(),
+            "grad_params": [p.grad.numpy().copy() for p in ps]}
+
+
+def lasso_reference(make_oracle, n, seed):
+    """The lasso ISTA of the paper's timed run at size n: y = Q beta + w, then
+    x^{k+1} = eta(x^k + tau Q^T (y - Q x^k); 0.6), 50 iterations, FP64."""
+    import numpy as np
+    import synth
+    from oracle.dynamics import soft_threshold
+    m, K = n // 2, 50
+    ora = make_oracle("ginibre", m, n, 2 * K + 1, seed, sigma=m ** -0.5)
+    beta = synth.bernoulli_gauss(n, seed, trial=0, p_nonzero=0.8, scale=2.0)
+    w = synth.noise(m, seed, trial=0, sigma=0.1)
+    ins, trs, outs, frac = [], [], [], []
+
+    def app(v, tr):
+        ins.append(v); trs.append(tr)
+        o = ora.apply(v, tr).numpy()
+        outs.append(o)
+        frac.append(unrevealed_fraction(ora, v, tr))
+        return o
+    y = app(beta, False) + w
+    x = np.zeros(n)
+    for _ in range(K):
+        r = y - app(x, False)
+        x = soft_threshold(x + 0.3 * app(r, True), 0.6)
+    return {"ensemble": "ginibre", "m": m, "n": n, "sigma": m ** -0.5, "seed": seed, "ins": ins, "trs": trs,
+            "outs": outs, "frac": frac}
+
+
+def spectral_reference(make_oracle, n, seed, K=30):
+    """Power iterations of the spectral method at size n (m = 2n): every product's input,
+    flag and output."""
+    import numpy as np
+    import synth
+    m = 2 * n
+    ora = make_oracle("haar", m, m, 1 + 2 * K, seed)
+    xi = synth.x1(n, seed)
+    x = synth.x1(n, seed + 1)
+    z = np.zeros(m - n)
+    ins, trs, outs, frac = [], [], [], []
+
+    def app(v, tr):
+        ins.append(v); trs.append(tr)
+        o = ora.apply(v, tr).numpy()
+        outs.append(o)
+        frac.append(unrevealed_fraction(ora, v, tr))
+        return o
+    yv = np.tanh(np.abs(app(np.concatenate([xi, z]), True)))
+    x = x / np.linalg.norm(x)
+    for _ in range(K):
+        v = app(yv * app(np.concatenate([x, z]), True), False)[:n] / m
+        x = v / np.linalg.norm(v)
+    return {"ensemble": "haar", "m": m, "n": m, "sigma": 1.0, "seed": seed, "ins": ins, "trs": trs, "outs": outs,
+            "frac": frac}
+
+
+# ----------------------------------------------------------------------------------------
+# Accuracy fields (GPU side): the library's results against the oracle reference values that
+# cpu_baseline_leg computed.  Element-wise errors are max_i |a_i - b_i| / max_i |b_i| per step.
+def _g3(v):
+    return float("%.3g" % v)
+
+
+def per_t(errs):
+    return {"max": _g3(max(errs)) if errs else None, "per_T": [_g3(e) for e in errs]}
+
+
+def max_rel_dev(a, b, head=0):
+    """Element-wise error of a (CUDA tensor) against the oracle's b (numpy float64): rows below
+    `head` (the pivot rows fixed by the reflectors so far, t after step t) relative to
+    ||b||_2, the others relative to max_i |b_i|.  The oracle forms each pivot row as the
+    difference of two terms of the size of ||x_t|| (eq. Householder applied literally), so
+    its own rounding there scales with the norm."""
+    import torch
+    bt = torch.from_numpy(b).to(device=a.device)
+    d = (a.double() - bt).abs()
+    h = min(int(head), bt.numel())
+    s = bt.abs().max().item()
+    e = (d[h:].max().item() / s if s > 0 else d[h:].max().item()) if h < bt.numel() else 0.0
+    if h > 0:
+        nb = bt.norm().item()
+        e = max(e, d[:h].max().item() / nb if nb > 0 else d[:h].max().item())
+    return e
+
+
+def rows_of(vs, L, tdt):
+    import torch
+    out = torch.zeros((len(vs), L), dtype=tdt, device="cuda")
+    for i, v in enumerate(vs):
+        out[i, :v.shape[0]] = torch.from_numpy(v).to(device="cuda", dtype=tdt)
+    return out
+
+
+def run_records(st, flags, dyn, a, x1, L, given=None, aux=None, graph=True):
+    """One hd_run of the trajectory with y_t (and f_t's result) recorded, teacher-forced when
+    `given` holds the next inputs; returns the two T x L device records."""
+    import torch
+    import paper_2101_07464_gb300 as hd
+    T = len(flags)
+    tdt = st.torch_dtype
+    yrec = torch.zeros((T, L), dtype=tdt, device="cuda")
+    xrec = torch.zeros((T, L), dtype=tdt, device="cuda")
+    out = torch.empty(L, dtype=tdt, device="cuda")
+    spec = hd.make_run_spec(flags, dyn, a, use_graph=graph, aux=aux, y_record=yrec, x_record=xrec, x_given=given)
+    hd.hd_run(st.h, spec, x1, out)
+    torch.cuda.synchronize()
+    return yrec, xrec
+
+
+def ortho_defect(st, xs, flags):
+    """||Q^T Q x_t - x_t|| / ||x_t|| (Q^T applied to Q x_t, both through hd_probe on the
+    state's revealed part) for each recorded input x_t (host float64 vectors)."""
+    import torch
+    out = []
+    for x, tr in zip(xs, flags):
+        xt = torch.from_numpy(x).to(device="cuda", dtype=st.torch_dtype)
+        y, _ = st.probe(xt, bool(tr))
+        back, _ = st.probe(y, not bool(tr))
+        out.append(((back.double() - xt.double()).norm() / xt.double().norm()).item())
+    return out
+
+
+def accuracy_haar_sign(dtype, n, T, seed, teacher, free):
+    """Teacher-forced and free-running per-step errors and the orthogonality defect of the
+    benchmarked trajectory path (hd_run, fused sweeps, one graph) at size n."""
+    import torch
+    import paper_2101_07464_gb300 as hd
+    xs, ys, _ = teacher
+    flags = [alt(t) for t in range(1, T + 1)]
+    st = hd.HD("haar", n, n, T, seed, dtype)
+    tdt = st.torch_dtype
+    x1 = torch.from_numpy(xs[0]).to(device="cuda", dtype=tdt)
+    yrec, _ = run_records(st, flags, "sign_mem", 0.5, x1, n, given=rows_of(xs[1:] + [xs[-1]], n, tdt))
+    tf = [max_rel_dev(yrec[t], ys[t], t + 1) for t in range(T)]
+    orth = ortho_defect(st, xs, flags)
+    del yrec
+    fx, fy, _ = free
+    yrec, _ = run_records(st, flags, "sign_mem", 0.5, torch.from_numpy(fx[0]).to(device="cuda", dtype=tdt), n)
+    fr = [max_rel_dev(yrec[t], fy[t], t + 1) for t in range(T)]
+    st.close()
+    return {"n": n, "teacher_forced_error": per_t(tf), "free_run_error": per_t(fr),
+            "orthogonality_defect": per_t(orth),
+            "how": "per step t: max_i |y_gpu - y_oracle| / max_i |y_oracle| (the t pivot rows relative "
+                   "to ||y_oracle||, where the oracle's own rounding scales with the norm); teacher-forced = both "
+                   "given the oracle's x_t (hd_run x_given), free-run = each on its own trajectory; "
+                   "defect = ||Q^T Q x_t - x_t|| / ||x_t|| by hd_probe on the final state"}
+
+
+def accuracy_products(ref, dtype):
+    """Per-product teacher-forced error of host-driven hd_apply products (the path of the
+    host-driven workloads) on the oracle's inputs."""
+    import paper_2101_07464_gb300 as hd
+    import torch
+    st = hd.HD(ref["ensemble"], ref["m"], ref["n"], len(ref["ins"]), ref["seed"], dtype, sigma=ref["sigma"])
+    errs = []
+    for x, tr, yo in zip(ref["ins"], ref["trs"], ref["outs"]):
+        y = st.apply(torch.from_numpy(x).to(device="cuda", dtype=st.torch_dtype), tr)
+        errs.append(max_rel_dev(y, yo, len(errs) + 1))
+    st.close()
+    ok = [e for e, f in zip(errs, ref["frac"]) if f >= COND_MIN[dtype]]
+    return {"error": per_t(errs), "unrevealed_fraction": per_t(ref["frac"]),
+            "max_error_while_conditioned": _g3(max(ok)) if ok else None, "products_conditioned": len(ok)}
+
+
+def accuracy_c1(ref, seed):
+    """Small Ginibre configuration (full size): teacher-forced and free-running errors of the
+    hd_run path (all Q, unfused sweeps, one graph)."""
+    import torch
+    import paper_2101_07464_gb300 as hd
+    xs, ys, fs = ref
+    n, T = 1000, len(ys)
+    flags = [False] * T
+    st = hd.HD("ginibre", n, n, T, seed, "f64", sigma=n ** -0.5)
+    x1 = torch.from_numpy(xs[0]).to("cuda")
+    yrec, _ = run_records(st, flags, "tanh", 0.0, x1, n, given=rows_of(xs[1:] + [xs[-1]], n, torch.float64))
+    tf = [max_rel_dev(yrec[t], ys[t], t + 1) for t in range(T)]
+    yrec, _ = run_records(st, flags, "tanh", 0.0, x1, n)
+    fr = [max_rel_dev(yrec[t], ys[t], t + 1) for t in range(T)]
+    st.close()
+    return {"teacher_forced_error": per_t(tf), "free_run_error": per_t(fr)}
+
+
+def accuracy_amp(ref, seed):
+    """Batched AMP (FP32): the workload's first trials in one batched state, teacher-forced
+    through the fused AMP sweep; per step the largest error over the trials of the products
+    and of the AMP updates."""
+    import numpy as np
+    import torch
+    import paper_2101_07464_gb300 as hd
+    ns = [r["n"] for r in ref]
+    ms = [r["m"] for r in ref]
+    T = 30
+    b = hd.HDBatch("ginibre", ms, ns, T, seed, "f32")
+    b.set_trial_sigmas([m ** -0.5 for m in ms])
+    off_n, off_m = b.off_n, b.off_m
+    L = int(max(off_n[-1], off_m[-1]))
+    given = torch.zeros((T, L), dtype=torch.float32, device="cuda")
+    for t in range(1, T):
+        row = np.concatenate([r["trace"]["used"][t - 1] for r in ref])
+        given[t - 1, :row.shape[0]] = torch.from_numpy(row).to(device="cuda", dtype=torch.float32)
+    beta = torch.from_numpy(np.concatenate([r["beta"] for r in ref])).to(device="cuda", dtype=torch.float32)
+    w = torch.from_numpy(np.concatenate([r["w"] for r in ref])).to(device="cuda", dtype=torch.float32)
+    yrec, xrec = run_records(b, [alt(t) for t in range(1, T + 1)], "amp", 1.1, beta, L, given=given, aux=w)
+    ep, eu = [], []
+    for t in range(1, T + 1):
+        off = off_n if t % 2 == 0 else off_m
+        ep.append(max(max_rel_dev(yrec[t - 1, int(off[i]):int(off[i + 1])], r["trace"]["products"][t - 1], t)
+                      for i, r in enumerate(ref)))
+        eu.append(max(max_rel_dev(xrec[t - 1, int(off[i]):int(off[i + 1])], r["trace"]["updates"][t - 1], t)
+                      for i, r in enumerate(ref)))
+    b.close()
+    return {"trials_checked": len(ref), "n": ns, "teacher_forced_error": per_t(ep),
+            "update_error": per_t(eu),
+            "how": "the workload's first %d trials (same sizes, seeds and trial words), FP32, "
+                   "teacher-forced AMP vectors (hd_run x_given); products y_t and updates z^k / x^k "
+                   "element-wise against the oracle's AMP" % len(ref)}
+
+
+def accuracy_large(ref, seed):
+    """The large configuration's path (all Q, norm-tanh, unfused sweeps, one graph, FP32) at
+    reduced n over all T = 256 steps: teacher-forced errors and the orthogonality defect."""
+    import torch
+    import paper_2101_07464_gb300 as hd
+    n = ref["n"]
+    xs, ys, _ = ref["teacher"]
+    T = len(ys)
+    flags = [False] * T
+    st = hd.HD("haar", n, n, T, seed, "f32")
+    x1 = torch.from_numpy(xs[0]).to(device="cuda", dtype=torch.float32)
+    yrec, _ = run_records(st, flags, "norm_tanh", 0.1, x1, n, given=rows_of(xs[1:] + [xs[-1]], n, torch.float32))
+    tf = [max_rel_dev(yrec[t], ys[t], t + 1) for t in range(T)]
+    orth = ortho_defect(st, xs, flags)
+    st.close()
+    frac = ref["unrevealed_fraction"]
+    ok = [e for e, f in zip(tf, frac) if f >= COND_MIN["f32"]]
+    return {"n": n, "T": T, "teacher_forced_error": per_t(tf), "orthogonality_defect": per_t(orth),
+            "unrevealed_fraction": per_t(frac),
+            "max_error_while_conditioned": _g3(max(ok)) if ok else None,
+            "steps_conditioned": len(ok),
+            "note": "this dynamics converges: alpha_t / ||x_t|| (the part of x_t the revealed reflectors do "
+                    "not fix, from the oracle) falls geometrically, so each new reflector is built from an "
+                    "ever smaller tail and FP32 rounding of order 6e-8 ||x_t|| / alpha_t enters it.  Per-step "
+                    "parity is meaningful while alpha_t / ||x_t|| >= 6e-3, the FP32 unit roundoff over the "
+                    "1e-5 tolerance (max_error_while_conditioned); "
+                    "later steps remain valid samples of the ensemble but follow their own rounding"}
+
+
+def accuracy_grad(kind, ref, seed):
+    """Reverse mode at reduced n, in the timed entry's precision (FP32): the gradients against
+    the oracle's float64 autograd on the same FP32-representable inputs."""
+    import numpy as np
+    import torch
+    import paper_2101_07464_gb300 as hd
+    from paper_2101_07464_gb300.autograd import trajectory
+    ens, m, n, T, sched, f, x1, params, extra, sigma = adjoint_problem(kind, ref["n"], seed)
+    st = hd.HD(ens, m, n, T, seed, "f32", sigma=sigma)
+    xt = torch.from_numpy(x1).to(device="cuda", dtype=torch.float32).requires_grad_(True)
+    ps = [torch.tensor(np.asarray(p), dtype=torch.float32, device="cuda").requires_grad_(True) for p in params]
+    if kind == "adjoint":
+        out = trajectory(st, xt, sched, f, tuple(ps))
+        L = torch.dot(torch.from_numpy(extra).to(device="cuda", dtype=torch.float32), out)
+    else:
+        out = trajectory(st, xt, sched, f(torch.from_numpy(extra).to(device="cuda", dtype=torch.float32)), tuple(ps))
+        L = torch.sum((out - xt.detach()) ** 2) / n
+    L.backward()
+    st.close()
+
+    def rel(a, b):
+        a, b = np.atleast_1d(np.asarray(a, dtype=np.float64)), np.atleast_1d(b)
+        return _g3(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+    res = {"n": n, "T": T, "loss_rel_error": _g3(abs(L.item() - ref["loss"]) / max(abs(ref["loss"]), 1e-300)),
+           "grad_params_rel_error": [rel(p.grad.double().cpu().numpy(), g) for p, g in zip(ps, ref["grad_params"])]}
+    if kind == "adjoint":
+        res["grad_x1_rel_error"] = rel(xt.grad.double().cpu().numpy(), ref["grad_x1"])
+    res["how"] = ("FP32 reverse mode (autograd.trajectory) against the oracle's float64 autograd, "
+                  "relative 2-norm error of each gradient, at reduced n; the whole trajectory for the "
+                  "adjoint workload, the first %d iterations for ISTA, whose converging residuals make "
+                  "later FP32 and FP64 trajectories separate by their conditioning, not by the reverse "
+                  "mode" % K_ACC_ISTA)
+    return res
+
+
+def measure_c1(args):
+    """Small Ginibre configuration: Gin(n, n), n = 1000, entries N(0, 1/n), T = 10, all Q,
+    x_{t+1} = tanh(y_t), FP64: microseconds per product through hd_run, replayed as one CUDA
+    graph and launched stream-ordered without the graph."""
+    import torch
+    import synth
+    import paper_2101_07464_gb300 as hd
+    n, T = 1000, 10
+    flags = [False] * T
+    st = hd.HD("ginibre", n, n, T, args.seed, "f64", sigma=n ** -0.5)
+    x1 = torch.tensor(synth.x1(n, args.seed), dtype=torch.float64, device="cuda")
+    out = torch.empty(n, dtype=torch.float64, device="cuda")
+    res = {}
+    stream = torch.cuda.current_stream()
+    for graph in (True, False):
+        spec = hd.make_run_spec(flags, "tanh", 0.0, use_graph=graph)
+        for _ in range(5):
+            hd.hd_run(st.h, spec, x1, out)
+        torch.cuda.synchronize()
+        reps = 200
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            hd.hd_run(st.h, spec, x1, out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        res["us_per_product_graph" if graph else "us_per_product_stream"] = e0.elapsed_time(e1) * 1e3 / reps / T
+    st.close()
+    res.update({"config": "Gin(1000, 1000), entries N(0, 1/n), T=10, all Q, x_{t+1} = tanh(y_t), FP64",
+                "value": float(n) * T * T / (res["us_per_product_graph"] * T * 1e-6), "unit": UNIT,
+                "timing": "CUDA events around 200 back-to-back trajectories (hd_run), per product"})
+    return res
+
+
+def roofline_of(prof, dtype, n, T, peaks):
+    """Roofline of the dominant sweep (largest total time inside the timed trajectories):
+    FP64 against the measured FP64 FMA rate (algorithmic flops), FP32 against the measured
+    HBM copy rate (algorithmic bytes).  Times are CUDA events on the launching stream."""
+    dom = max(prof, key=lambda k: prof[k][0])
+    ms, nl, by = prof[dom]
+    per_kernel = {k: {"ms_total": v[0], "launches": v[1], "GBps": (v[2] / (v[0] / 1e3) / 1e9) if v[0] else None}
+                  for k, v in prof.items()}
+    cols = haar_columns(T)
+    trajectories = (nl / T) if nl else 0.0   # every trajectory launches T update and T output sweeps
+    if dtype == "f64":
+        flops = FLOPS_PER_ELEMENT[dom] * n * cols[dom] * trajectories
+        achieved = (flops / nl) / ((ms / nl) / 1e3) / 1e12 if nl else 0.0
+        for k, v in prof.items():
+            if v[0] and v[1]:
+                per_kernel[k]["TFLOPs"] = FLOPS_PER_ELEMENT[k] * n * cols[k] * (v[1] / T) / (v[0] / 1e3) / 1e12
+        r = {"bound": "alu", "kernel": KERNEL_NAME[dom], "achieved": achieved, "peak": peaks["fp64_tflops"],
+             "unit": "TFLOP/s", "frac": achieved / peaks["fp64_tflops"],
+             "peak_source": "measured now on this GPU: hd_fp64_fma_rate (8 independent FMA chains per "
+                            "thread, 8 CTAs of 256 threads per SM, best of 5 event-timed launches)",
+             "work": "%g FP64 flops per stack element (2 per FMA) x n x the columns of each launch "
+                     "(t - 1 before step t)" % FLOPS_PER_ELEMENT[dom],
+             "traffic": ((by / nl) * TRAFFIC_RATIO["f64"] if (nl and dom == "update" and TRAFFIC_RATIO["f64"])
+                         else None),
+             "hbm_GBps": (by / nl) / ((ms / nl) / 1e3) / 1e9 if nl else None}
+    else:
+        achieved = (by / nl) / ((ms / nl) / 1e3) / 1e9 if nl else 0.0
+        r = {"bound": "hbm", "kernel": KERNEL_NAME[dom], "achieved": achieved, "peak": peaks["hbm_gbs"],
+             "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "peak_source": peaks["hbm_source"],
+             "traffic": ((by / nl) * TRAFFIC_RATIO["f32"] if (nl and dom == "update" and TRAFFIC_RATIO["f32"])
+                         else None)}
+    if r["traffic"] is not None:
+        r["traffic_source"] = TRAFFIC_SOURCE
+    r["timing"] = ("CUDA events on the launching stream around every sweep, recorded in a second pass "
+                   "of the same trajectories (events inside the graph would perturb the headline timing)")
+    r["per_kernel"] = per_kernel
+    return r
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -643,6 +1184,8 @@ def run_ours(args):
     hdbuild.build()
     n, T = args.n, args.T
     flags = schedule(T)
+    hbm, hbm_kind = measured_peaks()
+    peaks = {"hbm_gbs": hbm, "hbm_source": hbm_kind, "fp64_tflops": fp64_peak()}
 
     def measure(dtype, profile):
         tdt = torch.float32 if dtype == "f32" else torch.float64
@@ -682,39 +1225,24 @@ def run_ours(args):
     e2e = {"value": units / (e2e_secs / args.steps), "unit": UNIT,
            "h2d_bytes_per_step": n * x1h.element_size(), "d2h_bytes_per_step": n * xouth.element_size()}
     st.close()
-
-    # roofline of the dominant kernel (largest total time inside the timed region)
-    peak, peak_kind = measured_peaks()
-    dom = max(prof, key=lambda k: prof[k][0])
-    ms, nl, by = prof[dom]
-    achieved = (by / nl) / ((ms / nl) / 1e3) / 1e9 if nl else 0.0
-    roofline = {"bound": "hbm", "kernel": {"dots": "k_dots", "update": "k_update",
-                                            "output": "k_out_haar"}[dom],
-                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "peak_source": peak_kind,
-                "traffic": ((by / nl) * UPDATE_TRAFFIC_RATIO
-                            if (nl and dom == "update" and UPDATE_TRAFFIC_RATIO) else None),
-                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_update "
-                                  "launch at k = 60 (250.15 MB for 252.0 MB algorithmic), scaled to "
-                                  "the average launch by algorithmic bytes",
-                "timing": "CUDA events on the launching stream around every sweep, recorded "
-                          "in a second pass of the same trajectories (events inside the graph "
-                          "would perturb the headline timing)",
-                "per_kernel": {k: {"ms_total": v[0], "launches": v[1],
-                                   "GBps": (v[2] / (v[0] / 1e3) / 1e9) if v[0] else None}
-                               for k, v in prof.items()}}
-    if args.dtype == "f64":
-        roofline["note"] = "FP64 sweeps are bound by the FP64 FMA rate, not HBM"
+    roofline = roofline_of(prof, args.dtype, n, T, peaks)
     credited = 2.0 * n * tdt.itemsize * T * (T + 1) / 2.0 * world
-    step_gbps = credited / per_step / 1e9
 
-    fp64 = None
-    if args.dtype == "f32" and not args.no_fp64:
-        st64, _, secs64, _, _ = measure("f64", profile=False)
-        st64.close()
-        fp64 = {"value": units / (secs64 / args.steps), "ms_per_step": secs64 / args.steps * 1e3,
-                "unit": UNIT}
+    side = None
+    other = "f32" if args.dtype == "f64" else "f64"
+    if not args.no_side:
+        st2, _, secs2, prof2, _ = measure(other, profile=True)
+        st2.close()
+        ps = secs2 / args.steps
+        side = {"value": units / ps, "unit": UNIT, "ms_per_step": ps * 1e3, "dtype": other,
+                "storage": "FP32 stacks and vectors, FP64 coefficients and cross-thread sums" if other == "f32"
+                else "FP64",
+                "step_credited_GBps": 2.0 * n * (4 if other == "f32" else 8) * T * (T + 1) / 2.0 * world / ps / 1e9,
+                "roofline": roofline_of(prof2, other, n, T, peaks)}
 
+    c1 = None
+    if not args.no_c1:
+        c1 = measure_c1(args)
     amp = None
     if not args.no_amp:
         amp = measure_amp_batch(args, rank, world, dist)
@@ -746,12 +1274,40 @@ def run_ours(args):
         except Exception as exc:   # reported in the line, the headline stands
             large = {"error": "%s: %s" % (type(exc).__name__, exc)}
 
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu:   # N = 1 only: the oracle is a single-host baseline
-        done, csecs, thr, per = oracle_sample(n, T, args.seed, time_limit_s=15.0)
-        cval, _, how = oracle_throughput(n, T, [per])
-        cpu = {"value": cval, "unit": UNIT, "cores": thr, "kind": "oracle",
-               "sample": "%s, FP64, wall %.1f s" % (how, csecs)}
+    # the CPU-baseline leg (N = 1 only: the oracle is a single-host baseline), then the
+    # accuracy of every result against the oracle's reference values
+    cpu, accuracy = None, None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu, refs = cpu_baseline_leg(args, n, T, not args.no_accuracy)
+        if not args.no_accuracy:
+            hr = refs["headline"]
+            acc64 = accuracy_haar_sign("f64", n, T, args.seed, (hr["xs"], hr["ys"], hr["fs"]),
+                                       (hr["xs"], hr["ys"], hr["fs"]))
+            fx = refs["fp32"]
+            acc32 = accuracy_haar_sign("f32", fx["n"], T, args.seed, fx["teacher"], fx["free"])
+            acc32["note"] = ("reduced n; teacher-forced inputs are the oracle's rounded to FP32, the "
+                             "free run is against the oracle's FP64 trajectory")
+            accuracy = acc64 if args.dtype == "f64" else acc32
+            if side is not None:
+                side["accuracy"] = acc32 if other == "f32" else acc64
+            if c1 is not None:
+                c1["accuracy"] = accuracy_c1(refs["c1"], args.seed)
+            if amp is not None:
+                amp["accuracy"] = accuracy_amp(refs["amp"], args.seed)
+            if adj is not None:
+                adj["accuracy"] = accuracy_grad("adjoint", refs["adjoint"], args.seed)
+            if ista is not None and "error" not in ista:
+                ista["accuracy"] = accuracy_grad("ista", refs["ista"], args.seed)
+            if paper_ista is not None and "seconds" in paper_ista:
+                paper_ista["accuracy"] = {"n": refs["paper_ista"]["n"], "products": accuracy_products(refs["paper_ista"], "f64"),
+                                          "how": "reduced n, FP64, every product teacher-forced (hd_apply on the oracle's inputs)"}
+            if spectral is not None and "seconds" in spectral:
+                spectral["accuracy"] = {"n": refs["spectral"]["n"] // 2,
+                                        "products": accuracy_products(refs["spectral"], "f64"),
+                                        "how": "reduced n, FP64, 30 power iterations, every product teacher-forced"}
+            if large is not None and "forward" in large:
+                large["accuracy"] = accuracy_large(refs["large"], args.seed)
+        del refs
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -768,9 +1324,11 @@ def run_ours(args):
                            "launch_shapes": "built-in" if args.no_autotune
                            else "hd_autotune (untimed, before the timed region)"},
                 "roofline": roofline,
-                "step_credited_GBps": step_gbps,
+                "step_credited_GBps": credited / per_step / 1e9,
+                "accuracy": accuracy,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk, "fp64": fp64, "batched_amp": amp, "adjoint": adj, "ista": ista, "paper_ista": paper_ista, "spectral": spectral, "large": large}
+                "clocks": clk, other: side, "c1": c1, "batched_amp": amp, "adjoint": adj, "ista": ista,
+                "paper_ista": paper_ista, "spectral": spectral, "large": large}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -53,6 +53,7 @@ def parse(argv=None):
     ap.add_argument("--no-accuracy", action="store_true",
                     help="skip the accuracy fields (and the oracle reference values they need)")
     ap.add_argument("--no-c1", action="store_true", help="skip the small Ginibre configuration")
+    ap.add_argument("--no-complex", action="store_true", help="skip the complex (unitary) workload")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-amp", action="store_true", help="skip the batched AMP measurement")
     ap.add_argument("--amp-trials", type=int, default=4096)
@@ -669,9 +670,10 @@ def measure_large(args, rank, world, dist):
 N_ACC_FP32 = 200_000          # Haar workload in FP32: teacher-forced at this n
 N_ACC_LARGE, T_LARGE = 10_000, 256
 N_ACC_GRAD = 10_000           # reverse-mode gradients against the oracle's float64 autograd
-K_ACC_ISTA = 10               # ISTA iterations within the converging residuals' conditioning
+T_ACC_ADJ, K_ACC_ISTA = 24, 10    # steps within the converging trajectories' conditioning
 N_ACC_ISTA = 20_000           # lasso ISTA, Gin(n/2, n)
 N_ACC_SPECTRAL = 3_000
+N_ACC_COMPLEX = 20_000
 AMP_ACC_TRIALS = 4
 
 
@@ -689,7 +691,7 @@ def unrevealed_fraction(ora, x, transpose):
     """alpha of the data-side reflector the oracle's last product built, over ||x||."""
     import numpy as np
     r = (ora.L if transpose else ora.R)[-1]
-    nx = float(np.linalg.norm(np.asarray(x, dtype=np.float64)))
+    nx = float(np.linalg.norm(np.asarray(x)))
     return float(r.alpha) / nx if nx > 0 else 0.0
 
 
@@ -753,6 +755,7 @@ def cpu_baseline_leg(args, n, T, want_accuracy):
     # lasso ISTA (the paper's timed run) and the spectral method at reduced n: every product's
     # input, transpose flag and output
     refs["paper_ista"] = lasso_reference(make_oracle, N_ACC_ISTA, args.seed)
+    refs["complex"] = complex_reference(N_ACC_COMPLEX, T, args.seed)
     refs["spectral"] = spectral_reference(make_oracle, N_ACC_SPECTRAL, args.seed)
     return cpu, refs
 
@@ -763,7 +766,7 @@ def adjoint_problem(kind, n, seed):
     import numpy as np
     import synth
     if kind == "adjoint":
-        T = 100
+        T = T_ACC_ADJ
         sched = [alt(t) for t in range(1, T + 1)]
 
         def f(t, y, x, xprev, theta):
@@ -841,6 +844,25 @@ def lasso_reference(make_oracle, n, seed):
             "outs": outs, "frac": frac}
 
 
+def complex_reference(n, T, seed):
+    """The complex workload at size n: the oracle's trajectory of the phase map (all Q), with
+    every product's input, flag, output and unrevealed fraction."""
+    import numpy as np
+    import synth
+    from oracle.complex_hd import ComplexHaarOracle
+    ora = ComplexHaarOracle(n, T, seed)
+    x = synth.x1(n, seed) + 1j * synth.x1(n, seed + 7)
+    ins, trs, outs, frac = [], [], [], []
+    for t in range(1, T + 1):
+        ins.append(x); trs.append(False)
+        y = ora.apply(x, False).numpy()
+        outs.append(y)
+        frac.append(unrevealed_fraction(ora, x, False))
+        a = np.abs(y)
+        x = np.where(a > 0, y / np.where(a > 0, a, 1.0), 0.0)
+    return {"n": n, "seed": seed, "ins": ins, "trs": trs, "outs": outs, "frac": frac}
+
+
 def spectral_reference(make_oracle, n, seed, K=30):
     """Power iterations of the spectral method at size n (m = 2n): every product's input,
     flag and output."""
@@ -887,7 +909,7 @@ def max_rel_dev(a, b, head=0):
     its own rounding there scales with the norm."""
     import torch
     bt = torch.from_numpy(b).to(device=a.device)
-    d = (a.double() - bt).abs()
+    d = (a.to(bt.dtype) - bt).abs()
     h = min(int(head), bt.numel())
     s = bt.abs().max().item()
     e = (d[h:].max().item() / s if s > 0 else d[h:].max().item()) if h < bt.numel() else 0.0
@@ -1087,11 +1109,37 @@ def accuracy_grad(kind, ref, seed):
     if kind == "adjoint":
         res["grad_x1_rel_error"] = rel(xt.grad.double().cpu().numpy(), ref["grad_x1"])
     res["how"] = ("FP32 reverse mode (autograd.trajectory) against the oracle's float64 autograd, "
-                  "relative 2-norm error of each gradient, at reduced n; the whole trajectory for the "
-                  "adjoint workload, the first %d iterations for ISTA, whose converging residuals make "
-                  "later FP32 and FP64 trajectories separate by their conditioning, not by the reverse "
-                  "mode" % K_ACC_ISTA)
+                  "relative 2-norm error of each gradient, at reduced n over the first %d products of the "
+                  "adjoint workload and the first %d ISTA iterations: both trajectories converge (the "
+                  "oracle's alpha_t / ||x_t|| falls below the FP32 unit roundoff over 1e-5 after about "
+                  "20 products), and later FP32 and FP64 trajectories separate by that conditioning, not "
+                  "by the reverse mode" % (T_ACC_ADJ, K_ACC_ISTA))
     return res
+
+
+def accuracy_complex(ref):
+    """Complex workload at reduced n, complex FP64, every product teacher-forced."""
+    import torch
+    import paper_2101_07464_gb300 as hd
+    st = hd.HDComplex(ref["n"], len(ref["ins"]), ref["seed"], "f64")
+    errs, ndef = [], []
+    for x, tr, yo in zip(ref["ins"], ref["trs"], ref["outs"]):
+        xt = torch.from_numpy(x).to("cuda")
+        y = st.apply(xt, tr)
+        errs.append(max_rel_dev(y, yo, len(errs) + 1))
+        ndef.append(abs((y.norm() / xt.norm()).item() - 1.0))
+    st.close()
+    ok = []
+    for e, f in zip(errs, ref["frac"]):
+        if f < COND_MIN["f64"]:
+            break
+        ok.append(e)
+    return {"n": ref["n"], "teacher_forced_error": per_t(errs), "norm_defect": per_t(ndef),
+            "unrevealed_fraction": per_t(ref["frac"]),
+            "max_error_while_conditioned": _g3(max(ok)) if ok else None, "steps_conditioned": len(ok),
+            "how": "complex FP64, every product teacher-forced on the oracle's inputs (hd_complex_apply); "
+                   "norm_defect = | ||y_t|| / ||x_t|| - 1 | (unitarity); parity is meaningful while the "
+                   "oracle's alpha_t / ||x_t|| >= 1.1e-4"}
 
 
 def measure_c1(args):
@@ -1126,6 +1174,58 @@ def measure_c1(args):
                 "value": float(n) * T * T / (res["us_per_product_graph"] * T * 1e-6), "unit": UNIT,
                 "timing": "CUDA events around 200 back-to-back trajectories (hd_run), per product"})
     return res
+
+
+def complex_phase(y):
+    """Entrywise phase y / |y| (0 where y is 0): the dynamics of the complex workload."""
+    import torch
+    a = torch.abs(y)
+    return torch.where(a > 0, y / torch.where(a > 0, a, torch.ones_like(a)), torch.zeros_like(y))
+
+
+def measure_complex(args, rank, world, dist):
+    """Complex ensemble (the paper's section "Other Random Matrix Ensembles"): Q ~ Haar on the
+    unitary group U(n), n = 10^6, T = 100 products of Q, x_{t+1} = y_t / |y_t| entrywise,
+    complex FP64 (hd_complex_apply, host-driven, the phase map in torch).  CUDA events around
+    whole trajectories.  Algorithmic work: five passes of complex multiply-adds over the stacks
+    per step (4 real FMAs each), 40 n k flops at k = t - 1.  All products are Q: under Q / Q^H
+    alternation the phase map converges (the oracle's alpha_t / ||x_t|| falls to 1.5e-4 by
+    step 20 at n = 2e4), after which every new reflector is built from rounding."""
+    import torch
+    import synth
+    import paper_2101_07464_gb300 as hd
+    n, T = 10 ** 6, 100
+    st = hd.HDComplex(n, T, args.seed, "f64", trial=rank)
+    x1 = torch.complex(torch.tensor(synth.x1(n, args.seed, trial=rank)),
+                       torch.tensor(synth.x1(n, args.seed + 7, trial=rank))).to("cuda")
+
+    def run():
+        st.reset()
+        x = x1
+        for t in range(1, T + 1):
+            x = complex_phase(st.apply(x, False))
+        return x
+
+    run()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 3
+    e0.record(stream)
+    for _ in range(reps):
+        run()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    secs = max_over_ranks(e0.elapsed_time(e1) / 1e3 / reps, dist)
+    st.close()
+    flops = 40.0 * n * T * (T - 1) / 2.0
+    return {"value": job_throughput(float(n) * T * T, world, secs), "unit": UNIT, "ms_per_trajectory": secs * 1e3,
+            "n": n, "T": T, "dtype": "c128 (complex FP64)",
+            "fp64_TFLOPs": flops / secs / 1e12,
+            "config": "Haar U(n), n=1e6, T=100, all Q, x_{t+1} = y_t / |y_t| entrywise",
+            "timing": "CUDA events around 3 host-driven trajectories (hd_complex_apply, torch phase map)"}
 
 
 def roofline_of(prof, dtype, n, T, peaks):
@@ -1267,6 +1367,12 @@ def run_ours(args):
             spectral = measure_spectral(args, rank, world, dist)
         except Exception as exc:   # reported in the line, the headline stands
             spectral = {"error": "%s: %s" % (type(exc).__name__, exc)}
+    cplx = None
+    if not args.no_complex:
+        try:
+            cplx = measure_complex(args, rank, world, dist)
+        except Exception as exc:   # reported in the line, the headline stands
+            cplx = {"error": "%s: %s" % (type(exc).__name__, exc)}
     large = None
     if not args.no_large:
         try:
@@ -1307,6 +1413,8 @@ def run_ours(args):
                                         "how": "reduced n, FP64, 30 power iterations, every product teacher-forced"}
             if large is not None and "forward" in large:
                 large["accuracy"] = accuracy_large(refs["large"], args.seed)
+            if cplx is not None and "value" in cplx:
+                cplx["accuracy"] = accuracy_complex(refs["complex"])
         del refs
 
     if rank == 0:
@@ -1328,7 +1436,7 @@ def run_ours(args):
                 "accuracy": accuracy,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk, other: side, "c1": c1, "batched_amp": amp, "adjoint": adj, "ista": ista,
-                "paper_ista": paper_ista, "spectral": spectral, "large": large}
+                "paper_ista": paper_ista, "spectral": spectral, "complex": cplx, "large": large}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -299,6 +299,42 @@ HD_API int hd_usv_apply(hd_state* U, hd_state* V, const double* s, const void* x
  * (iters or reps < 1, null output), HD_ERR_CUDA. */
 HD_API int hd_fp64_fma_rate(int32_t iters, int32_t reps, double* tflops_host, void* stream);
 
+/* ---- Complex ensembles ---------------------------------------------------------------
+ * The paper's section "Other Random Matrix Ensembles" carries Householder Dice over to
+ * complex matrices, with M^T replaced by M^H and the complex reflector of eq.
+ * Householder_c, H(v) = -e^{-i theta}[I - w w^H / (1 + r)], w = v/||v|| + e^{i theta} e_1,
+ * v_1/||v|| = r e^{i theta} (theta = 0 when v_1 = 0), which maps v to ||v|| e_1.  For Q ~ Haar
+ * on the unitary group U(n) the algorithm is Algorithm 2 with adjoints where a reflector acts
+ * on the left of the revealed block:
+ *   M_t = Q:    p = R_{t-1}...R_1 x, R_t = H_t(p), L_t = H_t(g_t), y = L_1^H...L_t^H R_t p;
+ *   M_t = Q^H:  p = L_{t-1}...L_1 x, L_t = H_t(p), R_t = H_t(g_t), y = R_1^H...R_t^H L_t p.
+ * Draws: entry i of g_t is (N_{2i} + i N_{2i+1}) / sqrt(2), N the standard normals of step
+ * t's Philox stream (key = seed, counter = (i, t, trial, 0): one Box-Muller pair per entry).
+ *
+ * hd_complex_create: a single-trial state for Q ~ Haar(U(n)) (ensemble HD_HAAR; HD_ERR_ARG
+ * for any other), 1 <= T_max <= min(n, 256) (HD_ERR_TMAX otherwise).  dtype HD_F64 stores
+ * vectors and stacks as interleaved complex FP64 pairs (re, im); HD_F32 as complex FP32 pairs
+ * with FP32 streaming arithmetic, and FP64 for every cross-thread sum, the reflector
+ * coefficients, the phases and the compact-WY factor S.  Allocates two stacks of n x T_max
+ * complex elements, two T_max x T_max FP64 complex factors and an n-vector up front;
+ * *out is owned by the caller (hd_complex_destroy).
+ * hd_complex_set_options: the Philox trial word (changing it after the first step gives
+ * HD_ERR_ARG; reset first) and the CUDA stream the work goes on (NULL = legacy stream).
+ * hd_complex_apply: y = Q x (adjoint = 0) or y = Q^H x (adjoint = 1), x and y distinct device
+ * vectors of n complex elements aligned to one element (16 bytes for HD_F64, 8 for HD_F32;
+ * HD_ERR_ARG otherwise); enqueued on the stream.  HD_ERR_TMAX after T_max products (state
+ * unchanged); after a launch failure (HD_ERR_CUDA) the state stays poisoned until reset.
+ * hd_complex_reset: forget all steps and re-key with seed (synchronises the stream).
+ * hd_complex_get_counts: products so far. */
+typedef struct hd_cstate hd_cstate;
+HD_API int hd_complex_create(int ensemble, int64_t n, int32_t T_max, uint64_t seed, int dtype,
+                             hd_cstate** out);
+HD_API int hd_complex_set_options(hd_cstate* st, uint32_t trial, void* stream);
+HD_API int hd_complex_apply(hd_cstate* st, const void* x, int adjoint, void* y);
+HD_API int hd_complex_reset(hd_cstate* st, uint64_t seed);
+HD_API int hd_complex_get_counts(const hd_cstate* st, int32_t* t);
+HD_API void hd_complex_destroy(hd_cstate* st);
+
 /* Number of kernels this state has launched (graph replays count their kernels). */
 HD_API int hd_get_launches(const hd_state* st, int64_t* launches);
 

@@ -44,6 +44,12 @@ _PROTOS = {
     "hd_set_trial_sigmas": (_c.c_int, [_P, _P]),
     "hd_set_engine": (_c.c_int, [_P, _c.c_int]),
     "hd_fp64_fma_rate": (_c.c_int, [_c.c_int32, _c.c_int32, _c.POINTER(_c.c_double), _P]),
+    "hd_complex_create": (_c.c_int, [_c.c_int, _c.c_int64, _c.c_int32, _c.c_uint64, _c.c_int, _c.POINTER(_P)]),
+    "hd_complex_set_options": (_c.c_int, [_P, _c.c_uint32, _P]),
+    "hd_complex_apply": (_c.c_int, [_P, _P, _c.c_int, _P]),
+    "hd_complex_reset": (_c.c_int, [_P, _c.c_uint64]),
+    "hd_complex_get_counts": (_c.c_int, [_P, _c.POINTER(_c.c_int32)]),
+    "hd_complex_destroy": (None, [_P]),
     "hd_adjoint_enable": (_c.c_int, [_P, _c.c_int]),
     "hd_adjoint_step": (_c.c_int, [_P, _P, _P, _P]),
     "hd_adjoint_restart": (_c.c_int, [_P]),
@@ -597,3 +603,56 @@ class USV:
     def close(self):
         self.U.close()
         self.V.close()
+
+
+class HDComplex:
+    """Owner of a complex Householder Dice state (Q ~ Haar(U(n)); hd_complex_* of include/hd.h).
+
+    HDComplex(n, T_max, seed, "f64").apply(x, adjoint) returns Q x or Q^H x as a new CUDA
+    tensor (complex128 for "f64", complex64 for "f32"), on torch's current stream.
+    """
+
+    def __init__(self, n, T_max, seed, dtype="f64", trial=0, stream=None, ensemble="haar"):
+        import torch
+        self.n, self.T_max, self.seed = n, T_max, seed
+        self.dtype_code = DTYPES.get(dtype, dtype)
+        self.torch_dtype = torch.complex128 if self.dtype_code == HD_F64 else torch.complex64
+        h = ctypes.c_void_p()
+        _check(lib().hd_complex_create(ENSEMBLES.get(ensemble, ensemble), int(n), int(T_max), int(seed),
+                                       self.dtype_code, ctypes.byref(h)), "hd_complex_create")
+        self.h = h
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        _check(lib().hd_complex_set_options(self.h, int(trial), _stream_ptr(stream)), "hd_complex_set_options")
+
+    def apply(self, x, adjoint=False, out=None):
+        import torch
+        if out is None:
+            out = torch.empty(self.n, dtype=self.torch_dtype, device=x.device)
+        for t, what in ((x, "x"), (out, "y")):
+            if t.dtype != self.torch_dtype or not t.is_cuda or not t.is_contiguous() or t.numel() != self.n:
+                raise ValueError("%s must be a contiguous CUDA %s tensor of %d elements" % (what, self.torch_dtype, self.n))
+        _check(lib().hd_complex_apply(self.h, x.data_ptr(), 1 if adjoint else 0, out.data_ptr()), "hd_complex_apply")
+        return out
+
+    def reset(self, seed=None):
+        if seed is not None:
+            self.seed = seed
+        _check(lib().hd_complex_reset(self.h, int(self.seed)), "hd_complex_reset")
+
+    def counts(self):
+        t = ctypes.c_int32()
+        _check(lib().hd_complex_get_counts(self.h, ctypes.byref(t)), "hd_complex_get_counts")
+        return t.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().hd_complex_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -6,6 +6,10 @@ import synth
 from oracle.hd import make_oracle
 
 TOL = {"f64": 1e-12, "f32": 1e-5}
+# Smallest alpha_t / ||x_t|| (the part of a step's input that the revealed reflectors do not
+# already fix) at which per-step parity is meaningful: the unit roundoff over the tolerance.
+# Below it the new reflector is built from a tail dominated by rounding (reading A13(i)).
+COND_MIN = {"f64": 1.1e-16 / 1e-12, "f32": 6.0e-8 / 1e-5}
 
 
 def next_input(y, t_next, transpose_next, m, n, seed):
@@ -71,8 +75,8 @@ def elem_err(a, b, head):
     its own rounding there scales with the vector norm and the length of its dot products
     (1.2e-11 absolute at n = 10^6, ||x|| = 10^3, with the GPU host's BLAS); the other rows
     carry rounding on the scale of the entries."""
-    a = np.asarray(a, dtype=np.float64)
-    b = np.asarray(b, dtype=np.float64)
+    a = np.asarray(a)
+    b = np.asarray(b)
     d = np.abs(a - b)
     h = min(int(head), b.shape[0])
     tail = d[h:].max() / np.abs(b).max() if h < b.shape[0] else 0.0

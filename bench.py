@@ -54,6 +54,7 @@ def parse(argv=None):
                     help="skip the accuracy fields (and the oracle reference values they need)")
     ap.add_argument("--no-c1", action="store_true", help="skip the small Ginibre configuration")
     ap.add_argument("--no-complex", action="store_true", help="skip the complex (unitary) workload")
+    ap.add_argument("--no-fig1a", action="store_true", help="skip the Fig. 1a run (10^5 lasso ISTA trials)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-amp", action="store_true", help="skip the batched AMP measurement")
     ap.add_argument("--amp-trials", type=int, default=4096)
@@ -756,6 +757,7 @@ def cpu_baseline_leg(args, n, T, want_accuracy):
     # input, transpose flag and output
     refs["paper_ista"] = lasso_reference(make_oracle, N_ACC_ISTA, args.seed)
     refs["complex"] = complex_reference(N_ACC_COMPLEX, T, args.seed)
+    refs["fig1a"] = fig1a_direct_reference(args.seed)
     refs["spectral"] = spectral_reference(make_oracle, N_ACC_SPECTRAL, args.seed)
     return cpu, refs
 
@@ -842,6 +844,33 @@ def lasso_reference(make_oracle, n, seed):
         x = soft_threshold(x + 0.3 * app(r, True), 0.6)
     return {"ensemble": "ginibre", "m": m, "n": n, "sigma": m ** -0.5, "seed": seed, "ins": ins, "trs": trs,
             "outs": outs, "frac": frac}
+
+
+FIG1A_DIRECT_TRIALS = 300
+
+
+def fig1a_direct_reference(seed):
+    """The direct approach of Fig. 1a (a dense Gin(n/2, n) matrix per trial, oracle/direct.py)
+    at n = 1000 over FIG1A_DIRECT_TRIALS trials: per-iteration mean MSE and its standard error."""
+    import numpy as np
+    from oracle.direct import ginibre
+    n, K = FIG1A_N, FIG1A_K
+    m = n // 2
+    rng = np.random.default_rng([seed, 1234])
+    curves = []
+    for _ in range(FIG1A_DIRECT_TRIALS):
+        beta = (rng.random(n) < 0.8) * 2.0 * rng.standard_normal(n)
+        w = 0.1 * rng.standard_normal(m)
+        A = ginibre(rng, m, n, m ** -0.5)
+        y = A @ beta + w
+        x, mse = np.zeros(n), []
+        for _ in range(K):
+            v = x + 0.3 * (A.T @ (y - A @ x))
+            x = np.sign(v) * np.maximum(np.abs(v) - 0.6, 0.0)
+            mse.append(float(np.sum((x - beta) ** 2) / n))
+        curves.append(mse)
+    c = np.array(curves)
+    return {"mean": c.mean(axis=0), "se": c.std(axis=0, ddof=1) / np.sqrt(len(curves)), "trials": len(curves)}
 
 
 def complex_reference(n, T, seed):
@@ -1228,6 +1257,70 @@ def measure_complex(args, rank, world, dist):
             "timing": "CUDA events around 3 host-driven trajectories (hd_complex_apply, torch phase map)"}
 
 
+FIG1A_N, FIG1A_K, FIG1A_TRIALS, FIG1A_CHUNK = 1000, 50, 100_000, 25_000
+
+
+def measure_fig1a(args, rank, world, dist):
+    """The paper's Fig. 1a experiment (Section 2.1) at its size: ISTA for the lasso on
+    Gin(m, n), n = 1000, m = 500, entries N(0, 1/m), beta* ~ 0.2 delta_0 + 0.8 N(0, 2^2),
+    w ~ N(0, 0.1^2), tau = 0.3, threshold 0.6, 50 iterations, over 10^5 independent trials:
+    the mean MSE (1/n) ||x^k - beta*||^2 per iteration with its standard error.  Batched HD
+    ISTA (hd_run with HD_DYN_ISTA, FP32 storage, one graph per chunk of 25,000 trials); x^k
+    recorded per step (x_record) and reduced on the GPU.  Wall clock around all chunks,
+    synchronised, including the per-chunk state creation and input uploads."""
+    import numpy as np
+    import torch
+    import synth
+    import paper_2101_07464_gb300 as hd
+    n, K = FIG1A_N, FIG1A_K
+    m, T = n // 2, 2 * FIG1A_K
+    flags = [alt(t) for t in range(1, T + 1)]
+    total = FIG1A_TRIALS
+    s1 = np.zeros(K)
+    s2 = np.zeros(K)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    t0 = time.perf_counter()
+    run_secs = 0.0
+    for c0 in range(0, total, FIG1A_CHUNK):
+        cnt = min(FIG1A_CHUNK, total - c0)
+        base = rank * total + c0
+        b = hd.HDBatch("ginibre", [m] * cnt, [n] * cnt, T, args.seed, "f32", trial=base)
+        b.set_trial_sigmas([m ** -0.5] * cnt)
+        rng_b = synth.rng(args.seed, 10, base)
+        beta = ((rng_b.random((cnt, n)) < 0.8) * 2.0 * rng_b.standard_normal((cnt, n))).astype(np.float32)
+        w = (0.1 * synth.rng(args.seed, 11, base).standard_normal((cnt, m))).astype(np.float32)
+        bt = torch.from_numpy(beta.reshape(-1)).cuda()
+        wt = torch.from_numpy(w.reshape(-1)).cuda()
+        xrec = torch.zeros((T, n * cnt), dtype=torch.float32, device="cuda")
+        out = torch.empty(n * cnt, dtype=torch.float32, device="cuda")
+        spec = hd.make_run_spec(flags, "ista", 0.6, use_graph=True, aux=wt, x_record=xrec, b=0.3)
+        torch.cuda.synchronize()
+        r0 = time.perf_counter()
+        hd.hd_run(b.h, spec, bt, out)
+        torch.cuda.synchronize()
+        run_secs += time.perf_counter() - r0
+        xs = xrec[1::2].reshape(K, cnt, n).double()
+        mse = ((xs - bt.double().reshape(1, cnt, n)) ** 2).mean(dim=2)
+        s1 += mse.sum(dim=1).cpu().numpy()
+        s2 += (mse ** 2).sum(dim=1).cpu().numpy()
+        del xrec, xs, mse
+        b.close()
+    secs = max_over_ranks(time.perf_counter() - t0, dist)
+    mean = s1 / total
+    se = np.sqrt(np.maximum(s2 / total - mean ** 2, 0.0) / (total - 1))
+    return {"trials": total * world, "n": n, "m": m, "iterations": K, "products": T, "dtype": "f32",
+            "seconds": secs, "seconds_in_hd_run": run_secs,
+            "mse_per_iteration": [_g3(v) for v in mean], "se_per_iteration": [_g3(v) for v in se],
+            "value": job_throughput(float(total) * n * T * T, world, run_secs), "unit": "trials*n*T^2/s",
+            "config": "Fig. 1a: lasso ISTA on Gin(n/2, n), n=1000, entries N(0, 1/m), 50 iterations, tau=0.3, "
+                      "threshold 0.6, beta* ~ 0.2 delta_0 + 0.8 N(0, 4), w ~ N(0, 0.01), 10^5 trials "
+                      "(chunks of 25,000 in one batched state each)",
+            "timing": "wall clock, synchronised: seconds covers state creation, inputs and reductions; "
+                      "seconds_in_hd_run the hd_run calls alone (value uses the latter)"}
+
+
 def roofline_of(prof, dtype, n, T, peaks):
     """Roofline of the dominant sweep (largest total time inside the timed trajectories):
     FP64 against the measured FP64 FMA rate (algorithmic flops), FP32 against the measured
@@ -1373,6 +1466,12 @@ def run_ours(args):
             cplx = measure_complex(args, rank, world, dist)
         except Exception as exc:   # reported in the line, the headline stands
             cplx = {"error": "%s: %s" % (type(exc).__name__, exc)}
+    fig1a = None
+    if not args.no_fig1a:
+        try:
+            fig1a = measure_fig1a(args, rank, world, dist)
+        except Exception as exc:   # reported in the line, the headline stands
+            fig1a = {"error": "%s: %s" % (type(exc).__name__, exc)}
     large = None
     if not args.no_large:
         try:
@@ -1415,6 +1514,17 @@ def run_ours(args):
                 large["accuracy"] = accuracy_large(refs["large"], args.seed)
             if cplx is not None and "value" in cplx:
                 cplx["accuracy"] = accuracy_complex(refs["complex"])
+            if fig1a is not None and "mse_per_iteration" in fig1a:
+                import numpy as np
+                d = refs["fig1a"]
+                hm = np.array(fig1a["mse_per_iteration"])
+                hs = np.array(fig1a["se_per_iteration"])
+                z = np.abs(hm - d["mean"]) / np.sqrt(hs ** 2 + d["se"] ** 2)
+                fig1a["accuracy"] = {"direct_trials": d["trials"], "direct_mse_per_iteration": [_g3(v) for v in d["mean"]],
+                                     "max_gap_in_combined_se": _g3(z.max()),
+                                     "how": "HD's mean MSE per iteration against the direct approach (dense "
+                                            "Gin(n/2, n) per trial, oracle/direct.py, same n) over its trials; "
+                                            "gap in units of the combined standard error"}
         del refs
 
     if rank == 0:
@@ -1436,7 +1546,7 @@ def run_ours(args):
                 "accuracy": accuracy,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk, other: side, "c1": c1, "batched_amp": amp, "adjoint": adj, "ista": ista,
-                "paper_ista": paper_ista, "spectral": spectral, "complex": cplx, "large": large}
+                "paper_ista": paper_ista, "spectral": spectral, "complex": cplx, "fig1a": fig1a, "large": large}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

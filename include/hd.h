@@ -145,8 +145,13 @@ HD_API int hd_probe(hd_state* st, const void* x, int transpose, void* y,
  *                     eta the soft threshold, a the threshold multiplier (1.1 in the batched
  *                     AMP workload), norms and counts per trial.  spec.aux = w (m-space);
  *                     x_out receives the last x^k (n-space).  The schedule must be Q, Q^T,
- *                     Q, ... (HD_ERR_ARG otherwise).                                       */
-typedef enum { HD_DYN_TANH = 1, HD_DYN_SIGN_MEM = 2, HD_DYN_NORM_TANH = 3, HD_DYN_AMP = 4 } hd_dynamics;
+ *                     Q, ... (HD_ERR_ARG otherwise).
+ *   HD_DYN_ISTA       ISTA for the lasso (Section 2.1), the same products and buffers as
+ *                     HD_DYN_AMP with a fixed threshold and step size and no Onsager term:
+ *                       x^{k+1} = eta(x^k + b Q^T z^k; a),   z^{k+1} = y - Q x^{k+1},
+ *                     a = the threshold (lambda tau in Section 2.1), b = the step size tau;
+ *                     z^0 = y is y - Q x^0 with x^0 = 0, so that product is not made.      */
+typedef enum { HD_DYN_TANH = 1, HD_DYN_SIGN_MEM = 2, HD_DYN_NORM_TANH = 3, HD_DYN_AMP = 4, HD_DYN_ISTA = 5 } hd_dynamics;
 
 typedef struct {
   int32_t T;                 /* number of products, 1 <= T <= T_max                      */
@@ -157,7 +162,7 @@ typedef struct {
                                 replay it on later calls with the same (T, flags,
                                 dynamics, a); the first call with use_graph must not
                                 happen while the state's stream is being captured       */
-  const void* aux;           /* HD_DYN_AMP: the noise w (packed m-space vector, device or
+  const void* aux;           /* HD_DYN_AMP / HD_DYN_ISTA: the noise w (packed m-space vector, device or
                                 page-locked host, copied at the start of every call);
                                 ignored otherwise                                       */
   /* Trajectory records, all optional (NULL = off).  Each is a device buffer of the state's
@@ -177,6 +182,8 @@ typedef struct {
                                 HD_ENGINE_NO_FUSE or reverse-mode recording)            */
   int64_t ld_rows;           /* elements between rows; >= the longest packed vector of the
                                 state when any record is given (HD_ERR_ARG otherwise)     */
+  double b;                  /* second coefficient of the dynamics (HD_DYN_ISTA: the step
+                                size); ignored otherwise                                  */
 } hd_run_spec;
 
 /* A whole trajectory of eq. (dynamics): resets the state (same seed, trial and sigma),

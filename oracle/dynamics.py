@@ -124,6 +124,39 @@ def amp_trace(state, beta, w, T, thr=1.1, cast=None):
     return tr
 
 
+def ista_trace(state, beta, w, T, theta, tau, cast=None):
+    """T products of ISTA for the lasso (Section 2.1): y = Q beta + w, x^0 = 0, and
+        x^{k+1} = eta(x^k + tau Q^T (y - Q x^k); theta),
+    as products: Q beta (t = 1), then Q^T z^k (even t, z^k = y - Q x^k; z^0 = y because
+    x^0 = 0, so Q x^0 is not formed) and Q x^{k+1} (odd t).  theta is the threshold
+    (lambda tau in the paper's notation).  cast and the returned lists are as in amp_trace:
+    products, updates (z^0, x^1, z^1, x^2, ...) and the updates after cast."""
+    c = cast if cast is not None else (lambda v: v)
+    beta = np.asarray(beta, dtype=np.float64)
+    w = np.asarray(w, dtype=np.float64)
+    q = np.asarray(state.apply(beta, transpose=False), dtype=np.float64)
+    y = q + w
+    z = c(y.copy())
+    x = np.zeros_like(beta)
+    tr = {"products": [q], "updates": [y.copy()], "used": [z]}
+    for t in range(2, T + 1):
+        if t % 2 == 0:
+            s = np.asarray(state.apply(z, transpose=True), dtype=np.float64)
+            x_new = soft_threshold(x + tau * s, theta)
+            tr["products"].append(s)
+            tr["updates"].append(x_new)
+            x = c(x_new)
+            tr["used"].append(x)
+        else:
+            q = np.asarray(state.apply(x, transpose=False), dtype=np.float64)
+            z_new = y - q
+            tr["products"].append(q)
+            tr["updates"].append(z_new)
+            z = c(z_new)
+            tr["used"].append(z)
+    return tr
+
+
 def amp(state, beta, w, T, thr=1.1):
     """T products of AMP (amp_trace without rounding).  Returns (xs, zs): the x^k after each
     Q^T product and the z^k (z^0 first)."""

@@ -20,15 +20,16 @@ DTYPES = {"f64": HD_F64, "f32": HD_F32}
 
 _LIB = None
 
-HD_DYN_TANH, HD_DYN_SIGN_MEM, HD_DYN_NORM_TANH, HD_DYN_AMP = 1, 2, 3, 4
-DYNAMICS = {"tanh": HD_DYN_TANH, "sign_mem": HD_DYN_SIGN_MEM, "norm_tanh": HD_DYN_NORM_TANH, "amp": HD_DYN_AMP}
+HD_DYN_TANH, HD_DYN_SIGN_MEM, HD_DYN_NORM_TANH, HD_DYN_AMP, HD_DYN_ISTA = 1, 2, 3, 4, 5
+DYNAMICS = {"tanh": HD_DYN_TANH, "sign_mem": HD_DYN_SIGN_MEM, "norm_tanh": HD_DYN_NORM_TANH, "amp": HD_DYN_AMP,
+            "ista": HD_DYN_ISTA}
 
 
 class hd_run_spec(ctypes.Structure):
     _fields_ = [("T", ctypes.c_int32), ("transpose", ctypes.POINTER(ctypes.c_uint8)),
                 ("dynamics", ctypes.c_int32), ("a", ctypes.c_double), ("use_graph", ctypes.c_int32),
                 ("aux", ctypes.c_void_p), ("y_record", ctypes.c_void_p), ("x_record", ctypes.c_void_p),
-                ("x_given", ctypes.c_void_p), ("ld_rows", ctypes.c_int64)]
+                ("x_given", ctypes.c_void_p), ("ld_rows", ctypes.c_int64), ("b", ctypes.c_double)]
 
 HD_ENGINE_NO_FUSE, HD_ENGINE_NO_PDL = 1, 2
 
@@ -241,9 +242,10 @@ def _rows_addr(t, what):
 
 
 def make_run_spec(transpose_flags, dynamics, a=0.0, use_graph=True, aux=None, y_record=None,
-                  x_record=None, x_given=None):
+                  x_record=None, x_given=None, b=0.0):
     """hd_run_spec for a schedule (sequence of 0/1 flags) and a built-in dynamics name/code.
-    aux: HD_DYN_AMP's noise vector w (CUDA or page-locked tensor, or an address).
+    aux: the noise vector w of HD_DYN_AMP / HD_DYN_ISTA (CUDA or page-locked tensor, or an address);
+    b: HD_DYN_ISTA's step size.
     y_record / x_record / x_given: optional T x L CUDA tensors of the state's dtype (row t-1
     for step t; L >= the longest packed vector): records of y_t and of f_t's result, and
     teacher-forced replacements of f_t's result (hd_run_spec)."""
@@ -264,7 +266,7 @@ def make_run_spec(transpose_flags, dynamics, a=0.0, use_graph=True, aux=None, y_
     spec = hd_run_spec(len(transpose_flags), ctypes.cast(flags, ctypes.POINTER(ctypes.c_uint8)),
                        DYNAMICS.get(dynamics, dynamics), float(a), 1 if use_graph else 0, aux_addr,
                        _rows_addr(y_record, "y_record"), _rows_addr(x_record, "x_record"),
-                       _rows_addr(x_given, "x_given"), int(ld))
+                       _rows_addr(x_given, "x_given"), int(ld), float(b))
     spec._flags = flags  # keep the array alive with the struct
     spec._aux = aux
     spec._rows = rows
@@ -444,10 +446,10 @@ class HDBatch:
     def _dims(self):
         return (int(self.off_n[-1]), int(self.off_m[-1]))
 
-    def autotune(self, schedule, dynamics, x1, a=0.0, reps=2, aux=None):
-        """hd_autotune on the trajectory (schedule, dynamics, a) from x1; leaves the state reset."""
+    def autotune(self, schedule, dynamics, x1, a=0.0, reps=2, aux=None, b=0.0):
+        """hd_autotune on the trajectory (schedule, dynamics, a, b) from x1; leaves the state reset."""
         import torch
-        spec = make_run_spec(schedule, dynamics, a, use_graph=False, aux=aux)
+        spec = make_run_spec(schedule, dynamics, a, use_graph=False, aux=aux, b=b)
         dmax = int(max(self._dims()))
         out = torch.empty(dmax, dtype=self.torch_dtype, device=x1.device)
         hd_autotune(self.h, spec, x1, out, reps)
@@ -550,10 +552,10 @@ class HD:
     def _dims(self):
         return (self.n, self.m)
 
-    def autotune(self, schedule, dynamics, x1, a=0.0, reps=2, aux=None):
-        """hd_autotune on the trajectory (schedule, dynamics, a) from x1; leaves the state reset."""
+    def autotune(self, schedule, dynamics, x1, a=0.0, reps=2, aux=None, b=0.0):
+        """hd_autotune on the trajectory (schedule, dynamics, a, b) from x1; leaves the state reset."""
         import torch
-        spec = make_run_spec(schedule, dynamics, a, use_graph=False, aux=aux)
+        spec = make_run_spec(schedule, dynamics, a, use_graph=False, aux=aux, b=b)
         dmax = int(max(self._dims()))
         out = torch.empty(dmax, dtype=self.torch_dtype, device=x1.device)
         hd_autotune(self.h, spec, x1, out, reps)

@@ -135,7 +135,8 @@ struct FuseSpec {
   double a = 0.0;
   void* xnext = nullptr;
   const void* xprev = nullptr;
-  int amp_mode = 0;          // HD_DYN_AMP: 1 after Q beta, 2 after Q^T z, 3 after Q x
+  int amp_mode = 0;          // HD_DYN_AMP / HD_DYN_ISTA: 1 after Q beta, 2 after Q^T z, 3 after Q x
+  double amp_tau = 1.0;      // step size of the x update (1 for AMP)
   void* amp_v = nullptr;
   void* amp_y = nullptr;
   const void* amp_w = nullptr;
@@ -169,6 +170,7 @@ int do_step(hd_state* st, const void* x, int transpose, void* y, const FuseSpec*
       b.base.xnext = (T*)fs->xnext;
       b.base.xprev = (const T*)fs->xprev;
       b.base.amp_mode = fs->amp_mode;
+      b.base.amp_tau = (T)fs->amp_tau;
       b.base.amp_v = (T*)fs->amp_v;
       b.base.amp_y = (T*)fs->amp_y;
       b.base.amp_w = (const T*)fs->amp_w;
@@ -326,8 +328,10 @@ int run_amp(hd_state* st, const hd_run_spec* sp) {
     FuseSpec fs;
     fs.skip_dots = prev_fused;
     fs.fuse = st->fuse && t < sp->T && !(st->adj && st->adj->on);
-    fs.dyn = HD_DYN_AMP;
+    const int ista = sp->dynamics == HD_DYN_ISTA;
+    fs.dyn = sp->dynamics;
     fs.a = sp->a;
+    fs.amp_tau = ista ? sp->b : 1.0;
     fs.amp_mode = mode;
     fs.amp_v = (mode == 2) ? st->amp_x : st->amp_z;
     fs.amp_y = st->amp_y;
@@ -353,10 +357,10 @@ int run_amp(hd_state* st, const hd_run_spec* sp) {
                              (T*)st->amp_z, st->amp_zsq, st->stream);
     else if (mode == 2)
       e = launch_amp_x<T>(cnt, st->d_off[0], st->d_off[1], (const T*)st->yw, (T*)st->amp_x, st->amp_zsq, sp->a,
-                          st->amp_nnz, st->stream);
+                          fs.amp_tau, ista, st->amp_nnz, st->stream);
     else
       e = launch_amp_z<T>(cnt, st->d_off[1], (const T*)st->amp_y, (const T*)st->yw, (T*)st->amp_z, st->amp_nnz,
-                          st->amp_zsq, st->stream);
+                          ista, st->amp_zsq, st->stream);
     if (e != cudaSuccess) return cuda_fail(st, e);
     st->launches += 1;
     if (fs.xrec) {
@@ -391,13 +395,14 @@ int amp_buffers(hd_state* st) {
 }
 
 int run_any(hd_state* st, const hd_run_spec* sp) {
-  if (sp->dynamics == HD_DYN_AMP)
+  if (sp->dynamics == HD_DYN_AMP || sp->dynamics == HD_DYN_ISTA)
     return (st->dtype == HD_F64) ? run_amp<double>(st, sp) : run_amp<float>(st, sp);
   return (st->dtype == HD_F64) ? run_steps<double>(st, sp) : run_steps<float>(st, sp);
 }
 
 bool graph_matches(const hd_state* st, const hd_run_spec* sp) {
-  if (!st->gexec || st->g_T != sp->T || st->g_dyn != sp->dynamics || st->g_a != sp->a) return false;
+  if (!st->gexec || st->g_T != sp->T || st->g_dyn != sp->dynamics || st->g_a != sp->a || st->g_b != sp->b)
+    return false;
   if (st->g_seed != st->seed || st->g_trial != st->trial || st->g_sigma != st->sigma) return false;
   if (st->g_sigma_gen != st->sigma_gen) return false;
   if (st->g_tune_gen != st->tune_gen) return false;
@@ -806,10 +811,11 @@ HD_API int hd_run(hd_state* st, const hd_run_spec* sp, const void* x1, void* x_o
   if (st->poisoned) return st->poisoned;
   if (sp->T < 1 || sp->T > st->Tm) return HD_ERR_TMAX;
   if (sp->dynamics != HD_DYN_TANH && sp->dynamics != HD_DYN_SIGN_MEM && sp->dynamics != HD_DYN_NORM_TANH &&
-      sp->dynamics != HD_DYN_AMP)
+      sp->dynamics != HD_DYN_AMP && sp->dynamics != HD_DYN_ISTA)
     return HD_ERR_ARG;
   if (sp->dynamics == HD_DYN_NORM_TANH && st->count != 1) return HD_ERR_ARG;
-  const bool amp = sp->dynamics == HD_DYN_AMP;
+  const bool amp = sp->dynamics == HD_DYN_AMP || sp->dynamics == HD_DYN_ISTA;
+  if (sp->dynamics == HD_DYN_ISTA && !std::isfinite(sp->b)) return HD_ERR_ARG;
   if (amp) {
     if (!sp->aux || st->ens != HD_GINIBRE) return HD_ERR_ARG;
     for (int t = 0; t < sp->T; t++)
@@ -897,6 +903,7 @@ HD_API int hd_run(hd_state* st, const hd_run_spec* sp, const void* x1, void* x_o
       st->g_T = sp->T;
       st->g_dyn = sp->dynamics;
       st->g_a = sp->a;
+      st->g_b = sp->b;
       st->g_seed = st->seed;
       st->g_trial = st->trial;
       st->g_sigma = st->sigma;

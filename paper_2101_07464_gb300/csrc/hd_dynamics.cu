@@ -116,15 +116,15 @@ __device__ __forceinline__ T soft_thr(T r, T theta) {
 template <typename T>
 __global__ void __launch_bounds__(kAmpThreads) k_amp_x(const int64_t* offn, const int64_t* offm,
                                                        const T* __restrict__ sv, T* x, const double* zsq,
-                                                       double a, int* nnz) {
+                                                       double a, T tau, int ista, int* nnz) {
   __shared__ double red[kAmpThreads / 32];
   const int i = blockIdx.x;
   const int64_t r0 = offn[i], r1 = offn[i + 1];
   const double mi = (double)(offm[i + 1] - offm[i]);
-  const T theta = (T)(a * sqrt(zsq[i] / mi));
+  const T theta = ista ? (T)a : (T)(a * sqrt(zsq[i] / mi));
   double c = 0.0;
   for (int64_t r = r0 + threadIdx.x; r < r1; r += kAmpThreads) {
-    const T v = soft_thr(x[r] + sv[r], theta);
+    const T v = soft_thr(fma(tau, sv[r], x[r]), theta);
     x[r] = v;
     c += (v != T(0)) ? 1.0 : 0.0;
   }
@@ -134,11 +134,12 @@ __global__ void __launch_bounds__(kAmpThreads) k_amp_x(const int64_t* offn, cons
 
 template <typename T>
 __global__ void __launch_bounds__(kAmpThreads) k_amp_z(const int64_t* offm, const T* __restrict__ ymeas,
-                                                       const T* __restrict__ q, T* z, const int* nnz, double* zsq) {
+                                                       const T* __restrict__ q, T* z, const int* nnz, int ista,
+                                                       double* zsq) {
   __shared__ double red[kAmpThreads / 32];
   const int i = blockIdx.x;
   const int64_t r0 = offm[i], r1 = offm[i + 1];
-  const T ons = (T)((double)nnz[i] / (double)(r1 - r0));
+  const T ons = ista ? T(0) : (T)((double)nnz[i] / (double)(r1 - r0));
   double s = 0.0;
   for (int64_t r = r0 + threadIdx.x; r < r1; r += kAmpThreads) {
     const T v = fma(z[r], ons, ymeas[r] - q[r]);
@@ -157,14 +158,14 @@ cudaError_t launch_amp_init(int count, const int64_t* offm, const T* q, const T*
 }
 template <typename T>
 cudaError_t launch_amp_x(int count, const int64_t* offn, const int64_t* offm, const T* sv, T* x,
-                         const double* zsq, double a, int* nnz, cudaStream_t s) {
-  k_amp_x<T><<<count, kAmpThreads, 0, s>>>(offn, offm, sv, x, zsq, a, nnz);
+                         const double* zsq, double a, double tau, int ista, int* nnz, cudaStream_t s) {
+  k_amp_x<T><<<count, kAmpThreads, 0, s>>>(offn, offm, sv, x, zsq, a, (T)tau, ista, nnz);
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_amp_z(int count, const int64_t* offm, const T* ymeas, const T* q, T* z, const int* nnz,
-                         double* zsq, cudaStream_t s) {
-  k_amp_z<T><<<count, kAmpThreads, 0, s>>>(offm, ymeas, q, z, nnz, zsq);
+                         int ista, double* zsq, cudaStream_t s) {
+  k_amp_z<T><<<count, kAmpThreads, 0, s>>>(offm, ymeas, q, z, nnz, ista, zsq);
   return cudaGetLastError();
 }
 
@@ -172,8 +173,8 @@ cudaError_t launch_amp_z(int count, const int64_t* offm, const T* ymeas, const T
   template cudaError_t launch_amp_init<T>(int, const int64_t*, const T*, const T*, T*, T*, double*,  \
                                           cudaStream_t);                                             \
   template cudaError_t launch_amp_x<T>(int, const int64_t*, const int64_t*, const T*, T*,            \
-                                       const double*, double, int*, cudaStream_t);                   \
-  template cudaError_t launch_amp_z<T>(int, const int64_t*, const T*, const T*, T*, const int*,      \
+                                       const double*, double, double, int, int*, cudaStream_t);      \
+  template cudaError_t launch_amp_z<T>(int, const int64_t*, const T*, const T*, T*, const int*, int, \
                                        double*, cudaStream_t);
 HD_AMP_INST(float)
 HD_AMP_INST(double)

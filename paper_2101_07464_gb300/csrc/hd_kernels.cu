@@ -1326,7 +1326,8 @@ __global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_out_gin(BatchStep
   // not needed; the column pass forms the dots of x_{t+1} with V_N and B_n instead
   const int ncc = FUSE ? nc : kN;   // column-owner columns
   WtSmem<T> sm(dsm_raw, blockDim.x >> 5, cfg.nbuf, nc, FUSE ? 3 : 1, ncc, 1);
-  const bool amp = FUSE && p.dyn == 4;
+  const bool ista = FUSE && p.dyn == 5;
+  const bool amp = FUSE && (p.dyn == 4 || ista);
   const int amode = amp ? p.amp_mode : 0;
   const ColSrc<T> src{(const T*)p.N.V, p.N.ld, kN, (const T*)p.Bn, p.ldBn};
   const int64_t dim = p.N.dim;
@@ -1361,7 +1362,8 @@ __global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_out_gin(BatchStep
       [&]() {   // outputs of the preceding kernel's finalisation
         if (amode == 2 || amode == 3) {
           const double mi = (double)bs.desc[cc.trial].st[1].dim;
-          amp_s = (amode == 2) ? (T)(p.dyn_a * sqrt(p.amp_zsq[cc.trial] / mi)) : (T)((double)p.amp_nnz[cc.trial] / mi);
+          if (ista) amp_s = (amode == 2) ? p.dyn_a : T(0);
+          else amp_s = (amode == 2) ? (T)(p.dyn_a * sqrt(p.amp_zsq[cc.trial] / mi)) : (T)((double)p.amp_nnz[cc.trial] / mi);
         }
         for (int j = threadIdx.x; j < sm.cpad; j += blockDim.x) {
           T c0 = T(0), c1 = T(0);
@@ -1398,11 +1400,11 @@ __global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_out_gin(BatchStep
             if (amode == 1) {          // y = Q beta + w; z = y
               xn = yi + sm.srow(st, 1)[lane];
               p.amp_y[r] = xn;
-            } else if (amode == 2) {   // x = eta(x + Q^T z; theta)
-              const T v = sm.srow(st, 1)[lane] + yi;
+            } else if (amode == 2) {   // x = eta(x + tau Q^T z; theta), tau = 1 for AMP
+              const T v = fma(p.amp_tau, yi, sm.srow(st, 1)[lane]);
               const T m = fabs(v) - amp_s;
               xn = (m > T(0)) ? copysign(m, v) : T(0);
-            } else if (amode == 3) {   // z = y - Q x + z ||x||_0 / m
+            } else if (amode == 3) {   // z = y - Q x + z ||x||_0 / m (AMP; the factor is 0 for ISTA)
               xn = fma(sm.srow(st, 1)[lane], amp_s, sm.srow(st, 2)[lane] - yi);
             } else {
               xn = fused_dyn<T>(p.dyn, p.dyn_a, yi, need_prev ? sm.srow(st, 1)[lane] : T(0));

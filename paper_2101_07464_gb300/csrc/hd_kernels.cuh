@@ -124,6 +124,9 @@ struct StepPlan {
   const T* amp_w;       // the noise w (mode 1)
   double* amp_zsq;      // per trial ||z||^2: written in modes 1 and 3, read in mode 2
   int* amp_nnz;         // per trial ||x||_0: written in mode 2, read in mode 3
+  // ISTA in the same sweep (dyn == kDynIsta): mode 2 is x = eta(x + amp_tau Q^T z; dyn_a) with
+  // the fixed threshold dyn_a, mode 3 is z = y - Q x (no Onsager term)
+  T amp_tau;
   // Trajectory records of the fused K3 (hd_run's y_record / x_record / x_given; null = off),
   // output-space packed bases of this step's rows: y_t, the library's own f_t result, and
   // the caller's replacement of that result (teacher forcing).

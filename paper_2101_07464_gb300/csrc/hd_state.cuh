@@ -123,7 +123,7 @@ struct hd_state {
   cudaGraphExec_t gexec = nullptr;
   std::vector<uint8_t> g_flags;
   int g_T = 0, g_dyn = 0;
-  double g_a = 0.0, g_sigma = 0.0;
+  double g_a = 0.0, g_b = 0.0, g_sigma = 0.0;
   int64_t g_sigma_gen = -1;
   uint64_t g_seed = 0;
   uint32_t g_trial = 0;

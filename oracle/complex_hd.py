@@ -1,4 +1,4 @@
-"""Complex Householder Dice on the unitary group (test infrastructure only).
+"""Complex Householder Dice: the unitary group, complex Ginibre and GUE (test infrastructure only).
 
 The paper's section "Other Random Matrix Ensembles" states that the construction carries over
 to complex matrices, with M^T replaced by M^H, and gives the complex reflector of
@@ -18,6 +18,18 @@ block.  Q = L_1^H ... L_t^H [I_t 0; 0 Q~] R_t ... R_1 with Q~ ~ Haar(U(n - t)):
 H_k(p) is the identity on the first k coordinates and H(p[k:]) on the rest (eq.
 Householder_e), the identity when p[k:] = 0.  In the real case H^H = H^T = H and this is
 Algorithm 2.
+
+Complex Ginibre CGin(m, n) (entries sigma CN(0, 1)): Algorithm 1 with the same adjoints.  Its
+revealed part is sum_i u_i v_i^H, and the hidden block sits between L^H and R (Q = L_1^H ...
+L_l^H [revealed; 0 G~] R_r ... R_1):
+
+  * Q step:   r <- r + 1, g in C^m drawn on rows l..m-1 (Z_{1:l} g), p = R_{r-1} ... R_1 x,
+              R_r = H_r(p), u_t = L_1^H ... L_l^H (Z g), v_t = R_1^H ... R_r^H e_r,
+              y = sum_{i <= t} (v_i^H x) u_i;
+  * Q^H step: l <- l + 1, g in C^n drawn on rows r..n-1, L_l = H_l(L_{l-1} ... L_1 x),
+              u_t = L_1^H ... L_l^H e_l, v_t = R_1^H ... R_r^H (Z g), y = sum_i (u_i^H x) v_i.
+
+GUE(n) = (Q + Q^H) / sqrt(2) for Q ~ CGin(n, n) (two products of one square state per query).
 
 Complex draws: entry i of step t's vector g_t is (N_{2i} + i N_{2i+1}) / sqrt(2), with N_j
 the j-th normal of step t's Philox stream (the pair that one Box-Muller transform gives), so
@@ -148,3 +160,70 @@ class ComplexHaarOracle:
                 z = h.apply_h(z)
             cols.append(z)
         return torch.stack(cols, dim=1)
+
+
+def apply_h_reversed(refls, z):
+    """refls[0]^H refls[1]^H ... refls[-1]^H z (the last reflector acts first)."""
+    for h in reversed(refls):
+        z = h.apply_h(z)
+    return z
+
+
+class ComplexGinibreOracle:
+    """Algorithm 1 on complex matrices: y_t = M_t x_t, M_t in {Q, Q^H}, Q ~ CGin(m, n) with
+    entries sigma CN(0, 1), one reflector at a time, in the paper's order."""
+
+    def __init__(self, m, n, T_max, seed, trial=0, sigma=1.0):
+        if T_max > min(m, n):
+            raise ValueError("Algorithm 1 requires T <= min(m, n)")
+        self.m, self.n, self.T_max = m, n, T_max
+        self.seed, self.trial, self.sigma = seed, trial, sigma
+        self.R, self.L, self.u, self.v = [], [], [], []
+        self.t = self.r = self.l = 0
+
+    def apply(self, x, adjoint=False):
+        t = self.t + 1
+        if t > self.T_max:
+            raise ValueError("step would exceed T_max")
+        x = _cvec(x)
+        if not adjoint:
+            self.r += 1
+            g = self.sigma * torch.as_tensor(complex_gaussian_vector(self.seed, self.trial, t, self.m, self.l))
+            p = x
+            for h in self.R:
+                p = h.apply(p)                                   # R_{r-1} ... R_1 x
+            self.R.append(ComplexReflector(self.r - 1, p))       # R_r = H_r(p)
+            self.u.append(apply_h_reversed(self.L, g))           # L_1^H ... L_l^H Z g
+            self.v.append(apply_h_reversed(self.R, unit(self.n, self.r - 1)))   # R_1^H ... R_r^H e_r
+            y = torch.zeros(self.m, dtype=C128)
+            for ui, vi in zip(self.u, self.v):                   # sum_i (v_i^H x) u_i
+                y = y + torch.vdot(vi, x) * ui
+        else:
+            self.l += 1
+            g = self.sigma * torch.as_tensor(complex_gaussian_vector(self.seed, self.trial, t, self.n, self.r))
+            q = x
+            for h in self.L:
+                q = h.apply(q)                                   # L_{l-1} ... L_1 x
+            self.L.append(ComplexReflector(self.l - 1, q))       # L_l = H_l(q)
+            self.u.append(apply_h_reversed(self.L, unit(self.m, self.l - 1)))   # L_1^H ... L_l^H e_l
+            self.v.append(apply_h_reversed(self.R, g))           # R_1^H ... R_r^H Z g
+            y = torch.zeros(self.n, dtype=C128)
+            for ui, vi in zip(self.u, self.v):                   # sum_i (u_i^H x) v_i
+                y = y + torch.vdot(ui, x) * vi
+        self.t = t
+        return y
+
+    def revealed(self):
+        """sum_i u_i v_i^H (m x n): the part of Q built so far (the whole Q once all of it is
+        revealed)."""
+        Q = torch.zeros(self.m, self.n, dtype=C128)
+        for ui, vi in zip(self.u, self.v):
+            Q = Q + torch.outer(ui, vi.conj())
+        return Q
+
+
+def gue_apply(gin, x):
+    """W x for W = (Q + Q^H) / sqrt(2) ~ GUE(n): a Q and a Q^H product of one square complex
+    Ginibre state."""
+    x = _cvec(x)
+    return (gin.apply(x, False) + gin.apply(x, True)) / math.sqrt(2.0)

@@ -118,3 +118,78 @@ def test_revealed_unitary_trace_moments():
                          (a1 ** 2, 2.0), (a1 ** 3, 6.0), (np.abs(t2) ** 2, 2.0)):
         se = sample.std(ddof=1) / np.sqrt(trials)
         assert abs(sample.mean() - want) <= 4.5 * se, (sample.mean(), want, se)
+
+
+# ---- complex Ginibre (Algorithm 1 with adjoints) and GUE ------------------------------------
+from oracle.complex_hd import ComplexGinibreOracle, gue_apply   # noqa: E402
+
+
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_complex_ginibre_first_step_closed_form(adjoint):
+    """Step 1: v_1 = x / ||x|| (R_1^H e_1 = x/||x||), u_1 = g, so y_1 = ||x|| g (sigma g)."""
+    m, n, seed, sigma = 7, 11, 3, 0.5
+    x = crand(m if adjoint else n, 4)
+    y = ComplexGinibreOracle(m, n, 3, seed, sigma=sigma).apply(x, adjoint).numpy()
+    g = sigma * complex_gaussian_vector(seed, 0, 1, n if adjoint else m, 0)
+    np.testing.assert_allclose(y, np.linalg.norm(x) * g, rtol=0, atol=1e-13 * np.linalg.norm(x))
+
+
+@pytest.mark.parametrize("m,n", [(6, 6), (5, 8), (8, 5)])
+def test_complex_ginibre_revealed_part_reproduces_queries(m, n):
+    """Every earlier query is reproduced by the revealed part sum_i u_i v_i^H (its hidden
+    block never meets an earlier input), for mixed Q / Q^H schedules, rectangular both ways."""
+    T = min(m, n)
+    sched = [t % 3 == 1 for t in range(T)]
+    o = ComplexGinibreOracle(m, n, T, 21)
+    qs, ys = [], []
+    for t in range(T):
+        x = crand(m if sched[t] else n, 30 + t)
+        ys.append(o.apply(x, sched[t]).numpy())
+        qs.append(x)
+    Q = o.revealed().numpy()
+    for t in range(T):
+        M = Q.conj().T if sched[t] else Q
+        np.testing.assert_allclose(M @ qs[t], ys[t], rtol=0, atol=1e-12 * max(1.0, np.linalg.norm(ys[t])))
+
+
+def test_complex_ginibre_all_q_square_reconstruction_has_complex_gaussian_entries():
+    """Square, all Q, T = n: the revealed part is all of Q.  Over independent trials its
+    entries are CN(0, sigma^2): real and imaginary parts N(0, sigma^2 / 2) (KS), uncorrelated,
+    and E Q_ij^2 = 0 (circular symmetry: a planted real draw makes E Q^2 = sigma^2)."""
+    n, trials, sigma = 4, 800, 1.5
+    rng = np.random.default_rng(9)
+    qs = [rng.standard_normal(n) + 1j * rng.standard_normal(n) for _ in range(n)]
+    ent = []
+    for i in range(trials):
+        o = ComplexGinibreOracle(n, n, n, 77, trial=i, sigma=sigma)
+        for t in range(n):
+            o.apply(qs[t], False)
+        ent.append(o.revealed().numpy().reshape(-1))
+    ent = np.array(ent)
+    sd = sigma / math.sqrt(2.0)
+    for j in (0, 5, 15):
+        assert stats.kstest(ent[:, j].real / sd, "norm").pvalue > 1e-3
+        assert stats.kstest(ent[:, j].imag / sd, "norm").pvalue > 1e-3
+        sq = ent[:, j] ** 2
+        se = np.abs(sq).std(ddof=1) / math.sqrt(trials)
+        assert abs(sq.mean()) <= 4.5 * se, (j, sq.mean(), se)
+
+
+def test_gue_entry_laws_and_hermitian_revealed_block():
+    """W = (Q + Q^H)/sqrt(2): W_11 ~ N(0, sigma^2) real, W_12 ~ CN(0, sigma^2); and every
+    query pair W e_j, W e_k is consistent with a Hermitian W: e_k^H W e_j = conj(e_j^H W e_k)."""
+    n, trials = 5, 1500
+    w11, w12, herm = [], [], []
+    for i in range(trials):
+        o = ComplexGinibreOracle(n, n, 4, 5, trial=i)
+        c1 = gue_apply(o, unit(n, 0)).numpy()
+        c2 = gue_apply(o, unit(n, 1)).numpy()
+        w11.append(c1[0])
+        w12.append(c2[0])
+        herm.append(abs(c2[0] - np.conj(c1[1])))
+    w11, w12 = np.array(w11), np.array(w12)
+    assert np.abs(w11.imag).max() <= 1e-13
+    assert stats.kstest(w11.real, "norm").pvalue > 1e-3
+    assert stats.kstest(w12.real * math.sqrt(2.0), "norm").pvalue > 1e-3
+    assert stats.kstest(w12.imag * math.sqrt(2.0), "norm").pvalue > 1e-3
+    assert max(herm) <= 1e-12

@@ -1150,7 +1150,7 @@ def accuracy_complex(ref):
     """Complex workload at reduced n, complex FP64, every product teacher-forced."""
     import torch
     import paper_2101_07464_gb300 as hd
-    st = hd.HDComplex(ref["n"], len(ref["ins"]), ref["seed"], "f64")
+    st = hd.HDComplex("haar", ref["n"], ref["n"], len(ref["ins"]), ref["seed"], "f64")
     errs, ndef = [], []
     for x, tr, yo in zip(ref["ins"], ref["trs"], ref["outs"]):
         xt = torch.from_numpy(x).to("cuda")
@@ -1224,7 +1224,7 @@ def measure_complex(args, rank, world, dist):
     import synth
     import paper_2101_07464_gb300 as hd
     n, T = 10 ** 6, 100
-    st = hd.HDComplex(n, T, args.seed, "f64", trial=rank)
+    st = hd.HDComplex("haar", n, n, T, args.seed, "f64", trial=rank)
     x1 = torch.complex(torch.tensor(synth.x1(n, args.seed, trial=rank)),
                        torch.tensor(synth.x1(n, args.seed + 7, trial=rank))).to("cuda")
 

@@ -310,34 +310,48 @@ HD_API int hd_fp64_fma_rate(int32_t iters, int32_t reps, double* tflops_host, vo
  * The paper's section "Other Random Matrix Ensembles" carries Householder Dice over to
  * complex matrices, with M^T replaced by M^H and the complex reflector of eq.
  * Householder_c, H(v) = -e^{-i theta}[I - w w^H / (1 + r)], w = v/||v|| + e^{i theta} e_1,
- * v_1/||v|| = r e^{i theta} (theta = 0 when v_1 = 0), which maps v to ||v|| e_1.  For Q ~ Haar
- * on the unitary group U(n) the algorithm is Algorithm 2 with adjoints where a reflector acts
- * on the left of the revealed block:
- *   M_t = Q:    p = R_{t-1}...R_1 x, R_t = H_t(p), L_t = H_t(g_t), y = L_1^H...L_t^H R_t p;
- *   M_t = Q^H:  p = L_{t-1}...L_1 x, L_t = H_t(p), R_t = H_t(g_t), y = R_1^H...R_t^H L_t p.
+ * v_1/||v|| = r e^{i theta} (theta = 0 when v_1 = 0), which maps v to ||v|| e_1.  The
+ * reflectors enter as adjoints where they act on the left of the revealed block:
+ *   Q ~ Haar(U(n)) (Algorithm 2):
+ *     M_t = Q:    p = R_{t-1}...R_1 x, R_t = H_t(p), L_t = H_t(g_t), y = L_1^H...L_t^H R_t p;
+ *     M_t = Q^H:  the mirror image with L and R exchanged;
+ *   Q ~ CGin(m, n), entries sigma CN(0, 1) (Algorithm 1):
+ *     M_t = Q:    R_r = H_r(R_{r-1}...R_1 x), u_t = L_1^H...L_l^H (Z g_t), v_t = R_1^H...R_r^H e_r,
+ *                 y = sum_{i <= t} (v_i^H x) u_i;
+ *     M_t = Q^H:  the mirror image (L_l = H_l(L_{l-1}...L_1 x), u_t = L_1^H...L_l^H e_l,
+ *                 v_t = R_1^H...R_r^H (Z g_t), y = sum_i (u_i^H x) v_i).
  * Draws: entry i of g_t is (N_{2i} + i N_{2i+1}) / sqrt(2), N the standard normals of step
- * t's Philox stream (key = seed, counter = (i, t, trial, 0): one Box-Muller pair per entry).
+ * t's Philox stream (key = seed, counter = (i, t, trial, 0): one Box-Muller pair per entry);
+ * Ginibre draws are scaled by sigma and masked to the unrevealed rows.
  *
- * hd_complex_create: a single-trial state for Q ~ Haar(U(n)) (ensemble HD_HAAR; HD_ERR_ARG
- * for any other), 1 <= T_max <= min(n, 256) (HD_ERR_TMAX otherwise).  dtype HD_F64 stores
- * vectors and stacks as interleaved complex FP64 pairs (re, im); HD_F32 as complex FP32 pairs
- * with FP32 streaming arithmetic, and FP64 for every cross-thread sum, the reflector
- * coefficients, the phases and the compact-WY factor S.  Allocates two stacks of n x T_max
- * complex elements, two T_max x T_max FP64 complex factors and an n-vector up front;
- * *out is owned by the caller (hd_complex_destroy).
- * hd_complex_set_options: the Philox trial word (changing it after the first step gives
- * HD_ERR_ARG; reset first) and the CUDA stream the work goes on (NULL = legacy stream).
- * hd_complex_apply: y = Q x (adjoint = 0) or y = Q^H x (adjoint = 1), x and y distinct device
- * vectors of n complex elements aligned to one element (16 bytes for HD_F64, 8 for HD_F32;
- * HD_ERR_ARG otherwise); enqueued on the stream.  HD_ERR_TMAX after T_max products (state
- * unchanged); after a launch failure (HD_ERR_CUDA) the state stays poisoned until reset.
+ * hd_complex_create: a single-trial state for ensemble HD_HAAR (Q ~ Haar(U(n)), m == n, else
+ * HD_ERR_DIM) or HD_GINIBRE (Q ~ CGin(m, n)); 1 <= T_max <= min(m, n, 256) (HD_ERR_TMAX
+ * otherwise).  dtype HD_F64 stores vectors, stacks and (Ginibre) basis stores as interleaved
+ * complex FP64 pairs (re, im); HD_F32 as complex FP32 pairs with FP32 streaming arithmetic,
+ * and FP64 for every cross-thread sum, the reflector coefficients, the phases and the
+ * compact-WY factor S.  Allocates everything up front (two stacks of n x T_max and m x T_max
+ * complex elements, for Ginibre two basis stores of the same sizes, two T_max x T_max FP64
+ * complex factors, work vectors); *out is owned by the caller (hd_complex_destroy).
+ * hd_complex_set_options: the Ginibre entry scale sigma (> 0, finite; ignored for Haar), the
+ * Philox trial word (changing either after the first step gives HD_ERR_ARG; reset first)
+ * and the CUDA stream the work goes on (NULL = legacy stream).
+ * hd_complex_apply: y = Q x (adjoint = 0; x of n entries, y of m) or y = Q^H x (adjoint = 1;
+ * x of m, y of n), x and y distinct device vectors of complex elements aligned to one element
+ * (16 bytes for HD_F64, 8 for HD_F32; HD_ERR_ARG otherwise); enqueued on the stream.
+ * HD_ERR_TMAX after T_max products (state unchanged); after a launch failure (HD_ERR_CUDA)
+ * the state stays poisoned until reset.
+ * hd_complex_gue_apply: y = W x for W = (Q + Q^H)/sqrt(2) ~ GUE(n) (sigma = 1: W_ii ~ N(0, 1),
+ * W_ij ~ CN(0, 1)), Q the square complex Ginibre matrix of the state (HD_ERR_ARG for Haar or
+ * m != n): a Q and a Q^H product (T_max counts both; HD_ERR_TMAX when fewer than two are left)
+ * and their scaled sum, with the intermediate in a state-owned vector.
  * hd_complex_reset: forget all steps and re-key with seed (synchronises the stream).
  * hd_complex_get_counts: products so far. */
 typedef struct hd_cstate hd_cstate;
-HD_API int hd_complex_create(int ensemble, int64_t n, int32_t T_max, uint64_t seed, int dtype,
+HD_API int hd_complex_create(int ensemble, int64_t m, int64_t n, int32_t T_max, uint64_t seed, int dtype,
                              hd_cstate** out);
-HD_API int hd_complex_set_options(hd_cstate* st, uint32_t trial, void* stream);
+HD_API int hd_complex_set_options(hd_cstate* st, double sigma, uint32_t trial, void* stream);
 HD_API int hd_complex_apply(hd_cstate* st, const void* x, int adjoint, void* y);
+HD_API int hd_complex_gue_apply(hd_cstate* st, const void* x, void* y);
 HD_API int hd_complex_reset(hd_cstate* st, uint64_t seed);
 HD_API int hd_complex_get_counts(const hd_cstate* st, int32_t* t);
 HD_API void hd_complex_destroy(hd_cstate* st);

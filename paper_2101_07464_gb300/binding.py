@@ -45,9 +45,11 @@ _PROTOS = {
     "hd_set_trial_sigmas": (_c.c_int, [_P, _P]),
     "hd_set_engine": (_c.c_int, [_P, _c.c_int]),
     "hd_fp64_fma_rate": (_c.c_int, [_c.c_int32, _c.c_int32, _c.POINTER(_c.c_double), _P]),
-    "hd_complex_create": (_c.c_int, [_c.c_int, _c.c_int64, _c.c_int32, _c.c_uint64, _c.c_int, _c.POINTER(_P)]),
-    "hd_complex_set_options": (_c.c_int, [_P, _c.c_uint32, _P]),
+    "hd_complex_create": (_c.c_int, [_c.c_int, _c.c_int64, _c.c_int64, _c.c_int32, _c.c_uint64, _c.c_int,
+                                     _c.POINTER(_P)]),
+    "hd_complex_set_options": (_c.c_int, [_P, _c.c_double, _c.c_uint32, _P]),
     "hd_complex_apply": (_c.c_int, [_P, _P, _c.c_int, _P]),
+    "hd_complex_gue_apply": (_c.c_int, [_P, _P, _P]),
     "hd_complex_reset": (_c.c_int, [_P, _c.c_uint64]),
     "hd_complex_get_counts": (_c.c_int, [_P, _c.POINTER(_c.c_int32)]),
     "hd_complex_destroy": (None, [_P]),
@@ -608,34 +610,48 @@ class USV:
 
 
 class HDComplex:
-    """Owner of a complex Householder Dice state (Q ~ Haar(U(n)); hd_complex_* of include/hd.h).
-
-    HDComplex(n, T_max, seed, "f64").apply(x, adjoint) returns Q x or Q^H x as a new CUDA
-    tensor (complex128 for "f64", complex64 for "f32"), on torch's current stream.
+    """Owner of a complex Householder Dice state (hd_complex_* of include/hd.h): Q ~ Haar on
+    the unitary group U(n) (ensemble "haar", m == n) or Q ~ CGin(m, n) with entries sigma
+    CN(0, 1) ("ginibre").  apply(x, adjoint) returns Q x or Q^H x as a new CUDA tensor
+    (complex128 for "f64", complex64 for "f32"), on torch's current stream; gue(x) returns
+    (Q + Q^H) x / sqrt(2) for a square Ginibre state.
     """
 
-    def __init__(self, n, T_max, seed, dtype="f64", trial=0, stream=None, ensemble="haar"):
+    def __init__(self, ensemble, m, n, T_max, seed, dtype="f64", sigma=1.0, trial=0, stream=None):
         import torch
-        self.n, self.T_max, self.seed = n, T_max, seed
+        self.ensemble, self.m, self.n, self.T_max, self.seed = ensemble, m, n, T_max, seed
         self.dtype_code = DTYPES.get(dtype, dtype)
         self.torch_dtype = torch.complex128 if self.dtype_code == HD_F64 else torch.complex64
         h = ctypes.c_void_p()
-        _check(lib().hd_complex_create(ENSEMBLES.get(ensemble, ensemble), int(n), int(T_max), int(seed),
+        _check(lib().hd_complex_create(ENSEMBLES.get(ensemble, ensemble), int(m), int(n), int(T_max), int(seed),
                                        self.dtype_code, ctypes.byref(h)), "hd_complex_create")
         self.h = h
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
-        _check(lib().hd_complex_set_options(self.h, int(trial), _stream_ptr(stream)), "hd_complex_set_options")
+        _check(lib().hd_complex_set_options(self.h, float(sigma), int(trial), _stream_ptr(stream)),
+               "hd_complex_set_options")
+
+    def _vec(self, t, dim, what):
+        if t.dtype != self.torch_dtype or not t.is_cuda or not t.is_contiguous() or t.numel() != dim:
+            raise ValueError("%s must be a contiguous CUDA %s tensor of %d elements" % (what, self.torch_dtype, dim))
+        return t.data_ptr()
 
     def apply(self, x, adjoint=False, out=None):
         import torch
+        din, dout = (self.m, self.n) if adjoint else (self.n, self.m)
+        if out is None:
+            out = torch.empty(dout, dtype=self.torch_dtype, device=x.device)
+        _check(lib().hd_complex_apply(self.h, self._vec(x, din, "x"), 1 if adjoint else 0,
+                                      self._vec(out, dout, "y")), "hd_complex_apply")
+        return out
+
+    def gue(self, x, out=None):
+        import torch
         if out is None:
             out = torch.empty(self.n, dtype=self.torch_dtype, device=x.device)
-        for t, what in ((x, "x"), (out, "y")):
-            if t.dtype != self.torch_dtype or not t.is_cuda or not t.is_contiguous() or t.numel() != self.n:
-                raise ValueError("%s must be a contiguous CUDA %s tensor of %d elements" % (what, self.torch_dtype, self.n))
-        _check(lib().hd_complex_apply(self.h, x.data_ptr(), 1 if adjoint else 0, out.data_ptr()), "hd_complex_apply")
+        _check(lib().hd_complex_gue_apply(self.h, self._vec(x, self.n, "x"), self._vec(out, self.n, "y")),
+               "hd_complex_gue_apply")
         return out
 
     def reset(self, seed=None):

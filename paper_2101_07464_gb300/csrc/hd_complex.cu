@@ -104,6 +104,9 @@ struct CWs {
   Cd* wout;         // Tm + 1: row-pass coefficients of the output
   Cd* d;            // Tm + 1: the output's head entries
   Cd* s2;           // Tm + 1: summed dots of the random side
+  Cd* wg;           // Tm + 1: (Ginibre) coefficients of the new basis vector's row pass
+  Cd* c;            // Tm + 1: (Ginibre) coefficients of the stored basis vectors in y
+  Cd* h;            // Tm + 1: (Ginibre) dots of x with the data space's stored basis vectors
   void* p;          // Cx<T>, n: p = R_{t-1} ... R_1 x (the data-side product)
 };
 
@@ -115,39 +118,48 @@ __device__ __forceinline__ Cx<T> draw_c(const DrawKey& key, int64_t i) {
   return {a * s, b * s};
 }
 
-// Column pass over rows [blockIdx.x * kCRows, +kCRows) of a stack with k columns: per CTA
-// the partial sums of conj(V[:, j]) . r for j < k and of |r|^2, r restricted to rows >= lo.
-// r is the vector src (mode 0) or the draw of `key` (mode 1).  When write_col, r (rows >= lo)
-// is also stored as column k of the stack (its pivot entry is replaced by the finalisation).
+// Column pass over rows [blockIdx.x * kCRows, +kCRows): per CTA the partial sums of
+// conj(c_j) . r for the k1 columns of the stack st (column j is zero above row j) and then the
+// k2 dense columns of B, and of |r|^2 (slot k1 + k2); r is restricted to rows >= lo and is the
+// vector src (mode 0) or sigma times the draw of `key` (mode 1).  When wcol is non-null, r
+// (rows >= lo) is also stored there (a new stack or basis column; a stack column's pivot entry
+// is replaced by the finalisation).
 template <typename T>
-__global__ void __launch_bounds__(kCThreads) k_c_colpass(CStack st, int k, int64_t dim, int mode, const void* src,
-                                                         DrawKey key, int64_t lo, int write_col, Cd* part, int P) {
+__global__ void __launch_bounds__(kCThreads) k_c_colpass(CStack st, int k1, const void* B, int64_t ldb, int k2,
+                                                         int64_t dim, int mode, const void* src, DrawKey key,
+                                                         T sigma, int64_t lo, void* wcol, Cd* part, int P) {
   extern __shared__ __align__(16) unsigned char c_smem[];
   Cx<T>* r = (Cx<T>*)c_smem;
   __shared__ double red[kCThreads / 32];
   const int64_t r0 = (int64_t)blockIdx.x * kCRows;
   const int rows = (int)min((int64_t)kCRows, dim - r0);
-  const Cx<T>* V = (const Cx<T>*)st.V;
-  Cx<T>* Vw = (Cx<T>*)st.V;
+  Cx<T>* wc = (Cx<T>*)wcol;
   T nrm = T(0);
   for (int q = threadIdx.x; q < kCRows; q += blockDim.x) {
     const int64_t i = r0 + q;
     Cx<T> v = {T(0), T(0)};
     if (q < rows && i >= lo) {
-      v = (mode == 0) ? ((const Cx<T>*)src)[i] : draw_c<T>(key, i);
-      if (write_col) Vw[i + (int64_t)k * st.ld] = v;
+      if (mode == 0) {
+        v = ((const Cx<T>*)src)[i];
+      } else {
+        v = draw_c<T>(key, i);
+        v = {sigma * v.re, sigma * v.im};
+      }
+      if (wc) wc[i] = v;
       nrm = fma(v.re, v.re, fma(v.im, v.im, nrm));
     }
     r[q] = v;
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int j = warp; j < k; j += nw) {
-    // column j is zero above row j: start at max(r0, j, lo)
-    const int q0 = (int)max((int64_t)0, max((int64_t)j, lo) - r0);
+  for (int j = warp; j < k1 + k2; j += nw) {
+    // a stack column is zero above its pivot row j; basis columns are dense
+    const int64_t first = (j < k1) ? max((int64_t)j, lo) : lo;
+    const int q0 = (int)max((int64_t)0, first - r0);
+    const Cx<T>* col = (j < k1) ? (const Cx<T>*)st.V + (int64_t)j * st.ld + r0
+                                : (const Cx<T>*)B + (int64_t)(j - k1) * ldb + r0;
     // four independent accumulators: the dependent FMA latency (long in FP64) is hidden
     Cx<T> a0 = {T(0), T(0)}, a1 = a0, a2 = a0, a3 = a0;
-    const Cx<T>* col = V + (int64_t)j * st.ld + r0;
     int q = q0 + lane;
     for (; q + 96 < rows; q += 128) {
       cdotacc(a0, col[q], r[q]);
@@ -173,7 +185,7 @@ __global__ void __launch_bounds__(kCThreads) k_c_colpass(CStack st, int k, int64
   if (threadIdx.x == 0) {
     double s = 0.0;
     for (int w = 0; w < nw; w++) s += red[w];
-    part[(int64_t)blockIdx.x * P + k] = {s, 0.0};
+    part[(int64_t)blockIdx.x * P + k1 + k2] = {s, 0.0};
   }
 }
 
@@ -334,21 +346,170 @@ __global__ void __launch_bounds__(kCThreads) k_c_fin2(CStack D, CStack N, int k,
   }
 }
 
+// ---- complex Ginibre (Algorithm 1 with adjoints) ----------------------------------------
+// A step with data space d and output space o (Q: d = the n-space; Q^H: the m-space): the data
+// stack D holds kD reflectors, the other stack N holds kN; the basis store of the data space
+// (Bd) holds kN columns (v_i of the other-type steps for Q, u_i for Q^H) and the one of the
+// output space (Bo) kD columns.  Only D and Bo grow.
+//   colpass(D-space, x)      z = V_D^H x, h = Bd^H x
+//   colpass(o-space, draw)   V_N^H (sigma Z g); sigma Z g -> Bo column kD
+//   fin1                     w = S_D^H z, w_g = S_N Delta_N^H V_N^H (Z g)  (the new basis vector
+//                            u = Delta_N^H Z g - V_N w_g = N_1^H ... N_kN^H Z g)
+//   rowpass(D), colpass(D, p), fin2   as for Haar; then w_h = S_N V_N^H Delta_N^H h over the head
+//   out                      u as above -> Bo column kD;
+//                            y = Bo[:, :kD] p_head + alpha u + Delta_N^H h - V_N w_h
+// (the coefficients of the earlier same-type basis vectors are entries of p, eq. Gaussian_t).
+
+// fin1 (Ginibre): partials of colpass(D-space) in part[0 .. ncD) with P slots (kD + kN dots),
+// of colpass(o-space) in part[ncD .. ncD + ncN).
+template <typename T>
+__global__ void __launch_bounds__(kCThreads) k_cg_fin1(CStack D, CStack N, int kD, int kN, int Tm, CWs ws, int ncD,
+                                                       int ncN, int P) {
+  c_sum_parts(ws.part, ncD, P, ws.z);
+  c_sum_parts(ws.part + (int64_t)ncD * P, ncN, P, ws.s2);
+  for (int i = threadIdx.x; i < kN; i += blockDim.x) ws.h[i] = ws.z[kD + i];
+  for (int i = threadIdx.x; i < kD; i += blockDim.x) {
+    Cd acc = {0.0, 0.0};
+    for (int j = 0; j <= i; j++) acc = cadd(acc, cmul(cconj(D.S[j + (int64_t)i * Tm]), ws.z[j]));
+    ws.w[i] = acc;
+  }
+  // Delta_N^H on the draw's rows (>= kN) is the constant conj(dpre[kN])
+  const Cd ph = cconj(N.dpre[kN]);
+  for (int i = threadIdx.x; i < kN; i += blockDim.x) {
+    Cd acc = {0.0, 0.0};
+    for (int j = i; j < kN; j++) acc = cadd(acc, cmul(N.S[i + (int64_t)j * Tm], ws.s2[j]));
+    ws.wg[i] = cmul(acc, ph);
+  }
+}
+
+// fin2 (Ginibre): the data-side reflector, then the output coefficients.
+template <typename T>
+__global__ void __launch_bounds__(kCThreads) k_cg_fin2(CStack D, CStack N, int kD, int kN, int Tm, CWs ws, int ncta,
+                                                       int P, double* alpha_out) {
+  __shared__ double nrm2;
+  c_sum_parts(ws.part, ncta, P, ws.z);
+  if (threadIdx.x == 0) nrm2 = ws.z[kD].re;
+  const Cx<T>* p = (const Cx<T>*)ws.p;
+  for (int i = threadIdx.x; i < kD; i += blockDim.x) ws.c[i] = to_cd(p[i]);
+  __syncthreads();
+  c_append<T>(D, kD, Tm, ws.z, nrm2, ws.d, alpha_out);
+  // w_h = S_N v, v_j = sum_{j <= i < kN} conj(V_N[i, j]) conj(dpre_N[i + 1]) h_i
+  const Cx<T>* VN = (const Cx<T>*)N.V;
+  Cd* v = ws.d;
+  for (int j = threadIdx.x; j < kN; j += blockDim.x) {
+    Cd acc = {0.0, 0.0};
+    for (int i = j; i < kN; i++)
+      acc = cadd(acc, cmul(cconj(to_cd(VN[i + (int64_t)j * N.ld])), cmul(cconj(N.dpre[i + 1]), ws.h[i])));
+    v[j] = acc;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kN; i += blockDim.x) {
+    Cd acc = {0.0, 0.0};
+    for (int j = i; j < kN; j++) acc = cadd(acc, cmul(N.S[i + (int64_t)j * Tm], v[j]));
+    ws.wout[i] = acc;
+  }
+}
+
+// Output rows of a Ginibre step (rows [blockIdx.x * kCRows, +kCRows) of the output space):
+// u = (rows >= kN: conj(dpre_N[kN]) g) - V_N w_g, stored over g in Bo column kD;
+// y = Bo[:, :kD] c + alpha u + (rows < kN: conj(dpre_N[i + 1]) h_i) - V_N w_h.
+template <typename T>
+__global__ void __launch_bounds__(kCThreads) k_cg_out(CStack N, int kN, void* Bo, int64_t ldb, int kD, int64_t dim,
+                                                      CWs ws, const double* alpha, void* out) {
+  __shared__ Cx<T> cg[kCTmax], chh[kCTmax], cc[kCTmax];
+  for (int j = threadIdx.x; j < kN; j += blockDim.x) {
+    cg[j] = from_cd<T>(ws.wg[j]);
+    chh[j] = from_cd<T>(ws.wout[j]);
+  }
+  for (int j = threadIdx.x; j < kD; j += blockDim.x) cc[j] = from_cd<T>(ws.c[j]);
+  __syncthreads();
+  const Cx<T>* VN = (const Cx<T>*)N.V;
+  Cx<T>* B = (Cx<T>*)Bo;
+  const T a = (T)(*alpha);
+  const Cx<T> ph = from_cd<T>(cconj(N.dpre[kN]));
+  const int64_t r0 = (int64_t)blockIdx.x * kCRows;
+  constexpr int R = kCRows / kCThreads;
+  Cx<T> u[R], y[R];
+  int64_t row[R];
+#pragma unroll
+  for (int m = 0; m < R; m++) {
+    const int64_t i = r0 + threadIdx.x + (int64_t)m * kCThreads;
+    row[m] = i;
+    u[m] = {T(0), T(0)};
+    y[m] = {T(0), T(0)};
+    if (i < dim) {
+      if (i >= kN) {
+        const Cx<T> g = B[i + (int64_t)kD * ldb];
+        u[m] = {ph.re * g.re - ph.im * g.im, ph.re * g.im + ph.im * g.re};
+      } else {
+        const Cx<T> hp = from_cd<T>(cmul(cconj(N.dpre[i + 1]), ws.h[i]));
+        y[m] = hp;
+      }
+    }
+  }
+  for (int j = 0; j < kN; j++) {
+    const Cx<T> wgj = cg[j], whj = chh[j];
+    const Cx<T>* col = VN + (int64_t)j * N.ld;
+#pragma unroll
+    for (int m = 0; m < R; m++) {
+      if (row[m] < dim && row[m] >= j) {
+        const Cx<T> vv = col[row[m]];
+        cfms(u[m], vv, wgj);
+        cfms(y[m], vv, whj);
+      }
+    }
+  }
+  for (int j = 0; j < kD; j++) {
+    const Cx<T> cj = cc[j];
+    const Cx<T>* col = B + (int64_t)j * ldb;
+#pragma unroll
+    for (int m = 0; m < R; m++) {
+      if (row[m] < dim) {
+        const Cx<T> b = col[row[m]];
+        y[m].re = fma(b.re, cj.re, fma(-b.im, cj.im, y[m].re));
+        y[m].im = fma(b.re, cj.im, fma(b.im, cj.re, y[m].im));
+      }
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < R; m++) {
+    const int64_t i = row[m];
+    if (i >= dim) continue;
+    B[i + (int64_t)kD * ldb] = u[m];
+    ((Cx<T>*)out)[i] = {fma(a, u[m].re, y[m].re), fma(a, u[m].im, y[m].im)};
+  }
+}
+
+// y = (y + yh) / sqrt(2), elementwise (the GUE combination), complex.
+template <typename T>
+__global__ void __launch_bounds__(256) k_c_gue_combine(Cx<T>* y, const Cx<T>* yh, int64_t len) {
+  const T r = (T)0.70710678118654752440;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = {(y[i].re + yh[i].re) * r, (y[i].im + yh[i].im) * r};
+}
+
 }  // namespace
 
 struct hd_cstate {
+  int ens = HD_HAAR;
   int dtype = HD_F64;
-  int64_t n = 0;
+  int64_t dim[2] = {0, 0};   // 0: the n-space (R, input of Q), 1: the m-space (L)
   int Tm = 0;
   uint64_t seed = 0;
   uint32_t trial = 0;
+  double sigma = 1.0;        // Ginibre entry scale
   cudaStream_t stream = nullptr;
   int device = 0;
   int t = 0;
+  int cnt[2] = {0, 0};       // Ginibre: reflectors per stack (Q steps, Q^H steps)
   int poisoned = 0;
-  size_t esz = 16;        // bytes of one complex element
-  int ncta = 1;
-  CStack st[2];           // 0: R (acts on the input of Q), 1: L
+  size_t esz = 16;           // bytes of one complex element
+  int ncta[2] = {1, 1};
+  CStack st[2];              // 0: R (acts on the n-space), 1: L (the m-space)
+  void* B[2] = {nullptr, nullptr};   // Ginibre basis stores per space (dim x Tm)
+  int64_t ldb[2] = {0, 0};
+  double* alpha = nullptr;   // Ginibre: the step's alpha (device)
+  void* tmp = nullptr;       // GUE: the Q^H product
   CWs ws;
   std::vector<void*> allocs;
 };
@@ -377,8 +538,8 @@ int c_fail(hd_cstate* s, const char* where, cudaError_t e) {
   return HD_ERR_CUDA;
 }
 
-// zero S and the phases, dpre[0] = 1 (V's columns are rewritten from their pivot down by
-// every step, and the passes never read above a column's pivot)
+// zero S and the phases, dpre[0] = 1 (stack and basis columns are rewritten by the step that
+// creates them, and the passes never read a stack column above its pivot)
 int c_clear(hd_cstate* s) {
   const size_t sb = (size_t)s->Tm * s->Tm * sizeof(Cd);
   const size_t db = (size_t)(s->Tm + 1) * sizeof(Cd);
@@ -391,7 +552,19 @@ int c_clear(hd_cstate* s) {
   }
   // the host value `one` must outlive the copy
   if (cudaStreamSynchronize(s->stream) != cudaSuccess) return c_fail(s, "hd_complex state clear", cudaGetLastError());
+  s->t = 0;
+  s->cnt[0] = s->cnt[1] = 0;
   return HD_OK;
+}
+
+DrawKey c_key(const hd_cstate* s) {
+  DrawKey key;
+  key.k0 = (uint32_t)(s->seed & 0xFFFFFFFFu);
+  key.k1 = (uint32_t)(s->seed >> 32);
+  key.step = (uint32_t)(s->t + 1);
+  key.trial = s->trial;
+  key.stream = 0;
+  return key;
 }
 
 template <typename T>
@@ -399,45 +572,84 @@ int c_step(hd_cstate* s, const void* x, int adjoint, void* y) {
   const int k = s->t;
   const int d = adjoint ? 1 : 0;
   const CStack D = s->st[d], N = s->st[1 - d];
-  DrawKey key;
-  key.k0 = (uint32_t)(s->seed & 0xFFFFFFFFu);
-  key.k1 = (uint32_t)(s->seed >> 32);
-  key.step = (uint32_t)(k + 1);
-  key.trial = s->trial;
-  key.stream = 0;
+  const DrawKey key = c_key(s);
+  const int64_t n = s->dim[0];
   const int P = s->Tm + 1;
-  const int nc = s->ncta;
+  const int nc = s->ncta[0];
   const size_t smem = (size_t)kCRows * sizeof(Cx<T>);
   cudaStream_t q = s->stream;
   Cd* partN = s->ws.part + (int64_t)nc * P;
-  k_c_colpass<T><<<nc, kCThreads, smem, q>>>(D, k, s->n, 0, x, key, 0, 0, s->ws.part, P);
-  k_c_colpass<T><<<nc, kCThreads, smem, q>>>(N, k, s->n, 1, nullptr, key, k, 1, partN, P);
+  Cx<T>* colD = (Cx<T>*)D.V + (int64_t)k * D.ld;
+  Cx<T>* colN = (Cx<T>*)N.V + (int64_t)k * N.ld;
+  k_c_colpass<T><<<nc, kCThreads, smem, q>>>(D, k, nullptr, 0, 0, n, 0, x, key, T(1), 0, nullptr, s->ws.part, P);
+  k_c_colpass<T><<<nc, kCThreads, smem, q>>>(N, k, nullptr, 0, 0, n, 1, nullptr, key, T(1), k, colN, partN, P);
   k_c_fin1<T><<<1, kCThreads, 0, q>>>(D, N, k, s->Tm, s->ws, nc, P);
-  k_c_rowpass<T><<<nc, kCThreads, 0, q>>>(D, k, s->n, x, nullptr, 0, s->ws.w, 1, s->ws.p);
-  k_c_colpass<T><<<nc, kCThreads, smem, q>>>(D, k, s->n, 0, s->ws.p, key, k, 1, s->ws.part, P);
+  k_c_rowpass<T><<<nc, kCThreads, 0, q>>>(D, k, n, x, nullptr, 0, s->ws.w, 1, s->ws.p);
+  k_c_colpass<T><<<nc, kCThreads, smem, q>>>(D, k, nullptr, 0, 0, n, 0, s->ws.p, key, T(1), k, colD, s->ws.part, P);
   k_c_fin2<T><<<1, kCThreads, 0, q>>>(D, N, k, s->Tm, s->ws, nc, P);
-  k_c_rowpass<T><<<nc, kCThreads, 0, q>>>(N, k + 1, s->n, nullptr, s->ws.d, k + 1, s->ws.wout, 0, y);
+  k_c_rowpass<T><<<nc, kCThreads, 0, q>>>(N, k + 1, n, nullptr, s->ws.d, k + 1, s->ws.wout, 0, y);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return c_fail(s, "hd_complex_apply launch", e);
   s->t += 1;
   return HD_OK;
 }
 
+// One product of the complex Ginibre ensemble (see the kernels above).
+template <typename T>
+int c_step_gin(hd_cstate* s, const void* x, int adjoint, void* y) {
+  const int d = adjoint ? 1 : 0, o = 1 - d;
+  const int kD = s->cnt[d], kN = s->cnt[o];
+  const CStack D = s->st[d], N = s->st[o];
+  const DrawKey key = c_key(s);
+  const int P = s->Tm + 1;
+  const int ncD = s->ncta[d], ncN = s->ncta[o];
+  const size_t smem = (size_t)kCRows * sizeof(Cx<T>);
+  cudaStream_t q = s->stream;
+  Cd* partN = s->ws.part + (int64_t)ncD * P;
+  Cx<T>* colD = (Cx<T>*)D.V + (int64_t)kD * D.ld;
+  Cx<T>* colBo = (Cx<T>*)s->B[o] + (int64_t)kD * s->ldb[o];
+  k_c_colpass<T><<<ncD, kCThreads, smem, q>>>(D, kD, s->B[d], s->ldb[d], kN, s->dim[d], 0, x, key, T(1), 0, nullptr,
+                                             s->ws.part, P);
+  k_c_colpass<T><<<ncN, kCThreads, smem, q>>>(N, kN, nullptr, 0, 0, s->dim[o], 1, nullptr, key, (T)s->sigma, kN,
+                                             colBo, partN, P);
+  k_cg_fin1<T><<<1, kCThreads, 0, q>>>(D, N, kD, kN, s->Tm, s->ws, ncD, ncN, P);
+  k_c_rowpass<T><<<ncD, kCThreads, 0, q>>>(D, kD, s->dim[d], x, nullptr, 0, s->ws.w, 1, s->ws.p);
+  k_c_colpass<T><<<ncD, kCThreads, smem, q>>>(D, kD, nullptr, 0, 0, s->dim[d], 0, s->ws.p, key, T(1), kD, colD,
+                                             s->ws.part, P);
+  k_cg_fin2<T><<<1, kCThreads, 0, q>>>(D, N, kD, kN, s->Tm, s->ws, ncD, P, s->alpha);
+  k_cg_out<T><<<ncN, kCThreads, 0, q>>>(N, kN, s->B[o], s->ldb[o], kD, s->dim[o], s->ws, s->alpha, y);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return c_fail(s, "hd_complex_apply launch", e);
+  s->t += 1;
+  s->cnt[d] += 1;
+  return HD_OK;
+}
+
+int c_product(hd_cstate* s, const void* x, int adjoint, void* y) {
+  if (s->ens == HD_HAAR)
+    return (s->dtype == HD_F64) ? c_step<double>(s, x, adjoint, y) : c_step<float>(s, x, adjoint, y);
+  return (s->dtype == HD_F64) ? c_step_gin<double>(s, x, adjoint, y) : c_step_gin<float>(s, x, adjoint, y);
+}
+
 }  // namespace
 
 extern "C" {
 
-HD_API int hd_complex_create(int ensemble, int64_t n, int32_t T_max, uint64_t seed, int dtype, hd_cstate** out) {
+HD_API int hd_complex_create(int ensemble, int64_t m, int64_t n, int32_t T_max, uint64_t seed, int dtype,
+                             hd_cstate** out) {
   if (!out) return HD_ERR_ARG;
   *out = nullptr;
-  if (ensemble != HD_HAAR) return HD_ERR_ARG;
+  if (ensemble != HD_HAAR && ensemble != HD_GINIBRE) return HD_ERR_ARG;
   if (dtype != HD_F64 && dtype != HD_F32) return HD_ERR_ARG;
-  if (n <= 0 || n > ((int64_t)1 << 36)) return HD_ERR_DIM;
-  if (T_max <= 0 || T_max > kCTmax || (int64_t)T_max > n) return HD_ERR_TMAX;
+  if (m <= 0 || n <= 0 || m > ((int64_t)1 << 36) || n > ((int64_t)1 << 36)) return HD_ERR_DIM;
+  if (ensemble == HD_HAAR && m != n) return HD_ERR_DIM;
+  if (T_max <= 0 || T_max > kCTmax || (int64_t)T_max > std::min(m, n)) return HD_ERR_TMAX;
   hd_cstate* s = new (std::nothrow) hd_cstate();
   if (!s) return HD_ERR_OOM;
+  s->ens = ensemble;
   s->dtype = dtype;
-  s->n = n;
+  s->dim[0] = n;
+  s->dim[1] = m;
   s->Tm = T_max;
   s->seed = seed;
   s->esz = (dtype == HD_F64) ? 16 : 8;
@@ -446,30 +658,46 @@ HD_API int hd_complex_create(int ensemble, int64_t n, int32_t T_max, uint64_t se
     delete s;
     return HD_ERR_CUDA;
   }
-  s->ncta = (int)((n + kCRows - 1) / kCRows);
-  const int64_t ld = (n + 63) / 64 * 64;
   const int P = T_max + 1;
+  int64_t ldmax = 0;
   bool ok = true;
   for (int q = 0; q < 2 && ok; q++) {
+    s->ncta[q] = (int)((s->dim[q] + kCRows - 1) / kCRows);
+    const int64_t ld = (s->dim[q] + 63) / 64 * 64;
+    ldmax = std::max(ldmax, ld);
     s->st[q].ld = ld;
     s->st[q].V = c_alloc(s, (size_t)ld * T_max * s->esz);
     s->st[q].S = (Cd*)c_alloc(s, (size_t)T_max * T_max * sizeof(Cd));
     s->st[q].dpre = (Cd*)c_alloc(s, (size_t)(T_max + 1) * sizeof(Cd));
     ok = s->st[q].V && s->st[q].S && s->st[q].dpre;
     if (ok) ok = cudaMemset(s->st[q].V, 0, (size_t)ld * T_max * s->esz) == cudaSuccess;
+    if (ok && ensemble == HD_GINIBRE) {
+      s->ldb[q] = ld;
+      s->B[q] = c_alloc(s, (size_t)ld * T_max * s->esz);
+      ok = s->B[q] && cudaMemset(s->B[q], 0, (size_t)ld * T_max * s->esz) == cudaSuccess;
+    }
   }
   if (ok) {
-    s->ws.part = (Cd*)c_alloc(s, (size_t)2 * s->ncta * P * sizeof(Cd));
-    Cd* small = (Cd*)c_alloc(s, (size_t)5 * P * sizeof(Cd));
-    s->ws.p = c_alloc(s, (size_t)ld * s->esz);
-    ok = s->ws.part && small && s->ws.p;
+    const int nmax = std::max(s->ncta[0], s->ncta[1]);
+    s->ws.part = (Cd*)c_alloc(s, (size_t)2 * nmax * P * sizeof(Cd));
+    Cd* small = (Cd*)c_alloc(s, (size_t)8 * P * sizeof(Cd));
+    s->ws.p = c_alloc(s, (size_t)ldmax * s->esz);
+    s->alpha = (double*)c_alloc(s, 64);
+    ok = s->ws.part && small && s->ws.p && s->alpha;
     if (ok) {
       s->ws.z = small;
       s->ws.w = small + P;
       s->ws.wout = small + 2 * P;
       s->ws.d = small + 3 * P;
       s->ws.s2 = small + 4 * P;
-      ok = cudaMemset(small, 0, (size_t)5 * P * sizeof(Cd)) == cudaSuccess;
+      s->ws.wg = small + 5 * P;
+      s->ws.c = small + 6 * P;
+      s->ws.h = small + 7 * P;
+      ok = cudaMemset(small, 0, (size_t)8 * P * sizeof(Cd)) == cudaSuccess;
+    }
+    if (ok && ensemble == HD_GINIBRE && m == n) {
+      s->tmp = c_alloc(s, (size_t)ldmax * s->esz);
+      ok = s->tmp != nullptr;
     }
   }
   if (!ok) {
@@ -487,10 +715,12 @@ HD_API int hd_complex_create(int ensemble, int64_t n, int32_t T_max, uint64_t se
   return HD_OK;
 }
 
-HD_API int hd_complex_set_options(hd_cstate* s, uint32_t trial, void* stream) {
+HD_API int hd_complex_set_options(hd_cstate* s, double sigma, uint32_t trial, void* stream) {
   if (!s) return HD_ERR_ARG;
-  if (s->t > 0 && trial != s->trial) return HD_ERR_ARG;
+  if (!(sigma > 0.0) || !std::isfinite(sigma)) return HD_ERR_ARG;
+  if (s->t > 0 && (trial != s->trial || sigma != s->sigma)) return HD_ERR_ARG;
   s->trial = trial;
+  s->sigma = sigma;
   s->stream = (cudaStream_t)stream;
   return HD_OK;
 }
@@ -502,14 +732,33 @@ HD_API int hd_complex_apply(hd_cstate* s, const void* x, int adjoint, void* y) {
   if (s->poisoned) return s->poisoned;
   if (s->t >= s->Tm) return HD_ERR_TMAX;
   if (cudaSetDevice(s->device) != cudaSuccess) return c_fail(s, "cudaSetDevice", cudaErrorInvalidDevice);
-  return (s->dtype == HD_F64) ? c_step<double>(s, x, adjoint, y) : c_step<float>(s, x, adjoint, y);
+  return c_product(s, x, adjoint, y);
+}
+
+HD_API int hd_complex_gue_apply(hd_cstate* s, const void* x, void* y) {
+  if (!s || !x || !y || x == y) return HD_ERR_ARG;
+  if (s->ens != HD_GINIBRE || s->dim[0] != s->dim[1]) return HD_ERR_ARG;
+  if (((uintptr_t)x % s->esz) != 0 || ((uintptr_t)y % s->esz) != 0) return HD_ERR_ARG;
+  if (s->poisoned) return s->poisoned;
+  if (s->t + 2 > s->Tm) return HD_ERR_TMAX;
+  if (cudaSetDevice(s->device) != cudaSuccess) return c_fail(s, "cudaSetDevice", cudaErrorInvalidDevice);
+  int rc = c_product(s, x, 0, y);
+  if (!rc) rc = c_product(s, x, 1, s->tmp);
+  if (rc) return rc;
+  const int64_t n = s->dim[0];
+  const unsigned blocks = (unsigned)std::min<int64_t>((n + 255) / 256, 4096);
+  if (s->dtype == HD_F64)
+    k_c_gue_combine<double><<<blocks, 256, 0, s->stream>>>((Cx<double>*)y, (const Cx<double>*)s->tmp, n);
+  else
+    k_c_gue_combine<float><<<blocks, 256, 0, s->stream>>>((Cx<float>*)y, (const Cx<float>*)s->tmp, n);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? HD_OK : c_fail(s, "hd_complex_gue_apply launch", e);
 }
 
 HD_API int hd_complex_reset(hd_cstate* s, uint64_t seed) {
   if (!s) return HD_ERR_ARG;
   if (cudaSetDevice(s->device) != cudaSuccess) return c_fail(s, "cudaSetDevice", cudaErrorInvalidDevice);
   s->seed = seed;
-  s->t = 0;
   s->poisoned = 0;
   return c_clear(s);
 }

@@ -383,24 +383,27 @@ HD_API int hd_philox_words(uint64_t seed, const uint32_t* counters, int64_t nblo
  * paper has no gradients; this is the pathwise derivative of the sampler, so it is an
  * unbiased estimator of the derivative of an expectation, not the derivative for a fixed
  * dense Q.  The sign choices of the reflectors are piecewise constant and pass no
- * derivative; an identity reflector (zero tail) passes none either.  Single-trial states only.
+ * derivative; an identity reflector (zero tail) passes none either.  A batched state whose
+ * trials all have the same dimensions reverses all its trials at once (packed vectors, one
+ * set of launches per reverse step); batches of unequal trials give HD_ERR_ARG.
  *
  * hd_adjoint_enable(st, flags): call on a fresh or just-reset state (no step taken).  From
  * then on every forward step is recorded; with HD_ADJ_RECORD_X the library also keeps a copy
  * of each x_t (T_max vectors of the longer dimension, state dtype), otherwise the caller
  * passes x_t back to hd_adjoint_step (recomputing them, e.g. from checkpoints with hd_probe).
- * Allocates the accumulators once: per stack dim x T_max elements of the state dtype (dV) and
- * T_max^2 FP64 (dS), per Gin basis store dim x T_max of the state dtype, plus 4 work vectors.
+ * Allocates the accumulators once, per trial: per stack dim x T_max elements of the state dtype
+ * (dV) and T_max^2 FP64 (dS), per Gin basis store dim x T_max of the state dtype, plus 4 work
+ * vectors; with HD_ADJ_RECORD_X one packed input vector per step.
  * The streaming passes compute in the state's precision with FP64 cross-thread sums, as the
  * forward sweeps do.  hd_run on a recording state
- * runs without its CUDA graph.  Errors: HD_ERR_ARG (batched state, unknown flag),
+ * runs without its CUDA graph.  Errors: HD_ERR_ARG (batch of unequal trials, unknown flag),
  * HD_ERR_STATE (steps already taken), HD_ERR_OOM, HD_ERR_CUDA. */
 #define HD_ADJ_RECORD_X 1
 HD_API int hd_adjoint_enable(hd_state* st, int flags);
 
 /* Reverse the latest forward step not yet reversed (step t, counting down from the last).
- * ybar: dLoss/dy_t, a device buffer of y_t's length (state dtype).  x_t: the step's input
- * (device, x_t's length) or NULL to use the recorded copy.  xbar (device, x_t's length)
+ * ybar: dLoss/dy_t, a device buffer of y_t's length (state dtype; packed for a batch).  x_t:
+ * the step's input (device, x_t's length) or NULL to use the recorded copy.  xbar (device, x_t's length)
  * receives dLoss/dx_t through y_t and through every later product that used a reflector or
  * basis vector built from x_t (their contributions were accumulated when those later steps
  * were reversed).  It does not include the caller's own f_t: the caller adds

@@ -14,6 +14,10 @@ It then calls the library's reverse step (hd_adjoint_step, CUDA), which returns 
 dLoss/dx_t that flows through y_t and through every later product that used the reflector
 built from x_t.  x_{t-1} is None at t = 1.
 
+A batched state (HDBatch, every trial of the same dimensions) runs all its trials at once:
+vectors are packed, f_t sees the packed vectors, and every reverse step is one set of
+launches for the whole batch.
+
 Memory: without checkpointing the library records every x_t, and this module keeps every y_t.
 With `checkpoint=S` only x_t at every S-th step is kept.  In backward, each segment is
 recomputed from its first x with hd_probe: the final state maps every earlier x_s to y_s
@@ -23,14 +27,16 @@ pass up to rounding; a discontinuous f_t can amplify that.
 """
 import torch
 
-from .binding import HD
+from .binding import HD, HDBatch
 
 
 class _Trajectory(torch.autograd.Function):
     @staticmethod
     def forward(ctx, hd, schedule, f, checkpoint, x1, *params):
-        if not isinstance(hd, HD):
-            raise TypeError("hd must be a paper_2101_07464_gb300.HD state")
+        if not isinstance(hd, (HD, HDBatch)):
+            raise TypeError("hd must be a paper_2101_07464_gb300.HD or HDBatch state")
+        if isinstance(hd, HDBatch) and checkpoint is not None:
+            raise ValueError("segment checkpointing needs hd_probe, which takes single-trial states")
         T = len(schedule)
         hd.reset()
         hd.adjoint_enable(record_x=checkpoint is None)

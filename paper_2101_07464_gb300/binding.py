@@ -422,6 +422,7 @@ class HDBatch:
         import torch
         self.dtype_code = DTYPES.get(dtype, dtype)
         self.torch_dtype = torch.float64 if self.dtype_code == HD_F64 else torch.float32
+        self.seed = seed
         self.h = hd_create_batched(ensemble, ms, ns, T_max, seed, self.dtype_code)
         self.off_n, self.off_m = hd_get_batch_layout(self.h)
         if stream is None:
@@ -439,8 +440,28 @@ class HDBatch:
         hd_apply(self.h, x, transpose, out)
         return out
 
-    def reset(self, seed):
-        hd_reset(self.h, seed)
+    def adjoint_enable(self, record_x=True):
+        """Record the following forward steps for hd_adjoint_step (every trial of the batch must
+        have the same dimensions; call on a fresh or reset state)."""
+        hd_adjoint_enable(self.h, record_x)
+
+    def adjoint_step(self, ybar, transpose, x_t=None):
+        """Reverse the latest unreversed step for every trial at once (packed vectors): returns
+        dLoss/dx_t through y_t and every later product; x_t=None uses the recorded input."""
+        import torch
+        n_in, n_out = (int(self.off_m[-1]), int(self.off_n[-1])) if transpose else \
+            (int(self.off_n[-1]), int(self.off_m[-1]))
+        _ptr(ybar, self.dtype_code, n_out, "ybar")
+        if x_t is not None:
+            _ptr(x_t, self.dtype_code, n_in, "x_t")
+        xbar = torch.empty(n_in, dtype=self.torch_dtype, device=ybar.device)
+        hd_adjoint_step(self.h, ybar, x_t, xbar)
+        return xbar
+
+    def reset(self, seed=None):
+        if seed is not None:
+            self.seed = seed
+        hd_reset(self.h, self.seed)
 
     def set_trial_sigmas(self, sigmas):
         hd_set_trial_sigmas(self.h, sigmas)

@@ -42,6 +42,18 @@ namespace {
 constexpr int kAT = 256;   // threads of every adjoint kernel
 constexpr int kSmallT = 1024;   // threads of the small FP64 kernels (FP64 latency wants many warps)
 
+// A pointer with the distance between consecutive trials of a batched state (all trials of
+// a batch in reverse mode have the same dimensions, so every per-trial array is evenly
+// spaced).  Kernels take the trial from blockIdx.z.
+template <typename P>
+struct TP {
+  P* p;
+  int64_t s;
+  __host__ __device__ P* at(int tr) const { return p ? p + (int64_t)tr * s : nullptr; }
+};
+template <typename P>
+__host__ __device__ inline TP<P> tp(P* p, int64_t s) { return TP<P>{p, s}; }
+
 enum AdjVec { kVp, kVub, kVqb, kVg, kAdjVecs };
 enum AdjSmall {
   kSz, kSw, kSh, kSbb, kSb, kScb, kSzb, kSwb, kSE, kSc, kShb, kSau, kSbu, kSbbu, kSabu, kSscal,
@@ -67,9 +79,13 @@ __device__ __forceinline__ double a_block_sum(double v, double* red) {
 // column; part[(x K + j) 2 + v] = sum over the chunk of A[r, j] v_v[r] (per-lane sums in T over
 // at most ~100 rows, eight loads in flight per lane, FP64 across lanes).
 template <typename T>
-__global__ void __launch_bounds__(kAT) k_colpass(const T* __restrict__ A, int64_t ld, int K, int64_t dim,
-                                                 const T* __restrict__ v1, const T* __restrict__ v2,
-                                                 double* part) {
+__global__ void __launch_bounds__(kAT) k_colpass(TP<const T> A_, int64_t ld, int K, int64_t dim,
+                                                 TP<const T> v1_, TP<const T> v2_, TP<double> part_) {
+  const int tr = blockIdx.z;
+  const T* __restrict__ A = A_.at(tr);
+  const T* __restrict__ v1 = v1_.at(tr);
+  const T* __restrict__ v2 = v2_.at(tr);
+  double* part = part_.at(tr);
   const int64_t per = ((dim + gridDim.x - 1) / gridDim.x + 31) / 32 * 32;
   const int64_t r0 = (int64_t)blockIdx.x * per, r1 = min(dim, r0 + per);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -118,19 +134,27 @@ __device__ __forceinline__ void colreduce_col(const double* __restrict__ part, i
     if (out2) out2[j] = s2 * b;
   }
 }
-__global__ void __launch_bounds__(kAT) k_colreduce(const double* __restrict__ part, int nblk, int K,
-                                                   double s1, double* out1, double s2, double* out2) {
+__global__ void __launch_bounds__(kAT) k_colreduce(TP<const double> part, int nblk, int K,
+                                                   double s1, TP<double> out1, double s2, TP<double> out2) {
+  const int tr = blockIdx.z;
   const int j = blockIdx.x * (kAT / 32) + (threadIdx.x >> 5);
-  if (j < K) colreduce_col(part, nblk, K, j, s1, out1, s2, out2);
+  if (j < K) colreduce_col(part.at(tr), nblk, K, j, s1, out1.at(tr), s2, out2.at(tr));
 }
 
 // out[r] (+)= sgn(r) (s_in in[r] + c_scale sum_{j<K} A[r, j] c[j]), sgn(r) = dpre[min(r+1, Kd)]
 // (or 1); optionally per-CTA FP64 partial sums of out[r]^2 over r >= rnorm.
 template <typename T>
-__global__ void __launch_bounds__(kAT) k_rowpass(T* out, const T* in, double s_in, const T* __restrict__ A,
-                                                 int64_t ld, int K, const double* __restrict__ c, double c_scale,
-                                                 int64_t dim, const double* __restrict__ dpre, int Kd,
-                                                 int accumulate, int64_t rnorm, double* npart) {
+__global__ void __launch_bounds__(kAT) k_rowpass(TP<T> out_, TP<const T> in_, double s_in, TP<const T> A_,
+                                                 int64_t ld, int K, TP<const double> c_, double c_scale,
+                                                 int64_t dim, TP<const double> dpre_, int Kd,
+                                                 int accumulate, int64_t rnorm, TP<double> npart_) {
+  const int tr = blockIdx.z;
+  T* out = out_.at(tr);
+  const T* in = in_.at(tr);
+  const T* __restrict__ A = A_.at(tr);
+  const double* __restrict__ c = c_.at(tr);
+  const double* __restrict__ dpre = dpre_.at(tr);
+  double* npart = npart_.at(tr);
   __shared__ T cs[kTmaxLimit + 1];
   __shared__ double red[kAT / 32];
   for (int j = threadIdx.x; j < K; j += blockDim.x) cs[j] = (T)(c_scale * c[j]);
@@ -163,10 +187,18 @@ __global__ void __launch_bounds__(kAT) k_rowpass(T* out, const T* in, double s_i
 // Ab[r, j] += a[r] b[j] + c[r] d[j] + e[r] f[j] for r < dim, j < K (column-major, leading dim
 // ld; b, d, f are FP64 coefficient vectors with the scales sb, sd, sf; c, e may be null).
 template <typename T>
-__global__ void __launch_bounds__(kAT) k_rank(T* Ab, int64_t ld, int K, int64_t dim, const T* __restrict__ a,
-                                              const double* __restrict__ b, double sb, const T* __restrict__ c,
-                                              const double* __restrict__ d, double sd, const T* __restrict__ e,
-                                              const double* __restrict__ f, double sf, int Kf) {
+__global__ void __launch_bounds__(kAT) k_rank(TP<T> Ab_, int64_t ld, int K, int64_t dim, TP<const T> a_,
+                                              TP<const double> b_, double sb, TP<const T> c_,
+                                              TP<const double> d_, double sd, TP<const T> e_,
+                                              TP<const double> f_, double sf, int Kf) {
+  const int tr = blockIdx.z;
+  T* Ab = Ab_.at(tr);
+  const T* __restrict__ a = a_.at(tr);
+  const double* __restrict__ b = b_.at(tr);
+  const T* __restrict__ c = c_.at(tr);
+  const double* __restrict__ d = d_.at(tr);
+  const T* __restrict__ e = e_.at(tr);
+  const double* __restrict__ f = f_.at(tr);
   __shared__ T bs[8], ds[8], fs[8];
   const int j0 = blockIdx.y * 8;
   if (threadIdx.x < 8) {
@@ -193,10 +225,18 @@ __global__ void __launch_bounds__(kAT) k_rank(T* Ab, int64_t ld, int K, int64_t 
 // FP32 with 16-byte aligned vectors: the same passes four rows per thread (float4 accesses).
 __host__ __device__ __forceinline__ bool al16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
-__global__ void __launch_bounds__(kAT) k_rank4(float* Ab, int64_t ld, int K, int64_t dim4, const float* __restrict__ a,
-                                               const double* __restrict__ b, double sb, const float* __restrict__ c,
-                                               const double* __restrict__ d, double sd, const float* __restrict__ e,
-                                               const double* __restrict__ f, double sf, int Kf) {
+__global__ void __launch_bounds__(kAT) k_rank4(TP<float> Ab_, int64_t ld, int K, int64_t dim4, TP<const float> a_,
+                                               TP<const double> b_, double sb, TP<const float> c_,
+                                               TP<const double> d_, double sd, TP<const float> e_,
+                                               TP<const double> f_, double sf, int Kf) {
+  const int tr = blockIdx.z;
+  float* Ab = Ab_.at(tr);
+  const float* __restrict__ a = a_.at(tr);
+  const double* __restrict__ b = b_.at(tr);
+  const float* __restrict__ c = c_.at(tr);
+  const double* __restrict__ d = d_.at(tr);
+  const float* __restrict__ e = e_.at(tr);
+  const double* __restrict__ f = f_.at(tr);
   __shared__ float bs[8], ds[8], fs[8];
   const int j0 = blockIdx.y * 8;
   if (threadIdx.x < 8) {
@@ -230,10 +270,21 @@ struct RankTerms {
   const double* c[5];
   double s[5];
   int K[5];
+  int64_t sv[5];   // trial strides of v (elements) and c (doubles)
+  int64_t sc[5];
   int n;
 };
 template <typename T>
-__global__ void __launch_bounds__(kAT) k_rankN(T* Ab, int64_t ld, int K, int64_t dim, RankTerms t) {
+__global__ void __launch_bounds__(kAT) k_rankN(TP<T> Ab_, int64_t ld, int K, int64_t dim, RankTerms t) {
+  const int tr = blockIdx.z;
+  T* Ab = Ab_.at(tr);
+#pragma unroll
+  for (int q = 0; q < 5; q++) {
+    if (q < t.n) {
+      t.v[q] = (const T*)t.v[q] + (int64_t)tr * t.sv[q];
+      t.c[q] = t.c[q] + (int64_t)tr * t.sc[q];
+    }
+  }
   __shared__ T cs[5][8];
   const int j0 = blockIdx.y * 8;
   if (threadIdx.x < 40) {
@@ -255,7 +306,16 @@ __global__ void __launch_bounds__(kAT) k_rankN(T* Ab, int64_t ld, int K, int64_t
     }
   }
 }
-__global__ void __launch_bounds__(kAT) k_rankN4(float* Ab, int64_t ld, int K, int64_t dim4, RankTerms t) {
+__global__ void __launch_bounds__(kAT) k_rankN4(TP<float> Ab_, int64_t ld, int K, int64_t dim4, RankTerms t) {
+  const int tr = blockIdx.z;
+  float* Ab = Ab_.at(tr);
+#pragma unroll
+  for (int q = 0; q < 5; q++) {
+    if (q < t.n) {
+      t.v[q] = (const float*)t.v[q] + (int64_t)tr * t.sv[q];
+      t.c[q] = t.c[q] + (int64_t)tr * t.sc[q];
+    }
+  }
   __shared__ float cs[5][8];
   const int j0 = blockIdx.y * 8;
   if (threadIdx.x < 40) {
@@ -285,9 +345,14 @@ __global__ void __launch_bounds__(kAT) k_rankN4(float* Ab, int64_t ld, int K, in
   }
 }
 
-__global__ void __launch_bounds__(kAT) k_rowpass4(float* out, const float* in, double s_in, const float* __restrict__ A,
-                                                  int64_t ld, int K, const double* __restrict__ c, double c_scale,
-                                                  int64_t dim4, int accumulate) {
+__global__ void __launch_bounds__(kAT) k_rowpass4(TP<float> out_, TP<const float> in_, double s_in,
+                                                  TP<const float> A_, int64_t ld, int K, TP<const double> c_,
+                                                  double c_scale, int64_t dim4, int accumulate) {
+  const int tr = blockIdx.z;
+  float* out = out_.at(tr);
+  const float* in = in_.at(tr);
+  const float* __restrict__ A = A_.at(tr);
+  const double* __restrict__ c = c_.at(tr);
   __shared__ float cs[kTmaxLimit + 1];
   for (int j = threadIdx.x; j < K; j += blockDim.x) cs[j] = (float)(c_scale * c[j]);
   __syncthreads();
@@ -312,9 +377,13 @@ __global__ void __launch_bounds__(kAT) k_rowpass4(float* out, const float* in, d
 }
 
 // Column pass, float4: CTA (x, y) = row chunk x (a multiple of 128 rows) and columns 8y..8y+7.
-__global__ void __launch_bounds__(kAT) k_colpass4(const float* __restrict__ A, int64_t ld, int K, int64_t dim4,
-                                                  const float* __restrict__ v1, const float* __restrict__ v2,
-                                                  double* part) {
+__global__ void __launch_bounds__(kAT) k_colpass4(TP<const float> A_, int64_t ld, int K, int64_t dim4,
+                                                  TP<const float> v1_, TP<const float> v2_, TP<double> part_) {
+  const int tr = blockIdx.z;
+  const float* __restrict__ A = A_.at(tr);
+  const float* __restrict__ v1 = v1_.at(tr);
+  const float* __restrict__ v2 = v2_.at(tr);
+  double* part = part_.at(tr);
   const int64_t per = ((dim4 + gridDim.x - 1) / gridDim.x + 31) / 32 * 32;
   const int64_t q0 = (int64_t)blockIdx.x * per, q1 = min(dim4, q0 + per);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -375,9 +444,10 @@ __device__ void rec_col_dev(const double* __restrict__ S, double* Sb, int Tm, in
     if (i <= j) Sb[i + (int64_t)j * Tm] += -tau * cb[i] * a[j];
   }
 }
-__global__ void __launch_bounds__(kSmallT) k_rec_col(const double* __restrict__ S, double* Sb, int Tm, int k,
-                                                     const double* __restrict__ a, double* coef) {
-  rec_col_dev(S, Sb, Tm, k, a, coef);
+__global__ void __launch_bounds__(kSmallT) k_rec_col(TP<const double> S, TP<double> Sb, int Tm, int k,
+                                                     TP<const double> a, TP<double> coef) {
+  const int tr = blockIdx.z;
+  rec_col_dev(S.at(tr), Sb.at(tr), Tm, k, a.at(tr), coef.at(tr));
 }
 
 // out = scale S v (trans = 0) or scale S^T v (trans = 1), leading K x K block of the upper
@@ -396,10 +466,10 @@ __device__ void tri_dev(const double* __restrict__ S, int Tm, int K, const doubl
     if (lane == 0) out[i] = scale * s;
   }
 }
-__global__ void __launch_bounds__(kSmallT) k_tri(const double* __restrict__ S, int Tm, int K,
-                                                 const double* __restrict__ v, double scale, int trans,
-                                                 double* out) {
-  tri_dev(S, Tm, K, v, scale, trans, out);
+__global__ void __launch_bounds__(kSmallT) k_tri(TP<const double> S, int Tm, int K, TP<const double> v,
+                                                 double scale, int trans, TP<double> out) {
+  const int tr = blockIdx.z;
+  tri_dev(S.at(tr), Tm, K, v.at(tr), scale, trans, out.at(tr));
 }
 
 // Sb[i, j] += a[i] b[j] on the upper triangle i <= j < K (S has no free entries below).
@@ -410,13 +480,18 @@ __device__ __forceinline__ void outer_upper_dev(double* Sb, int Tm, int K, const
     if (i <= j) Sb[i + (int64_t)j * Tm] += a[i] * b[j];
   }
 }
-__global__ void __launch_bounds__(kAT) k_outer_upper(double* Sb, int Tm, int K, const double* __restrict__ a,
-                                                     const double* __restrict__ b) {
-  outer_upper_dev(Sb, Tm, K, a, b);
+__global__ void __launch_bounds__(kAT) k_outer_upper(TP<double> Sb, int Tm, int K, TP<const double> a,
+                                                     TP<const double> b) {
+  const int tr = blockIdx.z;
+  outer_upper_dev(Sb.at(tr), Tm, K, a.at(tr), b.at(tr));
 }
 
 // c = [p_head[0:k]; alpha] from the step's record
-__global__ void k_head_alpha(const double* __restrict__ phead, int k, const double* __restrict__ rs, double* c) {
+__global__ void k_head_alpha(TP<const double> phead_, int k, TP<const double> rs_, TP<double> c_) {
+  const int tr = blockIdx.z;
+  const double* phead = phead_.at(tr);
+  const double* rs = rs_.at(tr);
+  double* c = c_.at(tr);
   for (int i = threadIdx.x; i <= k; i += blockDim.x) c[i] = (i < k) ? phead[i] : rs[1];
 }
 
@@ -469,27 +544,41 @@ __device__ void out_small_dev(const T* __restrict__ V, int64_t ld, int Ke, int n
   }
 }
 template <typename T>
-__global__ void __launch_bounds__(kSmallT) k_out_small(const T* __restrict__ V, int64_t ld, int Ke, int nc,
-                                                       const double* __restrict__ S, int Tm,
-                                                       const double* __restrict__ dpre, const double* __restrict__ c,
-                                                       const double* __restrict__ bb, const T* __restrict__ ybd,
-                                                       double* Sb, T* Vb, double* b_out, double* cbar) {
-  out_small_dev<T>(V, ld, Ke, nc, S, Tm, dpre, c, bb, ybd, Sb, Vb, b_out, cbar);
+__global__ void __launch_bounds__(kSmallT) k_out_small(TP<const T> V, int64_t ld, int Ke, int nc,
+                                                       TP<const double> S, int Tm, TP<const double> dpre,
+                                                       TP<const double> c, TP<const double> bb, TP<const T> ybd,
+                                                       TP<double> Sb, TP<T> Vb, TP<double> b_out, TP<double> cbar) {
+  const int tr = blockIdx.z;
+  out_small_dev<T>(V.at(tr), ld, Ke, nc, S.at(tr), Tm, dpre.at(tr), c.at(tr), bb.at(tr), ybd.at(tr), Sb.at(tr),
+                   Vb.at(tr), b_out.at(tr), cbar.at(tr));
 }
 
 // Haar output side in one CTA: bb = -V^T ybar from the column pass's partials, c = [p_head;
 // alpha], the output-product adjoint (k_out_small) and the S recurrence of the step's random
 // column (k_rec_col, after the Sbar update it depends on).
 template <typename T>
-__global__ void __launch_bounds__(kSmallT) k_out_haar_adj(const double* __restrict__ part, int nblk,
-                                                          const T* __restrict__ V, int64_t ld, int Ke,
-                                                          const double* __restrict__ S, int Tm,
-                                                          const double* __restrict__ dpre,
-                                                          const double* __restrict__ phead,
-                                                          const double* __restrict__ rs, double* cv, double* bb,
-                                                          const T* __restrict__ ybd, double* Sb, T* Vb, double* bo,
-                                                          double* cbar, const double* __restrict__ rag,
-                                                          double* au) {
+__global__ void __launch_bounds__(kSmallT) k_out_haar_adj(TP<const double> part_, int nblk, TP<const T> V_,
+                                                          int64_t ld, int Ke, TP<const double> S_, int Tm,
+                                                          TP<const double> dpre_, TP<const double> phead_,
+                                                          TP<const double> rs_, TP<double> cv_, TP<double> bb_,
+                                                          TP<const T> ybd_, TP<double> Sb_, TP<T> Vb_, TP<double> bo_,
+                                                          TP<double> cbar_, TP<const double> rag_, TP<double> au_) {
+  const int tr = blockIdx.z;
+  const double* __restrict__ part = part_.at(tr);
+  const T* __restrict__ V = V_.at(tr);
+  const double* __restrict__ S = S_.at(tr);
+  const double* __restrict__ dpre = dpre_.at(tr);
+  const double* __restrict__ phead = phead_.at(tr);
+  const double* __restrict__ rs = rs_.at(tr);
+  double* cv = cv_.at(tr);
+  double* bb = bb_.at(tr);
+  const T* __restrict__ ybd = ybd_.at(tr);
+  double* Sb = Sb_.at(tr);
+  T* Vb = Vb_.at(tr);
+  double* bo = bo_.at(tr);
+  double* cbar = cbar_.at(tr);
+  const double* __restrict__ rag = rag_.at(tr);
+  double* au = au_.at(tr);
   const int wid = threadIdx.x >> 5, nw = blockDim.x >> 5, k = Ke - 1;
   for (int j = wid; j < Ke; j += nw) colreduce_col(part, nblk, Ke, j, -1.0, bb, 0.0, nullptr);
   for (int i = threadIdx.x; i <= k; i += blockDim.x) cv[i] = (i < k) ? phead[i] : rs[1];
@@ -501,11 +590,18 @@ __global__ void __launch_bounds__(kSmallT) k_out_haar_adj(const double* __restri
 
 // The step's record (adj_record_after) in one launch: z (nz), w, p_head, V_D^T u (kD each),
 // p's pivot entry and alpha, and (Haar) V_N^T u_g (nug).
-__global__ void __launch_bounds__(kAT) k_adj_record(double* r, int64_t L, const double* __restrict__ z, int nz,
-                                                    const double* __restrict__ w, const double* __restrict__ ph,
-                                                    int kD, const double* __restrict__ scal,
-                                                    const double* __restrict__ ua, const double* __restrict__ ug,
-                                                    int nug) {
+__global__ void __launch_bounds__(kAT) k_adj_record(TP<double> r_, int64_t L, TP<const double> z_, int nz,
+                                                    TP<const double> w_, TP<const double> ph_, int kD,
+                                                    TP<const double> scal_, TP<const double> ua_,
+                                                    TP<const double> ug_, int nug) {
+  const int tr = blockIdx.z;
+  double* r = r_.at(tr);
+  const double* __restrict__ z = z_.at(tr);
+  const double* __restrict__ w = w_.at(tr);
+  const double* __restrict__ ph = ph_.at(tr);
+  const double* __restrict__ scal = scal_.at(tr);
+  const double* __restrict__ ua = ua_.at(tr);
+  const double* __restrict__ ug = ug_.at(tr);
   for (int i = threadIdx.x; i < nz; i += blockDim.x) r[i] = z[i];
   for (int i = threadIdx.x; i < kD; i += blockDim.x) {
     r[L + i] = w[i];
@@ -518,10 +614,16 @@ __global__ void __launch_bounds__(kAT) k_adj_record(double* r, int64_t L, const 
 
 // Data side after the column pass of qbar in one CTA: wbar = -V^T qbar from the partials,
 // zbar = S wbar, Sbar += z wbar^T.
-__global__ void __launch_bounds__(kSmallT) k_data_small(const double* __restrict__ part, int nblk, int K,
-                                                        const double* __restrict__ S, int Tm,
-                                                        const double* __restrict__ z, double* wb, double* zb,
-                                                        double* Sb) {
+__global__ void __launch_bounds__(kSmallT) k_data_small(TP<const double> part_, int nblk, int K,
+                                                        TP<const double> S_, int Tm, TP<const double> z_,
+                                                        TP<double> wb_, TP<double> zb_, TP<double> Sb_) {
+  const int tr = blockIdx.z;
+  const double* __restrict__ part = part_.at(tr);
+  const double* __restrict__ S = S_.at(tr);
+  const double* __restrict__ z = z_.at(tr);
+  double* wb = wb_.at(tr);
+  double* zb = zb_.at(tr);
+  double* Sb = Sb_.at(tr);
   const int wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int j = wid; j < K; j += nw) colreduce_col(part, nblk, K, j, -1.0, wb, 0.0, nullptr);
   __syncthreads();
@@ -534,10 +636,15 @@ __global__ void __launch_bounds__(kSmallT) k_data_small(const double* __restrict
 // tail of p is read back from the stored column (p[r] = u[r] for r > kD, p[kD] recorded).
 // rs = the step's record: rs[0] = p[kD], rs[1] = alpha.
 template <typename T>
-__global__ void __launch_bounds__(kAT) k_pbar(T* __restrict__ qbar, const T* __restrict__ u,
-                                              const T* __restrict__ ub, const double* __restrict__ cb,
-                                              const double* __restrict__ rs, int kD,
-                                              const double* __restrict__ dpre, int64_t dim) {
+__global__ void __launch_bounds__(kAT) k_pbar(TP<T> qbar_, TP<const T> u_, TP<const T> ub_, TP<const double> cb_,
+                                              TP<const double> rs_, int kD, TP<const double> dpre_, int64_t dim) {
+  const int tr = blockIdx.z;
+  T* __restrict__ qbar = qbar_.at(tr);
+  const T* __restrict__ u = u_.at(tr);
+  const T* __restrict__ ub = ub_.at(tr);
+  const double* __restrict__ cb = cb_.at(tr);
+  const double* __restrict__ rs = rs_.at(tr);
+  const double* __restrict__ dpre = dpre_.at(tr);
   __shared__ T coef_s;
   const double ppiv = rs[0], alpha = rs[1];
   if (threadIdx.x == 0) {   // one FP64 division per CTA
@@ -557,9 +664,13 @@ __global__ void __launch_bounds__(kAT) k_pbar(T* __restrict__ qbar, const T* __r
 // out[r] = sgn * (sigma g_r) for first <= r < dim (the step's draw, in the state's precision),
 // 0 elsewhere; sgn = *sgnp.
 template <typename T>
-__global__ void __launch_bounds__(kAT) k_draw_d(DrawKey key, int64_t first, int64_t dim, T sigma,
-                                                const double* __restrict__ sgnp, T* out) {
-  const T sg = (T)*sgnp;
+__global__ void __launch_bounds__(kAT) k_draw_d(DrawKey key, int64_t first, int64_t dim,
+                                                const TrialDesc* __restrict__ desc, TP<const double> sgnp_, TP<T> out_) {
+  const int tr = blockIdx.z;
+  key.trial = desc[tr].trial;
+  const T sigma = (T)desc[tr].sigma;
+  T* out = out_.at(tr);
+  const T sg = (T)*sgnp_.at(tr);
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < dim; r += (int64_t)gridDim.x * blockDim.x) {
     T v = T(0);
     if (r >= first) {
@@ -572,72 +683,110 @@ __global__ void __launch_bounds__(kAT) k_draw_d(DrawKey key, int64_t first, int6
 }
 
 // ------------------------------------------------------------------------------------
-// Host side
+// Host side.  Every launch covers all trials of the state (grid z = trial); per-trial arrays
+// are addressed through TP (pointer of trial 0, distance between trials).
 struct Ctx {
   hd_state* st;
   cudaStream_t s;
+  int nz;           // trials
 };
+
+template <typename P>
+bool al16tp(const TP<P>& t) {
+  return t.p == nullptr || (((uintptr_t)t.p & 15u) == 0 && ((t.s * (int64_t)sizeof(P)) & 15) == 0);
+}
 
 unsigned rows_grid(const hd_state* st, int64_t dim) {
   const int64_t want = (dim + kAT - 1) / kAT;
-  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)st->nsm * 8));
+  const int64_t cap = std::max<int64_t>(1, (int64_t)st->nsm * 8 / std::max(1, st->count));
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, cap));
 }
+
+template <typename P>
+TP<const P> cst(const TP<P>& t) { return TP<const P>{t.p, t.s}; }
 
 // Column pass o_v = s_v A^T v_v; with o1 null only the partial sums are formed (a following
 // single-CTA kernel reduces them).
 template <typename T>
-void colpass(const Ctx& c, const T* A, int64_t ld, int K, int64_t dim, const T* v1, double s1, double* o1,
-             const T* v2 = nullptr, double s2 = 0.0, double* o2 = nullptr) {
+void colpass(const Ctx& c, TP<const T> A, int64_t ld, int K, int64_t dim, TP<const T> v1, double s1, TP<double> o1,
+             TP<const T> v2 = TP<const T>{nullptr, 0}, double s2 = 0.0, TP<double> o2 = TP<double>{nullptr, 0}) {
   if (K <= 0) return;
   AdjState& A_ = *c.st->adj;
-  if (sizeof(T) == 4 && dim % 4 == 0 && al16(A) && al16(v1) && (!v2 || al16(v2)))
-    k_colpass4<<<dim3(A_.nblk, (K + 7) / 8), kAT, 0, c.s>>>((const float*)A, ld, K, dim / 4, (const float*)v1,
-                                                            (const float*)v2, A_.part);
+  const TP<double> part = tp(A_.part, A_.part_stride);
+  if (sizeof(T) == 4 && dim % 4 == 0 && al16tp(A) && al16tp(v1) && al16tp(v2))
+    k_colpass4<<<dim3(A_.nblk, (K + 7) / 8, c.nz), kAT, 0, c.s>>>(
+        TP<const float>{(const float*)A.p, A.s}, ld, K, dim / 4, TP<const float>{(const float*)v1.p, v1.s},
+        TP<const float>{(const float*)v2.p, v2.s}, part);
   else
-    k_colpass<T><<<dim3(A_.nblk, (K + 7) / 8), kAT, 0, c.s>>>(A, ld, K, dim, v1, v2, A_.part);
-  if (o1) k_colreduce<<<(K + kAT / 32 - 1) / (kAT / 32), kAT, 0, c.s>>>(A_.part, A_.nblk, K, s1, o1, s2, o2);
+    k_colpass<T><<<dim3(A_.nblk, (K + 7) / 8, c.nz), kAT, 0, c.s>>>(A, ld, K, dim, v1, v2, part);
+  if (o1.p)
+    k_colreduce<<<dim3((K + kAT / 32 - 1) / (kAT / 32), 1, c.nz), kAT, 0, c.s>>>(cst(part), A_.nblk, K, s1, o1, s2, o2);
 }
 
 template <typename T>
-void rowpass(const Ctx& c, T* out, const T* in, double s_in, const T* A, int64_t ld, int K, const double* coef,
-             double cscale, int64_t dim, const double* dpre, int Kd, int acc, int64_t rnorm = INT64_MAX,
-             double* npart = nullptr, unsigned grid = 0) {
+void rowpass(const Ctx& c, TP<T> out, TP<const T> in, double s_in, TP<const T> A, int64_t ld, int K,
+             TP<const double> coef, double cscale, int64_t dim, TP<const double> dpre, int Kd, int acc,
+             int64_t rnorm = INT64_MAX, TP<double> npart = TP<double>{nullptr, 0}, unsigned grid = 0) {
   const unsigned g = grid ? grid : rows_grid(c.st, dim);
-  if (sizeof(T) == 4 && !dpre && !npart && dim % 4 == 0 && al16(out) && (!in || al16(in)) && al16(A)) {
-    k_rowpass4<<<rows_grid(c.st, dim / 4), kAT, 0, c.s>>>((float*)out, (const float*)in, s_in, (const float*)A, ld, K,
-                                                          coef, cscale, dim / 4, acc);
+  if (sizeof(T) == 4 && !dpre.p && !npart.p && dim % 4 == 0 && al16tp(out) && al16tp(in) && al16tp(A)) {
+    k_rowpass4<<<dim3(rows_grid(c.st, dim / 4), 1, c.nz), kAT, 0, c.s>>>(
+        TP<float>{(float*)out.p, out.s}, TP<const float>{(const float*)in.p, in.s}, s_in,
+        TP<const float>{(const float*)A.p, A.s}, ld, K, coef, cscale, dim / 4, acc);
     return;
   }
-  k_rowpass<T><<<g, kAT, 0, c.s>>>(out, in, s_in, A, ld, K, coef, cscale, dim, dpre, Kd, acc, rnorm, npart);
+  k_rowpass<T><<<dim3(g, 1, c.nz), kAT, 0, c.s>>>(out, in, s_in, A, ld, K, coef, cscale, dim, dpre, Kd, acc, rnorm,
+                                                  npart);
 }
 
 template <typename T>
-void rankN(const Ctx& c, T* Ab, int64_t ld, int K, int64_t dim, const RankTerms& t) {
+void rankN(const Ctx& c, TP<T> Ab, int64_t ld, int K, int64_t dim, const RankTerms& t) {
   if (K <= 0 || t.n <= 0) return;
-  bool al = sizeof(T) == 4 && dim % 4 == 0 && al16(Ab);
-  for (int q = 0; q < t.n; q++) al = al && al16(t.v[q]);
+  bool al = sizeof(T) == 4 && dim % 4 == 0 && al16tp(Ab);
+  for (int q = 0; q < t.n; q++) al = al && al16tp(TP<const T>{(const T*)t.v[q], t.sv[q]});
   if (al) {
-    dim3 g4(rows_grid(c.st, dim / 4), (unsigned)((K + 7) / 8));
-    k_rankN4<<<g4, kAT, 0, c.s>>>((float*)Ab, ld, K, dim / 4, t);
+    dim3 g4(rows_grid(c.st, dim / 4), (unsigned)((K + 7) / 8), c.nz);
+    k_rankN4<<<g4, kAT, 0, c.s>>>(TP<float>{(float*)Ab.p, Ab.s}, ld, K, dim / 4, t);
     return;
   }
-  dim3 g(rows_grid(c.st, dim), (unsigned)((K + 7) / 8));
+  dim3 g(rows_grid(c.st, dim), (unsigned)((K + 7) / 8), c.nz);
   k_rankN<T><<<g, kAT, 0, c.s>>>(Ab, ld, K, dim, t);
 }
 
 template <typename T>
-void rank(const Ctx& c, T* Ab, int64_t ld, int K, int64_t dim, const T* a, const double* b, double sb,
-          const T* cc = nullptr, const double* d = nullptr, double sd = 0.0, const T* e = nullptr,
-          const double* f = nullptr, double sf = 0.0, int Kf = 0) {
+void rank(const Ctx& c, TP<T> Ab, int64_t ld, int K, int64_t dim, TP<const T> a, TP<const double> b, double sb,
+          TP<const T> cc = TP<const T>{nullptr, 0}, TP<const double> d = TP<const double>{nullptr, 0}, double sd = 0.0,
+          TP<const T> e = TP<const T>{nullptr, 0}, TP<const double> f = TP<const double>{nullptr, 0}, double sf = 0.0,
+          int Kf = 0) {
   if (K <= 0) return;
-  if (sizeof(T) == 4 && dim % 4 == 0 && al16(Ab) && al16(a) && (!cc || al16(cc)) && (!e || al16(e))) {
-    dim3 g4(rows_grid(c.st, dim / 4), (unsigned)((K + 7) / 8));
-    k_rank4<<<g4, kAT, 0, c.s>>>((float*)Ab, ld, K, dim / 4, (const float*)a, b, sb, (const float*)cc, d, sd,
-                                 (const float*)e, f, sf, Kf);
+  if (sizeof(T) == 4 && dim % 4 == 0 && al16tp(Ab) && al16tp(a) && al16tp(cc) && al16tp(e)) {
+    dim3 g4(rows_grid(c.st, dim / 4), (unsigned)((K + 7) / 8), c.nz);
+    k_rank4<<<g4, kAT, 0, c.s>>>(TP<float>{(float*)Ab.p, Ab.s}, ld, K, dim / 4,
+                                 TP<const float>{(const float*)a.p, a.s}, b, sb,
+                                 TP<const float>{(const float*)cc.p, cc.s}, d, sd,
+                                 TP<const float>{(const float*)e.p, e.s}, f, sf, Kf);
     return;
   }
-  dim3 g(rows_grid(c.st, dim), (unsigned)((K + 7) / 8));
+  dim3 g(rows_grid(c.st, dim), (unsigned)((K + 7) / 8), c.nz);
   k_rank<T><<<g, kAT, 0, c.s>>>(Ab, ld, K, dim, a, b, sb, cc, d, sd, e, f, sf, Kf);
+}
+
+// Distances between consecutive trials of the state's own arrays (0 for a single trial).
+struct Strides {
+  int64_t V[2], S, dpre, B[2], ws;
+};
+Strides state_strides(const hd_state* st) {
+  Strides r{};
+  if (st->count < 2) return r;
+  const TrialDesc& a = st->hdesc[0];
+  const TrialDesc& b = st->hdesc[1];
+  for (int s = 0; s < 2; s++) {
+    r.V[s] = ((const char*)b.st[s].V - (const char*)a.st[s].V) / (int64_t)st->esz;
+    r.B[s] = a.basis[s] ? ((const char*)b.basis[s] - (const char*)a.basis[s]) / (int64_t)st->esz : 0;
+  }
+  r.S = b.st[0].S - a.st[0].S;
+  r.dpre = b.st[0].dpre - a.st[0].dpre;
+  r.ws = b.ws.z - a.ws.z;
+  return r;
 }
 
 template <typename T>
@@ -651,46 +800,47 @@ int adj_step(hd_state* st, const void* ybar, const void* x_in, void* xbar) {
   const StackDev& Se = td.st[e];
   const int64_t nd = st->dims[d][0], ne = st->dims[e][0];
   const bool haar = st->ens == HD_HAAR;
-  const T* Vd = (const T*)Sd.V;
-  const T* Ve = (const T*)Se.V;
-  T* Vbd = (T*)A.Vbar[d];
-  T* Vbe = (T*)A.Vbar[e];
+  const Strides ss = state_strides(st);
+  const TP<const T> Vd{(const T*)Sd.V, ss.V[d]};
+  const TP<const T> Ve{(const T*)Se.V, ss.V[e]};
+  const TP<T> Vbd{(T*)A.Vbar[d], A.vbar_stride[d]};
+  const TP<T> Vbe{(T*)A.Vbar[e], A.vbar_stride[e]};
+  const TP<const double> SdS{Sd.S, ss.S}, SeS{Se.S, ss.S};
+  const TP<const double> Sdp{Sd.dpre, ss.dpre}, Sep{Se.dpre, ss.dpre};
+  const TP<double> Sbd{A.Sbar[d], A.sbar_stride}, Sbe{A.Sbar[e], A.sbar_stride};
   const int Tm = st->Sld;   // leading dimension of S and Sbar
-  const Ctx c{st, st->stream};
+  const Ctx c{st, st->stream, st->count};
   const int64_t L = A.dmax;
   T* vec = (T*)A.vec;
-  T* ub = vec + kVub * L;
-  T* qb = vec + kVqb * L;
-  T* gd = vec + kVg * L;
-  const T* xd = x_in ? (const T*)x_in : (const T*)((const char*)A.X + (size_t)(t - 1) * A.ldx * sizeof(T));
-  const T* ybd = (const T*)ybar;
-  T* xb = (T*)xbar;
-  auto sm = [&](int slot) { return A.small + (int64_t)slot * A.small_ld; };
-  double* bb = sm(kSbb);
-  double* bo = sm(kSb);
-  double* cb = sm(kScb);
-  double* zb = sm(kSzb);
-  double* wb = sm(kSwb);
-  double* E = sm(kSE);
-  double* cv = sm(kSc);
-  double* hb = sm(kShb);
-  double* au = sm(kSau);
-  double* bu = sm(kSbu);
-  double* bbu = sm(kSbbu);
-  double* abu = sm(kSabu);
+  const TP<T> ub{vec + kVub * L, A.vec_stride};
+  const TP<T> qb{vec + kVqb * L, A.vec_stride};
+  const TP<T> gd{vec + kVg * L, A.vec_stride};
+  // the step input: the caller's (packed) or the recorded one (slot t - 1, packed)
+  const TP<const T> xd = x_in ? TP<const T>{(const T*)x_in, nd}
+                              : TP<const T>{(const T*)((const char*)A.X + (size_t)(t - 1) * A.ldx * sizeof(T)), nd};
+  const TP<const T> ybd{(const T*)ybar, ne};
+  const TP<T> xb{(T*)xbar, nd};
+  auto sm = [&](int slot) { return TP<double>{A.small + (int64_t)slot * A.small_ld, A.small_stride}; };
+  const TP<double> bb = sm(kSbb), bo = sm(kSb), cb = sm(kScb), zb = sm(kSzb), wb = sm(kSwb), E = sm(kSE);
+  const TP<double> cv = sm(kSc), hb = sm(kShb), au = sm(kSau), bu = sm(kSbu), bbu = sm(kSbbu), abu = sm(kSabu);
+  const TP<double> part{A.part, A.part_stride};
   const unsigned gv = rows_grid(st, std::max(nd, ne));
+  const TP<double> none{nullptr, 0};
+  const TP<const double> cnone{nullptr, 0};
+  const TP<const T> tnone{nullptr, 0};
 
   // forward quantities of step t, recorded after it: z = V_D^T x, (Gin) h = B_D^T x, w, p_head,
   // p's pivot entry and alpha; p's tail is the stored column u of V_D (minus s alpha at the pivot)
   const double* rz = A.rec + (int64_t)(t - 1) * A.rec_ld;
-  const double* z = rz;
-  const double* h = rz + kD;
-  const double* w = rz + st->Sld;
-  const double* phead = rz + 2 * (int64_t)st->Sld;
-  const double* rs = rz + 3 * (int64_t)st->Sld;
-  const double* ra = rz + 3 * (int64_t)st->Sld + 8;    // V_D^T u (new data column)
-  const double* rag = rz + 4 * (int64_t)st->Sld + 8;   // V_N^T u_g (Haar: new random column)
-  const T* ucol = Vd + (int64_t)kD * Sd.ld;
+  const int64_t sr = A.rec_stride;
+  const TP<const double> z{rz, sr};
+  const TP<const double> h{rz + kD, sr};
+  const TP<const double> w{rz + st->Sld, sr};
+  const TP<const double> phead{rz + 2 * (int64_t)st->Sld, sr};
+  const TP<const double> rs{rz + 3 * (int64_t)st->Sld, sr};
+  const TP<const double> ra{rz + 3 * (int64_t)st->Sld + 8, sr};    // V_D^T u (new data column)
+  const TP<const double> rag{rz + 4 * (int64_t)st->Sld + 8, sr};   // V_N^T u_g (Haar: new random column)
+  const TP<const T> ucol{Vd.p + (int64_t)kD * Sd.ld, Vd.s};
   const unsigned gp = rows_grid(st, nd);
 
   // A data-side update held back by the previous call (the next-later step) joins this
@@ -704,6 +854,8 @@ int adj_step(hd_state* st, const void* ybar, const void* x_in, void* xbar) {
       rt.c[rt.n] = pd.c[q];
       rt.s[rt.n] = pd.sc[q];
       rt.K[rt.n] = pd.Kq[q];
+      rt.sv[rt.n] = pd.sv[q];
+      rt.sc[rt.n] = pd.scs[q];
       rt.n++;
     }
     pd.on = 0;
@@ -712,7 +864,7 @@ int adj_step(hd_state* st, const void* ybar, const void* x_in, void* xbar) {
     RankTerms rt{};
     const int s0 = pd.s, K0 = pd.K;
     pending_terms(rt);
-    rankN<T>(c, (T*)A.Vbar[s0], td.st[s0].ld, K0, st->dims[s0][0], rt);
+    rankN<T>(c, TP<T>{(T*)A.Vbar[s0], A.vbar_stride[s0]}, td.st[s0].ld, K0, st->dims[s0][0], rt);
   }
 
   // output product
@@ -720,58 +872,61 @@ int adj_step(hd_state* st, const void* ybar, const void* x_in, void* xbar) {
     const int Ke = kD + 1;   // the other stack including this step's random reflector
     // bb = -V_N^T ybar, the output-product adjoint, and the S recurrence of this step's random
     // column (L_t = H_t(g_t), column kD of V_N)
-    colpass<T>(c, Ve, Se.ld, Ke, ne, ybd, -1.0, nullptr);
-    k_out_haar_adj<T><<<1, kSmallT, 0, c.s>>>(A.part, A.nblk, Ve, Se.ld, Ke, Se.S, Tm, Se.dpre, phead, rs, cv, bb,
-                                              ybd, A.Sbar[e], Vbe, bo, cb, rag, au);
+    colpass<T>(c, Ve, Se.ld, Ke, ne, ybd, -1.0, none);
+    k_out_haar_adj<T><<<dim3(1, 1, c.nz), kSmallT, 0, c.s>>>(cst(part), A.nblk, Ve, Se.ld, Ke, SeS, Tm, Sep, phead, rs,
+                                                             cv, bb, ybd, Sbe, Vbe, bo, cb, rag, au);
     RankTerms rt{};
-    rt.v[0] = ybd; rt.c[0] = bo; rt.s[0] = -1.0; rt.K[0] = Ke;
-    rt.v[1] = Ve + (int64_t)kD * Se.ld; rt.c[1] = au; rt.s[1] = 1.0; rt.K[1] = Ke;
+    rt.v[0] = ybd.p; rt.c[0] = bo.p; rt.s[0] = -1.0; rt.K[0] = Ke; rt.sv[0] = ybd.s; rt.sc[0] = bo.s;
+    rt.v[1] = Ve.p + (int64_t)kD * Se.ld; rt.c[1] = au.p; rt.s[1] = 1.0; rt.K[1] = Ke; rt.sv[1] = Ve.s;
+    rt.sc[1] = au.s;
     rt.n = 2;
     if (join) pending_terms(rt);
     rankN<T>(c, Vbe, Se.ld, Ke, ne, rt);
   } else {
     if (kN > 0) {
       colpass<T>(c, Ve, Se.ld, kN, ne, ybd, -1.0, bb);
-      k_out_small<T><<<1, kSmallT, 0, c.s>>>(Ve, Se.ld, kN, kN, Se.S, Tm, Se.dpre, h, bb, ybd, A.Sbar[e], Vbe, bo,
-                                        hb);
-      rank<T>(c, Vbe, Se.ld, kN, ne, ybd, bo, -1.0);
+      k_out_small<T><<<dim3(1, 1, c.nz), kSmallT, 0, c.s>>>(Ve, Se.ld, kN, kN, SeS, Tm, Sep, h, cst(bb), ybd, Sbe,
+                                                            Vbe, bo, hb);
+      rank<T>(c, Vbe, Se.ld, kN, ne, ybd, cst(bo), -1.0);
     }
-    const T* Be = (const T*)td.basis[e];
+    const TP<const T> Be{(const T*)td.basis[e], ss.B[e]};
     const int64_t lde = td.ldb[e];
-    T* Bbe = (T*)A.Bbar[e];
+    const TP<T> Bbe{(T*)A.Bbar[e], A.bbar_stride[e]};
     colpass<T>(c, Be, lde, kD + 1, ne, ybd, 1.0, cb);         // [pbar_head; alphabar]
-    k_head_alpha<<<1, kAT, 0, c.s>>>(phead, kD, rs, cv);        // [p_head; alpha]
-    rank<T>(c, Bbe, lde, kD + 1, ne, ybd, cv, 1.0);
+    k_head_alpha<<<dim3(1, 1, c.nz), kAT, 0, c.s>>>(phead, kD, rs, cv);   // [p_head; alpha]
+    rank<T>(c, Bbe, lde, kD + 1, ne, ybd, cst(cv), 1.0);
     if (kN > 0) {
       // the basis column built at this step, u = (I - V_N S_N V_N^T) Delta_N g: its adjoint
       // is complete; g is constant
-      const T* ubar_b = Bbe + (int64_t)kD * lde;
+      const TP<const T> ubar_b{(const T*)Bbe.p + (int64_t)kD * lde, Bbe.s};
       DrawKey key = key_for(st, t);
-      k_draw_d<T><<<gv, kAT, 0, c.s>>>(key, kN, ne, (T)td.sigma, Se.dpre + kN, gd);
-      colpass<T>(c, Ve, Se.ld, kN, ne, ubar_b, -1.0, bbu, gd, 1.0, au);
-      k_tri<<<1, kSmallT, 0, c.s>>>(Se.S, Tm, kN, au, 1.0, 0, bu);
-      k_tri<<<1, kSmallT, 0, c.s>>>(Se.S, Tm, kN, bbu, 1.0, 1, abu);
-      k_outer_upper<<<1, kAT, 0, c.s>>>(A.Sbar[e], Tm, kN, bbu, au);
-      rank<T>(c, Vbe, Se.ld, kN, ne, ubar_b, bu, -1.0, gd, abu, 1.0);
+      k_draw_d<T><<<dim3(gv, 1, c.nz), kAT, 0, c.s>>>(key, kN, ne, st->ddesc, TP<const double>{Sep.p + kN, Sep.s},
+                                                       gd);
+      colpass<T>(c, Ve, Se.ld, kN, ne, ubar_b, -1.0, bbu, cst(gd), 1.0, au);
+      k_tri<<<dim3(1, 1, c.nz), kSmallT, 0, c.s>>>(SeS, Tm, kN, cst(au), 1.0, 0, bu);
+      k_tri<<<dim3(1, 1, c.nz), kSmallT, 0, c.s>>>(SeS, Tm, kN, cst(bbu), 1.0, 1, abu);
+      k_outer_upper<<<dim3(1, 1, c.nz), kAT, 0, c.s>>>(Sbe, Tm, kN, cst(bbu), cst(au));
+      rank<T>(c, Vbe, Se.ld, kN, ne, ubar_b, cst(bu), -1.0, cst(gd), cst(abu), 1.0);
     }
   }
 
   // the data-side reflector of this step (column kD of V_D): ubar = Vbar[:, kD] + the S
   // recurrence's V[:, 0..kD] coef (E = [abar; -tau^2 taubar])
-  k_rec_col<<<1, kSmallT, 0, c.s>>>(Sd.S, A.Sbar[d], Tm, kD, ra, E);
-  rowpass<T>(c, ub, Vbd + (int64_t)kD * Sd.ld, 1.0, Vd, Sd.ld, kD + 1, E, 1.0, nd, nullptr, 0, 0);
-  k_pbar<T><<<gp, kAT, 0, c.s>>>(qb, ucol, ub, cb, rs, kD, Sd.dpre, nd);
+  k_rec_col<<<dim3(1, 1, c.nz), kSmallT, 0, c.s>>>(SdS, Sbd, Tm, kD, ra, E);
+  rowpass<T>(c, ub, TP<const T>{(const T*)Vbd.p + (int64_t)kD * Sd.ld, Vbd.s}, 1.0, Vd, Sd.ld, kD + 1, cst(E), 1.0,
+             nd, cnone, 0, 0);
+  k_pbar<T><<<dim3(gp, 1, c.nz), kAT, 0, c.s>>>(qb, ucol, cst(ub), cst(cb), rs, kD, Sdp, nd);
 
   // the data product p = Delta (I - V S^T V^T) x
   if (kD > 0) {   // wbar = -V_D^T qbar, zbar = S wbar, Sbar += z wbar^T
-    colpass<T>(c, Vd, Sd.ld, kD, nd, qb, -1.0, nullptr);
-    k_data_small<<<1, kSmallT, 0, c.s>>>(A.part, A.nblk, kD, Sd.S, Tm, z, wb, zb, A.Sbar[d]);
+    colpass<T>(c, Vd, Sd.ld, kD, nd, cst(qb), -1.0, none);
+    k_data_small<<<dim3(1, 1, c.nz), kSmallT, 0, c.s>>>(cst(part), A.nblk, kD, SdS, Tm, z, wb, zb, Sbd);
   }
-  rowpass<T>(c, xb, qb, 1.0, Vd, Sd.ld, kD, zb, 1.0, nd, nullptr, 0, 0);
+  rowpass<T>(c, xb, cst(qb), 1.0, Vd, Sd.ld, kD, cst(zb), 1.0, nd, cnone, 0, 0);
   if (!haar && kN > 0) {
-    const T* Bd = (const T*)td.basis[d];
-    rowpass<T>(c, xb, nullptr, 0.0, Bd, td.ldb[d], kN, hb, 1.0, nd, nullptr, 0, 1);
-    rank<T>(c, (T*)A.Bbar[d], td.ldb[d], kN, nd, xd, hb, 1.0);
+    const TP<const T> Bd{(const T*)td.basis[d], ss.B[d]};
+    rowpass<T>(c, xb, tnone, 0.0, Bd, td.ldb[d], kN, cst(hb), 1.0, nd, cnone, 0, 1);
+    rank<T>(c, TP<T>{(T*)A.Bbar[d], A.bbar_stride[d]}, td.ldb[d], kN, nd, xd, cst(hb), 1.0);
   }
   // Vbar_D += -qbar w^T + x zbar^T + u abar^T.  Haar with the recorded x_t and the next reverse
   // step on the other product: held back for that step's output-side pass over this stack
@@ -781,11 +936,11 @@ int adj_step(hd_state* st, const void* ybar, const void* x_in, void* xbar) {
     pd.s = d;
     pd.K = kD;
     pd.n = 3;
-    pd.v[0] = qb; pd.c[0] = w; pd.sc[0] = -1.0; pd.Kq[0] = kD;
-    pd.v[1] = xd; pd.c[1] = zb; pd.sc[1] = 1.0; pd.Kq[1] = kD;
-    pd.v[2] = ucol; pd.c[2] = E; pd.sc[2] = 1.0; pd.Kq[2] = kD;
+    pd.v[0] = qb.p; pd.c[0] = w.p; pd.sc[0] = -1.0; pd.Kq[0] = kD; pd.sv[0] = qb.s; pd.scs[0] = w.s;
+    pd.v[1] = xd.p; pd.c[1] = zb.p; pd.sc[1] = 1.0; pd.Kq[1] = kD; pd.sv[1] = xd.s; pd.scs[1] = zb.s;
+    pd.v[2] = ucol.p; pd.c[2] = E.p; pd.sc[2] = 1.0; pd.Kq[2] = kD; pd.sv[2] = ucol.s; pd.scs[2] = E.s;
   } else {
-    rank<T>(c, Vbd, Sd.ld, kD, nd, qb, w, -1.0, xd, zb, 1.0, ucol, E, 1.0, kD);   // + u abar^T
+    rank<T>(c, Vbd, Sd.ld, kD, nd, cst(qb), w, -1.0, xd, cst(zb), 1.0, ucol, cst(E), 1.0, kD);   // + u abar^T
   }
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return cuda_fail(st, err);
@@ -796,12 +951,12 @@ int adj_step(hd_state* st, const void* ybar, const void* x_in, void* xbar) {
 int adj_zero(hd_state* st) {
   AdjState& A = *st->adj;
   A.pend.on = 0;
-  const TrialDesc& td = st->hdesc[0];
+  const int nt = st->count;
   for (int s = 0; s < 2; s++) {
-    if (cudaMemsetAsync(A.Vbar[s], 0, (size_t)td.st[s].ld * st->Tm * st->esz, st->stream) != cudaSuccess ||
-        cudaMemsetAsync(A.Sbar[s], 0, (size_t)st->Sld * st->Sld * sizeof(double), st->stream) != cudaSuccess)
+    if (cudaMemsetAsync(A.Vbar[s], 0, (size_t)A.vbar_stride[s] * nt * st->esz, st->stream) != cudaSuccess ||
+        cudaMemsetAsync(A.Sbar[s], 0, (size_t)A.sbar_stride * nt * sizeof(double), st->stream) != cudaSuccess)
       return cuda_fail(st, cudaGetLastError());
-    if (A.Bbar[s] && cudaMemsetAsync(A.Bbar[s], 0, (size_t)td.ldb[s] * st->Tm * st->esz, st->stream) != cudaSuccess)
+    if (A.Bbar[s] && cudaMemsetAsync(A.Bbar[s], 0, (size_t)A.bbar_stride[s] * nt * st->esz, st->stream) != cudaSuccess)
       return cuda_fail(st, cudaGetLastError());
   }
   return HD_OK;
@@ -809,7 +964,8 @@ int adj_zero(hd_state* st) {
 
 }  // namespace
 
-// Called by the forward step when reverse mode is on: record the step and its input.
+// Called by the forward step when reverse mode is on: record the step and its input (the
+// packed vector of all trials).
 int adj_record_step(hd_state* st, const void* x, int transpose, int kD, int kN) {
   AdjState& A = *st->adj;
   if (A.rev != st->t) return HD_ERR_STATE;   // a reverse pass has started: no more forward steps
@@ -817,7 +973,7 @@ int adj_record_step(hd_state* st, const void* x, int transpose, int kD, int kN) 
   A.kD.push_back(kD);
   A.kN.push_back(kN);
   if (A.record_x) {
-    const int64_t nin = st->dims[transpose ? 1 : 0][0];
+    const int64_t nin = st->off[transpose ? 1 : 0][st->count];
     cudaError_t e = cudaMemcpyAsync((char*)A.X + (size_t)st->t * A.ldx * st->esz, x, (size_t)nin * st->esz,
                                     cudaMemcpyDeviceToDevice, st->stream);
     if (e != cudaSuccess) return cuda_fail(st, e);
@@ -826,16 +982,19 @@ int adj_record_step(hd_state* st, const void* x, int transpose, int kD, int kN) 
   return HD_OK;
 }
 
-// Called by the forward step after its launches: copy the step's small vectors from the
-// workspace (they are overwritten by the next step).
+// Called by the forward step after its launches: copy the step's small vectors from each
+// trial's workspace (they are overwritten by the next step).
 int adj_record_after(hd_state* st, int kD, int kN) {
   AdjState& A = *st->adj;
   const Ws& ws = st->hdesc[0].ws;
+  const int64_t sw = state_strides(st).ws;
   double* r = A.rec + (int64_t)(st->t) * A.rec_ld;   // st->t is still this step's index
   const int nz = (st->ens == HD_GINIBRE) ? kD + kN : kD;   // Haar's K1 forms no basis dots
   const int nug = (st->ens == HD_HAAR) ? kN : 0;            // V_N^T u_g of the new random column
-  k_adj_record<<<1, kAT, 0, st->stream>>>(r, st->Sld, ws.z, nz, ws.w, ws.phead, kD, ws.scal,
-                                          ws.scrb + ws.scr_stride * 1, ws.scrb + ws.scr_stride * 2, nug);
+  k_adj_record<<<dim3(1, 1, st->count), kAT, 0, st->stream>>>(
+      TP<double>{r, A.rec_stride}, st->Sld, TP<const double>{ws.z, sw}, nz, TP<const double>{ws.w, sw},
+      TP<const double>{ws.phead, sw}, kD, TP<const double>{ws.scal, sw},
+      TP<const double>{ws.scrb + ws.scr_stride * 1, sw}, TP<const double>{ws.scrb + ws.scr_stride * 2, sw}, nug);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(st, e);
   return HD_OK;
@@ -859,35 +1018,46 @@ using namespace hd;
 HD_API int hd_adjoint_enable(hd_state* st, int flags) {
   if (!st) return HD_ERR_ARG;
   if (st->poisoned) return st->poisoned;
-  if (st->count != 1) return HD_ERR_ARG;
   if (st->t != 0) return HD_ERR_STATE;
   if (flags & ~(HD_ADJ_RECORD_X)) return HD_ERR_ARG;
+  // a batch must have trials of one shape (every per-trial array then evenly spaced)
+  for (int i = 1; i < st->count; i++)
+    if (st->dims[0][i] != st->dims[0][0] || st->dims[1][i] != st->dims[1][0]) return HD_ERR_ARG;
   if (cudaSetDevice(st->device) != cudaSuccess) return cuda_fail(st, cudaErrorInvalidDevice);
+  const int nt = st->count;
   if (!st->adj) {
     AdjState* A = new (std::nothrow) AdjState();
     if (!A) return HD_ERR_OOM;
     st->adj = A;
     const TrialDesc& td = st->hdesc[0];
     const int Tm = st->Tm;
+    A->sbar_stride = (int64_t)st->Sld * st->Sld;
     for (int s = 0; s < 2; s++) {
-      A->Vbar[s] = dalloc(st, (size_t)td.st[s].ld * Tm * st->esz);
-      A->Sbar[s] = (double*)dalloc(st, (size_t)st->Sld * st->Sld * sizeof(double));
+      A->vbar_stride[s] = td.st[s].ld * Tm;
+      A->Vbar[s] = dalloc(st, (size_t)A->vbar_stride[s] * nt * st->esz);
+      A->Sbar[s] = (double*)dalloc(st, (size_t)A->sbar_stride * nt * sizeof(double));
       if (!A->Vbar[s] || !A->Sbar[s]) return HD_ERR_OOM;
       if (st->ens == HD_GINIBRE) {
-        A->Bbar[s] = dalloc(st, (size_t)td.ldb[s] * Tm * st->esz);
+        A->bbar_stride[s] = td.ldb[s] * Tm;
+        A->Bbar[s] = dalloc(st, (size_t)A->bbar_stride[s] * nt * st->esz);
         if (!A->Bbar[s]) return HD_ERR_OOM;
       }
     }
     A->dmax = round_up(std::max(st->dims[0][0], st->dims[1][0]), 256);
-    A->ldx = A->dmax;
-    A->vec = dalloc(st, (size_t)kAdjVecs * A->dmax * st->esz);
+    A->ldx = round_up(std::max(st->off[0][nt], st->off[1][nt]), 256);   // one packed input per step
+    A->vec_stride = (int64_t)kAdjVecs * A->dmax;
+    A->vec = dalloc(st, (size_t)A->vec_stride * nt * st->esz);
     A->small_ld = Tm + 8;
-    A->small = (double*)dalloc(st, (size_t)kAdjSmall * A->small_ld * sizeof(double));
-    A->nblk = std::max(1, 2 * st->nsm);
+    A->small_stride = (int64_t)kAdjSmall * A->small_ld;
+    A->small = (double*)dalloc(st, (size_t)A->small_stride * nt * sizeof(double));
+    // row chunks of a column pass per trial: about two CTAs per SM over the whole batch
+    A->nblk = std::max(4, 2 * st->nsm / nt);
     const int64_t gmax = (int64_t)st->nsm * 8;
-    A->part = (double*)dalloc(st, (size_t)std::max<int64_t>((int64_t)A->nblk * (Tm + 1) * 2, gmax) * sizeof(double));
+    A->part_stride = std::max<int64_t>((int64_t)A->nblk * (Tm + 1) * 2, gmax);
+    A->part = (double*)dalloc(st, (size_t)A->part_stride * nt * sizeof(double));
     A->rec_ld = 5 * (int64_t)st->Sld + 8;
-    A->rec = (double*)dalloc(st, (size_t)A->rec_ld * Tm * sizeof(double));
+    A->rec_stride = A->rec_ld * Tm;
+    A->rec = (double*)dalloc(st, (size_t)A->rec_stride * nt * sizeof(double));
     if (!A->vec || !A->small || !A->part || !A->rec) return HD_ERR_OOM;
   }
   AdjState& A = *st->adj;

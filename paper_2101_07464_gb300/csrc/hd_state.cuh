@@ -32,6 +32,7 @@ struct AdjState {
   int record_x = 0;
   std::vector<int8_t> flag;      // per forward step: transpose flag
   std::vector<int> kD, kN;       // per forward step: reflectors in the data / other stack before it
+                                 // (every trial of a batched state has the same dimensions)
   int rev = 0;                   // forward steps not yet reversed
   void* Vbar[2] = {nullptr, nullptr};     // d loss / d V per stack (state dtype, dim x T_max, ld of the stack)
   void* Bbar[2] = {nullptr, nullptr};     // d loss / d basis store per space (Ginibre; state dtype)
@@ -44,6 +45,9 @@ struct AdjState {
   int64_t small_ld = 0;
   double* part = nullptr;        // column-pass partial sums
   int nblk = 1;
+  // distances between consecutive trials of the reverse mode's own arrays (batched states)
+  int64_t part_stride = 0, vec_stride = 0, small_stride = 0, rec_stride = 0, sbar_stride = 0;
+  int64_t vbar_stride[2] = {0, 0}, bbar_stride[2] = {0, 0};
   // per forward step: z (k_D + k_N: data-stack dots, then Gin basis dots), w (k_D), p_head
   // (k_D), then p's pivot entry and alpha, copied from the workspace after the step
   double* rec = nullptr;
@@ -60,6 +64,8 @@ struct AdjState {
     const double* c[3] = {nullptr, nullptr, nullptr};
     double sc[3] = {0.0, 0.0, 0.0};
     int Kq[3] = {0, 0, 0};       // columns each term covers
+    int64_t sv[3] = {0, 0, 0};   // trial strides of v and c
+    int64_t scs[3] = {0, 0, 0};
   } pend;
 };
 

@@ -132,6 +132,15 @@ HD_API int hd_apply(hd_state* st, const void* x, int transpose, void* y);
 HD_API int hd_probe(hd_state* st, const void* x, int transpose, void* y,
                     double* unrevealed_host);
 
+/* hd_probe with the representation as it stood after product `step` (0 <= step <= t; the
+ * leading columns of the reflector stacks, S and the signs are exactly that step's, since
+ * later steps only append): y = Q^(step) x on the part revealed by then.  For an earlier input
+ * x_s this reproduces y_s = M_s x_s with the reflectors that step used, at the cost of s
+ * rather than t columns (the checkpointed reverse mode recomputes segments with it).
+ * Errors: those of hd_probe; HD_ERR_ARG for a step out of range. */
+HD_API int hd_probe_at(hd_state* st, int32_t step, const void* x, int transpose, void* y,
+                       double* unrevealed_host);
+
 /* Built-in dynamics f_t for hd_run (run in the library's kernels):
  *   HD_DYN_TANH       x_{t+1} = tanh(y_t)
  *   HD_DYN_SIGN_MEM   x_{t+1} = sign(y_t) + a x_{t-1}   (sign(0) = 0; x_0 = 0)

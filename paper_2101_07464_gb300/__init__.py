@@ -8,7 +8,7 @@ from .binding import (HD, HDBatch, HDComplex, HDError, USV, HD_F32, HD_F64, HD_G
                       hd_create_batched, hd_destroy, hd_first_product_noalloc, hd_fp64_fma_rate, hd_get_batch_layout,
                       hd_get_counts, hd_get_device_bytes, hd_get_launches, hd_get_map_options,
                       hd_get_tuning, hd_goe_apply, hd_philox_normals,
-                      hd_philox_words, hd_probe, hd_profile_enable, hd_profile_read, hd_reset, hd_run,
+                      hd_philox_words, hd_probe, hd_probe_at, hd_profile_enable, hd_profile_read, hd_reset, hd_run,
                       hd_set_engine, hd_set_options, hd_set_trial_sigmas, hd_set_tuning, hd_sync, hd_usv_apply, lib, library_path,
                       make_run_spec)
 
@@ -16,7 +16,7 @@ __all__ = ["HD", "HDBatch", "HDComplex", "HDError", "USV", "HD_F32", "HD_F64", "
            "hd_adjoint_enable", "hd_adjoint_position", "hd_adjoint_restart", "hd_adjoint_step",
            "hd_apply", "hd_autotune", "hd_check_bounded_wait", "hd_create", "hd_create_batched", "hd_destroy", "hd_first_product_noalloc", "hd_fp64_fma_rate",
            "hd_get_batch_layout", "hd_get_counts", "hd_get_device_bytes", "hd_get_launches",
-           "hd_get_map_options", "hd_get_tuning", "hd_goe_apply", "hd_philox_normals", "hd_philox_words", "hd_probe", "hd_profile_enable",
+           "hd_get_map_options", "hd_get_tuning", "hd_goe_apply", "hd_philox_normals", "hd_philox_words", "hd_probe", "hd_probe_at", "hd_profile_enable",
            "hd_profile_read", "hd_reset", "hd_run", "hd_set_engine", "hd_set_options", "hd_set_trial_sigmas", "hd_set_tuning",
            "hd_sync", "hd_usv_apply", "lib",
            "library_path", "make_run_spec"]

@@ -20,8 +20,9 @@ launches for the whole batch.
 
 Memory: without checkpointing the library records every x_t, and this module keeps every y_t.
 With `checkpoint=S` only x_t at every S-th step is kept.  In backward, each segment is
-recomputed from its first x with hd_probe: the final state maps every earlier x_s to y_s
-exactly on its revealed part (eq. H_t / eq. Gaussian_t), so no step is redrawn.  The
+recomputed from its first x with hd_probe_at: the representation as it stood after step s
+maps x_s to y_s exactly on its revealed part (eq. H_t / eq. Gaussian_t), with the reflectors
+that step used, so no step is redrawn.  The
 segment's x_t are then passed back to the library.  Recomputed values agree with the forward
 pass up to rounding; a discontinuous f_t can amplify that.
 """
@@ -108,7 +109,7 @@ class _Trajectory(torch.autograd.Function):
                 seg = []
                 with torch.no_grad():
                     for t in range(a, b + 1):
-                        y, _ = hd.probe(x, bool(sched[t - 1]))
+                        y, _ = hd.probe(x, bool(sched[t - 1]), step=t)
                         seg.append((x, xprev, y))
                         x, xprev = f(t, y, x, xprev, *params), x
                 for t in range(b, a - 1, -1):

@@ -61,6 +61,7 @@ _PROTOS = {
                                             _c.c_uint64, _c.c_uint32, _c.c_double, _P, _P, _P]),
     "hd_apply": (_c.c_int, [_P, _P, _c.c_int, _P]),
     "hd_probe": (_c.c_int, [_P, _P, _c.c_int, _P, _c.POINTER(_c.c_double)]),
+    "hd_probe_at": (_c.c_int, [_P, _c.c_int32, _P, _c.c_int, _P, _c.POINTER(_c.c_double)]),
     "hd_reset": (_c.c_int, [_P, _c.c_uint64]),
     "hd_sync": (_c.c_int, [_P]),
     "hd_check_bounded_wait": (_c.c_int, [_P, _c.c_uint32]),
@@ -241,6 +242,13 @@ def _rows_addr(t, what):
     if not t.is_cuda or not t.is_contiguous() or t.dim() != 2:
         raise ValueError("%s must be a contiguous 2-D CUDA tensor (T rows)" % what)
     return t.data_ptr()
+
+
+def hd_probe_at(state, step, x, transpose, y):
+    u = ctypes.c_double()
+    _check(lib().hd_probe_at(state, int(step), _ptr(x, what="x"), int(bool(transpose)), _ptr(y, what="y"),
+                             ctypes.byref(u)), "hd_probe_at")
+    return u.value
 
 
 def make_run_spec(transpose_flags, dynamics, a=0.0, use_graph=True, aux=None, y_record=None,
@@ -528,11 +536,13 @@ class HD:
         hd_apply(self.h, x, transpose, out)
         return out
 
-    def probe(self, x, transpose=False):
+    def probe(self, x, transpose=False, step=None):
+        """Q x (or Q^T x) on the revealed part; with `step`, as the representation stood after
+        that product (hd_probe_at)."""
         import torch
         dim_out = self.n if transpose else self.m
         out = torch.empty(dim_out, dtype=self.torch_dtype, device=x.device)
-        u = hd_probe(self.h, x, transpose, out)
+        u = hd_probe(self.h, x, transpose, out) if step is None else hd_probe_at(self.h, step, x, transpose, out)
         return out, u
 
     def reset(self, seed=None):

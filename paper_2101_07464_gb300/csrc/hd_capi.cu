@@ -222,15 +222,19 @@ int do_step(hd_state* st, const void* x, int transpose, void* y, const FuseSpec*
   }
   st->t += 1;
   if (transpose) st->l += 1; else st->r += 1;
+  st->hist.push_back((uint8_t)(transpose ? 1 : 0));
   return HD_OK;
 }
 
+// Probe with the representation as it stood after step `step` (1..t): the leading columns of
+// the stacks, S and the prefix signs are exactly those of that step.
 template <typename T>
-int do_probe(hd_state* st, const void* x, int transpose, void* y, double* unrevealed_host) {
+int do_probe(hd_state* st, const void* x, int transpose, void* y, double* unrevealed_host, int step) {
   const int d = transpose ? 1 : 0;
-  const int cnt[2] = {st->r, st->l};
-  const int kD = (st->ens == HD_HAAR) ? st->t : cnt[d];
-  const int kN = (st->ens == HD_HAAR) ? st->t : cnt[1 - d];
+  int cnt[2] = {0, 0};
+  for (int q = 0; q < step; q++) cnt[st->hist[q] ? 1 : 0] += 1;
+  const int kD = (st->ens == HD_HAAR) ? step : cnt[d];
+  const int kN = (st->ens == HD_HAAR) ? step : cnt[1 - d];
   BatchStep<T> b = make_batch<T>(st, d, kD, kN, x, y);
   b.base.pdl = 0;
   // workspace of max(m, n) + 1 doubles, allocated by the first probe and kept by the state
@@ -259,6 +263,7 @@ template <typename T>
 int run_steps(hd_state* st, const hd_run_spec* sp) {
   if (st->prof_on) st->prof_used = 0;
   st->t = st->r = st->l = 0;
+  st->hist.clear();
   st->drawn = 0;
   if (int rc = adj_on_reset(st)) return rc;
   int cur = 0;
@@ -314,6 +319,7 @@ template <typename T>
 int run_amp(hd_state* st, const hd_run_spec* sp) {
   if (st->prof_on) st->prof_used = 0;
   st->t = st->r = st->l = 0;
+  st->hist.clear();
   st->drawn = 0;
   if (int rc = adj_on_reset(st)) return rc;
   const int cnt = st->count;
@@ -927,6 +933,8 @@ HD_API int hd_run(hd_state* st, const hd_run_spec* sp, const void* x1, void* x_o
     st->launches += st->g_launches;
     st->t = sp->T;
     st->r = st->l = 0;
+    st->hist.assign(sp->transpose, sp->transpose + sp->T);
+    for (auto& f : st->hist) f = f ? 1 : 0;
     for (int t = 0; t < sp->T; t++) (sp->transpose[t] ? st->l : st->r) += 1;
     st->drawn = 1;
     st->run_final = st->g_final;
@@ -949,8 +957,19 @@ HD_API int hd_probe(hd_state* st, const void* x, int transpose, void* y, double*
   if (st->count != 1) return HD_ERR_ARG;
   if (st->poisoned) return st->poisoned;
   if (cudaSetDevice(st->device) != cudaSuccess) return cuda_fail(st, cudaErrorInvalidDevice);
-  return (st->dtype == HD_F64) ? do_probe<double>(st, x, transpose, y, unrevealed_host)
-                               : do_probe<float>(st, x, transpose, y, unrevealed_host);
+  return (st->dtype == HD_F64) ? do_probe<double>(st, x, transpose, y, unrevealed_host, st->t)
+                               : do_probe<float>(st, x, transpose, y, unrevealed_host, st->t);
+}
+
+HD_API int hd_probe_at(hd_state* st, int32_t step, const void* x, int transpose, void* y, double* unrevealed_host) {
+  if (!st || !x || !y || !unrevealed_host) return HD_ERR_ARG;
+  if (transpose != 0 && transpose != 1) return HD_ERR_ARG;
+  if (st->count != 1) return HD_ERR_ARG;
+  if (step < 0 || step > st->t || (size_t)st->t != st->hist.size()) return HD_ERR_ARG;
+  if (st->poisoned) return st->poisoned;
+  if (cudaSetDevice(st->device) != cudaSuccess) return cuda_fail(st, cudaErrorInvalidDevice);
+  return (st->dtype == HD_F64) ? do_probe<double>(st, x, transpose, y, unrevealed_host, step)
+                               : do_probe<float>(st, x, transpose, y, unrevealed_host, step);
 }
 
 HD_API int hd_profile_enable(hd_state* st, int on) {
@@ -1045,6 +1064,7 @@ HD_API int hd_reset(hd_state* st, uint64_t seed) {
   }
   st->seed = seed;
   st->t = st->r = st->l = 0;
+  st->hist.clear();
   st->drawn = 0;
   st->poisoned = 0;
   return adj_on_reset(st);

@@ -1628,15 +1628,28 @@ __device__ __forceinline__ StepPlan<T> trial0_plan(const BatchStep<T>& b) {
 }
 
 template <typename T>
-__global__ void k_probe_q(BatchStep<T> b, double* q, double* unrev) {
+__global__ void __launch_bounds__(256) k_probe_q(BatchStep<T> b, double* q, double* unrev) {
   const StepPlan<T> p = trial0_plan(b);
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // row pass in the storage type, as the sweeps' row passes; four independent chains
+  __shared__ T wsh[kTmaxLimit];
   const int k = p.kD;
+  for (int j = threadIdx.x; j < k; j += blockDim.x) wsh[j] = (T)p.ws.w[j];
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double u2 = 0.0;
   if (i < p.D.dim) {
-    const T* V = (const T*)p.D.V;
-    double acc = (double)p.x[i];
-    for (int j = 0; j < k; j++) acc -= (double)V[i + (int64_t)j * p.D.ld] * p.ws.w[j];
+    const T* V = (const T*)p.D.V + i;
+    const int64_t ld = p.D.ld;
+    T a0 = p.x[i], a1 = T(0), a2 = T(0), a3 = T(0);
+    int j = 0;
+    for (; j + 4 <= k; j += 4) {
+      a0 = fma(-V[(int64_t)j * ld], wsh[j], a0);
+      a1 = fma(-V[(int64_t)(j + 1) * ld], wsh[j + 1], a1);
+      a2 = fma(-V[(int64_t)(j + 2) * ld], wsh[j + 2], a2);
+      a3 = fma(-V[(int64_t)(j + 3) * ld], wsh[j + 3], a3);
+    }
+    for (; j < k; j++) a0 = fma(-V[(int64_t)j * ld], wsh[j], a0);
+    const double acc = (double)((a0 + a1) + (a2 + a3));
     const double d = (k == 0) ? 1.0 : ((i < k) ? p.D.dpre[i + 1] : p.D.dpre[k]);
     q[i] = d * acc;
     if (i >= k) u2 = q[i] * q[i];
@@ -1667,21 +1680,35 @@ __global__ void k_probe_coef(BatchStep<T> b, const double* q) {
 }
 
 template <typename T>
-__global__ void k_probe_out(BatchStep<T> b, const double* q) {
+__global__ void __launch_bounds__(256) k_probe_out(BatchStep<T> b, const double* q) {
   const StepPlan<T> p = trial0_plan(b);
+  // row passes in the storage type, as the sweeps' row passes; independent chains per column block
+  __shared__ T wsh[kTmaxLimit], qsh[kTmaxLimit];
+  const int kN = p.kN;
+  const int kB = (p.ens == 0) ? p.kD : 0;
+  for (int j = threadIdx.x; j < kN; j += blockDim.x) wsh[j] = (T)p.ws.wout[j];
+  for (int j = threadIdx.x; j < kB; j += blockDim.x) qsh[j] = (T)q[j];
+  __syncthreads();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= p.N.dim) return;
-  const int kN = p.kN;
-  const T* VN = (const T*)p.N.V;
+  const T* VN = (const T*)p.N.V + i;
+  const int64_t ld = p.N.ld;
   const double* c = (p.ens == 1) ? q : p.ws.z + p.kD;
   const double d = (kN == 0) ? 1.0 : ((i < kN) ? p.N.dpre[i + 1] : p.N.dpre[kN]);
-  double acc = (i < kN) ? d * c[i] : 0.0;
-  for (int j = 0; j < kN; j++) acc -= (double)VN[i + (int64_t)j * p.N.ld] * p.ws.wout[j];
-  if (p.ens == 0) {
-    const T* Bn = (const T*)p.Bn;
-    for (int j = 0; j < p.kD; j++) acc += (double)Bn[i + (int64_t)j * p.ldBn] * q[j];
+  T a0 = (i < kN) ? (T)(d * c[i]) : T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+  int j = 0;
+  for (; j + 4 <= kN; j += 4) {
+    a0 = fma(-VN[(int64_t)j * ld], wsh[j], a0);
+    a1 = fma(-VN[(int64_t)(j + 1) * ld], wsh[j + 1], a1);
+    a2 = fma(-VN[(int64_t)(j + 2) * ld], wsh[j + 2], a2);
+    a3 = fma(-VN[(int64_t)(j + 3) * ld], wsh[j + 3], a3);
   }
-  p.y[i] = (T)acc;
+  for (; j < kN; j++) a0 = fma(-VN[(int64_t)j * ld], wsh[j], a0);
+  if (kB > 0) {
+    const T* Bn = (const T*)p.Bn + i;
+    for (j = 0; j < kB; j++) a1 = fma(Bn[(int64_t)j * p.ldBn], qsh[j], a1);
+  }
+  p.y[i] = (a0 + a1) + (a2 + a3);
 }
 
 template <typename T>

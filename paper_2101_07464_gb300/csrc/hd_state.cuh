@@ -89,6 +89,7 @@ struct hd_state {
   cudaStream_t stream = nullptr;
   int device = 0;
   int t = 0, r = 0, l = 0;
+  std::vector<uint8_t> hist;     // transpose flag of every step since create/reset
   int drawn = 0;                 // first draws made since create/reset
   int poisoned = 0;              // sticky error code
   size_t esz = 8;                // element size of vectors and stacks

@@ -155,7 +155,8 @@ def test_step_limit_and_reset_replay():
 @pytest.mark.parametrize("ens,m,n", [("haar", 5003, 5003), ("ginibre", 3001, 4999)])
 def test_probe_reproduces_earlier_queries(dtype, ens, m, n):
     """After s steps the state still maps every earlier x_t to y_t (unrevealed part 0), and
-    for Haar Q^T maps y_t back to x_t (eq. H_t / eq. Gaussian_t)."""
+    for Haar Q^T maps y_t back to x_t (eq. H_t / eq. Gaussian_t); hd_probe_at with the
+    representation of step t does the same."""
     from paper_2101_07464_gb300 import HD
     import synth
     T = 16
@@ -181,9 +182,20 @@ def test_probe_reproduces_earlier_queries(dtype, ens, m, n):
             xb, unrev2 = st.probe(ys[t - 1], not tr)
             assert unrev2 <= tol * ys[t - 1].norm().item()
             assert (xb - xs[t - 1]).norm().item() <= tol * xs[t - 1].norm().item()
+        # the representation as it stood after step t reproduces y_t too
+        ya, unra = st.probe(xs[t - 1], tr, step=t)
+        assert unra <= tol * xs[t - 1].norm().item()
+        assert (ya - ys[t - 1]).norm().item() <= tol * ys[t - 1].norm().item()
     # a fresh direction is seen by the hidden block
     _, unrev = st.probe(torch.tensor(synth.x1(n, 99), dtype=tdt, device="cuda"), False)
     assert unrev > 0.5 * np.sqrt(n)
+    # ... also at an earlier step, and step 0 (nothing revealed) gives 0 and the whole norm
+    x0 = torch.tensor(synth.x1(n, 98), dtype=tdt, device="cuda")
+    y0, unr0 = st.probe(x0, False, step=0)
+    assert torch.count_nonzero(y0).item() == 0 and abs(unr0 - x0.norm().item()) <= tol * unr0
+    import paper_2101_07464_gb300 as hd
+    with pytest.raises(hd.HDError):
+        st.probe(x0, False, step=T + 1)
     st.close()
 
 

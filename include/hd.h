@@ -399,7 +399,7 @@ HD_API int hd_philox_words(uint64_t seed, const uint32_t* counters, int64_t nblo
  * hd_adjoint_enable(st, flags): call on a fresh or just-reset state (no step taken).  From
  * then on every forward step is recorded; with HD_ADJ_RECORD_X the library also keeps a copy
  * of each x_t (T_max vectors of the longer dimension, state dtype), otherwise the caller
- * passes x_t back to hd_adjoint_step (recomputing them, e.g. from checkpoints with hd_probe).
+ * passes x_t back to hd_adjoint_step (recomputing them, e.g. from checkpoints with hd_probe_at).
  * Allocates the accumulators once, per trial: per stack dim x T_max elements of the state dtype
  * (dV) and T_max^2 FP64 (dS), per Gin basis store dim x T_max of the state dtype, plus 4 work
  * vectors; with HD_ADJ_RECORD_X one packed input vector per step.

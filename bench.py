@@ -250,19 +250,21 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-# DRAM bytes / algorithmic bytes of one k_update launch, from ncu --set full captures of the
-# current kernel at k = 60, n = 10^6 (FP32: 250.15 MB for 252.0 MB; FP64: 494.3 MB for 504.0 MB);
-# None once the kernel has changed since the capture.
-TRAFFIC_RATIO = {"f32": 250.15 / 252.0, "f64": 494.30 / 504.0}
+# DRAM bytes / algorithmic bytes of one launch of the dominant kernel, from an ncu capture of
+# the current kernel at k = 60, n = 10^6; None until a capture of the current kernel exists.
+# (FP32: 245.57 MB for 248.0 MB at k = 59.)
+TRAFFIC_RATIO = {"f32": 245.57 / 248.0, "f64": None}
+TRAFFIC_KERNEL = "update"
 TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_update launch "
-                  "(k = 60, n = 10^6, same dtype), scaled to the average launch by algorithmic bytes")
+                  "(k = 59, n = 10^6, same dtype), scaled to the average launch by algorithmic bytes")
 
 # Algorithmic FP64 flops per stack element of each sweep in the fused Q / Q^T alternating
 # trajectory (2 per FMA): the update sweep forms p = Delta (x - V w) and the two column
 # products V^T p~ and V^T g_{t+1}; the fused output sweep forms y = c - V w' and the next
 # step's V^T x_{t+1}; the dot sweep V^T x.
-FLOPS_PER_ELEMENT = {"dots": 2.0, "update": 6.0, "output": 4.0}
-KERNEL_NAME = {"dots": "k_dots", "update": "k_update", "output": "k_out_haar"}
+# The step kernel runs both sweeps of a step in one launch.
+FLOPS_PER_ELEMENT = {"dots": 2.0, "update": 6.0, "output": 4.0, "step": 10.0}
+KERNEL_NAME = {"dots": "k_dots", "update": "k_update", "output": "k_out_haar", "step": "k_step"}
 
 
 def measured_peaks():
@@ -280,11 +282,14 @@ def fp64_peak():
     return hd.hd_fp64_fma_rate(iters=1 << 14, reps=5)
 
 
-def haar_columns(T):
-    """Columns each sweep kind streams over one Haar trajectory of T products: before step t
-    both stacks hold t - 1 reflectors; every step has one update and one output sweep."""
-    k = float(T * (T - 1) / 2)
-    return {"update": k, "output": k, "dots": 0.0}
+def haar_columns(T, step_launches):
+    """Columns each kernel kind streams over one Haar trajectory of T products: before step t
+    both stacks hold t - 1 reflectors.  The step kernel runs steps 1 .. s (s = step_launches
+    per trajectory, 0 or T - 1); the other steps launch one update and one output sweep."""
+    s = step_launches
+    k_step = float(s * (s - 1) / 2)
+    k_rest = float(T * (T - 1) / 2) - k_step
+    return {"step": k_step, "update": k_rest, "output": k_rest, "dots": 0.0}
 
 
 def time_trajectories(st, spec, x1, xout, steps, warmup, dist):
@@ -328,6 +333,53 @@ def profile_kernels(st, spec, x1, xout, steps):
     return prof
 
 
+def time_engine_ab(st, spec, x1, out, reps):
+    """ms per trajectory of hd_run with the two-launch steps and with the step kernel
+    (hd_set_engine), CUDA events on the launching stream; the state is left on two launches."""
+    import torch
+    import paper_2101_07464_gb300 as hd
+    res = {}
+    stream = torch.cuda.current_stream()
+    for name, on in (("two_launches_ms", False), ("step_kernel_ms", True)):
+        hd.hd_set_engine(st.h, step_kernel=on)
+        for _ in range(2):
+            hd.hd_run(st.h, spec, x1, out)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            hd.hd_run(st.h, spec, x1, out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        hd.hd_sync(st.h)
+        res[name] = e0.elapsed_time(e1) / reps
+    hd.hd_set_engine(st.h, step_kernel=False)
+    return res
+
+
+def measure_step_kernel(args, rank):
+    """The step kernel (update sweep and fused output sweep in one cooperative launch per
+    step) against the default two launches per step, on the Haar workload (n = 10^6, T = 100,
+    alternating, sign with memory) in FP64 and FP32 with the built-in launch shapes: ms per
+    trajectory, one graph per trajectory, CUDA events."""
+    import torch
+    import synth
+    import paper_2101_07464_gb300 as hd
+    n, T = args.n, args.T
+    flags = schedule(T)
+    out = {}
+    for dtype in ("f64", "f32"):
+        st = hd.HD("haar", n, n, T, args.seed, dtype, trial=rank)
+        x1 = torch.tensor(synth.x1(n, args.seed, trial=rank), dtype=st.torch_dtype, device="cuda")
+        xo = torch.empty_like(x1)
+        spec = hd.make_run_spec(flags, "sign_mem", 0.5, use_graph=True)
+        out[dtype] = time_engine_ab(st, spec, x1, xo, 5 if dtype == "f64" else 10)
+        st.close()
+    out["launch_shapes"] = "built-in"
+    out["kernel"] = "k_step (cooperative launch; per-trial release flags between the two sweeps)"
+    return out
+
+
 def measure_amp_batch(args, rank, world, dist):
     """Batched AMP workload: `amp_trials` independent Gin(m_i, n_i) trials in one state,
     n_i ~ U{1000..100000}, m_i = n_i / 2, entries N(0, 1/m_i), beta ~ Bernoulli(0.1) N(0, 1),
@@ -367,13 +419,14 @@ def measure_amp_batch(args, rank, world, dist):
     torch.cuda.synchronize()
     secs = max_over_ranks(e0.elapsed_time(e1) / 1e3 / steps, dist)
     mse = float(((out.double() - bt.double()) ** 2).sum().item() / float(ns.sum()))
+    ab = time_engine_ab(b, spec, bt, out, steps)   # the same trajectory with the step kernel
     sum_n, sum_mn = float(ns.sum()), float((ns + ms).sum())
     credited = sum_mn * 4.0 * T * (T + 1) / 2.0
     b.close()
     return {"metric": "trials*n*T^2/s", "value": job_throughput(sum_n * T * T, world, secs),
             "ms_per_trajectory": secs * 1e3, "trials": count * world, "sum_n": sum_n * world, "T": T,
             "dtype": "f32 (FP64 coefficients)", "graph": "one CUDA graph per trajectory",
-            "credited_GBps": credited / secs / 1e9, "mse": mse,
+            "credited_GBps": credited / secs / 1e9, "mse": mse, "engine_ab": ab,
             "launch_shapes": "built-in" if args.no_autotune else "hd_autotune (untimed, before the runs)",
             "config": "Gin(m_i, n_i), n_i ~ U{1000..100000}, m_i = n_i/2, AMP soft threshold 1.1 sigma_t"}
 
@@ -1327,28 +1380,29 @@ def roofline_of(prof, dtype, n, T, peaks):
     ms, nl, by = prof[dom]
     per_kernel = {k: {"ms_total": v[0], "launches": v[1], "GBps": (v[2] / (v[0] / 1e3) / 1e9) if v[0] else None}
                   for k, v in prof.items()}
-    cols = haar_columns(T)
-    trajectories = (nl / T) if nl else 0.0   # every trajectory launches T update and T output sweeps
+    # every step of a trajectory launches either the step kernel or an update sweep
+    trajectories = (prof["update"][1] + prof.get("step", (0, 0, 0))[1]) / T
+    cols = haar_columns(T, round(prof.get("step", (0, 0, 0))[1] / trajectories) if trajectories else 0)
     if dtype == "f64":
         flops = FLOPS_PER_ELEMENT[dom] * n * cols[dom] * trajectories
         achieved = (flops / nl) / ((ms / nl) / 1e3) / 1e12 if nl else 0.0
         for k, v in prof.items():
             if v[0] and v[1]:
-                per_kernel[k]["TFLOPs"] = FLOPS_PER_ELEMENT[k] * n * cols[k] * (v[1] / T) / (v[0] / 1e3) / 1e12
+                per_kernel[k]["TFLOPs"] = FLOPS_PER_ELEMENT[k] * n * cols[k] * trajectories / (v[0] / 1e3) / 1e12
         r = {"bound": "alu", "kernel": KERNEL_NAME[dom], "achieved": achieved, "peak": peaks["fp64_tflops"],
              "unit": "TFLOP/s", "frac": achieved / peaks["fp64_tflops"],
              "peak_source": "measured now on this GPU: hd_fp64_fma_rate (8 independent FMA chains per "
                             "thread, 8 CTAs of 256 threads per SM, best of 5 event-timed launches)",
              "work": "%g FP64 flops per stack element (2 per FMA) x n x the columns of each launch "
                      "(t - 1 before step t)" % FLOPS_PER_ELEMENT[dom],
-             "traffic": ((by / nl) * TRAFFIC_RATIO["f64"] if (nl and dom == "update" and TRAFFIC_RATIO["f64"])
+             "traffic": ((by / nl) * TRAFFIC_RATIO["f64"] if (nl and dom == TRAFFIC_KERNEL and TRAFFIC_RATIO["f64"])
                          else None),
              "hbm_GBps": (by / nl) / ((ms / nl) / 1e3) / 1e9 if nl else None}
     else:
         achieved = (by / nl) / ((ms / nl) / 1e3) / 1e9 if nl else 0.0
         r = {"bound": "hbm", "kernel": KERNEL_NAME[dom], "achieved": achieved, "peak": peaks["hbm_gbs"],
              "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "peak_source": peaks["hbm_source"],
-             "traffic": ((by / nl) * TRAFFIC_RATIO["f32"] if (nl and dom == "update" and TRAFFIC_RATIO["f32"])
+             "traffic": ((by / nl) * TRAFFIC_RATIO["f32"] if (nl and dom == TRAFFIC_KERNEL and TRAFFIC_RATIO["f32"])
                          else None)}
     if r["traffic"] is not None:
         r["traffic_source"] = TRAFFIC_SOURCE
@@ -1434,6 +1488,9 @@ def run_ours(args):
     c1 = None
     if not args.no_c1:
         c1 = measure_c1(args)
+    stepk = None
+    if not args.no_side:
+        stepk = measure_step_kernel(args, rank)
     amp = None
     if not args.no_amp:
         amp = measure_amp_batch(args, rank, world, dist)
@@ -1543,7 +1600,7 @@ def run_ours(args):
                 "step_credited_GBps": credited / per_step / 1e9,
                 "accuracy": accuracy,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk, other: side, "c1": c1, "batched_amp": amp, "adjoint": adj, "ista": ista,
+                "clocks": clk, other: side, "c1": c1, "step_kernel": stepk, "batched_amp": amp, "adjoint": adj, "ista": ista,
                 "paper_ista": paper_ista, "spectral": spectral, "complex": cplx, "fig1a": fig1a, "large": large}
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -83,16 +83,28 @@ HD_API int hd_create(int ensemble, int64_t m, int64_t n, int32_t T_max, uint64_t
 HD_API int hd_create_batched(int ensemble, int32_t count, const int64_t* m, const int64_t* n,
                              int32_t T_max, uint64_t seed, int dtype, hd_state** out);
 
-/* Engine switches of a state (both off by default), for measurement and for checking one
+/* Engine switches of a state (all off by default), for measurement and for checking one
  * code path against another; results differ only in the order of floating-point sums.
  *   HD_ENGINE_NO_FUSE  hd_run keeps the three separate sweeps of every step instead of
  *                      folding f_t and the next step's dot sweep into the output sweep
  *   HD_ENGINE_NO_PDL   launch the sweeps without programmatic dependent launch (no early
  *                      start of a sweep's prologue while its predecessor drains)
+ *   HD_ENGINE_STEP_KERNEL  run the update sweep and the fused output sweep of a step of hd_run
+ *                      as one launch, the step kernel, instead of two.  The step kernel is a
+ *                      cooperative launch over all trials of the batch: its CTAs take the
+ *                      update sweep's CTAs, then the output sweep's, from work queues, and a
+ *                      trial's output CTAs start as soon as that trial's update finaliser has
+ *                      released them (a bounded wait: on expiry the step fails with
+ *                      HD_ERR_TIMEOUT at hd_sync).  Used for every fused step except the last
+ *                      of a trajectory, when its launch shape fits at least one CTA per SM.
+ *                      Off by default: on GB300 the merged kernel executes about 11 % more
+ *                      instructions per sub-tile than the two sweeps apart (register allocation
+ *                      over both sweep bodies), which costs more than the launch it saves.
  * Take effect from the next step; a cached hd_run graph is recaptured.  HD_ERR_ARG for an
  * unknown bit. */
 #define HD_ENGINE_NO_FUSE 1
 #define HD_ENGINE_NO_PDL 2
+#define HD_ENGINE_STEP_KERNEL 4
 HD_API int hd_set_engine(hd_state* st, int flags);
 
 /* Per-trial entry scales of a Gin batch (count values, each finite and > 0): trial i's draws
@@ -212,10 +224,12 @@ HD_API int hd_run(hd_state* st, const hd_run_spec* spec, const void* x1, void* x
 HD_API int hd_sync(hd_state* st);
 
 /* Check of the failure path of the kernels' bounded waits (no fault involved): launches one
- * CTA that waits on a shared-memory barrier nothing will complete, gives up after `polls`
- * polls (1..2^24), sets the state's device error word and exits.  The next hd_sync then
- * returns HD_ERR_TIMEOUT and poisons the state, as after a real expired wait; hd_reset clears
- * it.  Errors: HD_ERR_ARG (polls out of range), the state's sticky status, HD_ERR_CUDA. */
+ * CTA that waits on a shared-memory barrier nothing will complete, then on a step-kernel flag
+ * nothing will release; each wait gives up after `polls` polls (1..2^24; the flag wait sleeps
+ * about 64 ns between polls) and sets its bit of the state's device error word (bit 0, bit 1).
+ * The next hd_sync then returns HD_ERR_TIMEOUT and poisons the state, as after a real
+ * expired wait; hd_reset clears it.  Errors: HD_ERR_ARG (polls out of range), the state's
+ * sticky status, HD_ERR_CUDA. */
 HD_API int hd_check_bounded_wait(hd_state* st, uint32_t polls);
 
 /* Forget all steps (t = r = l = 0) and re-key the generator with seed; keeps the
@@ -236,15 +250,16 @@ HD_API int hd_get_device_bytes(const hd_state* st, int64_t* bytes);
  * (empty if none); valid until the next failing call in that thread. */
 HD_API const char* hd_last_error(void);
 
-/* Profiling of the three sweeps of every step (kind 0 = dots K1, 1 = update K2, 2 = output
- * K3): when enabled, CUDA events are recorded on the state's stream around each sweep
- * launch (also inside a graph captured by hd_run, which then re-records the same events on
+/* Profiling of the sweeps of every step (kind 0 = dots K1, 1 = update K2, 2 = output K3,
+ * 3 = the step kernel, K2 and the fused K3 in one launch): when enabled, CUDA events are
+ * recorded on the state's stream around each sweep launch (also inside a graph captured by
+ * hd_run, which then re-records the same events on
  * every replay).  hd_profile_read synchronises the stream, adds the elapsed times of the
  * recorded launches to running totals and returns, per kind, the total milliseconds, the
  * number of launches and their algorithmic bytes (each stack read once plus the vectors
  * the sweep reads and writes); clear != 0 zeroes the totals after reading. */
 HD_API int hd_profile_enable(hd_state* st, int on);
-HD_API int hd_profile_read(hd_state* st, double* ms3, int64_t* launches3, double* bytes3,
+HD_API int hd_profile_read(hd_state* st, double* ms4, int64_t* launches4, double* bytes4,
                            int clear);
 
 /* Launch shapes of the sweeps (the paper fixes none: these are the engine's own choices for

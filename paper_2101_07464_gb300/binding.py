@@ -31,7 +31,7 @@ class hd_run_spec(ctypes.Structure):
                 ("aux", ctypes.c_void_p), ("y_record", ctypes.c_void_p), ("x_record", ctypes.c_void_p),
                 ("x_given", ctypes.c_void_p), ("ld_rows", ctypes.c_int64), ("b", ctypes.c_double)]
 
-HD_ENGINE_NO_FUSE, HD_ENGINE_NO_PDL = 1, 2
+HD_ENGINE_NO_FUSE, HD_ENGINE_NO_PDL, HD_ENGINE_STEP_KERNEL = 1, 2, 4
 
 _c = ctypes
 _P = _c.c_void_p
@@ -291,10 +291,11 @@ def hd_fp64_fma_rate(iters=1 << 16, reps=5, stream=None):
     return out.value
 
 
-def hd_set_engine(state, no_fuse=False, no_pdl=False):
-    """Engine switches (hd_set_engine): keep hd_run's separate sweeps, or launch without
-    programmatic dependent launch."""
-    flags = (HD_ENGINE_NO_FUSE if no_fuse else 0) | (HD_ENGINE_NO_PDL if no_pdl else 0)
+def hd_set_engine(state, no_fuse=False, no_pdl=False, step_kernel=False):
+    """Engine switches (hd_set_engine): keep hd_run's separate sweeps, launch without
+    programmatic dependent launch, or run each fused step as one launch (the step kernel)."""
+    flags = ((HD_ENGINE_NO_FUSE if no_fuse else 0) | (HD_ENGINE_NO_PDL if no_pdl else 0)
+             | (HD_ENGINE_STEP_KERNEL if step_kernel else 0))
     _check(lib().hd_set_engine(state, flags), "hd_set_engine")
 
 
@@ -360,12 +361,13 @@ def hd_profile_enable(state, on=True):
 
 
 def hd_profile_read(state, clear=False):
-    """Returns {kind: (ms, launches, bytes)} for kinds 'dots', 'update', 'output'."""
-    ms = (ctypes.c_double * 3)()
-    nl = (ctypes.c_int64 * 3)()
-    by = (ctypes.c_double * 3)()
+    """Returns {kind: (ms, launches, bytes)} for kinds 'dots', 'update', 'output' and 'step'
+    (the step kernel: update and fused output sweep in one launch)."""
+    ms = (ctypes.c_double * 4)()
+    nl = (ctypes.c_int64 * 4)()
+    by = (ctypes.c_double * 4)()
     _check(lib().hd_profile_read(state, ms, nl, by, 1 if clear else 0), "hd_profile_read")
-    return {k: (ms[i], nl[i], by[i]) for i, k in enumerate(("dots", "update", "output"))}
+    return {k: (ms[i], nl[i], by[i]) for i, k in enumerate(("dots", "update", "output", "step"))}
 
 
 def hd_get_launches(state):

@@ -28,11 +28,13 @@ thread_local char g_last_error[256] = "";
 // columns, NR right-hand sides): the (warps per CTA, pipeline stages per warp) pair that puts
 // the most bytes in flight per SM (capped at 128 KB; then more resident warps, then fewer
 // stages), unless the state carries a measured shape for this kernel and column range
-// (hd_autotune, hd_set_tuning).  The CTA count comes from the space's CTA map.
+// (hd_autotune, hd_set_tuning).  The CTA count comes from the space's CTA map.  fixW > 0
+// restricts the choice to that many warps per CTA (the step kernel runs both of its sweeps
+// with the update sweep's warps).
 template <typename T>
-SweepCfg make_sweep(const hd_state* st, int which, int ncolT, int NRV, int ncolC, int NR) {
+SweepCfg make_sweep(const hd_state* st, int which, int ncolT, int NRV, int ncolC, int NR, int fixW = 0) {
   SweepCfg c;
-  c.W = 8;
+  c.W = (fixW > 0) ? fixW : 8;
   c.nbuf = 1;
   const int stat = st->static_smem[which] + 1024;
   const int blk = st->smem_blk_max - stat;
@@ -46,6 +48,7 @@ SweepCfg make_sweep(const hd_state* st, int which, int ncolT, int NRV, int ncolC
   };
   double best = -1.0;
   for (int W = 8; W >= 1; W /= 2) {
+    if (fixW > 0 && W != fixW) continue;
     for (int nb = 1; nb <= 8; nb *= 2) {
       const int ctas = ctas_of(W, nb);
       if (ctas < 1) continue;
@@ -66,7 +69,7 @@ SweepCfg make_sweep(const hd_state* st, int which, int ncolT, int NRV, int ncolC
     tW = st->tuneW[which][bucket];
     tnb = st->tuneNb[which][bucket];
   }
-  if (tW > 0 && tnb > 0 && ctas_of(tW, tnb) >= 1) {
+  if (tW > 0 && tnb > 0 && (fixW == 0 || tW == fixW) && ctas_of(tW, tnb) >= 1) {
     c.W = tW;
     c.nbuf = tnb;
   }
@@ -98,6 +101,7 @@ BatchStep<T> make_batch(const hd_state* st, int d, int kD, int kN, const void* x
   else
     p.c3 = make_sweep<T>(st, 3, kN + kD, 1, kN, 1);
   p.pdl = st->pdl;
+  p.fin_out = st->count > 1 ? 1 : 0;
   // trial 0's stacks give the host-side launch code its dimensions (probe)
   p.D = st->hdesc[0].st[d];
   p.N = st->hdesc[0].st[1 - d];
@@ -106,6 +110,41 @@ BatchStep<T> make_batch(const hd_state* st, int d, int kD, int kN, const void* x
   b.map[0] = st->map[0];
   b.map[1] = st->map[1];
   return b;
+}
+
+// CTAs of the step kernel resident per SM for a block size and dynamic shared memory, cached
+// per state (the occupancy query is a host call; trajectories ask once per step).
+template <typename T>
+int step_occupancy(hd_state* st, bool haar, int threads, size_t smem) {
+  const int64_t key = ((int64_t)(haar ? 1 : 0) << 48) | ((int64_t)threads << 32) | (int64_t)smem;
+  for (const auto& kv : st->step_occ)
+    if (kv.first == key) return kv.second;
+  const int occ = step_kernel_occupancy<T>(haar, threads, smem);
+  st->step_occ.emplace_back(key, occ);
+  return occ;
+}
+
+// The step kernel's shape: the update sweep's warps for both sweeps (the output sweep's stages
+// re-chosen for them), the larger of the two shared-memory carves, and as many CTAs as are
+// resident at once, at most the larger of the two CTA maps (the CTAs walk the maps' virtual
+// CTAs).  Leaves step_ctas = 0, i.e. two launches, when no CTA of that shape fits an SM.
+template <typename T>
+void plan_step_kernel(hd_state* st, BatchStep<T>& b) {
+  StepPlan<T>& p = b.base;
+  const int kD = p.kD, kN = p.kN;
+  const bool haar = st->ens == HD_HAAR;
+  const int W = p.c2.W;
+  if (p.c3.W != W)
+    p.c3 = haar ? make_sweep<T>(st, 4, kN, 2, kN, 1, W) : make_sweep<T>(st, 5, kN + kD, 3, kN + kD, 1, W);
+  const size_t s2 = sweep_smem_bytes<T>(W, p.c2.nbuf, kD, 1, kD, 2);
+  const size_t s3 = haar ? sweep_smem_bytes<T>(W, p.c3.nbuf, kN, 2, kN, 1)
+                         : sweep_smem_bytes<T>(W, p.c3.nbuf, kN + kD, 3, kN + kD, 1);
+  const size_t smem = std::max(s2, s3);
+  const int occ = step_occupancy<T>(st, haar, 32 * W, smem);
+  if (occ < 1) return;
+  const int want = std::max(b.map[b.d].ctas, b.map[1 - b.d].ctas);
+  p.step_ctas = std::min(want, occ * st->nsm);
+  p.step_smem = (int)smem;
 }
 
 // Row t (0-based) of one of hd_run's optional trajectory buffers (null when not given).
@@ -161,6 +200,7 @@ int do_step(hd_state* st, const void* x, int transpose, void* y, const FuseSpec*
   }
   BatchStep<T> b = make_batch<T>(st, d, kD, kN, x, y);
   b.base.key_next = key_for(st, st->t + 2);
+  bool step_fallback = false;   // a fused step that the step kernel could not take
   if (fs) {
     b.base.skip_dots = fs->skip_dots;
     if (fs->fuse) {
@@ -184,6 +224,10 @@ int do_step(hd_state* st, const void* x, int transpose, void* y, const FuseSpec*
         b.base.c3 = make_sweep<T>(st, 4, kN, 2, kN, 1);
       else
         b.base.c3 = make_sweep<T>(st, 5, kN + kD, 3, kN + kD, 1);
+      if (st->step_kernel) {
+        plan_step_kernel<T>(st, b);
+        step_fallback = b.base.step_ctas == 0;
+      }
     }
   }
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -202,7 +246,7 @@ int do_step(hd_state* st, const void* x, int transpose, void* y, const FuseSpec*
     const int rc = adj_record_after(st, kD, kN);
     if (rc) return rc;
   }
-  st->launches += launched[0] + launched[1] + launched[2];
+  st->launches += launched[0] + (launched[1] ? 1 : 0) + launched[2];
   if (slot0 >= 0) {
     // algorithmic bytes: each sweep reads its stack once plus the vectors it reads/writes
     const double es = (double)sizeof(T);
@@ -210,13 +254,20 @@ int do_step(hd_state* st, const void* x, int transpose, void* y, const FuseSpec*
     const double bd = (st->ens == HD_GINIBRE) ? (double)kN * nD : 0.0;
     const double bn = (st->ens == HD_GINIBRE) ? (double)(kD + 1) * nN : 0.0;
     const bool fz = fs && fs->fuse;
-    const double bb[3] = {es * (nD * kD + bd + nD), es * (nD * kD + 3.0 * nD),
-                          es * (nN * kN + bn + (fz ? 5.0 : 4.0) * nN)};
+    double bb[3] = {es * (nD * kD + bd + nD), es * (nD * kD + 3.0 * nD),
+                    es * (nN * kN + bn + (fz ? 5.0 : 4.0) * nN)};
     const SweepCfg* cs[3] = {&b.base.c1, &b.base.c2, &b.base.c3};
+    int kind[3] = {launched[0] ? 0 : -1, launched[1] ? 1 : -1, launched[2] ? 2 : -1};
+    if (launched[1] == 2) {   // the step kernel: K2 and K3 in the K2 slot, profiled as kind 3
+      kind[1] = 3;
+      bb[1] += bb[2];
+    }
     for (int q = 0; q < 3; q++) {
-      st->prof_kind[slot0 + q] = launched[q] ? q : -1;
+      st->prof_kind[slot0 + q] = kind[q];
       st->prof_bytes[slot0 + q] = bb[q];
       st->prof_tag[slot0 + q] = cs[q]->tag | (cs[q]->W << 8) | (cs[q]->nbuf << 12);
+      // a forced shape that left the step kernel is no shape for it: the autotuner drops it
+      if (step_fallback && q >= 1) st->prof_tag[slot0 + q] &= ~(0xf << 8);
     }
     st->prof_used += 3;
   }
@@ -594,7 +645,7 @@ int create_common(int ensemble, int count, const int64_t* m, const int64_t* n, i
   const int64_t per_trial = vs /*z*/ + 4 * vs /*w phead wout wout2*/ + 4 * vs /*scr*/ + kNumScal +
                             (int64_t)st->maxncta * vs /*part*/ + gmax * vs /*gpart*/;
   double* wsb = (double*)dalloc(st, (size_t)count * per_trial * 8);
-  st->cnt_bytes = (size_t)count * 3 * (kMaxGroups + 1) * sizeof(unsigned int);
+  st->cnt_bytes = (size_t)count * kCntSets * (kMaxGroups + 1) * sizeof(unsigned int);
   st->cnt = (unsigned int*)dalloc(st, st->cnt_bytes);
   st->err = (unsigned int*)dalloc(st, 16);
   if (!wsb || !st->cnt || !st->err) return fail(HD_ERR_OOM);
@@ -628,7 +679,7 @@ int create_common(int ensemble, int count, const int64_t* m, const int64_t* n, i
     ws.scal = w; w += kNumScal;
     ws.part = w; w += (int64_t)st->maxncta * vs;
     ws.gpart = w; w += gmax * vs;
-    ws.cnt = st->cnt + (size_t)i * 3 * (kMaxGroups + 1);
+    ws.cnt = st->cnt + (size_t)i * kCntSets * (kMaxGroups + 1);
     ws.err = st->err;
     td.trial = (uint32_t)i;
     td.sigma = 1.0;
@@ -784,9 +835,10 @@ HD_API int hd_set_options(hd_state* st, double sigma, uint32_t trial, void* stre
 
 HD_API int hd_set_engine(hd_state* st, int flags) {
   if (!st) return HD_ERR_ARG;
-  if (flags & ~(HD_ENGINE_NO_FUSE | HD_ENGINE_NO_PDL)) return HD_ERR_ARG;
+  if (flags & ~(HD_ENGINE_NO_FUSE | HD_ENGINE_NO_PDL | HD_ENGINE_STEP_KERNEL)) return HD_ERR_ARG;
   st->fuse = (flags & HD_ENGINE_NO_FUSE) ? 0 : 1;
   st->pdl = (flags & HD_ENGINE_NO_PDL) ? 0 : 1;
+  st->step_kernel = (flags & HD_ENGINE_STEP_KERNEL) ? 1 : 0;
   st->tune_gen += 1;   // a cached trajectory graph was captured with the old launches
   return HD_OK;
 }
@@ -992,7 +1044,7 @@ HD_API int hd_profile_enable(hd_state* st, int on) {
   return HD_OK;
 }
 
-HD_API int hd_profile_read(hd_state* st, double* ms3, int64_t* launches3, double* bytes3, int clear) {
+HD_API int hd_profile_read(hd_state* st, double* ms4, int64_t* launches4, double* bytes4, int clear) {
   if (!st) return HD_ERR_ARG;
   if (st->prof_used > 0) {
     if (cudaStreamSynchronize(st->stream) != cudaSuccess) return cuda_fail(st, cudaGetLastError());
@@ -1011,13 +1063,13 @@ HD_API int hd_profile_read(hd_state* st, double* ms3, int64_t* launches3, double
     // graph replays re-record the same events: keep the slots, read them again next time
     if (!st->gexec || !st->prof_on) st->prof_used = 0;
   }
-  for (int q = 0; q < 3; q++) {
-    if (ms3) ms3[q] = st->prof_ms[q];
-    if (launches3) launches3[q] = st->prof_n[q];
-    if (bytes3) bytes3[q] = st->prof_b[q];
+  for (int q = 0; q < 4; q++) {
+    if (ms4) ms4[q] = st->prof_ms[q];
+    if (launches4) launches4[q] = st->prof_n[q];
+    if (bytes4) bytes4[q] = st->prof_b[q];
   }
   if (clear)
-    for (int q = 0; q < 3; q++) st->prof_ms[q] = st->prof_n[q] = 0, st->prof_b[q] = 0.0;
+    for (int q = 0; q < 4; q++) st->prof_ms[q] = st->prof_n[q] = 0, st->prof_b[q] = 0.0;
   return HD_OK;
 }
 
@@ -1048,7 +1100,8 @@ HD_API int hd_sync(hd_state* st) {
     return cuda_fail(st, e);
   }
   if (err) {
-    snprintf(g_last_error, sizeof(g_last_error), "device error word 0x%x (bounded wait expired)", err);
+    snprintf(g_last_error, sizeof(g_last_error), "device error word 0x%x (bounded wait expired: bit 0 a "
+             "staging barrier, bit 1 a step kernel flag)", err);
     st->poisoned = HD_ERR_TIMEOUT;
     return HD_ERR_TIMEOUT;
   }

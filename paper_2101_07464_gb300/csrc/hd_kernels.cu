@@ -112,13 +112,14 @@ __device__ bool reduce_partials(const Ws& ws, int set, int P, int local, int nct
 struct CtaCtx {
   int trial, local, ncta, spc;
 };
+// vb: the CTA's index in the space's CTA map (blockIdx.x, or a virtual CTA of the step kernel).
 template <typename T>
-__device__ __forceinline__ StepPlan<T> make_plan(const BatchStep<T>& b, int space, CtaCtx& c) {
+__device__ __forceinline__ StepPlan<T> make_plan(const BatchStep<T>& b, int space, int vb, CtaCtx& c) {
   const CtaMap& m = b.map[space];
-  c.trial = m.cta_trial[blockIdx.x];
+  c.trial = m.cta_trial[vb];
   const int c0 = m.cta0[c.trial];
   c.ncta = m.cta0[c.trial + 1] - c0;
-  c.local = (int)blockIdx.x - c0;
+  c.local = vb - c0;
   c.spc = m.spc[c.trial];
   const TrialDesc& td = b.desc[c.trial];
   const int d = b.d;
@@ -217,6 +218,12 @@ __device__ __forceinline__ uint32_t smem_u32(const void* ptr) {
 __device__ __forceinline__ void mbar_init(uint64_t* bar) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar)) : "memory");
   asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+// A finalisation can run several times in one CTA of the step kernel (one trial after
+// another), so it invalidates its barrier when done: an mbarrier is initialised only when
+// the location holds no valid barrier object.
+__device__ __forceinline__ void mbar_inval(uint64_t* bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];\n" ::"r"(smem_u32(bar)) : "memory");
 }
 __device__ __forceinline__ void mbar_arrive_tx(uint64_t* bar, unsigned bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
@@ -425,6 +432,8 @@ __device__ void fin_dots(const double* S, int Sld, int na, const double* zs, dou
   } else {
     col_dots(S, (int64_t)Sld, na, zs, [](int j, int& lo, int& hi) { lo = 0; hi = j; }, w);
   }
+  __syncthreads();
+  if (threadIdx.x == 0) mbar_inval(&dbar);
 }
 
 // Finalisation after K2 (one CTA).  r[0..k) = dots of the next draw with the old columns of
@@ -589,6 +598,23 @@ __device__ void fin_update(const StepPlan<T>& p, const double* r, double* scr, i
                   deltaN);
     }
   }
+  __syncthreads();
+  if (tid == 0) mbar_inval(&fbar);
+}
+
+// The finalisations out of line.  In a batch every trial has its own finaliser, so most CTAs
+// of a launch run one (in a single-trial launch only the last CTA does, on the critical
+// path); kept out of the sweep kernels' bodies, their code no longer shares the register
+// allocation of the streaming loops, which then run faster, while each call pays for copying
+// its arguments.  The batched sweeps call these (FIN_OUT), single-trial launches the inlined
+// forms.
+template <typename T>
+__device__ __noinline__ void fin_update_out(const StepPlan<T>& p, const double* r, double* scr, int cap) {
+  fin_update<T>(p, r, scr, cap);
+}
+__device__ __noinline__ void fin_dots_out(const double* S, int Sld, int na, const double* zs, double* w, double* scr,
+                                          int64_t capb, unsigned* err) {
+  fin_dots(S, Sld, na, zs, w, scr, capb, err);
 }
 
 // ------------------------------------------------------------------------------------
@@ -1030,22 +1056,89 @@ __device__ __forceinline__ void pdl_trigger() {
   asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
 }
 
+// Hand-over between the two phases of the step kernel (k_step), per trial.  The finaliser of
+// the trial's update sweep publishes its results with a release store of 1 into the trial's
+// step flag; every output-sweep CTA of that trial polls it with acquire loads, at most `limit`
+// polls with a short sleep between them (about a second in all).  On expiry the error word
+// gets bit 1 and false is returned: the CTA leaves the kernel and the state is poisoned until
+// hd_reset, which clears the flags with the election counters.  The output sweep's own
+// finaliser clears the flag (every CTA that waits on it has passed by then).
+constexpr unsigned kFlagSpins = 1u << 21;
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;\n" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned* step_flag(const Ws& ws) { return ws.cnt + kStepFlagSlot; }
+__device__ bool flag_wait(const unsigned* flag, unsigned* err, unsigned limit) {
+  __shared__ int s_go;
+  if (threadIdx.x == 0) {
+    unsigned spins = 0;
+    int ok = 1;
+    while (ld_acquire_u32(flag) == 0u) {
+      if (++spins > limit) {
+        ok = 0;
+        if (err) atomicOr(err, 2u);
+        break;
+      }
+      __nanosleep(64);
+    }
+    s_go = ok;
+  }
+  __syncthreads();
+  const bool ok = s_go != 0;
+  asm volatile("fence.acq_rel.gpu;\n" ::: "memory");
+  __syncthreads();   // s_go is reused by the next wait
+  return ok;
+}
+// Called by every thread of the finalising CTA once its results are written.
+__device__ __forceinline__ void flag_release(const Ws& ws) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    st_release_u32(step_flag(ws), 1u);
+  }
+}
+
+// Gates of the sweeps (wt_pipeline): a stand-alone kernel waits for its predecessor under
+// programmatic dependent launch; the step kernel's update phase needs no wait (the launch
+// starts after the preceding one has completed) and its output phase waits for the trial's
+// flag.
+enum GateKind { kGatePdl = 0, kGateNone = 1, kGateFlag = 2 };
+template <int G>
+__device__ __forceinline__ bool gate_pass(const Ws& ws) {
+  if (G == kGatePdl) {
+    pdl_wait();
+    pdl_trigger();
+    return true;
+  }
+  if (G == kGateNone) return true;
+  return flag_wait(step_flag(ws), ws.err, kFlagSpins);
+}
+
 // The walk of one warp as an nb-stage cp.async pipeline.  pre(it, stage) issues the copies of
-// local sub-tile it that do not depend on the preceding kernel (stack columns written by
-// earlier kernels), post(it, stage) the rest; the prologue issues pre for the first nb - 1
-// stages, then waits for the preceding kernel (pdl_wait), then issues their post part.
-// setup() runs in every thread of the CTA right after the wait (then one CTA barrier): it
-// stages what the preceding kernel produced (coefficients).  body(it, stage) runs once the
-// stage is complete.
-template <typename Pre, typename Setup, typename Post, typename Body>
-__device__ __forceinline__ void wt_pipeline(int count, int nb, Pre&& pre, Setup&& setup, Post&& post,
+// local sub-tile it that do not depend on the preceding phase (stack columns written by
+// earlier launches), post(it, stage) the rest.  The prologue issues pre for the first nb - 1
+// stages, then passes the gate (the wait for the preceding phase: the preceding kernel under
+// programmatic dependent launch, or the trial's flag inside the step kernel), then issues their
+// post part.  setup() runs in every thread of the CTA right after the gate (then one CTA
+// barrier): it stages what the preceding phase produced (coefficients).  body(it, stage) runs
+// once the stage is complete.  When the gate gives up (false), the copies in flight are
+// drained and false is returned without running the walk.
+template <typename Gate, typename Pre, typename Setup, typename Post, typename Body>
+__device__ __forceinline__ bool wt_pipeline(int count, int nb, Gate&& gate, Pre&& pre, Setup&& setup, Post&& post,
                                             Body&& body) {
   for (int q = 0; q < nb - 1; q++) {
     if (q < count) pre(q, q);
     cp_async_commit();
   }
-  pdl_wait();
-  pdl_trigger();
+  if (!gate()) {
+    cp_async_wait<0>();
+    return false;
+  }
   setup();
   __syncthreads();
   for (int q = 0; q < nb - 1; q++)
@@ -1063,6 +1156,7 @@ __device__ __forceinline__ void wt_pipeline(int count, int nb, Pre&& pre, Setup&
     body(it, it % nb);
     __syncwarp();
   }
+  return true;
 }
 
 // ------------------------------------------------------------------------------------
@@ -1071,7 +1165,8 @@ __device__ __forceinline__ void wt_pipeline(int count, int nb, Pre&& pre, Setup&
 template <typename T>
 __global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_dots(BatchStep<T> bs) {
   CtaCtx cc;
-  const StepPlan<T> p = make_plan(bs, bs.d, cc);
+  const int vb = blockIdx.x;
+  const StepPlan<T> p = make_plan(bs, bs.d, vb, cc);
   extern __shared__ __align__(16) unsigned char dsm_raw[];
   const int na = p.kD, nb = (p.ens == 0) ? p.kN : 0, nc = na + nb;
   const SweepCfg& cfg = p.c1;
@@ -1086,7 +1181,7 @@ __global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_dots(BatchStep<T>
   const int cnt = ww.count();
   const bool xal = ((uintptr_t)p.x & 15u) == 0;   // per-trial offsets may break alignment
   wt_zero_cols<1>(sm.comb, nc);
-  wt_pipeline(cnt, cfg.nbuf,
+  wt_pipeline(cnt, cfg.nbuf, [&]() { return gate_pass<kGatePdl>(p.ws); },
       [&](int it, int b) { wt_load_cols(sm.stage(warp, b), src, nc, ww.sub(it) * 32); },
       [&]() {},
       [&](int it, int b) { wt_load_vec(sm.srow(sm.stage(warp, b), 0), p.x, ww.sub(it) * 32, dim, xal); },
@@ -1107,11 +1202,12 @@ __global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_dots(BatchStep<T>
 
 // K2: p = Delta_D (x - V_D w); writes p[k:] as the new column k of V_D; draws g_{t+1}
 // (rows > k) into the data stack's buffer; exact V_D^T p[k:] and V_D^T g_{t+1}.
-template <typename T>
-__global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_update(BatchStep<T> bs) {
+// The sweep of CTA vb of the data space's map.  G: its gate; STEP (inside k_step): the
+// finalising CTA releases the trial's step flag once its results are written.
+template <typename T, int G, bool STEP, bool FIN_OUT = false>
+__device__ __forceinline__ void update_sweep(const BatchStep<T>& bs, int vb, unsigned char* dsm_raw) {
   CtaCtx cc;
-  const StepPlan<T> p = make_plan(bs, bs.d, cc);
-  extern __shared__ __align__(16) unsigned char dsm_raw[];
+  const StepPlan<T> p = make_plan(bs, bs.d, vb, cc);
   __shared__ double red[kWarps * 4];
   const int k = p.kD;
   const SweepCfg& cfg = p.c2;
@@ -1133,7 +1229,7 @@ __global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_update(BatchStep<
   const int cnt = ww.count();
   const bool xal = ((uintptr_t)p.x & 15u) == 0;   // per-trial offsets may break alignment
   wt_zero_cols<2>(sm.comb, k);
-  wt_pipeline(cnt, cfg.nbuf,
+  wt_pipeline(cnt, cfg.nbuf, [&]() { return gate_pass<G>(p.ws); },
       [&](int it, int b) {
         T* st = sm.stage(warp, b);
         const int64_t r0 = ww.sub(it) * 32;
@@ -1179,7 +1275,14 @@ __global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_update(BatchStep<
   block_sum_to<3>(ex, red, part + k, 3);
   double* rr = p.ws.scr(3);
   if (!reduce_partials(p.ws, 1, P, cc.local, cc.ncta, rr)) return;
-  fin_update<T>(p, rr, (double*)dsm_raw, (int)(sm.bytes() / sizeof(double)));
+  if constexpr (FIN_OUT) fin_update_out<T>(p, rr, (double*)dsm_raw, (int)(sm.bytes() / sizeof(double)));
+  else fin_update<T>(p, rr, (double*)dsm_raw, (int)(sm.bytes() / sizeof(double)));
+  if (STEP) flag_release(p.ws);
+}
+template <typename T, bool FIN_OUT>
+__global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_update(BatchStep<T> bs) {
+  extern __shared__ __align__(16) unsigned char dsm_raw[];
+  update_sweep<T, kGatePdl, false, FIN_OUT>(bs, blockIdx.x, dsm_raw);
 }
 
 // Elementwise dynamics of the fused K3 (the same arithmetic as the stand-alone kernel).
@@ -1196,11 +1299,12 @@ __device__ __forceinline__ T fused_dyn(int kind, T a, T y, T xprev) {
 // FUSE: instead of storing y, applies the dynamics x_{t+1} = f(y, x_{t-1}) and adds the dots
 // of x_{t+1} with V_N and the new column, i.e. the next step's K1 (this stack is the next
 // step's data stack), finished by w = S_N^T z in the last CTA.
-template <typename T, bool FUSE>
-__global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_out_haar(BatchStep<T> bs) {
+// The sweep of CTA vb of the output space's map.  G: its gate; STEP (inside k_step, FUSE):
+// the finaliser clears the trial's step flag.
+template <typename T, bool FUSE, int G, bool STEP, bool FIN_OUT = false>
+__device__ __forceinline__ bool out_haar_sweep(const BatchStep<T>& bs, int vb, unsigned char* dsm_raw) {
   CtaCtx cc;
-  const StepPlan<T> p = make_plan(bs, 1 - bs.d, cc);
-  extern __shared__ __align__(16) unsigned char dsm_raw[];
+  const StepPlan<T> p = make_plan(bs, 1 - bs.d, vb, cc);
   __shared__ double red[kWarps * 4];
   const int k = p.kN;
   const SweepCfg& cfg = p.c3;
@@ -1226,7 +1330,7 @@ __global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_out_haar(BatchSte
   const int cnt = ww.count();
   const int64_t ld = p.N.ld;
   wt_zero_cols<1>(sm.comb, k);
-  wt_pipeline(cnt, cfg.nbuf,
+  const bool gate_ok = wt_pipeline(cnt, cfg.nbuf, [&]() { return gate_pass<G>(p.ws); },
       [&](int it, int b) {
         T* st = sm.stage(warp, b);
         const int64_t r0 = ww.sub(it) * 32;
@@ -1284,6 +1388,7 @@ __global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_out_haar(BatchSte
         }
         if (wt_flush_due<T>(it, cnt)) wt_flush_cols<T, 1>(acc, sm.comb, k);
       });
+  if (!gate_ok) return false;
   // partial sums: [0, k) V_N . r, [k] new column . r, r = g_{t+1} or (FUSE) x_{t+1}
   const int P = k + 1;
   double* part = p.ws.part + (int64_t)cc.local * P;
@@ -1291,7 +1396,8 @@ __global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_out_haar(BatchSte
   wt_store_cols<1>(sm.comb, k, part, off);
   block_sum_to<1>(ex, red, part + k, 1);
   double* rr = p.ws.scr(3);
-  if (!reduce_partials(p.ws, 2, P, cc.local, cc.ncta, rr)) return;
+  if (!reduce_partials(p.ws, 2, P, cc.local, cc.ncta, rr)) return true;
+  if (STEP && threadIdx.x == 0) *step_flag(p.ws) = 0u;   // every waiter of the trial has passed
   if (!FUSE) {
     for (int j = threadIdx.x; j <= k; j += blockDim.x) p.N.gdot[j] = rr[j];
     if (threadIdx.x == 0) p.N.gg[0] = p.D.gg[0];
@@ -1303,8 +1409,15 @@ __global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_out_haar(BatchSte
       p.ws.z[j] = rr[j];
     }
     __syncthreads();
-    fin_dots(p.N.S, p.Tm, k + 1, zs, p.ws.w, (double*)dsm_raw, (int64_t)sm.bytes(), p.ws.err);
+    if constexpr (FIN_OUT) fin_dots_out(p.N.S, p.Tm, k + 1, zs, p.ws.w, (double*)dsm_raw, (int64_t)sm.bytes(), p.ws.err);
+    else fin_dots(p.N.S, p.Tm, k + 1, zs, p.ws.w, (double*)dsm_raw, (int64_t)sm.bytes(), p.ws.err);
   }
+  return true;
+}
+template <typename T, bool FUSE, bool FIN_OUT = false>
+__global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_out_haar(BatchStep<T> bs) {
+  extern __shared__ __align__(16) unsigned char dsm_raw[];
+  out_haar_sweep<T, FUSE, kGatePdl, false, FIN_OUT>(bs, blockIdx.x, dsm_raw);
 }
 
 // K3 (Ginibre): u = Delta_N g - V_N w_2 (= L_1..L_l Z_{1:l} g), y = alpha u + Delta_N h
@@ -1313,11 +1426,11 @@ __global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_out_haar(BatchSte
 // FUSE: applies the dynamics instead of storing y and adds the next step's K1: the dots of
 // x_{t+1} with V_N (the next data stack) and with B_n including u (the next step's data-space
 // basis), then w = S_N^T z in the last CTA.
-template <typename T, bool FUSE>
-__global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_out_gin(BatchStep<T> bs) {
+// The sweep of CTA vb of the output space's map (G, STEP as for out_haar_sweep).
+template <typename T, bool FUSE, int G, bool STEP, bool FIN_OUT = false>
+__device__ __forceinline__ bool out_gin_sweep(const BatchStep<T>& bs, int vb, unsigned char* dsm_raw) {
   CtaCtx cc;
-  const StepPlan<T> p = make_plan(bs, 1 - bs.d, cc);
-  extern __shared__ __align__(16) unsigned char dsm_raw[];
+  const StepPlan<T> p = make_plan(bs, 1 - bs.d, vb, cc);
   __shared__ double red[kWarps * 4];
   const int kN = p.kN, kD = p.kD, nc = kN + kD;
   const SweepCfg& cfg = p.c3;
@@ -1347,7 +1460,7 @@ __global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_out_gin(BatchStep
   const int cnt = ww.count();
   const int64_t ld = p.N.ld;
   wt_zero_cols<1>(sm.comb, ncc);
-  wt_pipeline(cnt, cfg.nbuf,
+  const bool gate_ok = wt_pipeline(cnt, cfg.nbuf, [&]() { return gate_pass<G>(p.ws); },
       [&](int it, int b) {
         T* st = sm.stage(warp, b);
         const int64_t r0 = ww.sub(it) * 32;
@@ -1433,7 +1546,8 @@ __global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_out_gin(BatchStep
         __syncwarp();
         if (wt_flush_due<T>(it, cnt)) wt_flush_cols<T, 1>(acc, sm.comb, ncc);
       });
-  if (!FUSE && kN == 0) return;   // no dots to form
+  if (!gate_ok) return false;
+  if (!FUSE && kN == 0) return true;   // no dots to form
   // partial sums: [0, ncc) columns . r (r = g_{t+1}, or (FUSE) x_{t+1}), (FUSE) [nc] u . x_{t+1}
   const int P = FUSE ? nc + 1 + (amp ? 1 : 0) : kN;
   double* part = p.ws.part + (int64_t)cc.local * P;
@@ -1441,7 +1555,8 @@ __global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_out_gin(BatchStep
   wt_store_cols<1>(sm.comb, ncc, part, off);
   if (FUSE) block_sum_to<2>(ex, red, part + nc, amp ? 2 : 1);
   double* rr = p.ws.scr(3);
-  if (!reduce_partials(p.ws, 2, P, cc.local, cc.ncta, rr)) return;
+  if (!reduce_partials(p.ws, 2, P, cc.local, cc.ncta, rr)) return true;
+  if (STEP && threadIdx.x == 0) *step_flag(p.ws) = 0u;   // every waiter of the trial has passed
   if (!FUSE) {
     for (int j = threadIdx.x; j < kN; j += blockDim.x) p.N.gdot[j] = rr[j];
   } else {
@@ -1458,7 +1573,71 @@ __global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_out_gin(BatchStep
       else p.amp_zsq[cc.trial] = rr[nc + 1];
     }
     __syncthreads();
-    fin_dots(p.N.S, p.Tm, kN, zs, p.ws.w, (double*)dsm_raw, (int64_t)sm.bytes(), p.ws.err);
+    if constexpr (FIN_OUT) fin_dots_out(p.N.S, p.Tm, kN, zs, p.ws.w, (double*)dsm_raw, (int64_t)sm.bytes(), p.ws.err);
+    else fin_dots(p.N.S, p.Tm, kN, zs, p.ws.w, (double*)dsm_raw, (int64_t)sm.bytes(), p.ws.err);
+  }
+  return true;
+}
+template <typename T, bool FUSE, bool FIN_OUT = false>
+__global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_out_gin(BatchStep<T> bs) {
+  extern __shared__ __align__(16) unsigned char dsm_raw[];
+  out_gin_sweep<T, FUSE, kGatePdl, false, FIN_OUT>(bs, blockIdx.x, dsm_raw);
+}
+
+// ------------------------------------------------------------------------------------
+// The step kernel: one launch per step of a fused trajectory (K2, then the fused K3).  It
+// runs as a cooperative launch, so all its CTAs are resident at once.  Each CTA takes virtual
+// CTAs of the data space's map through the update sweep, then virtual CTAs of the output
+// space's map through the fused output sweep: first its own index, then (when a map has more
+// CTAs than the launch) the next free index from a queue, as the hardware scheduler hands out
+// the CTAs of a multi-wave launch; the fetch of the next index is issued before the current
+// one's work, so its latency is hidden.  The update phase never waits.  A trial's output CTAs
+// wait only for that trial's update finaliser (its step flag), after prefetching their first
+// stages; that finaliser is the trial's last update CTA to arrive, so every flag is released
+// once the update phase has run everywhere, and the per-trial flags let a trial's output
+// sweep start while other trials still update.  Queues are taken in trial order, so the
+// trials finalised first are the ones the output phase asks for first.  The last CTA to finish
+// clears the queues for the next launch.
+template <typename T, bool HAAR>
+__global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_step(BatchStep<T> bs) {
+  extern __shared__ __align__(16) unsigned char dsm_raw[];
+  __shared__ int s_next;
+  const int n2 = bs.map[bs.d].ctas, n3 = bs.map[1 - bs.d].ctas;
+  const int G = (int)gridDim.x;
+  unsigned* q = bs.desc[0].ws.cnt + kStepQueueSlot;   // [0]: update queue, [1]: output queue, [2]: CTAs done
+  const bool queued = n2 > G || n3 > G;
+  int v = blockIdx.x;
+  while (v < n2) {
+    int nxt = n2;
+    if (threadIdx.x == 0 && n2 > G) nxt = G + (int)atomicAdd(&q[0], 1u);
+    update_sweep<T, kGateNone, true>(bs, v, dsm_raw);
+    if (n2 <= G) break;
+    if (threadIdx.x == 0) s_next = nxt;
+    __syncthreads();   // also: the next virtual CTA reuses the shared memory
+    v = s_next;
+    __syncthreads();
+  }
+  __syncthreads();
+  bool ok = true;
+  v = blockIdx.x;
+  while (v < n3) {
+    int nxt = n3;
+    if (threadIdx.x == 0 && n3 > G) nxt = G + (int)atomicAdd(&q[1], 1u);
+    if constexpr (HAAR) ok = out_haar_sweep<T, true, kGateFlag, true>(bs, v, dsm_raw);
+    else ok = out_gin_sweep<T, true, kGateFlag, true>(bs, v, dsm_raw);
+    if (!ok || n3 <= G) break;   // (!ok: the flag wait expired, error word set)
+    if (threadIdx.x == 0) s_next = nxt;
+    __syncthreads();
+    v = s_next;
+    __syncthreads();
+  }
+  if (queued && threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&q[2], 1u) == (unsigned)G - 1u) {   // every CTA has left both queues
+      q[0] = 0u;
+      q[1] = 0u;
+      q[2] = 0u;
+    }
   }
 }
 
@@ -1516,12 +1695,30 @@ cudaError_t launch_step(const BatchStep<T>& b, cudaStream_t s, cudaEvent_t* ev, 
     rec(1);
     if (launched) launched[0] = 1;
   }
+  if (p.step_ctas > 0) {   // K2 and the fused K3 in one cooperative launch
+    rec(2);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)p.step_ctas);
+    cfg.blockDim = dim3((unsigned)(32 * p.c2.W));
+    cfg.dynamicSmemBytes = (size_t)p.step_smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = (p.ens == 1) ? cudaLaunchKernelEx(&cfg, k_step<T, true>, b) : cudaLaunchKernelEx(&cfg, k_step<T, false>, b);
+    if (e != cudaSuccess) return e;
+    rec(3);
+    if (launched) launched[1] = 2;
+    return cudaGetLastError();
+  }
   rec(2);
   // K2 prefetches x and its stack columns before waiting for the preceding kernel.  That
   // kernel is K1 or, at step 1, the first-draw kernel: both start only after everything
   // before them on the stream has completed, so x and the older columns are final.  After a
   // fused K3 (which writes x and the newest column) K2 is launched without the early start
-  e = launch_sweep<T>(k_update<T>, p.c2, b.map[dspace].ctas,
+  e = launch_sweep<T>(p.fin_out ? k_update<T, true> : k_update<T, false>, p.c2, b.map[dspace].ctas,
                       sweep_smem_bytes<T>(p.c2.W, p.c2.nbuf, p.kD, 1, p.kD, 2), s, pdl && !p.skip_dots, b);
   if (e != cudaSuccess) return e;
   rec(3);
@@ -1529,13 +1726,13 @@ cudaError_t launch_step(const BatchStep<T>& b, cudaStream_t s, cudaEvent_t* ev, 
   rec(4);
   const int ncg = p.kN + p.kD;
   if (p.ens == 1 && p.fuse)
-    e = launch_sweep<T>(k_out_haar<T, true>, p.c3, b.map[ospace].ctas,
+    e = launch_sweep<T>(p.fin_out ? k_out_haar<T, true, true> : k_out_haar<T, true>, p.c3, b.map[ospace].ctas,
                         sweep_smem_bytes<T>(p.c3.W, p.c3.nbuf, p.kN, 2, p.kN, 1), s, pdl, b);
   else if (p.ens == 1)
     e = launch_sweep<T>(k_out_haar<T, false>, p.c3, b.map[ospace].ctas,
                         sweep_smem_bytes<T>(p.c3.W, p.c3.nbuf, p.kN, 2, p.kN, 1), s, pdl, b);
   else if (p.fuse)
-    e = launch_sweep<T>(k_out_gin<T, true>, p.c3, b.map[ospace].ctas,
+    e = launch_sweep<T>(p.fin_out ? k_out_gin<T, true, true> : k_out_gin<T, true>, p.c3, b.map[ospace].ctas,
                         sweep_smem_bytes<T>(p.c3.W, p.c3.nbuf, ncg, 3, ncg, 1), s, pdl, b);
   else
     e = launch_sweep<T>(k_out_gin<T, false>, p.c3, b.map[ospace].ctas,
@@ -1558,11 +1755,16 @@ cudaError_t set_sweep_smem_limit(int bytes) {
     if (r != cudaSuccess) e = r;
   };
   one((const void*)k_dots<T>);
-  one((const void*)k_update<T>);
+  one((const void*)k_update<T, false>);
+  one((const void*)k_update<T, true>);
   one((const void*)k_out_haar<T, false>);
   one((const void*)k_out_gin<T, false>);
   one((const void*)k_out_haar<T, true>);
   one((const void*)k_out_gin<T, true>);
+  one((const void*)k_out_haar<T, true, true>);
+  one((const void*)k_out_gin<T, true, true>);
+  one((const void*)k_step<T, true>);
+  one((const void*)k_step<T, false>);
   return e;
 }
 template cudaError_t set_sweep_smem_limit<float>(int);
@@ -1574,7 +1776,7 @@ int kernel_static_smem(int which) {
   cudaError_t e = cudaErrorInvalidValue;
   switch (which) {
     case 0: e = cudaFuncGetAttributes(&fa, k_dots<T>); break;
-    case 1: e = cudaFuncGetAttributes(&fa, k_update<T>); break;
+    case 1: e = cudaFuncGetAttributes(&fa, k_update<T, false>); break;
     case 2: e = cudaFuncGetAttributes(&fa, k_out_haar<T, false>); break;
     case 3: e = cudaFuncGetAttributes(&fa, k_out_gin<T, false>); break;
     case 4: e = cudaFuncGetAttributes(&fa, k_out_haar<T, true>); break;
@@ -1591,7 +1793,7 @@ int kernel_occupancy(int which, size_t dynsmem) {
   cudaError_t e = cudaSuccess;
   switch (which) {
     case 0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_dots<T>, kThreads, dynsmem); break;
-    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_update<T>, kThreads, dynsmem); break;
+    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_update<T, false>, kThreads, dynsmem); break;
     case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_out_haar<T, false>, kThreads, dynsmem); break;
     case 3: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_out_gin<T, false>, kThreads, dynsmem); break;
     case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_out_haar<T, true>, kThreads, dynsmem); break;
@@ -1601,6 +1803,20 @@ int kernel_occupancy(int which, size_t dynsmem) {
 }
 template int kernel_occupancy<float>(int, size_t);
 template int kernel_occupancy<double>(int, size_t);
+
+template <typename T>
+int step_kernel_occupancy(bool haar, int threads, size_t dynsmem) {
+  int nb = 0;
+  const cudaError_t e = haar ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step<T, true>, threads, dynsmem)
+                             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step<T, false>, threads, dynsmem);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return nb;
+}
+template int step_kernel_occupancy<float>(bool, int, size_t);
+template int step_kernel_occupancy<double>(bool, int, size_t);
 
 template cudaError_t launch_first_draw<float>(const BatchStep<float>&, int, DrawKey, cudaStream_t);
 template cudaError_t launch_first_draw<double>(const BatchStep<double>&, int, DrawKey, cudaStream_t);
@@ -1734,11 +1950,14 @@ template cudaError_t launch_probe<double>(const BatchStep<double>&, double*, dou
 // Check of the bounded-wait path: one staging round that posts 16 expected bytes and issues
 // no copy, so the wait runs out after `limit` polls, sets the error word and returns (no copy
 // is ever in flight on the abandoned barrier).
+// Both bounded waits, made to expire: a staging barrier whose copies are never issued, then
+// a step flag that nothing releases (err[2], a word of the error block that stays zero).
 __global__ void k_wait_selftest(unsigned* err, unsigned limit) {
   __shared__ uint64_t bar;
   if (threadIdx.x == 0) mbar_init(&bar);
   Stager sg{&bar, 0u, err, limit};
   sg.run(16u, []() {});
+  flag_wait(err + 2, err, limit);
 }
 
 cudaError_t launch_wait_selftest(unsigned* err, unsigned limit, cudaStream_t s) {

@@ -54,11 +54,17 @@ struct Ws {
   double* scal;   // kNumScal
   double* part;   // per-CTA partial sums
   double* gpart;  // per-group partial sums
-  unsigned int* cnt;  // election counters: [3][kMaxGroups + 1]
+  unsigned int* cnt;  // election counters: [kCntSets][kMaxGroups + 1]; set 3, slot 0: step flag
   unsigned int* err;  // device error word: bit 0 = a bounded mbarrier wait expired
   __device__ __forceinline__ double* scr(int i) const { return scrb + i * scr_stride; }
 };
 constexpr int kMaxGroups = 512;
+// Counter sets of a trial's workspace: the elections of K1, K2 and K3, then the flag that
+// hands the update sweep's results to the output sweep inside the step kernel (and, in trial
+// 0's set only, the step kernel's two work queues and its count of finished CTAs).
+constexpr int kCntSets = 4;
+constexpr int kStepFlagSlot = 3 * (kMaxGroups + 1);
+constexpr int kStepQueueSlot = kStepFlagSlot + 1;
 
 struct Grid {
   int ctas;         // CTAs of the sweep
@@ -106,6 +112,11 @@ struct StepPlan {
   T sigma;              // entry scale of the draws (Ginibre), 1 for Haar
   SweepCfg c1, c2, c3;  // launch shapes of the three sweeps
   int pdl;              // launch with programmatic dependent launch
+  int fin_out;          // the update and fused output sweeps call their finalisations out of line
+                        // (batches: every trial has a finaliser)
+  int step_ctas;        // > 0: K2 and the fused K3 run as one step kernel (k_step) of this many
+                        // CTAs (cooperative launch; c2.W == c3.W) with step_smem bytes of
+  int step_smem;        // dynamic shared memory
   // Fused trajectories (hd_run, Q / Q^T alternating, elementwise f_t): K3 also applies the
   // dynamics x_{t+1} = f(y_t, x_{t-1}) and forms the next step's K1 results (z, h, w), so the
   // next step skips K1.
@@ -170,7 +181,8 @@ template <typename T>
 cudaError_t launch_first_draw(const BatchStep<T>& b, int space, DrawKey key,
                               cudaStream_t s);
 // ev (optional): start/stop event pairs recorded around K1, K2, K3 (ev[2*kind], ev[2*kind+1]);
-// a null entry skips the record.  launched[kind] is set to 1 for each sweep launched.
+// a null entry skips the record.  launched[kind] is set to 1 for each sweep launched;
+// launched[1] = 2 (and the K2 events) when the step kernel ran K2 and K3 as one launch.
 template <typename T>
 cudaError_t launch_step(const BatchStep<T>& b, cudaStream_t s, cudaEvent_t* ev = nullptr,
                         int* launched = nullptr);
@@ -179,6 +191,10 @@ cudaError_t launch_probe(const BatchStep<T>& b, double* q, double* unrevealed, c
 
 template <typename T>
 int kernel_occupancy(int which, size_t dynsmem);
+// CTAs of the step kernel (Haar or Ginibre) resident per SM with `threads` threads and dynsmem
+// bytes of dynamic shared memory (0 when it does not fit).
+template <typename T>
+int step_kernel_occupancy(bool haar, int threads, size_t dynsmem);
 template <typename T>
 int kernel_static_smem(int which);
 template <typename T>

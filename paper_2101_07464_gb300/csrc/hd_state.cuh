@@ -113,6 +113,8 @@ struct hd_state {
   int nsm = 1;
   int pdl = 1;                   // programmatic dependent launch of the sweeps (hd_set_engine)
   int fuse = 1;                  // fused output + dynamics + dot sweeps in hd_run (hd_set_engine)
+  int step_kernel = 0;           // update + fused output sweep as one launch (hd_set_engine)
+  std::vector<std::pair<int64_t, int>> step_occ;   // step kernel occupancy per launch shape
   int occ_regs[6] = {1, 1, 1, 1, 1, 1};  // CTAs of 256 threads per SM allowed by registers, per sweep kernel
   int static_smem[6] = {0, 0, 0, 0, 0, 0};   // (dots, update, out Haar, out Gin, fused out Haar, fused out Gin)
   int smem_sm = 0;
@@ -150,9 +152,9 @@ struct hd_state {
   std::vector<int> prof_kind;
   std::vector<double> prof_bytes;
   std::vector<int> prof_tag;     // per slot: kernel | bucket << 4 | W << 8 | stages << 12
-  double prof_ms[3] = {0, 0, 0};
-  int64_t prof_n[3] = {0, 0, 0};
-  double prof_b[3] = {0, 0, 0};
+  double prof_ms[4] = {0, 0, 0, 0};   // per kind: dots, update, output, step kernel
+  int64_t prof_n[4] = {0, 0, 0, 0};
+  double prof_b[4] = {0, 0, 0, 0};
   hd::AdjState* adj = nullptr;   // reverse mode (hd_adjoint_enable)
   // hd_run with HD_DYN_AMP: packed per-trial vectors and scalars (allocated on first use)
   void* amp_y = nullptr;         // y = Q beta + w (m-space)

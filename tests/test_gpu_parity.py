@@ -200,8 +200,8 @@ def test_probe_reproduces_earlier_queries(dtype, ens, m, n):
 
 
 def test_expired_bounded_wait_poisons_until_reset():
-    """The kernels' bounded waits: a wait that runs out (on a barrier nothing completes) sets
-    the error word; hd_sync reports HD_ERR_TIMEOUT, later calls return it, hd_reset clears it
+    """The kernels' bounded waits: a wait that runs out (on a barrier nothing completes, on a
+    step flag nothing releases) sets the error word; hd_sync reports HD_ERR_TIMEOUT, later calls return it, hd_reset clears it
     and the state computes the oracle's products again."""
     import paper_2101_07464_gb300 as hd
     import synth
@@ -213,6 +213,7 @@ def test_expired_bounded_wait_poisons_until_reset():
     with pytest.raises(hd.HDError) as ei:
         hd.hd_sync(st.h)
     assert ei.value.code == 6
+    assert "0x3" in str(ei.value)   # both waits expired: the staging barrier and the step flag
     with pytest.raises(hd.HDError) as ei:   # sticky
         st.apply(x)
     assert ei.value.code == 6

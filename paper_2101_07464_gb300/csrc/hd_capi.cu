@@ -73,6 +73,7 @@ SweepCfg make_sweep(const hd_state* st, int which, int ncolT, int NRV, int ncolC
     c.W = tW;
     c.nbuf = tnb;
   }
+  c.per_sm = ctas_of(c.W, c.nbuf);
   c.tag = which | (bucket << 4);
   c.g.ctas = 0;
   c.g.vpc = 0;
@@ -80,6 +81,9 @@ SweepCfg make_sweep(const hd_state* st, int which, int ncolT, int NRV, int ncolC
   c.g.ngroups = 1;
   return c;
 }
+
+template <typename T>
+void pick_maps(const hd_state* st, BatchStep<T>& b);
 
 template <typename T>
 BatchStep<T> make_batch(const hd_state* st, int d, int kD, int kN, const void* x, void* y) {
@@ -224,11 +228,12 @@ int do_step(hd_state* st, const void* x, int transpose, void* y, const FuseSpec*
         b.base.c3 = make_sweep<T>(st, 4, kN, 2, kN, 1);
       else
         b.base.c3 = make_sweep<T>(st, 5, kN + kD, 3, kN + kD, 1);
-      if (st->step_kernel) {
-        plan_step_kernel<T>(st, b);
-        step_fallback = b.base.step_ctas == 0;
-      }
     }
+  }
+  pick_maps<T>(st, b);
+  if (fs && fs->fuse && st->step_kernel) {
+    plan_step_kernel<T>(st, b);
+    step_fallback = b.base.step_ctas == 0;
   }
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   int slot0 = -1;
@@ -538,7 +543,33 @@ bool build_maps(hd_state* st) {
   st->map_opt = 0;
   st->map[0] = st->maps[0][0];
   st->map[1] = st->maps[0][1];
+  // the built-in rule for one CTA per SM
+  st->has_map_one = 0;
+  int64_t spc1[2];
+  for (int s = 0; s < 2; s++) {
+    int64_t total = 0;
+    for (int i = 0; i < st->count; i++) total += (st->dims[s][i] + 31) / 32;
+    spc1[s] = std::max<int64_t>(16, (total + st->nsm - 1) / st->nsm);
+  }
+  if (spc1[0] != spc0[0] || spc1[1] != spc0[1]) {
+    for (int s = 0; s < 2; s++)
+      if (!build_map(st, s, spc1[s], &st->map_one[s])) return false;
+    st->has_map_one = 1;
+  }
   return true;
+}
+
+// With the built-in split, a sweep whose launch shape leaves room for one CTA per SM takes
+// the split with one CTA per SM, one wave of CTAs instead of two (the second wave's
+// stragglers would otherwise leave SMs idle at the end of the sweep).  K1 and K2 share the
+// data space's split, K3 has the output space's.  Every split of a space gives the same
+// results up to the order of the FP64 sums over CTAs.
+template <typename T>
+void pick_maps(const hd_state* st, BatchStep<T>& b) {
+  if (st->map_opt != 0 || !st->has_map_one) return;
+  const StepPlan<T>& p = b.base;
+  if (p.c2.per_sm == 1) b.map[b.d] = st->map_one[b.d];
+  if (p.c3.per_sm == 1) b.map[1 - b.d] = st->map_one[1 - b.d];
 }
 
 int create_common(int ensemble, int count, const int64_t* m, const int64_t* n, int32_t T_max,

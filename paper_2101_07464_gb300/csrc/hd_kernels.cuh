@@ -78,6 +78,7 @@ struct Grid {
 struct SweepCfg {
   int W;
   int nbuf;
+  int per_sm;       // CTAs of this shape resident per SM (host bookkeeping)
   Grid g;
   int tag;          // host bookkeeping (profiling): kernel | column bucket << 4
 };

@@ -100,6 +100,10 @@ struct hd_state {
   int map_spc[hd::kMapOpts][2] = {};
   int nmaps = 1;
   int map_opt = 0;
+  // the built-in split with one CTA per SM instead of kSweepCtasPerSm (one wave for sweeps whose
+  // shape leaves room for one CTA per SM); has_map_one = 0 when it equals the built-in split
+  CtaMap map_one[2];
+  int has_map_one = 0;
   int maxncta = 1;
   // launch shapes: tuned table, autotuner override, cache key of the state's shape
   int8_t tuneW[hd::kSweepKinds][hd::kTuneBuckets] = {};

@@ -48,6 +48,27 @@ __device__ __forceinline__ void block_sum_to(const T (&a)[NV], double* red, doub
   __syncthreads();
 }
 
+// d * v for a prefix sign d, which is exactly +1 or -1 (a product of the reflectors' signs):
+// the sign bit of d is moved onto v with integer operations (on this GPU an FP64 multiply
+// takes a slot of the FP64 pipe, which bounds the FP64 sweeps).
+__device__ __forceinline__ double sign_mul(double d, double v) {
+  return __longlong_as_double(__double_as_longlong(v) ^ (__double_as_longlong(d) & (long long)0x8000000000000000ull));
+}
+__device__ __forceinline__ float sign_mul(float d, float v) {
+  return __int_as_float(__float_as_int(v) ^ (__float_as_int(d) & (int)0x80000000u));
+}
+// sign(y) in {-1, 0, 1} (0 for +-0 and NaN) from the bits of y.
+__device__ __forceinline__ double sign_of(double y) {
+  const long long b = __double_as_longlong(y);
+  const long long a = b & 0x7FFFFFFFFFFFFFFFll;
+  return (a == 0 || a > 0x7FF0000000000000ll) ? 0.0 : ((b < 0) ? -1.0 : 1.0);
+}
+__device__ __forceinline__ float sign_of(float y) {
+  const int b = __float_as_int(y);
+  const int a = b & 0x7FFFFFFF;
+  return (a == 0 || a > 0x7F800000) ? 0.0f : ((b < 0) ? -1.0f : 1.0f);
+}
+
 __device__ __forceinline__ bool elect_last(unsigned int* counter, int expected) {
   __shared__ bool last;
   __threadfence();
@@ -803,9 +824,12 @@ __device__ __forceinline__ void wt_col_pair(const T* buf, int ncol, int m, const
   const int j0 = lane + 32 * m, j1 = j0 + 32;
   const bool h1 = TWO && j1 < ncol;
   if (j0 >= ncol) return;
-  T s0[NR], s1[NR];
+  T s0[NR], s1[NR];   // the running sums themselves (no separate add per sub-tile)
 #pragma unroll
-  for (int r = 0; r < NR; r++) s0[r] = s1[r] = T(0);
+  for (int r = 0; r < NR; r++) {
+    s0[r] = acc[r][m];
+    s1[r] = (TWO && h1) ? acc[r][m + 1] : T(0);
+  }
   const T* col0 = buf + j0 * 32;
   const T* col1 = buf + (h1 ? j1 : j0) * 32;
 #pragma unroll
@@ -830,8 +854,8 @@ __device__ __forceinline__ void wt_col_pair(const T* buf, int ncol, int m, const
   }
 #pragma unroll
   for (int r = 0; r < NR; r++) {
-    acc[r][m] += s0[r];
-    if (TWO && h1) acc[r][m + 1] += s1[r];
+    acc[r][m] = s0[r];
+    if (TWO && h1) acc[r][m + 1] = s1[r];
   }
 }
 
@@ -852,7 +876,7 @@ __device__ __forceinline__ void wt_cols_grouped(const T* buf, int ncol, const T*
   const T* col = buf + j * 32;
   T s[NR];
 #pragma unroll
-  for (int r = 0; r < NR; r++) s[r] = T(0);
+  for (int r = 0; r < NR; r++) s[r] = acc[r][0];
 #pragma unroll
   for (int i = 0; i < S; i++) {
     const int c = q * D + (i % D) + 8 * (i / D);
@@ -867,7 +891,7 @@ __device__ __forceinline__ void wt_cols_grouped(const T* buf, int ncol, const T*
     }
   }
 #pragma unroll
-  for (int r = 0; r < NR; r++) acc[r][0] += s[r];
+  for (int r = 0; r < NR; r++) acc[r][0] = s[r];
 }
 
 // Column owner: acc[r][m] += sum_i V[i, lane + 32 m] rhs_r[i] over the 32 rows, m < 8.
@@ -1249,7 +1273,7 @@ __device__ __forceinline__ void update_sweep(const BatchStep<T>& bs, int vb, uns
         T out[1];
         wt_rows<T, 1>(st, k, sm.coef, nullptr, out);
         const T d = (r < k) ? (T)p.D.dpre[r + 1] : dconst;
-        const T pvv = (sm.srow(st, 0)[lane] - out[0]) * d;
+        const T pvv = sign_mul(d, sm.srow(st, 0)[lane] - out[0]);
         if (r < dim) {
           if (r < k) {
             p.ws.phead[r] = (double)pvv;
@@ -1289,8 +1313,7 @@ __global__ void __launch_bounds__(kThreads, kSweepCtasPerSm) k_update(BatchStep<
 template <typename T>
 __device__ __forceinline__ T fused_dyn(int kind, T a, T y, T xprev) {
   if (kind == 1) return tanh(y);
-  const T sg = (y > T(0)) ? T(1) : ((y < T(0)) ? T(-1) : T(0));
-  return sg + a * xprev;
+  return fma(a, xprev, sign_of(y));
 }
 
 // K3 (Haar): y = Delta_N c - V_N w' with c = [p_head; coef g_t[k:]]; appends the random
@@ -1360,7 +1383,7 @@ __device__ __forceinline__ bool out_haar_sweep(const BatchStep<T>& bs, int vb, u
         else if (flag) ci = (r == k) ? alpha : T(0);
         else ci = coef * g;
         const T d = (r < k) ? (T)p.N.dpre[r + 1] : dconst;
-        const T yi = d * ci - out[0];
+        const T yi = sign_mul(d, ci) - out[0];
         const T nc = (r > k) ? g : ((r == k) ? usg : T(0));
         if (r < dim) {
           if (!FUSE) p.y[r] = yi;
@@ -1501,8 +1524,8 @@ __device__ __forceinline__ bool out_gin_sweep(const BatchStep<T>& bs, int vb, un
         T out[2];
         wt_rows<T, 2>(st, nc, sm.coef, sm.coef + sm.cpad, out);
         const T d = (r < kN) ? (T)p.N.dpre[r + 1] : dconst;
-        const T u = d * g - out[0];
-        const T yi = fma(alpha, u, d * hi) - out[1];
+        const T u = sign_mul(d, g) - out[0];
+        const T yi = fma(alpha, u, sign_mul(d, hi)) - out[1];
         if (r < dim) {
           ucol[r] = u;
           if (!FUSE) p.y[r] = yi;

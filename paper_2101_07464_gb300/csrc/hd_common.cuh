@@ -3,6 +3,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "hd_log_table.cuh"
+
 namespace hd {
 
 constexpr int kThreads = 256;          // threads per CTA of every streaming kernel
@@ -99,15 +101,80 @@ struct DrawKey {
   uint32_t stream;
 };
 
+// ---------------------------------------------------------------------------------
+// FP64 Box-Muller with few FP64 operations.  On this GPU the FP64 pipe runs at 1/64 of the
+// FP32 rate and bounds the FP64 sweeps, so the logarithm and the sine-cosine of the draws
+// keep FP64 arithmetic for the terms whose size needs it and take the rest from integer and
+// FP32 operations; each result is within a few units in the last place of the FP64 value.
+constexpr double kLn2 = 0x1.62e42fefa39efp-1;          // ln 2 rounded to FP64
+constexpr double kPiScaled = 0x1.921fb54442d18p-51;    // pi 2^-52 (pi rounded to FP64)
+
+// ln u for u = K 2^-53, K in [1, 2^53].  u = m 2^e with m in [0.75, 1.5) (from the bits of K:
+// no cancellation between e ln 2 and ln m near u = 1), and ln m = -ln c_i + ln(1 + r) with
+// r = m c_i - 1 (one FMA) for the table entry i = round(256 (m - 1)), |r| <= 0.0026 (table
+// method: Tang, ACM TOMS 16, 1990).  ln(1 + r) = r + r^2 (-1/2 + r (1/3 + q)): the series'
+// terms beyond r^3 / 3, q = -r/4 + r^2/5 - r^3/6, are below 2^-30 and are formed in FP32.
+__device__ __forceinline__ double log_u53(uint64_t K) {
+  if (K >= (1ull << 53)) return 0.0;
+  const int lz = __clzll((long long)K) - 11;             // K < 2^53: 0 .. 52
+  const uint64_t Kp = K << lz;                            // [2^52, 2^53): m_n = Kp 2^-52 in [1, 2)
+  const bool half = (Kp >> 51) & 1ull;                    // m_n >= 1.5: take m = m_n / 2
+  const uint64_t mant = Kp & ((1ull << 52) - 1ull);
+  const double m = __longlong_as_double((long long)(((half ? 0x3FEull : 0x3FFull) << 52) | mant));
+  const int e = half ? -lz : -1 - lz;                     // u = m 2^e
+  const int i = half ? -(int)(((1ull << 53) - Kp + (1ull << 44)) >> 45)   // m in [0.75, 1): -64 .. 0
+                     : (int)((Kp - (1ull << 52) + (1ull << 43)) >> 44);   // m in [1, 1.5): 0 .. 128
+  const double2 ct = __ldg(&kLogTab[i - kLogTabLo]);
+  const double r = fma(m, ct.x, -1.0);
+  const float rf = (float)r;
+  const float q = rf * fmaf(rf, fmaf(rf, -1.0f / 6.0f, 0.2f), -0.25f);
+  const double inner = fma(r, 0x1.5555555555555p-2 + (double)q, -0.5);   // -1/2 + r (1/3 + q)
+  const double lm = fma(r * r, inner, r);                                 // ln(1 + r)
+  return fma((double)e, kLn2, ct.y) + lm;
+}
+
+// sin(pi x), cos(pi x) for x = K 2^-52, K in [1, 2^53] (x in (0, 2]).  x = n/2 + y with
+// n = round(2x) and |y| <= 1/4 exactly in integers; z = pi y; the Taylor series of sin z and
+// cos z in w = z^2 keep FP64 for the terms above 4e-8 and FP32 for the rest (the error of the
+// FP32 part stays below 2e-16); then the quadrant n mod 4 selects and signs the two.
+__device__ __forceinline__ void sincospi_u52(uint64_t K, double& sn, double& cs) {
+  const uint64_t n = (K + (1ull << 50)) >> 51;                  // 0 .. 4
+  const long long D = (long long)K - (long long)(n << 51);     // 2^52 y, |D| <= 2^50
+  const double z = (double)D * kPiScaled;
+  const double w = z * z;
+  const float wf = (float)w;
+  // sin z = z + z^3 S(w): S = -1/3! + w/5! - w^2/7! + w^3/9! + w^4 (-1/11! + w/13! - w^2/15!)
+  const float ts = fmaf(wf, fmaf(wf, -0x1.ae7f3ep-41f, 0x1.612462p-33f), -0x1.ae6456p-26f);
+  double S = fma(w, (double)ts, 0x1.71de3a556c734p-19);         // 1/9!
+  S = fma(w, S, -0x1.a01a01a01a01ap-13);                        // -1/7!
+  S = fma(w, S, 0x1.1111111111111p-7);                          // 1/5!
+  S = fma(w, S, -0x1.5555555555555p-3);                         // -1/3!
+  const double s = fma(z * w, S, z);
+  // cos z = 1 + w C(w): C = -1/2! + w/4! - w^2/6! + w^3/8! - w^4/10! + w^5 (1/12! - w/14! + w^2/16!)
+  const float tc = fmaf(wf, fmaf(wf, 0x1.ae7f3ep-45f, -0x1.93974ap-37f), 0x1.1eed8ep-29f);
+  double C = fma(w, (double)tc, -0x1.27e4fb7789f5cp-22);        // -1/10!
+  C = fma(w, C, 0x1.a01a01a01a01ap-16);                         // 1/8!
+  C = fma(w, C, -0x1.6c16c16c16c17p-10);                        // -1/6!
+  C = fma(w, C, 0x1.5555555555555p-5);                          // 1/4!
+  C = fma(w, C, -0.5);
+  const double c = fma(w, C, 1.0);
+  // theta = n pi / 2 + z
+  const unsigned q = (unsigned)n & 3u;
+  const double a = (q & 1u) ? c : s;                            // |sin theta|
+  const double b = (q & 1u) ? s : c;                            // |cos theta|
+  sn = (q >= 2u) ? -a : a;
+  cs = (q == 1u || q == 2u) ? -b : b;
+}
+
 // Normals 2j and 2j+1: u = (53-bit integer + 1) 2^-53 in (0, 1] from two words, then
 // Box-Muller r = sqrt(-2 ln u1), (r cos 2 pi u2, r sin 2 pi u2).
 __device__ __forceinline__ void normal_pair(const DrawKey& k, uint64_t j, double& z0, double& z1) {
   PhiloxOut o = philox4x32_10((uint32_t)j, k.step, k.trial, k.stream, k.k0, k.k1);
-  const double u1 = ((double)((((uint64_t)o.w[0]) << 21) | (o.w[1] >> 11)) + 1.0) * 0x1.0p-53;
-  const double u2 = ((double)((((uint64_t)o.w[2]) << 21) | (o.w[3] >> 11)) + 1.0) * 0x1.0p-53;
-  const double r = sqrt(-2.0 * log(u1));
+  const uint64_t K1 = ((((uint64_t)o.w[0]) << 21) | (o.w[1] >> 11)) + 1ull;
+  const uint64_t K2 = ((((uint64_t)o.w[2]) << 21) | (o.w[3] >> 11)) + 1ull;
+  const double r = sqrt(-2.0 * log_u53(K1));
   double sn, cs;
-  sincospi(2.0 * u2, &sn, &cs);
+  sincospi_u52(K2, sn, cs);
   z0 = r * cs;
   z1 = r * sn;
 }

@@ -145,9 +145,12 @@ def test_batched_argument_checks():
 
 def test_batched_fused_run_matches_apply():
     """Fused alternating trajectory on a batch (FP64, sign dynamics): per trial equal to the
-    step-by-step products up to the dots' summation order."""
+    step-by-step products up to the dots' summation order.  Every trial has n >= 333: with
+    n <= 257 this schedule revisits sign vectors exactly (x_t falls in the span the earlier
+    reflectors fix, alpha_t = 0 in exact arithmetic, reading A15), and the reflector built from
+    that rounding-level remainder differs between any two summation orders."""
     import paper_2101_07464_gb300 as hd
-    ns = [10_007, 31, 65_536, 4099]
+    ns = [10_007, 333, 65_536, 4099]
     T, a = 14, 0.5
     flags = [ALT(t) for t in range(1, T + 1)]
     x1 = torch.tensor(np.concatenate([synth.x1(n, 9, trial=i) for i, n in enumerate(ns)]),

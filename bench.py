@@ -67,6 +67,8 @@ def parse(argv=None):
                     help="skip the large configuration (Haar n = 2e7, T = 256, forward and reverse mode)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the built-in launch shapes (no hd_autotune before timing)")
+    ap.add_argument("--step-kernel", action="store_true",
+                    help="time the headline with the step kernel (one launch per step, hd_set_engine)")
     return ap.parse_args(argv)
 
 
@@ -252,11 +254,12 @@ class ClockSampler:
 
 # DRAM bytes / algorithmic bytes of one launch of the dominant kernel, from an ncu capture of
 # the current kernel at k = 60, n = 10^6; None until a capture of the current kernel exists.
-# (FP32: 245.57 MB for 248.0 MB at k = 59.)
-TRAFFIC_RATIO = {"f32": 245.57 / 248.0, "f64": None}
+# (FP32: 245.57 MB for 248.0 MB at k = 59; FP64: 493.91 MB for 504.0 MB at k = 60.)
+TRAFFIC_RATIO = {"f32": 245.57 / 248.0, "f64": 493.91 / 504.0}
 TRAFFIC_KERNEL = "update"
 TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_update launch "
-                  "(k = 59, n = 10^6, same dtype), scaled to the average launch by algorithmic bytes")
+                  "(k = 59 in FP32, k = 60 in FP64, n = 10^6, same dtype), scaled to the average "
+                  "launch by algorithmic bytes")
 
 # Algorithmic FP64 flops per stack element of each sweep in the fused Q / Q^T alternating
 # trajectory (2 per FMA): the update sweep forms p = Delta (x - V w) and the two column
@@ -1435,6 +1438,8 @@ def run_ours(args):
     def measure(dtype, profile):
         tdt = torch.float32 if dtype == "f32" else torch.float64
         st = hd.HD("haar", n, n, T, args.seed, dtype, trial=rank)
+        if args.step_kernel:
+            hd.hd_set_engine(st.h, step_kernel=True)
         spec = hd.make_run_spec(flags, "sign_mem", 0.5, use_graph=True)
         x1 = torch.tensor(synth.x1(n, args.seed, trial=rank), dtype=tdt, device="cuda")
         xout = torch.empty(n, dtype=tdt, device="cuda")
@@ -1594,6 +1599,8 @@ def run_ours(args):
                            "l2": "inputs larger than L2 (two reflector stacks of %.0f MB each)"
                            % (n * T * tdt.itemsize / 1e6),
                            "graph": "one CUDA graph per trajectory",
+                           "engine": ("step kernel (one launch per step)" if args.step_kernel
+                                      else "two launches per step (update sweep, fused output sweep)"),
                            "launch_shapes": "built-in" if args.no_autotune
                            else "hd_autotune (untimed, before the timed region)"},
                 "roofline": roofline,

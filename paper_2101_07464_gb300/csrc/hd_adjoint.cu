@@ -122,13 +122,20 @@ __global__ void __launch_bounds__(kAT) k_colpass(TP<const T> A_, int64_t ld, int
 __device__ __forceinline__ void colreduce_col(const double* __restrict__ part, int nblk, int K, int j,
                                               double s1, double* out1, double s2, double* out2) {
   const int lane = threadIdx.x & 31;
-  double a = 0.0, b = 0.0;
-  for (int q = lane; q < nblk; q += 32) {
-    a += part[((int64_t)q * K + j) * 2];
-    b += part[((int64_t)q * K + j) * 2 + 1];
+  double a0 = 0.0, b0 = 0.0, a1 = 0.0, b1 = 0.0;   // two chains each: the loads overlap
+  int q = lane;
+  for (; q + 32 < nblk; q += 64) {
+    a0 += part[((int64_t)q * K + j) * 2];
+    b0 += part[((int64_t)q * K + j) * 2 + 1];
+    a1 += part[((int64_t)(q + 32) * K + j) * 2];
+    b1 += part[((int64_t)(q + 32) * K + j) * 2 + 1];
   }
-  a = warp_sum(a);
-  b = warp_sum(b);
+  if (q < nblk) {
+    a0 += part[((int64_t)q * K + j) * 2];
+    b0 += part[((int64_t)q * K + j) * 2 + 1];
+  }
+  const double a = warp_sum(a0 + a1);
+  const double b = warp_sum(b0 + b1);
   if (lane == 0) {
     out1[j] = s1 * a;
     if (out2) out2[j] = s2 * b;
@@ -329,18 +336,25 @@ __global__ void __launch_bounds__(kAT) k_rankN4(TP<float> Ab_, int64_t ld, int K
 #pragma unroll
     for (int q = 0; q < 5; q++)
       vr[q] = (q < t.n) ? reinterpret_cast<const float4*>(t.v[q])[q4] : make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int jj = 0; jj < jn; jj++) {
-      float4* col = reinterpret_cast<float4*>(Ab + (int64_t)(j0 + jj) * ld);
-      float4 v = col[q4];
+    float4* col0 = reinterpret_cast<float4*>(Ab + (int64_t)j0 * ld) + q4;
+    const int64_t ld4 = ld / 4;
+    float4 v[8];
 #pragma unroll
-      for (int q = 0; q < 5; q++) {
-        const float cq = cs[q][jj];
-        v.x = fmaf(vr[q].x, cq, v.x);
-        v.y = fmaf(vr[q].y, cq, v.y);
-        v.z = fmaf(vr[q].z, cq, v.z);
-        v.w = fmaf(vr[q].w, cq, v.w);
+    for (int jj = 0; jj < 8; jj++)   // the eight column loads in flight together
+      if (jj < jn) v[jj] = col0[(int64_t)jj * ld4];
+#pragma unroll
+    for (int jj = 0; jj < 8; jj++) {
+      if (jj < jn) {
+#pragma unroll
+        for (int q = 0; q < 5; q++) {
+          const float cq = cs[q][jj];
+          v[jj].x = fmaf(vr[q].x, cq, v[jj].x);
+          v[jj].y = fmaf(vr[q].y, cq, v[jj].y);
+          v[jj].z = fmaf(vr[q].z, cq, v[jj].z);
+          v[jj].w = fmaf(vr[q].w, cq, v[jj].w);
+        }
+        col0[(int64_t)jj * ld4] = v[jj];
       }
-      col[q4] = v;
     }
   }
 }
@@ -360,8 +374,20 @@ __global__ void __launch_bounds__(kAT) k_rowpass4(TP<float> out_, TP<const float
   for (int64_t q4 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q4 < dim4; q4 += (int64_t)gridDim.x * blockDim.x) {
     float4 v = in ? reinterpret_cast<const float4*>(in)[q4] : make_float4(0.f, 0.f, 0.f, 0.f);
     v.x *= si; v.y *= si; v.z *= si; v.w *= si;
-    for (int j = 0; j < K; j++) {
-      const float4 aj = reinterpret_cast<const float4*>(A + (int64_t)j * ld)[q4];
+    const float4* Aq = reinterpret_cast<const float4*>(A) + q4;
+    const int64_t ld4 = ld / 4;
+    int j = 0;
+    for (; j + 4 <= K; j += 4) {   // four column loads in flight
+      const float4 a0 = Aq[(int64_t)j * ld4], a1 = Aq[(int64_t)(j + 1) * ld4];
+      const float4 a2 = Aq[(int64_t)(j + 2) * ld4], a3 = Aq[(int64_t)(j + 3) * ld4];
+      const float c0 = cs[j], c1 = cs[j + 1], c2 = cs[j + 2], c3 = cs[j + 3];
+      v.x = fmaf(a3.x, c3, fmaf(a2.x, c2, fmaf(a1.x, c1, fmaf(a0.x, c0, v.x))));
+      v.y = fmaf(a3.y, c3, fmaf(a2.y, c2, fmaf(a1.y, c1, fmaf(a0.y, c0, v.y))));
+      v.z = fmaf(a3.z, c3, fmaf(a2.z, c2, fmaf(a1.z, c1, fmaf(a0.z, c0, v.z))));
+      v.w = fmaf(a3.w, c3, fmaf(a2.w, c2, fmaf(a1.w, c1, fmaf(a0.w, c0, v.w))));
+    }
+    for (; j < K; j++) {
+      const float4 aj = Aq[(int64_t)j * ld4];
       const float cj = cs[j];
       v.x = fmaf(aj.x, cj, v.x);
       v.y = fmaf(aj.y, cj, v.y);
@@ -532,15 +558,24 @@ __device__ void out_small_dev(const T* __restrict__ V, int64_t ld, int Ke, int n
     const int i = idx % Ke, j = idx / Ke;
     if (i <= j) Sb[i + (int64_t)j * Tm] += bb[i] * a[j];
   }
-  for (int i = wid; i < nc; i += nw) {   // cbar = Delta (ybar + V abar) on rows < nc
+  // cbar = Delta (ybar + V abar) on rows < nc: a row per thread, so that a warp reads (and
+  // updates) consecutive rows of each column
+  for (int i = threadIdx.x; i < nc; i += blockDim.x) {
     const int jm = min(i, Ke - 1);
-    double s = 0.0;
-    for (int j = lane; j <= jm; j += 32) {
-      s = fma((double)V[i + (int64_t)j * ld], ab[j], s);
-      Vb[i + (int64_t)j * ld] += (T)(cp[i] * ab[j]);
+    const double ci = cp[i];
+    double s0 = 0.0, s1 = 0.0;
+    int j = 0;
+    for (; j + 1 <= jm; j += 2) {
+      s0 = fma((double)V[i + (int64_t)j * ld], ab[j], s0);
+      s1 = fma((double)V[i + (int64_t)(j + 1) * ld], ab[j + 1], s1);
+      Vb[i + (int64_t)j * ld] += (T)(ci * ab[j]);
+      Vb[i + (int64_t)(j + 1) * ld] += (T)(ci * ab[j + 1]);
     }
-    s = warp_sum(s);
-    if (lane == 0) cbar[i] = dpre[i + 1] * ((double)ybd[i] + s);
+    if (j <= jm) {
+      s0 = fma((double)V[i + (int64_t)j * ld], ab[j], s0);
+      Vb[i + (int64_t)j * ld] += (T)(ci * ab[j]);
+    }
+    cbar[i] = dpre[i + 1] * ((double)ybd[i] + (s0 + s1));
   }
 }
 template <typename T>
@@ -553,18 +588,17 @@ __global__ void __launch_bounds__(kSmallT) k_out_small(TP<const T> V, int64_t ld
                    Vb.at(tr), b_out.at(tr), cbar.at(tr));
 }
 
-// Haar output side in one CTA: bb = -V^T ybar from the column pass's partials, c = [p_head;
-// alpha], the output-product adjoint (k_out_small) and the S recurrence of the step's random
-// column (k_rec_col, after the Sbar update it depends on).
+// Haar output side in one CTA: with bb = -V^T ybar (the column pass, reduced over its row blocks
+// by k_colreduce), c = [p_head; alpha], the output-product adjoint (k_out_small) and the S
+// recurrence of the step's random column (k_rec_col, after the Sbar update it depends on).
 template <typename T>
-__global__ void __launch_bounds__(kSmallT) k_out_haar_adj(TP<const double> part_, int nblk, TP<const T> V_,
+__global__ void __launch_bounds__(kSmallT) k_out_haar_adj(TP<const T> V_,
                                                           int64_t ld, int Ke, TP<const double> S_, int Tm,
                                                           TP<const double> dpre_, TP<const double> phead_,
                                                           TP<const double> rs_, TP<double> cv_, TP<double> bb_,
                                                           TP<const T> ybd_, TP<double> Sb_, TP<T> Vb_, TP<double> bo_,
                                                           TP<double> cbar_, TP<const double> rag_, TP<double> au_) {
   const int tr = blockIdx.z;
-  const double* __restrict__ part = part_.at(tr);
   const T* __restrict__ V = V_.at(tr);
   const double* __restrict__ S = S_.at(tr);
   const double* __restrict__ dpre = dpre_.at(tr);
@@ -579,8 +613,7 @@ __global__ void __launch_bounds__(kSmallT) k_out_haar_adj(TP<const double> part_
   double* cbar = cbar_.at(tr);
   const double* __restrict__ rag = rag_.at(tr);
   double* au = au_.at(tr);
-  const int wid = threadIdx.x >> 5, nw = blockDim.x >> 5, k = Ke - 1;
-  for (int j = wid; j < Ke; j += nw) colreduce_col(part, nblk, Ke, j, -1.0, bb, 0.0, nullptr);
+  const int k = Ke - 1;
   for (int i = threadIdx.x; i <= k; i += blockDim.x) cv[i] = (i < k) ? phead[i] : rs[1];
   __syncthreads();
   out_small_dev<T>(V, ld, Ke, Ke, S, Tm, dpre, cv, bb, ybd, Sb, Vb, bo, cbar);
@@ -612,21 +645,16 @@ __global__ void __launch_bounds__(kAT) k_adj_record(TP<double> r_, int64_t L, TP
   for (int i = threadIdx.x; i < nug; i += blockDim.x) r[4 * L + 8 + i] = ug[i];
 }
 
-// Data side after the column pass of qbar in one CTA: wbar = -V^T qbar from the partials,
-// zbar = S wbar, Sbar += z wbar^T.
-__global__ void __launch_bounds__(kSmallT) k_data_small(TP<const double> part_, int nblk, int K,
-                                                        TP<const double> S_, int Tm, TP<const double> z_,
-                                                        TP<double> wb_, TP<double> zb_, TP<double> Sb_) {
+// Data side after the column pass of qbar in one CTA: with wbar = -V^T qbar (reduced by
+// k_colreduce), zbar = S wbar, Sbar += z wbar^T.
+__global__ void __launch_bounds__(kSmallT) k_data_small(int K, TP<const double> S_, int Tm, TP<const double> z_,
+                                                        TP<const double> wb_, TP<double> zb_, TP<double> Sb_) {
   const int tr = blockIdx.z;
-  const double* __restrict__ part = part_.at(tr);
   const double* __restrict__ S = S_.at(tr);
   const double* __restrict__ z = z_.at(tr);
-  double* wb = wb_.at(tr);
+  const double* wb = wb_.at(tr);
   double* zb = zb_.at(tr);
   double* Sb = Sb_.at(tr);
-  const int wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int j = wid; j < K; j += nw) colreduce_col(part, nblk, K, j, -1.0, wb, 0.0, nullptr);
-  __syncthreads();
   tri_dev(S, Tm, K, wb, 1.0, 0, zb);
   outer_upper_dev(Sb, Tm, K, z, wb);
 }
@@ -713,7 +741,7 @@ void colpass(const Ctx& c, TP<const T> A, int64_t ld, int K, int64_t dim, TP<con
   if (K <= 0) return;
   AdjState& A_ = *c.st->adj;
   const TP<double> part = tp(A_.part, A_.part_stride);
-  if (sizeof(T) == 4 && dim % 4 == 0 && al16tp(A) && al16tp(v1) && al16tp(v2))
+  if (sizeof(T) == 4 && dim % 4 == 0 && ld % 4 == 0 && al16tp(A) && al16tp(v1) && al16tp(v2))
     k_colpass4<<<dim3(A_.nblk, (K + 7) / 8, c.nz), kAT, 0, c.s>>>(
         TP<const float>{(const float*)A.p, A.s}, ld, K, dim / 4, TP<const float>{(const float*)v1.p, v1.s},
         TP<const float>{(const float*)v2.p, v2.s}, part);
@@ -728,7 +756,8 @@ void rowpass(const Ctx& c, TP<T> out, TP<const T> in, double s_in, TP<const T> A
              TP<const double> coef, double cscale, int64_t dim, TP<const double> dpre, int Kd, int acc,
              int64_t rnorm = INT64_MAX, TP<double> npart = TP<double>{nullptr, 0}, unsigned grid = 0) {
   const unsigned g = grid ? grid : rows_grid(c.st, dim);
-  if (sizeof(T) == 4 && !dpre.p && !npart.p && dim % 4 == 0 && al16tp(out) && al16tp(in) && al16tp(A)) {
+  if (sizeof(T) == 4 && !dpre.p && !npart.p && dim % 4 == 0 && ld % 4 == 0 && al16tp(out) && al16tp(in) &&
+      al16tp(A)) {
     k_rowpass4<<<dim3(rows_grid(c.st, dim / 4), 1, c.nz), kAT, 0, c.s>>>(
         TP<float>{(float*)out.p, out.s}, TP<const float>{(const float*)in.p, in.s}, s_in,
         TP<const float>{(const float*)A.p, A.s}, ld, K, coef, cscale, dim / 4, acc);
@@ -741,7 +770,7 @@ void rowpass(const Ctx& c, TP<T> out, TP<const T> in, double s_in, TP<const T> A
 template <typename T>
 void rankN(const Ctx& c, TP<T> Ab, int64_t ld, int K, int64_t dim, const RankTerms& t) {
   if (K <= 0 || t.n <= 0) return;
-  bool al = sizeof(T) == 4 && dim % 4 == 0 && al16tp(Ab);
+  bool al = sizeof(T) == 4 && dim % 4 == 0 && ld % 4 == 0 && al16tp(Ab);
   for (int q = 0; q < t.n; q++) al = al && al16tp(TP<const T>{(const T*)t.v[q], t.sv[q]});
   if (al) {
     dim3 g4(rows_grid(c.st, dim / 4), (unsigned)((K + 7) / 8), c.nz);
@@ -758,7 +787,7 @@ void rank(const Ctx& c, TP<T> Ab, int64_t ld, int K, int64_t dim, TP<const T> a,
           TP<const T> e = TP<const T>{nullptr, 0}, TP<const double> f = TP<const double>{nullptr, 0}, double sf = 0.0,
           int Kf = 0) {
   if (K <= 0) return;
-  if (sizeof(T) == 4 && dim % 4 == 0 && al16tp(Ab) && al16tp(a) && al16tp(cc) && al16tp(e)) {
+  if (sizeof(T) == 4 && dim % 4 == 0 && ld % 4 == 0 && al16tp(Ab) && al16tp(a) && al16tp(cc) && al16tp(e)) {
     dim3 g4(rows_grid(c.st, dim / 4), (unsigned)((K + 7) / 8), c.nz);
     k_rank4<<<g4, kAT, 0, c.s>>>(TP<float>{(float*)Ab.p, Ab.s}, ld, K, dim / 4,
                                  TP<const float>{(const float*)a.p, a.s}, b, sb,
@@ -872,8 +901,8 @@ int adj_step(hd_state* st, const void* ybar, const void* x_in, void* xbar) {
     const int Ke = kD + 1;   // the other stack including this step's random reflector
     // bb = -V_N^T ybar, the output-product adjoint, and the S recurrence of this step's random
     // column (L_t = H_t(g_t), column kD of V_N)
-    colpass<T>(c, Ve, Se.ld, Ke, ne, ybd, -1.0, none);
-    k_out_haar_adj<T><<<dim3(1, 1, c.nz), kSmallT, 0, c.s>>>(cst(part), A.nblk, Ve, Se.ld, Ke, SeS, Tm, Sep, phead, rs,
+    colpass<T>(c, Ve, Se.ld, Ke, ne, ybd, -1.0, bb);
+    k_out_haar_adj<T><<<dim3(1, 1, c.nz), kSmallT, 0, c.s>>>(Ve, Se.ld, Ke, SeS, Tm, Sep, phead, rs,
                                                              cv, bb, ybd, Sbe, Vbe, bo, cb, rag, au);
     RankTerms rt{};
     rt.v[0] = ybd.p; rt.c[0] = bo.p; rt.s[0] = -1.0; rt.K[0] = Ke; rt.sv[0] = ybd.s; rt.sc[0] = bo.s;
@@ -919,8 +948,8 @@ int adj_step(hd_state* st, const void* ybar, const void* x_in, void* xbar) {
 
   // the data product p = Delta (I - V S^T V^T) x
   if (kD > 0) {   // wbar = -V_D^T qbar, zbar = S wbar, Sbar += z wbar^T
-    colpass<T>(c, Vd, Sd.ld, kD, nd, cst(qb), -1.0, none);
-    k_data_small<<<dim3(1, 1, c.nz), kSmallT, 0, c.s>>>(cst(part), A.nblk, kD, SdS, Tm, z, wb, zb, Sbd);
+    colpass<T>(c, Vd, Sd.ld, kD, nd, cst(qb), -1.0, wb);
+    k_data_small<<<dim3(1, 1, c.nz), kSmallT, 0, c.s>>>(kD, SdS, Tm, z, cst(wb), zb, Sbd);
   }
   rowpass<T>(c, xb, cst(qb), 1.0, Vd, Sd.ld, kD, cst(zb), 1.0, nd, cnone, 0, 0);
   if (!haar && kN > 0) {

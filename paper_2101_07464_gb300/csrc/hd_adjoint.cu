@@ -54,9 +54,12 @@ struct TP {
 template <typename P>
 __host__ __device__ inline TP<P> tp(P* p, int64_t s) { return TP<P>{p, s}; }
 
-enum AdjVec { kVp, kVub, kVqb, kVg, kAdjVecs };
+// qbar, zbar and E have a second copy: a reverse step uses the copy of its step's parity, so a
+// step's data-side update held back for the next call keeps its vectors while that call forms
+// its own (the two sides of a Haar reverse step run on two streams).
+enum AdjVec { kVp, kVub, kVqb, kVg, kVqb2, kAdjVecs };
 enum AdjSmall {
-  kSz, kSw, kSh, kSbb, kSb, kScb, kSzb, kSwb, kSE, kSc, kShb, kSau, kSbu, kSbbu, kSabu, kSscal,
+  kSz, kSw, kSh, kSbb, kSb, kScb, kSzb, kSwb, kSE, kSc, kShb, kSau, kSbu, kSbbu, kSabu, kSscal, kSzb2, kSE2,
   kAdjSmall
 };
 
@@ -232,6 +235,8 @@ __global__ void __launch_bounds__(kAT) k_rank(TP<T> Ab_, int64_t ld, int K, int6
 // FP32 with 16-byte aligned vectors: the same passes four rows per thread (float4 accesses).
 __host__ __device__ __forceinline__ bool al16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
+// FP32, 16-byte aligned: four rows per thread; every thread loads its rows of a, c, e once and
+// walks all K columns, eight column loads in flight at a time.
 __global__ void __launch_bounds__(kAT) k_rank4(TP<float> Ab_, int64_t ld, int K, int64_t dim4, TP<const float> a_,
                                                TP<const double> b_, double sb, TP<const float> c_,
                                                TP<const double> d_, double sd, TP<const float> e_,
@@ -244,29 +249,36 @@ __global__ void __launch_bounds__(kAT) k_rank4(TP<float> Ab_, int64_t ld, int K,
   const double* __restrict__ d = d_.at(tr);
   const float* __restrict__ e = e_.at(tr);
   const double* __restrict__ f = f_.at(tr);
-  __shared__ float bs[8], ds[8], fs[8];
-  const int j0 = blockIdx.y * 8;
-  if (threadIdx.x < 8) {
-    const int j = j0 + threadIdx.x;
-    bs[threadIdx.x] = (j < K) ? (float)(sb * b[j]) : 0.f;
-    ds[threadIdx.x] = (j < K && c) ? (float)(sd * d[j]) : 0.f;
-    fs[threadIdx.x] = (j < Kf && e) ? (float)(sf * f[j]) : 0.f;
+  __shared__ float bs[kTmaxLimit + 1], ds[kTmaxLimit + 1], fs[kTmaxLimit + 1];
+  for (int j = threadIdx.x; j < K; j += blockDim.x) {
+    bs[j] = (float)(sb * b[j]);
+    ds[j] = c ? (float)(sd * d[j]) : 0.f;
+    fs[j] = (e && j < Kf) ? (float)(sf * f[j]) : 0.f;
   }
   __syncthreads();
-  const int jn = min(K, j0 + 8) - j0;
+  const int64_t ld4 = ld / 4;
   for (int64_t q4 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q4 < dim4; q4 += (int64_t)gridDim.x * blockDim.x) {
     const float4 ar = reinterpret_cast<const float4*>(a)[q4];
     const float4 cr = c ? reinterpret_cast<const float4*>(c)[q4] : make_float4(0.f, 0.f, 0.f, 0.f);
     const float4 er = e ? reinterpret_cast<const float4*>(e)[q4] : make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int q = 0; q < jn; q++) {
-      float4* col = reinterpret_cast<float4*>(Ab + (int64_t)(j0 + q) * ld);
-      float4 v = col[q4];
-      const float bq = bs[q], dq = ds[q], fq = fs[q];
-      v.x = fmaf(er.x, fq, fmaf(cr.x, dq, fmaf(ar.x, bq, v.x)));
-      v.y = fmaf(er.y, fq, fmaf(cr.y, dq, fmaf(ar.y, bq, v.y)));
-      v.z = fmaf(er.z, fq, fmaf(cr.z, dq, fmaf(ar.z, bq, v.z)));
-      v.w = fmaf(er.w, fq, fmaf(cr.w, dq, fmaf(ar.w, bq, v.w)));
-      col[q4] = v;
+    float4* col0 = reinterpret_cast<float4*>(Ab) + q4;
+    for (int j0 = 0; j0 < K; j0 += 8) {
+      const int jn = min(8, K - j0);
+      float4 v[8];
+#pragma unroll
+      for (int jj = 0; jj < 8; jj++)
+        if (jj < jn) v[jj] = col0[(int64_t)(j0 + jj) * ld4];
+#pragma unroll
+      for (int jj = 0; jj < 8; jj++) {
+        if (jj < jn) {
+          const float bq = bs[j0 + jj], dq = ds[j0 + jj], fq = fs[j0 + jj];
+          v[jj].x = fmaf(er.x, fq, fmaf(cr.x, dq, fmaf(ar.x, bq, v[jj].x)));
+          v[jj].y = fmaf(er.y, fq, fmaf(cr.y, dq, fmaf(ar.y, bq, v[jj].y)));
+          v[jj].z = fmaf(er.z, fq, fmaf(cr.z, dq, fmaf(ar.z, bq, v[jj].z)));
+          v[jj].w = fmaf(er.w, fq, fmaf(cr.w, dq, fmaf(ar.w, bq, v[jj].w)));
+          col0[(int64_t)(j0 + jj) * ld4] = v[jj];
+        }
+      }
     }
   }
 }
@@ -313,6 +325,8 @@ __global__ void __launch_bounds__(kAT) k_rankN(TP<T> Ab_, int64_t ld, int K, int
     }
   }
 }
+// FP32, 16-byte aligned: four rows per thread; every thread loads its rows of the terms' vectors
+// once and walks all K columns, eight column loads in flight at a time.
 __global__ void __launch_bounds__(kAT) k_rankN4(TP<float> Ab_, int64_t ld, int K, int64_t dim4, RankTerms t) {
   const int tr = blockIdx.z;
   float* Ab = Ab_.at(tr);
@@ -323,37 +337,38 @@ __global__ void __launch_bounds__(kAT) k_rankN4(TP<float> Ab_, int64_t ld, int K
       t.c[q] = t.c[q] + (int64_t)tr * t.sc[q];
     }
   }
-  __shared__ float cs[5][8];
-  const int j0 = blockIdx.y * 8;
-  if (threadIdx.x < 40) {
-    const int q = threadIdx.x >> 3, jj = threadIdx.x & 7, j = j0 + jj;
-    cs[q][jj] = (q < t.n && j < K && j < t.K[q]) ? (float)(t.s[q] * t.c[q][j]) : 0.f;
+  __shared__ float cs[5][kTmaxLimit + 1];
+  for (int idx = threadIdx.x; idx < 5 * K; idx += blockDim.x) {
+    const int q = idx / K, j = idx % K;
+    cs[q][j] = (q < t.n && j < t.K[q]) ? (float)(t.s[q] * t.c[q][j]) : 0.f;
   }
   __syncthreads();
-  const int jn = min(K, j0 + 8) - j0;
+  const int64_t ld4 = ld / 4;
   for (int64_t q4 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q4 < dim4; q4 += (int64_t)gridDim.x * blockDim.x) {
     float4 vr[5];
 #pragma unroll
     for (int q = 0; q < 5; q++)
       vr[q] = (q < t.n) ? reinterpret_cast<const float4*>(t.v[q])[q4] : make_float4(0.f, 0.f, 0.f, 0.f);
-    float4* col0 = reinterpret_cast<float4*>(Ab + (int64_t)j0 * ld) + q4;
-    const int64_t ld4 = ld / 4;
-    float4 v[8];
+    float4* col0 = reinterpret_cast<float4*>(Ab) + q4;
+    for (int j0 = 0; j0 < K; j0 += 8) {
+      const int jn = min(8, K - j0);
+      float4 v[8];
 #pragma unroll
-    for (int jj = 0; jj < 8; jj++)   // the eight column loads in flight together
-      if (jj < jn) v[jj] = col0[(int64_t)jj * ld4];
+      for (int jj = 0; jj < 8; jj++)
+        if (jj < jn) v[jj] = col0[(int64_t)(j0 + jj) * ld4];
 #pragma unroll
-    for (int jj = 0; jj < 8; jj++) {
-      if (jj < jn) {
+      for (int jj = 0; jj < 8; jj++) {
+        if (jj < jn) {
 #pragma unroll
-        for (int q = 0; q < 5; q++) {
-          const float cq = cs[q][jj];
-          v[jj].x = fmaf(vr[q].x, cq, v[jj].x);
-          v[jj].y = fmaf(vr[q].y, cq, v[jj].y);
-          v[jj].z = fmaf(vr[q].z, cq, v[jj].z);
-          v[jj].w = fmaf(vr[q].w, cq, v[jj].w);
+          for (int q = 0; q < 5; q++) {
+            const float cq = cs[q][j0 + jj];
+            v[jj].x = fmaf(vr[q].x, cq, v[jj].x);
+            v[jj].y = fmaf(vr[q].y, cq, v[jj].y);
+            v[jj].z = fmaf(vr[q].z, cq, v[jj].z);
+            v[jj].w = fmaf(vr[q].w, cq, v[jj].w);
+          }
+          col0[(int64_t)(j0 + jj) * ld4] = v[jj];
         }
-        col0[(int64_t)jj * ld4] = v[jj];
       }
     }
   }
@@ -437,6 +452,77 @@ __global__ void __launch_bounds__(kAT) k_colpass4(TP<const float> A_, int64_t ld
   }
 }
 
+// Readers of the small matrices of the single-CTA kernels: S's upper triangle and the head
+// block of a stack (rows below the diagonal), from global memory or packed in shared memory.
+// Staged, each entry is read from global memory once, with coalesced loads, instead of once
+// per product term.
+struct SGlob {
+  const double* p;
+  int Tm;
+  __device__ __forceinline__ double operator()(int i, int j) const { return p[i + (int64_t)j * Tm]; }
+};
+struct SUpper {   // column j's rows 0..j at j (j + 1) / 2
+  const double* p;
+  __device__ __forceinline__ double operator()(int i, int j) const { return p[j * (j + 1) / 2 + i]; }
+};
+template <typename T>
+struct VGlob {
+  const T* p;
+  int64_t ld;
+  __device__ __forceinline__ T operator()(int i, int j) const { return p[i + (int64_t)j * ld]; }
+};
+template <typename T>
+struct VLower {   // column j's rows j..n-1 at j n - j (j - 1) / 2
+  const T* p;
+  int n;
+  __device__ __forceinline__ T operator()(int i, int j) const { return p[j * n - j * (j - 1) / 2 + (i - j)]; }
+};
+__host__ __device__ __forceinline__ int64_t packed_tri(int n) { return (int64_t)n * (n + 1) / 2; }
+// A[i, j] += f(i, j) over the entries of an n_i x n_j block (leading dim ld) with i <= j
+// (upper) or j <= i (lower), the CTA's threads over the entries in column order.  The entries
+// are distinct, so each thread issues four loads before its four stores instead of waiting for
+// a store before every next load.
+template <bool UPPER, typename E, typename F>
+__device__ __forceinline__ void tri_add(E* A, int64_t ld, int ni, int nj, F f) {
+  const int n = ni * nj, step = (int)blockDim.x;
+  for (int q0 = threadIdx.x; q0 < n; q0 += 4 * step) {
+    E v[4];
+    int ii[4], jj[4];
+    bool on[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      const int q = q0 + u * step;
+      ii[u] = q % ni;
+      jj[u] = q / ni;
+      on[u] = q < n && (UPPER ? ii[u] <= jj[u] : jj[u] <= ii[u]);
+      if (on[u]) v[u] = A[ii[u] + (int64_t)jj[u] * ld];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; u++)
+      if (on[u]) A[ii[u] + (int64_t)jj[u] * ld] = v[u] + (E)f(ii[u], jj[u]);
+  }
+}
+// Copy the K x K upper triangle of S (leading dim Tm) to dst (SUpper order), a warp per column.
+__device__ void stage_upper_sm(const double* __restrict__ S, int Tm, int K, double* dst) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = wid; j < K; j += nw)
+    for (int i = lane; i <= j; i += 32) dst[j * (j + 1) / 2 + i] = S[i + (int64_t)j * Tm];
+}
+// Copy rows j..n-1 of columns j < n of V (leading dim ld) to dst (VLower order).
+template <typename T>
+__device__ void stage_lower_sm(const T* __restrict__ V, int64_t ld, int n, T* dst) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = wid; j < n; j += nw)
+    for (int i = j + lane; i < n; i += 32) dst[j * n - j * (j - 1) / 2 + (i - j)] = V[i + (int64_t)j * ld];
+}
+// Dynamic shared memory of the staged single-CTA kernels: the packed upper triangle of a K x K
+// block of S, then (when sizeof_v > 0) the packed lower triangle of the K x K head of a stack.
+inline size_t staged_bytes(int K, int sizeof_v) {
+  const size_t s = (size_t)packed_tri(K) * 8;
+  return ((s + 15) & ~(size_t)15) + (size_t)packed_tri(K) * (size_t)sizeof_v;
+}
+constexpr size_t kStagedMax = 200 * 1024;   // larger blocks read S and V from global memory
+
 // Adjoint of the S-column recurrence of column k of a stack: S[:k, k] = c = -tau S_k a with
 // a = V_k^T u (recorded) and S[k, k] = tau = 2 / u^T u.  With cbar = Sbar[:k, k] and
 // taubar = Sbar[k, k] + cbar . c / tau:  abar = -tau S_k^T cbar (a = V^T u passes it on as
@@ -444,49 +530,55 @@ __global__ void __launch_bounds__(kAT) k_colpass4(TP<const float> A_, int64_t ld
 // tau = 2 / u^T u gives ubar += -tau^2 taubar u.  Writes coef[0..k) = abar, coef[k] =
 // -tau^2 taubar (the coefficients of ubar += V[:, 0..k] coef).  An identity column (tau = 0)
 // passes nothing.
-__device__ void rec_col_dev(const double* __restrict__ S, double* Sb, int Tm, int k, const double* __restrict__ a,
-                            double* coef) {
+template <typename SA>
+__device__ void rec_col_dev(SA S, double* Sb, int Tm, int k, const double* __restrict__ a, double* coef) {
   __shared__ double cb[kTmaxLimit + 1];
   __shared__ double tb;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const double tau = S[k + (int64_t)k * Tm];
+  const double tau = S(k, k);
   for (int i = threadIdx.x; i < k; i += blockDim.x) cb[i] = (tau != 0.0) ? Sb[i + (int64_t)k * Tm] : 0.0;
   if (wid == 0) {
     double s = 0.0;
-    for (int i = lane; i < k; i += 32) s = fma(Sb[i + (int64_t)k * Tm], S[i + (int64_t)k * Tm], s);
+    for (int i = lane; i < k; i += 32) s = fma(Sb[i + (int64_t)k * Tm], S(i, k), s);
     s = warp_sum(s);
     if (lane == 0) tb = (tau != 0.0) ? Sb[k + (int64_t)k * Tm] + s / tau : 0.0;
   }
   __syncthreads();
   for (int j = wid; j < k; j += nw) {   // abar_j = -tau sum_{i <= j} S[i, j] cbar_i
     double s = 0.0;
-    for (int i = lane; i <= j; i += 32) s = fma(S[i + (int64_t)j * Tm], cb[i], s);
+    for (int i = lane; i <= j; i += 32) s = fma(S(i, j), cb[i], s);
     s = warp_sum(s);
     if (lane == 0) coef[j] = -tau * s;
   }
   if (threadIdx.x == 0) coef[k] = -tau * tau * tb;
-  for (int idx = threadIdx.x; idx < k * k; idx += blockDim.x) {
-    const int i = idx % k, j = idx / k;
-    if (i <= j) Sb[i + (int64_t)j * Tm] += -tau * cb[i] * a[j];
-  }
+  tri_add<true>(Sb, Tm, k, k, [&](int i, int j) { return -tau * cb[i] * a[j]; });
 }
+template <bool STAGED>
 __global__ void __launch_bounds__(kSmallT) k_rec_col(TP<const double> S, TP<double> Sb, int Tm, int k,
                                                      TP<const double> a, TP<double> coef) {
   const int tr = blockIdx.z;
-  rec_col_dev(S.at(tr), Sb.at(tr), Tm, k, a.at(tr), coef.at(tr));
+  if constexpr (STAGED) {
+    extern __shared__ __align__(16) unsigned char adj_dsm[];
+    double* Su = (double*)adj_dsm;
+    stage_upper_sm(S.at(tr), Tm, k + 1, Su);
+    __syncthreads();
+    rec_col_dev(SUpper{Su}, Sb.at(tr), Tm, k, a.at(tr), coef.at(tr));
+  } else {
+    rec_col_dev(SGlob{S.at(tr), Tm}, Sb.at(tr), Tm, k, a.at(tr), coef.at(tr));
+  }
 }
 
 // out = scale S v (trans = 0) or scale S^T v (trans = 1), leading K x K block of the upper
 // triangular S (column-major, leading dim Tm): one warp per output, lanes over the sum.
-__device__ void tri_dev(const double* __restrict__ S, int Tm, int K, const double* __restrict__ v, double scale,
-                        int trans, double* out) {
+template <typename SA>
+__device__ void tri_dev(SA S, int K, const double* __restrict__ v, double scale, int trans, double* out) {
   const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int i = threadIdx.x >> 5; i < K; i += nw) {
     double s = 0.0;
     if (!trans) {
-      for (int j = i + lane; j < K; j += 32) s = fma(S[i + (int64_t)j * Tm], v[j], s);
+      for (int j = i + lane; j < K; j += 32) s = fma(S(i, j), v[j], s);
     } else {
-      for (int q = lane; q <= i; q += 32) s = fma(S[q + (int64_t)i * Tm], v[q], s);
+      for (int q = lane; q <= i; q += 32) s = fma(S(q, i), v[q], s);
     }
     s = warp_sum(s);
     if (lane == 0) out[i] = scale * s;
@@ -495,16 +587,13 @@ __device__ void tri_dev(const double* __restrict__ S, int Tm, int K, const doubl
 __global__ void __launch_bounds__(kSmallT) k_tri(TP<const double> S, int Tm, int K, TP<const double> v,
                                                  double scale, int trans, TP<double> out) {
   const int tr = blockIdx.z;
-  tri_dev(S.at(tr), Tm, K, v.at(tr), scale, trans, out.at(tr));
+  tri_dev(SGlob{S.at(tr), Tm}, K, v.at(tr), scale, trans, out.at(tr));
 }
 
 // Sb[i, j] += a[i] b[j] on the upper triangle i <= j < K (S has no free entries below).
 __device__ __forceinline__ void outer_upper_dev(double* Sb, int Tm, int K, const double* __restrict__ a,
                                                 const double* __restrict__ b) {
-  for (int idx = threadIdx.x; idx < K * K; idx += blockDim.x) {
-    const int i = idx % K, j = idx / K;
-    if (i <= j) Sb[i + (int64_t)j * Tm] += a[i] * b[j];
-  }
+  tri_add<true>(Sb, Tm, K, K, [&](int i, int j) { return a[i] * b[j]; });
 }
 __global__ void __launch_bounds__(kAT) k_outer_upper(TP<double> Sb, int Tm, int K, TP<const double> a,
                                                      TP<const double> b) {
@@ -526,26 +615,25 @@ __global__ void k_head_alpha(TP<const double> phead_, int k, TP<const double> rs
 // b = S a (for Vbar += -ybar b^T, done by the caller), cbar = Delta (ybar + V S^T bb) on the
 // first nc rows, and adds Sbar += bb a^T and Vbar[:nc, :] += (Delta c) (S^T bb)^T.  One warp
 // per output, lanes over the sums.
-template <typename T>
-__device__ void out_small_dev(const T* __restrict__ V, int64_t ld, int Ke, int nc, const double* __restrict__ S,
-                              int Tm, const double* __restrict__ dpre, const double* __restrict__ c,
-                              const double* __restrict__ bb, const T* __restrict__ ybd, double* Sb, T* Vb,
-                              double* b_out, double* cbar) {
+template <typename T, typename VA, typename SA>
+__device__ void out_small_dev(VA V, T* Vb, int64_t ld, int Ke, int nc, SA S, int Tm, const double* __restrict__ dpre,
+                              const double* __restrict__ c, const double* __restrict__ bb,
+                              const T* __restrict__ ybd, double* Sb, double* b_out, double* cbar) {
   __shared__ double cp[kTmaxLimit + 1], a[kTmaxLimit + 1], ab[kTmaxLimit + 1];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int i = threadIdx.x; i < nc; i += blockDim.x) cp[i] = dpre[i + 1] * c[i];
   __syncthreads();
   for (int j = wid; j < Ke; j += nw) {   // a = V^T Delta c (rows j..nc-1 of column j)
     double s = 0.0;
-    for (int i = j + lane; i < nc; i += 32) s = fma((double)V[i + (int64_t)j * ld], cp[i], s);
+    for (int i = j + lane; i < nc; i += 32) s = fma((double)V(i, j), cp[i], s);
     s = warp_sum(s);
     if (lane == 0) a[j] = s;
   }
   __syncthreads();
   for (int i = wid; i < Ke; i += nw) {   // b = S a, abar = S^T bb
     double sb = 0.0, sa = 0.0;
-    for (int j = i + lane; j < Ke; j += 32) sb = fma(S[i + (int64_t)j * Tm], a[j], sb);
-    for (int q = lane; q <= i; q += 32) sa = fma(S[q + (int64_t)i * Tm], bb[q], sa);
+    for (int j = i + lane; j < Ke; j += 32) sb = fma(S(i, j), a[j], sb);
+    for (int q = lane; q <= i; q += 32) sa = fma(S(q, i), bb[q], sa);
     sb = warp_sum(sb);
     sa = warp_sum(sa);
     if (lane == 0) {
@@ -554,27 +642,19 @@ __device__ void out_small_dev(const T* __restrict__ V, int64_t ld, int Ke, int n
     }
   }
   __syncthreads();
-  for (int idx = threadIdx.x; idx < Ke * Ke; idx += blockDim.x) {
-    const int i = idx % Ke, j = idx / Ke;
-    if (i <= j) Sb[i + (int64_t)j * Tm] += bb[i] * a[j];
-  }
-  // cbar = Delta (ybar + V abar) on rows < nc: a row per thread, so that a warp reads (and
-  // updates) consecutive rows of each column
+  tri_add<true>(Sb, Tm, Ke, Ke, [&](int i, int j) { return bb[i] * a[j]; });
+  // Vbar[:nc, :] += (Delta c) abar^T on the stored (lower) part
+  tri_add<false>(Vb, ld, nc, Ke, [&](int i, int j) { return cp[i] * ab[j]; });
+  // cbar = Delta (ybar + V abar) on rows < nc: a row per thread
   for (int i = threadIdx.x; i < nc; i += blockDim.x) {
     const int jm = min(i, Ke - 1);
-    const double ci = cp[i];
     double s0 = 0.0, s1 = 0.0;
     int j = 0;
     for (; j + 1 <= jm; j += 2) {
-      s0 = fma((double)V[i + (int64_t)j * ld], ab[j], s0);
-      s1 = fma((double)V[i + (int64_t)(j + 1) * ld], ab[j + 1], s1);
-      Vb[i + (int64_t)j * ld] += (T)(ci * ab[j]);
-      Vb[i + (int64_t)(j + 1) * ld] += (T)(ci * ab[j + 1]);
+      s0 = fma((double)V(i, j), ab[j], s0);
+      s1 = fma((double)V(i, j + 1), ab[j + 1], s1);
     }
-    if (j <= jm) {
-      s0 = fma((double)V[i + (int64_t)j * ld], ab[j], s0);
-      Vb[i + (int64_t)j * ld] += (T)(ci * ab[j]);
-    }
+    if (j <= jm) s0 = fma((double)V(i, j), ab[j], s0);
     cbar[i] = dpre[i + 1] * ((double)ybd[i] + (s0 + s1));
   }
 }
@@ -584,14 +664,14 @@ __global__ void __launch_bounds__(kSmallT) k_out_small(TP<const T> V, int64_t ld
                                                        TP<const double> c, TP<const double> bb, TP<const T> ybd,
                                                        TP<double> Sb, TP<T> Vb, TP<double> b_out, TP<double> cbar) {
   const int tr = blockIdx.z;
-  out_small_dev<T>(V.at(tr), ld, Ke, nc, S.at(tr), Tm, dpre.at(tr), c.at(tr), bb.at(tr), ybd.at(tr), Sb.at(tr),
-                   Vb.at(tr), b_out.at(tr), cbar.at(tr));
+  out_small_dev<T>(VGlob<T>{V.at(tr), ld}, Vb.at(tr), ld, Ke, nc, SGlob{S.at(tr), Tm}, Tm, dpre.at(tr), c.at(tr),
+                   bb.at(tr), ybd.at(tr), Sb.at(tr), b_out.at(tr), cbar.at(tr));
 }
 
 // Haar output side in one CTA: with bb = -V^T ybar (the column pass, reduced over its row blocks
 // by k_colreduce), c = [p_head; alpha], the output-product adjoint (k_out_small) and the S
 // recurrence of the step's random column (k_rec_col, after the Sbar update it depends on).
-template <typename T>
+template <typename T, bool STAGED>
 __global__ void __launch_bounds__(kSmallT) k_out_haar_adj(TP<const T> V_,
                                                           int64_t ld, int Ke, TP<const double> S_, int Tm,
                                                           TP<const double> dpre_, TP<const double> phead_,
@@ -615,10 +695,22 @@ __global__ void __launch_bounds__(kSmallT) k_out_haar_adj(TP<const T> V_,
   double* au = au_.at(tr);
   const int k = Ke - 1;
   for (int i = threadIdx.x; i <= k; i += blockDim.x) cv[i] = (i < k) ? phead[i] : rs[1];
-  __syncthreads();
-  out_small_dev<T>(V, ld, Ke, Ke, S, Tm, dpre, cv, bb, ybd, Sb, Vb, bo, cbar);
-  __syncthreads();
-  rec_col_dev(S, Sb, Tm, k, rag, au);
+  if constexpr (STAGED) {   // S's upper triangle and V's head block in shared memory
+    extern __shared__ __align__(16) unsigned char adj_dsm[];
+    double* Su = (double*)adj_dsm;
+    T* Vl = (T*)(adj_dsm + ((packed_tri(Ke) * 8 + 15) & ~(int64_t)15));
+    stage_upper_sm(S, Tm, Ke, Su);
+    stage_lower_sm<T>(V, ld, Ke, Vl);
+    __syncthreads();
+    out_small_dev<T>(VLower<T>{Vl, Ke}, Vb, ld, Ke, Ke, SUpper{Su}, Tm, dpre, cv, bb, ybd, Sb, bo, cbar);
+    __syncthreads();
+    rec_col_dev(SUpper{Su}, Sb, Tm, k, rag, au);
+  } else {
+    __syncthreads();
+    out_small_dev<T>(VGlob<T>{V, ld}, Vb, ld, Ke, Ke, SGlob{S, Tm}, Tm, dpre, cv, bb, ybd, Sb, bo, cbar);
+    __syncthreads();
+    rec_col_dev(SGlob{S, Tm}, Sb, Tm, k, rag, au);
+  }
 }
 
 // The step's record (adj_record_after) in one launch: z (nz), w, p_head, V_D^T u (kD each),
@@ -647,6 +739,7 @@ __global__ void __launch_bounds__(kAT) k_adj_record(TP<double> r_, int64_t L, TP
 
 // Data side after the column pass of qbar in one CTA: with wbar = -V^T qbar (reduced by
 // k_colreduce), zbar = S wbar, Sbar += z wbar^T.
+template <bool STAGED>
 __global__ void __launch_bounds__(kSmallT) k_data_small(int K, TP<const double> S_, int Tm, TP<const double> z_,
                                                         TP<const double> wb_, TP<double> zb_, TP<double> Sb_) {
   const int tr = blockIdx.z;
@@ -655,7 +748,15 @@ __global__ void __launch_bounds__(kSmallT) k_data_small(int K, TP<const double> 
   const double* wb = wb_.at(tr);
   double* zb = zb_.at(tr);
   double* Sb = Sb_.at(tr);
-  tri_dev(S, Tm, K, wb, 1.0, 0, zb);
+  if constexpr (STAGED) {
+    extern __shared__ __align__(16) unsigned char adj_dsm[];
+    double* Su = (double*)adj_dsm;
+    stage_upper_sm(S, Tm, K, Su);
+    __syncthreads();
+    tri_dev(SUpper{Su}, K, wb, 1.0, 0, zb);
+  } else {
+    tri_dev(SGlob{S, Tm}, K, wb, 1.0, 0, zb);
+  }
   outer_upper_dev(Sb, Tm, K, z, wb);
 }
 
@@ -773,7 +874,7 @@ void rankN(const Ctx& c, TP<T> Ab, int64_t ld, int K, int64_t dim, const RankTer
   bool al = sizeof(T) == 4 && dim % 4 == 0 && ld % 4 == 0 && al16tp(Ab);
   for (int q = 0; q < t.n; q++) al = al && al16tp(TP<const T>{(const T*)t.v[q], t.sv[q]});
   if (al) {
-    dim3 g4(rows_grid(c.st, dim / 4), (unsigned)((K + 7) / 8), c.nz);
+    dim3 g4(rows_grid(c.st, dim / 4), 1, c.nz);
     k_rankN4<<<g4, kAT, 0, c.s>>>(TP<float>{(float*)Ab.p, Ab.s}, ld, K, dim / 4, t);
     return;
   }
@@ -788,7 +889,7 @@ void rank(const Ctx& c, TP<T> Ab, int64_t ld, int K, int64_t dim, TP<const T> a,
           int Kf = 0) {
   if (K <= 0) return;
   if (sizeof(T) == 4 && dim % 4 == 0 && ld % 4 == 0 && al16tp(Ab) && al16tp(a) && al16tp(cc) && al16tp(e)) {
-    dim3 g4(rows_grid(c.st, dim / 4), (unsigned)((K + 7) / 8), c.nz);
+    dim3 g4(rows_grid(c.st, dim / 4), 1, c.nz);
     k_rank4<<<g4, kAT, 0, c.s>>>(TP<float>{(float*)Ab.p, Ab.s}, ld, K, dim / 4,
                                  TP<const float>{(const float*)a.p, a.s}, b, sb,
                                  TP<const float>{(const float*)cc.p, cc.s}, d, sd,
@@ -841,8 +942,9 @@ int adj_step(hd_state* st, const void* ybar, const void* x_in, void* xbar) {
   const Ctx c{st, st->stream, st->count};
   const int64_t L = A.dmax;
   T* vec = (T*)A.vec;
+  const int par = t & 1;   // the copy of qbar, zbar and E of this step's parity
   const TP<T> ub{vec + kVub * L, A.vec_stride};
-  const TP<T> qb{vec + kVqb * L, A.vec_stride};
+  const TP<T> qb{vec + (par ? kVqb2 : kVqb) * L, A.vec_stride};
   const TP<T> gd{vec + kVg * L, A.vec_stride};
   // the step input: the caller's (packed) or the recorded one (slot t - 1, packed)
   const TP<const T> xd = x_in ? TP<const T>{(const T*)x_in, nd}
@@ -850,7 +952,8 @@ int adj_step(hd_state* st, const void* ybar, const void* x_in, void* xbar) {
   const TP<const T> ybd{(const T*)ybar, ne};
   const TP<T> xb{(T*)xbar, nd};
   auto sm = [&](int slot) { return TP<double>{A.small + (int64_t)slot * A.small_ld, A.small_stride}; };
-  const TP<double> bb = sm(kSbb), bo = sm(kSb), cb = sm(kScb), zb = sm(kSzb), wb = sm(kSwb), E = sm(kSE);
+  const TP<double> bb = sm(kSbb), bo = sm(kSb), cb = sm(kScb), zb = sm(par ? kSzb2 : kSzb), wb = sm(kSwb),
+                   E = sm(par ? kSE2 : kSE);
   const TP<double> cv = sm(kSc), hb = sm(kShb), au = sm(kSau), bu = sm(kSbu), bbu = sm(kSbbu), abu = sm(kSabu);
   const TP<double> part{A.part, A.part_stride};
   const unsigned gv = rows_grid(st, std::max(nd, ne));
@@ -895,6 +998,15 @@ int adj_step(hd_state* st, const void* ybar, const void* x_in, void* xbar) {
     pending_terms(rt);
     rankN<T>(c, TP<T>{(T*)A.Vbar[s0], A.vbar_stride[s0]}, td.st[s0].ld, K0, st->dims[s0][0], rt);
   }
+  // Haar: the data side (cd) runs on the second stream beside the output side (c).  It needs
+  // the output side only for cbar (the event ev_mid); the two sides write different stacks'
+  // Sbar and Vbar, different small slots, and the partial-sum buffer only after ev_mid.
+  const bool two = haar && A.aux != nullptr;
+  const Ctx cd = two ? Ctx{st, A.aux, c.nz} : c;
+  if (two) {
+    cudaEventRecord(A.ev_fork, c.s);
+    cudaStreamWaitEvent(A.aux, A.ev_fork, 0);
+  }
 
   // output product
   if (haar) {
@@ -902,8 +1014,14 @@ int adj_step(hd_state* st, const void* ybar, const void* x_in, void* xbar) {
     // bb = -V_N^T ybar, the output-product adjoint, and the S recurrence of this step's random
     // column (L_t = H_t(g_t), column kD of V_N)
     colpass<T>(c, Ve, Se.ld, Ke, ne, ybd, -1.0, bb);
-    k_out_haar_adj<T><<<dim3(1, 1, c.nz), kSmallT, 0, c.s>>>(Ve, Se.ld, Ke, SeS, Tm, Sep, phead, rs,
-                                                             cv, bb, ybd, Sbe, Vbe, bo, cb, rag, au);
+    const size_t sb_out = staged_bytes(Ke, (int)sizeof(T));
+    if (sb_out <= kStagedMax)
+      k_out_haar_adj<T, true><<<dim3(1, 1, c.nz), kSmallT, sb_out, c.s>>>(Ve, Se.ld, Ke, SeS, Tm, Sep, phead, rs,
+                                                                         cv, bb, ybd, Sbe, Vbe, bo, cb, rag, au);
+    else
+      k_out_haar_adj<T, false><<<dim3(1, 1, c.nz), kSmallT, 0, c.s>>>(Ve, Se.ld, Ke, SeS, Tm, Sep, phead, rs,
+                                                                      cv, bb, ybd, Sbe, Vbe, bo, cb, rag, au);
+    if (two) cudaEventRecord(A.ev_mid, c.s);   // cbar is ready
     RankTerms rt{};
     rt.v[0] = ybd.p; rt.c[0] = bo.p; rt.s[0] = -1.0; rt.K[0] = Ke; rt.sv[0] = ybd.s; rt.sc[0] = bo.s;
     rt.v[1] = Ve.p + (int64_t)kD * Se.ld; rt.c[1] = au.p; rt.s[1] = 1.0; rt.K[1] = Ke; rt.sv[1] = Ve.s;
@@ -941,21 +1059,30 @@ int adj_step(hd_state* st, const void* ybar, const void* x_in, void* xbar) {
 
   // the data-side reflector of this step (column kD of V_D): ubar = Vbar[:, kD] + the S
   // recurrence's V[:, 0..kD] coef (E = [abar; -tau^2 taubar])
-  k_rec_col<<<dim3(1, 1, c.nz), kSmallT, 0, c.s>>>(SdS, Sbd, Tm, kD, ra, E);
-  rowpass<T>(c, ub, TP<const T>{(const T*)Vbd.p + (int64_t)kD * Sd.ld, Vbd.s}, 1.0, Vd, Sd.ld, kD + 1, cst(E), 1.0,
+  const size_t sb_rec = staged_bytes(kD + 1, 0);
+  if (sb_rec <= kStagedMax)
+    k_rec_col<true><<<dim3(1, 1, cd.nz), kSmallT, sb_rec, cd.s>>>(SdS, Sbd, Tm, kD, ra, E);
+  else
+    k_rec_col<false><<<dim3(1, 1, cd.nz), kSmallT, 0, cd.s>>>(SdS, Sbd, Tm, kD, ra, E);
+  rowpass<T>(cd, ub, TP<const T>{(const T*)Vbd.p + (int64_t)kD * Sd.ld, Vbd.s}, 1.0, Vd, Sd.ld, kD + 1, cst(E), 1.0,
              nd, cnone, 0, 0);
-  k_pbar<T><<<dim3(gp, 1, c.nz), kAT, 0, c.s>>>(qb, ucol, cst(ub), cst(cb), rs, kD, Sdp, nd);
+  if (two) cudaStreamWaitEvent(cd.s, A.ev_mid, 0);   // k_pbar reads cbar
+  k_pbar<T><<<dim3(gp, 1, cd.nz), kAT, 0, cd.s>>>(qb, ucol, cst(ub), cst(cb), rs, kD, Sdp, nd);
 
   // the data product p = Delta (I - V S^T V^T) x
   if (kD > 0) {   // wbar = -V_D^T qbar, zbar = S wbar, Sbar += z wbar^T
-    colpass<T>(c, Vd, Sd.ld, kD, nd, cst(qb), -1.0, wb);
-    k_data_small<<<dim3(1, 1, c.nz), kSmallT, 0, c.s>>>(kD, SdS, Tm, z, cst(wb), zb, Sbd);
+    colpass<T>(cd, Vd, Sd.ld, kD, nd, cst(qb), -1.0, wb);
+    const size_t sb_dat = staged_bytes(kD, 0);
+    if (sb_dat <= kStagedMax)
+      k_data_small<true><<<dim3(1, 1, cd.nz), kSmallT, sb_dat, cd.s>>>(kD, SdS, Tm, z, cst(wb), zb, Sbd);
+    else
+      k_data_small<false><<<dim3(1, 1, cd.nz), kSmallT, 0, cd.s>>>(kD, SdS, Tm, z, cst(wb), zb, Sbd);
   }
-  rowpass<T>(c, xb, cst(qb), 1.0, Vd, Sd.ld, kD, cst(zb), 1.0, nd, cnone, 0, 0);
+  rowpass<T>(cd, xb, cst(qb), 1.0, Vd, Sd.ld, kD, cst(zb), 1.0, nd, cnone, 0, 0);
   if (!haar && kN > 0) {
     const TP<const T> Bd{(const T*)td.basis[d], ss.B[d]};
-    rowpass<T>(c, xb, tnone, 0.0, Bd, td.ldb[d], kN, cst(hb), 1.0, nd, cnone, 0, 1);
-    rank<T>(c, TP<T>{(T*)A.Bbar[d], A.bbar_stride[d]}, td.ldb[d], kN, nd, xd, cst(hb), 1.0);
+    rowpass<T>(cd, xb, tnone, 0.0, Bd, td.ldb[d], kN, cst(hb), 1.0, nd, cnone, 0, 1);
+    rank<T>(cd, TP<T>{(T*)A.Bbar[d], A.bbar_stride[d]}, td.ldb[d], kN, nd, xd, cst(hb), 1.0);
   }
   // Vbar_D += -qbar w^T + x zbar^T + u abar^T.  Haar with the recorded x_t and the next reverse
   // step on the other product: held back for that step's output-side pass over this stack
@@ -969,7 +1096,11 @@ int adj_step(hd_state* st, const void* ybar, const void* x_in, void* xbar) {
     pd.v[1] = xd.p; pd.c[1] = zb.p; pd.sc[1] = 1.0; pd.Kq[1] = kD; pd.sv[1] = xd.s; pd.scs[1] = zb.s;
     pd.v[2] = ucol.p; pd.c[2] = E.p; pd.sc[2] = 1.0; pd.Kq[2] = kD; pd.sv[2] = ucol.s; pd.scs[2] = E.s;
   } else {
-    rank<T>(c, Vbd, Sd.ld, kD, nd, cst(qb), w, -1.0, xd, cst(zb), 1.0, ucol, cst(E), 1.0, kD);   // + u abar^T
+    rank<T>(cd, Vbd, Sd.ld, kD, nd, cst(qb), w, -1.0, xd, cst(zb), 1.0, ucol, cst(E), 1.0, kD);   // + u abar^T
+  }
+  if (two) {   // join: the caller's stream waits for the data side
+    cudaEventRecord(A.ev_join, cd.s);
+    cudaStreamWaitEvent(c.s, A.ev_join, 0);
   }
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return cuda_fail(st, err);
@@ -1053,6 +1184,15 @@ HD_API int hd_adjoint_enable(hd_state* st, int flags) {
   for (int i = 1; i < st->count; i++)
     if (st->dims[0][i] != st->dims[0][0] || st->dims[1][i] != st->dims[1][0]) return HD_ERR_ARG;
   if (cudaSetDevice(st->device) != cudaSuccess) return cuda_fail(st, cudaErrorInvalidDevice);
+  {   // the staged single-CTA kernels take up to kStagedMax bytes of dynamic shared memory
+    const int b = (int)kStagedMax;
+    cudaError_t e = cudaFuncSetAttribute(k_out_haar_adj<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_out_haar_adj<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rec_col<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_data_small<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e != cudaSuccess) return cuda_fail(st, e);
+  }
   const int nt = st->count;
   if (!st->adj) {
     AdjState* A = new (std::nothrow) AdjState();
@@ -1090,6 +1230,13 @@ HD_API int hd_adjoint_enable(hd_state* st, int flags) {
     if (!A->vec || !A->small || !A->part || !A->rec) return HD_ERR_OOM;
   }
   AdjState& A = *st->adj;
+  if (!A.aux && st->ens == HD_HAAR) {   // the data side's stream (Haar reverse steps)
+    if (cudaStreamCreateWithFlags(&A.aux, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&A.ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&A.ev_mid, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&A.ev_join, cudaEventDisableTiming) != cudaSuccess)
+      return cuda_fail(st, cudaGetLastError());
+  }
   A.record_x = (flags & HD_ADJ_RECORD_X) ? 1 : 0;
   if (A.record_x && !A.X) {
     A.X = dalloc(st, (size_t)A.ldx * st->Tm * st->esz);

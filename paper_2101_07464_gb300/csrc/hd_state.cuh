@@ -67,6 +67,16 @@ struct AdjState {
     int64_t sv[3] = {0, 0, 0};   // trial strides of v and c
     int64_t scs[3] = {0, 0, 0};
   } pend;
+  // Haar: the data side of a reverse step runs on a second stream beside the output side
+  // (fork at the start, cbar hand-over in the middle, join at the end)
+  cudaStream_t aux = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_mid = nullptr, ev_join = nullptr;
+  ~AdjState() {
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_mid) cudaEventDestroy(ev_mid);
+    if (ev_join) cudaEventDestroy(ev_join);
+    if (aux) cudaStreamDestroy(aux);
+  }
 };
 
 }  // namespace hd

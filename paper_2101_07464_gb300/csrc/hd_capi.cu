@@ -478,29 +478,45 @@ bool graph_matches(const hd_state* st, const hd_run_spec* sp) {
 }
 
 // CTA map of one space: every trial gets ceil(nsub_i / spc) CTAs of spc 32-row sub-tiles.
+// The trials' CTA ranges are laid out largest trial first.  The GPU hands out the CTAs of a
+// launch roughly in index order, so the longest CTAs start first and the short ones fill in
+// behind them (the longest-processing-time-first rule), instead of a large trial at the end
+// of the batch running alone.  cta0[i] is trial i's first CTA and nct[i] its number of CTAs
+// (contiguous: a CTA's local index is blockIdx - cta0[trial]); cta0[count] is the total.
 bool build_map(hd_state* st, int s, int64_t spc, CtaMap* out) {
   const int count = st->count;
-  std::vector<int> cta0(count + 1), spcv(count);
+  std::vector<int> cta0(count + 1), spcv(count), nct(count), order(count);
   std::vector<int> ct;
-  cta0[0] = 0;
   for (int i = 0; i < count; i++) {
     const int64_t nsub = (st->dims[s][i] + 31) / 32;
-    const int n_i = (int)((nsub + spc - 1) / spc);
+    nct[i] = (int)((nsub + spc - 1) / spc);
     spcv[i] = (int)spc;
-    for (int c = 0; c < n_i; c++) ct.push_back(i);
-    cta0[i + 1] = cta0[i] + n_i;
-    st->maxncta = std::max(st->maxncta, n_i);
+    order[i] = i;
+    st->maxncta = std::max(st->maxncta, nct[i]);
   }
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return st->dims[s][a] > st->dims[s][b]; });
+  int next = 0;
+  for (int q = 0; q < count; q++) {
+    const int i = order[q];
+    cta0[i] = next;
+    for (int c = 0; c < nct[i]; c++) ct.push_back(i);
+    next += nct[i];
+  }
+  cta0[count] = next;
   int* d_ct = (int*)dalloc(st, ct.size() * sizeof(int));
   int* d_c0 = (int*)dalloc(st, cta0.size() * sizeof(int));
+  int* d_nc = (int*)dalloc(st, nct.size() * sizeof(int));
   int* d_sp = (int*)dalloc(st, spcv.size() * sizeof(int));
-  if (!d_ct || !d_c0 || !d_sp) return false;
+  if (!d_ct || !d_c0 || !d_nc || !d_sp) return false;
   if (cudaMemcpy(d_ct, ct.data(), ct.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(d_c0, cta0.data(), cta0.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(d_nc, nct.data(), nct.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(d_sp, spcv.data(), spcv.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
     return false;
   out->cta_trial = d_ct;
   out->cta0 = d_c0;
+  out->nct = d_nc;
   out->spc = d_sp;
   out->ctas = cta0[count];
   return true;

@@ -139,7 +139,7 @@ __device__ __forceinline__ StepPlan<T> make_plan(const BatchStep<T>& b, int spac
   const CtaMap& m = b.map[space];
   c.trial = m.cta_trial[vb];
   const int c0 = m.cta0[c.trial];
-  c.ncta = m.cta0[c.trial + 1] - c0;
+  c.ncta = m.nct[c.trial];
   c.local = vb - c0;
   c.spc = m.spc[c.trial];
   const TrialDesc& td = b.desc[c.trial];
@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(kThreads) k_first_draw(BatchStep<T> b, int spa
   const CtaMap& m = b.map[space];
   c.trial = m.cta_trial[blockIdx.x];
   const int c0 = m.cta0[c.trial];
-  c.ncta = m.cta0[c.trial + 1] - c0;
+  c.ncta = m.nct[c.trial];
   c.local = (int)blockIdx.x - c0;
   c.spc = m.spc[c.trial];
   const TrialDesc& td = b.desc[c.trial];

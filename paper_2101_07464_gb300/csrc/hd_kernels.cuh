@@ -165,7 +165,8 @@ struct TrialDesc {
 
 struct CtaMap {
   const int* cta_trial; // [ctas]: trial of each CTA
-  const int* cta0;      // [count + 1]: first CTA of each trial
+  const int* cta0;      // [count]: first CTA of each trial (trials laid out largest first)
+  const int* nct;       // [count]: CTAs of each trial (contiguous from cta0)
   const int* spc;       // [count]: sub-tiles per CTA of each trial
   int ctas;             // CTAs of a launch over this space
 };

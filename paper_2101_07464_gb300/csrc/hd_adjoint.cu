@@ -232,9 +232,6 @@ __global__ void __launch_bounds__(kAT) k_rank(TP<T> Ab_, int64_t ld, int K, int6
   }
 }
 
-// FP32 with 16-byte aligned vectors: the same passes four rows per thread (float4 accesses).
-__host__ __device__ __forceinline__ bool al16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
-
 // FP32, 16-byte aligned: four rows per thread; every thread loads its rows of a, c, e once and
 // walks all K columns, eight column loads in flight at a time.
 __global__ void __launch_bounds__(kAT) k_rank4(TP<float> Ab_, int64_t ld, int K, int64_t dim4, TP<const float> a_,

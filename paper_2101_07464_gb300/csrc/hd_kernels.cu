@@ -859,16 +859,18 @@ __device__ __forceinline__ void wt_col_pair(const T* buf, int ncol, int m, const
   }
 }
 
-// Few columns (ncol <= 16): Q = 32 / C lanes per column (C = 4, 8 or 16 column slots),
-// lane = j Q + q.  Lane (j, q) takes NCH / Q chunks of column j, chunk q D + (i mod D) +
-// 8 (i div D) at step i (D = 8 / Q), so that the 8 lanes of every quarter warp read 8
-// distinct 16-byte bank groups.  Its running sums stay in acc[r][0]; wt_flush_cols adds the
-// Q lanes of a column.
-__device__ __forceinline__ int wt_col_slots(int ncol) {
+// The FP32 column pass (wt_cols in FP32).  Few columns (ncol <= 16): Q = 32 / C lanes per
+// column (C = 4, 8 or 16 column slots), lane = j Q + q.  Lane (j, q) takes NCH / Q chunks of
+// column j, chunk q D + (i mod D) + 8 (i div D) at step i (D = 8 / Q), so that the 8 lanes of
+// every quarter warp read 8 distinct 16-byte bank groups.  Its running sums stay in acc[r][0];
+// wt_flush_cols_f32 adds the Q lanes of a column.  (The same scheme as wt_cols_seg, kept apart:
+// the FP32 sweeps, bound by instruction issue with 128 registers, lose a few per cent to the
+// register allocation that the shared form leads to.)
+__device__ __forceinline__ int wt_col_slots_f32(int ncol) {
   return ncol <= 4 ? 4 : (ncol <= 8 ? 8 : (ncol <= 16 ? 16 : 0));
 }
 template <typename T, int NR, int Q>
-__device__ __forceinline__ void wt_cols_grouped(const T* buf, int ncol, const T* rhs0, const T* rhs1,
+__device__ __forceinline__ void wt_cols_grouped_f32(const T* buf, int ncol, const T* rhs0, const T* rhs1,
                                                 T (&acc)[NR][kColsPerLane]) {
   constexpr int NCH = WT<T>::NCH, VEC = WT<T>::VEC, S = NCH / Q, D = 8 / Q;
   const int lane = threadIdx.x & 31, j = lane / Q, q = lane % Q;
@@ -894,19 +896,17 @@ __device__ __forceinline__ void wt_cols_grouped(const T* buf, int ncol, const T*
   for (int r = 0; r < NR; r++) acc[r][0] = s[r];
 }
 
-// Column owner: acc[r][m] += sum_i V[i, lane + 32 m] rhs_r[i] over the 32 rows, m < 8.
-// Logical chunk c of column j sits at slot (c + j) mod NCH, and j mod NCH = lane mod NCH for
-// every m, so the NCH chunk offsets are per-lane constants.  Columns go two per lane while a
-// second one exists anywhere in the warp, then one; up to 16 columns use wt_cols_grouped.
-// acc is in the storage type and covers at most kColFlush sub-tiles (wt_flush_cols).
+// More than 16 columns: column lane + 32 m in slot m, two per lane while a second one exists
+// anywhere in the warp, then one (a partial last group shares the right-hand-side loads of
+// the group before it, which issues fewer instructions than tail segments would).
 template <typename T, int NR>
-__device__ __forceinline__ void wt_cols(const T* buf, int ncol, const T* rhs0, const T* rhs1,
+__device__ __forceinline__ void wt_cols_f32(const T* buf, int ncol, const T* rhs0, const T* rhs1,
                                         T (&acc)[NR][kColsPerLane]) {
   constexpr int NCH = WT<T>::NCH, VEC = WT<T>::VEC;
-  switch (wt_col_slots(ncol)) {   // uniform over the launch
-    case 4: wt_cols_grouped<T, NR, 8>(buf, ncol, rhs0, rhs1, acc); return;
-    case 8: wt_cols_grouped<T, NR, 4>(buf, ncol, rhs0, rhs1, acc); return;
-    case 16: wt_cols_grouped<T, NR, 2>(buf, ncol, rhs0, rhs1, acc); return;
+  switch (wt_col_slots_f32(ncol)) {   // uniform over the launch
+    case 4: wt_cols_grouped_f32<T, NR, 8>(buf, ncol, rhs0, rhs1, acc); return;
+    case 8: wt_cols_grouped_f32<T, NR, 4>(buf, ncol, rhs0, rhs1, acc); return;
+    case 16: wt_cols_grouped_f32<T, NR, 2>(buf, ncol, rhs0, rhs1, acc); return;
     default: break;
   }
   const int lane = threadIdx.x & 31;
@@ -921,6 +921,106 @@ __device__ __forceinline__ void wt_cols(const T* buf, int ncol, const T* rhs0, c
     else
       wt_col_pair<T, NR, false>(buf, ncol, m, coff, rhs0, rhs1, acc);
   }
+}
+
+// The FP64 column pass.  Its layout over ncol columns (uniform over the launch): groups of 32
+// columns go one column per lane, column lane + 32 m in acc slot m < mfull.  Up to 16 columns,
+// and the ncol mod 32 columns after the whole groups, form instead at most two tail segments of
+// C = 4, 8 or 16 column slots each, with Q = 32 / C lanes per column: segment A (columns
+// 32 mfull .. + min(rem, 16)) in slot kColsPerLane - 1, segment B (the columns past 16 of a
+// longer tail) in slot kColsPerLane - 2.  A tail segment costs C FMA instructions per
+// right-hand side and sub-tile, where a partial group of 32 costs 32: the FP64 sweeps are bound
+// by the FP64 pipe, which takes a warp's FMA instruction whole however few of its lanes are
+// active.  With mfull = 7 and more than 16 tail columns there is no second free slot: the tail
+// is then a partial eighth group (its lanes past ncol idle).
+struct ColLayout {
+  int mfull, ca, cb;
+};
+__device__ __forceinline__ int wt_col_slots(int ncol) {
+  return ncol <= 4 ? 4 : (ncol <= 8 ? 8 : 16);
+}
+__device__ __forceinline__ ColLayout wt_col_layout(int ncol) {
+  const int rem = ncol & 31;
+  if (ncol <= 16) return ColLayout{0, ncol > 0 ? wt_col_slots(ncol) : 0, 0};
+  if (rem == 0) return ColLayout{ncol >> 5, 0, 0};
+  if (rem <= 16) return ColLayout{ncol >> 5, wt_col_slots(rem), 0};
+  if ((ncol >> 5) + 2 <= kColsPerLane) return ColLayout{ncol >> 5, 16, wt_col_slots(rem - 16)};
+  return ColLayout{(ncol + 31) >> 5, 0, 0};
+}
+
+// A tail segment: columns j0 + j, j < nseg <= C = 32 / Q, lane = j Q + q.  Lane (j, q) takes
+// NCH / Q chunks of column j, chunk q D + (i mod D) + 8 (i div D) at step i (D = 8 / Q), so
+// that the 8 lanes of every quarter warp read 8 distinct 16-byte bank groups (j0 is a multiple
+// of 16, so the rotation of column j0 + j is that of column j).  Its running sums stay in
+// acc[r][M]; wt_flush_cols adds the Q lanes of a column.
+template <typename T, int NR, int Q, int M>
+__device__ __forceinline__ void wt_cols_seg(const T* buf, int j0, int nseg, const T* rhs0, const T* rhs1,
+                                            T (&acc)[NR][kColsPerLane]) {
+  constexpr int NCH = WT<T>::NCH, VEC = WT<T>::VEC, S = NCH / Q, D = 8 / Q;
+  const int lane = threadIdx.x & 31, j = lane / Q, q = lane % Q;
+  if (j >= nseg) return;
+  const T* col = buf + (j0 + j) * 32;
+  T s[NR];
+#pragma unroll
+  for (int r = 0; r < NR; r++) s[r] = acc[r][M];
+#pragma unroll
+  for (int i = 0; i < S; i++) {
+    const int c = q * D + (i % D) + 8 * (i / D);
+    const Vec<T> v = *reinterpret_cast<const Vec<T>*>(col + ((c + j) & (NCH - 1)) * VEC);
+    const Vec<T> b0 = *reinterpret_cast<const Vec<T>*>(rhs0 + c * VEC);
+#pragma unroll
+    for (int e = 0; e < VEC; e++) s[0] = fma(v.e[e], b0.e[e], s[0]);
+    if (NR > 1) {
+      const Vec<T> b1 = *reinterpret_cast<const Vec<T>*>(rhs1 + c * VEC);
+#pragma unroll
+      for (int e = 0; e < VEC; e++) s[NR - 1] = fma(v.e[e], b1.e[e], s[NR - 1]);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < NR; r++) acc[r][M] = s[r];
+}
+template <typename T, int NR, int M>
+__device__ __forceinline__ void wt_cols_tail(const T* buf, int C, int j0, int nseg, const T* rhs0, const T* rhs1,
+                                             T (&acc)[NR][kColsPerLane]) {
+  switch (C) {   // uniform over the launch
+    case 4: wt_cols_seg<T, NR, 8, M>(buf, j0, nseg, rhs0, rhs1, acc); return;
+    case 8: wt_cols_seg<T, NR, 4, M>(buf, j0, nseg, rhs0, rhs1, acc); return;
+    default: wt_cols_seg<T, NR, 2, M>(buf, j0, nseg, rhs0, rhs1, acc); return;
+  }
+}
+
+// Column owner: acc[r][m] += sum_i V[i, lane + 32 m] rhs_r[i] over the 32 rows.  FP32 goes to
+// wt_cols_f32; FP64 takes the groups of 32 columns (two per lane while a second group exists),
+// then the tail segments of its layout.  Logical chunk c of column j sits at slot (c + j) mod
+// NCH, and j mod NCH = lane mod NCH for every m, so the NCH chunk offsets are per-lane
+// constants.  acc is in the storage type and covers at most kColFlush sub-tiles
+// (wt_flush_cols).
+template <typename T, int NR>
+__device__ __forceinline__ void wt_cols(const T* buf, int ncol, const T* rhs0, const T* rhs1,
+                                        T (&acc)[NR][kColsPerLane]) {
+  if constexpr (sizeof(T) == 4) {
+    wt_cols_f32<T, NR>(buf, ncol, rhs0, rhs1, acc);
+    return;
+  }
+  constexpr int NCH = WT<T>::NCH, VEC = WT<T>::VEC;
+  const ColLayout L = wt_col_layout(ncol);
+  const int lane = threadIdx.x & 31;
+  if (L.mfull > 0) {
+    int coff[NCH];
+#pragma unroll
+    for (int c = 0; c < NCH; c++) coff[c] = ((c + lane) & (NCH - 1)) * VEC;
+#pragma unroll
+    for (int m = 0; m < kColsPerLane; m += 2) {
+      if (m >= L.mfull) break;
+      if (m + 1 < L.mfull)   // warp-uniform
+        wt_col_pair<T, NR, true>(buf, ncol, m, coff, rhs0, rhs1, acc);
+      else
+        wt_col_pair<T, NR, false>(buf, ncol, m, coff, rhs0, rhs1, acc);
+    }
+  }
+  const int rem = ncol - 32 * L.mfull, j0 = 32 * L.mfull;
+  if (L.ca) wt_cols_tail<T, NR, kColsPerLane - 1>(buf, L.ca, j0, min(rem, 16), rhs0, rhs1, acc);
+  if (L.cb) wt_cols_tail<T, NR, kColsPerLane - 2>(buf, L.cb, j0 + 16, rem - 16, rhs0, rhs1, acc);
 }
 
 // The column owners' running sums in the storage type cover at most kColFlush sub-tiles
@@ -942,9 +1042,9 @@ __device__ __forceinline__ bool wt_flush_due(int it, int count) {
   return (it + 1) % kColFlush == 0 || it + 1 == count;
 }
 template <typename T, int NR>
-__device__ __forceinline__ void wt_flush_cols(T (&acc)[NR][kColsPerLane], double* comb, int ncolC) {
+__device__ __forceinline__ void wt_flush_cols_f32(T (&acc)[NR][kColsPerLane], double* comb, int ncolC) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int C = wt_col_slots(ncolC);
+  const int C = wt_col_slots_f32(ncolC);
   if (C) {   // wt_cols_grouped: add the Q = 32 / C lanes of each column (fixed order)
     const int Q = 32 / C, j = lane / Q;
 #pragma unroll
@@ -966,6 +1066,43 @@ __device__ __forceinline__ void wt_flush_cols(T (&acc)[NR][kColsPerLane], double
       acc[r][m] = T(0);
     }
   }
+}
+
+// A tail segment's running sums: add the Q lanes of each column (fixed order), then into comb.
+template <typename T, int NR, int M>
+__device__ __forceinline__ void wt_flush_seg(T (&acc)[NR][kColsPerLane], double* comb, int ncolC, int C, int j0,
+                                             int nseg) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int Q = 32 / C, j = lane / Q;
+#pragma unroll
+  for (int r = 0; r < NR; r++) {
+    T v = acc[r][M];
+    for (int o = Q >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane % Q == 0 && j < nseg) comb[((size_t)warp * NR + r) * ncolC + j0 + j] += (double)v;
+    acc[r][M] = T(0);
+  }
+}
+template <typename T, int NR>
+__device__ __forceinline__ void wt_flush_cols(T (&acc)[NR][kColsPerLane], double* comb, int ncolC) {
+  if constexpr (sizeof(T) == 4) {
+    wt_flush_cols_f32<T, NR>(acc, comb, ncolC);
+    return;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const ColLayout L = wt_col_layout(ncolC);
+#pragma unroll
+  for (int m = 0; m < kColsPerLane; m++) {
+    if (m >= L.mfull) break;
+    const int j = lane + 32 * m;
+#pragma unroll
+    for (int r = 0; r < NR; r++) {
+      if (j < ncolC) comb[((size_t)warp * NR + r) * ncolC + j] += (double)acc[r][m];
+      acc[r][m] = T(0);
+    }
+  }
+  const int rem = ncolC - 32 * L.mfull, j0 = 32 * L.mfull;
+  if (L.ca) wt_flush_seg<T, NR, kColsPerLane - 1>(acc, comb, ncolC, L.ca, j0, min(rem, 16));
+  if (L.cb) wt_flush_seg<T, NR, kColsPerLane - 2>(acc, comb, ncolC, L.cb, j0 + 16, rem - 16);
 }
 
 // Shared-memory layout of a sweep launch with W warps, each with nb pipeline stages of ncolT

@@ -762,6 +762,12 @@ __device__ __forceinline__ void cp_async_wait_dyn(int pending) {
   }
 }
 
+// FP32 dot-product steps as packed FMAs (two FP32 FMAs per instruction, sm_100 and later):
+// acc.x collects the even terms, acc.y the odd ones, added once at the end of a sub-tile.
+__device__ __forceinline__ float2 ffma2(float a0, float a1, float b0, float b1, float2 acc) {
+  return __ffma2_rn(make_float2(a0, a1), make_float2(b0, b1), acc);
+}
+
 // Row owner: out[o] = sum_j V[lane, j] coef_o[j], o < NO (coef arrays padded to NCH).
 // Column j = NCH g + u of the lane's row sits at NCH * 32 * g + off[u]; the NCH offsets of one
 // rotation period depend only on the lane.
@@ -778,19 +784,43 @@ __device__ __forceinline__ void wt_rows(const T* buf, int ncol, const T* coef0, 
   for (int o = 0; o < NO; o++) out[o] = T(0);
   const int ng = ncol / NCH;
   const T* base = buf;
-  for (int g = 0; g < ng; g++, base += NCH * 32) {
-    const T* c0 = coef0 + g * NCH;
-    const T* c1 = coef1 + g * NCH;
+  if constexpr (sizeof(T) == 4) {   // packed FMAs over pairs of columns
+    float2 p[NO];
 #pragma unroll
-    for (int u0 = 0; u0 < NCH; u0 += VEC) {
-      const Vec<T> a0 = *reinterpret_cast<const Vec<T>*>(c0 + u0);
-      Vec<T> a1;
-      if (NO > 1) a1 = *reinterpret_cast<const Vec<T>*>(c1 + u0);
+    for (int o = 0; o < NO; o++) p[o] = make_float2(0.f, 0.f);
+    for (int g = 0; g < ng; g++, base += NCH * 32) {
+      const T* c0 = coef0 + g * NCH;
+      const T* c1 = coef1 + g * NCH;
 #pragma unroll
-      for (int e = 0; e < VEC; e++) {
-        const T v = base[off[u0 + e]];
-        out[0] = fma(v, a0.e[e], out[0]);
-        if (NO > 1) out[NO - 1] = fma(v, a1.e[e], out[NO - 1]);
+      for (int u0 = 0; u0 < NCH; u0 += VEC) {
+        const Vec<T> a0 = *reinterpret_cast<const Vec<T>*>(c0 + u0);
+        Vec<T> a1;
+        if (NO > 1) a1 = *reinterpret_cast<const Vec<T>*>(c1 + u0);
+#pragma unroll
+        for (int e = 0; e < VEC; e += 2) {
+          const T v0 = base[off[u0 + e]], v1 = base[off[u0 + e + 1]];
+          p[0] = ffma2(v0, v1, a0.e[e], a0.e[e + 1], p[0]);
+          if (NO > 1) p[NO - 1] = ffma2(v0, v1, a1.e[e], a1.e[e + 1], p[NO - 1]);
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 0; o < NO; o++) out[o] = p[o].x + p[o].y;
+  } else {
+    for (int g = 0; g < ng; g++, base += NCH * 32) {
+      const T* c0 = coef0 + g * NCH;
+      const T* c1 = coef1 + g * NCH;
+#pragma unroll
+      for (int u0 = 0; u0 < NCH; u0 += VEC) {
+        const Vec<T> a0 = *reinterpret_cast<const Vec<T>*>(c0 + u0);
+        Vec<T> a1;
+        if (NO > 1) a1 = *reinterpret_cast<const Vec<T>*>(c1 + u0);
+#pragma unroll
+        for (int e = 0; e < VEC; e++) {
+          const T v = base[off[u0 + e]];
+          out[0] = fma(v, a0.e[e], out[0]);
+          if (NO > 1) out[NO - 1] = fma(v, a1.e[e], out[NO - 1]);
+        }
       }
     }
   }
@@ -824,38 +854,72 @@ __device__ __forceinline__ void wt_col_pair(const T* buf, int ncol, int m, const
   const int j0 = lane + 32 * m, j1 = j0 + 32;
   const bool h1 = TWO && j1 < ncol;
   if (j0 >= ncol) return;
-  T s0[NR], s1[NR];   // the running sums themselves (no separate add per sub-tile)
-#pragma unroll
-  for (int r = 0; r < NR; r++) {
-    s0[r] = acc[r][m];
-    s1[r] = (TWO && h1) ? acc[r][m + 1] : T(0);
-  }
   const T* col0 = buf + j0 * 32;
   const T* col1 = buf + (h1 ? j1 : j0) * 32;
+  if constexpr (sizeof(T) == 4) {   // packed FMAs over pairs of rows
+    float2 q0[NR], q1[NR];
 #pragma unroll
-  for (int c = 0; c < NCH; c++) {
-    const Vec<T> v0 = *reinterpret_cast<const Vec<T>*>(col0 + coff[c]);
-    Vec<T> v1;
-    if (TWO) v1 = *reinterpret_cast<const Vec<T>*>(col1 + coff[c]);
-    const Vec<T> b0 = *reinterpret_cast<const Vec<T>*>(rhs0 + c * VEC);
-#pragma unroll
-    for (int e = 0; e < VEC; e++) {
-      s0[0] = fma(v0.e[e], b0.e[e], s0[0]);
-      if (TWO) s1[0] = fma(v1.e[e], b0.e[e], s1[0]);
+    for (int r = 0; r < NR; r++) {
+      q0[r] = make_float2(acc[r][m], 0.f);
+      q1[r] = make_float2((TWO && h1) ? acc[r][m + 1] : 0.f, 0.f);
     }
-    if (NR > 1) {
-      const Vec<T> b1 = *reinterpret_cast<const Vec<T>*>(rhs1 + c * VEC);
 #pragma unroll
-      for (int e = 0; e < VEC; e++) {
-        s0[NR - 1] = fma(v0.e[e], b1.e[e], s0[NR - 1]);
-        if (TWO) s1[NR - 1] = fma(v1.e[e], b1.e[e], s1[NR - 1]);
+    for (int c = 0; c < NCH; c++) {
+      const Vec<T> v0 = *reinterpret_cast<const Vec<T>*>(col0 + coff[c]);
+      Vec<T> v1;
+      if (TWO) v1 = *reinterpret_cast<const Vec<T>*>(col1 + coff[c]);
+      const Vec<T> b0 = *reinterpret_cast<const Vec<T>*>(rhs0 + c * VEC);
+#pragma unroll
+      for (int e = 0; e < VEC; e += 2) {
+        q0[0] = ffma2(v0.e[e], v0.e[e + 1], b0.e[e], b0.e[e + 1], q0[0]);
+        if (TWO) q1[0] = ffma2(v1.e[e], v1.e[e + 1], b0.e[e], b0.e[e + 1], q1[0]);
+      }
+      if (NR > 1) {
+        const Vec<T> b1 = *reinterpret_cast<const Vec<T>*>(rhs1 + c * VEC);
+#pragma unroll
+        for (int e = 0; e < VEC; e += 2) {
+          q0[NR - 1] = ffma2(v0.e[e], v0.e[e + 1], b1.e[e], b1.e[e + 1], q0[NR - 1]);
+          if (TWO) q1[NR - 1] = ffma2(v1.e[e], v1.e[e + 1], b1.e[e], b1.e[e + 1], q1[NR - 1]);
+        }
       }
     }
-  }
 #pragma unroll
-  for (int r = 0; r < NR; r++) {
-    acc[r][m] = s0[r];
-    if (TWO && h1) acc[r][m + 1] = s1[r];
+    for (int r = 0; r < NR; r++) {
+      acc[r][m] = q0[r].x + q0[r].y;
+      if (TWO && h1) acc[r][m + 1] = q1[r].x + q1[r].y;
+    }
+  } else {
+    T s0[NR], s1[NR];   // the running sums themselves (no separate add per sub-tile)
+#pragma unroll
+    for (int r = 0; r < NR; r++) {
+      s0[r] = acc[r][m];
+      s1[r] = (TWO && h1) ? acc[r][m + 1] : T(0);
+    }
+#pragma unroll
+    for (int c = 0; c < NCH; c++) {
+      const Vec<T> v0 = *reinterpret_cast<const Vec<T>*>(col0 + coff[c]);
+      Vec<T> v1;
+      if (TWO) v1 = *reinterpret_cast<const Vec<T>*>(col1 + coff[c]);
+      const Vec<T> b0 = *reinterpret_cast<const Vec<T>*>(rhs0 + c * VEC);
+#pragma unroll
+      for (int e = 0; e < VEC; e++) {
+        s0[0] = fma(v0.e[e], b0.e[e], s0[0]);
+        if (TWO) s1[0] = fma(v1.e[e], b0.e[e], s1[0]);
+      }
+      if (NR > 1) {
+        const Vec<T> b1 = *reinterpret_cast<const Vec<T>*>(rhs1 + c * VEC);
+#pragma unroll
+        for (int e = 0; e < VEC; e++) {
+          s0[NR - 1] = fma(v0.e[e], b1.e[e], s0[NR - 1]);
+          if (TWO) s1[NR - 1] = fma(v1.e[e], b1.e[e], s1[NR - 1]);
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < NR; r++) {
+      acc[r][m] = s0[r];
+      if (TWO && h1) acc[r][m + 1] = s1[r];
+    }
   }
 }
 
@@ -876,24 +940,24 @@ __device__ __forceinline__ void wt_cols_grouped_f32(const T* buf, int ncol, cons
   const int lane = threadIdx.x & 31, j = lane / Q, q = lane % Q;
   if (j >= ncol) return;
   const T* col = buf + j * 32;
-  T s[NR];
+  float2 s[NR];   // packed FMAs over pairs of rows
 #pragma unroll
-  for (int r = 0; r < NR; r++) s[r] = acc[r][0];
+  for (int r = 0; r < NR; r++) s[r] = make_float2(acc[r][0], 0.f);
 #pragma unroll
   for (int i = 0; i < S; i++) {
     const int c = q * D + (i % D) + 8 * (i / D);
     const Vec<T> v = *reinterpret_cast<const Vec<T>*>(col + ((c + j) & (NCH - 1)) * VEC);
     const Vec<T> b0 = *reinterpret_cast<const Vec<T>*>(rhs0 + c * VEC);
 #pragma unroll
-    for (int e = 0; e < VEC; e++) s[0] = fma(v.e[e], b0.e[e], s[0]);
+    for (int e = 0; e < VEC; e += 2) s[0] = ffma2(v.e[e], v.e[e + 1], b0.e[e], b0.e[e + 1], s[0]);
     if (NR > 1) {
       const Vec<T> b1 = *reinterpret_cast<const Vec<T>*>(rhs1 + c * VEC);
 #pragma unroll
-      for (int e = 0; e < VEC; e++) s[NR - 1] = fma(v.e[e], b1.e[e], s[NR - 1]);
+      for (int e = 0; e < VEC; e += 2) s[NR - 1] = ffma2(v.e[e], v.e[e + 1], b1.e[e], b1.e[e + 1], s[NR - 1]);
     }
   }
 #pragma unroll
-  for (int r = 0; r < NR; r++) acc[r][0] = s[r];
+  for (int r = 0; r < NR; r++) acc[r][0] = s[r].x + s[r].y;
 }
 
 // More than 16 columns: column lane + 32 m in slot m, two per lane while a second one exists

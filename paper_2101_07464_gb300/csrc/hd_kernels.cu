@@ -696,7 +696,15 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 
 // Copy rows [r0, r0 + 32) of ncol columns into a warp stage (no commit).  Lane l always
-// copies chunk q = l mod NCH of the columns l / NCH, l / NCH + 32 / NCH, ...
+// copies chunk q = l mod NCH of the columns l / NCH, l / NCH + 32 / NCH, ...  Staged layout:
+// column j at 32 j.  In FP64 chunk c of column j sits at slot (c + j) mod NCH (rotated); in
+// FP32 at slot c (plain), and the column owners visit the chunks in rotated order instead
+// (wt_col_pair), which keeps the same bank pattern and lets the row owners read at constant
+// offsets (wt_rows).
+template <typename T>
+__device__ __forceinline__ int wt_slot(int c, int j) {
+  return sizeof(T) == 4 ? c : ((c + j) & (WT<T>::NCH - 1));
+}
 template <typename T>
 __device__ __forceinline__ void wt_load_cols(T* buf, const ColSrc<T>& src, int ncol, int64_t r0) {
   constexpr int NCH = WT<T>::NCH, VEC = WT<T>::VEC, CPI = 32 / NCH;
@@ -708,12 +716,12 @@ __device__ __forceinline__ void wt_load_cols(T* buf, const ColSrc<T>& src, int n
   {
     const T* g = src.A + (int64_t)j * src.ldA + r0 + q * VEC;
     const int64_t gstep = (int64_t)CPI * src.ldA;
-    for (; j < nA; j += CPI, g += gstep) cp_async16_stream(buf + j * 32 + ((q + j) & (NCH - 1)) * VEC, g, pol);
+    for (; j < nA; j += CPI, g += gstep) cp_async16_stream(buf + j * 32 + wt_slot<T>(q, j) * VEC, g, pol);
   }
   if (j < ncol) {
     const T* g = src.B + (int64_t)(j - src.nA) * src.ldB + r0 + q * VEC;
     const int64_t gstep = (int64_t)CPI * src.ldB;
-    for (; j < ncol; j += CPI, g += gstep) cp_async16_stream(buf + j * 32 + ((q + j) & (NCH - 1)) * VEC, g, pol);
+    for (; j < ncol; j += CPI, g += gstep) cp_async16_stream(buf + j * 32 + wt_slot<T>(q, j) * VEC, g, pol);
   }
 }
 __device__ __forceinline__ void cp_async16_zfill(void* smem, const void* gmem, int src_bytes) {
@@ -769,7 +777,8 @@ __device__ __forceinline__ float2 ffma2(float a0, float a1, float b0, float b1, 
 }
 
 // Row owner: out[o] = sum_j V[lane, j] coef_o[j], o < NO (coef arrays padded to NCH).
-// Column j = NCH g + u of the lane's row sits at NCH * 32 * g + off[u]; the NCH offsets of one
+// FP32 (plain layout): row lane of column j sits at 32 j + lane.  FP64 (rotated): column
+// j = NCH g + u of the lane's row sits at NCH * 32 * g + off[u]; the NCH offsets of one
 // rotation period depend only on the lane.
 template <typename T, int NO>
 __device__ __forceinline__ void wt_rows(const T* buf, int ncol, const T* coef0, const T* coef1,
@@ -784,11 +793,12 @@ __device__ __forceinline__ void wt_rows(const T* buf, int ncol, const T* coef0, 
   for (int o = 0; o < NO; o++) out[o] = T(0);
   const int ng = ncol / NCH;
   const T* base = buf;
-  if constexpr (sizeof(T) == 4) {   // packed FMAs over pairs of columns
-    float2 p[NO];
+  if constexpr (sizeof(T) == 4) {   // plain layout: row lane of column u at 32 u + lane
+    float2 p[NO];   // packed FMAs over pairs of columns
 #pragma unroll
     for (int o = 0; o < NO; o++) p[o] = make_float2(0.f, 0.f);
-    for (int g = 0; g < ng; g++, base += NCH * 32) {
+    const T* bl = buf + lane;
+    for (int g = 0; g < ng; g++, bl += NCH * 32) {
       const T* c0 = coef0 + g * NCH;
       const T* c1 = coef1 + g * NCH;
 #pragma unroll
@@ -798,7 +808,7 @@ __device__ __forceinline__ void wt_rows(const T* buf, int ncol, const T* coef0, 
         if (NO > 1) a1 = *reinterpret_cast<const Vec<T>*>(c1 + u0);
 #pragma unroll
         for (int e = 0; e < VEC; e += 2) {
-          const T v0 = base[off[u0 + e]], v1 = base[off[u0 + e + 1]];
+          const T v0 = bl[(u0 + e) * 32], v1 = bl[(u0 + e + 1) * 32];
           p[0] = ffma2(v0, v1, a0.e[e], a0.e[e + 1], p[0]);
           if (NO > 1) p[NO - 1] = ffma2(v0, v1, a1.e[e], a1.e[e + 1], p[NO - 1]);
         }
@@ -831,7 +841,7 @@ __device__ __forceinline__ void wt_rows(const T* buf, int ncol, const T* coef0, 
 #pragma unroll
     for (int u = 0; u < NCH; u++) {
       if (u < rem) {
-        const T v = base[off[u]];
+        const T v = (sizeof(T) == 4) ? buf[(ng * NCH + u) * 32 + lane] : base[off[u]];
         out[0] = fma(v, c0[u], out[0]);
         if (NO > 1) out[NO - 1] = fma(v, c1[u], out[NO - 1]);
       }
@@ -842,9 +852,11 @@ __device__ __forceinline__ void wt_rows(const T* buf, int ncol, const T* coef0, 
 constexpr int kColsPerLane = 8;   // column owner: up to 8 * 32 = 256 columns
 
 // Column owner: acc[r][m] += sum_i V[i, lane + 32 m] rhs_r[i] over the 32 rows, m < 8.
-// Logical chunk c of column j sits at slot (c + j) mod NCH, and j mod NCH = lane mod NCH for
-// every m, so the NCH chunk offsets are per-lane constants.  acc is in the storage type and
-// covers at most kColFlush sub-tiles (wt_flush_cols).
+// Step c reads slot coff[c] = (c + lane) mod NCH of the lane's columns (j mod NCH = lane mod
+// NCH for every m), so the 8 lanes of a quarter warp read 8 distinct 16-byte bank groups.  In
+// FP64 (rotated layout) that slot holds logical chunk c; in FP32 (plain layout) it holds chunk
+// coff[c], and the same slot of the right-hand sides is read with it.  acc is in the storage
+// type and covers at most kColFlush sub-tiles (wt_flush_cols).
 // Columns j0 = lane + 32 m and (TWO) j1 = j0 + 32 of the sub-tile against the right-hand sides.
 template <typename T, int NR, bool TWO>
 __device__ __forceinline__ void wt_col_pair(const T* buf, int ncol, int m, const int (&coff)[WT<T>::NCH],
@@ -868,14 +880,14 @@ __device__ __forceinline__ void wt_col_pair(const T* buf, int ncol, int m, const
       const Vec<T> v0 = *reinterpret_cast<const Vec<T>*>(col0 + coff[c]);
       Vec<T> v1;
       if (TWO) v1 = *reinterpret_cast<const Vec<T>*>(col1 + coff[c]);
-      const Vec<T> b0 = *reinterpret_cast<const Vec<T>*>(rhs0 + c * VEC);
+      const Vec<T> b0 = *reinterpret_cast<const Vec<T>*>(rhs0 + coff[c]);
 #pragma unroll
       for (int e = 0; e < VEC; e += 2) {
         q0[0] = ffma2(v0.e[e], v0.e[e + 1], b0.e[e], b0.e[e + 1], q0[0]);
         if (TWO) q1[0] = ffma2(v1.e[e], v1.e[e + 1], b0.e[e], b0.e[e + 1], q1[0]);
       }
       if (NR > 1) {
-        const Vec<T> b1 = *reinterpret_cast<const Vec<T>*>(rhs1 + c * VEC);
+        const Vec<T> b1 = *reinterpret_cast<const Vec<T>*>(rhs1 + coff[c]);
 #pragma unroll
         for (int e = 0; e < VEC; e += 2) {
           q0[NR - 1] = ffma2(v0.e[e], v0.e[e + 1], b1.e[e], b1.e[e + 1], q0[NR - 1]);
@@ -925,8 +937,10 @@ __device__ __forceinline__ void wt_col_pair(const T* buf, int ncol, int m, const
 
 // The FP32 column pass (wt_cols in FP32).  Few columns (ncol <= 16): Q = 32 / C lanes per
 // column (C = 4, 8 or 16 column slots), lane = j Q + q.  Lane (j, q) takes NCH / Q chunks of
-// column j, chunk q D + (i mod D) + 8 (i div D) at step i (D = 8 / Q), so that the 8 lanes of
-// every quarter warp read 8 distinct 16-byte bank groups.  Its running sums stay in acc[r][0];
+// column j, slot (c + j) mod NCH with c = q D + (i mod D) + 8 (i div D) at step i (D = 8 / Q),
+// so that the 8 lanes of every quarter warp read 8 distinct 16-byte bank groups; in the plain
+// FP32 layout the slot is the chunk, and the same chunk of the right-hand sides is read with
+// it.  Its running sums stay in acc[r][0];
 // wt_flush_cols_f32 adds the Q lanes of a column.  (The same scheme as wt_cols_seg, kept apart:
 // the FP32 sweeps, bound by instruction issue with 128 registers, lose a few per cent to the
 // register allocation that the shared form leads to.)
@@ -946,12 +960,13 @@ __device__ __forceinline__ void wt_cols_grouped_f32(const T* buf, int ncol, cons
 #pragma unroll
   for (int i = 0; i < S; i++) {
     const int c = q * D + (i % D) + 8 * (i / D);
-    const Vec<T> v = *reinterpret_cast<const Vec<T>*>(col + ((c + j) & (NCH - 1)) * VEC);
-    const Vec<T> b0 = *reinterpret_cast<const Vec<T>*>(rhs0 + c * VEC);
+    const int sl = ((c + j) & (NCH - 1)) * VEC;   // plain layout: chunk (c + j) mod NCH
+    const Vec<T> v = *reinterpret_cast<const Vec<T>*>(col + sl);
+    const Vec<T> b0 = *reinterpret_cast<const Vec<T>*>(rhs0 + sl);
 #pragma unroll
     for (int e = 0; e < VEC; e += 2) s[0] = ffma2(v.e[e], v.e[e + 1], b0.e[e], b0.e[e + 1], s[0]);
     if (NR > 1) {
-      const Vec<T> b1 = *reinterpret_cast<const Vec<T>*>(rhs1 + c * VEC);
+      const Vec<T> b1 = *reinterpret_cast<const Vec<T>*>(rhs1 + sl);
 #pragma unroll
       for (int e = 0; e < VEC; e += 2) s[NR - 1] = ffma2(v.e[e], v.e[e + 1], b1.e[e], b1.e[e + 1], s[NR - 1]);
     }

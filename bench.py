@@ -254,11 +254,11 @@ class ClockSampler:
 
 # DRAM bytes / algorithmic bytes of one launch of the dominant kernel, from an ncu capture of
 # the current kernel at k = 60, n = 10^6; None until a capture of the current kernel exists.
-# (FP32: 245.57 MB for 248.0 MB at k = 59; FP64: 494.20 MB for 504.0 MB at k = 60.)
-TRAFFIC_RATIO = {"f32": 245.57 / 248.0, "f64": 494.20 / 504.0}
+# (FP32: 250.60 MB for 252.0 MB at k = 60; FP64: 494.20 MB for 504.0 MB at k = 60.)
+TRAFFIC_RATIO = {"f32": 250.60 / 252.0, "f64": 494.20 / 504.0}
 TRAFFIC_KERNEL = "update"
 TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_update launch "
-                  "(k = 59 in FP32, k = 60 in FP64, n = 10^6, same dtype), scaled to the average "
+                  "(k = 60, n = 10^6, same dtype), scaled to the average "
                   "launch by algorithmic bytes")
 
 # Algorithmic FP64 flops per stack element of each sweep in the fused Q / Q^T alternating
